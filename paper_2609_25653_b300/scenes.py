@@ -1,0 +1,325 @@
+"""Seeded synthetic scene generators (inputs only).
+
+This module produces the geometry, materials, kinematic trajectories and
+parameters of the grasp scenes that the IPC step (Eq. 3, §III-C.2) is run on.
+It holds none of the method's arithmetic: no surface extraction, no rest
+shape matrices, no masses, no energies.  Both the CUDA path and the CPU
+oracle consume the dictionaries it returns.
+
+Random numbers come from splitmix64 (Steele, Lea, Flood 2014), written out
+here from its published definition so any consumer can regenerate them.
+
+Units are SI (metres, seconds, kilograms, pascals).
+
+A scene dictionary has the keys
+
+  fem_X      (nv, 3) float64  rest = initial positions of all FEM vertices
+  fem_tets   (nt, 4) int32    tetrahedra, positively oriented
+  fem_logE   (nt,)   float64  natural log of Young's modulus per tet
+  fem_nu     (nt,)   float64  Poisson ratio per tet
+  fem_rho    (nt,)   float64  density per tet
+  fem_body   (nt,)   int32    FEM body id per tet (fingertip 0, 1, object ...)
+  kin        list of {"X": (n,3) local rest vertices, "tris": (m,3) int32}
+  kin_T      (n_steps + 1, n_kin, 3, 4) rigid transforms [R | t] per step
+  abd        list of {"X": (n,3) body-frame vertices, "tris": (m,3) int32,
+                      "rho": float, "q0": (12,) [p, A[:,0], A[:,1], A[:,2]]}
+  stitch_v   (ns,) int32      FEM vertex of each stitch spring (Eq. 2)
+  stitch_b   (ns,) int32      kinematic body carrying the anchor
+  stitch_X   (ns, 3) float64  anchor point in that body's local frame
+  gravity    (3,) float64
+  params     dict of scalar parameters (see ``default_params``)
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """splitmix64: state += golden gamma, then two xor-shift-multiply rounds."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, n: int) -> np.ndarray:
+        """n doubles in [0, 1): top 53 bits of each draw times 2^-53."""
+        out = np.empty(n, dtype=np.float64)
+        for i in range(n):
+            out[i] = (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+        return out
+
+    def normal(self, n: int) -> np.ndarray:
+        """n standard normals by Box-Muller on pairs of uniforms."""
+        m = (n + 1) // 2
+        u = self.uniform(2 * m)
+        u1 = 1.0 - u[0::2]
+        u2 = u[1::2]
+        r = np.sqrt(-2.0 * np.log(u1))
+        z = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
+        return z[:n]
+
+
+def default_params(**kw) -> dict:
+    p = dict(
+        dt=1e-2,          # time step (s)
+        dhat=1e-3,        # barrier activation distance (m)
+        kappa=0.0,        # barrier stiffness; 0 = auto-scaled at create
+        mu=0.5,           # friction coefficient
+        eps_v=1e-3,       # friction static-velocity threshold (m/s)
+        k_c=0.0,          # stitch stiffness (N/m); 0 = auto
+        kappa_A=1e8,      # ABD orthogonality stiffness (Pa)
+        newton_tol=1e-6,  # ||p||_inf / (dt * L_bbox)
+        pcg_rtol=1e-4,
+        max_newton=100,
+        max_pcg=0,        # 0 = 10 * sqrt(n_dof)
+        s_ccd=0.1,        # ACCD minimum-separation fraction
+        n_steps=20,
+    )
+    p.update(kw)
+    return p
+
+
+# ----------------------------------------------------------------------------
+# mesh builders
+# ----------------------------------------------------------------------------
+
+def grid_tets(origin, cell, nx, ny, nz):
+    """Regular grid of cubes, each cut into 6 tets around its main diagonal.
+
+    The split follows the Kuhn (Freudenthal) scheme: every cube uses the same
+    diagonal from corner (0,0,0) to (1,1,1), which makes the mesh conforming.
+    Returns (verts (nv,3), tets (nt,4) int32), tets positively oriented.
+    """
+    ox, oy, oz = origin
+    hx, hy, hz = cell if np.ndim(cell) else (cell, cell, cell)
+    ii, jj, kk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    verts = np.stack([ox + ii * hx, oy + jj * hy, oz + kk * hz], axis=-1)
+    verts = verts.transpose(2, 1, 0, 3).reshape(-1, 3)  # index = i + (nx+1)(j + (ny+1)k)
+
+    def vid(i, j, k):
+        return i + (nx + 1) * (j + (ny + 1) * k)
+
+    perms = [(0, 1, 2, +1), (1, 2, 0, +1), (2, 0, 1, +1), (0, 2, 1, -1), (2, 1, 0, -1), (1, 0, 2, -1)]
+    tets = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                for a0, a1, a2, sgn in perms:
+                    c0 = [0, 0, 0]
+                    c1 = list(c0); c1[a0] = 1
+                    c2 = list(c1); c2[a1] = 1
+                    c3 = [1, 1, 1]
+                    v = [vid(i + c[0], j + c[1], k + c[2]) for c in (c0, c1, c2, c3)]
+                    if sgn < 0:
+                        v[1], v[2] = v[2], v[1]
+                    tets.append(v)
+    return verts.astype(np.float64), np.asarray(tets, dtype=np.int32)
+
+
+def box_surface(lo, hi):
+    """Closed box surface: 8 verts, 12 outward-facing triangles."""
+    x0, y0, z0 = lo
+    x1, y1, z1 = hi
+    v = np.array([[x0, y0, z0], [x1, y0, z0], [x1, y1, z0], [x0, y1, z0],
+                  [x0, y0, z1], [x1, y0, z1], [x1, y1, z1], [x0, y1, z1]], dtype=np.float64)
+    t = np.array([[0, 2, 1], [0, 3, 2],   # bottom (-z)
+                  [4, 5, 6], [4, 6, 7],   # top (+z)
+                  [0, 1, 5], [0, 5, 4],   # -y
+                  [2, 3, 7], [2, 7, 6],   # +y
+                  [1, 2, 6], [1, 6, 5],   # +x
+                  [3, 0, 4], [3, 4, 7]],  # -x
+                 dtype=np.int32)
+    return v, t
+
+
+def uv_ellipsoid(a, b, c, n_lat, n_lon):
+    """Closed ellipsoid surface, outward triangles, 2 + (n_lat-1) n_lon verts."""
+    verts = [[0.0, 0.0, c]]
+    for i in range(1, n_lat):
+        th = math.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2 * math.pi * j / n_lon
+            verts.append([a * math.sin(th) * math.cos(ph), b * math.sin(th) * math.sin(ph), c * math.cos(th)])
+    verts.append([0.0, 0.0, -c])
+    tris = []
+    for j in range(n_lon):
+        tris.append([0, 1 + j, 1 + (j + 1) % n_lon])
+    for i in range(n_lat - 2):
+        r0 = 1 + i * n_lon
+        r1 = r0 + n_lon
+        for j in range(n_lon):
+            j1 = (j + 1) % n_lon
+            tris.append([r0 + j, r1 + j, r1 + j1])
+            tris.append([r0 + j, r1 + j1, r0 + j1])
+    last = len(verts) - 1
+    r0 = 1 + (n_lat - 2) * n_lon
+    for j in range(n_lon):
+        tris.append([last, r0 + (j + 1) % n_lon, r0 + j])
+    return np.asarray(verts, dtype=np.float64), np.asarray(tris, dtype=np.int32)
+
+
+def superellipsoid_capsule(rx, ry, length, n_ring, n_seg, expo=2.5):
+    """Convex-ish link shell: super-elliptic cross-section swept along z, hemispherical-ish caps."""
+    verts = []
+    n_cap = max(2, n_ring // 4)
+    rings = []
+    for i in range(n_cap, 0, -1):  # bottom cap
+        th = 0.5 * math.pi * i / (n_cap + 1)
+        rings.append((math.cos(th), -math.sin(th) * min(rx, ry)))
+    for i in range(n_seg + 1):
+        rings.append((1.0, length * i / n_seg))
+    for i in range(1, n_cap + 1):  # top cap
+        th = 0.5 * math.pi * i / (n_cap + 1)
+        rings.append((math.cos(th), length + math.sin(th) * min(rx, ry)))
+    verts.append([0.0, 0.0, -min(rx, ry)])
+    for scale, z in rings:
+        for j in range(n_ring):
+            ph = 2 * math.pi * j / n_ring
+            c, s = math.cos(ph), math.sin(ph)
+            e = 2.0 / expo
+            x = rx * scale * math.copysign(abs(c) ** e, c)
+            y = ry * scale * math.copysign(abs(s) ** e, s)
+            verts.append([x, y, z])
+    verts.append([0.0, 0.0, length + min(rx, ry)])
+    nr = len(rings)
+    tris = []
+    for j in range(n_ring):
+        tris.append([0, 1 + (j + 1) % n_ring, 1 + j])
+    for i in range(nr - 1):
+        r0 = 1 + i * n_ring
+        r1 = r0 + n_ring
+        for j in range(n_ring):
+            j1 = (j + 1) % n_ring
+            tris.append([r0 + j, r0 + j1, r1 + j1])
+            tris.append([r0 + j, r1 + j1, r1 + j])
+    last = len(verts) - 1
+    r0 = 1 + (nr - 1) * n_ring
+    for j in range(n_ring):
+        tris.append([last, r0 + j, r0 + (j + 1) % n_ring])
+    return np.asarray(verts, dtype=np.float64), np.asarray(tris, dtype=np.int32)
+
+
+def translation(t):
+    T = np.zeros((3, 4))
+    T[:, :3] = np.eye(3)
+    T[:, 3] = t
+    return T
+
+
+def rot_z(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, -s, 0], [s, c, 0], [0, 0, 1.0]])
+
+
+def rot_y(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]])
+
+
+def rot_x(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[1, 0, 0], [0, c, -s], [0, s, c]])
+
+
+def _empty_stitch():
+    return (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros((0, 3)))
+
+
+# ----------------------------------------------------------------------------
+# workload 1: one soft fingertip pressed by a plate onto a fixed cube
+# ----------------------------------------------------------------------------
+
+def fingertip_press(seed: int = 0, n_steps: int = 20, **param_overrides) -> dict:
+    """10 x 6 x 20 mm soft box (5 x 3 x 10 cubes, 6 tets each: 264 verts, 900 tets).
+
+    E = 1e5 Pa, nu = 0.45, rho = 1100 kg/m^3.  The box stands 0.5 mm above a
+    fixed 30 mm rigid cube (top face at z = 0).  A 30 x 30 x 2 mm kinematic
+    plate starts 0.5 mm above the box top and moves down 0.1 mm per step
+    (2 mm over 20 steps).  Every rest coordinate gets uniform +/- 0.1 mm
+    jitter from splitmix64(seed); rest = initial, so the box starts unstressed.
+    """
+    mm = 1e-3
+    X, tets = grid_tets((-5 * mm, -3 * mm, 0.5 * mm), 2 * mm, 5, 3, 10)
+    rng = SplitMix64(seed)
+    X = X + (2.0 * rng.uniform(X.size).reshape(X.shape) - 1.0) * 0.1 * mm
+    nt = tets.shape[0]
+    cube_X, cube_T = box_surface((-15 * mm, -15 * mm, -30 * mm), (15 * mm, 15 * mm, 0.0))
+    plate_X, plate_T = box_surface((-15 * mm, -15 * mm, 0.0), (15 * mm, 15 * mm, 2 * mm))
+    kin_T = np.zeros((n_steps + 1, 2, 3, 4))
+    for s in range(n_steps + 1):
+        kin_T[s, 0] = translation((0.0, 0.0, 0.0))
+        kin_T[s, 1] = translation((0.0, 0.0, 21 * mm - 0.1 * mm * s))
+    sv, sb, sx = _empty_stitch()
+    params = default_params(dt=1e-2, dhat=1e-3, mu=0.5, newton_tol=1e-6, n_steps=n_steps)
+    params.update(param_overrides)
+    return dict(
+        name="fingertip_press_900tet",
+        fem_X=X, fem_tets=tets,
+        fem_logE=np.full(nt, math.log(1e5)), fem_nu=np.full(nt, 0.45), fem_rho=np.full(nt, 1100.0),
+        fem_body=np.zeros(nt, np.int32),
+        kin=[dict(X=cube_X, tris=cube_T), dict(X=plate_X, tris=plate_T)],
+        kin_T=kin_T,
+        abd=[],
+        stitch_v=sv, stitch_b=sb, stitch_X=sx,
+        gravity=np.array([0.0, 0.0, -9.81]),
+        params=params,
+    )
+
+
+def free_block(n_steps: int = 5, v0=(0.0, 0.0, 0.0), **param_overrides) -> dict:
+    """A 2 x 2 x 2 mm single-cube block (6 tets) with no obstacles: free fall."""
+    mm = 1e-3
+    X, tets = grid_tets((0.0, 0.0, 0.0), 2 * mm, 1, 1, 1)
+    nt = tets.shape[0]
+    sv, sb, sx = _empty_stitch()
+    params = default_params(n_steps=n_steps)
+    params.update(param_overrides)
+    sc = dict(
+        name="free_block",
+        fem_X=X, fem_tets=tets,
+        fem_logE=np.full(nt, math.log(1e5)), fem_nu=np.full(nt, 0.45), fem_rho=np.full(nt, 1100.0),
+        fem_body=np.zeros(nt, np.int32),
+        kin=[], kin_T=np.zeros((n_steps + 1, 0, 3, 4)), abd=[],
+        stitch_v=sv, stitch_b=sb, stitch_X=sx,
+        gravity=np.array([0.0, 0.0, -9.81]),
+        params=params,
+    )
+    sc["fem_V0"] = np.tile(np.asarray(v0, dtype=np.float64), (X.shape[0], 1))
+    return sc
+
+
+def block_on_plane(n_steps: int = 10, tilt: float = 0.0, mu: float = 0.5, **param_overrides) -> dict:
+    """4 x 4 x 4 mm block (4^3 cubes of 1 mm) starting 0.3 mm above a fixed plane tilted by `tilt` about y."""
+    mm = 1e-3
+    X, tets = grid_tets((-2 * mm, -2 * mm, 0.3 * mm), 1 * mm, 4, 4, 4)
+    nt = tets.shape[0]
+    # one large ground triangle whose edges are all far from the block
+    gX = np.array([[-50 * mm, -50 * mm, 0.0], [250 * mm, -50 * mm, 0.0], [-50 * mm, 250 * mm, 0.0]])
+    gT = np.array([[0, 1, 2]], dtype=np.int32)
+    R = rot_y(tilt)
+    X = X @ R.T
+    kin_T = np.zeros((n_steps + 1, 1, 3, 4))
+    for s in range(n_steps + 1):
+        kin_T[s, 0, :, :3] = R
+    sv, sb, sx = _empty_stitch()
+    params = default_params(dt=1e-2, dhat=2e-4, mu=mu, n_steps=n_steps)
+    params.update(param_overrides)
+    return dict(
+        name="block_on_plane",
+        fem_X=X, fem_tets=tets,
+        fem_logE=np.full(nt, math.log(1e5)), fem_nu=np.full(nt, 0.4), fem_rho=np.full(nt, 1000.0),
+        fem_body=np.zeros(nt, np.int32),
+        kin=[dict(X=gX, tris=gT)], kin_T=kin_T, abd=[],
+        stitch_v=sv, stitch_b=sb, stitch_X=sx,
+        gravity=np.array([0.0, 0.0, -9.81]),
+        params=params,
+    )
