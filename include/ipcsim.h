@@ -1,0 +1,208 @@
+/* ipcsim: one IPC time step on one GPU (sm_103a), behind a plain C ABI.
+ *
+ * What a step computes (Eq. 3 and §III-C.2 of the paper): the positions at
+ * t+1 minimise one incremental potential over every free degree of freedom,
+ *
+ *   E(z) = 1/2 (z - z~)^T M (z - z~)
+ *        + dt^2 [ E_FEM + E_barrier + E_friction + E_stitch + E_ABD ],
+ *
+ * with E_FEM the Neo-Hookean energy of the tetrahedral fingertips and
+ * deformable objects (§III-C.1), E_barrier the log-barrier contact potential
+ * on point-triangle and edge-edge pairs, E_friction the lagged, smoothly
+ * mollified friction potential, E_stitch the stitch springs of Eq. 2 that
+ * attach fingertip vertices to the gripper bases, and E_ABD the stiff
+ * orthogonality energy of affine bodies (§III-C.1).  Arm links and finger
+ * bases are kinematic: they follow the rigid transforms given to each step
+ * (the joint drive E_joint of Eq. 3 is not modelled; the links are
+ * prescribed).  The step is a projected Newton iteration with a
+ * block-Jacobi PCG linear solve, an additive-CCD bound on every step length
+ * and a backtracking line search, so no pair of primitives ever
+ * interpenetrates.
+ *
+ * Conventions for every entry point
+ *   - Units are SI.  Positions are double, row-major (n, 3).
+ *   - Pointers named *_host point to host memory and are read (or written)
+ *     during the call only; the caller keeps ownership.  Pointers named
+ *     *_dev are CUDA device pointers of the library's device.
+ *   - A 3x4 transform is 12 doubles, row-major [R | t]: x = R xbar + t.
+ *   - ABD generalised coordinates q are 12 doubles [p, A(:,0), A(:,1), A(:,2)]
+ *     with x = p + A xbar.
+ *   - Every call returns IPC_OK (0) or a negative ipc_status; no call aborts
+ *     or exits.  sim_last_error() gives a human-readable reason.
+ *   - On a failed sim_step the state stays at the start of that step.
+ *   - All device work is enqueued on the stream given to sim_create.
+ */
+#ifndef IPCSIM_H
+#define IPCSIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipcsim ipcsim;
+typedef int ipc_status;
+
+enum {
+  IPC_OK = 0,
+  IPC_ERR_ARG = -1,           /* bad argument or scene description */
+  IPC_ERR_INVERTED = -2,      /* a rest tetrahedron has non-positive volume */
+  IPC_ERR_INTERSECTING = -3,  /* initial state has a pair at zero distance */
+  IPC_ERR_NEWTON_MAXIT = -4,  /* Newton did not reach the tolerance */
+  IPC_ERR_PCG = -5,           /* PCG broke down (p^T A p <= 0) */
+  IPC_ERR_LS_STALL = -6,      /* line search halved 40 times without decrease */
+  IPC_ERR_NAN = -7,           /* non-finite energy, gradient or direction */
+  IPC_ERR_BVH_OVERFLOW = -8,  /* BVH traversal stack overflow */
+  IPC_ERR_CUDA = -9,          /* a CUDA runtime call failed */
+  IPC_ERR_CAPACITY = -10      /* a pair buffer could not grow */
+};
+
+/* Scene description, read once by sim_create.  Vertex ids are 0-based and
+ * local to their body (FEM ids index fem_X). */
+typedef struct {
+  /* deformable (FEM) bodies: tetrahedral meshes (§III-C.1) */
+  int n_fem_verts;
+  const double* fem_X_host;     /* (n_fem_verts, 3) rest = initial positions */
+  const double* fem_V0_host;    /* (n_fem_verts, 3) initial velocity, or NULL for 0 */
+  int n_tets;
+  const int* tets_host;         /* (n_tets, 4), positively oriented */
+  const double* logE_host;      /* (n_tets) ln Young's modulus */
+  const double* nu_host;        /* (n_tets) Poisson ratio */
+  const double* rho_host;       /* (n_tets) density */
+  const int* fem_body_host;     /* (n_tets) FEM body id, or NULL for one body */
+  /* affine bodies (ABD): closed outward triangle meshes in body frame */
+  int n_abd;
+  const int* abd_nverts_host;   /* (n_abd) */
+  const double* abd_X_host;     /* concatenated (sum nverts, 3) */
+  const int* abd_ntris_host;    /* (n_abd) */
+  const int* abd_tris_host;     /* concatenated (sum ntris, 3), ids local to the body */
+  const double* abd_rho_host;   /* (n_abd) density */
+  const double* abd_q0_host;    /* (n_abd, 12) initial q */
+  /* kinematic bodies: arm links, finger bases, plates, fixed obstacles */
+  int n_kin;
+  const int* kin_nverts_host;   /* (n_kin) */
+  const double* kin_X_host;     /* concatenated local rest vertices */
+  const int* kin_ntris_host;    /* (n_kin) */
+  const int* kin_tris_host;     /* concatenated, ids local to the body */
+  const double* kin_T0_host;    /* (n_kin, 12) transforms at t = 0 */
+  /* stitch springs of Eq. 2: FEM vertex -> point fixed to a kinematic body */
+  int n_stitch;
+  const int* stitch_v_host;     /* (n_stitch) FEM vertex id */
+  const int* stitch_b_host;     /* (n_stitch) kinematic body id */
+  const double* stitch_X_host;  /* (n_stitch, 3) anchor in that body's frame */
+  double gravity[3];
+} ipc_scene_desc;
+
+enum { IPC_PREC_FP64 = 0, IPC_PREC_MIXED = 1 };
+
+typedef struct {
+  double dt;          /* time step (s) */
+  double dhat;        /* barrier activation distance (m) */
+  double kappa;       /* barrier stiffness; <= 0: kbar / B''(dhat/2), kbar = E_max * mean soft edge */
+  double mu;          /* friction coefficient */
+  double eps_v;       /* friction velocity threshold (m/s); mollifier width eps_v * dt */
+  double k_c;         /* stitch stiffness (N/m); <= 0: 100 * E_max * mean soft edge */
+  double kappa_A;     /* ABD orthogonality stiffness (Pa) */
+  double newton_tol;  /* stop when max|p| / (dt * L_bbox) < newton_tol and kinematic DOFs reached */
+  double pcg_rtol;    /* PCG stops when |r|_2 <= pcg_rtol |b|_2 */
+  double s_ccd;       /* ACCD minimum-separation fraction (0.1) */
+  int max_newton;     /* Newton iteration cap */
+  int max_pcg;        /* PCG iteration cap; <= 0: 10 * sqrt(n_dof) + 100 */
+  int precision;      /* IPC_PREC_FP64 or IPC_PREC_MIXED */
+  int pair_capacity;  /* initial contact-pair capacity; <= 0: automatic (grows on demand) */
+} ipc_params;
+
+typedef struct {
+  int status;             /* ipc_status of the step */
+  int newton_iters;
+  int pcg_iters_total;
+  int pcg_iters_max;
+  int n_pairs_max;        /* most active barrier pairs seen in one iterate */
+  int n_friction_pairs;   /* lagged friction pairs of the step */
+  int n_ccd_max;          /* most CCD candidates seen in one iteration */
+  int ls_halvings;        /* total line-search halvings */
+  double alpha_min;       /* smallest accepted step fraction */
+  double min_dist;        /* smallest primitive distance over the accepted iterates (m) */
+  double energy_end;      /* incremental potential at the solution */
+  double pnorm_end;       /* max|p| / (dt L) of the last Newton direction */
+} ipc_step_stats;
+
+/* Build a simulator.  Validates the scene (IPC_ERR_INVERTED for a rest tet
+ * with det(Dm) <= 0), prepares rest shapes, masses, the BSR pattern and the
+ * contact surfaces on the host, uploads them, and allocates device memory
+ * with cudaMalloc.  stream: a cudaStream_t (NULL = legacy default stream). */
+ipc_status sim_create(const ipc_scene_desc* desc, const ipc_params* params, void* stream, ipcsim** out);
+
+/* Advance one time step (Eq. 3).  kin_T_next_host: (n_kin, 12) transforms of
+ * the kinematic bodies at t+1 (may be NULL when n_kin == 0).  stats_host may
+ * be NULL.  Synchronises the stream once per Newton iteration to read the
+ * convergence data and returns when the step is done. */
+ipc_status sim_step(ipcsim* sim, const double* kin_T_next_host, ipc_step_stats* stats_host);
+
+/* Copy the state out: FEM positions and velocities (n_fem_verts, 3) and ABD
+ * q / qdot (n_abd, 12).  Any pointer may be NULL.  `on_device` != 0 means the
+ * pointers are device pointers, else host pointers.  Synchronous. */
+ipc_status sim_get_state(const ipcsim* sim, double* x, double* v, double* abd_q, double* abd_qd, int on_device);
+
+/* Overwrite the state (same layouts).  Kinematic bodies keep their pose. */
+ipc_status sim_set_state(ipcsim* sim, const double* x, const double* v, const double* abd_q, const double* abd_qd,
+                         int on_device);
+
+/* Counts: [n_fem_verts, n_tets, n_abd, n_kin, n_surface_tris, n_surface_edges,
+ * n_surface_verts, n_nodes, bsr_blocks] written to out9. */
+ipc_status sim_sizes(const ipcsim* sim, int* out9);
+
+/* Derived scalars fixed at create: [kappa, k_c, L_bbox, dhat]. */
+ipc_status sim_scalars(const ipcsim* sim, double* out4);
+
+/* Reason of the last failure of `sim`; with sim == NULL, of the last failed
+ * sim_create on the calling thread. */
+const char* sim_last_error(const ipcsim* sim);
+void sim_destroy(ipcsim* sim);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points (the hot-path kernels one by one, for parity checks
+ * and profiling).  Positions are device pointers to (n_vertices_all, 3)
+ * doubles in the library's global vertex order: FEM vertices, then the
+ * ABD surface vertices body by body, then the kinematic vertices body by
+ * body (sim_sizes gives the counts).
+ * ---------------------------------------------------------------------- */
+
+/* Elastic energy, gradient (n_fem_verts, 3) and, if H_dev != NULL, the
+ * per-tet 12x12 Hessians (n_tets, 144), PSD-projected when project != 0, at
+ * FEM positions x_dev (n_fem_verts, 3).  Energies are V_e Psi (not scaled by
+ * dt^2).  E_dev: one double.  grad_dev is overwritten. */
+ipc_status sim_eval_elastic(ipcsim* sim, const double* x_dev, int project, double* E_dev, double* grad_dev,
+                            double* H_dev);
+
+/* Active contact pairs at all-vertex positions x_dev: every point-triangle
+ * and edge-edge pair with squared distance < dhat^2 after the exclusion
+ * rules.  Records (cap, 8) int32: kind (0 PT / 1 EE), primitive a, primitive b,
+ * distance type, 4 vertex ids; s_dev (cap) squared distances.  Writes the
+ * count to *n_host.  Returns IPC_ERR_CAPACITY (with the needed count in
+ * *n_host) when cap is too small.  Primitive numbering: surface vertices,
+ * triangles and edges as returned by sim_surface. */
+ipc_status sim_active_pairs(ipcsim* sim, const double* x_dev, int cap, int* rec_dev, double* s_dev, int* n_host);
+
+/* Surface topology (host buffers of sizes from sim_sizes): surface vertex
+ * ids, triangles (3 ids), edges (2 ids), all in the global vertex order. */
+ipc_status sim_surface(const ipcsim* sim, int* sv_host, int* tris_host, int* edges_host);
+
+/* Barrier energy kappa * sum m_k b(s_k) (not scaled by dt^2), its gradient
+ * with respect to the free DOF nodes (n_nodes, 3: FEM vertices, then the 4
+ * pseudo-nodes of each ABD body) and the per-pair vertex-space 12x12
+ * Hessians (n, 144), PSD-projected when project != 0, of n pair records (as
+ * from sim_active_pairs) at x_dev.  Allocates scratch with cudaMalloc. */
+ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* rec_dev, int project, double* E_dev,
+                            double* grad_dev, double* H_dev);
+
+/* Largest step fraction in (0, 1] along the vertex displacement p_dev
+ * (n_vertices_all, 3) from x_dev: minimum additive-CCD time of impact over
+ * all pairs whose swept boxes overlap.  *n_cand_host: candidates tested. */
+ipc_status sim_ccd_alpha(ipcsim* sim, const double* x_dev, const double* p_dev, double* alpha_host, int* n_cand_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPCSIM_H */

@@ -628,8 +628,13 @@ class Scene:
         x = _f64(self.positions(z).reshape(-1))
         pv = _f64(self.Jmap @ p)
         nc = C.c_int()
-        a = lib().orc_ccd_alpha(C.byref(self.surf), _d(x), _d(pv), self.s_ccd, 1_000_000, C.byref(nc))
+        a = lib().orc_ccd_alpha(C.byref(self.surf), _d(x), _d(pv), self.s_ccd, ACCD_MAX_ITER, C.byref(nc))
         return a, nc.value
+
+
+# Conservative-advancement iterations per candidate before ACCD returns the
+# time reached so far (still a safe bound).
+ACCD_MAX_ITER = 10000
 
 
 class StepError(RuntimeError):

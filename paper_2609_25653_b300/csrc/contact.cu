@@ -1,0 +1,363 @@
+// Contact kernels: log-barrier energy, gradient and PSD-projected Hessian per
+// point-triangle / edge-edge pair (E_barrier of Eq. 3), the edge-edge
+// mollifier, lagged friction (E_friction of Eq. 3), and the Dirichlet
+// coupling of kinematic vertices.
+//
+// Barrier (on squared distance s, sh = dhat^2): b(s) = -(s - sh)^2 ln(s / sh)
+// for 0 < s < sh.  Pair energy kappa * m * b(s), m the edge-edge mollifier
+// (1 for point-triangle pairs).  Friction per lagged pair: mu * lambda *
+// f0(|P u|), u = sum_k w_k (x_k - x_t,k), P = I - n n^T, f0 the C1 cubic
+// below eps = eps_v dt.
+#include "common.cuh"
+#include "dist.cuh"
+#include "eig.cuh"
+#include "kernels.h"
+
+namespace ipc {
+
+__device__ inline void barrier_fn(double s, double sh, double& b, double& b1, double& b2) {
+  if (s >= sh) { b = b1 = b2 = 0.0; return; }
+  double d = s - sh, l = log(s / sh);
+  b = -d * d * l;
+  b1 = -(2.0 * d * l + d * d / s);
+  b2 = -(2.0 * l + 4.0 * d / s - d * d / (s * s));
+}
+
+// Edge-edge mollifier value m(c) = -(c/eps)^2 + 2 c/eps below eps, else 1; c = |(a1-a0) x (b1-b0)|^2.
+__device__ inline double moll_value(const d3* x, double eps_x) {
+  d3 n = cross(x[1] - x[0], x[3] - x[2]);
+  double c = dot(n, n);
+  if (c >= eps_x) return 1.0;
+  double r = c / eps_x;
+  return -r * r + 2.0 * r;
+}
+
+// Edge-edge mollifier m(c): value, gradient g and Hessian H (c < eps_x assumed by callers that use g/H).
+__device__ inline double mollifier(const d3* x, double eps_x, double* g, double* H) {
+  d3 a = x[1] - x[0], b = x[3] - x[2];
+  d3 n = cross(a, b);
+  double c = dot(n, n);
+  if (c >= eps_x) return 1.0;
+  double r = c / eps_x;
+  double m = -r * r + 2.0 * r;
+  double m1 = (2.0 - 2.0 * r) / eps_x, m2 = -2.0 / (eps_x * eps_x);
+  d3 ga = 2.0 * cross(b, n), gb = 2.0 * cross(n, a);
+  double gc[12] = {-ga.x, -ga.y, -ga.z, ga.x, ga.y, ga.z, -gb.x, -gb.y, -gb.z, gb.x, gb.y, gb.z};
+  for (int i = 0; i < 12; ++i) g[i] = m1 * gc[i];
+  if (!H) return m;
+  double Sa[9], Sb[9], Sn[9], Haa[9], Hbb[9], Hab[9], T[9];
+  skew9(a, Sa);
+  skew9(b, Sb);
+  skew9(n, Sn);
+  mm3(Sb, Sb, T);
+  for (int i = 0; i < 9; ++i) Haa[i] = -2.0 * T[i];
+  mm3(Sa, Sa, T);
+  for (int i = 0; i < 9; ++i) Hbb[i] = -2.0 * T[i];
+  mm3(Sb, Sa, T);
+  for (int i = 0; i < 9; ++i) Hab[i] = 2.0 * T[i] - 2.0 * Sn[i];
+  // slot coefficients: a = x1 - x0, b = x3 - x2
+  const double ca[4] = {-1, 1, 0, 0}, cb[4] = {0, 0, -1, 1};
+  for (int k = 0; k < 4; ++k)
+    for (int l = 0; l < 4; ++l)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double h = ca[k] * ca[l] * Haa[3 * i + j] + cb[k] * cb[l] * Hbb[3 * i + j] + ca[k] * cb[l] * Hab[3 * i + j] +
+                     cb[k] * ca[l] * Hab[3 * j + i];
+          H[12 * (3 * k + i) + 3 * l + j] = m2 * gc[3 * k + i] * gc[3 * l + j] + m1 * h;
+        }
+  return m;
+}
+
+__device__ inline void load_stencil(const DevScene& S, const double* xv, const int* r, int* ids, d3* x) {
+  for (int k = 0; k < 4; ++k) {
+    ids[k] = r[4 + k];
+    x[k] = ld3(xv, ids[k]);
+  }
+}
+
+// slots of the stencil that the distance of (kind, type) depends on
+__device__ inline int involved_mask(int kind, int type) {
+  if (kind == 0) {
+    if (type <= 2) return 1 | (2 << type);
+    if (type <= 5) return 1 | (2 << (type - 3)) | (2 << ((type - 2) % 3));
+    return 15;
+  }
+  if (type <= 3) return (1 << (type / 2)) | (4 << (type % 2));
+  if (type <= 5) return 3 | (4 << (type - 4));
+  if (type <= 7) return 12 | (1 << (type - 6));
+  return 15;
+}
+
+// Project the sub-block of the slots in `mask` (other rows/columns are zero).
+__device__ inline void project_pair(double* H, int mask) {
+  int sl[4], ns = 0;
+  for (int k = 0; k < 4; ++k)
+    if (mask & (1 << k)) sl[ns++] = k;
+  if (ns == 4) { project_psd<12, double>(H); return; }
+  double A[81];
+  int n = 3 * ns;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A[n * (3 * a + i) + 3 * b + j] = H[12 * (3 * sl[a] + i) + 3 * sl[b] + j];
+  if (ns == 2) project_psd<6, double>(A);
+  else project_psd<9, double>(A);
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) H[12 * (3 * sl[a] + i) + 3 * sl[b] + j] = A[n * (3 * a + i) + 3 * b + j];
+}
+
+// Scatter a vertex-space 12-vector (scaled) to node space.
+__device__ inline void scatter_grad(const DevScene& S, const int* ids, const double* gv, double scale, double* g) {
+  for (int k = 0; k < 4; ++k) {
+    NodeMap m = vertex_nodes(S, ids[k]);
+    for (int r = 0; r < m.n; ++r) {
+      double w = scale * m.w[r];
+      atomicAdd(g + 3 * m.node[r], w * gv[3 * k]);
+      atomicAdd(g + 3 * m.node[r] + 1, w * gv[3 * k + 1]);
+      atomicAdd(g + 3 * m.node[r] + 2, w * gv[3 * k + 2]);
+    }
+  }
+}
+
+// Diagonal node blocks of J^T H J (for the block-Jacobi preconditioner) and
+// H_FD p_D (the Dirichlet coupling) of a dense 12x12 vertex-space block.
+__device__ inline void scatter_diag_dirichlet(const DevScene& S, const int* ids, const double* H, const double* pD,
+                                              double* Dc, double* gdir) {
+  NodeMap m[4];
+  bool kin[4];
+  d3 pk[4];
+  for (int k = 0; k < 4; ++k) {
+    m[k] = vertex_nodes(S, ids[k]);
+    kin[k] = S.vkind[ids[k]] == VK_KIN;
+    pk[k] = kin[k] ? ld3(pD, ids[k] - S.nf - S.na_v) : mk(0, 0, 0);
+  }
+  for (int a = 0; a < 4; ++a) {
+    if (kin[a]) continue;
+    // Dirichlet: y_a = sum_{kinematic b} H_ab pD_b
+    d3 y = mk(0, 0, 0);
+    for (int b = 0; b < 4; ++b) {
+      if (!kin[b]) continue;
+      const double* Hr = H + 12 * 3 * a + 3 * b;
+      y = y + mk(Hr[0] * pk[b].x + Hr[1] * pk[b].y + Hr[2] * pk[b].z, Hr[12] * pk[b].x + Hr[13] * pk[b].y + Hr[14] * pk[b].z,
+                 Hr[24] * pk[b].x + Hr[25] * pk[b].y + Hr[26] * pk[b].z);
+    }
+    if (y.x != 0.0 || y.y != 0.0 || y.z != 0.0)
+      for (int r = 0; r < m[a].n; ++r) {
+        atomicAdd(gdir + 3 * m[a].node[r], m[a].w[r] * y.x);
+        atomicAdd(gdir + 3 * m[a].node[r] + 1, m[a].w[r] * y.y);
+        atomicAdd(gdir + 3 * m[a].node[r] + 2, m[a].w[r] * y.z);
+      }
+    // diagonal node blocks
+    for (int b = 0; b < 4; ++b) {
+      if (kin[b]) continue;
+      for (int r = 0; r < m[a].n; ++r)
+        for (int q = 0; q < m[b].n; ++q) {
+          if (m[a].node[r] != m[b].node[q]) continue;
+          double w = m[a].w[r] * m[b].w[q];
+          double* dst = Dc + 9 * m[a].node[r];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) atomicAdd(dst + 3 * i + j, w * H[12 * (3 * a + i) + 3 * b + j]);
+        }
+    }
+  }
+}
+
+// mode 0: energy (and min s) only; mode 2: also gradient, projected Hessian, preconditioner diagonal, Dirichlet term.
+__global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __restrict__ xv, const int* __restrict__ rec,
+                                                 const int* __restrict__ n_dev, int cap, double sh, double kappa,
+                                                 double scale, int mode, int project, double* __restrict__ g,
+                                                 double* __restrict__ pairH, double* __restrict__ Dc,
+                                                 const double* __restrict__ pD, double* __restrict__ gdir,
+                                                 double* __restrict__ E, unsigned long long* __restrict__ min_s) {
+  int n = min(*n_dev, cap);
+  double e_acc = 0.0, smin = 1e300;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    {
+      const int* r = rec + 8 * k;
+      int kind = r[0], type = r[3];
+      int ids[4];
+      d3 x[4];
+      load_stencil(S, xv, r, ids, x);
+      Red R;
+      double s;
+      dist_reduced(kind, type, x, R, s);
+      smin = fmin(smin, s);
+      double b, b1, b2;
+      barrier_fn(s, sh, b, b1, b2);
+      double eps_x = kind == 1 ? 1e-3 * S.edge_rest_sq[r[1]] * S.edge_rest_sq[r[2]] : 0.0;
+      if (mode == 0) {
+        double m = kind == 1 ? moll_value(x, eps_x) : 1.0;
+        e_acc += kappa * m * b;
+      } else if (b != 0.0 || b1 != 0.0) {
+        double gs[12], Hs[144];
+        red_expand(R, gs, Hs);
+        double gm[12], Hm[144];
+        double m = 1.0;
+        bool moll = false;
+        if (kind == 1) {
+          d3 a = x[1] - x[0], bb = x[3] - x[2];
+          d3 nn = cross(a, bb);
+          if (dot(nn, nn) < eps_x) { m = mollifier(x, eps_x, gm, Hm); moll = true; }
+        }
+        e_acc += kappa * m * b;
+        double grad[12];
+        for (int i = 0; i < 12; ++i) grad[i] = kappa * (m * b1 * gs[i] + (moll ? b * gm[i] : 0.0));
+        double* H = pairH + 144 * (size_t)k;
+        for (int i = 0; i < 12; ++i)
+          for (int j = 0; j < 12; ++j) {
+            double h = m * (b2 * gs[i] * gs[j] + b1 * Hs[12 * i + j]);
+            if (moll) h += b * Hm[12 * i + j] + b1 * (gm[i] * gs[j] + gs[i] * gm[j]);
+            Hs[12 * i + j] = kappa * h;
+          }
+        if (project) project_pair(Hs, moll ? 15 : involved_mask(kind, type));
+        for (int i = 0; i < 144; ++i) {
+          Hs[i] *= scale;
+          H[i] = Hs[i];
+        }
+        scatter_grad(S, ids, grad, scale, g);
+        scatter_diag_dirichlet(S, ids, Hs, pD, Dc, gdir);
+      } else {
+        double* H = pairH + 144 * (size_t)k;
+        for (int i = 0; i < 144; ++i) H[i] = 0.0;
+      }
+    }
+  }
+  double s = block_sum(e_acc);
+  if (threadIdx.x == 0) atomicAdd(E, s);
+  double m = block_max(-smin);
+  if (threadIdx.x == 0 && min_s) atomicMin(min_s, dbits(-m));
+}
+
+// Lagged friction data at the start of the step for every active pair:
+// closest-point weights w, unit normal n, normal force lambda = -kappa m 2 d b'(s).
+__global__ void k_friction_lag(DevScene S, const double* __restrict__ xv, const int* __restrict__ rec,
+                               const int* __restrict__ n_dev, int cap, double sh, double kappa, int* __restrict__ f_ids,
+                               double* __restrict__ f_w, double* __restrict__ f_n, double* __restrict__ f_lam) {
+  int n = min(*n_dev, cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int* r = rec + 8 * k;
+    int kind = r[0];
+    int ids[4];
+    d3 x[4];
+    load_stencil(S, xv, r, ids, x);
+    double s, w[4];
+    if (kind == 0) pt_classify(x, s, w);
+    else ee_classify(x, s, w);
+    double d = sqrt(s);
+    d3 nrm = (1.0 / d) * (w[0] * x[0] + w[1] * x[1] + w[2] * x[2] + w[3] * x[3]);
+    double b, b1, b2;
+    barrier_fn(s, sh, b, b1, b2);
+    double m = kind == 1 ? moll_value(x, 1e-3 * S.edge_rest_sq[r[1]] * S.edge_rest_sq[r[2]]) : 1.0;
+    for (int q = 0; q < 4; ++q) { f_ids[4 * k + q] = ids[q]; f_w[4 * k + q] = w[q]; }
+    f_n[3 * k] = nrm.x; f_n[3 * k + 1] = nrm.y; f_n[3 * k + 2] = nrm.z;
+    f_lam[k] = -kappa * m * 2.0 * d * b1;
+  }
+}
+
+// Friction on the lagged pairs.  Stores the 3x3 tangent Hessian Hu (scaled)
+// per pair: the pair's 12x12 block is (w w^T) (x) Hu.
+__global__ void k_friction(DevScene S, const double* __restrict__ xv, const double* __restrict__ xv_t, int n,
+                           const int* __restrict__ f_ids, const double* __restrict__ f_w, const double* __restrict__ f_n,
+                           const double* __restrict__ f_lam, double mu, double eps, double scale, int mode,
+                           double* __restrict__ g, double* __restrict__ f_Hu, double* __restrict__ Dc,
+                           const double* __restrict__ pD, double* __restrict__ gdir, double* __restrict__ E) {
+  double e_acc = 0.0;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    int ids[4];
+    double w[4];
+    d3 u = mk(0, 0, 0);
+    for (int q = 0; q < 4; ++q) {
+      ids[q] = f_ids[4 * k + q];
+      w[q] = f_w[4 * k + q];
+      u = u + w[q] * (ld3(xv, ids[q]) - ld3(xv_t, ids[q]));
+    }
+    d3 nrm = ld3(f_n, k);
+    d3 t = u - dot(nrm, u) * nrm;
+    double y = sqrt(dot(t, t));
+    double c = mu * f_lam[k];
+    double f0 = y < eps ? -y * y * y / (3.0 * eps * eps) + y * y / eps + eps / 3.0 : y;
+    e_acc = c * f0;
+    if (mode >= 1) {
+      double a = y < eps ? (-y / (eps * eps) + 2.0 / eps) : 1.0 / y;
+      d3 gu = (c * a) * t;
+      for (int q = 0; q < 4; ++q) {
+        NodeMap m = vertex_nodes(S, ids[q]);
+        for (int r = 0; r < m.n; ++r) {
+          double ww = scale * w[q] * m.w[r];
+          atomicAdd(g + 3 * m.node[r], ww * gu.x);
+          atomicAdd(g + 3 * m.node[r] + 1, ww * gu.y);
+          atomicAdd(g + 3 * m.node[r] + 2, ww * gu.z);
+        }
+      }
+    }
+    if (mode >= 2) {
+      double a = y < eps ? (-y / (eps * eps) + 2.0 / eps) : 1.0 / y;
+      double bc = y < eps ? (y > 0.0 ? (-1.0 / (eps * eps)) / y : 0.0) : -1.0 / (y * y * y);
+      double nv[3] = {nrm.x, nrm.y, nrm.z}, tv[3] = {t.x, t.y, t.z};
+      double Hu[9];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          Hu[3 * i + j] = scale * c * (a * ((i == j ? 1.0 : 0.0) - nv[i] * nv[j]) + bc * tv[i] * tv[j]);
+      for (int q = 0; q < 9; ++q) f_Hu[9 * k + q] = Hu[q];
+      // diagonal blocks and Dirichlet term of (w w^T) (x) Hu
+      NodeMap m[4];
+      bool kin[4];
+      d3 ud = mk(0, 0, 0);
+      for (int q = 0; q < 4; ++q) {
+        m[q] = vertex_nodes(S, ids[q]);
+        kin[q] = S.vkind[ids[q]] == VK_KIN;
+        if (kin[q]) ud = ud + w[q] * ld3(pD, ids[q] - S.nf - S.na_v);
+      }
+      d3 hd = mk(Hu[0] * ud.x + Hu[1] * ud.y + Hu[2] * ud.z, Hu[3] * ud.x + Hu[4] * ud.y + Hu[5] * ud.z,
+                 Hu[6] * ud.x + Hu[7] * ud.y + Hu[8] * ud.z);
+      for (int a_ = 0; a_ < 4; ++a_) {
+        if (kin[a_] || w[a_] == 0.0) continue;
+        for (int r = 0; r < m[a_].n; ++r) {
+          double ww = w[a_] * m[a_].w[r];
+          if (hd.x != 0.0 || hd.y != 0.0 || hd.z != 0.0) {
+            atomicAdd(gdir + 3 * m[a_].node[r], ww * hd.x);
+            atomicAdd(gdir + 3 * m[a_].node[r] + 1, ww * hd.y);
+            atomicAdd(gdir + 3 * m[a_].node[r] + 2, ww * hd.z);
+          }
+        }
+        for (int b_ = 0; b_ < 4; ++b_) {
+          if (kin[b_] || w[b_] == 0.0) continue;
+          for (int r = 0; r < m[a_].n; ++r)
+            for (int q = 0; q < m[b_].n; ++q) {
+              if (m[a_].node[r] != m[b_].node[q]) continue;
+              double ww = w[a_] * m[a_].w[r] * w[b_] * m[b_].w[q];
+              for (int i = 0; i < 9; ++i) atomicAdd(Dc + 9 * m[a_].node[r] + i, ww * Hu[i]);
+            }
+        }
+      }
+    }
+  }
+  double s = block_sum(e_acc);
+  if (threadIdx.x == 0) atomicAdd(E, s);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
+                    int cap, double sh, double kappa, double scale, int mode, int project, double* g, double* pairH,
+                    double* Dc, const double* pD, double* gdir, double* E, unsigned long long* min_s) {
+  k_barrier<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, mode, project, g, pairH, Dc, pD, gdir, E,
+                                  min_s);
+}
+void launch_friction_lag(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
+                         int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam) {
+  k_friction_lag<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, f_ids, f_w, f_n, f_lam);
+}
+void launch_friction(cudaStream_t st, const DevScene& S, const double* xv, const double* xv_t, int n, const int* f_ids,
+                     const double* f_w, const double* f_n, const double* f_lam, double mu, double eps, double scale,
+                     int mode, double* g, double* f_Hu, double* Dc, const double* pD, double* gdir, double* E) {
+  if (n <= 0) return;
+  k_friction<<<(n + 127) / 128, 128, 0, st>>>(S, xv, xv_t, n, f_ids, f_w, f_n, f_lam, mu, eps, scale, mode, g, f_Hu, Dc,
+                                              pD, gdir, E);
+}
+
+}  // namespace ipc

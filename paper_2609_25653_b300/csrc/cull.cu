@@ -1,0 +1,188 @@
+// Contact candidate culling and continuous collision detection (§III-C.1:
+// barrier potentials together with continuous collision detection).
+//
+// Active set: every (surface vertex, surface triangle) and (surface edge,
+// surface edge) pair with squared distance below dhat^2, after the exclusion
+// rules (shared vertex; both primitives on one rigid or kinematic body; both
+// kinematic).  CCD: the additive-CCD time of impact of every pair whose
+// swept boxes over [x, x + p] overlap; the step bound is their minimum.
+//
+// This file is compiled with -fmad=false: the classification and the
+// squared distance that decide membership (s < dhat^2) round operation by
+// operation as written, so the active set is exactly reproducible.
+#include "common.cuh"
+#include "dist.cuh"
+#include "kernels.h"
+
+namespace ipc {
+
+__device__ inline bool excluded(const DevScene& S, const int* va, int na, const int* vb, int nb) {
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j)
+      if (va[i] == vb[j]) return true;
+  int ba = S.vbody[va[0]], bb = S.vbody[vb[0]];
+  int ka = S.bkind[ba], kb = S.bkind[bb];
+  if (ba == bb && ka != VK_FEM) return true;
+  if (ka == VK_KIN && kb == VK_KIN) return true;
+  return false;
+}
+
+__device__ inline void emit(int* rec, double* rec_s, int* count, int cap, int kind, int a, int b, int type,
+                            const int* ids, double s) {
+  int slot = atomicAdd(count, 1);
+  if (slot < cap) {
+    int* r = rec + 8 * slot;
+    r[0] = kind; r[1] = a; r[2] = b; r[3] = type;
+    r[4] = ids[0]; r[5] = ids[1]; r[6] = ids[2]; r[7] = ids[3];
+    if (rec_s) rec_s[slot] = s;
+  }
+}
+
+// Point-triangle pairs: thread per (surface vertex i, triangle t)
+__global__ void k_cull_pt_brute(DevScene S, const double* __restrict__ xv, double sh, int* rec, double* rec_s,
+                                int* count, int cap) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)S.nsv * S.ntri;
+  if (idx >= total) return;
+  int i = (int)(idx / S.ntri), t = (int)(idx % S.ntri);
+  int p = S.sv[i];
+  int3 tv = S.tris[t];
+  int tvv[3] = {tv.x, tv.y, tv.z};
+  if (excluded(S, &p, 1, tvv, 3)) return;
+  int ids[4] = {p, tv.x, tv.y, tv.z};
+  d3 x[4] = {ld3(xv, p), ld3(xv, tv.x), ld3(xv, tv.y), ld3(xv, tv.z)};
+  double s, w[4];
+  int type = pt_classify(x, s, w);
+  if (s < sh) emit(rec, rec_s, count, cap, 0, i, t, type, ids, s);
+}
+
+// Edge-edge pairs: thread per (edge a, edge b), a < b
+__global__ void k_cull_ee_brute(DevScene S, const double* __restrict__ xv, double sh, int* rec, double* rec_s,
+                                int* count, int cap) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)S.nedge * S.nedge;
+  if (idx >= total) return;
+  int ea = (int)(idx / S.nedge), eb = (int)(idx % S.nedge);
+  if (eb <= ea) return;
+  int2 A = S.edges[ea], B = S.edges[eb];
+  int va[2] = {A.x, A.y}, vb[2] = {B.x, B.y};
+  if (excluded(S, va, 2, vb, 2)) return;
+  int ids[4] = {A.x, A.y, B.x, B.y};
+  d3 x[4] = {ld3(xv, A.x), ld3(xv, A.y), ld3(xv, B.x), ld3(xv, B.y)};
+  double s, w[4];
+  int type = ee_classify(x, s, w);
+  if (s < sh) emit(rec, rec_s, count, cap, 1, ea, eb, type, ids, s);
+}
+
+// ---------------------------------------------------------------------------
+// additive CCD (Li et al., "Codimensional Incremental Potential Contact", 2021)
+// ---------------------------------------------------------------------------
+// The distance of the stencil can shrink at most at rate lp (the two
+// primitives' largest speeds relative to the stencil mean), so advancing by
+// (1 - s) d0 / lp, then by 0.9 d / lp, never passes a contact.  Stops before
+// the distance falls below s d0; returns tmax if that does not happen.
+__device__ double accd(int kind, const d3* x0, const d3* p0, double s_frac, double tmax, int max_iter) {
+  d3 pbar = mk(0.0, 0.0, 0.0);
+  for (int k = 0; k < 4; ++k) pbar = pbar + 0.25 * p0[k];
+  d3 p[4];
+  double nrm[4];
+  for (int k = 0; k < 4; ++k) {
+    p[k] = p0[k] - pbar;
+    nrm[k] = sqrt(dot(p[k], p[k]));
+  }
+  double lp = (kind == 0) ? nrm[0] + fmax(nrm[1], fmax(nrm[2], nrm[3])) : fmax(nrm[0], nrm[1]) + fmax(nrm[2], nrm[3]);
+  if (lp == 0.0) return tmax;
+  double d0 = sqrt(pair_s(kind, x0));
+  double target = s_frac * d0;
+  double t = 0.0, tl = (1.0 - s_frac) * d0 / lp;
+  d3 xt[4];
+  for (int it = 0; it < max_iter; ++it) {
+    double tn = t + tl;
+    for (int k = 0; k < 4; ++k) xt[k] = mk(x0[k].x + tn * p[k].x, x0[k].y + tn * p[k].y, x0[k].z + tn * p[k].z);
+    double d = sqrt(pair_s(kind, xt));
+    if (d < target && it > 0) return t;
+    t = tn;
+    if (t >= tmax) return tmax;
+    tl = 0.9 * d / lp;
+  }
+  return t;
+}
+
+__device__ inline void swept(const double* xv, const double* pv, int v, d3& lo, d3& hi) {
+  d3 a = ld3(xv, v), p = ld3(pv, v);
+  d3 b = a + p;
+  lo = mk(fmin(lo.x, fmin(a.x, b.x)), fmin(lo.y, fmin(a.y, b.y)), fmin(lo.z, fmin(a.z, b.z)));
+  hi = mk(fmax(hi.x, fmax(a.x, b.x)), fmax(hi.y, fmax(a.y, b.y)), fmax(hi.z, fmax(a.z, b.z)));
+}
+__device__ inline bool overlap(d3 la, d3 ha, d3 lb, d3 hb) {
+  return !(la.x > hb.x || lb.x > ha.x || la.y > hb.y || lb.y > ha.y || la.z > hb.z || lb.z > ha.z);
+}
+
+__global__ void k_ccd_pt_brute(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
+                               int max_iter, unsigned long long* alpha_bits, int* n_cand) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)S.nsv * S.ntri;
+  if (idx >= total) return;
+  int i = (int)(idx / S.ntri), t = (int)(idx % S.ntri);
+  int p = S.sv[i];
+  int3 tv = S.tris[t];
+  int tvv[3] = {tv.x, tv.y, tv.z};
+  if (excluded(S, &p, 1, tvv, 3)) return;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf), lb = la, hb = ha;
+  swept(xv, pv, p, la, ha);
+  swept(xv, pv, tv.x, lb, hb);
+  swept(xv, pv, tv.y, lb, hb);
+  swept(xv, pv, tv.z, lb, hb);
+  if (!overlap(la, ha, lb, hb)) return;
+  int ids[4] = {p, tv.x, tv.y, tv.z};
+  d3 x[4], pp[4];
+  for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
+  atomicAdd(n_cand, 1);
+  double toi = accd(0, x, pp, s_frac, 1.0, max_iter);
+  if (toi < 1.0) atomicMin(alpha_bits, dbits(toi));
+}
+
+__global__ void k_ccd_ee_brute(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
+                               int max_iter, unsigned long long* alpha_bits, int* n_cand) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)S.nedge * S.nedge;
+  if (idx >= total) return;
+  int ea = (int)(idx / S.nedge), eb = (int)(idx % S.nedge);
+  if (eb <= ea) return;
+  int2 A = S.edges[ea], B = S.edges[eb];
+  int va[2] = {A.x, A.y}, vb[2] = {B.x, B.y};
+  if (excluded(S, va, 2, vb, 2)) return;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf), lb = la, hb = ha;
+  swept(xv, pv, A.x, la, ha);
+  swept(xv, pv, A.y, la, ha);
+  swept(xv, pv, B.x, lb, hb);
+  swept(xv, pv, B.y, lb, hb);
+  if (!overlap(la, ha, lb, hb)) return;
+  int ids[4] = {A.x, A.y, B.x, B.y};
+  d3 x[4], pp[4];
+  for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
+  atomicAdd(n_cand, 1);
+  double toi = accd(1, x, pp, s_frac, 1.0, max_iter);
+  if (toi < 1.0) atomicMin(alpha_bits, dbits(toi));
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+void launch_cull_brute(cudaStream_t st, const DevScene& S, const double* xv, double sh, int* rec, double* rec_s,
+                       int* count, int cap) {
+  long long npt = (long long)S.nsv * S.ntri, nee = (long long)S.nedge * S.nedge;
+  if (npt) k_cull_pt_brute<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(S, xv, sh, rec, rec_s, count, cap);
+  if (nee) k_cull_ee_brute<<<(unsigned)((nee + 255) / 256), 256, 0, st>>>(S, xv, sh, rec, rec_s, count, cap);
+}
+
+void launch_ccd_brute(cudaStream_t st, const DevScene& S, const double* xv, const double* pv, double s_frac,
+                      int max_iter, unsigned long long* alpha_bits, int* n_cand) {
+  long long npt = (long long)S.nsv * S.ntri, nee = (long long)S.nedge * S.nedge;
+  if (npt) k_ccd_pt_brute<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(S, xv, pv, s_frac, max_iter, alpha_bits, n_cand);
+  if (nee) k_ccd_ee_brute<<<(unsigned)((nee + 255) / 256), 256, 0, st>>>(S, xv, pv, s_frac, max_iter, alpha_bits, n_cand);
+}
+
+}  // namespace ipc

@@ -1,0 +1,338 @@
+// Per-node and per-element kernels of the incremental potential (Eq. 3):
+// predictor, kinematic targets, vertex positions, inertia, Neo-Hookean
+// elasticity (§III-C.1), stitch springs (Eq. 2), affine-body orthogonality,
+// step update and velocities.
+#include "common.cuh"
+#include "eig.cuh"
+#include "kernels.h"
+
+namespace ipc {
+
+// z_t <- z ; z~ = z + dt zd + dt^2 a, a = gravity on FEM nodes and on ABD translation nodes.
+__global__ void k_predict(int n_nodes, int nf, const double* __restrict__ z, const double* __restrict__ zd, double dt,
+                          d3 g, double* __restrict__ z_t, double* __restrict__ z_tilde) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  bool grav = (i < nf) || ((i - nf) % 4 == 0);
+  double dt2 = dt * dt;
+  for (int d = 0; d < 3; ++d) {
+    double zi = z[3 * i + d];
+    z_t[3 * i + d] = zi;
+    z_tilde[3 * i + d] = zi + dt * zd[3 * i + d] + (grav ? dt2 * comp(g, d) : 0.0);
+  }
+}
+
+// x = R xbar + t for every kinematic vertex; stitch anchors likewise.
+__global__ void k_kin_targets(DevScene S, const double* __restrict__ T, double* __restrict__ xk_hat,
+                              double* __restrict__ stitch_hat) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < S.nk) {
+    int b = S.kin_vbody[i];
+    const double* M = T + 12 * b;
+    d3 xb = ld3(S.xbar, S.nf + S.na_v + i);
+    st3(xk_hat, i, mk(M[0] * xb.x + M[1] * xb.y + M[2] * xb.z + M[3], M[4] * xb.x + M[5] * xb.y + M[6] * xb.z + M[7],
+                      M[8] * xb.x + M[9] * xb.y + M[10] * xb.z + M[11]));
+  }
+  if (i < S.n_stitch) {
+    const double* M = T + 12 * S.stitch_b[i];
+    d3 xb = ld3(S.stitch_X, i);
+    st3(stitch_hat, i, mk(M[0] * xb.x + M[1] * xb.y + M[2] * xb.z + M[3], M[4] * xb.x + M[5] * xb.y + M[6] * xb.z + M[7],
+                          M[8] * xb.x + M[9] * xb.y + M[10] * xb.z + M[11]));
+  }
+}
+
+// All vertex positions from the DOFs and the kinematic positions.
+__global__ void k_vertex_positions(DevScene S, const double* __restrict__ z, const double* __restrict__ xk,
+                                   double* __restrict__ xv) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= S.nv) return;
+  int k = S.vkind[v];
+  d3 x;
+  if (k == VK_FEM) x = ld3(z, v);
+  else if (k == VK_ABD) {
+    int base = S.nf + 4 * S.vabd[v];
+    d3 xb = ld3(S.xbar, v);
+    x = ld3(z, base) + xb.x * ld3(z, base + 1) + xb.y * ld3(z, base + 2) + xb.z * ld3(z, base + 3);
+  } else x = ld3(xk, v - S.nf - S.na_v);
+  st3(xv, v, x);
+}
+
+// Vertex displacement of a Newton direction: FEM p, ABD J(xbar) p, kinematic p_D.
+__global__ void k_vertex_disp(DevScene S, const double* __restrict__ p, const double* __restrict__ pD,
+                              double* __restrict__ pv) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= S.nv) return;
+  int k = S.vkind[v];
+  d3 x;
+  if (k == VK_FEM) x = ld3(p, v);
+  else if (k == VK_ABD) {
+    int base = S.nf + 4 * S.vabd[v];
+    d3 xb = ld3(S.xbar, v);
+    x = ld3(p, base) + xb.x * ld3(p, base + 1) + xb.y * ld3(p, base + 2) + xb.z * ld3(p, base + 3);
+  } else x = ld3(pD, v - S.nf - S.na_v);
+  st3(pv, v, x);
+}
+
+// Inertia 1/2 (z - z~)^T M (z - z~): energy into E[0]; gradient g = M (z - z~) (overwrites g).
+__global__ void k_inertia(DevScene S, const double* __restrict__ z, const double* __restrict__ z_tilde,
+                          double* __restrict__ g, double* __restrict__ E, int want_grad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (i < S.nf) {
+    d3 dz = ld3(z, i) - ld3(z_tilde, i);
+    double m = S.node_mass[i];
+    e = 0.5 * m * dot(dz, dz);
+    if (want_grad) st3(g, i, m * dz);
+  } else if (i < S.n_nodes) {
+    int b = (i - S.nf) / 4, r = (i - S.nf) % 4;
+    int base = S.nf + 4 * b;
+    const double* Sm = S.abd_S + 16 * b;
+    d3 acc = mk(0, 0, 0);
+    for (int s = 0; s < 4; ++s) acc = acc + Sm[4 * r + s] * (ld3(z, base + s) - ld3(z_tilde, base + s));
+    e = 0.5 * dot(ld3(z, i) - ld3(z_tilde, i), acc);
+    if (want_grad) st3(g, i, acc);
+  }
+  double s = block_sum(e);
+  if (threadIdx.x == 0) atomicAdd(E, s);
+}
+
+// Neo-Hookean energy Psi = mu/2 (|F|^2 - 3) - mu (J - 1) + lam/2 (J - 1)^2 per tet (§III-C.1),
+// its gradient and PSD-projected Hessian scattered into the BSR matrix.
+// scale = dt^2 for the incremental potential; mode: 0 energy only, 1 + gradient, 2 + Hessian.
+template <typename HT>
+__global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __restrict__ xv, double scale, int mode,
+                                                 int project, double* __restrict__ g, HT* __restrict__ Hval,
+                                                 double* __restrict__ tetH, double* __restrict__ E) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double energy = 0.0;
+  if (e < S.nt) {
+    int4 t = S.tets[e];
+    int id[4] = {t.x, t.y, t.z, t.w};
+    d3 x0 = ld3(xv, id[0]);
+    d3 c1 = ld3(xv, id[1]) - x0, c2 = ld3(xv, id[2]) - x0, c3 = ld3(xv, id[3]) - x0;
+    const double* B = S.B + 9 * e;
+    // F = Ds B, columns f_j = sum_k Ds(:,k) B(k,j)
+    d3 f[3];
+    for (int j = 0; j < 3; ++j) f[j] = B[j] * c1 + B[3 + j] * c2 + B[6 + j] * c3;
+    d3 cf[3] = {cross(f[1], f[2]), cross(f[2], f[0]), cross(f[0], f[1])};
+    double J = dot(f[0], cf[0]);
+    double Ic = dot(f[0], f[0]) + dot(f[1], f[1]) + dot(f[2], f[2]);
+    double mu = S.mu[e], lam = S.lam[e], V = S.vol[e];
+    energy = V * (0.5 * mu * (Ic - 3.0) - mu * (J - 1.0) + 0.5 * lam * (J - 1.0) * (J - 1.0));
+    if (mode >= 1) {
+      double kJ = lam * (J - 1.0) - mu;
+      d3 Pc[3];  // columns of P
+      for (int j = 0; j < 3; ++j) Pc[j] = mu * f[j] + kJ * cf[j];
+      double Cc[4][3];
+      for (int j = 0; j < 3; ++j) {
+        Cc[1][j] = B[j];
+        Cc[2][j] = B[3 + j];
+        Cc[3][j] = B[6 + j];
+        Cc[0][j] = -(B[j] + B[3 + j] + B[6 + j]);
+      }
+      double sv = scale * V;
+      for (int a = 0; a < 4; ++a) {
+        d3 ga = Cc[a][0] * Pc[0] + Cc[a][1] * Pc[1] + Cc[a][2] * Pc[2];
+        atomicAdd(g + 3 * id[a], sv * ga.x);
+        atomicAdd(g + 3 * id[a] + 1, sv * ga.y);
+        atomicAdd(g + 3 * id[a] + 2, sv * ga.z);
+      }
+      if (mode >= 2) {
+        double H[81];
+        double gv[9] = {cf[0].x, cf[0].y, cf[0].z, cf[1].x, cf[1].y, cf[1].z, cf[2].x, cf[2].y, cf[2].z};
+        for (int p = 0; p < 9; ++p)
+          for (int q = 0; q < 9; ++q) H[9 * p + q] = (p == q ? mu : 0.0) + lam * gv[p] * gv[q];
+        // d2J/df_a df_b blocks: (0,1) = -[f2]x, (0,2) = [f1]x, (1,2) = -[f0]x
+        const int A_[3] = {0, 0, 1}, B_[3] = {1, 2, 2}, W_[3] = {2, 1, 0};
+        const double sg[3] = {-1.0, 1.0, -1.0};
+        for (int k = 0; k < 3; ++k) {
+          d3 w = f[W_[k]];
+          double Sk[9] = {0, -w.z, w.y, w.z, 0, -w.x, -w.y, w.x, 0};
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+              double v = kJ * sg[k] * Sk[3 * i + j];
+              H[9 * (3 * A_[k] + i) + 3 * B_[k] + j] += v;
+              H[9 * (3 * B_[k] + j) + 3 * A_[k] + i] += v;
+            }
+        }
+        if (project) project_psd<9, double>(H);
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            double blk[9];
+            for (int i = 0; i < 3; ++i)
+              for (int k = 0; k < 3; ++k) {
+                double s = 0.0;
+                for (int j = 0; j < 3; ++j)
+                  for (int l = 0; l < 3; ++l) s += Cc[a][j] * Cc[b][l] * H[9 * (3 * j + i) + 3 * l + k];
+                blk[3 * i + k] = sv * s;
+              }
+            if (Hval) {
+              HT* dst = Hval + 9 * (size_t)S.tet_blk[16 * e + 4 * a + b];
+              for (int q = 0; q < 9; ++q) atomicAdd(dst + q, (HT)blk[q]);
+            }
+            if (tetH)
+              for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) tetH[144 * (size_t)e + 12 * (3 * a + i) + 3 * b + k] = blk[3 * i + k];
+          }
+      }
+    }
+  }
+  double s = block_sum(energy);
+  if (threadIdx.x == 0 && E) atomicAdd(E, s);
+}
+
+// Stitch springs 1/2 k_c |x_i - x^_i|^2 (Eq. 2); the constant Hessian k_c I is part of the fixed matrix.
+__global__ void k_stitch(DevScene S, const double* __restrict__ xv, const double* __restrict__ stitch_hat, double k_c,
+                         double scale, int mode, double* __restrict__ g, double* __restrict__ E) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (i < S.n_stitch) {
+    int v = S.stitch_v[i];
+    d3 d = ld3(xv, v) - ld3(stitch_hat, i);
+    e = 0.5 * k_c * dot(d, d);
+    if (mode >= 1) {
+      atomicAdd(g + 3 * v, scale * k_c * d.x);
+      atomicAdd(g + 3 * v + 1, scale * k_c * d.y);
+      atomicAdd(g + 3 * v + 2, scale * k_c * d.z);
+    }
+  }
+  double s = block_sum(e);
+  if (threadIdx.x == 0) atomicAdd(E, s);
+}
+
+// ABD orthogonality kappa_A V sum_ij (a_i . a_j - delta_ij)^2 over the columns of A.
+__global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kappa_A, double scale, int mode, int project,
+                           double* __restrict__ g, double* __restrict__ Hval, double* __restrict__ E) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (b < S.nab) {
+    int base = S.nf + 4 * b;
+    d3 a[3] = {ld3(z, base + 1), ld3(z, base + 2), ld3(z, base + 3)};
+    double k = kappa_A * S.abd_vol[b];
+    double G[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) G[i][j] = dot(a[i], a[j]) - (i == j ? 1.0 : 0.0);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) e += G[i][j] * G[i][j];
+    e *= k;
+    if (mode >= 1) {
+      for (int i = 0; i < 3; ++i) {
+        d3 gi = 4.0 * k * (G[i][0] * a[0] + G[i][1] * a[1] + G[i][2] * a[2]);
+        atomicAdd(g + 3 * (base + 1 + i), scale * gi.x);
+        atomicAdd(g + 3 * (base + 1 + i) + 1, scale * gi.y);
+        atomicAdd(g + 3 * (base + 1 + i) + 2, scale * gi.z);
+      }
+    }
+    if (mode >= 2) {
+      double H[81];
+      double AAt[9];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) AAt[3 * r + c] = comp(a[0], r) * comp(a[0], c) + comp(a[1], r) * comp(a[1], c) +
+                                                     comp(a[2], r) * comp(a[2], c);
+      for (int ki = 0; ki < 3; ++ki)
+        for (int li = 0; li < 3; ++li)
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+              double h = comp(a[li], r) * comp(a[ki], c) + (r == c ? G[ki][li] : 0.0);
+              if (ki == li) h += AAt[3 * r + c];
+              H[9 * (3 * ki + r) + 3 * li + c] = 4.0 * k * h;
+            }
+      if (project) project_psd<9, double>(H);
+      for (int ki = 0; ki < 3; ++ki)
+        for (int li = 0; li < 3; ++li) {
+          double* dst = Hval + 9 * (size_t)S.abd_blk[16 * b + 4 * (1 + ki) + (1 + li)];
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) atomicAdd(dst + 3 * r + c, scale * H[9 * (3 * ki + r) + 3 * li + c]);
+        }
+    }
+  }
+  double s = block_sum(e);
+  if (threadIdx.x == 0) atomicAdd(E, s);
+}
+
+// z_out = z + alpha p ; xk_out = alpha == 1 ? xk_hat : xk + alpha pD
+__global__ void k_trial(int ndof, int nk3, const double* __restrict__ z, const double* __restrict__ p, double alpha,
+                        double* __restrict__ z_out, const double* __restrict__ xk, const double* __restrict__ pD,
+                        const double* __restrict__ xk_hat, double* __restrict__ xk_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ndof) z_out[i] = z[i] + alpha * p[i];
+  if (i < nk3) xk_out[i] = (alpha == 1.0) ? xk_hat[i] : xk[i] + alpha * pD[i];
+}
+
+__global__ void k_velocity(int ndof, const double* __restrict__ z, const double* __restrict__ z_t, double inv_dt,
+                           double* __restrict__ zd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ndof) zd[i] = (z[i] - z_t[i]) * inv_dt;
+}
+
+// max |p_F| and max |p_D| into out[0], out[1] (as ordered bits of non-negative doubles)
+__global__ void k_pnorm(int ndof, const double* __restrict__ p, int nk3, const double* __restrict__ pD,
+                        unsigned long long* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double a = (i < ndof) ? fabs(p[i]) : 0.0;
+  double b = (i < nk3) ? fabs(pD[i]) : 0.0;
+  bool bad = (i < ndof && !isfinite(p[i]));
+  a = block_max(bad ? 1e300 : a);
+  if (threadIdx.x == 0) atomicMax(out, dbits(a));
+  b = block_max(b);
+  if (threadIdx.x == 0) atomicMax(out + 1, dbits(b));
+}
+
+// p_D = xk_hat - xk
+__global__ void k_sub(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = a[i] - b[i];
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static inline int nb(int n, int t) { return (n + t - 1) / t; }
+
+void launch_predict(cudaStream_t st, const DevScene& S, const double* z, const double* zd, double dt, const double* g,
+                    double* z_t, double* z_tilde) {
+  if (S.n_nodes) k_predict<<<nb(S.n_nodes, 256), 256, 0, st>>>(S.n_nodes, S.nf, z, zd, dt, mk(g[0], g[1], g[2]), z_t, z_tilde);
+}
+void launch_kin_targets(cudaStream_t st, const DevScene& S, const double* T, double* xk_hat, double* stitch_hat) {
+  int n = S.nk > S.n_stitch ? S.nk : S.n_stitch;
+  if (n) k_kin_targets<<<nb(n, 256), 256, 0, st>>>(S, T, xk_hat, stitch_hat);
+}
+void launch_vertex_positions(cudaStream_t st, const DevScene& S, const double* z, const double* xk, double* xv) {
+  if (S.nv) k_vertex_positions<<<nb(S.nv, 256), 256, 0, st>>>(S, z, xk, xv);
+}
+void launch_vertex_disp(cudaStream_t st, const DevScene& S, const double* p, const double* pD, double* pv) {
+  if (S.nv) k_vertex_disp<<<nb(S.nv, 256), 256, 0, st>>>(S, p, pD, pv);
+}
+void launch_inertia(cudaStream_t st, const DevScene& S, const double* z, const double* z_tilde, double* g, double* E,
+                    int want_grad) {
+  if (S.n_nodes) k_inertia<<<nb(S.n_nodes, 256), 256, 0, st>>>(S, z, z_tilde, g, E, want_grad);
+}
+void launch_elastic(cudaStream_t st, const DevScene& S, const double* xv, double scale, int mode, int project,
+                    double* g, double* Hval, double* tetH, double* E) {
+  if (S.nt) k_elastic<double><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+}
+void launch_stitch(cudaStream_t st, const DevScene& S, const double* xv, const double* stitch_hat, double k_c,
+                   double scale, int mode, double* g, double* E) {
+  if (S.n_stitch) k_stitch<<<nb(S.n_stitch, 256), 256, 0, st>>>(S, xv, stitch_hat, k_c, scale, mode, g, E);
+}
+void launch_abd_orth(cudaStream_t st, const DevScene& S, const double* z, double kappa_A, double scale, int mode,
+                     int project, double* g, double* Hval, double* E) {
+  if (S.nab) k_abd_orth<<<nb(S.nab, 64), 64, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E);
+}
+void launch_trial(cudaStream_t st, int ndof, int nk3, const double* z, const double* p, double alpha, double* z_out,
+                  const double* xk, const double* pD, const double* xk_hat, double* xk_out) {
+  int n = ndof > nk3 ? ndof : nk3;
+  if (n) k_trial<<<nb(n, 256), 256, 0, st>>>(ndof, nk3, z, p, alpha, z_out, xk, pD, xk_hat, xk_out);
+}
+void launch_velocity(cudaStream_t st, int ndof, const double* z, const double* z_t, double inv_dt, double* zd) {
+  if (ndof) k_velocity<<<nb(ndof, 256), 256, 0, st>>>(ndof, z, z_t, inv_dt, zd);
+}
+void launch_pnorm(cudaStream_t st, int ndof, const double* p, int nk3, const double* pD, unsigned long long* out) {
+  int n = ndof > nk3 ? ndof : nk3;
+  if (n) k_pnorm<<<nb(n, 256), 256, 0, st>>>(ndof, p, nk3, pD, out);
+}
+void launch_sub(cudaStream_t st, int n, const double* a, const double* b, double* o) {
+  if (n) k_sub<<<nb(n, 256), 256, 0, st>>>(n, a, b, o);
+}
+
+}  // namespace ipc

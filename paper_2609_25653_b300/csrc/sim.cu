@@ -1,0 +1,876 @@
+// Host orchestration and the C ABI of ipcsim (declared in include/ipcsim.h).
+//
+// One step (Eq. 3, §III-C.2): predictor and kinematic targets; friction lag
+// at x_t; then Newton iterations, each assembling gradient and PSD-projected
+// Hessian (inertia, Neo-Hookean, stitch, ABD, barrier, friction), solving
+// H_FF p_F = -(g_F + H_FD p_D) by block-Jacobi PCG, bounding the step by
+// additive CCD and backtracking on the incremental potential.  Kinematic
+// vertices are Dirichlet: p_D = x^_D - x_D moves them with the same step
+// fraction; while p_D != 0 the CCD-feasible step is taken without the
+// energy test, and a full step snaps them onto their targets.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+#include "../../include/ipcsim.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace ipc;
+
+namespace {
+thread_local std::string g_create_error;  // reason of the last failed sim_create on this thread
+}  // namespace
+
+struct ipcsim {
+  ipc_params P{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  std::vector<void*> allocs;
+
+  // host copies
+  int nf = 0, nt = 0, nab = 0, nkb = 0, nv = 0, na_v = 0, nk = 0, n_nodes = 0, nbody = 0;
+  std::vector<int> h_sv, h_tris, h_edges;
+  double kappa = 0, k_c = 0, L = 0, sh = 0;
+  double grav[3] = {0, 0, 0};
+  int nnzb = 0;
+  std::vector<double> h_Tcur;  // (nkb, 12) current kinematic transforms
+
+  DevScene S{};
+  // state
+  double *z = nullptr, *zd = nullptr, *xk = nullptr;
+  // step work
+  double *z_t = nullptr, *z_tilde = nullptr, *xk_t = nullptr, *xk_hat = nullptr, *stitch_hat = nullptr;
+  double *xv = nullptr, *xv_t = nullptr, *xv_trial = nullptr, *z_trial = nullptr, *xk_trial = nullptr;
+  double *g = nullptr, *gdir = nullptr, *rhs = nullptr, *p = nullptr, *pD = nullptr, *pv = nullptr;
+  double *Hconst = nullptr, *Hval = nullptr, *Dc = nullptr, *Dinv = nullptr;
+  double *r = nullptr, *zz = nullptr, *pp = nullptr, *y = nullptr, *partial = nullptr;
+  double* T_dev = nullptr;
+  // contact
+  int cap = 0;
+  int* rec = nullptr;
+  double* rec_s = nullptr;
+  double* pairH = nullptr;
+  int fcap = 0, n_fric = 0;
+  int* f_ids = nullptr;
+  double *f_w = nullptr, *f_n = nullptr, *f_lam = nullptr, *f_Hu = nullptr;
+  // scalars (device) and pinned host mirror
+  struct Scal {
+    double E[8];                 // inertia, elastic, barrier, friction, stitch, abd
+    unsigned long long pn[2];    // max|p_F|, max|p_D|
+    unsigned long long alpha;    // CCD bound
+    unsigned long long min_s;
+    int n_pairs;
+    int n_ccd;
+    int pcg_out[2];
+    double pcg_res;
+    int flags;
+    int pad;
+  };
+  Scal* sc_dev = nullptr;
+  Scal* sc_host = nullptr;
+  int pcg_grid_max = 1;
+};
+
+namespace {
+
+const int PCG_THREADS = 256;
+
+#define CUDA_TRY(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      sim->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return IPC_ERR_CUDA;                                                    \
+    }                                                                         \
+  } while (0)
+
+template <typename T>
+ipc_status dalloc(ipcsim* sim, T** ptr, size_t count) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    sim->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return IPC_ERR_CUDA;
+  }
+  cudaMemsetAsync(p, 0, bytes, sim->st);
+  sim->allocs.push_back(p);
+  *ptr = (T*)p;
+  return IPC_OK;
+}
+
+void dfree(ipcsim* sim, void* p) {
+  if (!p) return;
+  auto it = std::find(sim->allocs.begin(), sim->allocs.end(), p);
+  if (it != sim->allocs.end()) sim->allocs.erase(it);
+  cudaFree(p);
+}
+
+template <typename T>
+ipc_status upload(ipcsim* sim, T** ptr, const std::vector<T>& h) {
+  ipc_status s = dalloc(sim, ptr, h.size());
+  if (s) return s;
+  if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, sim->st));
+  return IPC_OK;
+}
+
+// d^2/dd^2 of b(d^2) with kappa = 1: 4 s b''(s) + 2 b'(s), s = d^2
+double barrier_dd(double d, double dhat) {
+  double sh = dhat * dhat, s = d * d, dd = s - sh, l = std::log(s / sh);
+  double b1 = -(2 * dd * l + dd * dd / s);
+  double b2 = -(2 * l + 4 * dd / s - dd * dd / (s * s));
+  return 4 * s * b2 + 2 * b1;
+}
+
+void inv3(const double* m, double* o, double& det) {
+  double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+  det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  double id = 1.0 / det;
+  o[0] = c00 * id; o[1] = (m[2] * m[7] - m[1] * m[8]) * id; o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+  o[3] = c01 * id; o[4] = (m[0] * m[8] - m[2] * m[6]) * id; o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+  o[6] = c02 * id; o[7] = (m[1] * m[6] - m[0] * m[7]) * id; o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+}
+
+ipc_status grow_pairs(ipcsim* sim, int need) {
+  int ncap = std::max(need + need / 2, 1024);
+  dfree(sim, sim->rec);
+  dfree(sim, sim->rec_s);
+  dfree(sim, sim->pairH);
+  sim->rec = nullptr; sim->rec_s = nullptr; sim->pairH = nullptr;
+  ipc_status s;
+  if ((s = dalloc(sim, &sim->rec, (size_t)8 * ncap))) return s;
+  if ((s = dalloc(sim, &sim->rec_s, (size_t)ncap))) return s;
+  if ((s = dalloc(sim, &sim->pairH, (size_t)144 * ncap))) return s;
+  sim->cap = ncap;
+  return IPC_OK;
+}
+
+ipc_status grow_fric(ipcsim* sim, int need) {
+  int ncap = std::max(need + need / 2, 1024);
+  dfree(sim, sim->f_ids); dfree(sim, sim->f_w); dfree(sim, sim->f_n); dfree(sim, sim->f_lam); dfree(sim, sim->f_Hu);
+  ipc_status s;
+  if ((s = dalloc(sim, &sim->f_ids, (size_t)4 * ncap))) return s;
+  if ((s = dalloc(sim, &sim->f_w, (size_t)4 * ncap))) return s;
+  if ((s = dalloc(sim, &sim->f_n, (size_t)3 * ncap))) return s;
+  if ((s = dalloc(sim, &sim->f_lam, (size_t)ncap))) return s;
+  if ((s = dalloc(sim, &sim->f_Hu, (size_t)9 * ncap))) return s;
+  sim->fcap = ncap;
+  return IPC_OK;
+}
+
+int pair_grid(int cap) { return std::max(1, std::min((cap + 127) / 128, 148 * 8)); }
+
+// Cull the active set at xv into sim->rec; count into sc_dev->n_pairs.
+void cull(ipcsim* sim, const double* xv) {
+  cudaMemsetAsync(&sim->sc_dev->n_pairs, 0, sizeof(int), sim->st);
+  launch_cull_brute(sim->st, sim->S, xv, sim->sh, sim->rec, sim->rec_s, &sim->sc_dev->n_pairs, sim->cap);
+}
+
+ipc_status sync_scalars(ipcsim* sim) {
+  CUDA_TRY(cudaMemcpyAsync(sim->sc_host, sim->sc_dev, sizeof(ipcsim::Scal), cudaMemcpyDeviceToHost, sim->st));
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  return IPC_OK;
+}
+
+double total_energy(const ipcsim* sim, const double* E) {
+  double dt2 = sim->P.dt * sim->P.dt;
+  return E[0] + dt2 * (E[1] + E[2] + E[3] + E[4] + E[5]);
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof(d));
+  return d;
+}
+unsigned long long double_bits(double d) {
+  unsigned long long b;
+  std::memcpy(&b, &d, sizeof(b));
+  return b;
+}
+
+// Energy of the incremental potential at (zq, xkq) with positions xvq (computed here).
+ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* xvq, double* E_out, int* n_pairs) {
+  const DevScene& S = sim->S;
+  double dt2 = sim->P.dt * sim->P.dt;
+  launch_vertex_positions(sim->st, S, zq, xkq, xvq);
+  for (;;) {
+    CUDA_TRY(cudaMemsetAsync(sim->sc_dev->E, 0, sizeof(double) * 8, sim->st));
+    unsigned long long big = double_bits(1e300);
+    CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->min_s, &big, sizeof(big), cudaMemcpyHostToDevice, sim->st));
+    cull(sim, xvq);
+    launch_inertia(sim->st, S, zq, sim->z_tilde, nullptr, &sim->sc_dev->E[0], 0);
+    launch_elastic(sim->st, S, xvq, dt2, 0, 0, nullptr, nullptr, nullptr, &sim->sc_dev->E[1]);
+    launch_barrier(sim->st, pair_grid(sim->cap), S, xvq, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
+                   sim->kappa, dt2, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, &sim->sc_dev->E[2],
+                   &sim->sc_dev->min_s);
+    if (sim->P.mu > 0)
+      launch_friction(sim->st, S, xvq, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, sim->P.mu,
+                      sim->P.eps_v * sim->P.dt, dt2, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      &sim->sc_dev->E[3]);
+    launch_stitch(sim->st, S, xvq, sim->stitch_hat, sim->k_c, dt2, 0, nullptr, &sim->sc_dev->E[4]);
+    launch_abd_orth(sim->st, S, zq, sim->P.kappa_A, dt2, 0, 0, nullptr, nullptr, &sim->sc_dev->E[5]);
+    ipc_status s = sync_scalars(sim);
+    if (s) return s;
+    if (sim->sc_host->n_pairs > sim->cap) {
+      if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s;
+      continue;
+    }
+    break;
+  }
+  *E_out = total_energy(sim, sim->sc_host->E);
+  if (n_pairs) *n_pairs = sim->sc_host->n_pairs;
+  return IPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sim_last_error(const ipcsim* sim) { return sim ? sim->err.c_str() : g_create_error.c_str(); }
+
+void sim_destroy(ipcsim* sim) {
+  if (!sim) return;
+  if (sim->st) cudaStreamSynchronize(sim->st);
+  for (void* p : sim->allocs) cudaFree(p);
+  if (sim->sc_host) cudaFreeHost(sim->sc_host);
+  delete sim;
+}
+
+ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* stream, ipcsim** out) {
+  if (!out) return IPC_ERR_ARG;
+  *out = nullptr;
+  if (!D || !params) return IPC_ERR_ARG;
+  ipcsim* sim = new ipcsim();
+  sim->P = *params;
+  sim->st = (cudaStream_t)stream;
+  auto fail = [&](ipc_status s, const std::string& msg) {
+    if (!msg.empty()) sim->err = msg;
+    g_create_error = sim->err;
+    sim_destroy(sim);
+    return s;
+  };
+  const ipc_params& P = sim->P;
+  if (!(P.dt > 0) || !(P.dhat > 0) || D->n_fem_verts < 0 || D->n_tets < 0 || D->n_abd < 0 || D->n_kin < 0 ||
+      D->n_stitch < 0)
+    return fail(IPC_ERR_ARG, "invalid parameters or sizes");
+  if ((D->n_tets > 0 && (!D->tets_host || !D->fem_X_host || !D->logE_host || !D->nu_host || !D->rho_host)))
+    return fail(IPC_ERR_ARG, "missing FEM arrays");
+
+  const int nf = D->n_fem_verts, nt = D->n_tets, nab = D->n_abd, nkb = D->n_kin;
+  sim->nf = nf; sim->nt = nt; sim->nab = nab; sim->nkb = nkb;
+  for (int d = 0; d < 3; ++d) sim->grav[d] = D->gravity[d];
+
+  // ---------------- FEM preparation
+  std::vector<double> B(9 * (size_t)nt), vol(nt), mu(nt), lam(nt), mass(nf, 0.0);
+  double Emax = 0.0;
+  for (int e = 0; e < nt; ++e) {
+    const int* t = D->tets_host + 4 * e;
+    for (int a = 0; a < 4; ++a)
+      if (t[a] < 0 || t[a] >= nf) return fail(IPC_ERR_ARG, "tet vertex id out of range");
+    const double* X0 = D->fem_X_host + 3 * t[0];
+    double Dm[9];
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i < 3; ++i) Dm[3 * i + k] = D->fem_X_host[3 * t[k + 1] + i] - X0[i];
+    double det;
+    inv3(Dm, &B[9 * e], det);
+    if (!(det > 0)) return fail(IPC_ERR_INVERTED, "rest tetrahedron " + std::to_string(e) + " is inverted or degenerate");
+    vol[e] = det / 6.0;
+    double E = std::exp(D->logE_host[e]), nu = D->nu_host[e];
+    mu[e] = E / (2 * (1 + nu));
+    // model parameter: first Lame parameter + mu (small-strain limit = linear material with E, nu)
+    lam[e] = E * nu / ((1 + nu) * (1 - 2 * nu)) + mu[e];
+    Emax = std::max(Emax, E);
+    for (int a = 0; a < 4; ++a) mass[t[a]] += D->rho_host[e] * vol[e] / 4.0;
+  }
+  // surface faces: tet faces used once, outward (same face enumeration order for every run)
+  std::vector<int> fem_surf;
+  {
+    const int fo[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+    std::unordered_map<unsigned long long, int> cnt;
+    cnt.reserve(4 * (size_t)nt);
+    auto key = [](int a, int b, int c) {
+      int v[3] = {a, b, c};
+      std::sort(v, v + 3);
+      return ((unsigned long long)v[0] << 42) | ((unsigned long long)v[1] << 21) | (unsigned long long)v[2];
+    };
+    for (int f = 0; f < 4; ++f)
+      for (int e = 0; e < nt; ++e) {
+        const int* t = D->tets_host + 4 * e;
+        cnt[key(t[fo[f][0]], t[fo[f][1]], t[fo[f][2]])]++;
+      }
+    for (int f = 0; f < 4; ++f)
+      for (int e = 0; e < nt; ++e) {
+        const int* t = D->tets_host + 4 * e;
+        int a = t[fo[f][0]], b = t[fo[f][1]], c = t[fo[f][2]];
+        if (cnt[key(a, b, c)] == 1) { fem_surf.push_back(a); fem_surf.push_back(b); fem_surf.push_back(c); }
+      }
+  }
+
+  // ---------------- bodies and vertices
+  std::vector<int> fem_vbody(nf, 0);
+  int n_fem_bodies = 0;
+  for (int e = 0; e < nt; ++e) {
+    int b = D->fem_body_host ? D->fem_body_host[e] : 0;
+    n_fem_bodies = std::max(n_fem_bodies, b + 1);
+    for (int a = 0; a < 4; ++a) fem_vbody[D->tets_host[4 * e + a]] = b;
+  }
+  if (nt == 0 && nf > 0) n_fem_bodies = 1;
+  int na_v = 0, nk = 0;
+  for (int i = 0; i < nab; ++i) na_v += D->abd_nverts_host[i];
+  for (int i = 0; i < nkb; ++i) nk += D->kin_nverts_host[i];
+  const int nv = nf + na_v + nk;
+  sim->na_v = na_v; sim->nk = nk; sim->nv = nv;
+  const int n_nodes = nf + 4 * nab;
+  sim->n_nodes = n_nodes;
+  std::vector<int> vkind(nv), vbody(nv), vabd(nv, -1), bkind;
+  std::vector<double> xbar(3 * (size_t)nv);
+  for (int b = 0; b < n_fem_bodies; ++b) bkind.push_back(VK_FEM);
+  for (int v = 0; v < nf; ++v) {
+    vkind[v] = VK_FEM; vbody[v] = fem_vbody[v];
+    for (int d = 0; d < 3; ++d) xbar[3 * v + d] = D->fem_X_host[3 * v + d];
+  }
+  std::vector<int> tris_all;
+  tris_all.insert(tris_all.end(), fem_surf.begin(), fem_surf.end());
+  std::vector<double> abd_S(16 * (size_t)nab), abd_vol(nab);
+  {
+    int off = nf, xo = 0, to = 0;
+    for (int i = 0; i < nab; ++i) {
+      int nvb = D->abd_nverts_host[i], ntb = D->abd_ntris_host[i];
+      int bid = (int)bkind.size();
+      bkind.push_back(VK_ABD);
+      const double* X = D->abd_X_host + 3 * xo;
+      const int* T = D->abd_tris_host + 3 * to;
+      // volume moments of the closed outward mesh: signed tets (origin, a, b, c)
+      double V = 0, f1[3] = {0, 0, 0}, f2[9] = {0};
+      for (int t = 0; t < ntb; ++t) {
+        const double *a = X + 3 * T[3 * t], *b = X + 3 * T[3 * t + 1], *c = X + 3 * T[3 * t + 2];
+        double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+        double Vt = (a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]) / 6.0;
+        V += Vt;
+        double s[3];
+        for (int d = 0; d < 3; ++d) {
+          s[d] = a[d] + b[d] + c[d];
+          f1[d] += Vt * s[d] / 4.0;
+        }
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) f2[3 * p + q] += Vt / 20.0 * (a[p] * a[q] + b[p] * b[q] + c[p] * c[q] + s[p] * s[q]);
+      }
+      if (!(V > 0)) return fail(IPC_ERR_ARG, "ABD mesh must be closed and outward oriented");
+      double rho = D->abd_rho_host[i];
+      double* Sb = &abd_S[16 * i];
+      Sb[0] = rho * V;
+      for (int d = 0; d < 3; ++d) { Sb[1 + d] = rho * f1[d]; Sb[4 * (1 + d)] = rho * f1[d]; }
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) Sb[4 * (1 + p) + 1 + q] = rho * f2[3 * p + q];
+      abd_vol[i] = V;
+      for (int v = 0; v < nvb; ++v) {
+        int gv = off + v;
+        vkind[gv] = VK_ABD; vbody[gv] = bid; vabd[gv] = i;
+        for (int d = 0; d < 3; ++d) xbar[3 * gv + d] = X[3 * v + d];
+      }
+      for (int t = 0; t < 3 * ntb; ++t) tris_all.push_back(off + T[t]);
+      off += nvb; xo += nvb; to += ntb;
+    }
+  }
+  std::vector<int> kin_vbody(nk);
+  {
+    int off = nf + na_v, xo = 0, to = 0;
+    for (int i = 0; i < nkb; ++i) {
+      int nvb = D->kin_nverts_host[i], ntb = D->kin_ntris_host[i];
+      int bid = (int)bkind.size();
+      bkind.push_back(VK_KIN);
+      for (int v = 0; v < nvb; ++v) {
+        int gv = off + v;
+        vkind[gv] = VK_KIN; vbody[gv] = bid;
+        kin_vbody[gv - nf - na_v] = i;
+        for (int d = 0; d < 3; ++d) xbar[3 * gv + d] = D->kin_X_host[3 * (xo + v) + d];
+      }
+      for (int t = 0; t < 3 * ntb; ++t) tris_all.push_back(off + D->kin_tris_host[3 * to + t]);
+      off += nvb; xo += nvb; to += ntb;
+    }
+  }
+  sim->nbody = (int)bkind.size();
+  // edges: unique sorted vertex pairs in lexicographic order; surface vertices sorted unique
+  std::vector<std::pair<int, int>> ev;
+  ev.reserve(tris_all.size());
+  for (size_t t = 0; t + 2 < tris_all.size(); t += 3)
+    for (int k = 0; k < 3; ++k) {
+      int a = tris_all[t + k], b = tris_all[t + (k + 1) % 3];
+      ev.push_back({std::min(a, b), std::max(a, b)});
+    }
+  std::sort(ev.begin(), ev.end());
+  ev.erase(std::unique(ev.begin(), ev.end()), ev.end());
+  std::vector<int> edges;
+  for (auto& e : ev) { edges.push_back(e.first); edges.push_back(e.second); }
+  std::vector<int> sv(tris_all.begin(), tris_all.end());
+  std::sort(sv.begin(), sv.end());
+  sv.erase(std::unique(sv.begin(), sv.end()), sv.end());
+  std::vector<double> edge_rest_sq(ev.size());
+  double ell_sum = 0;
+  int ell_n = 0;
+  for (size_t k = 0; k < ev.size(); ++k) {
+    double s = 0;
+    for (int d = 0; d < 3; ++d) {
+      double q = xbar[3 * ev[k].first + d] - xbar[3 * ev[k].second + d];
+      s += q * q;
+    }
+    edge_rest_sq[k] = s;
+    if (ev[k].first < nf && ev[k].second < nf) { ell_sum += std::sqrt(s); ++ell_n; }
+  }
+  double ell = 0;
+  if (ell_n) ell = ell_sum / ell_n;
+  else if (nt) {
+    for (int e = 0; e < nt; ++e) ell += std::cbrt(vol[e]);
+    ell /= nt;
+  } else ell = P.dhat;
+  sim->h_sv = sv; sim->h_tris = tris_all; sim->h_edges = edges;
+  sim->sh = P.dhat * P.dhat;
+  if (Emax == 0) Emax = 1e5;
+  sim->kappa = P.kappa > 0 ? P.kappa : Emax * ell / barrier_dd(0.5 * P.dhat, P.dhat);
+  sim->k_c = P.k_c > 0 ? P.k_c : 100.0 * Emax * ell;
+  // L_bbox over free bodies at the initial state
+  {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int v = 0; v < nf; ++v)
+      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], D->fem_X_host[3 * v + d]); hi[d] = std::max(hi[d], D->fem_X_host[3 * v + d]); }
+    int off = nf;
+    for (int i = 0; i < nab; ++i) {
+      const double* q = D->abd_q0_host + 12 * i;
+      for (int v = 0; v < D->abd_nverts_host[i]; ++v) {
+        const double* xb = &xbar[3 * (off + v)];
+        for (int d = 0; d < 3; ++d) {
+          double x = q[d] + q[3 + d] * xb[0] + q[6 + d] * xb[1] + q[9 + d] * xb[2];
+          lo[d] = std::min(lo[d], x); hi[d] = std::max(hi[d], x);
+        }
+      }
+      off += D->abd_nverts_host[i];
+    }
+    double s = 0;
+    for (int d = 0; d < 3; ++d) s += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+    sim->L = std::sqrt(s);
+  }
+
+  // ---------------- BSR pattern: diagonal, tet couplings, ABD 4x4 grids
+  std::vector<std::vector<int>> rows(n_nodes);
+  for (int i = 0; i < n_nodes; ++i) rows[i].push_back(i);
+  for (int e = 0; e < nt; ++e) {
+    const int* t = D->tets_host + 4 * e;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) rows[t[a]].push_back(t[b]);
+  }
+  for (int i = 0; i < nab; ++i)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) rows[nf + 4 * i + a].push_back(nf + 4 * i + b);
+  std::vector<int> row_ptr(n_nodes + 1, 0), col, diag(n_nodes);
+  for (int i = 0; i < n_nodes; ++i) {
+    auto& r = rows[i];
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    row_ptr[i + 1] = row_ptr[i] + (int)r.size();
+    for (int c : r) {
+      if (c == i) diag[i] = (int)col.size();
+      col.push_back(c);
+    }
+  }
+  const int nnzb = (int)col.size();
+  sim->nnzb = nnzb;
+  auto find_blk = [&](int i, int j) {
+    auto b = col.begin() + row_ptr[i], e = col.begin() + row_ptr[i + 1];
+    return (int)(std::lower_bound(b, e, j) - col.begin());
+  };
+  std::vector<int> tet_blk(16 * (size_t)nt), abd_blk(16 * (size_t)nab);
+  for (int e = 0; e < nt; ++e) {
+    const int* t = D->tets_host + 4 * e;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) tet_blk[16 * e + 4 * a + b] = find_blk(t[a], t[b]);
+  }
+  for (int i = 0; i < nab; ++i)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) abd_blk[16 * i + 4 * a + b] = find_blk(nf + 4 * i + a, nf + 4 * i + b);
+  // constant part: mass blocks and the stitch Hessian dt^2 k_c I
+  std::vector<double> Hc(9 * (size_t)nnzb, 0.0);
+  for (int v = 0; v < nf; ++v)
+    for (int d = 0; d < 3; ++d) Hc[9 * (size_t)diag[v] + 4 * d] += mass[v];
+  for (int i = 0; i < nab; ++i)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        for (int d = 0; d < 3; ++d) Hc[9 * (size_t)abd_blk[16 * i + 4 * a + b] + 4 * d] += abd_S[16 * i + 4 * a + b];
+  for (int k = 0; k < D->n_stitch; ++k) {
+    int v = D->stitch_v_host[k];
+    if (v < 0 || v >= nf || D->stitch_b_host[k] < 0 || D->stitch_b_host[k] >= nkb)
+      return fail(IPC_ERR_ARG, "stitch index out of range");
+    for (int d = 0; d < 3; ++d) Hc[9 * (size_t)diag[v] + 4 * d] += P.dt * P.dt * sim->k_c;
+  }
+
+  // ---------------- upload
+  if (cudaStreamQuery(sim->st) == cudaErrorInvalidResourceHandle) return fail(IPC_ERR_ARG, "invalid stream");
+  DevScene& S = sim->S;
+  S.nf = nf; S.nt = nt; S.nab = nab; S.nkb = nkb; S.nv = nv; S.na_v = na_v; S.nk = nk; S.n_nodes = n_nodes;
+  S.nsv = (int)sv.size(); S.ntri = (int)tris_all.size() / 3; S.nedge = (int)ev.size(); S.nbody = sim->nbody;
+  S.nnzb = nnzb;
+  S.n_stitch = D->n_stitch;
+  ipc_status s;
+  {
+    std::vector<int> tet_i(4 * (size_t)nt);
+    for (size_t i = 0; i < tet_i.size(); ++i) tet_i[i] = D->tets_host[i];
+    int* ptr;
+    if ((s = upload(sim, &ptr, tet_i))) return fail(s, "");
+    S.tets = (const int4*)ptr;
+  }
+  {
+    double* dp; int* ip;
+    if ((s = upload(sim, &dp, B))) return fail(s, ""); S.B = dp;
+    if ((s = upload(sim, &dp, vol))) return fail(s, ""); S.vol = dp;
+    if ((s = upload(sim, &dp, mu))) return fail(s, ""); S.mu = dp;
+    if ((s = upload(sim, &dp, lam))) return fail(s, ""); S.lam = dp;
+    if ((s = upload(sim, &ip, tet_blk))) return fail(s, ""); S.tet_blk = ip;
+    if ((s = upload(sim, &ip, vkind))) return fail(s, ""); S.vkind = ip;
+    if ((s = upload(sim, &ip, vbody))) return fail(s, ""); S.vbody = ip;
+    if ((s = upload(sim, &ip, vabd))) return fail(s, ""); S.vabd = ip;
+    if ((s = upload(sim, &dp, xbar))) return fail(s, ""); S.xbar = dp;
+    if ((s = upload(sim, &ip, bkind))) return fail(s, ""); S.bkind = ip;
+    if ((s = upload(sim, &ip, sv))) return fail(s, ""); S.sv = ip;
+    if ((s = upload(sim, &ip, tris_all))) return fail(s, ""); S.tris = (const int3*)ip;
+    if ((s = upload(sim, &ip, edges))) return fail(s, ""); S.edges = (const int2*)ip;
+    if ((s = upload(sim, &dp, edge_rest_sq))) return fail(s, ""); S.edge_rest_sq = dp;
+    if ((s = upload(sim, &dp, mass))) return fail(s, ""); S.node_mass = dp;
+    if ((s = upload(sim, &dp, abd_S))) return fail(s, ""); S.abd_S = dp;
+    if ((s = upload(sim, &dp, abd_vol))) return fail(s, ""); S.abd_vol = dp;
+    if ((s = upload(sim, &ip, abd_blk))) return fail(s, ""); S.abd_blk = ip;
+    if ((s = upload(sim, &ip, kin_vbody))) return fail(s, ""); S.kin_vbody = ip;
+    std::vector<int> stv(D->stitch_v_host, D->stitch_v_host + D->n_stitch), stb(D->stitch_b_host, D->stitch_b_host + D->n_stitch);
+    std::vector<double> stx(D->stitch_X_host, D->stitch_X_host + 3 * D->n_stitch);
+    if ((s = upload(sim, &ip, stv))) return fail(s, ""); S.stitch_v = ip;
+    if ((s = upload(sim, &ip, stb))) return fail(s, ""); S.stitch_b = ip;
+    if ((s = upload(sim, &dp, stx))) return fail(s, ""); S.stitch_X = dp;
+    if ((s = upload(sim, &ip, row_ptr))) return fail(s, ""); S.bsr_row = ip;
+    if ((s = upload(sim, &ip, col))) return fail(s, ""); S.bsr_col = ip;
+    if ((s = upload(sim, &ip, diag))) return fail(s, ""); S.bsr_diag = ip;
+    if ((s = upload(sim, &sim->Hconst, Hc))) return fail(s, "");
+  }
+  // state
+  const int ndof = 3 * n_nodes;
+  {
+    std::vector<double> z(ndof, 0.0), zd(ndof, 0.0);
+    for (int i = 0; i < 3 * nf; ++i) {
+      z[i] = D->fem_X_host[i];
+      if (D->fem_V0_host) zd[i] = D->fem_V0_host[i];
+    }
+    for (int i = 0; i < nab; ++i)
+      for (int k = 0; k < 12; ++k) z[3 * nf + 12 * i + k] = D->abd_q0_host[12 * i + k];
+    if ((s = upload(sim, &sim->z, z))) return fail(s, "");
+    if ((s = upload(sim, &sim->zd, zd))) return fail(s, "");
+    sim->h_Tcur.assign(D->kin_T0_host, D->kin_T0_host + 12 * nkb);
+    std::vector<double> xk(3 * (size_t)nk);
+    for (int i = 0; i < nk; ++i) {
+      const double* M = &sim->h_Tcur[12 * kin_vbody[i]];
+      const double* xb = &xbar[3 * (nf + na_v + i)];
+      for (int d = 0; d < 3; ++d) xk[3 * i + d] = M[4 * d] * xb[0] + M[4 * d + 1] * xb[1] + M[4 * d + 2] * xb[2] + M[4 * d + 3];
+    }
+    if ((s = upload(sim, &sim->xk, xk))) return fail(s, "");
+  }
+  double** bufs3n[] = {&sim->z_t, &sim->z_tilde, &sim->z_trial, &sim->g, &sim->gdir, &sim->rhs, &sim->p,
+                       &sim->r, &sim->zz, &sim->pp, &sim->y};
+  for (auto b : bufs3n)
+    if ((s = dalloc(sim, b, ndof))) return fail(s, "");
+  double** bufsk[] = {&sim->xk_t, &sim->xk_hat, &sim->xk_trial, &sim->pD};
+  for (auto b : bufsk)
+    if ((s = dalloc(sim, b, 3 * (size_t)nk))) return fail(s, "");
+  double** bufsv[] = {&sim->xv, &sim->xv_t, &sim->xv_trial, &sim->pv};
+  for (auto b : bufsv)
+    if ((s = dalloc(sim, b, 3 * (size_t)nv))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->stitch_hat, 3 * (size_t)D->n_stitch))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->Hval, 9 * (size_t)nnzb))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->Dc, 9 * (size_t)n_nodes))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->Dinv, 9 * (size_t)n_nodes))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->T_dev, 12 * (size_t)std::max(nkb, 1)))) return fail(s, "");
+  sim->pcg_grid_max = pcg_max_blocks(PCG_THREADS);
+  if ((s = dalloc(sim, &sim->partial, 3 * (size_t)sim->pcg_grid_max))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->sc_dev, 1))) return fail(s, "");
+  if (cudaMallocHost((void**)&sim->sc_host, sizeof(ipcsim::Scal)) != cudaSuccess) return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
+  std::memset(sim->sc_host, 0, sizeof(ipcsim::Scal));
+  int cap0 = P.pair_capacity > 0 ? P.pair_capacity : std::max(1024, 2 * (S.nsv + S.nedge));
+  if ((s = grow_pairs(sim, cap0 * 2 / 3 + 1))) return fail(s, "");
+  if ((s = grow_fric(sim, cap0 * 2 / 3 + 1))) return fail(s, "");
+  if (cudaMemcpyAsync(sim->T_dev, sim->h_Tcur.data(), sizeof(double) * 12 * nkb, cudaMemcpyHostToDevice, sim->st) != cudaSuccess && nkb)
+    return fail(IPC_ERR_CUDA, "upload of transforms failed");
+  // initial state must be intersection free: no pair at zero distance
+  launch_vertex_positions(sim->st, S, sim->z, sim->xk, sim->xv);
+  cull(sim, sim->xv);
+  if (sync_scalars(sim)) return fail(IPC_ERR_CUDA, "");
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return fail(IPC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(ce));
+  if (sim->sc_host->n_pairs > sim->cap) {
+    if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return fail(s, "");
+    cull(sim, sim->xv);
+    if (sync_scalars(sim)) return fail(IPC_ERR_CUDA, "");
+  }
+  {
+    int n = std::min(sim->sc_host->n_pairs, sim->cap);
+    std::vector<double> ss(n);
+    if (n) cudaMemcpy(ss.data(), sim->rec_s, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    for (double v : ss)
+      if (!(v > 0)) return fail(IPC_ERR_INTERSECTING, "initial state has a contact pair at zero distance");
+  }
+  *out = sim;
+  return IPC_OK;
+}
+
+ipc_status sim_sizes(const ipcsim* sim, int* o) {
+  if (!sim || !o) return IPC_ERR_ARG;
+  o[0] = sim->nf; o[1] = sim->nt; o[2] = sim->nab; o[3] = sim->nkb;
+  o[4] = (int)sim->h_tris.size() / 3; o[5] = (int)sim->h_edges.size() / 2; o[6] = (int)sim->h_sv.size();
+  o[7] = sim->n_nodes; o[8] = sim->nnzb;
+  return IPC_OK;
+}
+
+ipc_status sim_scalars(const ipcsim* sim, double* o) {
+  if (!sim || !o) return IPC_ERR_ARG;
+  o[0] = sim->kappa; o[1] = sim->k_c; o[2] = sim->L; o[3] = sim->P.dhat;
+  return IPC_OK;
+}
+
+ipc_status sim_surface(const ipcsim* sim, int* sv, int* tris, int* edges) {
+  if (!sim) return IPC_ERR_ARG;
+  if (sv) std::memcpy(sv, sim->h_sv.data(), sizeof(int) * sim->h_sv.size());
+  if (tris) std::memcpy(tris, sim->h_tris.data(), sizeof(int) * sim->h_tris.size());
+  if (edges) std::memcpy(edges, sim->h_edges.data(), sizeof(int) * sim->h_edges.size());
+  return IPC_OK;
+}
+
+ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats) {
+  if (!sim) return IPC_ERR_ARG;
+  if (sim->nkb && !kin_T_next) { sim->err = "kinematic transforms required"; return IPC_ERR_ARG; }
+  const DevScene& S = sim->S;
+  const ipc_params& P = sim->P;
+  const int ndof = 3 * sim->n_nodes, nk3 = 3 * sim->nk;
+  const double dt = P.dt, dt2 = dt * dt;
+  ipc_step_stats st{};
+  st.alpha_min = 1.0;
+  st.min_dist = 1e300;
+  cudaStream_t cs = sim->st;
+  if (sim->nkb) CUDA_TRY(cudaMemcpyAsync(sim->T_dev, kin_T_next, sizeof(double) * 12 * sim->nkb, cudaMemcpyHostToDevice, cs));
+  launch_predict(cs, S, sim->z, sim->zd, dt, sim->grav, sim->z_t, sim->z_tilde);
+  if (nk3) CUDA_TRY(cudaMemcpyAsync(sim->xk_t, sim->xk, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, cs));
+  launch_kin_targets(cs, S, sim->T_dev, sim->xk_hat, sim->stitch_hat);
+  launch_vertex_positions(cs, S, sim->z, sim->xk, sim->xv);
+  CUDA_TRY(cudaMemcpyAsync(sim->xv_t, sim->xv, sizeof(double) * 3 * sim->nv, cudaMemcpyDeviceToDevice, cs));
+  ipc_status s = IPC_OK;
+  // friction lag on the pairs active at x_t
+  sim->n_fric = 0;
+  if (P.mu > 0) {
+    for (;;) {
+      cull(sim, sim->xv);
+      if ((s = sync_scalars(sim))) return s;
+      if (sim->sc_host->n_pairs > sim->cap) { if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s; continue; }
+      break;
+    }
+    int n = sim->sc_host->n_pairs;
+    if (n > sim->fcap && (s = grow_fric(sim, n))) return s;
+    launch_friction_lag(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
+                        sim->kappa, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam);
+    sim->n_fric = n;
+  }
+  st.n_friction_pairs = sim->n_fric;
+  const double tol_abs = P.newton_tol * dt * sim->L;
+  const int max_pcg = P.max_pcg > 0 ? P.max_pcg : (int)(10.0 * std::sqrt((double)ndof)) + 100;
+  bool converged = false;
+  int it = 0;
+  auto restore = [&]() {
+    cudaMemcpyAsync(sim->z, sim->z_t, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, cs);
+    if (nk3) cudaMemcpyAsync(sim->xk, sim->xk_t, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, cs);
+    cudaStreamSynchronize(cs);
+  };
+  auto finish = [&](ipc_status code, const char* msg) {
+    st.status = code;
+    if (code != IPC_OK) {
+      sim->err = msg;
+      restore();
+    }
+    if (stats) *stats = st;
+    return code;
+  };
+  while (it < P.max_newton) {
+    // ---- assemble gradient, Hessian and Dirichlet coupling at the current iterate
+    CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
+    unsigned long long one = double_bits(1.0), big = double_bits(1e300);
+    CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, &one, sizeof(one), cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->min_s, &big, sizeof(big), cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
+    CUDA_TRY(cudaMemsetAsync(sim->gdir, 0, sizeof(double) * ndof, cs));
+    CUDA_TRY(cudaMemsetAsync(sim->Dc, 0, sizeof(double) * 9 * sim->n_nodes, cs));
+    launch_vertex_positions(cs, S, sim->z, sim->xk, sim->xv);
+    launch_sub(cs, nk3, sim->xk_hat, sim->xk, sim->pD);
+    cull(sim, sim->xv);
+    launch_inertia(cs, S, sim->z, sim->z_tilde, sim->g, &sim->sc_dev->E[0], 1);
+    launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
+    launch_stitch(cs, S, sim->xv, sim->stitch_hat, sim->k_c, dt2, 1, sim->g, &sim->sc_dev->E[4]);
+    launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g, sim->Hval, &sim->sc_dev->E[5]);
+    launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh, sim->kappa,
+                   dt2, 2, 1, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2], &sim->sc_dev->min_s);
+    if (P.mu > 0)
+      launch_friction(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, P.mu,
+                      P.eps_v * dt, dt2, 2, sim->g, sim->f_Hu, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[3]);
+    launch_rhs(cs, ndof, sim->g, sim->gdir, sim->rhs);
+    launch_dinv(cs, sim->n_nodes, S.bsr_diag, sim->Hval, sim->Dc, sim->Dinv);
+    // ---- PCG
+    PcgArgs a{};
+    a.S = S; a.n_nodes = sim->n_nodes; a.row = S.bsr_row; a.col = S.bsr_col; a.val = sim->Hval;
+    a.rec = sim->rec; a.n_pairs = &sim->sc_dev->n_pairs; a.cap = sim->cap; a.pairH = sim->pairH;
+    a.n_fric = P.mu > 0 ? sim->n_fric : 0; a.f_ids = sim->f_ids; a.f_w = sim->f_w; a.f_Hu = sim->f_Hu;
+    a.Dinv = sim->Dinv; a.b = sim->rhs; a.x = sim->p; a.r = sim->r; a.z = sim->zz; a.p = sim->pp; a.y = sim->y;
+    a.partial = sim->partial; a.rtol = P.pcg_rtol; a.max_iter = max_pcg;
+    a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
+    int work = std::max(sim->n_nodes, sim->cap / 4);
+    int grid = std::max(1, std::min(sim->pcg_grid_max, (work + PCG_THREADS - 1) / PCG_THREADS));
+    CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a));
+    // ---- direction norms and CCD bound
+    launch_pnorm(cs, ndof, sim->p, nk3, sim->pD, sim->sc_dev->pn);
+    launch_vertex_disp(cs, S, sim->p, sim->pD, sim->pv);
+    launch_ccd_brute(cs, S, sim->xv, sim->pv, P.s_ccd, ACCD_MAX_ITER, &sim->sc_dev->alpha, &sim->sc_dev->n_ccd);
+    if ((s = sync_scalars(sim))) return s;
+    CUDA_TRY(cudaGetLastError());
+    const ipcsim::Scal& h = *sim->sc_host;
+    if (h.n_pairs > sim->cap) {
+      if ((s = grow_pairs(sim, h.n_pairs))) return finish(s, "pair buffer growth failed");
+      continue;
+    }
+    ++it;
+    st.newton_iters = it;
+    st.pcg_iters_total += h.pcg_out[0];
+    st.pcg_iters_max = std::max(st.pcg_iters_max, h.pcg_out[0]);
+    st.n_pairs_max = std::max(st.n_pairs_max, h.n_pairs);
+    st.n_ccd_max = std::max(st.n_ccd_max, h.n_ccd);
+    double E = total_energy(sim, h.E);
+    if (!std::isfinite(E)) return finish(IPC_ERR_NAN, "non-finite energy");
+    if (h.pcg_out[1] == 2) return finish(IPC_ERR_NAN, "non-finite PCG iterate");
+    if (h.pcg_out[1] == 1) return finish(IPC_ERR_PCG, "PCG breakdown (p^T A p <= 0)");
+    double pn = bits_to_double(h.pn[0]), pdn = bits_to_double(h.pn[1]);
+    if (!std::isfinite(pn)) return finish(IPC_ERR_NAN, "non-finite Newton direction");
+    double min_s_it = bits_to_double(h.min_s);
+    if (min_s_it < 1e299) st.min_dist = std::min(st.min_dist, std::sqrt(min_s_it));
+    st.pnorm_end = pn / (dt * sim->L);
+    st.energy_end = E;
+    bool dirichlet_done = (pdn == 0.0);
+    if (dirichlet_done && pn <= tol_abs) { converged = true; break; }
+    double alpha = std::min(1.0, bits_to_double(h.alpha));
+    double E_new = 0;
+    if (dirichlet_done) {
+      int halv = 0;
+      for (;;) {
+        launch_trial(cs, ndof, nk3, sim->z, sim->p, alpha, sim->z_trial, sim->xk, sim->pD, sim->xk_hat, sim->xk_trial);
+        if ((s = energy_at(sim, sim->z_trial, sim->xk_trial, sim->xv_trial, &E_new, nullptr))) return s;
+        if (E_new <= E + 1e-13 * std::fabs(E)) break;
+        alpha *= 0.5;
+        if (++halv > 40) return finish(IPC_ERR_LS_STALL, "line search stalled");
+      }
+      st.ls_halvings += halv;
+    } else {
+      launch_trial(cs, ndof, nk3, sim->z, sim->p, alpha, sim->z_trial, sim->xk, sim->pD, sim->xk_hat, sim->xk_trial);
+    }
+    st.alpha_min = std::min(st.alpha_min, alpha);
+    std::swap(sim->z, sim->z_trial);
+    std::swap(sim->xk, sim->xk_trial);
+  }
+  if (!converged) return finish(IPC_ERR_NEWTON_MAXIT, "Newton did not converge");
+  launch_velocity(cs, ndof, sim->z, sim->z_t, 1.0 / dt, sim->zd);
+  std::memcpy(sim->h_Tcur.data(), kin_T_next, sizeof(double) * 12 * sim->nkb);
+  CUDA_TRY(cudaStreamSynchronize(cs));
+  CUDA_TRY(cudaGetLastError());
+  return finish(IPC_OK, "");
+}
+
+ipc_status sim_get_state(const ipcsim* csim, double* x, double* v, double* q, double* qd, int on_device) {
+  ipcsim* sim = const_cast<ipcsim*>(csim);
+  if (!sim) return IPC_ERR_ARG;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  size_t nfb = sizeof(double) * 3 * sim->nf, nab = sizeof(double) * 12 * sim->nab;
+  if (x && nfb) CUDA_TRY(cudaMemcpyAsync(x, sim->z, nfb, k, sim->st));
+  if (v && nfb) CUDA_TRY(cudaMemcpyAsync(v, sim->zd, nfb, k, sim->st));
+  if (q && nab) CUDA_TRY(cudaMemcpyAsync(q, sim->z + 3 * sim->nf, nab, k, sim->st));
+  if (qd && nab) CUDA_TRY(cudaMemcpyAsync(qd, sim->zd + 3 * sim->nf, nab, k, sim->st));
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  return IPC_OK;
+}
+
+ipc_status sim_set_state(ipcsim* sim, const double* x, const double* v, const double* q, const double* qd,
+                         int on_device) {
+  if (!sim) return IPC_ERR_ARG;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  size_t nfb = sizeof(double) * 3 * sim->nf, nab = sizeof(double) * 12 * sim->nab;
+  if (x && nfb) CUDA_TRY(cudaMemcpyAsync(sim->z, x, nfb, k, sim->st));
+  if (v && nfb) CUDA_TRY(cudaMemcpyAsync(sim->zd, v, nfb, k, sim->st));
+  if (q && nab) CUDA_TRY(cudaMemcpyAsync(sim->z + 3 * sim->nf, q, nab, k, sim->st));
+  if (qd && nab) CUDA_TRY(cudaMemcpyAsync(sim->zd + 3 * sim->nf, qd, nab, k, sim->st));
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  return IPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stage entry points
+// ---------------------------------------------------------------------------
+
+ipc_status sim_eval_elastic(ipcsim* sim, const double* x_dev, int project, double* E_dev, double* grad_dev,
+                            double* H_dev) {
+  if (!sim || !x_dev || !E_dev || !grad_dev) return IPC_ERR_ARG;
+  CUDA_TRY(cudaMemsetAsync(E_dev, 0, sizeof(double), sim->st));
+  CUDA_TRY(cudaMemsetAsync(grad_dev, 0, sizeof(double) * 3 * sim->nf, sim->st));
+  launch_elastic(sim->st, sim->S, x_dev, 1.0, H_dev ? 2 : 1, project, grad_dev, nullptr, H_dev, E_dev);
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+ipc_status sim_active_pairs(ipcsim* sim, const double* x_dev, int cap, int* rec_dev, double* s_dev, int* n_host) {
+  if (!sim || !x_dev || !rec_dev || !n_host) return IPC_ERR_ARG;
+  CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->n_pairs, 0, sizeof(int), sim->st));
+  launch_cull_brute(sim->st, sim->S, x_dev, sim->sh, rec_dev, s_dev, &sim->sc_dev->n_pairs, cap);
+  CUDA_TRY(cudaMemcpyAsync(n_host, &sim->sc_dev->n_pairs, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  CUDA_TRY(cudaGetLastError());
+  return *n_host > cap ? IPC_ERR_CAPACITY : IPC_OK;
+}
+
+ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* rec_dev, int project, double* E_dev,
+                            double* grad_dev, double* H_dev) {
+  if (!sim || !x_dev || n < 0 || (n && !rec_dev) || !E_dev || !grad_dev || (n && !H_dev)) return IPC_ERR_ARG;
+  int* n_dev;
+  double *Dc, *gdir, *pDz, *gnode;
+  ipc_status s;
+  if ((s = dalloc(sim, &n_dev, 1))) return s;
+  if ((s = dalloc(sim, &Dc, 9 * (size_t)sim->n_nodes))) return s;
+  if ((s = dalloc(sim, &gdir, 3 * (size_t)sim->n_nodes))) return s;
+  if ((s = dalloc(sim, &pDz, 3 * (size_t)std::max(sim->nk, 1)))) return s;
+  if ((s = dalloc(sim, &gnode, 3 * (size_t)sim->n_nodes))) return s;
+  CUDA_TRY(cudaMemcpyAsync(n_dev, &n, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+  CUDA_TRY(cudaMemsetAsync(E_dev, 0, sizeof(double), sim->st));
+  launch_barrier(sim->st, pair_grid(n), sim->S, x_dev, rec_dev, n_dev, n, sim->sh, sim->kappa, 1.0, 2, project, gnode,
+                 H_dev, Dc, pDz, gdir, E_dev, nullptr);
+  CUDA_TRY(cudaMemcpyAsync(grad_dev, gnode, sizeof(double) * 3 * sim->n_nodes, cudaMemcpyDeviceToDevice, sim->st));
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  CUDA_TRY(cudaGetLastError());
+  dfree(sim, n_dev); dfree(sim, Dc); dfree(sim, gdir); dfree(sim, pDz); dfree(sim, gnode);
+  return IPC_OK;
+}
+
+ipc_status sim_ccd_alpha(ipcsim* sim, const double* x_dev, const double* p_dev, double* alpha_host, int* n_cand_host) {
+  if (!sim || !x_dev || !p_dev || !alpha_host) return IPC_ERR_ARG;
+  unsigned long long one = double_bits(1.0);
+  CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, &one, sizeof(one), cudaMemcpyHostToDevice, sim->st));
+  CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->n_ccd, 0, sizeof(int), sim->st));
+  launch_ccd_brute(sim->st, sim->S, x_dev, p_dev, sim->P.s_ccd, ACCD_MAX_ITER, &sim->sc_dev->alpha, &sim->sc_dev->n_ccd);
+  if (sync_scalars(sim)) return IPC_ERR_CUDA;
+  CUDA_TRY(cudaGetLastError());
+  *alpha_host = bits_to_double(sim->sc_host->alpha);
+  if (n_cand_host) *n_cand_host = sim->sc_host->n_ccd;
+  return IPC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+"""Python binding of the ipcsim C ABI (include/ipcsim.h).
+
+Argument marshalling only: every step of the IPC path runs in the CUDA
+library.  There is no CPU fallback; loading fails loudly when the library
+has not been built.  Device buffers are torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libipcsim.so")
+
+dp = C.POINTER(C.c_double)
+ip = C.POINTER(C.c_int)
+vp = C.c_void_p
+
+IPC_OK = 0
+STATUS = {0: "IPC_OK", -1: "IPC_ERR_ARG", -2: "IPC_ERR_INVERTED", -3: "IPC_ERR_INTERSECTING",
+          -4: "IPC_ERR_NEWTON_MAXIT", -5: "IPC_ERR_PCG", -6: "IPC_ERR_LS_STALL", -7: "IPC_ERR_NAN",
+          -8: "IPC_ERR_BVH_OVERFLOW", -9: "IPC_ERR_CUDA", -10: "IPC_ERR_CAPACITY"}
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [
+        ("n_fem_verts", C.c_int), ("fem_X_host", dp), ("fem_V0_host", dp),
+        ("n_tets", C.c_int), ("tets_host", ip), ("logE_host", dp), ("nu_host", dp), ("rho_host", dp),
+        ("fem_body_host", ip),
+        ("n_abd", C.c_int), ("abd_nverts_host", ip), ("abd_X_host", dp), ("abd_ntris_host", ip),
+        ("abd_tris_host", ip), ("abd_rho_host", dp), ("abd_q0_host", dp),
+        ("n_kin", C.c_int), ("kin_nverts_host", ip), ("kin_X_host", dp), ("kin_ntris_host", ip),
+        ("kin_tris_host", ip), ("kin_T0_host", dp),
+        ("n_stitch", C.c_int), ("stitch_v_host", ip), ("stitch_b_host", ip), ("stitch_X_host", dp),
+        ("gravity", C.c_double * 3),
+    ]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("mu", C.c_double),
+                ("eps_v", C.c_double), ("k_c", C.c_double), ("kappa_A", C.c_double), ("newton_tol", C.c_double),
+                ("pcg_rtol", C.c_double), ("s_ccd", C.c_double), ("max_newton", C.c_int), ("max_pcg", C.c_int),
+                ("precision", C.c_int), ("pair_capacity", C.c_int)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
+                ("pcg_iters_max", C.c_int), ("n_pairs_max", C.c_int), ("n_friction_pairs", C.c_int),
+                ("n_ccd_max", C.c_int), ("ls_halvings", C.c_int), ("alpha_min", C.c_double),
+                ("min_dist", C.c_double), ("energy_end", C.c_double), ("pnorm_end", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# every exported symbol of the C ABI and its (argtypes, restype)
+SIGNATURES = {
+    "sim_create": ([C.POINTER(SceneDesc), C.POINTER(Params), vp, C.POINTER(vp)], C.c_int),
+    "sim_step": ([vp, dp, C.POINTER(StepStats)], C.c_int),
+    "sim_get_state": ([vp, vp, vp, vp, vp, C.c_int], C.c_int),
+    "sim_set_state": ([vp, vp, vp, vp, vp, C.c_int], C.c_int),
+    "sim_sizes": ([vp, ip], C.c_int),
+    "sim_scalars": ([vp, dp], C.c_int),
+    "sim_last_error": ([vp], C.c_char_p),
+    "sim_destroy": ([vp], None),
+    "sim_eval_elastic": ([vp, vp, C.c_int, vp, vp, vp], C.c_int),
+    "sim_active_pairs": ([vp, vp, C.c_int, vp, vp, ip], C.c_int),
+    "sim_surface": ([vp, ip, ip, ip], C.c_int),
+    "sim_eval_barrier": ([vp, vp, C.c_int, vp, C.c_int, vp, vp, vp], C.c_int),
+    "sim_ccd_alpha": ([vp, vp, vp, dp, ip], C.c_int),
+}
+
+
+def load():
+    """Load the built CUDA library (raises if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"ipcsim CUDA library not built: {LIB_PATH} (run paper_2609_25653_b300/build.py)")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+class IpcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def make_params(p: dict, precision=PREC_FP64) -> Params:
+    return Params(dt=p["dt"], dhat=p["dhat"], kappa=p.get("kappa", 0.0), mu=p["mu"], eps_v=p["eps_v"],
+                  k_c=p.get("k_c", 0.0), kappa_A=p.get("kappa_A", 1e8), newton_tol=p["newton_tol"],
+                  pcg_rtol=p.get("pcg_rtol", 1e-4), s_ccd=p.get("s_ccd", 0.1), max_newton=int(p.get("max_newton", 100)),
+                  max_pcg=int(p.get("max_pcg", 0)), precision=int(precision), pair_capacity=int(p.get("pair_capacity", 0)))
+
+
+class Simulator:
+    """One scene on the GPU.  `scene` is a dictionary from paper_2609_25653_b300.scenes."""
+
+    def __init__(self, scene: dict, precision=PREC_FP64, stream=None, **param_overrides):
+        L = load()
+        self.scene = scene
+        p = dict(scene["params"])
+        p.update(param_overrides)
+        self.params = p
+        keep = []
+
+        def arr_d(a):
+            a = _f64(a)
+            keep.append(a)
+            return a.ctypes.data_as(dp)
+
+        def arr_i(a):
+            a = _i32(a)
+            keep.append(a)
+            return a.ctypes.data_as(ip)
+
+        d = SceneDesc()
+        X = _f64(scene["fem_X"])
+        d.n_fem_verts = X.shape[0]
+        d.fem_X_host = arr_d(X)
+        d.fem_V0_host = arr_d(scene["fem_V0"]) if "fem_V0" in scene else None
+        d.n_tets = len(scene["fem_tets"])
+        d.tets_host = arr_i(scene["fem_tets"])
+        d.logE_host = arr_d(scene["fem_logE"])
+        d.nu_host = arr_d(scene["fem_nu"])
+        d.rho_host = arr_d(scene["fem_rho"])
+        d.fem_body_host = arr_i(scene["fem_body"]) if "fem_body" in scene else None
+        abd = scene.get("abd", [])
+        d.n_abd = len(abd)
+        if abd:
+            d.abd_nverts_host = arr_i([a["X"].shape[0] for a in abd])
+            d.abd_X_host = arr_d(np.concatenate([a["X"] for a in abd]))
+            d.abd_ntris_host = arr_i([len(a["tris"]) for a in abd])
+            d.abd_tris_host = arr_i(np.concatenate([a["tris"] for a in abd]))
+            d.abd_rho_host = arr_d([a["rho"] for a in abd])
+            d.abd_q0_host = arr_d(np.stack([a["q0"] for a in abd]))
+        kin = scene.get("kin", [])
+        d.n_kin = len(kin)
+        if kin:
+            d.kin_nverts_host = arr_i([k["X"].shape[0] for k in kin])
+            d.kin_X_host = arr_d(np.concatenate([k["X"] for k in kin]))
+            d.kin_ntris_host = arr_i([len(k["tris"]) for k in kin])
+            d.kin_tris_host = arr_i(np.concatenate([k["tris"] for k in kin]))
+            d.kin_T0_host = arr_d(scene["kin_T"][0].reshape(-1, 12))
+        sv = scene.get("stitch_v", np.zeros(0, np.int32))
+        d.n_stitch = len(sv)
+        if len(sv):
+            d.stitch_v_host = arr_i(sv)
+            d.stitch_b_host = arr_i(scene["stitch_b"])
+            d.stitch_X_host = arr_d(scene["stitch_X"])
+        for k in range(3):
+            d.gravity[k] = float(scene["gravity"][k])
+        par = make_params(p, precision)
+        h = C.c_void_p()
+        st = C.c_void_p(stream.cuda_stream if stream is not None else 0)
+        code = L.sim_create(C.byref(d), C.byref(par), st, C.byref(h))
+        if code != IPC_OK:
+            raise IpcError(code, L.sim_last_error(None).decode())
+        self.h = h
+        self.step_index = 0
+        sz = (C.c_int * 9)()
+        L.sim_sizes(h, sz)
+        (self.nf, self.nt, self.nab, self.nkb, self.ntri, self.nedge, self.nsv, self.n_nodes, self.nnzb) = list(sz)
+        self.nv = self.nf + sum(a["X"].shape[0] for a in abd) + sum(k["X"].shape[0] for k in kin)
+        sc = (C.c_double * 4)()
+        L.sim_scalars(h, sc)
+        self.kappa, self.k_c, self.L, self.dhat = list(sc)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code):
+        if code != IPC_OK:
+            raise IpcError(code, load().sim_last_error(self.h).decode())
+
+    def step(self, kin_T_next=None, raise_on_error=True):
+        """Advance one step; kin_T_next (n_kin, 3, 4).  Defaults to the scene's trajectory."""
+        if kin_T_next is None and self.nkb:
+            kin_T_next = self.scene["kin_T"][self.step_index + 1]
+        T = _f64(kin_T_next).reshape(-1) if self.nkb else None
+        stats = StepStats()
+        code = load().sim_step(self.h, T.ctypes.data_as(dp) if T is not None else None, C.byref(stats))
+        if code == IPC_OK:
+            self.step_index += 1
+        elif raise_on_error:
+            self._check(code)
+        return stats.as_dict()
+
+    def get_state(self):
+        x = np.zeros((self.nf, 3))
+        v = np.zeros((self.nf, 3))
+        q = np.zeros((self.nab, 12))
+        qd = np.zeros((self.nab, 12))
+        self._check(load().sim_get_state(self.h, x.ctypes.data_as(vp), v.ctypes.data_as(vp),
+                                         q.ctypes.data_as(vp) if self.nab else None,
+                                         qd.ctypes.data_as(vp) if self.nab else None, 0))
+        return x, v, q, qd
+
+    def get_state_device(self, x, v=None, q=None, qd=None):
+        self._check(load().sim_get_state(self.h, _ptr(x), _ptr(v), _ptr(q), _ptr(qd), 1))
+
+    def set_state(self, x=None, v=None, q=None, qd=None):
+        arrs = [None if a is None else _f64(a) for a in (x, v, q, qd)]
+        ptrs = [None if a is None else a.ctypes.data_as(vp) for a in arrs]
+        self._check(load().sim_set_state(self.h, *ptrs, 0))
+
+    # ---- stage entry points (device tensors) ---------------------------------
+    def surface(self):
+        sv = np.zeros(self.nsv, np.int32)
+        tris = np.zeros((self.ntri, 3), np.int32)
+        edges = np.zeros((self.nedge, 2), np.int32)
+        self._check(load().sim_surface(self.h, sv.ctypes.data_as(ip), tris.ctypes.data_as(ip), edges.ctypes.data_as(ip)))
+        return sv, tris, edges
+
+    def eval_elastic(self, x_dev, project=True, want_hess=True):
+        import torch
+        E = torch.zeros(1, dtype=torch.float64, device=x_dev.device)
+        g = torch.zeros((self.nf, 3), dtype=torch.float64, device=x_dev.device)
+        H = torch.zeros((self.nt, 12, 12), dtype=torch.float64, device=x_dev.device) if want_hess else None
+        self._check(load().sim_eval_elastic(self.h, _ptr(x_dev), int(project), _ptr(E), _ptr(g), _ptr(H)))
+        return E, g, H
+
+    def active_pairs(self, xv_dev, cap=None):
+        import torch
+        cap = cap or max(1024, 4 * (self.nsv + self.nedge))
+        while True:
+            rec = torch.zeros((cap, 8), dtype=torch.int32, device=xv_dev.device)
+            s = torch.zeros(cap, dtype=torch.float64, device=xv_dev.device)
+            n = C.c_int()
+            code = load().sim_active_pairs(self.h, _ptr(xv_dev), cap, _ptr(rec), _ptr(s), C.byref(n))
+            if code == -10:
+                cap = n.value
+                continue
+            self._check(code)
+            return rec[:n.value], s[:n.value]
+
+    def eval_barrier(self, xv_dev, rec_dev, project=True):
+        import torch
+        n = rec_dev.shape[0]
+        E = torch.zeros(1, dtype=torch.float64, device=xv_dev.device)
+        g = torch.zeros((self.n_nodes, 3), dtype=torch.float64, device=xv_dev.device)
+        H = torch.zeros((max(n, 1), 12, 12), dtype=torch.float64, device=xv_dev.device)
+        rec_dev = rec_dev.contiguous()
+        self._check(load().sim_eval_barrier(self.h, _ptr(xv_dev), n, _ptr(rec_dev), int(project), _ptr(E), _ptr(g),
+                                            _ptr(H)))
+        return E, g, H[:n]
+
+    def ccd_alpha(self, xv_dev, pv_dev):
+        a = C.c_double()
+        nc = C.c_int()
+        self._check(load().sim_ccd_alpha(self.h, _ptr(xv_dev), _ptr(pv_dev), C.byref(a), C.byref(nc)))
+        return a.value, nc.value
