@@ -1,0 +1,301 @@
+#!/usr/bin/env python
+"""Benchmark of the IPC time step (Eq. 3) on B300: steps/s.
+
+One "step" is one call of sim_step: the whole Newton solve of one time step
+of the workload (culling, assembly, PCG, CCD, line search).  Inputs live in
+HBM; between timed steps the L2 is flushed by writing a 256 MB buffer outside
+the timed events.  Each step is timed with CUDA events on the simulator's
+stream; `value` = steps / sum of step times (max over ranks for N > 1, each
+rank running its own replica: a single scene does not shard).
+
+`e2e` times the same steps through the public API with host buffers: the
+kinematic transforms go host -> device and the positions come back to host
+memory every step, inside the timed region.
+
+`--impl reference` times the plain FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IPC sim steps/s at 1e-5 rel pos error (plain FP64 vs batched/mixed); adjoint ms/step"
+UNIT = "steps/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def make_workload(name):
+    from paper_2609_25653_b300 import scenes
+    if name == "fingertip_press":
+        sc = scenes.fingertip_press(0, n_steps=20)
+        return sc
+    if name == "arm_gripper":
+        return scenes.arm_gripper_grasp(0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(sc, name, extra=None):
+    cfg = {"workload": sc["name"], "fem_tets": int(len(sc["fem_tets"])), "fem_verts": int(len(sc["fem_X"])),
+           "kinematic_bodies": len(sc.get("kin", [])), "abd_bodies": len(sc.get("abd", [])),
+           "dt": sc["params"]["dt"], "dhat": sc["params"]["dhat"], "mu": sc["params"]["mu"],
+           "newton_tol": sc["params"]["newton_tol"], "pcg_rtol": sc["params"]["pcg_rtol"],
+           "l2": "flushed between timed steps (256 MB write outside the timed events)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def pcg_bytes(work, sim):
+    """Algorithmic bytes the PCG kernel moves, summed over the recorded iterations.
+
+    Per iteration: every BSR block (72 B values + 4 B column index), the row
+    pointers, and per node the vectors p (read twice: gather + update), y, x,
+    r, z (read and written where updated) and the 3x3 inverse diagonal block;
+    per barrier pair its 12x12 FP64 block (1152 B) and record (32 B); per
+    friction pair its 3x3 block, weights, ids and normal (136 B)."""
+    n_nodes = sim.n_nodes
+    per_iter_fixed = work["bsr_blocks"] * (72 + 4) + (n_nodes + 1) * 4 + n_nodes * (24 * 11 + 72)
+    return (work["pcg_iters"] * per_iter_fixed + work["pcg_pair_iters"] * (1152 + 32)
+            + work["pcg_fric_iters"] * (72 + 32 + 16 + 24))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2609_25653_b300 import ipcsim
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    sc = make_workload(args.workload)
+    n_total = args.warmup + args.steps + args.steps + 1
+    if sc["kin_T"].shape[0] < n_total + 1 and len(sc.get("kin", [])):
+        raise SystemExit("workload trajectory too short for the requested steps")
+    sim = ipcsim.Simulator(sc, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        sim.step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sim.profile(True)
+    launches0 = ipcsim.kernel_launches()
+    times = []
+    stats = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = sim.step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(st)
+    torch.cuda.synchronize()
+    launches = ipcsim.kernel_launches() - launches0
+    prof, work = sim.profile_read()
+    sim.profile(False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # e2e through the public API with host buffers (transforms in, positions out)
+    x_host = np.zeros((sim.nf, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step()
+        x_host[:] = sim.get_state()[0]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps / e2e_s
+
+    # roofline of the dominant stage
+    peaks, peak_src = load_peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pcg = prof["pcg"]
+    pcg_avg_ms = pcg["ms"] / max(pcg["n"], 1)
+    pcg_bytes_per_launch = pcg_bytes(work, sim) / max(pcg["n"], 1)
+    achieved = pcg_bytes_per_launch / (pcg_avg_ms / 1e3) / 1e9 if pcg["n"] else 0.0
+    roofline = {"kernel": "k_pcg", "bound": "hbm", "achieved": round(achieved, 2),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 5),
+                "traffic": None, "peak_source": peak_src,
+                "launch_ms": round(pcg_avg_ms, 5), "algorithmic_bytes_per_launch": int(pcg_bytes_per_launch),
+                "dominant_stage": dom,
+                "stage_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["n"]}}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, args.cpu_seconds)
+    clocks = clk.summary()
+    if rank == 0:
+        newton = [s["newton_iters"] for s in stats]
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sc, args.workload, {"parallelism": f"replicas{world}",
+                                                          "newton_iters_per_step": round(sum(newton) / len(newton), 2),
+                                                          "pcg_iters_per_step": round(sum(s["pcg_iters_total"] for s in stats) / len(stats), 1),
+                                                          "active_pairs_max": max(s["n_pairs_max"] for s in stats)}),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 96 * sim.nkb,
+                    "d2h_bytes_per_step": 24 * sim.nf},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sc, seconds):
+    """The oracle as it stands, single-threaded, on a bounded prefix of the same workload."""
+    from oracle import ipc as orc
+    o = orc.Oracle(sc)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds or n >= sc["params"]["n_steps"]:
+            break
+    return {"value": round(n / el, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} steps of the same workload ({el:.1f} s, brute-force pairs, scipy sparse LU)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = make_workload(args.workload)
+    from oracle import ipc as orc
+    o = orc.Oracle(sc)
+    for _ in range(min(args.warmup, 1)):
+        o.step()
+    t0 = time.perf_counter()
+    n = 0
+    budget = args.cpu_seconds * 4
+    for _ in range(args.steps):
+        o.step()
+        n += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    el = time.perf_counter() - t0
+    v = n / el
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": 0, "steps": n,
+            "warmup": min(args.warmup, 1), "ms_per_step": round(1e3 * el / n, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sc, args.workload, {"parallelism": "cpu-1"}),
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} timed steps after the warm-up, stopped at {budget:.0f} s"},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fingertip_press")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -111,7 +111,10 @@ typedef struct {
   int max_pcg;        /* PCG iteration cap; <= 0: 10 * sqrt(n_dof) + 100 */
   int precision;      /* IPC_PREC_FP64 or IPC_PREC_MIXED */
   int pair_capacity;  /* initial contact-pair capacity; <= 0: automatic (grows on demand) */
+  int broad_phase;    /* IPC_BROAD_LBVH (default) or IPC_BROAD_ALL_PAIRS (every pair tested; for checks) */
 } ipc_params;
+
+enum { IPC_BROAD_LBVH = 0, IPC_BROAD_ALL_PAIRS = 1 };
 
 typedef struct {
   int status;             /* ipc_status of the step */
@@ -155,6 +158,20 @@ ipc_status sim_sizes(const ipcsim* sim, int* out9);
 
 /* Derived scalars fixed at create: [kappa, k_c, L_bbox, dhat]. */
 ipc_status sim_scalars(const ipcsim* sim, double* out4);
+
+/* Per-stage timing with CUDA events recorded on the simulator's stream
+ * around each stage of sim_step (cheap; intervals are read at the
+ * synchronisation points sim_step already has).  enable != 0 starts (and
+ * clears) accounting; sim_profile_read returns accumulated milliseconds and
+ * interval counts per stage [PCG, elastic, barrier, culling, CCD, friction,
+ * other, unused] and work4 = [PCG iterations, sum over iterations of barrier
+ * pairs, of friction pairs, BSR blocks]. */
+ipc_status sim_profile(ipcsim* sim, int enable);
+ipc_status sim_profile_read(const ipcsim* sim, double* ms8, long long* n8, long long* work4);
+
+/* Total number of CUDA kernels this library has launched in this process
+ * (all simulators, all threads), for launch accounting. */
+unsigned long long sim_kernel_launches(void);
 
 /* Reason of the last failure of `sim`; with sim == NULL, of the last failed
  * sim_create on the calling thread. */

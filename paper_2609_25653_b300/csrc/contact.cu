@@ -347,10 +347,12 @@ void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* 
                     double* Dc, const double* pD, double* gdir, double* E, unsigned long long* min_s) {
   k_barrier<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, mode, project, g, pairH, Dc, pD, gdir, E,
                                   min_s);
+  count_launch();
 }
 void launch_friction_lag(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
                          int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam) {
   k_friction_lag<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, f_ids, f_w, f_n, f_lam);
+  count_launch();
 }
 void launch_friction(cudaStream_t st, const DevScene& S, const double* xv, const double* xv_t, int n, const int* f_ids,
                      const double* f_w, const double* f_n, const double* f_lam, double mu, double eps, double scale,
@@ -358,6 +360,7 @@ void launch_friction(cudaStream_t st, const DevScene& S, const double* xv, const
   if (n <= 0) return;
   k_friction<<<(n + 127) / 128, 128, 0, st>>>(S, xv, xv_t, n, f_ids, f_w, f_n, f_lam, mu, eps, scale, mode, g, f_Hu, Dc,
                                               pD, gdir, E);
+  count_launch();
 }
 
 }  // namespace ipc

@@ -10,6 +10,7 @@
 // This file is compiled with -fmad=false: the classification and the
 // squared distance that decide membership (s < dhat^2) round operation by
 // operation as written, so the active set is exactly reproducible.
+#include "bvh.cuh"
 #include "common.cuh"
 #include "dist.cuh"
 #include "kernels.h"
@@ -169,20 +170,186 @@ __global__ void k_ccd_ee_brute(DevScene S, const double* __restrict__ xv, const 
 }
 
 // ---------------------------------------------------------------------------
+// LBVH queries: the same exact tests as above, on the leaves whose boxes overlap
+// ---------------------------------------------------------------------------
+constexpr int STACK = 64;
+
+struct TreeView {
+  int n;
+  const int* prim;
+  const int* left;
+  const int* right;
+  const double* box;
+};
+__host__ inline TreeView view(const Bvh& B) { return TreeView{B.n, B.prim, B.left, B.right, B.box}; }
+
+// Visit every leaf whose box overlaps q; f(primitive) per leaf.  Returns false on stack overflow.
+template <typename F>
+__device__ inline bool traverse(const TreeView& T, const double* q, F f) {
+  if (T.n <= 0) return true;
+  int stack[STACK];
+  int sp = 0;
+  stack[sp++] = 0;
+  while (sp > 0) {
+    int node = stack[--sp];
+    if (!box_overlap(T.box + 6 * (size_t)node, q)) continue;
+    if (node >= T.n - 1) {
+      f(T.prim[node - (T.n - 1)]);
+    } else {
+      if (sp + 2 > STACK) return false;
+      stack[sp++] = T.right[node];
+      stack[sp++] = T.left[node];
+    }
+  }
+  return true;
+}
+
+// Active point-triangle pairs: thread per surface vertex; the triangle leaves carry boxes widened by >= dhat.
+__global__ void k_cull_pt_bvh(DevScene S, const double* __restrict__ xv, double sh, TreeView T, int* rec, double* rec_s,
+                              int* count, int cap, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nsv) return;
+  int p = S.sv[i];
+  d3 xp = ld3(xv, p);
+  double q[6] = {xp.x, xp.y, xp.z, xp.x, xp.y, xp.z};
+  bool ok = traverse(T, q, [&](int t) {
+    int3 tv = S.tris[t];
+    int tvv[3] = {tv.x, tv.y, tv.z};
+    if (excluded(S, &p, 1, tvv, 3)) return;
+    int ids[4] = {p, tv.x, tv.y, tv.z};
+    d3 x[4] = {xp, ld3(xv, tv.x), ld3(xv, tv.y), ld3(xv, tv.z)};
+    double s, w[4];
+    int type = pt_classify(x, s, w);
+    if (s < sh) emit(rec, rec_s, count, cap, 0, i, t, type, ids, s);
+  });
+  if (!ok) atomicOr(err, ERRF_BVH);
+}
+
+// Active edge-edge pairs: thread per edge a, pairs with b > a; edge leaves widened by >= dhat.
+__global__ void k_cull_ee_bvh(DevScene S, const double* __restrict__ xv, double sh, TreeView T, int* rec, double* rec_s,
+                              int* count, int cap, int* err) {
+  int ea = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ea >= S.nedge) return;
+  int2 A = S.edges[ea];
+  d3 a0 = ld3(xv, A.x), a1 = ld3(xv, A.y);
+  double q[6] = {fmin(a0.x, a1.x), fmin(a0.y, a1.y), fmin(a0.z, a1.z), fmax(a0.x, a1.x), fmax(a0.y, a1.y), fmax(a0.z, a1.z)};
+  bool ok = traverse(T, q, [&](int eb) {
+    if (eb <= ea) return;
+    int2 B = S.edges[eb];
+    int va[2] = {A.x, A.y}, vb[2] = {B.x, B.y};
+    if (excluded(S, va, 2, vb, 2)) return;
+    int ids[4] = {A.x, A.y, B.x, B.y};
+    d3 x[4] = {a0, a1, ld3(xv, B.x), ld3(xv, B.y)};
+    double s, w[4];
+    int type = ee_classify(x, s, w);
+    if (s < sh) emit(rec, rec_s, count, cap, 1, ea, eb, type, ids, s);
+  });
+  if (!ok) atomicOr(err, ERRF_BVH);
+}
+
+// CCD candidates: leaves carry swept boxes over [x, x + p]; the query is the swept box of the point / edge.
+__global__ void k_ccd_pt_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
+                             int max_iter, TreeView T, unsigned long long* alpha_bits, int* n_cand, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nsv) return;
+  int p = S.sv[i];
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf);
+  swept(xv, pv, p, la, ha);
+  double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
+  double amin = 1.0;
+  int nc = 0;
+  bool ok = traverse(T, q, [&](int t) {
+    int3 tv = S.tris[t];
+    int tvv[3] = {tv.x, tv.y, tv.z};
+    if (excluded(S, &p, 1, tvv, 3)) return;
+    int ids[4] = {p, tv.x, tv.y, tv.z};
+    d3 x[4], pp[4];
+    for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
+    ++nc;
+    amin = fmin(amin, accd(0, x, pp, s_frac, 1.0, max_iter));
+  });
+  if (!ok) atomicOr(err, ERRF_BVH);
+  if (nc) atomicAdd(n_cand, nc);
+  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+}
+
+__global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
+                             int max_iter, TreeView T, unsigned long long* alpha_bits, int* n_cand, int* err) {
+  int ea = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ea >= S.nedge) return;
+  int2 A = S.edges[ea];
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf);
+  swept(xv, pv, A.x, la, ha);
+  swept(xv, pv, A.y, la, ha);
+  double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
+  double amin = 1.0;
+  int nc = 0;
+  bool ok = traverse(T, q, [&](int eb) {
+    if (eb <= ea) return;
+    int2 B = S.edges[eb];
+    int va[2] = {A.x, A.y}, vb[2] = {B.x, B.y};
+    if (excluded(S, va, 2, vb, 2)) return;
+    int ids[4] = {A.x, A.y, B.x, B.y};
+    d3 x[4], pp[4];
+    for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
+    ++nc;
+    amin = fmin(amin, accd(1, x, pp, s_frac, 1.0, max_iter));
+  });
+  if (!ok) atomicOr(err, ERRF_BVH);
+  if (nc) atomicAdd(n_cand, nc);
+  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 void launch_cull_brute(cudaStream_t st, const DevScene& S, const double* xv, double sh, int* rec, double* rec_s,
                        int* count, int cap) {
   long long npt = (long long)S.nsv * S.ntri, nee = (long long)S.nedge * S.nedge;
-  if (npt) k_cull_pt_brute<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(S, xv, sh, rec, rec_s, count, cap);
-  if (nee) k_cull_ee_brute<<<(unsigned)((nee + 255) / 256), 256, 0, st>>>(S, xv, sh, rec, rec_s, count, cap);
+  if (npt) { k_cull_pt_brute<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(S, xv, sh, rec, rec_s, count, cap); count_launch(); }
+  if (nee) { k_cull_ee_brute<<<(unsigned)((nee + 255) / 256), 256, 0, st>>>(S, xv, sh, rec, rec_s, count, cap); count_launch(); }
 }
 
 void launch_ccd_brute(cudaStream_t st, const DevScene& S, const double* xv, const double* pv, double s_frac,
                       int max_iter, unsigned long long* alpha_bits, int* n_cand) {
   long long npt = (long long)S.nsv * S.ntri, nee = (long long)S.nedge * S.nedge;
-  if (npt) k_ccd_pt_brute<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(S, xv, pv, s_frac, max_iter, alpha_bits, n_cand);
-  if (nee) k_ccd_ee_brute<<<(unsigned)((nee + 255) / 256), 256, 0, st>>>(S, xv, pv, s_frac, max_iter, alpha_bits, n_cand);
+  if (npt) { k_ccd_pt_brute<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(S, xv, pv, s_frac, max_iter, alpha_bits, n_cand); count_launch(); }
+  if (nee) { k_ccd_ee_brute<<<(unsigned)((nee + 255) / 256), 256, 0, st>>>(S, xv, pv, s_frac, max_iter, alpha_bits, n_cand); count_launch(); }
+}
+
+}  // namespace ipc
+
+namespace ipc {
+
+// Active set through the trees: refit both trees on boxes widened by pad, then query.
+void launch_cull_bvh(cudaStream_t st, const DevScene& S, const double* xv, double sh, double pad, Bvh& tri, Bvh& edge,
+                     int* rec, double* rec_s, int* count, int cap, int* err) {
+  bvh_leaf_boxes(st, tri, (const int*)S.tris, 3, xv, nullptr, pad);
+  bvh_refit(st, tri);
+  bvh_leaf_boxes(st, edge, (const int*)S.edges, 2, xv, nullptr, pad);
+  bvh_refit(st, edge);
+  if (S.nsv) { k_cull_pt_bvh<<<(S.nsv + 127) / 128, 128, 0, st>>>(S, xv, sh, view(tri), rec, rec_s, count, cap, err); count_launch(); }
+  if (S.nedge) { k_cull_ee_bvh<<<(S.nedge + 127) / 128, 128, 0, st>>>(S, xv, sh, view(edge), rec, rec_s, count, cap, err); count_launch(); }
+}
+
+void launch_ccd_bvh(cudaStream_t st, const DevScene& S, const double* xv, const double* pv, double s_frac, int max_iter,
+                    Bvh& tri, Bvh& edge, unsigned long long* alpha_bits, int* n_cand, int* err) {
+  bvh_leaf_boxes(st, tri, (const int*)S.tris, 3, xv, pv, 0.0);
+  bvh_refit(st, tri);
+  bvh_leaf_boxes(st, edge, (const int*)S.edges, 2, xv, pv, 0.0);
+  bvh_refit(st, edge);
+  if (S.nsv) { k_ccd_pt_bvh<<<(S.nsv + 127) / 128, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, view(tri), alpha_bits, n_cand, err); count_launch(); }
+  if (S.nedge) { k_ccd_ee_bvh<<<(S.nedge + 127) / 128, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, view(edge), alpha_bits, n_cand, err); count_launch(); }
+}
+
+// Rebuild both trees (Morton sort + hierarchy) on boxes at xv widened by pad.
+void bvh_rebuild(cudaStream_t st, const DevScene& S, const double* xv, double pad, Bvh& tri, Bvh& edge) {
+  bvh_leaf_boxes(st, tri, (const int*)S.tris, 3, xv, nullptr, pad);
+  bvh_build(st, tri);
+  bvh_leaf_boxes(st, edge, (const int*)S.edges, 2, xv, nullptr, pad);
+  bvh_build(st, edge);
 }
 
 }  // namespace ipc

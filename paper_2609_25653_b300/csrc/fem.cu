@@ -291,48 +291,48 @@ static inline int nb(int n, int t) { return (n + t - 1) / t; }
 
 void launch_predict(cudaStream_t st, const DevScene& S, const double* z, const double* zd, double dt, const double* g,
                     double* z_t, double* z_tilde) {
-  if (S.n_nodes) k_predict<<<nb(S.n_nodes, 256), 256, 0, st>>>(S.n_nodes, S.nf, z, zd, dt, mk(g[0], g[1], g[2]), z_t, z_tilde);
+  if (S.n_nodes) { k_predict<<<nb(S.n_nodes, 256), 256, 0, st>>>(S.n_nodes, S.nf, z, zd, dt, mk(g[0], g[1], g[2]), z_t, z_tilde); count_launch(); }
 }
 void launch_kin_targets(cudaStream_t st, const DevScene& S, const double* T, double* xk_hat, double* stitch_hat) {
   int n = S.nk > S.n_stitch ? S.nk : S.n_stitch;
-  if (n) k_kin_targets<<<nb(n, 256), 256, 0, st>>>(S, T, xk_hat, stitch_hat);
+  if (n) { k_kin_targets<<<nb(n, 256), 256, 0, st>>>(S, T, xk_hat, stitch_hat); count_launch(); }
 }
 void launch_vertex_positions(cudaStream_t st, const DevScene& S, const double* z, const double* xk, double* xv) {
-  if (S.nv) k_vertex_positions<<<nb(S.nv, 256), 256, 0, st>>>(S, z, xk, xv);
+  if (S.nv) { k_vertex_positions<<<nb(S.nv, 256), 256, 0, st>>>(S, z, xk, xv); count_launch(); }
 }
 void launch_vertex_disp(cudaStream_t st, const DevScene& S, const double* p, const double* pD, double* pv) {
-  if (S.nv) k_vertex_disp<<<nb(S.nv, 256), 256, 0, st>>>(S, p, pD, pv);
+  if (S.nv) { k_vertex_disp<<<nb(S.nv, 256), 256, 0, st>>>(S, p, pD, pv); count_launch(); }
 }
 void launch_inertia(cudaStream_t st, const DevScene& S, const double* z, const double* z_tilde, double* g, double* E,
                     int want_grad) {
-  if (S.n_nodes) k_inertia<<<nb(S.n_nodes, 256), 256, 0, st>>>(S, z, z_tilde, g, E, want_grad);
+  if (S.n_nodes) { k_inertia<<<nb(S.n_nodes, 256), 256, 0, st>>>(S, z, z_tilde, g, E, want_grad); count_launch(); }
 }
 void launch_elastic(cudaStream_t st, const DevScene& S, const double* xv, double scale, int mode, int project,
                     double* g, double* Hval, double* tetH, double* E) {
-  if (S.nt) k_elastic<double><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+  if (S.nt) { k_elastic<double><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E); count_launch(); }
 }
 void launch_stitch(cudaStream_t st, const DevScene& S, const double* xv, const double* stitch_hat, double k_c,
                    double scale, int mode, double* g, double* E) {
-  if (S.n_stitch) k_stitch<<<nb(S.n_stitch, 256), 256, 0, st>>>(S, xv, stitch_hat, k_c, scale, mode, g, E);
+  if (S.n_stitch) { k_stitch<<<nb(S.n_stitch, 256), 256, 0, st>>>(S, xv, stitch_hat, k_c, scale, mode, g, E); count_launch(); }
 }
 void launch_abd_orth(cudaStream_t st, const DevScene& S, const double* z, double kappa_A, double scale, int mode,
                      int project, double* g, double* Hval, double* E) {
-  if (S.nab) k_abd_orth<<<nb(S.nab, 64), 64, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E);
+  if (S.nab) { k_abd_orth<<<nb(S.nab, 64), 64, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E); count_launch(); }
 }
 void launch_trial(cudaStream_t st, int ndof, int nk3, const double* z, const double* p, double alpha, double* z_out,
                   const double* xk, const double* pD, const double* xk_hat, double* xk_out) {
   int n = ndof > nk3 ? ndof : nk3;
-  if (n) k_trial<<<nb(n, 256), 256, 0, st>>>(ndof, nk3, z, p, alpha, z_out, xk, pD, xk_hat, xk_out);
+  if (n) { k_trial<<<nb(n, 256), 256, 0, st>>>(ndof, nk3, z, p, alpha, z_out, xk, pD, xk_hat, xk_out); count_launch(); }
 }
 void launch_velocity(cudaStream_t st, int ndof, const double* z, const double* z_t, double inv_dt, double* zd) {
-  if (ndof) k_velocity<<<nb(ndof, 256), 256, 0, st>>>(ndof, z, z_t, inv_dt, zd);
+  if (ndof) { k_velocity<<<nb(ndof, 256), 256, 0, st>>>(ndof, z, z_t, inv_dt, zd); count_launch(); }
 }
 void launch_pnorm(cudaStream_t st, int ndof, const double* p, int nk3, const double* pD, unsigned long long* out) {
   int n = ndof > nk3 ? ndof : nk3;
-  if (n) k_pnorm<<<nb(n, 256), 256, 0, st>>>(ndof, p, nk3, pD, out);
+  if (n) { k_pnorm<<<nb(n, 256), 256, 0, st>>>(ndof, p, nk3, pD, out); count_launch(); }
 }
 void launch_sub(cudaStream_t st, int n, const double* a, const double* b, double* o) {
-  if (n) k_sub<<<nb(n, 256), 256, 0, st>>>(n, a, b, o);
+  if (n) { k_sub<<<nb(n, 256), 256, 0, st>>>(n, a, b, o); count_launch(); }
 }
 
 }  // namespace ipc

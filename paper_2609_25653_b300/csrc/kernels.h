@@ -1,9 +1,14 @@
 // Host-side launchers of the ipcsim kernels (declarations).
 #pragma once
 #include <cuda_runtime.h>
+#include "bvh.cuh"
 #include "common.cuh"
 
 namespace ipc {
+
+// Kernel launches issued by this library (all simulators, all threads).
+extern unsigned long long g_kernel_launches;
+inline void count_launch(int n = 1) { __atomic_fetch_add(&g_kernel_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
 
 struct PcgArgs {
   DevScene S;
@@ -68,6 +73,18 @@ void launch_cull_brute(cudaStream_t, const DevScene&, const double* xv, double s
                        int cap);
 void launch_ccd_brute(cudaStream_t, const DevScene&, const double* xv, const double* pv, double s_frac, int max_iter,
                       unsigned long long* alpha_bits, int* n_cand);
+
+// bvh.cu
+cudaError_t bvh_alloc(Bvh& B, int n);
+void bvh_free(Bvh& B);
+void bvh_leaf_boxes(cudaStream_t, Bvh& B, const int* ids, int nvp, const double* xv, const double* pv, double pad);
+void bvh_refit(cudaStream_t, Bvh& B);
+void bvh_build(cudaStream_t, Bvh& B);
+void launch_cull_bvh(cudaStream_t, const DevScene&, const double* xv, double sh, double pad, Bvh& tri, Bvh& edge,
+                     int* rec, double* rec_s, int* count, int cap, int* err);
+void launch_ccd_bvh(cudaStream_t, const DevScene&, const double* xv, const double* pv, double s_frac, int max_iter,
+                    Bvh& tri, Bvh& edge, unsigned long long* alpha_bits, int* n_cand, int* err);
+void bvh_rebuild(cudaStream_t, const DevScene&, const double* xv, double pad, Bvh& tri, Bvh& edge);
 
 // pcg.cu
 void launch_dinv(cudaStream_t, int n_nodes, const int* diag, const double* val, const double* Dc, double* Dinv);

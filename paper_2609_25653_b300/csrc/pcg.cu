@@ -219,10 +219,10 @@ __global__ void k_pcg(PcgArgs a) {
 }
 
 void launch_dinv(cudaStream_t st, int n_nodes, const int* diag, const double* val, const double* Dc, double* Dinv) {
-  if (n_nodes) k_dinv<<<(n_nodes + 255) / 256, 256, 0, st>>>(n_nodes, diag, val, Dc, Dinv);
+  if (n_nodes) { k_dinv<<<(n_nodes + 255) / 256, 256, 0, st>>>(n_nodes, diag, val, Dc, Dinv); count_launch(); }
 }
 void launch_rhs(cudaStream_t st, int n, const double* g, const double* gdir, double* rhs) {
-  if (n) k_rhs<<<(n + 255) / 256, 256, 0, st>>>(n, g, gdir, rhs);
+  if (n) { k_rhs<<<(n + 255) / 256, 256, 0, st>>>(n, g, gdir, rhs); count_launch(); }
 }
 
 int pcg_max_blocks(int threads) {
@@ -235,6 +235,7 @@ int pcg_max_blocks(int threads) {
 
 cudaError_t launch_pcg(cudaStream_t st, int grid, int threads, const PcgArgs& a) {
   void* args[] = {(void*)&a};
+  count_launch();
   return cudaLaunchCooperativeKernel((void*)k_pcg, dim3(grid), dim3(threads), args, 0, st);
 }
 

@@ -24,6 +24,10 @@
 
 using namespace ipc;
 
+namespace ipc {
+unsigned long long g_kernel_launches = 0;
+}
+
 namespace {
 thread_local std::string g_create_error;  // reason of the last failed sim_create on this thread
 }  // namespace
@@ -76,6 +80,19 @@ struct ipcsim {
   Scal* sc_dev = nullptr;
   Scal* sc_host = nullptr;
   int pcg_grid_max = 1;
+  // optional per-stage CUDA-event timing on the simulator's stream
+  bool prof = false;
+  cudaEvent_t ev[2 * 8] = {};
+  double prof_ms[8] = {0};
+  long long prof_n[8] = {0};
+  bool ev_open[8] = {false};
+  // broad phase
+  Bvh tri_tree, edge_tree;
+  double bvh_pad = 0;
+  // per-step PCG work, for algorithmic-byte accounting
+  long long pcg_iters_acc = 0;
+  long long pcg_pair_iters_acc = 0;
+  long long pcg_fric_iters_acc = 0;
 };
 
 namespace {
@@ -165,17 +182,66 @@ ipc_status grow_fric(ipcsim* sim, int need) {
   return IPC_OK;
 }
 
+enum { PROF_PCG = 0, PROF_ELASTIC = 1, PROF_BARRIER = 2, PROF_CULL = 3, PROF_CCD = 4, PROF_FRICTION = 5,
+       PROF_OTHER = 6 };
+
+inline void prof_begin(ipcsim* sim, int k) {
+  if (!sim->prof) return;
+  if (!sim->ev[2 * k]) {
+    cudaEventCreate(&sim->ev[2 * k]);
+    cudaEventCreate(&sim->ev[2 * k + 1]);
+  }
+  cudaEventRecord(sim->ev[2 * k], sim->st);
+}
+inline void prof_end(ipcsim* sim, int k) {
+  if (!sim->prof) return;
+  cudaEventRecord(sim->ev[2 * k + 1], sim->st);
+  sim->ev_open[k] = true;
+}
+// called after a stream synchronisation: accumulate the recorded intervals
+inline void prof_collect(ipcsim* sim) {
+  if (!sim->prof) return;
+  for (int k = 0; k < 8; ++k)
+    if (sim->ev_open[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, sim->ev[2 * k], sim->ev[2 * k + 1]) == cudaSuccess) {
+        sim->prof_ms[k] += ms;
+        sim->prof_n[k] += 1;
+      }
+      sim->ev_open[k] = false;
+    }
+}
+
 int pair_grid(int cap) { return std::max(1, std::min((cap + 127) / 128, 148 * 8)); }
 
 // Cull the active set at xv into sim->rec; count into sc_dev->n_pairs.
-void cull(ipcsim* sim, const double* xv) {
+void cull_into(ipcsim* sim, const double* xv, int* rec, double* rec_s, int cap) {
   cudaMemsetAsync(&sim->sc_dev->n_pairs, 0, sizeof(int), sim->st);
-  launch_cull_brute(sim->st, sim->S, xv, sim->sh, sim->rec, sim->rec_s, &sim->sc_dev->n_pairs, sim->cap);
+  if (sim->P.broad_phase == IPC_BROAD_ALL_PAIRS)
+    launch_cull_brute(sim->st, sim->S, xv, sim->sh, rec, rec_s, &sim->sc_dev->n_pairs, cap);
+  else
+    launch_cull_bvh(sim->st, sim->S, xv, sim->sh, sim->bvh_pad, sim->tri_tree, sim->edge_tree, rec, rec_s,
+                    &sim->sc_dev->n_pairs, cap, &sim->sc_dev->flags);
+}
+void cull(ipcsim* sim, const double* xv) { cull_into(sim, xv, sim->rec, sim->rec_s, sim->cap); }
+
+void ccd(ipcsim* sim, const double* xv, const double* pv) {
+  if (sim->P.broad_phase == IPC_BROAD_ALL_PAIRS)
+    launch_ccd_brute(sim->st, sim->S, xv, pv, sim->P.s_ccd, ACCD_MAX_ITER, &sim->sc_dev->alpha, &sim->sc_dev->n_ccd);
+  else
+    launch_ccd_bvh(sim->st, sim->S, xv, pv, sim->P.s_ccd, ACCD_MAX_ITER, sim->tri_tree, sim->edge_tree,
+                   &sim->sc_dev->alpha, &sim->sc_dev->n_ccd, &sim->sc_dev->flags);
+}
+
+// Sort the leaves and rebuild both hierarchies at xv (once per step; iterates refit).
+void rebuild_trees(ipcsim* sim, const double* xv) {
+  if (sim->P.broad_phase != IPC_BROAD_ALL_PAIRS) bvh_rebuild(sim->st, sim->S, xv, sim->bvh_pad, sim->tri_tree, sim->edge_tree);
 }
 
 ipc_status sync_scalars(ipcsim* sim) {
   CUDA_TRY(cudaMemcpyAsync(sim->sc_host, sim->sc_dev, sizeof(ipcsim::Scal), cudaMemcpyDeviceToHost, sim->st));
   CUDA_TRY(cudaStreamSynchronize(sim->st));
+  prof_collect(sim);
   return IPC_OK;
 }
 
@@ -218,6 +284,7 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
     launch_abd_orth(sim->st, S, zq, sim->P.kappa_A, dt2, 0, 0, nullptr, nullptr, &sim->sc_dev->E[5]);
     ipc_status s = sync_scalars(sim);
     if (s) return s;
+    if (sim->sc_host->flags & ERRF_BVH) { sim->err = "BVH traversal stack overflow"; return IPC_ERR_BVH_OVERFLOW; }
     if (sim->sc_host->n_pairs > sim->cap) {
       if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s;
       continue;
@@ -233,12 +300,18 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
 
 extern "C" {
 
+unsigned long long sim_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }
+
 const char* sim_last_error(const ipcsim* sim) { return sim ? sim->err.c_str() : g_create_error.c_str(); }
 
 void sim_destroy(ipcsim* sim) {
   if (!sim) return;
   if (sim->st) cudaStreamSynchronize(sim->st);
   for (void* p : sim->allocs) cudaFree(p);
+  bvh_free(sim->tri_tree);
+  bvh_free(sim->edge_tree);
+  for (auto& e : sim->ev)
+    if (e) cudaEventDestroy(e);
   if (sim->sc_host) cudaFreeHost(sim->sc_host);
   delete sim;
 }
@@ -601,8 +674,15 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
   if ((s = grow_fric(sim, cap0 * 2 / 3 + 1))) return fail(s, "");
   if (cudaMemcpyAsync(sim->T_dev, sim->h_Tcur.data(), sizeof(double) * 12 * nkb, cudaMemcpyHostToDevice, sim->st) != cudaSuccess && nkb)
     return fail(IPC_ERR_CUDA, "upload of transforms failed");
+  // broad phase: leaf boxes widened by slightly more than dhat, so that every
+  // pair closer than dhat overlaps despite rounding of the widened bounds
+  sim->bvh_pad = P.dhat * (1.0 + 1e-6);
+  if (bvh_alloc(sim->tri_tree, S.ntri) != cudaSuccess || bvh_alloc(sim->edge_tree, S.nedge) != cudaSuccess)
+    return fail(IPC_ERR_CUDA, "BVH allocation failed");
   // initial state must be intersection free: no pair at zero distance
   launch_vertex_positions(sim->st, S, sim->z, sim->xk, sim->xv);
+  rebuild_trees(sim, sim->xv);
+  cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), sim->st);
   cull(sim, sim->xv);
   if (sync_scalars(sim)) return fail(IPC_ERR_CUDA, "");
   cudaError_t ce = cudaGetLastError();
@@ -662,6 +742,8 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   launch_kin_targets(cs, S, sim->T_dev, sim->xk_hat, sim->stitch_hat);
   launch_vertex_positions(cs, S, sim->z, sim->xk, sim->xv);
   CUDA_TRY(cudaMemcpyAsync(sim->xv_t, sim->xv, sizeof(double) * 3 * sim->nv, cudaMemcpyDeviceToDevice, cs));
+  rebuild_trees(sim, sim->xv);
+  CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
   ipc_status s = IPC_OK;
   // friction lag on the pairs active at x_t
   sim->n_fric = 0;
@@ -708,16 +790,25 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     CUDA_TRY(cudaMemsetAsync(sim->Dc, 0, sizeof(double) * 9 * sim->n_nodes, cs));
     launch_vertex_positions(cs, S, sim->z, sim->xk, sim->xv);
     launch_sub(cs, nk3, sim->xk_hat, sim->xk, sim->pD);
+    prof_begin(sim, PROF_CULL);
     cull(sim, sim->xv);
+    prof_end(sim, PROF_CULL);
     launch_inertia(cs, S, sim->z, sim->z_tilde, sim->g, &sim->sc_dev->E[0], 1);
+    prof_begin(sim, PROF_ELASTIC);
     launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
+    prof_end(sim, PROF_ELASTIC);
     launch_stitch(cs, S, sim->xv, sim->stitch_hat, sim->k_c, dt2, 1, sim->g, &sim->sc_dev->E[4]);
     launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g, sim->Hval, &sim->sc_dev->E[5]);
+    prof_begin(sim, PROF_BARRIER);
     launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh, sim->kappa,
                    dt2, 2, 1, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2], &sim->sc_dev->min_s);
-    if (P.mu > 0)
+    prof_end(sim, PROF_BARRIER);
+    if (P.mu > 0) {
+      prof_begin(sim, PROF_FRICTION);
       launch_friction(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, P.mu,
                       P.eps_v * dt, dt2, 2, sim->g, sim->f_Hu, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[3]);
+      prof_end(sim, PROF_FRICTION);
+    }
     launch_rhs(cs, ndof, sim->g, sim->gdir, sim->rhs);
     launch_dinv(cs, sim->n_nodes, S.bsr_diag, sim->Hval, sim->Dc, sim->Dinv);
     // ---- PCG
@@ -730,14 +821,19 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
     int work = std::max(sim->n_nodes, sim->cap / 4);
     int grid = std::max(1, std::min(sim->pcg_grid_max, (work + PCG_THREADS - 1) / PCG_THREADS));
+    prof_begin(sim, PROF_PCG);
     CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a));
+    prof_end(sim, PROF_PCG);
     // ---- direction norms and CCD bound
     launch_pnorm(cs, ndof, sim->p, nk3, sim->pD, sim->sc_dev->pn);
     launch_vertex_disp(cs, S, sim->p, sim->pD, sim->pv);
-    launch_ccd_brute(cs, S, sim->xv, sim->pv, P.s_ccd, ACCD_MAX_ITER, &sim->sc_dev->alpha, &sim->sc_dev->n_ccd);
+    prof_begin(sim, PROF_CCD);
+    ccd(sim, sim->xv, sim->pv);
+    prof_end(sim, PROF_CCD);
     if ((s = sync_scalars(sim))) return s;
     CUDA_TRY(cudaGetLastError());
     const ipcsim::Scal& h = *sim->sc_host;
+    if (h.flags & ERRF_BVH) return finish(IPC_ERR_BVH_OVERFLOW, "BVH traversal stack overflow");
     if (h.n_pairs > sim->cap) {
       if ((s = grow_pairs(sim, h.n_pairs))) return finish(s, "pair buffer growth failed");
       continue;
@@ -745,6 +841,11 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     ++it;
     st.newton_iters = it;
     st.pcg_iters_total += h.pcg_out[0];
+    if (sim->prof) {
+      sim->pcg_iters_acc += h.pcg_out[0];
+      sim->pcg_pair_iters_acc += (long long)h.pcg_out[0] * std::min(h.n_pairs, sim->cap);
+      sim->pcg_fric_iters_acc += (long long)h.pcg_out[0] * (P.mu > 0 ? sim->n_fric : 0);
+    }
     st.pcg_iters_max = std::max(st.pcg_iters_max, h.pcg_out[0]);
     st.n_pairs_max = std::max(st.n_pairs_max, h.n_pairs);
     st.n_ccd_max = std::max(st.n_ccd_max, h.n_ccd);
@@ -785,6 +886,29 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   CUDA_TRY(cudaStreamSynchronize(cs));
   CUDA_TRY(cudaGetLastError());
   return finish(IPC_OK, "");
+}
+
+ipc_status sim_profile(ipcsim* sim, int enable) {
+  if (!sim) return IPC_ERR_ARG;
+  sim->prof = enable != 0;
+  for (int k = 0; k < 8; ++k) { sim->prof_ms[k] = 0; sim->prof_n[k] = 0; sim->ev_open[k] = false; }
+  sim->pcg_iters_acc = sim->pcg_pair_iters_acc = sim->pcg_fric_iters_acc = 0;
+  return IPC_OK;
+}
+
+ipc_status sim_profile_read(const ipcsim* sim, double* ms8, long long* n8, long long* work4) {
+  if (!sim) return IPC_ERR_ARG;
+  for (int k = 0; k < 8; ++k) {
+    if (ms8) ms8[k] = sim->prof_ms[k];
+    if (n8) n8[k] = sim->prof_n[k];
+  }
+  if (work4) {
+    work4[0] = sim->pcg_iters_acc;
+    work4[1] = sim->pcg_pair_iters_acc;
+    work4[2] = sim->pcg_fric_iters_acc;
+    work4[3] = sim->nnzb;
+  }
+  return IPC_OK;
 }
 
 ipc_status sim_get_state(const ipcsim* csim, double* x, double* v, double* q, double* qd, int on_device) {
@@ -830,8 +954,9 @@ ipc_status sim_eval_elastic(ipcsim* sim, const double* x_dev, int project, doubl
 
 ipc_status sim_active_pairs(ipcsim* sim, const double* x_dev, int cap, int* rec_dev, double* s_dev, int* n_host) {
   if (!sim || !x_dev || !rec_dev || !n_host) return IPC_ERR_ARG;
-  CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->n_pairs, 0, sizeof(int), sim->st));
-  launch_cull_brute(sim->st, sim->S, x_dev, sim->sh, rec_dev, s_dev, &sim->sc_dev->n_pairs, cap);
+  CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), sim->st));
+  rebuild_trees(sim, x_dev);
+  cull_into(sim, x_dev, rec_dev, s_dev, cap);
   CUDA_TRY(cudaMemcpyAsync(n_host, &sim->sc_dev->n_pairs, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
   CUDA_TRY(cudaStreamSynchronize(sim->st));
   CUDA_TRY(cudaGetLastError());
@@ -865,8 +990,11 @@ ipc_status sim_ccd_alpha(ipcsim* sim, const double* x_dev, const double* p_dev, 
   unsigned long long one = double_bits(1.0);
   CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, &one, sizeof(one), cudaMemcpyHostToDevice, sim->st));
   CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->n_ccd, 0, sizeof(int), sim->st));
-  launch_ccd_brute(sim->st, sim->S, x_dev, p_dev, sim->P.s_ccd, ACCD_MAX_ITER, &sim->sc_dev->alpha, &sim->sc_dev->n_ccd);
+  CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), sim->st));
+  rebuild_trees(sim, x_dev);
+  ccd(sim, x_dev, p_dev);
   if (sync_scalars(sim)) return IPC_ERR_CUDA;
+  if (sim->sc_host->flags & ERRF_BVH) { sim->err = "BVH traversal stack overflow"; return IPC_ERR_BVH_OVERFLOW; }
   CUDA_TRY(cudaGetLastError());
   *alpha_host = bits_to_double(sim->sc_host->alpha);
   if (n_cand_host) *n_cand_host = sim->sc_host->n_ccd;

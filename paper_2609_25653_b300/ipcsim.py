@@ -23,6 +23,7 @@ STATUS = {0: "IPC_OK", -1: "IPC_ERR_ARG", -2: "IPC_ERR_INVERTED", -3: "IPC_ERR_I
           -4: "IPC_ERR_NEWTON_MAXIT", -5: "IPC_ERR_PCG", -6: "IPC_ERR_LS_STALL", -7: "IPC_ERR_NAN",
           -8: "IPC_ERR_BVH_OVERFLOW", -9: "IPC_ERR_CUDA", -10: "IPC_ERR_CAPACITY"}
 PREC_FP64, PREC_MIXED = 0, 1
+BROAD_LBVH, BROAD_ALL_PAIRS = 0, 1
 
 
 class SceneDesc(C.Structure):
@@ -43,7 +44,7 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("mu", C.c_double),
                 ("eps_v", C.c_double), ("k_c", C.c_double), ("kappa_A", C.c_double), ("newton_tol", C.c_double),
                 ("pcg_rtol", C.c_double), ("s_ccd", C.c_double), ("max_newton", C.c_int), ("max_pcg", C.c_int),
-                ("precision", C.c_int), ("pair_capacity", C.c_int)]
+                ("precision", C.c_int), ("pair_capacity", C.c_int), ("broad_phase", C.c_int)]
 
 
 class StepStats(C.Structure):
@@ -73,7 +74,12 @@ SIGNATURES = {
     "sim_surface": ([vp, ip, ip, ip], C.c_int),
     "sim_eval_barrier": ([vp, vp, C.c_int, vp, C.c_int, vp, vp, vp], C.c_int),
     "sim_ccd_alpha": ([vp, vp, vp, dp, ip], C.c_int),
+    "sim_kernel_launches": ([], C.c_ulonglong),
+    "sim_profile": ([vp, C.c_int], C.c_int),
+    "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
 }
+
+PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "unused"]
 
 
 def load():
@@ -89,6 +95,11 @@ def load():
             f.restype = res
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the CUDA library so far in this process."""
+    return int(load().sim_kernel_launches())
 
 
 class IpcError(RuntimeError):
@@ -116,7 +127,8 @@ def make_params(p: dict, precision=PREC_FP64) -> Params:
     return Params(dt=p["dt"], dhat=p["dhat"], kappa=p.get("kappa", 0.0), mu=p["mu"], eps_v=p["eps_v"],
                   k_c=p.get("k_c", 0.0), kappa_A=p.get("kappa_A", 1e8), newton_tol=p["newton_tol"],
                   pcg_rtol=p.get("pcg_rtol", 1e-4), s_ccd=p.get("s_ccd", 0.1), max_newton=int(p.get("max_newton", 100)),
-                  max_pcg=int(p.get("max_pcg", 0)), precision=int(precision), pair_capacity=int(p.get("pair_capacity", 0)))
+                  max_pcg=int(p.get("max_pcg", 0)), precision=int(precision), pair_capacity=int(p.get("pair_capacity", 0)),
+                  broad_phase=int(p.get("broad_phase", BROAD_LBVH)))
 
 
 class Simulator:
@@ -237,6 +249,18 @@ class Simulator:
         arrs = [None if a is None else _f64(a) for a in (x, v, q, qd)]
         ptrs = [None if a is None else a.ctypes.data_as(vp) for a in arrs]
         self._check(load().sim_set_state(self.h, *ptrs, 0))
+
+    def profile(self, enable=True):
+        self._check(load().sim_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        ms = (C.c_double * 8)()
+        n = (C.c_longlong * 8)()
+        w = (C.c_longlong * 4)()
+        self._check(load().sim_profile_read(self.h, ms, n, w))
+        stages = {PROFILE_STAGES[k]: dict(ms=ms[k], n=n[k]) for k in range(8)}
+        work = dict(pcg_iters=w[0], pcg_pair_iters=w[1], pcg_fric_iters=w[2], bsr_blocks=w[3])
+        return stages, work
 
     # ---- stage entry points (device tensors) ---------------------------------
     def surface(self):

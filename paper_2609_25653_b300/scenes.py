@@ -323,3 +323,250 @@ def block_on_plane(n_steps: int = 10, tilt: float = 0.0, mu: float = 0.5, **para
         gravity=np.array([0.0, 0.0, -9.81]),
         params=params,
     )
+
+
+# ----------------------------------------------------------------------------
+# workload 2: arm-gripper grasp of a rigid ellipsoid (FP64)
+# ----------------------------------------------------------------------------
+
+def subdivided_box(lo, hi, n):
+    """Closed box surface with every face cut into n x n quads (2 n^2 triangles per face), outward."""
+    lo = np.asarray(lo, float)
+    hi = np.asarray(hi, float)
+    verts = {}
+    vlist = []
+
+    def vid(p):
+        key = tuple(np.round(p, 12))
+        if key not in verts:
+            verts[key] = len(vlist)
+            vlist.append(p)
+        return verts[key]
+
+    tris = []
+    for axis in range(3):
+        for side in (0, 1):
+            a1, a2 = [a for a in range(3) if a != axis]
+            for i in range(n):
+                for j in range(n):
+                    def P(ii, jj):
+                        p = np.zeros(3)
+                        p[axis] = hi[axis] if side else lo[axis]
+                        p[a1] = lo[a1] + (hi[a1] - lo[a1]) * ii / n
+                        p[a2] = lo[a2] + (hi[a2] - lo[a2]) * jj / n
+                        return vid(p)
+                    q = [P(i, j), P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)]
+                    # outward: (a1 x a2) points along +axis for cyclic (axis, a1, a2)
+                    cyclic = (a1 - axis) % 3 == 1
+                    flip = (side == 0) == cyclic
+                    if flip:
+                        tris.append([q[0], q[2], q[1]]); tris.append([q[0], q[3], q[2]])
+                    else:
+                        tris.append([q[0], q[1], q[2]]); tris.append([q[0], q[2], q[3]])
+    return np.asarray(vlist, dtype=np.float64), np.asarray(tris, dtype=np.int32)
+
+
+def finray_tip(h=1.25e-3, width=20e-3, height=40e-3, depth=20e-3):
+    """Voxelised fin-ray fingertip in its local frame (u, v, w).
+
+    Profile: the right triangle u in [0, width], w in [0, height],
+    u / width + w / height <= 1 (contact face u = 0, mounting face w = 0, back
+    face the hypotenuse), extruded over v in [0, depth].  Three slanted rib
+    voids (one cell thick) run between the contact face and the back face.
+    Cells are cut into 6 tets each."""
+    nu, nw, nv = int(round(width / h)), int(round(height / h)), int(round(depth / h))
+    keep = np.zeros((nu, nv, nw), bool)
+    for i in range(nu):
+        for k in range(nw):
+            uc, wc = (i + 0.5) * h, (k + 0.5) * h
+            if uc / width + wc / height > 1.0:
+                continue
+            keep[i, :, k] = True
+            # rib voids: bands along w = w0 + 0.6 u, away from the outer walls
+            umax = width * (1.0 - wc / height)
+            for w0 in (0.25 * height, 0.45 * height, 0.65 * height):
+                if abs(wc - (w0 + 0.6 * uc)) < 0.5 * h and 2 * h < uc < umax - 2 * h:
+                    keep[i, 1:nv - 1, k] = False
+    X, T = grid_tets((0.0, 0.0, 0.0), h, nu, nv, nw)
+    cell_of_tet = np.repeat(np.arange(nu * nv * nw), 6)
+    # grid_tets enumerates cells k-major, then j, then i
+    ci = np.arange(nu * nv * nw)
+    ii = ci % nu
+    jj = (ci // nu) % nv
+    kk = ci // (nu * nv)
+    cell_keep = keep[ii, jj, kk]
+    T = T[cell_keep[cell_of_tet]]
+    used = np.unique(T)
+    remap = -np.ones(len(X), np.int64)
+    remap[used] = np.arange(len(used))
+    return X[used], remap[T].astype(np.int32)
+
+
+def _frame(R, t):
+    T = np.zeros((3, 4))
+    T[:, :3] = R
+    T[:, 3] = t
+    return T
+
+
+def arm_gripper_grasp(seed: int = 0, n_steps: int = 400, tip_cell=1.25e-3, link_tris=2000, obj_tris=5000,
+                      **param_overrides) -> dict:
+    """Two fin-ray fingertips (E = 2e5 Pa, nu = 0.45, rho = 1100) stitched to
+    two kinematic finger bases grasp and lift a rigid ABD ellipsoid (semi-axes
+    30/25/20 mm, 0.1 kg) resting on a kinematic ground quad; seven kinematic
+    arm links (~2k triangles each) follow the gripper with seeded smooth
+    joint wobble.  dt = 5 ms, dhat = 0.5 mm, mu = 0.6.
+
+    Trajectory: the fingertips start in the pre-grasp pose 0.8 mm from the
+    object, close 0.05 mm per step for 100 steps (5 mm), hold 20 steps, then
+    the gripper and arm lift at 50 mm/s."""
+    mm = 1e-3
+    rng = SplitMix64(seed)
+    a, b, c = 30 * mm, 25 * mm, 20 * mm
+    # object
+    n_lon = max(8, int(round(math.sqrt(obj_tris * 1.6 / 2))))
+    n_lat = max(4, int(round(obj_tris / (2 * n_lon))) + 1)
+    oX, oT = uv_ellipsoid(a, b, c, n_lat, n_lon)
+    vol = 4.0 / 3.0 * math.pi * a * b * c
+    rho_obj = 0.1 / vol
+    q0 = np.concatenate([[0.0, 0.0, c + 0.3 * mm], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    # fingertips (local u: away from the object, v: along x, w: down)
+    tX, tT = finray_tip(h=tip_cell)
+    height = 40 * mm
+    z_top = q0[2] + 22 * mm
+    gap = 0.8 * mm
+    Xs, Ts = [], []
+    fem_body = []
+    offs = 0
+    tips = []
+    for side in (+1, -1):
+        # world = (x: v - depth/2, y: side * (b + gap + u), z: z_top - w)
+        Xw = np.stack([tX[:, 1] - 10 * mm, side * (b + gap + tX[:, 0]), z_top - tX[:, 2]], axis=1)
+        T = tT.copy()
+        if side < 0:
+            T[:, [1, 2]] = T[:, [2, 1]]  # the mirror flips orientation
+        Xs.append(Xw)
+        Ts.append(T + offs)
+        fem_body.append(np.full(len(T), len(tips), np.int32))
+        tips.append((offs, len(Xw)))
+        offs += len(Xw)
+    X = np.concatenate(Xs)
+    tets = np.concatenate(Ts)
+    fem_body = np.concatenate(fem_body)
+    nt = len(tets)
+    # finger bases: kinematic boxes 0.6 mm above each tip's mounting face (~1k triangles)
+    base_n = max(2, int(round(math.sqrt(1000 / 12))))
+    kin = []
+    base_up, base_tris = subdivided_box((-12 * mm, -2 * mm, 0.6 * mm), (12 * mm, 22 * mm, 8.6 * mm), base_n)
+    base_dn = base_up * np.array([1.0, -1.0, 1.0])  # mirror image for the -y finger
+    # ground quad, diagonal well away from the object
+    g = 0.5
+    gX = np.array([[-g + 0.2, -g + 0.3, 0], [g + 0.2, -g + 0.3, 0], [g + 0.2, g + 0.3, 0], [-g + 0.2, g + 0.3, 0.0]])
+    gT = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    kin.append(dict(X=gX, tris=gT))                   # body 0: ground
+    kin.append(dict(X=base_up, tris=base_tris))                        # body 1: base of tip +y
+    kin.append(dict(X=base_dn, tris=base_tris[:, [0, 2, 1]].copy()))   # body 2: base of tip -y
+    # arm links: capsules above the gripper, ~link_tris triangles each
+    n_ring = max(8, int(round(math.sqrt(link_tris / 2))))
+    n_seg = max(2, int(round(link_tris / (2 * n_ring))) - n_ring // 2)
+    links = []
+    for k in range(7):
+        lX, lT = superellipsoid_capsule(28 * mm - 2 * mm * k, 24 * mm - 2 * mm * k, 60 * mm, n_ring, n_seg)
+        kin.append(dict(X=lX, tris=lT))
+        links.append(k)
+    # stitch springs: tip vertices on the mounting face (w <= 0.5 mm) to their base
+    sv, sb, sx = [], [], []
+    for ti, side in enumerate((+1, -1)):
+        o, n = tips[ti]
+        for v in range(o, o + n):
+            if z_top - X[v, 2] <= 0.5 * mm:
+                sv.append(v)
+                sb.append(1 + ti)
+                # anchor in the base frame (axis-aligned, origin (0, side (b + gap), z_top))
+                sx.append([X[v, 0], X[v, 1] - side * (b + gap), X[v, 2] - z_top])
+    # trajectory
+    phases = np.zeros(n_steps + 1)
+    lift = np.zeros(n_steps + 1)
+    for s in range(n_steps + 1):
+        phases[s] = min(s, 100) * 0.05 * mm
+        lift[s] = max(0, s - 120) * 0.25 * mm
+    wob_amp = 0.02 * rng.uniform(7)
+    wob_w = 2 * math.pi * (0.5 + rng.uniform(7))
+    wob_ph = 2 * math.pi * rng.uniform(7)
+    dt = 5e-3
+    kin_T = np.zeros((n_steps + 1, len(kin), 3, 4))
+    for s in range(n_steps + 1):
+        kin_T[s, 0] = _frame(np.eye(3), (0, 0, 0))
+        for ti, side in enumerate((+1, -1)):
+            y0 = side * (b + gap - phases[s])
+            kin_T[s, 1 + ti] = _frame(np.eye(3), (0.0, y0, z_top + lift[s]))
+        t = s * dt
+        for k in range(7):
+            ang = wob_amp[k] * math.sin(wob_w[k] * t + wob_ph[k])
+            R = rot_z(ang + 0.3 * k) @ rot_x(0.05 * k)
+            kin_T[s, 3 + k] = _frame(R, (0.0, 0.0, z_top + 40 * mm + 75 * mm * k + lift[s]))
+    params = default_params(dt=dt, dhat=0.5 * mm, mu=0.6, newton_tol=1e-6, n_steps=n_steps)
+    params.update(param_overrides)
+    return dict(
+        name=f"arm_gripper_grasp_{nt}tet",
+        fem_X=X, fem_tets=tets,
+        fem_logE=np.full(nt, math.log(2e5)), fem_nu=np.full(nt, 0.45), fem_rho=np.full(nt, 1100.0),
+        fem_body=fem_body,
+        kin=kin, kin_T=kin_T,
+        abd=[dict(X=oX, tris=oT, rho=rho_obj, q0=q0)],
+        stitch_v=np.asarray(sv, np.int32), stitch_b=np.asarray(sb, np.int32), stitch_X=np.asarray(sx, np.float64),
+        gravity=np.array([0.0, 0.0, -9.81]),
+        params=params,
+    )
+
+
+def abd_box_drop(n_steps: int = 6, mu: float = 0.3, **param_overrides) -> dict:
+    """A 20 mm rigid (ABD) box, slightly tilted, falling onto a fixed ground triangle, beside a
+    soft 2 x 2 x 2 mm block resting on the same ground (ABD-kinematic and FEM-kinematic contact)."""
+    mm = 1e-3
+    bX, bT = box_surface((-10 * mm, -10 * mm, -10 * mm), (10 * mm, 10 * mm, 10 * mm))
+    R = rot_x(0.03) @ rot_y(0.02)
+    q0 = np.concatenate([[0.0, 0.0, 10.9 * mm], R[:, 0], R[:, 1], R[:, 2]])
+    X, tets = grid_tets((15 * mm, -1 * mm, 0.25 * mm), 1 * mm, 2, 2, 2)
+    nt = len(tets)
+    gX = np.array([[-50 * mm, -50 * mm, 0.0], [250 * mm, -50 * mm, 0.0], [-50 * mm, 250 * mm, 0.0]])
+    kin_T = np.tile(translation((0, 0, 0)), (n_steps + 1, 1, 1, 1))
+    sv, sb, sx = _empty_stitch()
+    params = default_params(dt=1e-2, dhat=0.5 * mm, mu=mu, n_steps=n_steps)
+    params.update(param_overrides)
+    return dict(
+        name="abd_box_drop",
+        fem_X=X, fem_tets=tets,
+        fem_logE=np.full(nt, math.log(1e5)), fem_nu=np.full(nt, 0.4), fem_rho=np.full(nt, 1000.0),
+        fem_body=np.zeros(nt, np.int32),
+        kin=[dict(X=gX, tris=np.array([[0, 1, 2]], np.int32))], kin_T=kin_T,
+        abd=[dict(X=bX, tris=bT, rho=1000.0, q0=q0)],
+        stitch_v=sv, stitch_b=sb, stitch_X=sx,
+        gravity=np.array([0.0, 0.0, -9.81]),
+        params=params,
+    )
+
+
+def stitched_block(n_steps: int = 6, **param_overrides) -> dict:
+    """A 4 x 4 x 4 mm soft block (2 mm cells) whose top vertices are stitched
+    (Eq. 2) to a kinematic base that moves sideways and up; the block swings."""
+    mm = 1e-3
+    X, tets = grid_tets((-2 * mm, -2 * mm, 0.0), 2 * mm, 2, 2, 2)
+    nt = len(tets)
+    top = np.where(np.abs(X[:, 2] - 4 * mm) < 1e-9)[0].astype(np.int32)
+    bX, bT = box_surface((-3 * mm, -3 * mm, 4.6 * mm), (3 * mm, 3 * mm, 6 * mm))
+    kin_T = np.zeros((n_steps + 1, 1, 3, 4))
+    for s in range(n_steps + 1):
+        kin_T[s, 0] = translation((0.2 * mm * s, 0.0, 0.1 * mm * s))
+    params = default_params(dt=1e-2, dhat=0.3 * mm, mu=0.0, n_steps=n_steps)
+    params.update(param_overrides)
+    return dict(
+        name="stitched_block",
+        fem_X=X, fem_tets=tets,
+        fem_logE=np.full(nt, math.log(1e5)), fem_nu=np.full(nt, 0.45), fem_rho=np.full(nt, 1100.0),
+        fem_body=np.zeros(nt, np.int32),
+        kin=[dict(X=bX, tris=bT)], kin_T=kin_T, abd=[],
+        stitch_v=top, stitch_b=np.zeros(len(top), np.int32), stitch_X=X[top].copy(),
+        gravity=np.array([0.0, 0.0, -9.81]),
+        params=params,
+    )

@@ -220,3 +220,50 @@ def test_initial_intersection_rejected():
     with pytest.raises(ipcsim.IpcError) as e:
         _sim(sc)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("name", ["abd_box_drop", "stitched_block"])
+def test_abd_and_stitch_parity(name):
+    """Affine-body contact and stitch springs: teacher-forced steps agree with the oracle to 1e-8 L."""
+    sc = getattr(scenes, name)(n_steps=6, **PARITY)
+    o = orc.Oracle(sc)
+    sim = _sim(sc)
+    nfd, nab = o.S.n_fem_dof, o.S.nab
+    for k in range(6):
+        x0 = o.z[:nfd].reshape(-1, 3).copy()
+        v0 = o.zd[:nfd].reshape(-1, 3).copy()
+        q0 = o.z[nfd:nfd + 12 * nab].reshape(-1, 12).copy() if nab else None
+        qd0 = o.zd[nfd:nfd + 12 * nab].reshape(-1, 12).copy() if nab else None
+        sim.set_state(x0, v0, q0, qd0)
+        st = sim.step()
+        o.step()
+        xg, _, qg, _ = sim.get_state()
+        err = np.max(np.abs(xg - o.z[:nfd].reshape(-1, 3))) / o.S.L
+        assert err < 1e-8, (k, err)
+        if nab:
+            qo = o.z[nfd:nfd + 12 * nab].reshape(-1, 12)
+            assert np.max(np.abs(qg[:, :3] - qo[:, :3])) / o.S.L < 1e-8
+            assert np.max(np.abs(qg[:, 3:] - qo[:, 3:])) < 1e-8
+
+
+def test_lbvh_matches_all_pairs_on_grasp_scene():
+    """The LBVH broad phase returns exactly the all-pairs active set on the arm-gripper geometry."""
+    from paper_2609_25653_b300 import ipcsim
+    sc = scenes.arm_gripper_grasp(0, n_steps=4)
+    a = _sim(sc)
+    b = _sim(sc, broad_phase=ipcsim.BROAD_ALL_PAIRS)
+    S = orc.Scene(sc)
+    xv = S.positions(S.z0).copy()
+    # squeeze the fingertips onto the object so that many pairs are active
+    r = np.random.default_rng(0)
+    xv[:S.nf, 1] *= 0.985
+    xv[:S.nf] += 2e-5 * r.normal(size=(S.nf, 3))
+    ra, sa = a.active_pairs(_dev(xv))
+    rb, sb = b.active_pairs(_dev(xv))
+    A = canon(ra.cpu().numpy(), sa.cpu().numpy())
+    B = canon(rb.cpu().numpy(), sb.cpu().numpy())
+    assert len(B) > 50 and A == B
+    p = np.zeros_like(xv)
+    p[:S.nf, 1] = -1e-3 * np.sign(xv[:S.nf, 1])
+    p[:S.nf] += 1e-4 * r.normal(size=(S.nf, 3))
+    assert a.ccd_alpha(_dev(xv), _dev(p)) == b.ccd_alpha(_dev(xv), _dev(p))
