@@ -14,7 +14,7 @@ def declared_functions():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(sim_[A-Za-z0-9_]+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^\s*[A-Za-z_][A-Za-z0-9_ ]*?[\s\*]+(sim_[A-Za-z0-9_]+)\s*\(", src, re.M))
     return names
 
 
