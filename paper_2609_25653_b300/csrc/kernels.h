@@ -34,8 +34,19 @@ struct PcgArgs {
   double* partial;  // 3 * grid doubles
   double rtol;
   int max_iter;
-  int* out;         // [iterations, status]
+  int* out;         // [iterations, status, FP64 residual replacements]
   double* res;      // [relative residual]
+  // mixed precision: FP32 copies of the operator and preconditioner, FP32
+  // search direction and preconditioned residual; x, r, y and all dot
+  // products stay FP64, and the residual is replaced by b - A x with the FP64
+  // operator when the FP32 iteration has converged.
+  int fp32;
+  const float* val32;
+  const float* pairH32;
+  const float* f_Hu32;
+  const float* Dinv32;
+  float* z32;
+  float* p32;
 };
 
 // fem.cu
@@ -91,6 +102,8 @@ void launch_dinv(cudaStream_t, int n_nodes, const int* diag, const double* val, 
 void launch_rhs(cudaStream_t, int n, const double* g, const double* gdir, double* rhs);
 int pcg_max_blocks(int threads);
 cudaError_t launch_pcg(cudaStream_t, int grid, int threads, const PcgArgs& a);
+int pcg_max_blocks_fp32(int threads);
+void launch_to_float(cudaStream_t, size_t n, const double* src, float* dst, const int* n_dev = nullptr, int stride = 0);
 
 // conservative-advancement iterations per CCD candidate
 constexpr int ACCD_MAX_ITER = 10000;

@@ -8,6 +8,7 @@
 // reduced per block and summed in block order by every block, so all blocks
 // take identical control decisions.
 #include <cooperative_groups.h>
+#include <algorithm>
 #include "common.cuh"
 #include "kernels.h"
 
@@ -69,91 +70,128 @@ __device__ inline void node_scatter(const DevScene& S, double* y, int v, d3 w) {
   }
 }
 
-// y += A p for the whole operator; returns this thread's share of p^T A p.
-__device__ inline double apply_A(const PcgArgs& a, const double* p, double* y, int tid, int nthr) {
+// y += A p for the whole operator (matrix values of type M, vector p of type V,
+// products and row sums in M); returns this thread's share of p^T A p in FP64.
+template <typename M, typename V>
+__device__ inline double apply_A(const PcgArgs& a, const M* val, const M* pairH, const M* fHu, const V* p, double* y,
+                                 int tid, int nthr) {
   const DevScene& S = a.S;
   double acc = 0.0;
   for (int i = tid; i < a.n_nodes; i += nthr) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    M s0 = M(0), s1 = M(0), s2 = M(0);
     for (int k = a.row[i]; k < a.row[i + 1]; ++k) {
-      const double* A = a.val + 9 * (size_t)k;
+      const M* A = val + 9 * (size_t)k;
       int j = a.col[k];
-      double p0 = p[3 * j], p1 = p[3 * j + 1], p2 = p[3 * j + 2];
+      M p0 = (M)p[3 * j], p1 = (M)p[3 * j + 1], p2 = (M)p[3 * j + 2];
       s0 += A[0] * p0 + A[1] * p1 + A[2] * p2;
       s1 += A[3] * p0 + A[4] * p1 + A[5] * p2;
       s2 += A[6] * p0 + A[7] * p1 + A[8] * p2;
     }
-    atomicAdd(y + 3 * i, s0);
-    atomicAdd(y + 3 * i + 1, s1);
-    atomicAdd(y + 3 * i + 2, s2);
-    acc += p[3 * i] * s0 + p[3 * i + 1] * s1 + p[3 * i + 2] * s2;
+    atomicAdd(y + 3 * i, (double)s0);
+    atomicAdd(y + 3 * i + 1, (double)s1);
+    atomicAdd(y + 3 * i + 2, (double)s2);
+    acc += (double)p[3 * i] * (double)s0 + (double)p[3 * i + 1] * (double)s1 + (double)p[3 * i + 2] * (double)s2;
   }
   int np = min(*a.n_pairs, a.cap);
   for (int k = tid; k < np; k += nthr) {
     const int* r = a.rec + 8 * k;
-    const double* H = a.pairH + 144 * (size_t)k;
-    double u[12];
+    const M* H = pairH + 144 * (size_t)k;
+    M u[12];
     bool kin[4];
     for (int q = 0; q < 4; ++q) {
       int v = r[4 + q];
       kin[q] = S.vkind[v] == VK_KIN;
-      d3 uq = kin[q] ? mk(0, 0, 0) : node_gather(S, p, v);
-      u[3 * q] = uq.x; u[3 * q + 1] = uq.y; u[3 * q + 2] = uq.z;
+      NodeMap m = vertex_nodes(S, v);
+      M ux = M(0), uy = M(0), uz = M(0);
+      if (!kin[q])
+        for (int t = 0; t < m.n; ++t) {
+          M w = (M)m.w[t];
+          ux += w * (M)p[3 * m.node[t]];
+          uy += w * (M)p[3 * m.node[t] + 1];
+          uz += w * (M)p[3 * m.node[t] + 2];
+        }
+      u[3 * q] = ux; u[3 * q + 1] = uy; u[3 * q + 2] = uz;
     }
     for (int q = 0; q < 4; ++q) {
       if (kin[q]) continue;
-      double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-      const double* H0 = H + 12 * (3 * q);
+      M w0 = M(0), w1 = M(0), w2 = M(0);
+      const M* H0 = H + 12 * (3 * q);
       for (int j = 0; j < 12; ++j) {
         w0 += H0[j] * u[j];
         w1 += H0[12 + j] * u[j];
         w2 += H0[24 + j] * u[j];
       }
-      node_scatter(S, y, r[4 + q], mk(w0, w1, w2));
-      acc += u[3 * q] * w0 + u[3 * q + 1] * w1 + u[3 * q + 2] * w2;
+      node_scatter(S, y, r[4 + q], mk((double)w0, (double)w1, (double)w2));
+      acc += (double)u[3 * q] * (double)w0 + (double)u[3 * q + 1] * (double)w1 + (double)u[3 * q + 2] * (double)w2;
     }
   }
   for (int k = tid; k < a.n_fric; k += nthr) {
     const int* ids = a.f_ids + 4 * k;
     const double* w = a.f_w + 4 * k;
-    const double* Hu = a.f_Hu + 9 * k;
-    d3 U = mk(0, 0, 0);
+    const M* Hu = fHu + 9 * k;
+    M U0 = M(0), U1 = M(0), U2 = M(0);
     bool kin[4];
     for (int q = 0; q < 4; ++q) {
       kin[q] = S.vkind[ids[q]] == VK_KIN;
-      if (!kin[q] && w[q] != 0.0) U = U + w[q] * node_gather(S, p, ids[q]);
+      if (kin[q] || w[q] == 0.0) continue;
+      NodeMap m = vertex_nodes(S, ids[q]);
+      for (int t = 0; t < m.n; ++t) {
+        M ww = (M)(w[q] * m.w[t]);
+        U0 += ww * (M)p[3 * m.node[t]];
+        U1 += ww * (M)p[3 * m.node[t] + 1];
+        U2 += ww * (M)p[3 * m.node[t] + 2];
+      }
     }
-    d3 t = mk(Hu[0] * U.x + Hu[1] * U.y + Hu[2] * U.z, Hu[3] * U.x + Hu[4] * U.y + Hu[5] * U.z,
-              Hu[6] * U.x + Hu[7] * U.y + Hu[8] * U.z);
+    M t0 = Hu[0] * U0 + Hu[1] * U1 + Hu[2] * U2, t1 = Hu[3] * U0 + Hu[4] * U1 + Hu[5] * U2,
+      t2 = Hu[6] * U0 + Hu[7] * U1 + Hu[8] * U2;
+    d3 t = mk((double)t0, (double)t1, (double)t2);
     for (int q = 0; q < 4; ++q)
       if (!kin[q] && w[q] != 0.0) node_scatter(S, y, ids[q], w[q] * t);
-    acc += dot(U, t);
+    acc += (double)U0 * t.x + (double)U1 * t.y + (double)U2 * t.z;
   }
   return acc;
 }
 
+// z = Dinv r for node i (Dinv of type M, z stored as V); returns r.z and r.r shares
+template <typename M, typename V>
+__device__ inline void precond_node(const M* Dinv, const double* r, V* z, int i, double& rz, double& rr) {
+  const M* D = Dinv + 9 * i;
+  M r0 = (M)r[3 * i], r1 = (M)r[3 * i + 1], r2 = (M)r[3 * i + 2];
+  M z0 = D[0] * r0 + D[1] * r1 + D[2] * r2, z1 = D[3] * r0 + D[4] * r1 + D[5] * r2, z2 = D[6] * r0 + D[7] * r1 + D[8] * r2;
+  z[3 * i] = (V)z0; z[3 * i + 1] = (V)z1; z[3 * i + 2] = (V)z2;
+  rz += r[3 * i] * (double)z[3 * i] + r[3 * i + 1] * (double)z[3 * i + 1] + r[3 * i + 2] * (double)z[3 * i + 2];
+  rr += r[3 * i] * r[3 * i] + r[3 * i + 1] * r[3 * i + 1] + r[3 * i + 2] * r[3 * i + 2];
+}
+
+// One PCG solve.  T = double: all FP64.  T = float: FP32 operator, preconditioner,
+// search direction and preconditioned residual, FP64 x / r / y / dots, and
+// at FP32 convergence up to 3 replacements r <- b - A x with the FP64 operator.
+template <typename T>
 __global__ void k_pcg(PcgArgs a) {
   cg::grid_group grid = cg::this_grid();
   int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   int nblk = gridDim.x;
   int n3 = 3 * a.n_nodes;
+  constexpr bool F32 = sizeof(T) == 4;
+  const T* val = F32 ? (const T*)a.val32 : (const T*)a.val;
+  const T* pairH = F32 ? (const T*)a.pairH32 : (const T*)a.pairH;
+  const T* fHu = F32 ? (const T*)a.f_Hu32 : (const T*)a.f_Hu;
+  const T* Dinv = F32 ? (const T*)a.Dinv32 : (const T*)a.Dinv;
+  T* pv = F32 ? (T*)a.p32 : (T*)a.p;
+  T* zv = F32 ? (T*)a.z32 : (T*)a.z;
   double* partA = a.partial;
   double* partB = a.partial + nblk;
   double* partC = a.partial + 2 * nblk;
   // x = 0, r = b, z = Dinv r, p = z, y = 0
   double rz_l = 0.0, bb_l = 0.0;
   for (int i = tid; i < a.n_nodes; i += nthr) {
-    const double* D = a.Dinv + 9 * i;
-    double r0 = a.b[3 * i], r1 = a.b[3 * i + 1], r2 = a.b[3 * i + 2];
-    double z0 = D[0] * r0 + D[1] * r1 + D[2] * r2, z1 = D[3] * r0 + D[4] * r1 + D[5] * r2,
-           z2 = D[6] * r0 + D[7] * r1 + D[8] * r2;
-    a.x[3 * i] = 0.0; a.x[3 * i + 1] = 0.0; a.x[3 * i + 2] = 0.0;
-    a.r[3 * i] = r0; a.r[3 * i + 1] = r1; a.r[3 * i + 2] = r2;
-    a.z[3 * i] = z0; a.z[3 * i + 1] = z1; a.z[3 * i + 2] = z2;
-    a.p[3 * i] = z0; a.p[3 * i + 1] = z1; a.p[3 * i + 2] = z2;
-    a.y[3 * i] = 0.0; a.y[3 * i + 1] = 0.0; a.y[3 * i + 2] = 0.0;
-    rz_l += r0 * z0 + r1 * z1 + r2 * z2;
-    bb_l += r0 * r0 + r1 * r1 + r2 * r2;
+    for (int d = 0; d < 3; ++d) {
+      a.x[3 * i + d] = 0.0;
+      a.r[3 * i + d] = a.b[3 * i + d];
+      a.y[3 * i + d] = 0.0;
+    }
+    precond_node<T, T>(Dinv, a.r, zv, i, rz_l, bb_l);
+    for (int d = 0; d < 3; ++d) pv[3 * i + d] = zv[3 * i + d];
   }
   double v = block_sum(rz_l);
   if (threadIdx.x == 0) partB[blockIdx.x] = v;
@@ -163,12 +201,12 @@ __global__ void k_pcg(PcgArgs a) {
   double rz = grid_total(partB, nblk);
   double bb = grid_total(partC, nblk);
   double tol2 = a.rtol * a.rtol * bb;
-  int it = 0, status = 0;
+  int it = 0, status = 0, replaced = 0;
   double rr = bb;
   if (bb > 0.0) {
     for (it = 0; it < a.max_iter; ++it) {
       // A: y = A p, partial p^T A p
-      double pap_l = apply_A(a, a.p, a.y, tid, nthr);
+      double pap_l = apply_A<T, T>(a, val, pairH, fHu, pv, a.y, tid, nthr);
       v = block_sum(pap_l);
       if (threadIdx.x == 0) partA[blockIdx.x] = v;
       grid.sync();
@@ -178,20 +216,12 @@ __global__ void k_pcg(PcgArgs a) {
       // B: x += alpha p, r -= alpha y, z = Dinv r, y = 0
       double rz_n = 0.0, rr_n = 0.0;
       for (int i = tid; i < a.n_nodes; i += nthr) {
-        const double* D = a.Dinv + 9 * i;
-        double r0 = a.r[3 * i] - alpha * a.y[3 * i];
-        double r1 = a.r[3 * i + 1] - alpha * a.y[3 * i + 1];
-        double r2 = a.r[3 * i + 2] - alpha * a.y[3 * i + 2];
-        a.x[3 * i] += alpha * a.p[3 * i];
-        a.x[3 * i + 1] += alpha * a.p[3 * i + 1];
-        a.x[3 * i + 2] += alpha * a.p[3 * i + 2];
-        a.r[3 * i] = r0; a.r[3 * i + 1] = r1; a.r[3 * i + 2] = r2;
-        double z0 = D[0] * r0 + D[1] * r1 + D[2] * r2, z1 = D[3] * r0 + D[4] * r1 + D[5] * r2,
-               z2 = D[6] * r0 + D[7] * r1 + D[8] * r2;
-        a.z[3 * i] = z0; a.z[3 * i + 1] = z1; a.z[3 * i + 2] = z2;
-        a.y[3 * i] = 0.0; a.y[3 * i + 1] = 0.0; a.y[3 * i + 2] = 0.0;
-        rz_n += r0 * z0 + r1 * z1 + r2 * z2;
-        rr_n += r0 * r0 + r1 * r1 + r2 * r2;
+        for (int d = 0; d < 3; ++d) {
+          a.x[3 * i + d] += alpha * (double)pv[3 * i + d];
+          a.r[3 * i + d] -= alpha * a.y[3 * i + d];
+          a.y[3 * i + d] = 0.0;
+        }
+        precond_node<T, T>(Dinv, a.r, zv, i, rz_n, rr_n);
       }
       v = block_sum(rz_n);
       if (threadIdx.x == 0) partB[blockIdx.x] = v;
@@ -201,11 +231,35 @@ __global__ void k_pcg(PcgArgs a) {
       double rz_new = grid_total(partB, nblk);
       rr = grid_total(partC, nblk);
       if (!isfinite(rr)) { status = 2; ++it; break; }
-      if (rr <= tol2) { ++it; break; }
+      if (rr <= tol2) {
+        if (!F32 || replaced >= 3) { ++it; break; }
+        // FP64 residual replacement: r = b - A64 x (y is zero here)
+        ++replaced;
+        apply_A<double, double>(a, a.val, a.pairH, a.f_Hu, a.x, a.y, tid, nthr);
+        grid.sync();
+        double rz2 = 0.0, rr2 = 0.0;
+        for (int i = tid; i < a.n_nodes; i += nthr) {
+          for (int d = 0; d < 3; ++d) {
+            a.r[3 * i + d] = a.b[3 * i + d] - a.y[3 * i + d];
+            a.y[3 * i + d] = 0.0;
+          }
+          precond_node<T, T>(Dinv, a.r, zv, i, rz2, rr2);
+          for (int d = 0; d < 3; ++d) pv[3 * i + d] = zv[3 * i + d];
+        }
+        v = block_sum(rz2);
+        if (threadIdx.x == 0) partB[blockIdx.x] = v;
+        v = block_sum(rr2);
+        if (threadIdx.x == 0) partC[blockIdx.x] = v;
+        grid.sync();
+        rz = grid_total(partB, nblk);
+        rr = grid_total(partC, nblk);
+        if (rr <= tol2) { ++it; break; }
+        continue;
+      }
       double beta = rz_new / rz;
       rz = rz_new;
       // C: p = z + beta p
-      for (int i = tid; i < n3; i += nthr) a.p[i] = a.z[i] + beta * a.p[i];
+      for (int i = tid; i < n3; i += nthr) pv[i] = (T)((double)zv[i] + beta * (double)pv[i]);
       grid.sync();
     }
   } else {
@@ -214,8 +268,17 @@ __global__ void k_pcg(PcgArgs a) {
   if (tid == 0) {
     a.out[0] = it;
     a.out[1] = status;
+    a.out[2] = replaced;
     a.res[0] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
   }
+}
+
+__global__ void k_to_float(size_t n, const double* __restrict__ src, float* __restrict__ dst, const int* n_dev,
+                           int stride) {
+  size_t lim = n;
+  if (n_dev) lim = min(n, (size_t)(*n_dev) * (size_t)stride);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < lim; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
 }
 
 void launch_dinv(cudaStream_t st, int n_nodes, const int* diag, const double* val, const double* Dc, double* Dinv) {
@@ -229,14 +292,30 @@ int pcg_max_blocks(int threads) {
   int dev, sms, per_sm;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double>, threads, 0);
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+int pcg_max_blocks_fp32(int threads) {
+  int dev, sms, per_sm;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float>, threads, 0);
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_pcg(cudaStream_t st, int grid, int threads, const PcgArgs& a) {
   void* args[] = {(void*)&a};
   count_launch();
-  return cudaLaunchCooperativeKernel((void*)k_pcg, dim3(grid), dim3(threads), args, 0, st);
+  if (a.fp32) return cudaLaunchCooperativeKernel((void*)k_pcg<float>, dim3(grid), dim3(threads), args, 0, st);
+  return cudaLaunchCooperativeKernel((void*)k_pcg<double>, dim3(grid), dim3(threads), args, 0, st);
+}
+
+void launch_to_float(cudaStream_t st, size_t n, const double* src, float* dst, const int* n_dev, int stride) {
+  if (!n) return;
+  int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+  k_to_float<<<grid, 256, 0, st>>>(n, src, dst, n_dev, stride);
+  count_launch();
 }
 
 }  // namespace ipc

@@ -56,6 +56,8 @@ struct ipcsim {
   double *Hconst = nullptr, *Hval = nullptr, *Dc = nullptr, *Dinv = nullptr;
   double *r = nullptr, *zz = nullptr, *pp = nullptr, *y = nullptr, *partial = nullptr;
   double* T_dev = nullptr;
+  // mixed precision copies
+  float *val32 = nullptr, *pairH32 = nullptr, *fHu32 = nullptr, *Dinv32 = nullptr, *z32 = nullptr, *p32 = nullptr;
   // contact
   int cap = 0;
   int* rec = nullptr;
@@ -72,10 +74,9 @@ struct ipcsim {
     unsigned long long min_s;
     int n_pairs;
     int n_ccd;
-    int pcg_out[2];
-    double pcg_res;
+    int pcg_out[3];
     int flags;
-    int pad;
+    double pcg_res;
   };
   Scal* sc_dev = nullptr;
   Scal* sc_host = nullptr;
@@ -165,6 +166,11 @@ ipc_status grow_pairs(ipcsim* sim, int need) {
   if ((s = dalloc(sim, &sim->rec, (size_t)8 * ncap))) return s;
   if ((s = dalloc(sim, &sim->rec_s, (size_t)ncap))) return s;
   if ((s = dalloc(sim, &sim->pairH, (size_t)144 * ncap))) return s;
+  if (sim->P.precision == IPC_PREC_MIXED) {
+    dfree(sim, sim->pairH32);
+    sim->pairH32 = nullptr;
+    if ((s = dalloc(sim, &sim->pairH32, (size_t)144 * ncap))) return s;
+  }
   sim->cap = ncap;
   return IPC_OK;
 }
@@ -178,6 +184,11 @@ ipc_status grow_fric(ipcsim* sim, int need) {
   if ((s = dalloc(sim, &sim->f_n, (size_t)3 * ncap))) return s;
   if ((s = dalloc(sim, &sim->f_lam, (size_t)ncap))) return s;
   if ((s = dalloc(sim, &sim->f_Hu, (size_t)9 * ncap))) return s;
+  if (sim->P.precision == IPC_PREC_MIXED) {
+    dfree(sim, sim->fHu32);
+    sim->fHu32 = nullptr;
+    if ((s = dalloc(sim, &sim->fHu32, (size_t)9 * ncap))) return s;
+  }
   sim->fcap = ncap;
   return IPC_OK;
 }
@@ -664,7 +675,14 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
   if ((s = dalloc(sim, &sim->Dc, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->Dinv, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->T_dev, 12 * (size_t)std::max(nkb, 1)))) return fail(s, "");
-  sim->pcg_grid_max = pcg_max_blocks(PCG_THREADS);
+  if (P.precision != IPC_PREC_FP64 && P.precision != IPC_PREC_MIXED) return fail(IPC_ERR_ARG, "unknown precision");
+  sim->pcg_grid_max = std::min(pcg_max_blocks(PCG_THREADS), pcg_max_blocks_fp32(PCG_THREADS));
+  if (P.precision == IPC_PREC_MIXED) {
+    if ((s = dalloc(sim, &sim->val32, 9 * (size_t)nnzb))) return fail(s, "");
+    if ((s = dalloc(sim, &sim->Dinv32, 9 * (size_t)n_nodes))) return fail(s, "");
+    if ((s = dalloc(sim, &sim->z32, (size_t)ndof))) return fail(s, "");
+    if ((s = dalloc(sim, &sim->p32, (size_t)ndof))) return fail(s, "");
+  }
   if ((s = dalloc(sim, &sim->partial, 3 * (size_t)sim->pcg_grid_max))) return fail(s, "");
   if ((s = dalloc(sim, &sim->sc_dev, 1))) return fail(s, "");
   if (cudaMallocHost((void**)&sim->sc_host, sizeof(ipcsim::Scal)) != cudaSuccess) return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
@@ -819,6 +837,15 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     a.Dinv = sim->Dinv; a.b = sim->rhs; a.x = sim->p; a.r = sim->r; a.z = sim->zz; a.p = sim->pp; a.y = sim->y;
     a.partial = sim->partial; a.rtol = P.pcg_rtol; a.max_iter = max_pcg;
     a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
+    if (P.precision == IPC_PREC_MIXED) {
+      a.fp32 = 1;
+      a.val32 = sim->val32; a.pairH32 = sim->pairH32; a.f_Hu32 = sim->fHu32; a.Dinv32 = sim->Dinv32;
+      a.z32 = sim->z32; a.p32 = sim->p32;
+      launch_to_float(cs, 9 * (size_t)sim->nnzb, sim->Hval, sim->val32);
+      launch_to_float(cs, 144 * (size_t)sim->cap, sim->pairH, sim->pairH32, &sim->sc_dev->n_pairs, 144);
+      if (a.n_fric) launch_to_float(cs, 9 * (size_t)a.n_fric, sim->f_Hu, sim->fHu32);
+      launch_to_float(cs, 9 * (size_t)sim->n_nodes, sim->Dinv, sim->Dinv32);
+    }
     int work = std::max(sim->n_nodes, sim->cap / 4);
     int grid = std::max(1, std::min(sim->pcg_grid_max, (work + PCG_THREADS - 1) / PCG_THREADS));
     prof_begin(sim, PROF_PCG);

@@ -267,3 +267,22 @@ def test_lbvh_matches_all_pairs_on_grasp_scene():
     p[:S.nf, 1] = -1e-3 * np.sign(xv[:S.nf, 1])
     p[:S.nf] += 1e-4 * r.normal(size=(S.nf, 3))
     assert a.ccd_alpha(_dev(xv), _dev(p)) == b.ccd_alpha(_dev(xv), _dev(p))
+
+
+def test_mixed_precision_within_1e5():
+    """FP32 operator / FP64 residual path: positions within 1e-5 of the bbox diagonal of the FP64 path and the oracle."""
+    from paper_2609_25653_b300 import ipcsim
+    sc = scenes.fingertip_press(0, n_steps=8)
+    a = _sim(sc)
+    b = _sim(sc, precision=ipcsim.PREC_MIXED)
+    o = orc.Oracle(sc)
+    for k in range(8):
+        sa = a.step()
+        sb = b.step()
+        o.step()
+        xa = a.get_state()[0]
+        xb = b.get_state()[0]
+        L = o.S.L
+        assert np.max(np.abs(xa - xb)) / L < 1e-5
+        assert np.max(np.abs(xb - o.x()[:o.S.nf])) / L < 1e-5
+        assert sb["status"] == 0 and sb["min_dist"] > 0
