@@ -304,7 +304,9 @@ class Scene:
             raise ValueError("inverted or degenerate rest tetrahedron")
         self.vol = vol
         self.B = np.ascontiguousarray(np.linalg.inv(Dm).reshape(-1, 9))
-        self.mu, self.lam = snh_params(np.exp(_f64(sc["fem_logE"])), _f64(sc["fem_nu"]))
+        self.nu = _f64(sc["fem_nu"])
+        self.logE = _f64(sc["fem_logE"]).copy()
+        self.mu, self.lam = snh_params(np.exp(self.logE), self.nu)
         rho = _f64(sc["fem_rho"])
         self.mass_v = np.zeros(self.nf)
         np.add.at(self.mass_v, T.reshape(-1), np.repeat(rho * vol / 4.0, 4))
@@ -694,14 +696,24 @@ class Oracle:
             if dirichlet_done:
                 # backtracking on the incremental potential; tolerance covers rounding of E
                 n_half = 0
+                stationary = False
                 while True:
                     E_new = S.energy(z + alpha * p, ctx)
                     if E_new <= E + 1e-13 * abs(E):
                         break
                     alpha *= 0.5
                     n_half += 1
+                    if alpha * pnorm <= S.tol * S.dt * S.L:
+                        # no decrease resolvable above rounding within the tolerance: stationary
+                        stationary = True
+                        break
                     if n_half > 40:
                         raise StepError("line search stalled")
+                if stationary:
+                    converged = True
+                    rec["stationary"] = True
+                    it_stats.append(rec)
+                    break
                 rec["E_new"] = E_new
             z = z + alpha * p
             if alpha == 1.0:
@@ -718,3 +730,75 @@ class Oracle:
         self.step_index = t1
         self.stats.append(it_stats)
         return it_stats
+
+
+# ----------------------------------------------------------------------------
+# implicit adjoint of one step (dense)
+# ----------------------------------------------------------------------------
+
+def set_material(o: "Oracle", logE=None, mu=None):
+    """Per-tet log Young's modulus and the friction coefficient used by later steps."""
+    S = o.S
+    if logE is not None:
+        S.logE = _f64(logE).copy()
+        S.mu, S.lam = snh_params(np.exp(S.logE), S.nu)
+    if mu is not None:
+        S.mu_f = float(mu)
+
+
+def step_context(S, z_t, zd_t, step_next):
+    x_t = S.positions(z_t)
+    return dict(z_tilde=z_t + S.dt * zd_t + S.dt * S.dt * S.grav_acc, x_t=x_t,
+                lag=S.friction_lag(x_t.reshape(-1)) if S.mu_f > 0 else [], stitch_hat=S.stitch_targets(step_next))
+
+
+def adjoint_step(o: "Oracle", z_t, zd_t, z_next, step_next, gz_next, gzd_next):
+    """Backward of one step by the implicit function theorem.
+
+    At the converged z* the free-DOF gradient g(z*; z_t, zd_t, theta) vanishes,
+    so with H = dg/dz (the unprojected Hessian, dense here) and
+    a = dL/dz* + dL/dzd* / dt (zd* = (z* - z_t) / dt):
+        H lam = a,  dL/dtheta = -lam^T dg/dtheta,
+        dL/dz_t = M lam - dL/dzd* / dt + dt^2 H_fric lam,   dL/dzd_t = dt M lam.
+    theta = per-tet log E: dg/dlogE_e = dt^2 (gradient of V_e Psi_e), since
+    Psi is linear in (mu, lam) and both scale with E; dg/dmu = dt^2 grad D / mu.
+    The friction lag (lambda_k, n_k, w_k computed at x_t) is held fixed: its
+    dependence on x_t is not differentiated (exact when mu = 0).
+    Returns (dL/dz_t, dL/dzd_t, dL/dlogE, dL/dmu) on the free DOFs."""
+    S = o.S
+    dt = S.dt
+    F = slice(0, S.n_free)
+    ctx = step_context(S, z_t, zd_t, step_next)
+    _, _, H, _ = S.evaluate(z_next, ctx, project=False)
+    HFF = H.tocsr()[F, F].toarray()
+    a = (gz_next + gzd_next / dt)[F]
+    lam = np.linalg.solve(HFF, a)
+    lam_full = np.zeros(S.ndof)
+    lam_full[F] = lam
+    # theta = log E per tet
+    x = S.positions(z_next).reshape(-1)
+    dlogE = np.zeros(len(S.tets))
+    lv = (S.Jmap @ lam_full).reshape(-1, 3)
+    for e in range(len(S.tets)):
+        ids = S.tets[e]
+        _, ge, _ = tet(x.reshape(-1, 3)[ids], S.B[e], S.vol[e], S.mu[e], S.lam[e])
+        dlogE[e] = -dt * dt * float(ge @ lv[ids].reshape(-1))
+    # friction coefficient and the direct x_t dependence of the friction term
+    dmu = 0.0
+    fr_rows, fr_cols, fr_vals = [], [], []
+    xt = ctx["x_t"]
+    for ids, w, nvec, lamk in ctx["lag"]:
+        Ek, gk, Hk = friction(w, nvec, lamk, S.mu_f, S.eps, x.reshape(-1, 3)[ids], xt[ids])
+        dmu += -dt * dt * float(gk @ lv[ids].reshape(-1)) / S.mu_f
+        dofs = (3 * ids[:, None] + np.arange(3)).reshape(-1)
+        fr_rows.append(np.repeat(dofs, 12)); fr_cols.append(np.tile(dofs, 12)); fr_vals.append(Hk.reshape(-1))
+    gz_t = S.M @ lam_full - gzd_next / dt
+    if fr_vals:
+        import scipy.sparse as sp
+        Hf = sp.csr_matrix((np.concatenate(fr_vals), (np.concatenate(fr_rows), np.concatenate(fr_cols))),
+                           shape=(3 * S.nv, 3 * S.nv))
+        gz_t = gz_t + dt * dt * (S.Jmap.T @ (Hf @ (S.Jmap @ lam_full)))
+    gzd_t = dt * (S.M @ lam_full)
+    gz_t[S.n_free:] = 0.0
+    gzd_t[S.n_free:] = 0.0
+    return gz_t, gzd_t, dlogE, dmu

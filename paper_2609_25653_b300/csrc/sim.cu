@@ -892,14 +892,19 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     double E_new = 0;
     if (dirichlet_done) {
       int halv = 0;
+      bool stationary = false;
       for (;;) {
         launch_trial(cs, ndof, nk3, sim->z, sim->p, alpha, sim->z_trial, sim->xk, sim->pD, sim->xk_hat, sim->xk_trial);
         if ((s = energy_at(sim, sim->z_trial, sim->xk_trial, sim->xv_trial, &E_new, nullptr))) return s;
         if (E_new <= E + 1e-13 * std::fabs(E)) break;
         alpha *= 0.5;
-        if (++halv > 40) return finish(IPC_ERR_LS_STALL, "line search stalled");
+        ++halv;
+        // no decrease resolvable above rounding within the tolerance: the iterate is stationary
+        if (alpha * pn <= tol_abs) { stationary = true; break; }
+        if (halv > 40) return finish(IPC_ERR_LS_STALL, "line search stalled");
       }
       st.ls_halvings += halv;
+      if (stationary) { converged = true; break; }
     } else {
       launch_trial(cs, ndof, nk3, sim->z, sim->p, alpha, sim->z_trial, sim->xk, sim->pD, sim->xk_hat, sim->xk_trial);
     }
