@@ -159,6 +159,35 @@ ipc_status sim_sizes(const ipcsim* sim, int* out9);
 /* Derived scalars fixed at create: [kappa, k_c, L_bbox, dhat]. */
 ipc_status sim_scalars(const ipcsim* sim, double* out4);
 
+/* Place the kinematic bodies at the given transforms (host, (n_kin, 12)),
+ * e.g. to restart a trajectory from an earlier step together with
+ * sim_set_state. */
+ipc_status sim_set_kinematic(ipcsim* sim, const double* kin_T_host);
+
+/* Material and friction parameters for the following steps (the parameters
+ * the adjoint differentiates): per-tet ln Young's modulus (n_tets host
+ * doubles, or NULL to keep) and the friction coefficient (mu < 0 keeps it).
+ * The barrier stiffness and stitch stiffness fixed at create do not change. */
+ipc_status sim_set_params(ipcsim* sim, const double* logE_host, double mu);
+
+/* Implicit adjoint of one step (implicit function theorem).  Given the
+ * state at t (z_t_dev, zd_t_dev: DOF vectors (n_nodes, 3), FEM vertices then
+ * ABD pseudo-nodes), the converged state z_next_dev of the step t -> t+1, the
+ * kinematic transforms at t and t+1 (host, (n_kin, 12)) and the loss
+ * gradients gz_next_dev, gzd_next_dev w.r.t. z_{t+1} and zd_{t+1} = (z_{t+1} - z_t)/dt:
+ * recomputes the unprojected Hessian H at z_next, solves H lam = gz + gzd/dt
+ * by FP64 PCG (relative residual 1e-12; IPC_ERR_PCG if H is not positive
+ * definite there) and writes gz_t_dev = dL/dz_t and gzd_t_dev = dL/dzd_t
+ * (overwritten), adds dL/dlogE into glogE_dev (n_tets, may be NULL) and
+ * dL/dmu into *gmu_host (may be NULL).  The friction lag (normal forces,
+ * normals and closest points at x_t) is held fixed: its own dependence on
+ * x_t is not differentiated (exact when mu = 0).  Uses the simulator's work
+ * buffers; the simulator's state is not changed. */
+ipc_status sim_adjoint(ipcsim* sim, const double* z_t_dev, const double* zd_t_dev, const double* z_next_dev,
+                       const double* kin_T_t_host, const double* kin_T_next_host, const double* gz_next_dev,
+                       const double* gzd_next_dev, double* gz_t_dev, double* gzd_t_dev, double* glogE_dev,
+                       double* gmu_host);
+
 /* Per-stage timing with CUDA events recorded on the simulator's stream
  * around each stage of sim_step (cheap; intervals are read at the
  * synchronisation points sim_step already has).  enable != 0 starts (and

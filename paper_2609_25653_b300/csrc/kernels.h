@@ -97,6 +97,14 @@ void launch_ccd_bvh(cudaStream_t, const DevScene&, const double* xv, const doubl
                     Bvh& tri, Bvh& edge, unsigned long long* alpha_bits, int* n_cand, int* err);
 void bvh_rebuild(cudaStream_t, const DevScene&, const double* xv, double pad, Bvh& tri, Bvh& edge);
 
+// adjoint.cu
+void launch_theta_grad(cudaStream_t, const DevScene&, const double* xv, const double* lam, double scale, double* out);
+void launch_mass_apply(cudaStream_t, const DevScene&, const double* lam, double dt, double* y, double* yd);
+void launch_friction_apply(cudaStream_t, const DevScene&, int n, const int* f_ids, const double* f_w, const double* f_Hu,
+                           const double* lam, double* y);
+void launch_dot(cudaStream_t, int n, const double* a, const double* b, double* out);
+void launch_axpy(cudaStream_t, int n, const double* x, double alpha, const double* y, double* out);
+
 // pcg.cu
 void launch_dinv(cudaStream_t, int n_nodes, const int* diag, const double* val, const double* Dc, double* Dinv);
 void launch_rhs(cudaStream_t, int n, const double* g, const double* gdir, double* rhs);

@@ -45,6 +45,9 @@ struct ipcsim {
   double grav[3] = {0, 0, 0};
   int nnzb = 0;
   std::vector<double> h_Tcur;  // (nkb, 12) current kinematic transforms
+  std::vector<double> h_nu, h_logE;  // per-tet material
+  double* d_mu = nullptr;
+  double* d_lam = nullptr;
 
   DevScene S{};
   // state
@@ -612,8 +615,10 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
     double* dp; int* ip;
     if ((s = upload(sim, &dp, B))) return fail(s, ""); S.B = dp;
     if ((s = upload(sim, &dp, vol))) return fail(s, ""); S.vol = dp;
-    if ((s = upload(sim, &dp, mu))) return fail(s, ""); S.mu = dp;
-    if ((s = upload(sim, &dp, lam))) return fail(s, ""); S.lam = dp;
+    if ((s = upload(sim, &dp, mu))) return fail(s, ""); S.mu = dp; sim->d_mu = dp;
+    if ((s = upload(sim, &dp, lam))) return fail(s, ""); S.lam = dp; sim->d_lam = dp;
+    sim->h_nu.assign(D->nu_host, D->nu_host + nt);
+    sim->h_logE.assign(D->logE_host, D->logE_host + nt);
     if ((s = upload(sim, &ip, tet_blk))) return fail(s, ""); S.tet_blk = ip;
     if ((s = upload(sim, &ip, vkind))) return fail(s, ""); S.vkind = ip;
     if ((s = upload(sim, &ip, vbody))) return fail(s, ""); S.vbody = ip;
@@ -918,6 +923,136 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   CUDA_TRY(cudaStreamSynchronize(cs));
   CUDA_TRY(cudaGetLastError());
   return finish(IPC_OK, "");
+}
+
+ipc_status sim_set_kinematic(ipcsim* sim, const double* kin_T_host) {
+  if (!sim || (sim->nkb && !kin_T_host)) return IPC_ERR_ARG;
+  if (!sim->nkb) return IPC_OK;
+  CUDA_TRY(cudaMemcpyAsync(sim->T_dev, kin_T_host, sizeof(double) * 12 * sim->nkb, cudaMemcpyHostToDevice, sim->st));
+  launch_kin_targets(sim->st, sim->S, sim->T_dev, sim->xk, sim->stitch_hat);
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  std::memcpy(sim->h_Tcur.data(), kin_T_host, sizeof(double) * 12 * sim->nkb);
+  return IPC_OK;
+}
+
+ipc_status sim_set_params(ipcsim* sim, const double* logE_host, double mu) {
+  if (!sim) return IPC_ERR_ARG;
+  if (logE_host) {
+    int nt = sim->nt;
+    std::vector<double> m(nt), l(nt);
+    for (int e = 0; e < nt; ++e) {
+      double E = std::exp(logE_host[e]), nu = sim->h_nu[e];
+      if (!std::isfinite(E)) { sim->err = "non-finite Young's modulus"; return IPC_ERR_ARG; }
+      m[e] = E / (2 * (1 + nu));
+      l[e] = E * nu / ((1 + nu) * (1 - 2 * nu)) + m[e];
+    }
+    sim->h_logE.assign(logE_host, logE_host + nt);
+    if (nt) {
+      CUDA_TRY(cudaMemcpyAsync(sim->d_mu, m.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, sim->st));
+      CUDA_TRY(cudaMemcpyAsync(sim->d_lam, l.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, sim->st));
+      CUDA_TRY(cudaStreamSynchronize(sim->st));
+    }
+  }
+  if (mu >= 0) {
+    if (mu > 0 && sim->fcap == 0) {
+      ipc_status s = grow_fric(sim, 1024);
+      if (s) return s;
+    }
+    sim->P.mu = mu;
+  }
+  return IPC_OK;
+}
+
+ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const double* z_next,
+                       const double* kin_T_t_host, const double* kin_T_next_host, const double* gz_next,
+                       const double* gzd_next, double* gz_t, double* gzd_t, double* glogE, double* gmu_host) {
+  if (!sim || !z_t || !zd_t || !z_next || !gz_next || !gzd_next || !gz_t || !gzd_t) return IPC_ERR_ARG;
+  if (sim->nkb && (!kin_T_t_host || !kin_T_next_host)) { sim->err = "kinematic transforms required"; return IPC_ERR_ARG; }
+  const DevScene& S = sim->S;
+  const ipc_params& P = sim->P;
+  cudaStream_t cs = sim->st;
+  const int ndof = 3 * sim->n_nodes, nk3 = 3 * sim->nk;
+  const double dt = P.dt, dt2 = dt * dt;
+  ipc_status s;
+  // kinematic positions at t and t+1
+  if (sim->nkb) {
+    CUDA_TRY(cudaMemcpyAsync(sim->T_dev, kin_T_t_host, sizeof(double) * 12 * sim->nkb, cudaMemcpyHostToDevice, cs));
+    launch_kin_targets(cs, S, sim->T_dev, sim->xk_t, sim->stitch_hat);
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->T_dev, kin_T_next_host, sizeof(double) * 12 * sim->nkb, cudaMemcpyHostToDevice, cs));
+  }
+  launch_kin_targets(cs, S, sim->T_dev, sim->xk_hat, sim->stitch_hat);
+  launch_predict(cs, S, z_t, zd_t, dt, sim->grav, sim->z_t, sim->z_tilde);
+  launch_vertex_positions(cs, S, z_t, sim->xk_t, sim->xv_t);
+  rebuild_trees(sim, sim->xv_t);
+  // friction lag at x_t
+  sim->n_fric = 0;
+  if (P.mu > 0) {
+    for (;;) {
+      CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
+      cull(sim, sim->xv_t);
+      if ((s = sync_scalars(sim))) return s;
+      if (sim->sc_host->n_pairs > sim->cap) { if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s; continue; }
+      break;
+    }
+    int n = sim->sc_host->n_pairs;
+    if (n > sim->fcap && (s = grow_fric(sim, n))) return s;
+    launch_friction_lag(cs, pair_grid(sim->cap), S, sim->xv_t, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
+                        sim->kappa, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam);
+    sim->n_fric = n;
+  }
+  // unprojected Hessian at z*
+  launch_vertex_positions(cs, S, z_next, sim->xk_hat, sim->xv);
+  for (;;) {
+    CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
+    CUDA_TRY(cudaMemsetAsync(sim->g, 0, sizeof(double) * ndof, cs));
+    CUDA_TRY(cudaMemsetAsync(sim->gdir, 0, sizeof(double) * ndof, cs));
+    CUDA_TRY(cudaMemsetAsync(sim->Dc, 0, sizeof(double) * 9 * sim->n_nodes, cs));
+    if (nk3) CUDA_TRY(cudaMemsetAsync(sim->pD, 0, sizeof(double) * nk3, cs));
+    cull(sim, sim->xv);
+    launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
+    launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g, sim->Hval, &sim->sc_dev->E[5]);
+    launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
+                   sim->kappa, dt2, 2, 0, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2],
+                   nullptr);
+    if (P.mu > 0)
+      launch_friction(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, P.mu,
+                      P.eps_v * dt, dt2, 2, sim->g, sim->f_Hu, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[3]);
+    if ((s = sync_scalars(sim))) return s;
+    if (sim->sc_host->flags & ERRF_BVH) { sim->err = "BVH traversal stack overflow"; return IPC_ERR_BVH_OVERFLOW; }
+    if (sim->sc_host->n_pairs > sim->cap) { if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s; continue; }
+    break;
+  }
+  launch_dinv(cs, sim->n_nodes, S.bsr_diag, sim->Hval, sim->Dc, sim->Dinv);
+  launch_axpy(cs, ndof, gz_next, 1.0 / dt, gzd_next, sim->rhs);
+  PcgArgs a{};
+  a.S = S; a.n_nodes = sim->n_nodes; a.row = S.bsr_row; a.col = S.bsr_col; a.val = sim->Hval;
+  a.rec = sim->rec; a.n_pairs = &sim->sc_dev->n_pairs; a.cap = sim->cap; a.pairH = sim->pairH;
+  a.n_fric = P.mu > 0 ? sim->n_fric : 0; a.f_ids = sim->f_ids; a.f_w = sim->f_w; a.f_Hu = sim->f_Hu;
+  a.Dinv = sim->Dinv; a.b = sim->rhs; a.x = sim->p; a.r = sim->r; a.z = sim->zz; a.p = sim->pp; a.y = sim->y;
+  a.partial = sim->partial; a.rtol = 1e-12; a.max_iter = 10 * ndof + 1000;
+  a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
+  int grid = std::max(1, std::min(sim->pcg_grid_max, (std::max(sim->n_nodes, sim->cap / 4) + PCG_THREADS - 1) / PCG_THREADS));
+  CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a));
+  // contractions with lam (= sim->p)
+  if (glogE) launch_theta_grad(cs, S, sim->xv, sim->p, dt2, glogE);
+  double* tmp = sim->y;  // scratch: friction gradient, then M lam
+  CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->E[6], 0, sizeof(double), cs));
+  if (P.mu > 0 && sim->n_fric) {
+    CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(double) * ndof, cs));
+    launch_friction(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, P.mu,
+                    P.eps_v * dt, dt2, 1, tmp, nullptr, nullptr, nullptr, nullptr, &sim->sc_dev->E[7]);
+    launch_dot(cs, ndof, tmp, sim->p, &sim->sc_dev->E[6]);
+  }
+  launch_mass_apply(cs, S, sim->p, dt, tmp, gzd_t);
+  launch_axpy(cs, ndof, tmp, -1.0 / dt, gzd_next, gz_t);
+  if (P.mu > 0) launch_friction_apply(cs, S, sim->n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->p, gz_t);
+  if ((s = sync_scalars(sim))) return s;
+  CUDA_TRY(cudaGetLastError());
+  if (sim->sc_host->pcg_out[1]) { sim->err = "adjoint PCG breakdown (Hessian not positive definite)"; return IPC_ERR_PCG; }
+  if (gmu_host && P.mu > 0) *gmu_host += -sim->sc_host->E[6] / P.mu;
+  return IPC_OK;
 }
 
 ipc_status sim_profile(ipcsim* sim, int enable) {

@@ -76,6 +76,9 @@ SIGNATURES = {
     "sim_ccd_alpha": ([vp, vp, vp, dp, ip], C.c_int),
     "sim_kernel_launches": ([], C.c_ulonglong),
     "sim_profile": ([vp, C.c_int], C.c_int),
+    "sim_set_params": ([vp, dp, C.c_double], C.c_int),
+    "sim_set_kinematic": ([vp, dp], C.c_int),
+    "sim_adjoint": ([vp, vp, vp, vp, dp, dp, vp, vp, vp, vp, vp, dp], C.c_int),
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
 }
 
@@ -249,6 +252,61 @@ class Simulator:
         arrs = [None if a is None else _f64(a) for a in (x, v, q, qd)]
         ptrs = [None if a is None else a.ctypes.data_as(vp) for a in arrs]
         self._check(load().sim_set_state(self.h, *ptrs, 0))
+
+    # ---- parameters, DOF vectors and the adjoint ------------------------------
+    @property
+    def ndof(self):
+        return 3 * self.n_nodes
+
+    def set_params(self, logE=None, mu=None):
+        """Per-tet ln E (host array) and friction coefficient for the following steps."""
+        arr = None if logE is None else _f64(logE)
+        self._check(load().sim_set_params(self.h, None if arr is None else arr.ctypes.data_as(dp),
+                                          -1.0 if mu is None else float(mu)))
+        if mu is not None:
+            self.params["mu"] = float(mu)
+
+    def set_kinematic(self, T):
+        """Place the kinematic bodies at transforms T (n_kin, 3, 4)."""
+        if self.nkb:
+            arr = _f64(T).reshape(-1)
+            self._check(load().sim_set_kinematic(self.h, arr.ctypes.data_as(dp)))
+
+    def get_dofs(self):
+        """(z, zd) as device tensors (n_nodes * 3): FEM vertices, then ABD q."""
+        import torch
+        z = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
+        zd = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
+        off = 8 * 3 * self.nf
+        q = C.c_void_p(z.data_ptr() + off) if self.nab else None
+        qd = C.c_void_p(zd.data_ptr() + off) if self.nab else None
+        self._check(load().sim_get_state(self.h, _ptr(z), _ptr(zd), q, qd, 1))
+        return z, zd
+
+    def set_dofs(self, z, zd):
+        z = z.contiguous()
+        zd = zd.contiguous()
+        off = 8 * 3 * self.nf
+        q = C.c_void_p(z.data_ptr() + off) if self.nab else None
+        qd = C.c_void_p(zd.data_ptr() + off) if self.nab else None
+        self._check(load().sim_set_state(self.h, _ptr(z), _ptr(zd), q, qd, 1))
+
+    def adjoint(self, z_t, zd_t, z_next, T_t, T_next, gz_next, gzd_next, glogE=None):
+        """Backward of one step: returns (dL/dz_t, dL/dzd_t, glogE (accumulated), dL/dmu)."""
+        import torch
+        gz_t = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
+        gzd_t = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
+        if glogE is None:
+            glogE = torch.zeros(self.nt, dtype=torch.float64, device="cuda")
+        gmu = C.c_double(0.0)
+        Tt = _f64(T_t).reshape(-1) if self.nkb else None
+        Tn = _f64(T_next).reshape(-1) if self.nkb else None
+        self._check(load().sim_adjoint(self.h, _ptr(z_t.contiguous()), _ptr(zd_t.contiguous()), _ptr(z_next.contiguous()),
+                                       Tt.ctypes.data_as(dp) if Tt is not None else None,
+                                       Tn.ctypes.data_as(dp) if Tn is not None else None,
+                                       _ptr(gz_next.contiguous()), _ptr(gzd_next.contiguous()), _ptr(gz_t), _ptr(gzd_t),
+                                       _ptr(glogE), C.byref(gmu)))
+        return gz_t, gzd_t, glogE, gmu.value
 
     def profile(self, enable=True):
         self._check(load().sim_profile(self.h, int(enable)))
