@@ -43,8 +43,8 @@ def load_peaks():
 def make_workload(name):
     from paper_2609_25653_b300 import scenes
     if name == "fingertip_press":
-        sc = scenes.fingertip_press(0, n_steps=20)
-        return sc
+        # the plate keeps pressing at 0.1 mm per step; 60 steps cover warm-up, timed and e2e steps
+        return scenes.fingertip_press(0, n_steps=60)
     if name == "arm_gripper":
         return scenes.arm_gripper_grasp(0)
     raise SystemExit(f"unknown workload {name}")
@@ -362,7 +362,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fingertip_press")
+    ap.add_argument("--workload", default="arm_gripper")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

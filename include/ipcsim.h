@@ -143,6 +143,18 @@ ipc_status sim_create(const ipc_scene_desc* desc, const ipc_params* params, void
  * convergence data and returns when the step is done. */
 ipc_status sim_step(ipcsim* sim, const double* kin_T_next_host, ipc_step_stats* stats_host);
 
+/* Advance n independent simulators by one step each, concurrently: every
+ * simulator runs its own Newton loop (its own convergence, step lengths and
+ * line search) on its own stream, driven from its own host thread, so the
+ * kernels of different scenes overlap on the GPU.  Simulators must be
+ * distinct, each created with its own stream, and of the current device.
+ * kin_T_next_host[i] as for sim_step (may be NULL for scenes without
+ * kinematic bodies, or the whole array NULL); stats_host and status_host
+ * (n entries each) may be NULL.  Returns IPC_OK if every step succeeded,
+ * else the first failing status. */
+ipc_status sim_step_many(ipcsim* const* sims, int n, const double* const* kin_T_next_host, ipc_step_stats* stats_host,
+                         ipc_status* status_host);
+
 /* Copy the state out: FEM positions and velocities (n_fem_verts, 3) and ABD
  * q / qdot (n_abd, 12).  Any pointer may be NULL.  `on_device` != 0 means the
  * pointers are device pointers, else host pointers.  Synchronous. */

@@ -17,6 +17,7 @@
 #include <string>
 #include <tuple>
 #include <unordered_map>
+#include <thread>
 #include <vector>
 #include "../../include/ipcsim.h"
 #include "common.cuh"
@@ -923,6 +924,28 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   CUDA_TRY(cudaStreamSynchronize(cs));
   CUDA_TRY(cudaGetLastError());
   return finish(IPC_OK, "");
+}
+
+ipc_status sim_step_many(ipcsim* const* sims, int n, const double* const* kin_T_next_host, ipc_step_stats* stats_host,
+                         ipc_status* status_host) {
+  if (n < 0 || (n && !sims)) return IPC_ERR_ARG;
+  std::vector<ipc_status> st(n, IPC_OK);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      st[i] = sim_step(sims[i], kin_T_next_host ? kin_T_next_host[i] : nullptr, stats_host ? stats_host + i : nullptr);
+    });
+  for (auto& t : th) t.join();
+  ipc_status worst = IPC_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status_host) status_host[i] = st[i];
+    if (st[i] != IPC_OK && worst == IPC_OK) worst = st[i];
+  }
+  return worst;
 }
 
 ipc_status sim_set_kinematic(ipcsim* sim, const double* kin_T_host) {

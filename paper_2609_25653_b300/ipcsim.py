@@ -78,6 +78,7 @@ SIGNATURES = {
     "sim_profile": ([vp, C.c_int], C.c_int),
     "sim_set_params": ([vp, dp, C.c_double], C.c_int),
     "sim_set_kinematic": ([vp, dp], C.c_int),
+    "sim_step_many": ([C.POINTER(vp), C.c_int, C.POINTER(dp), C.POINTER(StepStats), ip], C.c_int),
     "sim_adjoint": ([vp, vp, vp, vp, dp, dp, vp, vp, vp, vp, vp, dp], C.c_int),
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
 }
@@ -366,3 +367,31 @@ class Simulator:
         nc = C.c_int()
         self._check(load().sim_ccd_alpha(self.h, _ptr(xv_dev), _ptr(pv_dev), C.byref(a), C.byref(nc)))
         return a.value, nc.value
+
+
+def step_many(sims, kin_T_next=None):
+    """Advance independent simulators one step each, concurrently (one stream and host thread per scene).
+
+    kin_T_next: list of (n_kin, 3, 4) arrays (None entries for scenes without kinematic bodies); defaults to
+    each scene's trajectory.  Returns the list of per-scene stats dicts."""
+    n = len(sims)
+    handles = (vp * n)(*[s.h for s in sims])
+    arrs = []
+    ptrs = (dp * n)()
+    for i, s in enumerate(sims):
+        T = kin_T_next[i] if kin_T_next is not None else (s.scene["kin_T"][s.step_index + 1] if s.nkb else None)
+        if T is not None and s.nkb:
+            a = _f64(T).reshape(-1)
+            arrs.append(a)
+            ptrs[i] = a.ctypes.data_as(dp)
+        else:
+            ptrs[i] = None
+    stats = (StepStats * n)()
+    status = (C.c_int * n)()
+    load().sim_step_many(handles, n, ptrs, stats, status)
+    out = []
+    for i, s in enumerate(sims):
+        if status[i] == IPC_OK:
+            s.step_index += 1
+        out.append(stats[i].as_dict())
+    return out
