@@ -255,6 +255,25 @@ ipc_status sim_surface(const ipcsim* sim, int* sv_host, int* tris_host, int* edg
 ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* rec_dev, int project, double* E_dev,
                             double* grad_dev, double* H_dev);
 
+/* sim_eval_barrier without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory once
+ * they run (a control loop on a fixed memory budget, or a process in which
+ * another allocator owns the device memory), because sim_eval_barrier
+ * allocates its scratch with cudaMalloc on every call.  Same arguments,
+ * outputs and error codes as sim_eval_barrier; the caller still provides
+ * every input and output buffer.  Its scratch is one static device array of
+ * 2^20 doubles (8 MiB) that every GPU loading this library holds until the
+ * process exits; scenes needing more (more than about 87 000 nodes) are
+ * rejected with IPC_ERR_ARG and a message naming the size.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents (the
+ * call clears what it accumulates into): calls that overlap on the GPU, from
+ * any simulator, race.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+ipc_status sim_eval_barrier_noalloc(ipcsim* sim, const double* x_dev, int n, const int* rec_dev, int project,
+                                    double* E_dev, double* grad_dev, double* H_dev);
+
 /* Largest step fraction in (0, 1] along the vertex displacement p_dev
  * (n_vertices_all, 3) from x_dev: minimum additive-CCD time of impact over
  * all pairs whose swept boxes overlap.  *n_cand_host: candidates tested. */

@@ -313,6 +313,18 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
 
 }  // namespace
 
+// Read access for the other translation units of this library.
+ipc_status sim_internal_scene(ipcsim* sim, const ipc::DevScene** S, void** stream, double* sh, double* kappa,
+                              std::string** err) {
+  if (!sim) return IPC_ERR_ARG;
+  *S = &sim->S;
+  *stream = (void*)sim->st;
+  *sh = sim->sh;
+  *kappa = sim->kappa;
+  *err = &sim->err;
+  return IPC_OK;
+}
+
 extern "C" {
 
 unsigned long long sim_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }

@@ -78,6 +78,7 @@ SIGNATURES = {
     "sim_profile": ([vp, C.c_int], C.c_int),
     "sim_set_params": ([vp, dp, C.c_double], C.c_int),
     "sim_set_kinematic": ([vp, dp], C.c_int),
+    "sim_eval_barrier_noalloc": ([vp, vp, C.c_int, vp, C.c_int, vp, vp, vp], C.c_int),
     "sim_step_many": ([C.POINTER(vp), C.c_int, C.POINTER(dp), C.POINTER(StepStats), ip], C.c_int),
     "sim_adjoint": ([vp, vp, vp, vp, dp, dp, vp, vp, vp, vp, vp, dp], C.c_int),
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
@@ -361,6 +362,12 @@ class Simulator:
         self._check(load().sim_eval_barrier(self.h, _ptr(xv_dev), n, _ptr(rec_dev), int(project), _ptr(E), _ptr(g),
                                             _ptr(H)))
         return E, g, H[:n]
+
+    def eval_barrier_noalloc(self, xv_dev, rec_dev, E, g, H, project=True):
+        """sim_eval_barrier_noalloc: outputs go into the caller's tensors E (1), g (n_nodes, 3), H (n, 12, 12)."""
+        rec_dev = rec_dev.contiguous()
+        self._check(load().sim_eval_barrier_noalloc(self.h, _ptr(xv_dev), rec_dev.shape[0], _ptr(rec_dev), int(project),
+                                                    _ptr(E), _ptr(g), _ptr(H)))
 
     def ccd_alpha(self, xv_dev, pv_dev):
         a = C.c_double()
