@@ -47,12 +47,20 @@ def make_workload(name):
         return scenes.fingertip_press(0, n_steps=60)
     if name == "arm_gripper":
         return scenes.arm_gripper_grasp(0)
+    if name.startswith("batched"):
+        # "batched" = 64 scenes, "batched16" = 16 scenes, ...
+        n = int(name[len("batched"):] or 64)
+        return scenes.batched_grasps(n)
     raise SystemExit(f"unknown workload {name}")
 
 
-def workload_config(sc, name, extra=None):
-    cfg = {"workload": sc["name"], "fem_tets": int(len(sc["fem_tets"])), "fem_verts": int(len(sc["fem_X"])),
-           "kinematic_bodies": len(sc.get("kin", [])), "abd_bodies": len(sc.get("abd", [])),
+def workload_config(wl, name, extra=None):
+    scs = wl if isinstance(wl, list) else [wl]
+    sc = scs[0]
+    cfg = {"workload": sc["name"] if len(scs) == 1 else f"batched_grasps_{len(scs)}scenes",
+           "scenes": len(scs), "fem_tets": int(sum(len(s["fem_tets"]) for s in scs)),
+           "fem_verts": int(sum(len(s["fem_X"]) for s in scs)),
+           "kinematic_bodies": sum(len(s.get("kin", [])) for s in scs), "abd_bodies": sum(len(s.get("abd", [])) for s in scs),
            "dt": sc["params"]["dt"], "dhat": sc["params"]["dhat"], "mu": sc["params"]["mu"],
            "newton_tol": sc["params"]["newton_tol"], "pcg_rtol": sc["params"]["pcg_rtol"],
            "l2": "flushed between timed steps (256 MB write outside the timed events)"}
@@ -139,14 +147,28 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    sc = make_workload(args.workload)
+    wl = make_workload(args.workload)
+    batched = isinstance(wl, list)
+    precision = args.precision or ("mixed" if batched else "fp64")
+    prec = ipcsim.PREC_MIXED if precision == "mixed" else ipcsim.PREC_FP64
+    if batched:
+        sim = ipcsim.Simulator.batch(wl, precision=prec, stream=stream)
+        sc = sim.scene
+    else:
+        sc = wl
+        sim = ipcsim.Simulator(sc, precision=prec, stream=stream)
+    n_sc = len(wl) if batched else 1
     n_total = args.warmup + args.steps + args.steps + 1
     if sc["kin_T"].shape[0] < n_total + 1 and len(sc.get("kin", [])):
         raise SystemExit("workload trajectory too short for the requested steps")
-    sim = ipcsim.Simulator(sc, stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
+    from paper_2609_25653_b300 import autotune
+    tuned_from_cache = autotune.prepare(sim, prec) if not args.no_autotune else None
+    for w in range(args.warmup):
         sim.step()
+        if w == 0 and tuned_from_cache is False:
+            autotune.record(sim, prec)  # the first warm-up step timed every PCG launch shape
+    (rowg, bps), _ = sim.tuning()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -177,7 +199,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
         total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value = world * args.steps * n_sc / (total_ms / 1e3)
 
     # e2e through the public API with host buffers (transforms in, positions out)
     x_host = np.zeros((sim.nf, 3))
@@ -192,7 +214,7 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * args.steps / e2e_s
+    e2e_value = world * args.steps * n_sc / e2e_s
 
     # roofline of the dominant stage
     peaks, peak_src = load_peaks()
@@ -209,15 +231,20 @@ def run_ours(args):
                 "stage_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["n"]}}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(sc, args.cpu_seconds, sum(s["newton_iters"] for s in stats) / len(stats))
+        # the oracle advances one scene at a time: scene-steps/s of the first scene of a batch
+        cpu = cpu_baseline(wl[0] if batched else sc, args.cpu_seconds, sum(s["newton_iters"] for s in stats) / len(stats))
     clocks = clk.summary()
     if rank == 0:
         newton = [s["newton_iters"] for s in stats]
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(sc, args.workload, {"parallelism": f"replicas{world}",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": workload_config(wl, args.workload, {"parallelism": f"replicas{world}", "precision": precision,
+                                                          "value_counts": "scene-steps" if batched else "steps",
+                                                          "pcg_threads_per_row": rowg, "pcg_blocks_per_sm": bps,
+                                                          "pcg_shape": "cached" if tuned_from_cache else ("autotuned" if tuned_from_cache is False else "default"),
                                                           "newton_iters_per_step": round(sum(newton) / len(newton), 2),
                                                           "pcg_iters_per_step": round(sum(s["pcg_iters_total"] for s in stats) / len(stats), 1),
                                                           "active_pairs_max": max(s["n_pairs_max"] for s in stats)}),
@@ -322,7 +349,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc = make_workload(args.workload)
+    wl = make_workload(args.workload)
+    sc = wl[0] if isinstance(wl, list) else wl
     from oracle import ipc as orc
     o = orc.Oracle(sc)
     if _small_enough(o.S):
@@ -350,7 +378,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 7), "unit": UNIT, "n_gpus": 0, "steps": n,
             "warmup": min(args.warmup, 1), "ms_per_step": round(ms, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(sc, args.workload, {"parallelism": "cpu-1"}),
+            "config": workload_config(wl, args.workload, {"parallelism": "cpu-1", "reference_scene": sc["name"]}),
             "cpu_baseline": {"value": round(v, 7), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 7), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -365,6 +393,9 @@ def main():
     ap.add_argument("--workload", default="arm_gripper")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default PCG launch shape")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                    help="default: fp64 for single scenes, mixed (FP32 PCG, FP64 residuals) for batches")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

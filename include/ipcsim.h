@@ -137,6 +137,19 @@ typedef struct {
  * with cudaMalloc.  stream: a cudaStream_t (NULL = legacy default stream). */
 ipc_status sim_create(const ipc_scene_desc* desc, const ipc_params* params, void* stream, ipcsim** out);
 
+/* Batched data generation: one simulator for n independent scenes.  The
+ * scenes are concatenated (FEM vertices, tets, ABD bodies, kinematic bodies
+ * and stitch springs in scene order, ids shifted accordingly); pairs between
+ * different scenes are never formed; every scene keeps its own barrier and
+ * stitch stiffness (auto-scaled from its own material and mesh).  One
+ * sim_step then advances all scenes with one Newton loop (a common step
+ * length and a common convergence test, with the smallest scene bounding box
+ * as L_bbox) whose PCG solves their block-diagonal system in one cooperative
+ * launch.  sim_step takes the kinematic transforms of all scenes
+ * concatenated; sim_get_state / sim_set_state use the concatenated layout.
+ * Gravity is taken from the first scene. */
+ipc_status sim_create_batch(const ipc_scene_desc* descs, int n, const ipc_params* params, void* stream, ipcsim** out);
+
 /* Advance one time step (Eq. 3).  kin_T_next_host: (n_kin, 12) transforms of
  * the kinematic bodies at t+1 (may be NULL when n_kin == 0).  stats_host may
  * be NULL.  Synchronises the stream once per Newton iteration to read the
@@ -199,6 +212,15 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t_dev, const double* zd_t_de
                        const double* kin_T_t_host, const double* kin_T_next_host, const double* gz_next_dev,
                        const double* gzd_next_dev, double* gz_t_dev, double* gzd_t_dev, double* glogE_dev,
                        double* gmu_host);
+
+/* Launch shape of the cooperative PCG: threads per BSR row in the SpMV
+ * (rowg = 2, 4, 8 or 16; <= 0 keeps the current value) and blocks per SM
+ * (1 or 2; 0 = as many as the rows need, up to occupancy; < 0 keeps).  With
+ * autotune_next_step != 0 the next sim_step times every shape (2 x 4) on its
+ * first linear system and keeps the fastest.  out2 (may be NULL) receives
+ * the shape in use [rowg, blocks_per_sm]; ms8 (may be NULL) the last
+ * autotuning times in ms, index 4 * (blocks_per_sm - 1) + log2(rowg) - 1. */
+ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out2, float* ms8);
 
 /* Per-stage timing with CUDA events recorded on the simulator's stream
  * around each stage of sim_step (cheap; intervals are read at the

@@ -48,7 +48,14 @@ struct DevScene {
   const int* bsr_col;        // (nnzb)
   const int* bsr_diag;       // (n_nodes) index of the diagonal block
   int nnzb;
+  // independent scenes of a batch: scene of every body, per-scene barrier and stitch stiffness
+  int n_scenes;
+  const int* body_scene;     // (nbody)
+  const double* scene_kappa; // (n_scenes)
+  const double* scene_kc;    // (n_scenes)
 };
+
+__device__ inline int scene_of_vertex(const DevScene& S, int v) { return S.body_scene[S.vbody[v]]; }
 
 // ---------------------------------------------------------------------------
 // small vector helpers

@@ -12,6 +12,7 @@
 #include "dist.cuh"
 #include "eig.cuh"
 #include "kernels.h"
+#include <algorithm>
 
 namespace ipc {
 
@@ -166,7 +167,7 @@ __device__ inline void scatter_diag_dirichlet(const DevScene& S, const int* ids,
 
 // mode 0: energy (and min s) only; mode 2: also gradient, projected Hessian, preconditioner diagonal, Dirichlet term.
 __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __restrict__ xv, const int* __restrict__ rec,
-                                                 const int* __restrict__ n_dev, int cap, double sh, double kappa,
+                                                 const int* __restrict__ n_dev, int cap, double sh, double kappa_unused,
                                                  double scale, int mode, int project, double* __restrict__ g,
                                                  double* __restrict__ pairH, double* __restrict__ Dc,
                                                  const double* __restrict__ pD, double* __restrict__ gdir,
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
       int ids[4];
       d3 x[4];
       load_stencil(S, xv, r, ids, x);
+      const double kappa = S.scene_kappa[scene_of_vertex(S, ids[0])];
       Red R;
       double s;
       dist_reduced(kind, type, x, R, s);
@@ -230,10 +232,319 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
   if (threadIdx.x == 0 && min_s) atomicMin(min_s, dbits(-m));
 }
 
+
+// ---------------------------------------------------------------------------
+// warp-cooperative barrier assembly: one warp per pair
+// ---------------------------------------------------------------------------
+// Lane 0 evaluates the reduced distance derivatives, the barrier scalars and
+// the mollifier pieces; the 12x12 Hessian entries, its PSD projection
+// (parallel cyclic Jacobi: n/2 disjoint rotations per round, round-robin
+// pairing, n - 1 rounds per sweep) and every scatter are spread over the
+// lanes, with the matrices in shared memory.
+constexpr int BWARPS = 4;
+
+struct PairWork {
+  double H[144];
+  double V[144];
+  double RH[81];
+  double Rg[9];
+  double C[12];
+  double gs[12];
+  double gc[12];
+  double mH[27];   // mollifier pieces: Haa, Hbb, Hab (3x3 each)
+  double sc[8];    // s, b, b1, b2, m, m1, m2
+  double rc[6], rs[6];
+  double lam[12];
+  int rp[6], rq[6];
+  int idx[12];
+  int ids[4];
+  int nvar, moll, n;
+};
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// PSD projection of the n x n (n even <= 12) matrix A (row stride 12) in place.
+__device__ void warp_project(PairWork& W, int n, int lane) {
+  double* A = W.H;  // compact copy lives in H's storage with stride 12
+  double* V = W.V;
+  for (int e = lane; e < 144; e += 32) V[e] = ((e / 12) == (e % 12)) ? 1.0 : 0.0;
+  // Gershgorin: skip when diagonally dominant with non-negative diagonal
+  bool dom = true;
+  if (lane < n) {
+    double off = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (j != lane) off += fabs(A[12 * lane + j]);
+    dom = A[13 * lane] >= off;
+  }
+  if (__all_sync(0xffffffffu, dom)) return;
+  __syncwarp();
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = lane; e < 144; e += 32) {
+      int i = e / 12, j = e % 12;
+      if (i < n && j < n) {
+        double a2 = A[e] * A[e];
+        tot += a2;
+        if (i != j) off += a2;
+      }
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if (off <= 1e-30 * tot || tot == 0.0) break;
+    for (int r = 0; r < n - 1; ++r) {
+      if (lane < n / 2) {
+        int k = lane;
+        int pa = k, pb = n - 1 - k;
+        int p = pa == 0 ? 0 : 1 + (pa - 1 + r) % (n - 1);
+        int q = 1 + (pb - 1 + r) % (n - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        double apq = A[12 * p + q];
+        double c = 1.0, sn = 0.0;
+        if (apq != 0.0) {
+          double theta = (A[12 * q + q] - A[12 * p + p]) / (2.0 * apq);
+          double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          sn = t * c;
+        }
+        W.rp[k] = p; W.rq[k] = q; W.rc[k] = c; W.rs[k] = sn;
+      }
+      __syncwarp();
+      int items = (n / 2) * n;
+      for (int it = lane; it < items; it += 32) {  // rows: A <- J^T A
+        int k = it / n, j = it % n;
+        int p = W.rp[k], q = W.rq[k];
+        double c = W.rc[k], sn = W.rs[k];
+        double apj = A[12 * p + j], aqj = A[12 * q + j];
+        A[12 * p + j] = c * apj - sn * aqj;
+        A[12 * q + j] = sn * apj + c * aqj;
+      }
+      __syncwarp();
+      for (int it = lane; it < items; it += 32) {  // columns: A <- A J, V <- V J
+        int k = it / n, i = it % n;
+        int p = W.rp[k], q = W.rq[k];
+        double c = W.rc[k], sn = W.rs[k];
+        double aip = A[12 * i + p], aiq = A[12 * i + q];
+        A[12 * i + p] = c * aip - sn * aiq;
+        A[12 * i + q] = sn * aip + c * aiq;
+        double vip = V[12 * i + p], viq = V[12 * i + q];
+        V[12 * i + p] = c * vip - sn * viq;
+        V[12 * i + q] = sn * vip + c * viq;
+      }
+      __syncwarp();
+    }
+  }
+  // A <- V max(diag, 0) V^T (eigenvalues staged in shared memory)
+  if (lane < n) W.lam[lane] = fmax(A[13 * lane], 0.0);
+  __syncwarp();
+  double out[5] = {0, 0, 0, 0, 0};
+  int cnt = 0;
+  for (int e = lane; e < 144; e += 32, ++cnt) {
+    int i = e / 12, j = e % 12;
+    double sacc = 0.0;
+    if (i < n && j < n)
+      for (int k = 0; k < n; ++k) sacc += V[12 * i + k] * W.lam[k] * V[12 * j + k];
+    out[cnt] = sacc;
+  }
+  __syncwarp();
+  cnt = 0;
+  for (int e = lane; e < 144; e += 32, ++cnt) A[e] = out[cnt];
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const double* __restrict__ xv,
+                                                             const int* __restrict__ rec, const int* __restrict__ n_dev,
+                                                             int cap, double sh, double kappa_unused, double scale,
+                                                             int project, double* __restrict__ g,
+                                                             double* __restrict__ pairH, double* __restrict__ Dc,
+                                                             const double* __restrict__ pD, double* __restrict__ gdir,
+                                                             double* __restrict__ E, unsigned long long* min_s) {
+  __shared__ PairWork work[BWARPS];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  PairWork& W = work[wid];
+  int n = min(*n_dev, cap);
+  double e_acc = 0.0, smin = 1e300;
+  int gw = blockIdx.x * BWARPS + wid, nw = gridDim.x * BWARPS;
+  for (int k = gw; k < n; k += nw) {
+    const int* r = rec + 8 * k;
+    int kind = r[0], type = r[3];
+    const double kappa = S.scene_kappa[scene_of_vertex(S, r[4])];
+    if (lane == 0) {
+      d3 x[4];
+      for (int q = 0; q < 4; ++q) { W.ids[q] = r[4 + q]; x[q] = ld3(xv, W.ids[q]); }
+      Red R;
+      double sd;
+      dist_reduced(kind, type, x, R, sd);
+      double b, b1, b2;
+      barrier_fn(sd, sh, b, b1, b2);
+      W.nvar = R.nv;
+      for (int m = 0; m < 3; ++m)
+        for (int q = 0; q < 4; ++q) W.C[4 * m + q] = m < R.nv ? R.C[m][q] : 0.0;
+      for (int m = 0; m < R.nv; ++m) { W.Rg[3 * m] = R.g[m].x; W.Rg[3 * m + 1] = R.g[m].y; W.Rg[3 * m + 2] = R.g[m].z; }
+      for (int m = 0; m < R.nv; ++m)
+        for (int nn = 0; nn < R.nv; ++nn)
+          for (int q = 0; q < 9; ++q) W.RH[27 * m + 9 * nn + q] = R.H[m][nn][q];
+      double mval = 1.0, m1 = 0.0, m2 = 0.0;
+      int moll = 0;
+      if (kind == 1) {
+        double eps_x = 1e-3 * S.edge_rest_sq[r[1]] * S.edge_rest_sq[r[2]];
+        d3 a = x[1] - x[0], bb = x[3] - x[2];
+        d3 nn = cross(a, bb);
+        double c = dot(nn, nn);
+        if (c < eps_x) {
+          moll = 1;
+          double rr = c / eps_x;
+          mval = -rr * rr + 2.0 * rr;
+          m1 = (2.0 - 2.0 * rr) / eps_x;
+          m2 = -2.0 / (eps_x * eps_x);
+          d3 ga = 2.0 * cross(bb, nn), gb = 2.0 * cross(nn, a);
+          double gc[12] = {-ga.x, -ga.y, -ga.z, ga.x, ga.y, ga.z, -gb.x, -gb.y, -gb.z, gb.x, gb.y, gb.z};
+          for (int i = 0; i < 12; ++i) W.gc[i] = gc[i];
+          double Sa[9], Sb[9], Sn[9], T[9];
+          skew9(a, Sa); skew9(bb, Sb); skew9(nn, Sn);
+          mm3(Sb, Sb, T);
+          for (int i = 0; i < 9; ++i) W.mH[i] = -2.0 * T[i];
+          mm3(Sa, Sa, T);
+          for (int i = 0; i < 9; ++i) W.mH[9 + i] = -2.0 * T[i];
+          mm3(Sb, Sa, T);
+          for (int i = 0; i < 9; ++i) W.mH[18 + i] = 2.0 * T[i] - 2.0 * Sn[i];
+        }
+      }
+      W.moll = moll;
+      W.sc[0] = sd; W.sc[1] = b; W.sc[2] = b1; W.sc[3] = b2; W.sc[4] = mval; W.sc[5] = m1; W.sc[6] = m2;
+      smin = fmin(smin, sd);
+      e_acc += kappa * mval * b;
+    }
+    __syncwarp();
+    double b = W.sc[1], b1 = W.sc[2], b2 = W.sc[3], mval = W.sc[4], m1 = W.sc[5], m2 = W.sc[6];
+    int nvar = W.nvar, moll = W.moll;
+    double* Hout = pairH + 144 * (size_t)k;
+    if (b == 0.0 && b1 == 0.0) {
+      for (int e = lane; e < 144; e += 32) Hout[e] = 0.0;
+      __syncwarp();
+      continue;
+    }
+    // gradient of s (12 entries)
+    if (lane < 12) {
+      int q = lane / 3, d = lane % 3;
+      double acc = 0.0;
+      for (int m = 0; m < nvar; ++m) acc += W.C[4 * m + q] * W.Rg[3 * m + d];
+      W.gs[lane] = acc;
+    }
+    __syncwarp();
+    // Hessian entries
+    for (int e = lane; e < 144; e += 32) {
+      int i = e / 12, j = e % 12;
+      int ka = i / 3, ii = i % 3, la = j / 3, jj = j % 3;
+      double hs = 0.0;
+      for (int m = 0; m < nvar; ++m) {
+        double cm = W.C[4 * m + ka];
+        if (cm == 0.0) continue;
+        for (int nn = 0; nn < nvar; ++nn) {
+          double cn = W.C[4 * nn + la];
+          if (cn != 0.0) hs += cm * cn * W.RH[27 * m + 9 * nn + 3 * ii + jj];
+        }
+      }
+      double h = mval * (b2 * W.gs[i] * W.gs[j] + b1 * hs);
+      if (moll) {
+        const double ca[4] = {-1, 1, 0, 0}, cb[4] = {0, 0, -1, 1};
+        double hc = ca[ka] * ca[la] * W.mH[3 * ii + jj] + cb[ka] * cb[la] * W.mH[9 + 3 * ii + jj] +
+                    ca[ka] * cb[la] * W.mH[18 + 3 * ii + jj] + cb[ka] * ca[la] * W.mH[18 + 3 * jj + ii];
+        double hm = m2 * W.gc[i] * W.gc[j] + m1 * hc;
+        double gmi = m1 * W.gc[i], gmj = m1 * W.gc[j];
+        h += b * hm + b1 * (gmi * W.gs[j] + W.gs[i] * gmj);
+      }
+      W.V[e] = kappa * h;  // staging: full 12x12 in V
+    }
+    __syncwarp();
+    if (project) {
+      // compact the involved DOFs (padded to an even count) into H, project, scatter back
+      int mask = moll ? 15 : involved_mask(kind, type);
+      if (lane == 0) {
+        int c = 0;
+        for (int q = 0; q < 4; ++q)
+          if (mask & (1 << q))
+            for (int d = 0; d < 3; ++d) W.idx[c++] = 3 * q + d;
+        W.n = c + (c & 1);
+        if (c & 1) W.idx[c] = -1;
+      }
+      __syncwarp();
+      int nn = W.n;
+      for (int e = lane; e < 144; e += 32) {
+        int a = e / 12, bcol = e % 12;
+        double v = 0.0;
+        if (a < nn && bcol < nn && W.idx[a] >= 0 && W.idx[bcol] >= 0) v = W.V[12 * W.idx[a] + W.idx[bcol]];
+        W.H[e] = v;
+      }
+      __syncwarp();
+      warp_project(W, nn, lane);
+      // scatter H (compact) into a zeroed 12x12 in V
+      for (int e = lane; e < 144; e += 32) W.V[e] = 0.0;
+      __syncwarp();
+      for (int e = lane; e < 144; e += 32) {
+        int a = e / 12, bcol = e % 12;
+        if (a < nn && bcol < nn && W.idx[a] >= 0 && W.idx[bcol] >= 0) W.V[12 * W.idx[a] + W.idx[bcol]] = W.H[e];
+      }
+      __syncwarp();
+    }
+    // scale and store
+    for (int e = lane; e < 144; e += 32) {
+      double v = scale * W.V[e];
+      W.V[e] = v;
+      Hout[e] = v;
+    }
+    __syncwarp();
+    // gradient scatter
+    if (lane < 12) {
+      double gi = kappa * (mval * b1 * W.gs[lane] + (moll ? b * m1 * W.gc[lane] : 0.0));
+      NodeMap m = vertex_nodes(S, W.ids[lane / 3]);
+      for (int t = 0; t < m.n; ++t) atomicAdd(g + 3 * m.node[t] + lane % 3, scale * m.w[t] * gi);
+    }
+    // diagonal node blocks (a, b) entry (i, j): item = (a, b, i, j), 144 items
+    for (int e = lane; e < 144; e += 32) {
+      int row = e / 12, col = e % 12;
+      int a = row / 3, i = row % 3, bb = col / 3, j = col % 3;
+      int va = W.ids[a], vb = W.ids[bb];
+      if (S.vkind[va] == VK_KIN || S.vkind[vb] == VK_KIN) continue;
+      NodeMap ma = vertex_nodes(S, va), mb = vertex_nodes(S, vb);
+      double h = W.V[e];
+      for (int t = 0; t < ma.n; ++t)
+        for (int u = 0; u < mb.n; ++u)
+          if (ma.node[t] == mb.node[u]) atomicAdd(Dc + 9 * ma.node[t] + 3 * i + j, ma.w[t] * mb.w[u] * h);
+    }
+    // Dirichlet: free slot a row i: sum over kinematic slots b of H_ab pD_b
+    if (lane < 12) {
+      int a = lane / 3, i = lane % 3;
+      int va = W.ids[a];
+      if (S.vkind[va] != VK_KIN) {
+        double y = 0.0;
+        for (int bb = 0; bb < 4; ++bb) {
+          int vb = W.ids[bb];
+          if (S.vkind[vb] != VK_KIN) continue;
+          d3 pk = ld3(pD, vb - S.nf - S.na_v);
+          const double* Hr = W.V + 12 * (3 * a + i) + 3 * bb;
+          y += Hr[0] * pk.x + Hr[1] * pk.y + Hr[2] * pk.z;
+        }
+        if (y != 0.0) {
+          NodeMap m = vertex_nodes(S, va);
+          for (int t = 0; t < m.n; ++t) atomicAdd(gdir + 3 * m.node[t] + i, m.w[t] * y);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  double sblk = block_sum(e_acc);
+  if (threadIdx.x == 0) atomicAdd(E, sblk);
+  double mm = block_max(-smin);
+  if (threadIdx.x == 0 && min_s) atomicMin(min_s, dbits(-mm));
+}
+
 // Lagged friction data at the start of the step for every active pair:
 // closest-point weights w, unit normal n, normal force lambda = -kappa m 2 d b'(s).
 __global__ void k_friction_lag(DevScene S, const double* __restrict__ xv, const int* __restrict__ rec,
-                               const int* __restrict__ n_dev, int cap, double sh, double kappa, int* __restrict__ f_ids,
+                               const int* __restrict__ n_dev, int cap, double sh, double kappa_unused, int* __restrict__ f_ids,
                                double* __restrict__ f_w, double* __restrict__ f_n, double* __restrict__ f_lam) {
   int n = min(*n_dev, cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -245,6 +556,7 @@ __global__ void k_friction_lag(DevScene S, const double* __restrict__ xv, const 
     double s, w[4];
     if (kind == 0) pt_classify(x, s, w);
     else ee_classify(x, s, w);
+    const double kappa = S.scene_kappa[scene_of_vertex(S, ids[0])];
     double d = sqrt(s);
     d3 nrm = (1.0 / d) * (w[0] * x[0] + w[1] * x[1] + w[2] * x[2] + w[3] * x[3]);
     double b, b1, b2;
@@ -345,8 +657,15 @@ __global__ void k_friction(DevScene S, const double* __restrict__ xv, const doub
 void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
                     int cap, double sh, double kappa, double scale, int mode, int project, double* g, double* pairH,
                     double* Dc, const double* pD, double* gdir, double* E, unsigned long long* min_s) {
-  k_barrier<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, mode, project, g, pairH, Dc, pD, gdir, E,
-                                  min_s);
+  if (mode >= 2) {
+    // one warp per pair: as many warps as the thread-per-pair launch had threads / 32, at least one block
+    int wgrid = std::max(1, std::min((cap + BWARPS - 1) / BWARPS, 148 * 16));
+    k_barrier_warp<<<wgrid, 32 * BWARPS, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, project, g, pairH, Dc, pD,
+                                                   gdir, E, min_s);
+  } else {
+    k_barrier<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, mode, project, g, pairH, Dc, pD, gdir,
+                                    E, min_s);
+  }
   count_launch();
 }
 void launch_friction_lag(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,

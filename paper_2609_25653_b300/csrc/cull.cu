@@ -22,6 +22,7 @@ __device__ inline bool excluded(const DevScene& S, const int* va, int na, const 
     for (int j = 0; j < nb; ++j)
       if (va[i] == vb[j]) return true;
   int ba = S.vbody[va[0]], bb = S.vbody[vb[0]];
+  if (S.body_scene[ba] != S.body_scene[bb]) return true;  // independent scenes of a batch
   int ka = S.bkind[ba], kb = S.bkind[bb];
   if (ba == bb && ka != VK_FEM) return true;
   if (ka == VK_KIN && kb == VK_KIN) return true;
@@ -231,6 +232,9 @@ __global__ void k_cull_ee_bvh(DevScene S, const double* __restrict__ xv, double 
   int ea = blockIdx.x * blockDim.x + threadIdx.x;
   if (ea >= S.nedge) return;
   int2 A = S.edges[ea];
+  // edges are sorted by vertex id and kinematic vertices come last: every edge after a
+  // kinematic edge is kinematic, so this query could only meet excluded pairs
+  if (S.vkind[A.x] == VK_KIN) return;
   d3 a0 = ld3(xv, A.x), a1 = ld3(xv, A.y);
   double q[6] = {fmin(a0.x, a1.x), fmin(a0.y, a1.y), fmin(a0.z, a1.z), fmax(a0.x, a1.x), fmax(a0.y, a1.y), fmax(a0.z, a1.z)};
   bool ok = traverse(T, q, [&](int eb) {
@@ -279,6 +283,7 @@ __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const do
   int ea = blockIdx.x * blockDim.x + threadIdx.x;
   if (ea >= S.nedge) return;
   int2 A = S.edges[ea];
+  if (S.vkind[A.x] == VK_KIN) return;  // only kinematic edges follow: all pairs excluded
   const double inf = __longlong_as_double(0x7ff0000000000000LL);
   d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf);
   swept(xv, pv, A.x, la, ha);
@@ -300,6 +305,108 @@ __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const do
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_cand, nc);
   if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+}
+
+// ---------------------------------------------------------------------------
+// one sweep per Newton iteration: CCD bound and contact candidates together
+// ---------------------------------------------------------------------------
+// Leaves carry swept boxes over [x, x + p] widened by pad (>= dhat).  Every
+// non-excluded pair whose query box (the unwidened swept box of the point or
+// edge) overlaps a leaf is a candidate: it contains every pair that comes
+// within dhat anywhere on the segment, so the active sets along the line
+// search and at the next iterate are exactly the candidates with s < dhat^2.
+// Candidates whose unwidened swept boxes overlap also get the ACCD time of
+// impact, which reproduces the CCD of the plain sweep.
+__device__ inline void emit_cand(int* cand, int* n_cand, int ccap, int kind, int a, int b, const int* ids) {
+  int slot = atomicAdd(n_cand, 1);
+  if (slot < ccap) {
+    int* r = cand + 8 * slot;
+    r[0] = kind; r[1] = a; r[2] = b; r[3] = -1;
+    r[4] = ids[0]; r[5] = ids[1]; r[6] = ids[2]; r[7] = ids[3];
+  }
+}
+
+__global__ void k_sweep_pt_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
+                               int max_iter, TreeView T, int* cand, int* n_cand, int ccap,
+                               unsigned long long* alpha_bits, int* n_ccd, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nsv) return;
+  int p = S.sv[i];
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf);
+  swept(xv, pv, p, la, ha);
+  double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
+  double amin = 1.0;
+  int nc = 0;
+  bool ok = traverse(T, q, [&](int t) {
+    int3 tv = S.tris[t];
+    int tvv[3] = {tv.x, tv.y, tv.z};
+    if (excluded(S, &p, 1, tvv, 3)) return;
+    int ids[4] = {p, tv.x, tv.y, tv.z};
+    emit_cand(cand, n_cand, ccap, 0, i, t, ids);
+    d3 lb = mk(inf, inf, inf), hb = mk(-inf, -inf, -inf);
+    swept(xv, pv, tv.x, lb, hb);
+    swept(xv, pv, tv.y, lb, hb);
+    swept(xv, pv, tv.z, lb, hb);
+    if (!overlap(la, ha, lb, hb)) return;
+    d3 x[4], pp[4];
+    for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
+    ++nc;
+    amin = fmin(amin, accd(0, x, pp, s_frac, 1.0, max_iter));
+  });
+  if (!ok) atomicOr(err, ERRF_BVH);
+  if (nc) atomicAdd(n_ccd, nc);
+  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+}
+
+__global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
+                               int max_iter, TreeView T, int* cand, int* n_cand, int ccap,
+                               unsigned long long* alpha_bits, int* n_ccd, int* err) {
+  int ea = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ea >= S.nedge) return;
+  int2 A = S.edges[ea];
+  if (S.vkind[A.x] == VK_KIN) return;  // only kinematic edges follow: all pairs excluded
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf);
+  swept(xv, pv, A.x, la, ha);
+  swept(xv, pv, A.y, la, ha);
+  double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
+  double amin = 1.0;
+  int nc = 0;
+  bool ok = traverse(T, q, [&](int eb) {
+    if (eb <= ea) return;
+    int2 B = S.edges[eb];
+    int va[2] = {A.x, A.y}, vb[2] = {B.x, B.y};
+    if (excluded(S, va, 2, vb, 2)) return;
+    int ids[4] = {A.x, A.y, B.x, B.y};
+    emit_cand(cand, n_cand, ccap, 1, ea, eb, ids);
+    d3 lb = mk(inf, inf, inf), hb = mk(-inf, -inf, -inf);
+    swept(xv, pv, B.x, lb, hb);
+    swept(xv, pv, B.y, lb, hb);
+    if (!overlap(la, ha, lb, hb)) return;
+    d3 x[4], pp[4];
+    for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
+    ++nc;
+    amin = fmin(amin, accd(1, x, pp, s_frac, 1.0, max_iter));
+  });
+  if (!ok) atomicOr(err, ERRF_BVH);
+  if (nc) atomicAdd(n_ccd, nc);
+  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+}
+
+// Active pairs among the candidates: the exact classification and s < dhat^2 at xv.
+__global__ void k_filter_active(DevScene S, const double* __restrict__ xv, double sh, const int* __restrict__ cand,
+                                const int* __restrict__ n_cand, int ccap, int* rec, double* rec_s, int* count, int cap) {
+  int n = min(*n_cand, ccap);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const int* r = cand + 8 * c;
+    int kind = r[0];
+    int ids[4] = {r[4], r[5], r[6], r[7]};
+    d3 x[4] = {ld3(xv, ids[0]), ld3(xv, ids[1]), ld3(xv, ids[2]), ld3(xv, ids[3])};
+    double s, w[4];
+    int type = kind == 0 ? pt_classify(x, s, w) : ee_classify(x, s, w);
+    if (s < sh) emit(rec, rec_s, count, cap, kind, r[1], r[2], type, ids, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -350,6 +457,27 @@ void bvh_rebuild(cudaStream_t st, const DevScene& S, const double* xv, double pa
   bvh_build(st, tri);
   bvh_leaf_boxes(st, edge, (const int*)S.edges, 2, xv, nullptr, pad);
   bvh_build(st, edge);
+}
+
+}  // namespace ipc
+
+namespace ipc {
+
+void launch_sweep_bvh(cudaStream_t st, const DevScene& S, const double* xv, const double* pv, double pad, double s_frac,
+                      int max_iter, Bvh& tri, Bvh& edge, int* cand, int* n_cand, int ccap,
+                      unsigned long long* alpha_bits, int* n_ccd, int* err) {
+  bvh_leaf_boxes(st, tri, (const int*)S.tris, 3, xv, pv, pad);
+  bvh_refit(st, tri);
+  bvh_leaf_boxes(st, edge, (const int*)S.edges, 2, xv, pv, pad);
+  bvh_refit(st, edge);
+  if (S.nsv) { k_sweep_pt_bvh<<<(S.nsv + 127) / 128, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, view(tri), cand, n_cand, ccap, alpha_bits, n_ccd, err); count_launch(); }
+  if (S.nedge) { k_sweep_ee_bvh<<<(S.nedge + 127) / 128, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, view(edge), cand, n_cand, ccap, alpha_bits, n_ccd, err); count_launch(); }
+}
+
+void launch_filter_active(cudaStream_t st, int grid, const DevScene& S, const double* xv, double sh, const int* cand,
+                          const int* n_cand, int ccap, int* rec, double* rec_s, int* count, int cap) {
+  k_filter_active<<<grid, 128, 0, st>>>(S, xv, sh, cand, n_cand, ccap, rec, rec_s, count, cap);
+  count_launch();
 }
 
 }  // namespace ipc

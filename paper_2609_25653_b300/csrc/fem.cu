@@ -96,6 +96,144 @@ __global__ void k_inertia(DevScene S, const double* __restrict__ z, const double
   if (threadIdx.x == 0) atomicAdd(E, s);
 }
 
+
+// ---------------------------------------------------------------------------
+// analytic PSD projection of the Neo-Hookean Hessian
+// ---------------------------------------------------------------------------
+// With a rotation-variant SVD F = U diag(s) V^T (U, V rotations, s_2 may be
+// negative) the second derivative of J = det F in the rotated frame
+// X = U^T dF V is the quadratic form sum_{i<j} s_k (X_ii X_jj - X_ij X_ji)
+// (k the third index), and cof F = U diag(s1 s2, s0 s2, s0 s1) V^T.  Hence
+// d2Psi/dF2 = mu I + lam g g^T + kJ d2J/dF2 has the eigenvectors
+//   twist_k = U (e_i e_j^T - e_j e_i^T) V^T / sqrt2,  eigenvalue mu + kJ s_k
+//   flip_k  = U (e_i e_j^T + e_j e_i^T) V^T / sqrt2,  eigenvalue mu - kJ s_k
+// and three in span{U e_m e_m^T V^T} from the 3x3 matrix
+//   A = mu I + lam c c^T + kJ [[0, s2, s1], [s2, 0, s0], [s1, s0, 0]],
+//   c = (s1 s2, s0 s2, s0 s1).
+// Keeping the non-negative eigenvalues gives the nearest PSD matrix.
+
+// cyclic Jacobi for a symmetric 3x3 (row-major); eigenvectors in the columns of V
+__device__ inline void jacobi3(double* A, double* V) {
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 24; ++sweep) {
+    double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    double tot = A[0] * A[0] + A[4] * A[4] + A[8] * A[8] + 2.0 * off;
+    if (off <= 1e-32 * tot || tot == 0.0) break;
+    const int P[3] = {0, 0, 1}, Q[3] = {1, 2, 2};
+    for (int r = 0; r < 3; ++r) {
+      int p = P[r], q = Q[r];
+      double apq = A[3 * p + q];
+      if (apq == 0.0) continue;
+      double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+      double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+      for (int k = 0; k < 3; ++k) {
+        double akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = c * akp - sn * akq;
+        A[3 * k + q] = sn * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        double apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = c * apk - sn * aqk;
+        A[3 * q + k] = sn * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        double vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - sn * vkq;
+        V[3 * k + q] = sn * vkp + c * vkq;
+      }
+    }
+  }
+}
+
+// F = U diag(s) V^T with U, V proper rotations (columns), s0 >= s1 >= |s2|, s2 signed.
+__device__ inline void svd3_rv(const d3* f, d3* U, d3* Vc, double* s) {
+  // columns f[j] of F; S = F^T F
+  double A[9], V[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[3 * i + j] = dot(f[i], f[j]);
+  jacobi3(A, V);
+  double e[3] = {A[0], A[4], A[8]};
+  int ord[3] = {0, 1, 2};
+  for (int a = 0; a < 2; ++a)
+    for (int b = a + 1; b < 3; ++b)
+      if (e[ord[b]] > e[ord[a]]) { int t = ord[a]; ord[a] = ord[b]; ord[b] = t; }
+  for (int m = 0; m < 3; ++m) Vc[m] = mk(V[ord[m]], V[3 + ord[m]], V[6 + ord[m]]);
+  if (dot(cross(Vc[0], Vc[1]), Vc[2]) < 0.0) Vc[2] = -1.0 * Vc[2];
+  // b_m = F v_m = sum_j v_m[j] f_j
+  d3 b[3];
+  for (int m = 0; m < 3; ++m) b[m] = Vc[m].x * f[0] + Vc[m].y * f[1] + Vc[m].z * f[2];
+  double n0 = sqrt(dot(b[0], b[0]));
+  U[0] = n0 > 1e-300 ? (1.0 / n0) * b[0] : mk(1, 0, 0);
+  d3 u1 = b[1] - dot(U[0], b[1]) * U[0];
+  double n1 = sqrt(dot(u1, u1));
+  if (n1 > 1e-14 * (n0 + 1e-300)) u1 = (1.0 / n1) * u1;
+  else {
+    d3 t = fabs(U[0].x) < 0.9 ? mk(1, 0, 0) : mk(0, 1, 0);
+    u1 = cross(U[0], t);
+    u1 = (1.0 / sqrt(dot(u1, u1))) * u1;
+  }
+  U[1] = u1;
+  U[2] = cross(U[0], U[1]);
+  s[0] = dot(U[0], b[0]);
+  s[1] = dot(U[1], b[1]);
+  s[2] = dot(U[2], b[2]);
+}
+
+// Projected 12x12 tet Hessian (row-major, times sv) from the eigen-modes above.
+// Cc[a][j]: dF(:,j)/dx_a coefficients.
+__device__ inline void snh_projected_hessian(const d3* f, double mu, double lam, const double Cc[4][3], double sv,
+                                             double* H12) {
+  d3 U[3], V[3];
+  double s[3];
+  svd3_rv(f, U, V, s);
+  double J = s[0] * s[1] * s[2];
+  double kJ = lam * (J - 1.0) - mu;
+  for (int i = 0; i < 144; ++i) H12[i] = 0.0;
+  // w_a = M C[a], M = U B V^T  =>  M c = U (B (V^T c))
+  double Vt_c[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int m = 0; m < 3; ++m) Vt_c[a][m] = V[m].x * Cc[a][0] + V[m].y * Cc[a][1] + V[m].z * Cc[a][2];
+  auto add_mode = [&](const double* B, double lamb) {
+    if (!(lamb > 0.0)) return;
+    double w[12];
+    for (int a = 0; a < 4; ++a) {
+      double y0 = B[0] * Vt_c[a][0] + B[1] * Vt_c[a][1] + B[2] * Vt_c[a][2];
+      double y1 = B[3] * Vt_c[a][0] + B[4] * Vt_c[a][1] + B[5] * Vt_c[a][2];
+      double y2 = B[6] * Vt_c[a][0] + B[7] * Vt_c[a][1] + B[8] * Vt_c[a][2];
+      d3 m = y0 * U[0] + y1 * U[1] + y2 * U[2];
+      w[3 * a] = m.x; w[3 * a + 1] = m.y; w[3 * a + 2] = m.z;
+    }
+    double c = sv * lamb;
+    for (int i = 0; i < 12; ++i) {
+      double ci = c * w[i];
+      for (int j = 0; j < 12; ++j) H12[12 * i + j] += ci * w[j];
+    }
+  };
+  const double r2 = 0.70710678118654752440;
+  const int PI[3] = {1, 0, 0}, PJ[3] = {2, 2, 1};  // pair (i, j) for k = 0, 1, 2
+  for (int k = 0; k < 3; ++k) {
+    int i = PI[k], j = PJ[k];
+    double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    B[3 * i + j] = r2; B[3 * j + i] = -r2;
+    add_mode(B, mu + kJ * s[k]);   // twist
+    B[3 * j + i] = r2;
+    add_mode(B, mu - kJ * s[k]);   // flip
+  }
+  double c3[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+  double A[9], Y[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[3 * i + j] = (i == j ? mu : 0.0) + lam * c3[i] * c3[j];
+  A[1] += kJ * s[2]; A[3] += kJ * s[2];
+  A[2] += kJ * s[1]; A[6] += kJ * s[1];
+  A[5] += kJ * s[0]; A[7] += kJ * s[0];
+  jacobi3(A, Y);
+  for (int q = 0; q < 3; ++q) {
+    double B[9] = {Y[q], 0, 0, 0, Y[3 + q], 0, 0, 0, Y[6 + q]};
+    add_mode(B, A[4 * q]);
+  }
+}
+
 // Neo-Hookean energy Psi = mu/2 (|F|^2 - 3) - mu (J - 1) + lam/2 (J - 1)^2 per tet (§III-C.1),
 // its gradient and PSD-projected Hessian scattered into the BSR matrix.
 // scale = dt^2 for the incremental potential; mode: 0 energy only, 1 + gradient, 2 + Hessian.
@@ -137,7 +275,22 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
         atomicAdd(g + 3 * id[a] + 1, sv * ga.y);
         atomicAdd(g + 3 * id[a] + 2, sv * ga.z);
       }
-      if (mode >= 2) {
+      if (mode >= 2 && project) {
+        double H12[144];
+        snh_projected_hessian(f, mu, lam, Cc, sv, H12);
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            if (Hval) {
+              HT* dst = Hval + 9 * (size_t)S.tet_blk[16 * e + 4 * a + b];
+              for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) atomicAdd(dst + 3 * i + k, (HT)H12[12 * (3 * a + i) + 3 * b + k]);
+            }
+            if (tetH)
+              for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k)
+                  tetH[144 * (size_t)e + 12 * (3 * a + i) + 3 * b + k] = H12[12 * (3 * a + i) + 3 * b + k];
+          }
+      } else if (mode >= 2) {
         double H[81];
         double gv[9] = {cf[0].x, cf[0].y, cf[0].z, cf[1].x, cf[1].y, cf[1].z, cf[2].x, cf[2].y, cf[2].z};
         for (int p = 0; p < 9; ++p)
@@ -155,7 +308,6 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
               H[9 * (3 * B_[k] + j) + 3 * A_[k] + i] += v;
             }
         }
-        if (project) project_psd<9, double>(H);
         for (int a = 0; a < 4; ++a)
           for (int b = 0; b < 4; ++b) {
             double blk[9];
@@ -182,12 +334,13 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
 }
 
 // Stitch springs 1/2 k_c |x_i - x^_i|^2 (Eq. 2); the constant Hessian k_c I is part of the fixed matrix.
-__global__ void k_stitch(DevScene S, const double* __restrict__ xv, const double* __restrict__ stitch_hat, double k_c,
+__global__ void k_stitch(DevScene S, const double* __restrict__ xv, const double* __restrict__ stitch_hat, double k_c_unused,
                          double scale, int mode, double* __restrict__ g, double* __restrict__ E) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (i < S.n_stitch) {
     int v = S.stitch_v[i];
+    const double k_c = S.scene_kc[scene_of_vertex(S, v)];
     d3 d = ld3(xv, v) - ld3(stitch_hat, i);
     e = 0.5 * k_c * dot(d, d);
     if (mode >= 1) {

@@ -31,7 +31,8 @@ struct PcgArgs {
   double* z;
   double* p;
   double* y;
-  double* partial;  // 3 * grid doubles
+  double* s;        // Chronopoulos-Gear auxiliary direction (A p)
+  double* partial;  // 5 * grid doubles
   double rtol;
   int max_iter;
   int* out;         // [iterations, status, FP64 residual replacements]
@@ -96,6 +97,11 @@ void launch_cull_bvh(cudaStream_t, const DevScene&, const double* xv, double sh,
 void launch_ccd_bvh(cudaStream_t, const DevScene&, const double* xv, const double* pv, double s_frac, int max_iter,
                     Bvh& tri, Bvh& edge, unsigned long long* alpha_bits, int* n_cand, int* err);
 void bvh_rebuild(cudaStream_t, const DevScene&, const double* xv, double pad, Bvh& tri, Bvh& edge);
+void launch_sweep_bvh(cudaStream_t, const DevScene&, const double* xv, const double* pv, double pad, double s_frac,
+                      int max_iter, Bvh& tri, Bvh& edge, int* cand, int* n_cand, int ccap,
+                      unsigned long long* alpha_bits, int* n_ccd, int* err);
+void launch_filter_active(cudaStream_t, int grid, const DevScene&, const double* xv, double sh, const int* cand,
+                          const int* n_cand, int ccap, int* rec, double* rec_s, int* count, int cap);
 
 // adjoint.cu
 void launch_theta_grad(cudaStream_t, const DevScene&, const double* xv, const double* lam, double scale, double* out);
@@ -109,7 +115,9 @@ void launch_axpy(cudaStream_t, int n, const double* x, double alpha, const doubl
 void launch_dinv(cudaStream_t, int n_nodes, const int* diag, const double* val, const double* Dc, double* Dinv);
 void launch_rhs(cudaStream_t, int n, const double* g, const double* gdir, double* rhs);
 int pcg_max_blocks(int threads);
-cudaError_t launch_pcg(cudaStream_t, int grid, int threads, const PcgArgs& a);
+constexpr int PCG_ROW_GROUP = 4;  // default threads per BSR row in the PCG's SpMV
+// rowg: threads per BSR row in the SpMV (2, 4, 8 or 16)
+cudaError_t launch_pcg(cudaStream_t, int grid, int threads, const PcgArgs& a, int rowg = 4);
 int pcg_max_blocks_fp32(int threads);
 void launch_to_float(cudaStream_t, size_t n, const double* src, float* dst, const int* n_dev = nullptr, int stride = 0);
 

@@ -163,11 +163,169 @@ __device__ inline void precond_node(const M* Dinv, const double* r, V* z, int i,
   rr += r[3 * i] * r[3 * i] + r[3 * i + 1] * r[3 * i + 1] + r[3 * i + 2] * r[3 * i + 2];
 }
 
-// One PCG solve.  T = double: all FP64.  T = float: FP32 operator, preconditioner,
-// search direction and preconditioned residual, FP64 x / r / y / dots, and
-// at FP32 convergence up to 3 replacements r <- b - A x with the FP64 operator.
-template <typename T>
-__global__ void k_pcg(PcgArgs a) {
+// w += A u over the BSR rows, ROWG threads per row (row blocks strided among
+// them, partial sums combined by shuffles); returns this thread's share of
+// u^T (A_bsr u).  Every thread of the grid must call it (whole warps shuffle).
+template <typename M, typename V, int ROWG>
+__device__ inline double spmv_bsr(const PcgArgs& a, const M* val, const V* u, double* w, int tid, int nthr) {
+  double acc = 0.0;
+  int gl = threadIdx.x & (ROWG - 1);
+  int group = tid / ROWG, ngroups = nthr / ROWG;
+  int n_pad = ((a.n_nodes + ngroups - 1) / ngroups) * ngroups;
+  for (int i = group; i < n_pad; i += ngroups) {
+    M s0 = M(0), s1 = M(0), s2 = M(0);
+    if (i < a.n_nodes) {
+      int k1 = a.row[i + 1];
+      for (int k = a.row[i] + gl; k < k1; k += ROWG) {
+        const M* A = val + 9 * (size_t)k;
+        int j = a.col[k];
+        M p0 = (M)u[3 * j], p1 = (M)u[3 * j + 1], p2 = (M)u[3 * j + 2];
+        s0 += A[0] * p0 + A[1] * p1 + A[2] * p2;
+        s1 += A[3] * p0 + A[4] * p1 + A[5] * p2;
+        s2 += A[6] * p0 + A[7] * p1 + A[8] * p2;
+      }
+    }
+    for (int o = ROWG / 2; o > 0; o >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, o, ROWG);
+      s1 += __shfl_down_sync(0xffffffffu, s1, o, ROWG);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o, ROWG);
+    }
+    if (gl == 0 && i < a.n_nodes) {
+      atomicAdd(w + 3 * i, (double)s0);
+      atomicAdd(w + 3 * i + 1, (double)s1);
+      atomicAdd(w + 3 * i + 2, (double)s2);
+      acc += (double)u[3 * i] * (double)s0 + (double)u[3 * i + 1] * (double)s1 + (double)u[3 * i + 2] * (double)s2;
+    }
+  }
+  return acc;
+}
+
+// Contact terms of w += A u, one warp per barrier pair and per friction pair:
+// lane j < 12 gathers u for DOF j of the stencil (slot j / 3, component j % 3),
+// lane r < 12 forms row r of the 12x12 block product and scatters it.
+// Returns this lane's share of u^T (A_contact u).  Whole warps must call it.
+template <typename M, typename V>
+__device__ inline double apply_contact_warp(const PcgArgs& a, const M* pairH, const M* fHu, const V* u, double* w,
+                                            int tid, int nthr) {
+  const DevScene& S = a.S;
+  int lane = threadIdx.x & 31;
+  int warp = tid >> 5, nwarps = nthr >> 5;
+  double acc = 0.0;
+  int np = min(*a.n_pairs, a.cap);
+  int slot = lane / 3, comp = lane % 3;
+  for (int k = warp; k < np; k += nwarps) {
+    const int* r = a.rec + 8 * k;
+    int v = lane < 12 ? r[4 + slot] : 0;
+    bool active = lane < 12 && S.vkind[v] != VK_KIN;
+    M uj = M(0);
+    if (active) {
+      NodeMap m = vertex_nodes(S, v);
+      for (int t = 0; t < m.n; ++t) uj += (M)m.w[t] * (M)u[3 * m.node[t] + comp];
+    }
+    const M* H = pairH + 144 * (size_t)k + 12 * (lane < 12 ? lane : 0);
+    M wr = M(0);
+    for (int j = 0; j < 12; ++j) {
+      M uv = __shfl_sync(0xffffffffu, uj, j);
+      if (lane < 12) wr += H[j] * uv;
+    }
+    if (active) {
+      NodeMap m = vertex_nodes(S, v);
+      for (int t = 0; t < m.n; ++t) atomicAdd(w + 3 * m.node[t] + comp, m.w[t] * (double)wr);
+      acc += (double)uj * (double)wr;
+    }
+  }
+  for (int k = warp; k < a.n_fric; k += nwarps) {
+    const int* ids = a.f_ids + 4 * k;
+    const double* wk = a.f_w + 4 * k;
+    const M* Hu = fHu + 9 * k;
+    int v = lane < 12 ? ids[slot] : 0;
+    double wgt = lane < 12 ? wk[slot] : 0.0;
+    bool active = lane < 12 && wgt != 0.0 && S.vkind[v] != VK_KIN;
+    M uj = M(0);
+    if (active) {
+      NodeMap m = vertex_nodes(S, v);
+      for (int t = 0; t < m.n; ++t) uj += (M)m.w[t] * (M)u[3 * m.node[t] + comp];
+    }
+    // U_c = sum over slots of w_k u_{k,c}: lanes c, c+3, c+6, c+9
+    M contrib = (M)wgt * uj;
+    M U0 = M(0), U1 = M(0), U2 = M(0);
+    for (int q = 0; q < 4; ++q) {
+      U0 += __shfl_sync(0xffffffffu, contrib, 3 * q);
+      U1 += __shfl_sync(0xffffffffu, contrib, 3 * q + 1);
+      U2 += __shfl_sync(0xffffffffu, contrib, 3 * q + 2);
+    }
+    M tc = M(0);
+    if (lane < 12) tc = Hu[3 * comp] * U0 + Hu[3 * comp + 1] * U1 + Hu[3 * comp + 2] * U2;
+    if (active) {
+      NodeMap m = vertex_nodes(S, v);
+      double y = wgt * (double)tc;
+      for (int t = 0; t < m.n; ++t) atomicAdd(w + 3 * m.node[t] + comp, m.w[t] * y);
+      acc += (double)uj * y;
+    }
+  }
+  return acc;
+}
+
+// w += A u for the whole operator (BSR + barrier pairs + friction pairs); returns this thread's share of u^T A u.
+template <typename M, typename V, int ROWG>
+__device__ inline double apply_full(const PcgArgs& a, const M* val, const M* pairH, const M* fHu, const V* u, double* w,
+                                    int tid, int nthr) {
+  double acc = spmv_bsr<M, V, ROWG>(a, val, u, w, tid, nthr);
+  acc += apply_contact_warp<M, V>(a, pairH, fHu, u, w, tid, nthr);
+  return acc;
+}
+
+// Sums of up to three per-thread values over the block (result in every thread).
+__device__ inline void block_sum3(double& a0, double& a1, double& a2) {
+  __shared__ double sh3[3][32];
+  __shared__ double tot3[3];
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, o);
+    a1 += __shfl_down_sync(0xffffffffu, a1, o);
+    a2 += __shfl_down_sync(0xffffffffu, a2, o);
+  }
+  int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) { sh3[0][wi] = a0; sh3[1][wi] = a1; sh3[2][wi] = a2; }
+  __syncthreads();
+  if (wi == 0) {
+    double b0 = lane < nw ? sh3[0][lane] : 0.0, b1 = lane < nw ? sh3[1][lane] : 0.0, b2 = lane < nw ? sh3[2][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      b0 += __shfl_down_sync(0xffffffffu, b0, o);
+      b1 += __shfl_down_sync(0xffffffffu, b1, o);
+      b2 += __shfl_down_sync(0xffffffffu, b2, o);
+    }
+    if (lane == 0) { tot3[0] = b0; tot3[1] = b1; tot3[2] = b2; }
+  }
+  __syncthreads();
+  a0 = tot3[0]; a1 = tot3[1]; a2 = tot3[2];
+  __syncthreads();
+}
+
+// Totals of three partial arrays (one entry per block), identical in every block.
+__device__ inline void grid_total3(const double* p0, const double* p1, const double* p2, int nblk, double& t0,
+                                   double& t1, double& t2) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    a0 += p0[b];
+    a1 += p1[b];
+    a2 += p2[b];
+  }
+  block_sum3(a0, a1, a2);
+  t0 = a0; t1 = a1; t2 = a2;
+}
+
+// One PCG solve in the Chronopoulos-Gear form: both dot products of an
+// iteration come from one reduction point, so an iteration costs two grid
+// barriers (vector update | operator application).
+//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,  u = M^-1 r,
+//   w = A u,  gamma = r.u,  delta = u.w,
+//   beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old).
+// T = double: all FP64.  T = float: FP32 operator, preconditioner, u and p;
+// x, r, w, s and every dot product FP64; at FP32 convergence up to 3
+// replacements r <- b - A x with the FP64 operator.
+template <typename T, int ROWG>
+__global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   cg::grid_group grid = cg::this_grid();
   int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   int nblk = gridDim.x;
@@ -178,89 +336,115 @@ __global__ void k_pcg(PcgArgs a) {
   const T* fHu = F32 ? (const T*)a.f_Hu32 : (const T*)a.f_Hu;
   const T* Dinv = F32 ? (const T*)a.Dinv32 : (const T*)a.Dinv;
   T* pv = F32 ? (T*)a.p32 : (T*)a.p;
-  T* zv = F32 ? (T*)a.z32 : (T*)a.z;
+  T* uv = F32 ? (T*)a.z32 : (T*)a.z;
+  double* w = a.y;
+  double* sv = a.s;
+  // partial sums: A (u.Au) is rewritten one barrier after its last read; B (r.u) and C (r.r)
+  // are written in the vector phase right after the reads, so they alternate between two
+  // buffers by iteration parity (a buffer is rewritten two barriers after its last read)
   double* partA = a.partial;
-  double* partB = a.partial + nblk;
-  double* partC = a.partial + 2 * nblk;
-  // x = 0, r = b, z = Dinv r, p = z, y = 0
-  double rz_l = 0.0, bb_l = 0.0;
+  auto partB = [&](int par) { return a.partial + (1 + par) * nblk; };
+  auto partC = [&](int par) { return a.partial + (3 + par) * nblk; };
+  // x = 0, r = b, u = M^-1 r, p = s = w = 0
+  double g_l = 0.0, rr_l = 0.0;
   for (int i = tid; i < a.n_nodes; i += nthr) {
     for (int d = 0; d < 3; ++d) {
       a.x[3 * i + d] = 0.0;
       a.r[3 * i + d] = a.b[3 * i + d];
-      a.y[3 * i + d] = 0.0;
+      w[3 * i + d] = 0.0;
+      sv[3 * i + d] = 0.0;
+      pv[3 * i + d] = T(0);
     }
-    precond_node<T, T>(Dinv, a.r, zv, i, rz_l, bb_l);
-    for (int d = 0; d < 3; ++d) pv[3 * i + d] = zv[3 * i + d];
+    precond_node<T, T>(Dinv, a.r, uv, i, g_l, rr_l);
   }
-  double v = block_sum(rz_l);
-  if (threadIdx.x == 0) partB[blockIdx.x] = v;
-  v = block_sum(bb_l);
-  if (threadIdx.x == 0) partC[blockIdx.x] = v;
+  double zero = 0.0;
+  block_sum3(g_l, rr_l, zero);
+  if (threadIdx.x == 0) { partB(1)[blockIdx.x] = g_l; partC(1)[blockIdx.x] = rr_l; }
   grid.sync();
-  double rz = grid_total(partB, nblk);
-  double bb = grid_total(partC, nblk);
+  double d_l = apply_full<T, T, ROWG>(a, val, pairH, fHu, uv, w, tid, nthr);
+  double v = block_sum(d_l);
+  if (threadIdx.x == 0) partA[blockIdx.x] = v;
+  grid.sync();
+  double gamma, rr, delta;
+  grid_total3(partB(1), partC(1), partA, nblk, gamma, rr, delta);
+  double bb = rr;
   double tol2 = a.rtol * a.rtol * bb;
   int it = 0, status = 0, replaced = 0;
-  double rr = bb;
+  double alpha = 0.0, beta = 0.0;
   if (bb > 0.0) {
-    for (it = 0; it < a.max_iter; ++it) {
-      // A: y = A p, partial p^T A p
-      double pap_l = apply_A<T, T>(a, val, pairH, fHu, pv, a.y, tid, nthr);
-      v = block_sum(pap_l);
-      if (threadIdx.x == 0) partA[blockIdx.x] = v;
-      grid.sync();
-      double pap = grid_total(partA, nblk);
-      if (!(pap > 0.0)) { status = isfinite(pap) ? 1 : 2; break; }
-      double alpha = rz / pap;
-      // B: x += alpha p, r -= alpha y, z = Dinv r, y = 0
-      double rz_n = 0.0, rr_n = 0.0;
+    if (!(delta > 0.0)) status = isfinite(delta) ? 1 : 2;
+    alpha = gamma / delta;
+    for (it = 0; status == 0 && it < a.max_iter; ++it) {
+      // V: vector updates (node-local); w is consumed into s and cleared for the next product
+      g_l = 0.0;
+      rr_l = 0.0;
       for (int i = tid; i < a.n_nodes; i += nthr) {
         for (int d = 0; d < 3; ++d) {
-          a.x[3 * i + d] += alpha * (double)pv[3 * i + d];
-          a.r[3 * i + d] -= alpha * a.y[3 * i + d];
-          a.y[3 * i + d] = 0.0;
+          int q = 3 * i + d;
+          double pq = (double)uv[q] + beta * (double)pv[q];
+          double sq = w[q] + beta * sv[q];
+          pv[q] = (T)pq;
+          sv[q] = sq;
+          a.x[q] += alpha * pq;
+          a.r[q] -= alpha * sq;
+          w[q] = 0.0;
         }
-        precond_node<T, T>(Dinv, a.r, zv, i, rz_n, rr_n);
+        precond_node<T, T>(Dinv, a.r, uv, i, g_l, rr_l);
       }
-      v = block_sum(rz_n);
-      if (threadIdx.x == 0) partB[blockIdx.x] = v;
-      v = block_sum(rr_n);
-      if (threadIdx.x == 0) partC[blockIdx.x] = v;
+      const int par = it & 1;
+      zero = 0.0;
+      block_sum3(g_l, rr_l, zero);
+      if (threadIdx.x == 0) { partB(par)[blockIdx.x] = g_l; partC(par)[blockIdx.x] = rr_l; }
       grid.sync();
-      double rz_new = grid_total(partB, nblk);
-      rr = grid_total(partC, nblk);
-      if (!isfinite(rr)) { status = 2; ++it; break; }
+      // W: w = A u and u.w
+      d_l = apply_full<T, T, ROWG>(a, val, pairH, fHu, uv, w, tid, nthr);
+      v = block_sum(d_l);
+      if (threadIdx.x == 0) partA[blockIdx.x] = v;
+      grid.sync();
+      double gamma_new;
+      grid_total3(partB(par), partC(par), partA, nblk, gamma_new, rr, delta);
+      if (!isfinite(rr) || !isfinite(delta)) { status = 2; ++it; break; }
       if (rr <= tol2) {
         if (!F32 || replaced >= 3) { ++it; break; }
-        // FP64 residual replacement: r = b - A64 x (y is zero here)
+        // FP64 residual replacement and restart: r = b - A64 x
         ++replaced;
-        apply_A<double, double>(a, a.val, a.pairH, a.f_Hu, a.x, a.y, tid, nthr);
+        for (int q = tid; q < n3; q += nthr) sv[q] = 0.0;
         grid.sync();
-        double rz2 = 0.0, rr2 = 0.0;
+        apply_full<double, double, ROWG>(a, a.val, a.pairH, a.f_Hu, a.x, sv, tid, nthr);
+        grid.sync();
+        g_l = 0.0;
+        rr_l = 0.0;
         for (int i = tid; i < a.n_nodes; i += nthr) {
           for (int d = 0; d < 3; ++d) {
-            a.r[3 * i + d] = a.b[3 * i + d] - a.y[3 * i + d];
-            a.y[3 * i + d] = 0.0;
+            int q = 3 * i + d;
+            a.r[q] = a.b[q] - sv[q];
+            w[q] = 0.0;
+            sv[q] = 0.0;
+            pv[q] = T(0);
           }
-          precond_node<T, T>(Dinv, a.r, zv, i, rz2, rr2);
-          for (int d = 0; d < 3; ++d) pv[3 * i + d] = zv[3 * i + d];
+          precond_node<T, T>(Dinv, a.r, uv, i, g_l, rr_l);
         }
-        v = block_sum(rz2);
-        if (threadIdx.x == 0) partB[blockIdx.x] = v;
-        v = block_sum(rr2);
-        if (threadIdx.x == 0) partC[blockIdx.x] = v;
+        // this iteration's buffer: read before the two barriers above, rewritten next at it + 2
+        zero = 0.0;
+        block_sum3(g_l, rr_l, zero);
+        if (threadIdx.x == 0) { partB(par)[blockIdx.x] = g_l; partC(par)[blockIdx.x] = rr_l; }
         grid.sync();
-        rz = grid_total(partB, nblk);
-        rr = grid_total(partC, nblk);
+        d_l = apply_full<T, T, ROWG>(a, val, pairH, fHu, uv, w, tid, nthr);
+        v = block_sum(d_l);
+        if (threadIdx.x == 0) partA[blockIdx.x] = v;
+        grid.sync();
+        grid_total3(partB(par), partC(par), partA, nblk, gamma, rr, delta);
         if (rr <= tol2) { ++it; break; }
+        if (!(delta > 0.0)) { status = isfinite(delta) ? 1 : 2; ++it; break; }
+        beta = 0.0;
+        alpha = gamma / delta;
         continue;
       }
-      double beta = rz_new / rz;
-      rz = rz_new;
-      // C: p = z + beta p
-      for (int i = tid; i < n3; i += nthr) pv[i] = (T)((double)zv[i] + beta * (double)pv[i]);
-      grid.sync();
+      beta = gamma_new / gamma;
+      double den = delta - beta * gamma_new / alpha;
+      if (!(den > 0.0)) { status = isfinite(den) ? 1 : 2; ++it; break; }
+      alpha = gamma_new / den;
+      gamma = gamma_new;
     }
   } else {
     for (int i = tid; i < n3; i += nthr) a.x[i] = 0.0;
@@ -292,7 +476,7 @@ int pcg_max_blocks(int threads) {
   int dev, sms, per_sm;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double>, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double, 4>, threads, 0);
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
@@ -300,15 +484,25 @@ int pcg_max_blocks_fp32(int threads) {
   int dev, sms, per_sm;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float>, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float, 4>, threads, 0);
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-cudaError_t launch_pcg(cudaStream_t st, int grid, int threads, const PcgArgs& a) {
+template <typename T>
+static void* pcg_kernel(int rowg) {
+  switch (rowg) {
+    case 2: return (void*)k_pcg<T, 2>;
+    case 8: return (void*)k_pcg<T, 8>;
+    case 16: return (void*)k_pcg<T, 16>;
+    default: return (void*)k_pcg<T, 4>;
+  }
+}
+
+cudaError_t launch_pcg(cudaStream_t st, int grid, int threads, const PcgArgs& a, int rowg) {
   void* args[] = {(void*)&a};
   count_launch();
-  if (a.fp32) return cudaLaunchCooperativeKernel((void*)k_pcg<float>, dim3(grid), dim3(threads), args, 0, st);
-  return cudaLaunchCooperativeKernel((void*)k_pcg<double>, dim3(grid), dim3(threads), args, 0, st);
+  void* f = a.fp32 ? pcg_kernel<float>(rowg) : pcg_kernel<double>(rowg);
+  return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, 0, st);
 }
 
 void launch_to_float(cudaStream_t st, size_t n, const double* src, float* dst, const int* n_dev, int stride) {

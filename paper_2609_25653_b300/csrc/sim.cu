@@ -10,6 +10,7 @@
 // energy test, and a full step snaps them onto their targets.
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -43,6 +44,7 @@ struct ipcsim {
   int nf = 0, nt = 0, nab = 0, nkb = 0, nv = 0, na_v = 0, nk = 0, n_nodes = 0, nbody = 0;
   std::vector<int> h_sv, h_tris, h_edges;
   double kappa = 0, k_c = 0, L = 0, sh = 0;
+  int n_scenes = 1;
   double grav[3] = {0, 0, 0};
   int nnzb = 0;
   std::vector<double> h_Tcur;  // (nkb, 12) current kinematic transforms
@@ -58,7 +60,7 @@ struct ipcsim {
   double *xv = nullptr, *xv_t = nullptr, *xv_trial = nullptr, *z_trial = nullptr, *xk_trial = nullptr;
   double *g = nullptr, *gdir = nullptr, *rhs = nullptr, *p = nullptr, *pD = nullptr, *pv = nullptr;
   double *Hconst = nullptr, *Hval = nullptr, *Dc = nullptr, *Dinv = nullptr;
-  double *r = nullptr, *zz = nullptr, *pp = nullptr, *y = nullptr, *partial = nullptr;
+  double *r = nullptr, *zz = nullptr, *pp = nullptr, *y = nullptr, *svec = nullptr, *partial = nullptr;
   double* T_dev = nullptr;
   // mixed precision copies
   float *val32 = nullptr, *pairH32 = nullptr, *fHu32 = nullptr, *Dinv32 = nullptr, *z32 = nullptr, *p32 = nullptr;
@@ -67,24 +69,36 @@ struct ipcsim {
   int* rec = nullptr;
   double* rec_s = nullptr;
   double* pairH = nullptr;
+  int ccap = 0;
+  int* cand = nullptr;        // contact candidates of the current Newton iteration's sweep
+  bool cand_valid = false;
   int fcap = 0, n_fric = 0;
   int* f_ids = nullptr;
   double *f_w = nullptr, *f_n = nullptr, *f_lam = nullptr, *f_Hu = nullptr;
   // scalars (device) and pinned host mirror
   struct Scal {
+    // cleared at the start of every Newton iteration
     double E[8];                 // inertia, elastic, barrier, friction, stitch, abd
     unsigned long long pn[2];    // max|p_F|, max|p_D|
-    unsigned long long alpha;    // CCD bound
-    unsigned long long min_s;
-    int n_pairs;
     int n_ccd;
     int pcg_out[3];
     int flags;
+    int pad;
     double pcg_res;
+    // set at the start of every Newton iteration
+    unsigned long long alpha;    // CCD bound
+    unsigned long long min_s;
+    // kept across iterations: sizes of the active-pair and candidate lists
+    int n_pairs;
+    int n_cand;
   };
   Scal* sc_dev = nullptr;
   Scal* sc_host = nullptr;
-  int pcg_grid_max = 1;
+  int pcg_grid_max = 1, pcg_grid_max_d = 1, pcg_grid_max_f = 1;
+  // PCG launch shape: threads per BSR row and blocks per SM (0: as many as the work needs, up to occupancy)
+  int tune_rowg = PCG_ROW_GROUP, tune_bps = 0;
+  bool autotune_pending = false;
+  float tune_ms[8] = {0};
   // optional per-stage CUDA-event timing on the simulator's stream
   bool prof = false;
   cudaEvent_t ev[2 * 8] = {};
@@ -179,6 +193,17 @@ ipc_status grow_pairs(ipcsim* sim, int need) {
   return IPC_OK;
 }
 
+ipc_status grow_cand(ipcsim* sim, int need) {
+  int ncap = std::max(need + need / 2, 4096);
+  dfree(sim, sim->cand);
+  sim->cand = nullptr;
+  ipc_status s = dalloc(sim, &sim->cand, (size_t)8 * ncap);
+  if (s) return s;
+  sim->ccap = ncap;
+  sim->cand_valid = false;
+  return IPC_OK;
+}
+
 ipc_status grow_fric(ipcsim* sim, int need) {
   int ncap = std::max(need + need / 2, 1024);
   dfree(sim, sim->f_ids); dfree(sim, sim->f_w); dfree(sim, sim->f_n); dfree(sim, sim->f_lam); dfree(sim, sim->f_Hu);
@@ -227,7 +252,24 @@ inline void prof_collect(ipcsim* sim) {
     }
 }
 
+// Cooperative PCG grid: PCG_ROW_GROUP threads per BSR row, capped by co-residency.
+int pcg_grid(const ipcsim* sim, bool fp32) {
+  int cap = fp32 ? sim->pcg_grid_max_f : sim->pcg_grid_max_d;
+  if (sim->tune_bps > 0) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, std::min(cap, sms * sim->tune_bps));
+  }
+  long long threads = (long long)sim->n_nodes * sim->tune_rowg;
+  int want = (int)std::max(1LL, (threads + PCG_THREADS - 1) / PCG_THREADS);
+  return std::max(1, std::min(cap, want));
+}
+
 int pair_grid(int cap) { return std::max(1, std::min((cap + 127) / 128, 148 * 8)); }
+
+unsigned long long double_bits(double d);
+double bits_to_double(unsigned long long b);
 
 // Cull the active set at xv into sim->rec; count into sc_dev->n_pairs.
 void cull_into(ipcsim* sim, const double* xv, int* rec, double* rec_s, int cap) {
@@ -239,6 +281,26 @@ void cull_into(ipcsim* sim, const double* xv, int* rec, double* rec_s, int cap) 
                     &sim->sc_dev->n_pairs, cap, &sim->sc_dev->flags);
 }
 void cull(ipcsim* sim, const double* xv) { cull_into(sim, xv, sim->rec, sim->rec_s, sim->cap); }
+
+// Active set at xv: from the current sweep's candidates when they cover xv, else a full cull.
+void active_set(ipcsim* sim, const double* xv) {
+  if (sim->cand_valid) {
+    cudaMemsetAsync(&sim->sc_dev->n_pairs, 0, sizeof(int), sim->st);
+    launch_filter_active(sim->st, std::max(1, std::min((sim->ccap + 127) / 128, 148 * 8)), sim->S, xv, sim->sh,
+                         sim->cand, &sim->sc_dev->n_cand, sim->ccap, sim->rec, sim->rec_s, &sim->sc_dev->n_pairs,
+                         sim->cap);
+  } else {
+    cull(sim, xv);
+  }
+}
+
+// Clear the per-iteration scalars and set the CCD bound and minimum distance to their neutral values.
+ipc_status reset_iteration_scalars(ipcsim* sim) {
+  CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, offsetof(ipcsim::Scal, alpha), sim->st));
+  unsigned long long init[2] = {double_bits(1.0), double_bits(1e300)};
+  CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, init, sizeof(init), cudaMemcpyHostToDevice, sim->st));
+  return IPC_OK;
+}
 
 void ccd(ipcsim* sim, const double* xv, const double* pv) {
   if (sim->P.broad_phase == IPC_BROAD_ALL_PAIRS)
@@ -285,7 +347,7 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
     CUDA_TRY(cudaMemsetAsync(sim->sc_dev->E, 0, sizeof(double) * 8, sim->st));
     unsigned long long big = double_bits(1e300);
     CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->min_s, &big, sizeof(big), cudaMemcpyHostToDevice, sim->st));
-    cull(sim, xvq);
+    active_set(sim, xvq);
     launch_inertia(sim->st, S, zq, sim->z_tilde, nullptr, &sim->sc_dev->E[0], 0);
     launch_elastic(sim->st, S, xvq, dt2, 0, 0, nullptr, nullptr, nullptr, &sim->sc_dev->E[1]);
     launch_barrier(sim->st, pair_grid(sim->cap), S, xvq, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
@@ -343,7 +405,11 @@ void sim_destroy(ipcsim* sim) {
   delete sim;
 }
 
-ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* stream, ipcsim** out) {
+// Build a simulator for the scene D.  For a batch, D is the concatenation of
+// n_scenes independent scenes and tet_scene / abd_scene / kin_scene give the
+// scene of every tet, ABD body and kinematic body (NULL: all scene 0).
+static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params, void* stream, ipcsim** out,
+                              int n_scenes, const int* tet_scene, const int* abd_scene, const int* kin_scene) {
   if (!out) return IPC_ERR_ARG;
   *out = nullptr;
   if (!D || !params) return IPC_ERR_ARG;
@@ -368,8 +434,10 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
   for (int d = 0; d < 3; ++d) sim->grav[d] = D->gravity[d];
 
   // ---------------- FEM preparation
+  if (n_scenes < 1) return fail(IPC_ERR_ARG, "n_scenes must be positive");
   std::vector<double> B(9 * (size_t)nt), vol(nt), mu(nt), lam(nt), mass(nf, 0.0);
   double Emax = 0.0;
+  std::vector<double> Emax_s(n_scenes, 0.0);
   for (int e = 0; e < nt; ++e) {
     const int* t = D->tets_host + 4 * e;
     for (int a = 0; a < 4; ++a)
@@ -387,6 +455,8 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
     // model parameter: first Lame parameter + mu (small-strain limit = linear material with E, nu)
     lam[e] = E * nu / ((1 + nu) * (1 - 2 * nu)) + mu[e];
     Emax = std::max(Emax, E);
+    int sc_e = tet_scene ? tet_scene[e] : 0;
+    Emax_s[sc_e] = std::max(Emax_s[sc_e], E);
     for (int a = 0; a < 4; ++a) mass[t[a]] += D->rho_host[e] * vol[e] / 4.0;
   }
   // surface faces: tet faces used once, outward (same face enumeration order for every run)
@@ -422,6 +492,9 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
     for (int a = 0; a < 4; ++a) fem_vbody[D->tets_host[4 * e + a]] = b;
   }
   if (nt == 0 && nf > 0) n_fem_bodies = 1;
+  std::vector<int> body_scene(n_fem_bodies, 0);
+  for (int e = 0; e < nt; ++e)
+    body_scene[D->fem_body_host ? D->fem_body_host[e] : 0] = tet_scene ? tet_scene[e] : 0;
   int na_v = 0, nk = 0;
   for (int i = 0; i < nab; ++i) na_v += D->abd_nverts_host[i];
   for (int i = 0; i < nkb; ++i) nk += D->kin_nverts_host[i];
@@ -445,6 +518,7 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
       int nvb = D->abd_nverts_host[i], ntb = D->abd_ntris_host[i];
       int bid = (int)bkind.size();
       bkind.push_back(VK_ABD);
+      body_scene.push_back(abd_scene ? abd_scene[i] : 0);
       const double* X = D->abd_X_host + 3 * xo;
       const int* T = D->abd_tris_host + 3 * to;
       // volume moments of the closed outward mesh: signed tets (origin, a, b, c)
@@ -486,6 +560,7 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
       int nvb = D->kin_nverts_host[i], ntb = D->kin_ntris_host[i];
       int bid = (int)bkind.size();
       bkind.push_back(VK_KIN);
+      body_scene.push_back(kin_scene ? kin_scene[i] : 0);
       for (int v = 0; v < nvb; ++v) {
         int gv = off + v;
         vkind[gv] = VK_KIN; vbody[gv] = bid;
@@ -513,8 +588,8 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
   std::sort(sv.begin(), sv.end());
   sv.erase(std::unique(sv.begin(), sv.end()), sv.end());
   std::vector<double> edge_rest_sq(ev.size());
-  double ell_sum = 0;
-  int ell_n = 0;
+  std::vector<double> ell_sum(n_scenes, 0.0), vol_ell(n_scenes, 0.0);
+  std::vector<int> ell_n(n_scenes, 0), vol_n(n_scenes, 0);
   for (size_t k = 0; k < ev.size(); ++k) {
     double s = 0;
     for (int d = 0; d < 3; ++d) {
@@ -522,39 +597,62 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
       s += q * q;
     }
     edge_rest_sq[k] = s;
-    if (ev[k].first < nf && ev[k].second < nf) { ell_sum += std::sqrt(s); ++ell_n; }
+    if (ev[k].first < nf && ev[k].second < nf) {
+      int sc_k = body_scene[vbody[ev[k].first]];
+      ell_sum[sc_k] += std::sqrt(s);
+      ++ell_n[sc_k];
+    }
   }
-  double ell = 0;
-  if (ell_n) ell = ell_sum / ell_n;
-  else if (nt) {
-    for (int e = 0; e < nt; ++e) ell += std::cbrt(vol[e]);
-    ell /= nt;
-  } else ell = P.dhat;
+  for (int e = 0; e < nt; ++e) {
+    int sc_e = tet_scene ? tet_scene[e] : 0;
+    vol_ell[sc_e] += std::cbrt(vol[e]);
+    ++vol_n[sc_e];
+  }
+  // per-scene barrier stiffness kbar / B''(dhat / 2), kbar = E_max * mean soft surface edge, and stitch stiffness
+  std::vector<double> scene_kappa(n_scenes), scene_kc(n_scenes);
+  for (int sc_i = 0; sc_i < n_scenes; ++sc_i) {
+    double ell = ell_n[sc_i] ? ell_sum[sc_i] / ell_n[sc_i] : (vol_n[sc_i] ? vol_ell[sc_i] / vol_n[sc_i] : P.dhat);
+    double Em = Emax_s[sc_i] > 0 ? Emax_s[sc_i] : 1e5;
+    scene_kappa[sc_i] = P.kappa > 0 ? P.kappa : Em * ell / barrier_dd(0.5 * P.dhat, P.dhat);
+    scene_kc[sc_i] = P.k_c > 0 ? P.k_c : 100.0 * Em * ell;
+  }
   sim->h_sv = sv; sim->h_tris = tris_all; sim->h_edges = edges;
   sim->sh = P.dhat * P.dhat;
-  if (Emax == 0) Emax = 1e5;
-  sim->kappa = P.kappa > 0 ? P.kappa : Emax * ell / barrier_dd(0.5 * P.dhat, P.dhat);
-  sim->k_c = P.k_c > 0 ? P.k_c : 100.0 * Emax * ell;
-  // L_bbox over free bodies at the initial state
+  sim->kappa = scene_kappa[0];
+  sim->k_c = scene_kc[0];
+  sim->n_scenes = n_scenes;
+  // L_bbox over the free bodies at the initial state, per scene; the Newton test uses the smallest
   {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int v = 0; v < nf; ++v)
-      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], D->fem_X_host[3 * v + d]); hi[d] = std::max(hi[d], D->fem_X_host[3 * v + d]); }
+    std::vector<double> lo(3 * n_scenes, 1e300), hi(3 * n_scenes, -1e300);
+    for (int v = 0; v < nf; ++v) {
+      int sc_v = body_scene[vbody[v]];
+      for (int d = 0; d < 3; ++d) {
+        lo[3 * sc_v + d] = std::min(lo[3 * sc_v + d], D->fem_X_host[3 * v + d]);
+        hi[3 * sc_v + d] = std::max(hi[3 * sc_v + d], D->fem_X_host[3 * v + d]);
+      }
+    }
     int off = nf;
     for (int i = 0; i < nab; ++i) {
       const double* q = D->abd_q0_host + 12 * i;
+      int sc_v = abd_scene ? abd_scene[i] : 0;
       for (int v = 0; v < D->abd_nverts_host[i]; ++v) {
         const double* xb = &xbar[3 * (off + v)];
         for (int d = 0; d < 3; ++d) {
           double x = q[d] + q[3 + d] * xb[0] + q[6 + d] * xb[1] + q[9 + d] * xb[2];
-          lo[d] = std::min(lo[d], x); hi[d] = std::max(hi[d], x);
+          lo[3 * sc_v + d] = std::min(lo[3 * sc_v + d], x);
+          hi[3 * sc_v + d] = std::max(hi[3 * sc_v + d], x);
         }
       }
       off += D->abd_nverts_host[i];
     }
-    double s = 0;
-    for (int d = 0; d < 3; ++d) s += (hi[d] - lo[d]) * (hi[d] - lo[d]);
-    sim->L = std::sqrt(s);
+    sim->L = 0;
+    for (int sc_i = 0; sc_i < n_scenes; ++sc_i) {
+      if (lo[3 * sc_i] > hi[3 * sc_i]) continue;
+      double s2 = 0;
+      for (int d = 0; d < 3; ++d) s2 += (hi[3 * sc_i + d] - lo[3 * sc_i + d]) * (hi[3 * sc_i + d] - lo[3 * sc_i + d]);
+      double Ls = std::sqrt(s2);
+      sim->L = sim->L > 0 ? std::min(sim->L, Ls) : Ls;
+    }
   }
 
   // ---------------- BSR pattern: diagonal, tet couplings, ABD 4x4 grids
@@ -606,7 +704,7 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
     int v = D->stitch_v_host[k];
     if (v < 0 || v >= nf || D->stitch_b_host[k] < 0 || D->stitch_b_host[k] >= nkb)
       return fail(IPC_ERR_ARG, "stitch index out of range");
-    for (int d = 0; d < 3; ++d) Hc[9 * (size_t)diag[v] + 4 * d] += P.dt * P.dt * sim->k_c;
+    for (int d = 0; d < 3; ++d) Hc[9 * (size_t)diag[v] + 4 * d] += P.dt * P.dt * scene_kc[body_scene[vbody[v]]];
   }
 
   // ---------------- upload
@@ -656,6 +754,10 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
     if ((s = upload(sim, &ip, col))) return fail(s, ""); S.bsr_col = ip;
     if ((s = upload(sim, &ip, diag))) return fail(s, ""); S.bsr_diag = ip;
     if ((s = upload(sim, &sim->Hconst, Hc))) return fail(s, "");
+    if ((s = upload(sim, &ip, body_scene))) return fail(s, ""); S.body_scene = ip;
+    if ((s = upload(sim, &dp, scene_kappa))) return fail(s, ""); S.scene_kappa = dp;
+    if ((s = upload(sim, &dp, scene_kc))) return fail(s, ""); S.scene_kc = dp;
+    S.n_scenes = n_scenes;
   }
   // state
   const int ndof = 3 * n_nodes;
@@ -679,7 +781,7 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
     if ((s = upload(sim, &sim->xk, xk))) return fail(s, "");
   }
   double** bufs3n[] = {&sim->z_t, &sim->z_tilde, &sim->z_trial, &sim->g, &sim->gdir, &sim->rhs, &sim->p,
-                       &sim->r, &sim->zz, &sim->pp, &sim->y};
+                       &sim->r, &sim->zz, &sim->pp, &sim->y, &sim->svec};
   for (auto b : bufs3n)
     if ((s = dalloc(sim, b, ndof))) return fail(s, "");
   double** bufsk[] = {&sim->xk_t, &sim->xk_hat, &sim->xk_trial, &sim->pD};
@@ -694,19 +796,22 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
   if ((s = dalloc(sim, &sim->Dinv, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->T_dev, 12 * (size_t)std::max(nkb, 1)))) return fail(s, "");
   if (P.precision != IPC_PREC_FP64 && P.precision != IPC_PREC_MIXED) return fail(IPC_ERR_ARG, "unknown precision");
-  sim->pcg_grid_max = std::min(pcg_max_blocks(PCG_THREADS), pcg_max_blocks_fp32(PCG_THREADS));
+  sim->pcg_grid_max_d = pcg_max_blocks(PCG_THREADS);
+  sim->pcg_grid_max_f = pcg_max_blocks_fp32(PCG_THREADS);
+  sim->pcg_grid_max = std::max(sim->pcg_grid_max_d, sim->pcg_grid_max_f);  // sizes the partial-sum buffer
   if (P.precision == IPC_PREC_MIXED) {
     if ((s = dalloc(sim, &sim->val32, 9 * (size_t)nnzb))) return fail(s, "");
     if ((s = dalloc(sim, &sim->Dinv32, 9 * (size_t)n_nodes))) return fail(s, "");
     if ((s = dalloc(sim, &sim->z32, (size_t)ndof))) return fail(s, "");
     if ((s = dalloc(sim, &sim->p32, (size_t)ndof))) return fail(s, "");
   }
-  if ((s = dalloc(sim, &sim->partial, 3 * (size_t)sim->pcg_grid_max))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->partial, 5 * (size_t)sim->pcg_grid_max))) return fail(s, "");
   if ((s = dalloc(sim, &sim->sc_dev, 1))) return fail(s, "");
   if (cudaMallocHost((void**)&sim->sc_host, sizeof(ipcsim::Scal)) != cudaSuccess) return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
   std::memset(sim->sc_host, 0, sizeof(ipcsim::Scal));
   int cap0 = P.pair_capacity > 0 ? P.pair_capacity : std::max(1024, 2 * (S.nsv + S.nedge));
   if ((s = grow_pairs(sim, cap0 * 2 / 3 + 1))) return fail(s, "");
+  if ((s = grow_cand(sim, 4 * cap0))) return fail(s, "");
   if ((s = grow_fric(sim, cap0 * 2 / 3 + 1))) return fail(s, "");
   if (cudaMemcpyAsync(sim->T_dev, sim->h_Tcur.data(), sizeof(double) * 12 * nkb, cudaMemcpyHostToDevice, sim->st) != cudaSuccess && nkb)
     return fail(IPC_ERR_CUDA, "upload of transforms failed");
@@ -737,6 +842,105 @@ ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* s
   }
   *out = sim;
   return IPC_OK;
+}
+
+ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* stream, ipcsim** out) {
+  return create_impl(D, params, stream, out, 1, nullptr, nullptr, nullptr);
+}
+
+ipc_status sim_create_batch(const ipc_scene_desc* descs, int n, const ipc_params* params, void* stream, ipcsim** out) {
+  if (!out) return IPC_ERR_ARG;
+  *out = nullptr;
+  if (!descs || n <= 0 || !params) return IPC_ERR_ARG;
+  std::vector<double> fX, fV0, logE, nu, rho, aX, arho, aq0, kX, kT0, stX;
+  std::vector<int> tets, fbody, anv, antri, atris, knv, kntri, ktris, stv, stb, tet_scene, abd_scene, kin_scene;
+  bool any_v0 = false;
+  for (int k = 0; k < n; ++k) any_v0 |= descs[k].fem_V0_host != nullptr;
+  int voff = 0, boff = 0, koff = 0;
+  for (int k = 0; k < n; ++k) {
+    const ipc_scene_desc& D = descs[k];
+    if (D.n_fem_verts < 0 || D.n_tets < 0 || D.n_abd < 0 || D.n_kin < 0 || D.n_stitch < 0) return IPC_ERR_ARG;
+    fX.insert(fX.end(), D.fem_X_host, D.fem_X_host + 3 * D.n_fem_verts);
+    if (any_v0) {
+      if (D.fem_V0_host) fV0.insert(fV0.end(), D.fem_V0_host, D.fem_V0_host + 3 * D.n_fem_verts);
+      else fV0.insert(fV0.end(), 3 * (size_t)D.n_fem_verts, 0.0);
+    }
+    int nb = 0;
+    for (int e = 0; e < D.n_tets; ++e) {
+      for (int a = 0; a < 4; ++a) tets.push_back(D.tets_host[4 * e + a] + voff);
+      int b = D.fem_body_host ? D.fem_body_host[e] : 0;
+      fbody.push_back(b + boff);
+      nb = std::max(nb, b + 1);
+      tet_scene.push_back(k);
+    }
+    logE.insert(logE.end(), D.logE_host, D.logE_host + D.n_tets);
+    nu.insert(nu.end(), D.nu_host, D.nu_host + D.n_tets);
+    rho.insert(rho.end(), D.rho_host, D.rho_host + D.n_tets);
+    int av = 0, at = 0;
+    for (int i = 0; i < D.n_abd; ++i) {
+      anv.push_back(D.abd_nverts_host[i]);
+      antri.push_back(D.abd_ntris_host[i]);
+      av += D.abd_nverts_host[i];
+      at += D.abd_ntris_host[i];
+      abd_scene.push_back(k);
+    }
+    if (D.n_abd) {
+      aX.insert(aX.end(), D.abd_X_host, D.abd_X_host + 3 * av);
+      atris.insert(atris.end(), D.abd_tris_host, D.abd_tris_host + 3 * at);
+      arho.insert(arho.end(), D.abd_rho_host, D.abd_rho_host + D.n_abd);
+      aq0.insert(aq0.end(), D.abd_q0_host, D.abd_q0_host + 12 * D.n_abd);
+    }
+    int kv = 0, kt = 0;
+    for (int i = 0; i < D.n_kin; ++i) {
+      knv.push_back(D.kin_nverts_host[i]);
+      kntri.push_back(D.kin_ntris_host[i]);
+      kv += D.kin_nverts_host[i];
+      kt += D.kin_ntris_host[i];
+      kin_scene.push_back(k);
+    }
+    if (D.n_kin) {
+      kX.insert(kX.end(), D.kin_X_host, D.kin_X_host + 3 * kv);
+      ktris.insert(ktris.end(), D.kin_tris_host, D.kin_tris_host + 3 * kt);
+      kT0.insert(kT0.end(), D.kin_T0_host, D.kin_T0_host + 12 * D.n_kin);
+    }
+    for (int i = 0; i < D.n_stitch; ++i) {
+      stv.push_back(D.stitch_v_host[i] + voff);
+      stb.push_back(D.stitch_b_host[i] + koff);
+    }
+    if (D.n_stitch) stX.insert(stX.end(), D.stitch_X_host, D.stitch_X_host + 3 * D.n_stitch);
+    voff += D.n_fem_verts;
+    boff += (D.n_tets || D.n_fem_verts) ? std::max(nb, 1) : 0;
+    koff += D.n_kin;
+  }
+  ipc_scene_desc M{};
+  M.n_fem_verts = voff;
+  M.fem_X_host = fX.data();
+  M.fem_V0_host = any_v0 ? fV0.data() : nullptr;
+  M.n_tets = (int)tet_scene.size();
+  M.tets_host = tets.data();
+  M.logE_host = logE.data();
+  M.nu_host = nu.data();
+  M.rho_host = rho.data();
+  M.fem_body_host = fbody.data();
+  M.n_abd = (int)abd_scene.size();
+  M.abd_nverts_host = anv.data();
+  M.abd_X_host = aX.data();
+  M.abd_ntris_host = antri.data();
+  M.abd_tris_host = atris.data();
+  M.abd_rho_host = arho.data();
+  M.abd_q0_host = aq0.data();
+  M.n_kin = (int)kin_scene.size();
+  M.kin_nverts_host = knv.data();
+  M.kin_X_host = kX.data();
+  M.kin_ntris_host = kntri.data();
+  M.kin_tris_host = ktris.data();
+  M.kin_T0_host = kT0.data();
+  M.n_stitch = (int)stv.size();
+  M.stitch_v_host = stv.data();
+  M.stitch_b_host = stb.data();
+  M.stitch_X_host = stX.data();
+  for (int d = 0; d < 3; ++d) M.gravity[d] = descs[0].gravity[d];
+  return create_impl(&M, params, stream, out, n, tet_scene.data(), abd_scene.data(), kin_scene.data());
 }
 
 ipc_status sim_sizes(const ipcsim* sim, int* o) {
@@ -781,6 +985,9 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   rebuild_trees(sim, sim->xv);
   CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
   ipc_status s = IPC_OK;
+  sim->cand_valid = false;
+  bool rec_current = false;  // sim->rec holds the active set at the current iterate
+  const bool sweep = P.broad_phase != IPC_BROAD_ALL_PAIRS;
   // friction lag on the pairs active at x_t
   sim->n_fric = 0;
   if (P.mu > 0) {
@@ -795,6 +1002,7 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     launch_friction_lag(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
                         sim->kappa, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam);
     sim->n_fric = n;
+    rec_current = true;
   }
   st.n_friction_pairs = sim->n_fric;
   const double tol_abs = P.newton_tol * dt * sim->L;
@@ -817,18 +1025,17 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   };
   while (it < P.max_newton) {
     // ---- assemble gradient, Hessian and Dirichlet coupling at the current iterate
-    CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
-    unsigned long long one = double_bits(1.0), big = double_bits(1e300);
-    CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, &one, sizeof(one), cudaMemcpyHostToDevice, cs));
-    CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->min_s, &big, sizeof(big), cudaMemcpyHostToDevice, cs));
+    if ((s = reset_iteration_scalars(sim))) return s;
     CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
     CUDA_TRY(cudaMemsetAsync(sim->gdir, 0, sizeof(double) * ndof, cs));
     CUDA_TRY(cudaMemsetAsync(sim->Dc, 0, sizeof(double) * 9 * sim->n_nodes, cs));
     launch_vertex_positions(cs, S, sim->z, sim->xk, sim->xv);
     launch_sub(cs, nk3, sim->xk_hat, sim->xk, sim->pD);
-    prof_begin(sim, PROF_CULL);
-    cull(sim, sim->xv);
-    prof_end(sim, PROF_CULL);
+    if (!rec_current) {
+      prof_begin(sim, PROF_CULL);
+      cull(sim, sim->xv);
+      prof_end(sim, PROF_CULL);
+    }
     launch_inertia(cs, S, sim->z, sim->z_tilde, sim->g, &sim->sc_dev->E[0], 1);
     prof_begin(sim, PROF_ELASTIC);
     launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
@@ -853,6 +1060,7 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     a.rec = sim->rec; a.n_pairs = &sim->sc_dev->n_pairs; a.cap = sim->cap; a.pairH = sim->pairH;
     a.n_fric = P.mu > 0 ? sim->n_fric : 0; a.f_ids = sim->f_ids; a.f_w = sim->f_w; a.f_Hu = sim->f_Hu;
     a.Dinv = sim->Dinv; a.b = sim->rhs; a.x = sim->p; a.r = sim->r; a.z = sim->zz; a.p = sim->pp; a.y = sim->y;
+    a.s = sim->svec;
     a.partial = sim->partial; a.rtol = P.pcg_rtol; a.max_iter = max_pcg;
     a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
     if (P.precision == IPC_PREC_MIXED) {
@@ -864,16 +1072,53 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
       if (a.n_fric) launch_to_float(cs, 9 * (size_t)a.n_fric, sim->f_Hu, sim->fHu32);
       launch_to_float(cs, 9 * (size_t)sim->n_nodes, sim->Dinv, sim->Dinv32);
     }
-    int work = std::max(sim->n_nodes, sim->cap / 4);
-    int grid = std::max(1, std::min(sim->pcg_grid_max, (work + PCG_THREADS - 1) / PCG_THREADS));
+    if (sim->autotune_pending) {
+      // time every launch shape on this system (same right-hand side, same tolerance) and keep the fastest
+      const int rowgs[4] = {2, 4, 8, 16};
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      int best_r = sim->tune_rowg, best_b = sim->tune_bps;
+      for (int bi = 0; bi < 2; ++bi)
+        for (int ri = 0; ri < 4; ++ri) {
+          sim->tune_rowg = rowgs[ri];
+          sim->tune_bps = bi + 1;
+          int g = pcg_grid(sim, P.precision == IPC_PREC_MIXED);
+          float ms = 0.f;
+          for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, cs);
+            CUDA_TRY(launch_pcg(cs, g, PCG_THREADS, a, sim->tune_rowg));
+            cudaEventRecord(e1, cs);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+          }
+          sim->tune_ms[4 * bi + ri] = ms;
+          if (ms < best) { best = ms; best_r = sim->tune_rowg; best_b = sim->tune_bps; }
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      sim->tune_rowg = best_r;
+      sim->tune_bps = best_b;
+      sim->autotune_pending = false;
+    }
+    int grid = pcg_grid(sim, P.precision == IPC_PREC_MIXED);
     prof_begin(sim, PROF_PCG);
-    CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a));
+    CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a, sim->tune_rowg));
     prof_end(sim, PROF_PCG);
     // ---- direction norms and CCD bound
     launch_pnorm(cs, ndof, sim->p, nk3, sim->pD, sim->sc_dev->pn);
     launch_vertex_disp(cs, S, sim->p, sim->pD, sim->pv);
     prof_begin(sim, PROF_CCD);
-    ccd(sim, sim->xv, sim->pv);
+    if (sweep) {
+      // one traversal: the CCD bound and the candidates of the line search and the next iterate
+      CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->n_cand, 0, sizeof(int), cs));
+      launch_sweep_bvh(cs, S, sim->xv, sim->pv, sim->bvh_pad, P.s_ccd, ACCD_MAX_ITER, sim->tri_tree, sim->edge_tree,
+                       sim->cand, &sim->sc_dev->n_cand, sim->ccap, &sim->sc_dev->alpha, &sim->sc_dev->n_ccd,
+                       &sim->sc_dev->flags);
+    } else {
+      ccd(sim, sim->xv, sim->pv);
+    }
     prof_end(sim, PROF_CCD);
     if ((s = sync_scalars(sim))) return s;
     CUDA_TRY(cudaGetLastError());
@@ -881,8 +1126,14 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     if (h.flags & ERRF_BVH) return finish(IPC_ERR_BVH_OVERFLOW, "BVH traversal stack overflow");
     if (h.n_pairs > sim->cap) {
       if ((s = grow_pairs(sim, h.n_pairs))) return finish(s, "pair buffer growth failed");
+      rec_current = false;
       continue;
     }
+    if (sweep && h.n_cand > sim->ccap) {
+      if ((s = grow_cand(sim, h.n_cand))) return finish(s, "candidate buffer growth failed");
+      continue;
+    }
+    sim->cand_valid = sweep;
     ++it;
     st.newton_iters = it;
     st.pcg_iters_total += h.pcg_out[0];
@@ -923,12 +1174,17 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
       }
       st.ls_halvings += halv;
       if (stationary) { converged = true; break; }
+      rec_current = true;  // the accepted trial is the last one evaluated
     } else {
       launch_trial(cs, ndof, nk3, sim->z, sim->p, alpha, sim->z_trial, sim->xk, sim->pD, sim->xk_hat, sim->xk_trial);
+      launch_vertex_positions(cs, S, sim->z_trial, sim->xk_trial, sim->xv_trial);
+      active_set(sim, sim->xv_trial);
+      rec_current = true;
     }
     st.alpha_min = std::min(st.alpha_min, alpha);
     std::swap(sim->z, sim->z_trial);
     std::swap(sim->xk, sim->xk_trial);
+    sim->cand_valid = false;
   }
   if (!converged) return finish(IPC_ERR_NEWTON_MAXIT, "Newton did not converge");
   launch_velocity(cs, ndof, sim->z, sim->z_t, 1.0 / dt, sim->zd);
@@ -1066,10 +1322,11 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   a.rec = sim->rec; a.n_pairs = &sim->sc_dev->n_pairs; a.cap = sim->cap; a.pairH = sim->pairH;
   a.n_fric = P.mu > 0 ? sim->n_fric : 0; a.f_ids = sim->f_ids; a.f_w = sim->f_w; a.f_Hu = sim->f_Hu;
   a.Dinv = sim->Dinv; a.b = sim->rhs; a.x = sim->p; a.r = sim->r; a.z = sim->zz; a.p = sim->pp; a.y = sim->y;
+  a.s = sim->svec;
   a.partial = sim->partial; a.rtol = 1e-12; a.max_iter = 10 * ndof + 1000;
   a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
-  int grid = std::max(1, std::min(sim->pcg_grid_max, (std::max(sim->n_nodes, sim->cap / 4) + PCG_THREADS - 1) / PCG_THREADS));
-  CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a));
+  int grid = pcg_grid(sim, false);
+  CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a, sim->tune_rowg));
   // contractions with lam (= sim->p)
   if (glogE) launch_theta_grad(cs, S, sim->xv, sim->p, dt2, glogE);
   double* tmp = sim->y;  // scratch: friction gradient, then M lam
@@ -1087,6 +1344,19 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   CUDA_TRY(cudaGetLastError());
   if (sim->sc_host->pcg_out[1]) { sim->err = "adjoint PCG breakdown (Hessian not positive definite)"; return IPC_ERR_PCG; }
   if (gmu_host && P.mu > 0) *gmu_host += -sim->sc_host->E[6] / P.mu;
+  return IPC_OK;
+}
+
+ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out2, float* ms8) {
+  if (!sim) return IPC_ERR_ARG;
+  if (rowg > 0) {
+    if (rowg != 2 && rowg != 4 && rowg != 8 && rowg != 16) { sim->err = "rowg must be 2, 4, 8 or 16"; return IPC_ERR_ARG; }
+    sim->tune_rowg = rowg;
+  }
+  if (blocks_per_sm >= 0) sim->tune_bps = std::min(blocks_per_sm, 2);
+  if (autotune_next_step) sim->autotune_pending = true;
+  if (out2) { out2[0] = sim->tune_rowg; out2[1] = sim->tune_bps; }
+  if (ms8) std::memcpy(ms8, sim->tune_ms, sizeof(sim->tune_ms));
   return IPC_OK;
 }
 

@@ -62,6 +62,7 @@ _lib = None
 # every exported symbol of the C ABI and its (argtypes, restype)
 SIGNATURES = {
     "sim_create": ([C.POINTER(SceneDesc), C.POINTER(Params), vp, C.POINTER(vp)], C.c_int),
+    "sim_create_batch": ([C.POINTER(SceneDesc), C.c_int, C.POINTER(Params), vp, C.POINTER(vp)], C.c_int),
     "sim_step": ([vp, dp, C.POINTER(StepStats)], C.c_int),
     "sim_get_state": ([vp, vp, vp, vp, vp, C.c_int], C.c_int),
     "sim_set_state": ([vp, vp, vp, vp, vp, C.c_int], C.c_int),
@@ -78,6 +79,7 @@ SIGNATURES = {
     "sim_profile": ([vp, C.c_int], C.c_int),
     "sim_set_params": ([vp, dp, C.c_double], C.c_int),
     "sim_set_kinematic": ([vp, dp], C.c_int),
+    "sim_tuning": ([vp, C.c_int, C.c_int, C.c_int, ip, C.POINTER(C.c_float)], C.c_int),
     "sim_eval_barrier_noalloc": ([vp, vp, C.c_int, vp, C.c_int, vp, vp, vp], C.c_int),
     "sim_step_many": ([C.POINTER(vp), C.c_int, C.POINTER(dp), C.POINTER(StepStats), ip], C.c_int),
     "sim_adjoint": ([vp, vp, vp, vp, dp, dp, vp, vp, vp, vp, vp, dp], C.c_int),
@@ -136,67 +138,87 @@ def make_params(p: dict, precision=PREC_FP64) -> Params:
                   broad_phase=int(p.get("broad_phase", BROAD_LBVH)))
 
 
+def _fill_desc(d, scene, keep):
+    """Fill one SceneDesc from a scene dictionary (the arrays are kept alive in `keep`)."""
+    def arr_d(a):
+        a = _f64(a)
+        keep.append(a)
+        return a.ctypes.data_as(dp)
+
+    def arr_i(a):
+        a = _i32(a)
+        keep.append(a)
+        return a.ctypes.data_as(ip)
+
+    X = _f64(scene["fem_X"])
+    d.n_fem_verts = X.shape[0]
+    d.fem_X_host = arr_d(X)
+    d.fem_V0_host = arr_d(scene["fem_V0"]) if "fem_V0" in scene else None
+    d.n_tets = len(scene["fem_tets"])
+    d.tets_host = arr_i(scene["fem_tets"])
+    d.logE_host = arr_d(scene["fem_logE"])
+    d.nu_host = arr_d(scene["fem_nu"])
+    d.rho_host = arr_d(scene["fem_rho"])
+    d.fem_body_host = arr_i(scene["fem_body"]) if "fem_body" in scene else None
+    abd = scene.get("abd", [])
+    d.n_abd = len(abd)
+    if abd:
+        d.abd_nverts_host = arr_i([a["X"].shape[0] for a in abd])
+        d.abd_X_host = arr_d(np.concatenate([a["X"] for a in abd]))
+        d.abd_ntris_host = arr_i([len(a["tris"]) for a in abd])
+        d.abd_tris_host = arr_i(np.concatenate([a["tris"] for a in abd]))
+        d.abd_rho_host = arr_d([a["rho"] for a in abd])
+        d.abd_q0_host = arr_d(np.stack([a["q0"] for a in abd]))
+    kin = scene.get("kin", [])
+    d.n_kin = len(kin)
+    if kin:
+        d.kin_nverts_host = arr_i([k["X"].shape[0] for k in kin])
+        d.kin_X_host = arr_d(np.concatenate([k["X"] for k in kin]))
+        d.kin_ntris_host = arr_i([len(k["tris"]) for k in kin])
+        d.kin_tris_host = arr_i(np.concatenate([k["tris"] for k in kin]))
+        d.kin_T0_host = arr_d(scene["kin_T"][0].reshape(-1, 12))
+    sv = scene.get("stitch_v", np.zeros(0, np.int32))
+    d.n_stitch = len(sv)
+    if len(sv):
+        d.stitch_v_host = arr_i(sv)
+        d.stitch_b_host = arr_i(scene["stitch_b"])
+        d.stitch_X_host = arr_d(scene["stitch_X"])
+    for k in range(3):
+        d.gravity[k] = float(scene["gravity"][k])
+
+
+def batch_scene(scenes):
+    """Bookkeeping view of a batch (concatenated kinematic trajectories, first scene's parameters)."""
+    n_steps = min(sc["kin_T"].shape[0] for sc in scenes)
+    kin_T = np.concatenate([sc["kin_T"][:n_steps] for sc in scenes], axis=1)
+    return dict(name=f"batch_{len(scenes)}", params=dict(scenes[0]["params"]), kin_T=kin_T,
+                kin=[k for sc in scenes for k in sc.get("kin", [])], abd=[a for sc in scenes for a in sc.get("abd", [])],
+                fem_X=np.concatenate([sc["fem_X"] for sc in scenes]),
+                fem_tets=np.zeros((sum(len(sc["fem_tets"]) for sc in scenes), 4), np.int32),
+                gravity=scenes[0]["gravity"])
+
+
 class Simulator:
     """One scene on the GPU.  `scene` is a dictionary from paper_2609_25653_b300.scenes."""
 
-    def __init__(self, scene: dict, precision=PREC_FP64, stream=None, **param_overrides):
+    def __init__(self, scene: dict, precision=PREC_FP64, stream=None, _batch=None, **param_overrides):
         L = load()
         self.scene = scene
         p = dict(scene["params"])
         p.update(param_overrides)
         self.params = p
         keep = []
-
-        def arr_d(a):
-            a = _f64(a)
-            keep.append(a)
-            return a.ctypes.data_as(dp)
-
-        def arr_i(a):
-            a = _i32(a)
-            keep.append(a)
-            return a.ctypes.data_as(ip)
-
-        d = SceneDesc()
-        X = _f64(scene["fem_X"])
-        d.n_fem_verts = X.shape[0]
-        d.fem_X_host = arr_d(X)
-        d.fem_V0_host = arr_d(scene["fem_V0"]) if "fem_V0" in scene else None
-        d.n_tets = len(scene["fem_tets"])
-        d.tets_host = arr_i(scene["fem_tets"])
-        d.logE_host = arr_d(scene["fem_logE"])
-        d.nu_host = arr_d(scene["fem_nu"])
-        d.rho_host = arr_d(scene["fem_rho"])
-        d.fem_body_host = arr_i(scene["fem_body"]) if "fem_body" in scene else None
-        abd = scene.get("abd", [])
-        d.n_abd = len(abd)
-        if abd:
-            d.abd_nverts_host = arr_i([a["X"].shape[0] for a in abd])
-            d.abd_X_host = arr_d(np.concatenate([a["X"] for a in abd]))
-            d.abd_ntris_host = arr_i([len(a["tris"]) for a in abd])
-            d.abd_tris_host = arr_i(np.concatenate([a["tris"] for a in abd]))
-            d.abd_rho_host = arr_d([a["rho"] for a in abd])
-            d.abd_q0_host = arr_d(np.stack([a["q0"] for a in abd]))
-        kin = scene.get("kin", [])
-        d.n_kin = len(kin)
-        if kin:
-            d.kin_nverts_host = arr_i([k["X"].shape[0] for k in kin])
-            d.kin_X_host = arr_d(np.concatenate([k["X"] for k in kin]))
-            d.kin_ntris_host = arr_i([len(k["tris"]) for k in kin])
-            d.kin_tris_host = arr_i(np.concatenate([k["tris"] for k in kin]))
-            d.kin_T0_host = arr_d(scene["kin_T"][0].reshape(-1, 12))
-        sv = scene.get("stitch_v", np.zeros(0, np.int32))
-        d.n_stitch = len(sv)
-        if len(sv):
-            d.stitch_v_host = arr_i(sv)
-            d.stitch_b_host = arr_i(scene["stitch_b"])
-            d.stitch_X_host = arr_d(scene["stitch_X"])
-        for k in range(3):
-            d.gravity[k] = float(scene["gravity"][k])
+        scenes = _batch if _batch is not None else [scene]
+        descs = (SceneDesc * len(scenes))()
+        for i, sc in enumerate(scenes):
+            _fill_desc(descs[i], sc, keep)
         par = make_params(p, precision)
         h = C.c_void_p()
         st = C.c_void_p(stream.cuda_stream if stream is not None else 0)
-        code = L.sim_create(C.byref(d), C.byref(par), st, C.byref(h))
+        if _batch is None:
+            code = L.sim_create(C.byref(descs[0]), C.byref(par), st, C.byref(h))
+        else:
+            code = L.sim_create_batch(descs, len(scenes), C.byref(par), st, C.byref(h))
         if code != IPC_OK:
             raise IpcError(code, L.sim_last_error(None).decode())
         self.h = h
@@ -204,10 +226,17 @@ class Simulator:
         sz = (C.c_int * 9)()
         L.sim_sizes(h, sz)
         (self.nf, self.nt, self.nab, self.nkb, self.ntri, self.nedge, self.nsv, self.n_nodes, self.nnzb) = list(sz)
-        self.nv = self.nf + sum(a["X"].shape[0] for a in abd) + sum(k["X"].shape[0] for k in kin)
+        self.nv = self.nf + sum(a["X"].shape[0] for sc in scenes for a in sc.get("abd", [])) + \
+            sum(k["X"].shape[0] for sc in scenes for k in sc.get("kin", []))
+        self.n_scenes = len(scenes)
         sc = (C.c_double * 4)()
         L.sim_scalars(h, sc)
         self.kappa, self.k_c, self.L, self.dhat = list(sc)
+
+    @classmethod
+    def batch(cls, scenes, precision=PREC_FP64, stream=None, **param_overrides):
+        """One simulator advancing independent scenes together (sim_create_batch)."""
+        return cls(batch_scene(scenes), precision=precision, stream=stream, _batch=list(scenes), **param_overrides)
 
     def close(self):
         if getattr(self, "h", None):
@@ -309,6 +338,13 @@ class Simulator:
                                        _ptr(gz_next.contiguous()), _ptr(gzd_next.contiguous()), _ptr(gz_t), _ptr(gzd_t),
                                        _ptr(glogE), C.byref(gmu)))
         return gz_t, gzd_t, glogE, gmu.value
+
+    def tuning(self, rowg=0, blocks_per_sm=-1, autotune_next_step=False):
+        """Set / read the PCG launch shape; returns ((rowg, blocks_per_sm), last autotuning times in ms)."""
+        out = (C.c_int * 2)()
+        ms = (C.c_float * 8)()
+        self._check(load().sim_tuning(self.h, int(rowg), int(blocks_per_sm), int(bool(autotune_next_step)), out, ms))
+        return (out[0], out[1]), list(ms)
 
     def profile(self, enable=True):
         self._check(load().sim_profile(self.h, int(enable)))

@@ -570,3 +570,80 @@ def stitched_block(n_steps: int = 6, **param_overrides) -> dict:
         gravity=np.array([0.0, 0.0, -9.81]),
         params=params,
     )
+
+
+def ellipsoid_or_box_object(rng: SplitMix64, tris_lo=1000, tris_hi=8000, size_lo=20e-3, size_hi=60e-3):
+    """Seeded rigid object: an ellipsoid or a box (probability 1/2 each), 1k-8k triangles, 20-60 mm."""
+    u = rng.uniform(5)
+    ntris = int(tris_lo + (tris_hi - tris_lo) * u[0])
+    dims = size_lo + (size_hi - size_lo) * np.sort(u[1:4])[::-1]
+    if u[4] < 0.5:
+        n_lon = max(8, int(round(math.sqrt(ntris * 1.6 / 2))))
+        n_lat = max(4, int(round(ntris / (2 * n_lon))) + 1)
+        X, T = uv_ellipsoid(0.5 * dims[0], 0.5 * dims[1], 0.5 * dims[2], n_lat, n_lon)
+        vol = math.pi / 6 * dims[0] * dims[1] * dims[2]
+    else:
+        n = max(2, int(round(math.sqrt(ntris / 12))))
+        X, T = subdivided_box(-0.5 * dims, 0.5 * dims, n)
+        vol = float(dims[0] * dims[1] * dims[2])
+    return X, T, vol, dims
+
+
+def translate_scene(sc: dict, offset) -> dict:
+    """The same scene moved rigidly by `offset` (FEM rest/initial positions, ABD poses, kinematic transforms)."""
+    off = np.asarray(offset, dtype=np.float64)
+    sc = dict(sc)
+    sc["fem_X"] = sc["fem_X"] + off
+    sc["abd"] = [dict(a, q0=np.concatenate([a["q0"][:3] + off, a["q0"][3:]])) for a in sc.get("abd", [])]
+    kin_T = sc["kin_T"].copy()
+    kin_T[..., 3] += off
+    sc["kin_T"] = kin_T
+    return sc
+
+
+def batched_grasps(n_scenes: int = 64, seed0: int = 0, n_steps: int = 200, tets_lo=5000, tets_hi=40000,
+                   spacing: float = 1.2) -> list:
+    """Independent grasp scenes for batched data generation.
+
+    Scene k (seed seed0 + k): two fin-ray fingertips with a tet count drawn
+    log-uniformly in [tets_lo, tets_hi] (the voxel size is chosen to match),
+    a seeded rigid object (ellipsoid or box, 1k-8k triangles, 20-60 mm, ABD,
+    0.1 kg), a random approach pose (yaw in [0, 2 pi), offset +/- 10 mm), and
+    the close-and-lift trajectory of the single-scene grasp; no arm links.
+    FP32-PCG / FP64-barrier configuration, dt = 5 ms.  Scene k is translated
+    to grid cell (k mod 8, k div 8) with `spacing` metres between cells; a
+    rigid translation leaves each scene's motion unchanged."""
+    mm = 1e-3
+    out = []
+    base_tets = 47472 / 2  # one tip at 1.25 mm cells
+    for k in range(n_scenes):
+        rng = SplitMix64(seed0 + 1000 + k)
+        u = rng.uniform(4)
+        tets = math.exp(math.log(tets_lo) + (math.log(tets_hi) - math.log(tets_lo)) * u[0])
+        cell = 1.25e-3 * (base_tets / tets) ** (1.0 / 3.0)
+        sc = arm_gripper_grasp(seed0 + k, n_steps=n_steps, tip_cell=cell, link_tris=8, obj_tris=1000)
+        # replace the object and drop the arm links
+        oX, oT, vol, dims = ellipsoid_or_box_object(rng)
+        half_h = 0.5 * float(oX[:, 2].max() - oX[:, 2].min())
+        yaw = 2 * math.pi * u[1]
+        R = rot_z(yaw)
+        off = (2 * u[2:4] - 1) * 10 * mm
+        q0 = np.concatenate([[off[0], off[1], half_h + 0.3 * mm], R[:, 0], R[:, 1], R[:, 2]])
+        sc["abd"] = [dict(X=oX, tris=oT, rho=0.1 / vol, q0=q0)]
+        # keep ground and finger bases (bodies 0..2); arm links are not part of the batched scenes
+        sc["kin"] = sc["kin"][:3]
+        sc["kin_T"] = sc["kin_T"][:, :3].copy()
+        # open the fingers so that they clear the object: the object's half width along y
+        half_w = 0.5 * float((oX @ R.T)[:, 1].max() - (oX @ R.T)[:, 1].min()) + abs(off[1])
+        shift = max(0.0, half_w + 0.8 * mm - 25.8 * mm)
+        X = sc["fem_X"].copy()
+        X[:, 1] += np.sign(X[:, 1]) * shift
+        sc["fem_X"] = X
+        sc["stitch_X"] = sc["stitch_X"].copy()
+        for s in range(sc["kin_T"].shape[0]):
+            sc["kin_T"][s, 1, 1, 3] += shift
+            sc["kin_T"][s, 2, 1, 3] -= shift
+        sc["name"] = f"batched_grasp_{k}_{len(sc['fem_tets'])}tet"
+        # scenes sit on an 8-wide grid, `spacing` apart, so that their ground quads do not overlap
+        out.append(translate_scene(sc, ((k % 8) * spacing, (k // 8) * spacing, 0.0)) if spacing else sc)
+    return out

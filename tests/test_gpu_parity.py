@@ -287,3 +287,58 @@ def test_mixed_precision_within_1e5():
         assert np.max(np.abs(xa - xb)) / L < 1e-5
         assert np.max(np.abs(xb - o.x()[:o.S.nf])) / L < 1e-5
         assert sb["status"] == 0 and sb["min_dist"] > 0
+
+
+def test_step_many_matches_single_scene_steps():
+    """Concurrent stepping of independent scenes (one stream and host thread each) gives each scene's own result."""
+    from paper_2609_25653_b300 import ipcsim
+    scs = [scenes.fingertip_press(s, n_steps=4, **PARITY) for s in (0, 1, 2)] + [scenes.abd_box_drop(n_steps=4, **PARITY)]
+    streams = [torch.cuda.Stream() for _ in scs]
+    many = [_sim(sc, stream=st) for sc, st in zip(scs, streams)]
+    single = [_sim(sc) for sc in scs]
+    for k in range(4):
+        stats = ipcsim.step_many(many)
+        assert all(s["status"] == 0 for s in stats)
+        for sim in single:
+            sim.step()
+        for a, b in zip(many, single):
+            xa, _, qa, _ = a.get_state()
+            xb, _, qb, _ = b.get_state()
+            assert np.max(np.abs(xa - xb)) <= 1e-9 * b.L
+            if a.nab:
+                assert np.max(np.abs(qa - qb)) <= 1e-9
+
+
+def test_batch_matches_individual_scenes():
+    """Independent scenes concatenated into one simulator give each scene's own trajectory."""
+    from paper_2609_25653_b300 import ipcsim
+    scs = [scenes.fingertip_press(s, n_steps=4, **PARITY) for s in (0, 1, 2)]
+    batch = ipcsim.Simulator.batch(scs)
+    single = [_sim(sc) for sc in scs]
+    assert batch.n_scenes == 3 and batch.nf == sum(s.nf for s in single)
+    for k in range(4):
+        st = batch.step()
+        assert st["status"] == 0 and st["min_dist"] > 0
+        xb = batch.get_state()[0]
+        off = 0
+        for sim in single:
+            sim.step()
+            xs = sim.get_state()[0]
+            assert np.max(np.abs(xb[off:off + sim.nf] - xs)) <= 1e-8 * sim.L
+            off += sim.nf
+
+
+@pytest.mark.parametrize("name", ["fingertip_press", "abd_box_drop"])
+def test_sweep_candidates_match_all_pairs_steps(name):
+    """Whole steps with the LBVH sweep (candidates filtered along the line search) equal all-pairs culling."""
+    from paper_2609_25653_b300 import ipcsim
+    sc = getattr(scenes, name)(n_steps=5, **PARITY) if name != "fingertip_press" else scenes.fingertip_press(0, n_steps=5, **PARITY)
+    a = _sim(sc)
+    b = _sim(sc, broad_phase=ipcsim.BROAD_ALL_PAIRS)
+    for k in range(5):
+        sa = a.step()
+        sb = b.step()
+        assert sa["status"] == 0 and sb["status"] == 0
+        xa, _, qa, _ = a.get_state()
+        xb, _, qb, _ = b.get_state()
+        assert np.max(np.abs(xa - xb)) <= 1e-8 * a.L
