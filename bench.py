@@ -47,6 +47,9 @@ def make_workload(name):
         return scenes.fingertip_press(0, n_steps=60)
     if name == "arm_gripper":
         return scenes.arm_gripper_grasp(0)
+    if name == "soft_cylinder":
+        # fingertips squeeze a deformable 63k-tet cylinder; the timed steps sit in the contact-rich squeeze
+        return scenes.soft_gripper_cylinder(0, n_steps=300, close_per_step=0.25e-3)
     if name.startswith("batched"):
         # "batched" = 64 scenes, "batched16" = 16 scenes, ...
         n = int(name[len("batched"):] or 64)
@@ -120,18 +123,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def pcg_bytes(work, sim):
-    """Algorithmic bytes the PCG kernel moves, summed over the recorded iterations.
+def pcg_bytes(work, sim, fp32, resident, launches):
+    """Algorithmic bytes the PCG kernel has to move, summed over the recorded launches.
 
-    Per iteration: every BSR block (72 B values + 4 B column index), the row
-    pointers, and per node the vectors p (read twice: gather + update), y, x,
-    r, z (read and written where updated) and the 3x3 inverse diagonal block;
-    per barrier pair its 12x12 FP64 block (1152 B) and record (32 B); per
-    friction pair its 3x3 block, weights, ids and normal (136 B)."""
-    n_nodes = sim.n_nodes
-    per_iter_fixed = work["bsr_blocks"] * (72 + 4) + (n_nodes + 1) * 4 + n_nodes * (24 * 11 + 72)
-    return (work["pcg_iters"] * per_iter_fixed + work["pcg_pair_iters"] * (1152 + 32)
-            + work["pcg_fric_iters"] * (72 + 32 + 16 + 24))
+    Per iteration and node: the seven node-local iteration vectors (z, q, s, p,
+    r, u, w) read and written, m read and the next m written, and x (FP64)
+    read and written: 48 elements of the iteration type + 48 B.  The operator
+    (9 elements + 4 B column index per BSR block) and the 3x3 preconditioner
+    blocks (9 elements per node) once per iteration when they stream from
+    memory, once per launch when every CTA keeps its rows in shared memory.
+    Per barrier pair and iteration its 144-element block and 32 B record; per
+    friction pair its 9-element block, ids and weights (48 B)."""
+    e = 4 if fp32 else 8
+    n = sim.n_nodes
+    nodes = n * (48 * e + 48)
+    op = work["bsr_blocks"] * (9 * e + 4) + 9 * n * e
+    per_iter = nodes + (0 if resident else op)
+    return (work["pcg_iters"] * per_iter + (launches * op if resident else 0)
+            + work["pcg_pair_iters"] * (144 * e + 32) + work["pcg_fric_iters"] * (9 * e + 48))
 
 
 def run_ours(args):
@@ -221,12 +230,14 @@ def run_ours(args):
     dom = max(prof, key=lambda k: prof[k]["ms"])
     pcg = prof["pcg"]
     pcg_avg_ms = pcg["ms"] / max(pcg["n"], 1)
-    pcg_bytes_per_launch = pcg_bytes(work, sim) / max(pcg["n"], 1)
+    pcg_grid, pcg_resident = sim.pcg_layout()
+    pcg_bytes_per_launch = pcg_bytes(work, sim, prec == ipcsim.PREC_MIXED, pcg_resident, pcg["n"]) / max(pcg["n"], 1)
     achieved = pcg_bytes_per_launch / (pcg_avg_ms / 1e3) / 1e9 if pcg["n"] else 0.0
     roofline = {"kernel": "k_pcg", "bound": "hbm", "achieved": round(achieved, 2),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 5),
                 "traffic": None, "peak_source": peak_src,
                 "launch_ms": round(pcg_avg_ms, 5), "algorithmic_bytes_per_launch": int(pcg_bytes_per_launch),
+                "pcg_ctas": pcg_grid, "operator_in_shared_memory": pcg_resident,
                 "dominant_stage": dom,
                 "stage_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["n"]}}
     cpu = None

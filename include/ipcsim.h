@@ -213,21 +213,24 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t_dev, const double* zd_t_de
                        const double* gzd_next_dev, double* gz_t_dev, double* gzd_t_dev, double* glogE_dev,
                        double* gmu_host);
 
-/* Launch shape of the cooperative PCG: threads per BSR row in the SpMV
- * (rowg = 2, 4, 8 or 16; <= 0 keeps the current value) and blocks per SM
- * (1 or 2; 0 = as many as the rows need, up to occupancy; < 0 keeps).  With
+/* Launch shape of the cooperative PCG: threads per FEM row (rowg = 1, 2, 4
+ * or 8; <= 0 keeps the current value) and CTAs per SM (1 to 4; <= 0 keeps;
+ * fewer are launched when the kernel cannot keep that many resident).  With
  * autotune_next_step != 0 the next sim_step times every shape (2 x 4) on its
- * first linear system and keeps the fastest.  out2 (may be NULL) receives
- * the shape in use [rowg, blocks_per_sm]; ms8 (may be NULL) the last
- * autotuning times in ms, index 4 * (blocks_per_sm - 1) + log2(rowg) - 1. */
-ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out2, float* ms8);
+ * first linear system and keeps the fastest.  out4 (may be NULL) receives
+ * [rowg, blocks_per_sm, CTAs of the last PCG launch (0 before the first),
+ * 1 if that launch kept its operator rows in shared memory]; ms8 (may be
+ * NULL) the last autotuning times in ms, index 4 * (blocks_per_sm - 1) +
+ * log2(rowg). */
+ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out4, float* ms8);
 
 /* Per-stage timing with CUDA events recorded on the simulator's stream
  * around each stage of sim_step (cheap; intervals are read at the
  * synchronisation points sim_step already has).  enable != 0 starts (and
  * clears) accounting; sim_profile_read returns accumulated milliseconds and
  * interval counts per stage [PCG, elastic, barrier, culling, CCD, friction,
- * other, unused] and work4 = [PCG iterations, sum over iterations of barrier
+ * other, PCG setup (incidence lists, FP32 copies, operator layout)] and work4
+ * = [PCG iterations, sum over iterations of barrier
  * pairs, of friction pairs, BSR blocks]. */
 ipc_status sim_profile(ipcsim* sim, int enable);
 ipc_status sim_profile_read(const ipcsim* sim, double* ms8, long long* n8, long long* work4);

@@ -124,6 +124,7 @@ __device__ inline NodeMap vertex_nodes(const DevScene& S, int v) {
 }
 
 // error flag bits written by kernels
-enum : int { ERRF_BVH = 1, ERRF_PCG_BREAK = 2, ERRF_NAN = 4, ERRF_PAIR_OVF = 8, ERRF_FRIC_OVF = 16 };
+enum : int { ERRF_BVH = 1, ERRF_PCG_BREAK = 2, ERRF_NAN = 4, ERRF_PAIR_OVF = 8, ERRF_FRIC_OVF = 16, ERRF_INC = 32,
+             ERRF_ABD = 64 };
 
 }  // namespace ipc

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
   double e_acc = 0.0, smin = 1e300;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     {
-      const int* r = rec + 8 * k;
+      const int* r = rec + 8 * (size_t)k;
       int kind = r[0], type = r[3];
       int ids[4];
       d3 x[4];
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
   double e_acc = 0.0, smin = 1e300;
   int gw = blockIdx.x * BWARPS + wid, nw = gridDim.x * BWARPS;
   for (int k = gw; k < n; k += nw) {
-    const int* r = rec + 8 * k;
+    const int* r = rec + 8 * (size_t)k;
     int kind = r[0], type = r[3];
     const double kappa = S.scene_kappa[scene_of_vertex(S, r[4])];
     if (lane == 0) {
@@ -548,7 +548,7 @@ __global__ void k_friction_lag(DevScene S, const double* __restrict__ xv, const 
                                double* __restrict__ f_w, double* __restrict__ f_n, double* __restrict__ f_lam) {
   int n = min(*n_dev, cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int* r = rec + 8 * k;
+    const int* r = rec + 8 * (size_t)k;
     int kind = r[0];
     int ids[4];
     d3 x[4];

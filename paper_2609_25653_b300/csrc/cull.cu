@@ -29,11 +29,15 @@ __device__ inline bool excluded(const DevScene& S, const int* va, int na, const 
   return false;
 }
 
+// counters stop near 2^30 so that they never wrap; the host reports the overflow
+constexpr int COUNT_CEILING = 1 << 30;
+
 __device__ inline void emit(int* rec, double* rec_s, int* count, int cap, int kind, int a, int b, int type,
                             const int* ids, double s) {
+  if (*(volatile int*)count >= COUNT_CEILING) return;
   int slot = atomicAdd(count, 1);
   if (slot < cap) {
-    int* r = rec + 8 * slot;
+    int* r = rec + 8 * (size_t)slot;
     r[0] = kind; r[1] = a; r[2] = b; r[3] = type;
     r[4] = ids[0]; r[5] = ids[1]; r[6] = ids[2]; r[7] = ids[3];
     if (rec_s) rec_s[slot] = s;
@@ -318,9 +322,10 @@ __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const do
 // Candidates whose unwidened swept boxes overlap also get the ACCD time of
 // impact, which reproduces the CCD of the plain sweep.
 __device__ inline void emit_cand(int* cand, int* n_cand, int ccap, int kind, int a, int b, const int* ids) {
+  if (*(volatile int*)n_cand >= COUNT_CEILING) return;
   int slot = atomicAdd(n_cand, 1);
   if (slot < ccap) {
-    int* r = cand + 8 * slot;
+    int* r = cand + 8 * (size_t)slot;
     r[0] = kind; r[1] = a; r[2] = b; r[3] = -1;
     r[4] = ids[0]; r[5] = ids[1]; r[6] = ids[2]; r[7] = ids[3];
   }
@@ -399,7 +404,7 @@ __global__ void k_filter_active(DevScene S, const double* __restrict__ xv, doubl
                                 const int* __restrict__ n_cand, int ccap, int* rec, double* rec_s, int* count, int cap) {
   int n = min(*n_cand, ccap);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    const int* r = cand + 8 * c;
+    const int* r = cand + 8 * (size_t)c;
     int kind = r[0];
     int ids[4] = {r[4], r[5], r[6], r[7]};
     d3 x[4] = {ld3(xv, ids[0]), ld3(xv, ids[1]), ld3(xv, ids[2]), ld3(xv, ids[3])};

@@ -1,5 +1,6 @@
 // Host-side launchers of the ipcsim kernels (declarations).
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 #include "bvh.cuh"
 #include "common.cuh"
@@ -10,45 +11,59 @@ namespace ipc {
 extern unsigned long long g_kernel_launches;
 inline void count_launch(int n = 1) { __atomic_fetch_add(&g_kernel_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
 
+// Arguments of one PCG solve (see pcg.cu).  CTAs [0, n_fem_ctas) own the FEM
+// rows seg_row[c] .. seg_row[c + 1]; the others own ABD bodies
+// b = cta - n_fem_ctas (mod n_abd_ctas).  Pointers of the operator type
+// (double, or float when fp32) are passed as void*.
 struct PcgArgs {
   DevScene S;
   int n_nodes;
+  int n_fem_ctas, n_abd_ctas;
+  const int* seg_row;        // (n_fem_ctas + 1)
+  int resident;              // stage each FEM CTA's operator rows in shared memory
   const int* row;
   const int* col;
-  const double* val;
+  const void* op;            // BSR values in the CTA-major plane layout, operator type
+  const void* dinv;          // (n_nodes, 9) preconditioner blocks, operator type
+  const double* val64;       // BSR values as assembled (FP64), for the true residual
+  const void* pairH;         // (cap, 144) barrier pair blocks, operator type
+  const void* fHu;           // (n_fric, 9) friction blocks, operator type
+  const double* pairH64;
+  const double* fHu64;
   const int* rec;
-  const int* n_pairs;
+  const int* n_pairs;        // device count of active pairs
   int cap;
-  const double* pairH;
   int n_fric;
   const int* f_ids;
   const double* f_w;
-  const double* f_Hu;
-  const double* Dinv;
+  const int* inc_ptr;        // (nf + nab + 1) contact incidences per owner
+  const int2* inc;           // (code, owner) ordered by owner; code = pair << 3 | friction << 2 | slot
+  int max_rows;              // most FEM rows of one CTA (sizes the shared contact sums)
+  const int* abd_ptr;        // (nab + 1) contact coupling blocks per ABD body
+  const int* abd_ent;        // column node << 2 | pseudo-node row
+  const double* abd_val;     // (entries, 9)
+  long long abd_cap;
   const double* b;
   double* x;
-  double* r;
-  double* z;
-  double* p;
-  double* y;
-  double* s;        // Chronopoulos-Gear auxiliary direction (A p)
-  double* partial;  // 5 * grid doubles
+  void* vec;                 // nine FP64 vectors of 3 n_nodes values
+  double* t64;               // 3 n_nodes FP64 scratch (true residual)
+  void* partial;             // pcg_partial_doubles(grid) doubles
   double rtol;
   int max_iter;
-  int* out;         // [iterations, status, FP64 residual replacements]
-  double* res;      // [relative residual]
-  // mixed precision: FP32 copies of the operator and preconditioner, FP32
-  // search direction and preconditioned residual; x, r, y and all dot
-  // products stay FP64, and the residual is replaced by b - A x with the FP64
-  // operator when the FP32 iteration has converged.
   int fp32;
-  const float* val32;
-  const float* pairH32;
-  const float* f_Hu32;
-  const float* Dinv32;
-  float* z32;
-  float* p32;
+  int* out;                  // [iterations, status, true-residual restarts]
+  double* res;               // [relative residual]
+  long long inc_cap;         // entries of inc
+  int* check;                // non-null: validate every gathered index, record the first bad site here, skip it
 };
+
+// Row partition of one PCG launch shape.
+struct PcgPlan {
+  int grid = 0, n_fem_ctas = 0, n_abd_ctas = 0;
+  std::vector<int> seg;      // FEM CTA row boundaries, then nf + 4 b for every ABD body
+  int max_rows = 0, max_blocks = 0;
+};
+
 
 // fem.cu
 void launch_predict(cudaStream_t, const DevScene&, const double* z, const double* zd, double dt, const double* g,
@@ -114,11 +129,25 @@ void launch_axpy(cudaStream_t, int n, const double* x, double alpha, const doubl
 // pcg.cu
 void launch_dinv(cudaStream_t, int n_nodes, const int* diag, const double* val, const double* Dc, double* Dinv);
 void launch_rhs(cudaStream_t, int n, const double* g, const double* gdir, double* rhs);
-int pcg_max_blocks(int threads);
-constexpr int PCG_ROW_GROUP = 4;  // default threads per BSR row in the PCG's SpMV
-// rowg: threads per BSR row in the SpMV (2, 4, 8 or 16)
-cudaError_t launch_pcg(cudaStream_t, int grid, int threads, const PcgArgs& a, int rowg = 4);
-int pcg_max_blocks_fp32(int threads);
+constexpr int PCG_ROW_GROUP = 4;  // default threads per FEM row in the PCG
+constexpr int PCG_REPLICA_COUNT = 8;
+inline size_t pcg_partial_doubles(int grid) { return (size_t)PCG_REPLICA_COUNT * 7 * grid; }
+// co-resident CTAs of the PCG kernel for this shape (rowg: threads per FEM row, 1, 2, 4 or 8)
+int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem);
+size_t pcg_smem_limit();
+void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, PcgPlan& P);
+// dynamic shared memory of a PCG CTA: contact sums of its rows, plus the operator rows when resident
+size_t pcg_contact_bytes(const PcgPlan& P);
+size_t pcg_resident_bytes(const PcgPlan& P, int fp32);
+cudaError_t launch_pcg(cudaStream_t, int grid, int threads, const PcgArgs& a, int rowg, size_t dyn_smem);
+void launch_layout(cudaStream_t, int n_seg, const int* seg, const int* row, const double* src, void* dst, int fp32);
+void launch_incidence(cudaStream_t, const DevScene& S, const int* rec, const int* n_pairs, int cap, int n_fric,
+                      const int* f_ids, const double* f_w, int* inc_ptr, int* cursor, int* tiles, int2* inc,
+                      long long inc_cap, int* err);
+void launch_abd_contact(cudaStream_t, const DevScene& S, const int* rec, const int* n_pairs, int cap,
+                        const double* pairH, int n_fric, const int* f_ids, const double* f_w, const double* f_Hu,
+                        int* abd_ptr, int* cursor, int* ent, double* entv, long long ent_cap, double* Hval,
+                        double* Dc, int* err);
 void launch_to_float(cudaStream_t, size_t n, const double* src, float* dst, const int* n_dev = nullptr, int stride = 0);
 
 // conservative-advancement iterations per CCD candidate

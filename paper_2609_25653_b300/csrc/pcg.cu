@@ -1,14 +1,27 @@
 // Block-Jacobi preconditioned conjugate gradients for H_FF p = rhs.
 //
 // H_FF is the sum of (1) the fixed-pattern BSR 3x3 matrix (inertia, elastic,
-// stitch, ABD blocks), (2) the dense 12x12 vertex-space block of every active
+// stitch, ABD blocks), (2) the 12x12 vertex-space block of every active
 // barrier pair and (3) the rank-structured block (w w^T) (x) Hu of every
-// lagged friction pair, mapped to nodes by x = J z.  The whole solve is one
-// cooperative kernel: three grid-wide barriers per iteration, dot products
-// reduced per block and summed in block order by every block, so all blocks
-// take identical control decisions.
+// lagged friction pair, mapped to nodes by x = J z.
+//
+// The whole solve is one cooperative kernel built around three choices:
+//  * owner computes: each node row of A v is formed by one group of threads
+//    (a FEM node) or one CTA (the four pseudo-nodes of an ABD body).  Contact
+//    pairs reach their rows through per-owner incidence lists, so no atomics
+//    are needed and a row is complete inside the phase that forms it;
+//  * the pipelined recurrences of Ghysels and Vanroose (2014): the matrix
+//    product of iteration i does not depend on the dot products of iteration
+//    i, so an iteration costs one grid-wide barrier;
+//  * when they fit, every CTA keeps its rows of the operator and of the
+//    preconditioner in shared memory for the whole solve.
+// Dot products are reduced per CTA; every CTA writes its partial sums to R
+// replicas and sums one replica in a fixed order, so all CTAs take identical
+// control decisions without contending for one cache line.
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <type_traits>
+#include <vector>
 #include "common.cuh"
 #include "kernels.h"
 
@@ -43,417 +56,875 @@ __global__ void k_rhs(int n, const double* __restrict__ g, const double* __restr
   if (i < n) rhs[i] = -(g[i] + gdir[i]);
 }
 
-__device__ inline double grid_total(const double* part, int nblk) {
-  double v = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += part[b];
-  __shared__ double tot;
-  v = block_sum(v);
-  if (threadIdx.x == 0) tot = v;
-  __syncthreads();
-  double r = tot;
-  __syncthreads();
-  return r;
-}
+// ---------------------------------------------------------------------------
+// contact incidence lists: for every FEM node the (pair, slot) entries whose
+// rows land on it.  code = pair << 3 | friction << 2 | slot.  The rows of ABD
+// pseudo-nodes take their contact part from the block lists below instead.
+// ---------------------------------------------------------------------------
+__device__ inline int owner_of(const DevScene& S, int v) { return S.vkind[v] == VK_FEM ? v : -1; }
 
-__device__ inline d3 node_gather(const DevScene& S, const double* p, int v) {
-  NodeMap m = vertex_nodes(S, v);
-  d3 u = mk(0, 0, 0);
-  for (int r = 0; r < m.n; ++r) u = u + m.w[r] * ld3(p, m.node[r]);
-  return u;
-}
-__device__ inline void node_scatter(const DevScene& S, double* y, int v, d3 w) {
-  NodeMap m = vertex_nodes(S, v);
-  for (int r = 0; r < m.n; ++r) {
-    atomicAdd(y + 3 * m.node[r], m.w[r] * w.x);
-    atomicAdd(y + 3 * m.node[r] + 1, m.w[r] * w.y);
-    atomicAdd(y + 3 * m.node[r] + 2, m.w[r] * w.z);
-  }
-}
-
-// y += A p for the whole operator (matrix values of type M, vector p of type V,
-// products and row sums in M); returns this thread's share of p^T A p in FP64.
-template <typename M, typename V>
-__device__ inline double apply_A(const PcgArgs& a, const M* val, const M* pairH, const M* fHu, const V* p, double* y,
-                                 int tid, int nthr) {
-  const DevScene& S = a.S;
-  double acc = 0.0;
-  for (int i = tid; i < a.n_nodes; i += nthr) {
-    M s0 = M(0), s1 = M(0), s2 = M(0);
-    for (int k = a.row[i]; k < a.row[i + 1]; ++k) {
-      const M* A = val + 9 * (size_t)k;
-      int j = a.col[k];
-      M p0 = (M)p[3 * j], p1 = (M)p[3 * j + 1], p2 = (M)p[3 * j + 2];
-      s0 += A[0] * p0 + A[1] * p1 + A[2] * p2;
-      s1 += A[3] * p0 + A[4] * p1 + A[5] * p2;
-      s2 += A[6] * p0 + A[7] * p1 + A[8] * p2;
+template <bool FILL>
+__global__ void k_incidence(DevScene S, const int* __restrict__ rec, const int* __restrict__ n_pairs, int cap,
+                            int n_fric, const int* __restrict__ f_ids, const double* __restrict__ f_w,
+                            int* __restrict__ cnt_or_cursor, int2* __restrict__ inc, long long inc_cap,
+                            int* __restrict__ err) {
+  const int np = min(*n_pairs, cap);
+  const long long tot = 4LL * (np + n_fric);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int k = (int)(e >> 2), q = (int)(e & 3), v, code;
+    if (k < np) {
+      v = rec[8 * k + 4 + q];
+      code = (k << 3) | q;
+    } else {
+      k -= np;
+      if (f_w[4 * k + q] == 0.0) continue;
+      v = f_ids[4 * k + q];
+      code = (k << 3) | 4 | q;
     }
-    atomicAdd(y + 3 * i, (double)s0);
-    atomicAdd(y + 3 * i + 1, (double)s1);
-    atomicAdd(y + 3 * i + 2, (double)s2);
-    acc += (double)p[3 * i] * (double)s0 + (double)p[3 * i + 1] * (double)s1 + (double)p[3 * i + 2] * (double)s2;
+    int o = owner_of(S, v);
+    if (o < 0) continue;
+    int slot = atomicAdd(cnt_or_cursor + o, 1);
+    if (FILL) {
+      if (slot >= 0 && slot < inc_cap) inc[slot] = make_int2(code, o);
+      else atomicOr(err, ERRF_INC);
+    }
   }
-  int np = min(*a.n_pairs, a.cap);
-  for (int k = tid; k < np; k += nthr) {
-    const int* r = a.rec + 8 * k;
-    const M* H = pairH + 144 * (size_t)k;
-    M u[12];
-    bool kin[4];
-    for (int q = 0; q < 4; ++q) {
-      int v = r[4 + q];
-      kin[q] = S.vkind[v] == VK_KIN;
-      NodeMap m = vertex_nodes(S, v);
-      M ux = M(0), uy = M(0), uz = M(0);
-      if (!kin[q])
-        for (int t = 0; t < m.n; ++t) {
-          M w = (M)m.w[t];
-          ux += w * (M)p[3 * m.node[t]];
-          uy += w * (M)p[3 * m.node[t] + 1];
-          uz += w * (M)p[3 * m.node[t] + 2];
+}
+
+// exclusive scan in place: tiles of 4096, then the tile totals, then the carries
+constexpr int SCAN_TILE = 4096;
+__device__ inline int block_exclusive_scan_1024(int v, int* warp_tot, int& total) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = warp_tot[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  int incl = x + (w > 0 ? warp_tot[w - 1] : 0);
+  total = warp_tot[31];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(int n, int* __restrict__ a, int* __restrict__ tiles) {
+  __shared__ int warp_tot[32];
+  int base = blockIdx.x * SCAN_TILE + 4 * threadIdx.x;
+  int v[4], s = 0;
+  for (int j = 0; j < 4; ++j) {
+    v[j] = base + j < n ? a[base + j] : 0;
+    s += v[j];
+  }
+  int total;
+  int ex = block_exclusive_scan_1024(s, warp_tot, total);
+  for (int j = 0; j < 4; ++j) {
+    if (base + j < n) a[base + j] = ex;
+    ex += v[j];
+  }
+  if (threadIdx.x == 0) tiles[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_totals(int m, int* __restrict__ t) {
+  __shared__ int warp_tot[32];
+  int carry = 0;
+  for (int base = 0; base < m; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < m ? t[i] : 0, total;
+    int ex = block_exclusive_scan_1024(v, warp_tot, total);
+    if (i < m) t[i] = ex + carry;
+    carry += total;
+  }
+}
+
+__global__ void k_scan_add(int n, int* __restrict__ a, const int* __restrict__ tiles) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += tiles[i / SCAN_TILE];
+}
+
+void launch_incidence(cudaStream_t st, const DevScene& S, const int* rec, const int* n_pairs, int cap, int n_fric,
+                      const int* f_ids, const double* f_w, int* inc_ptr, int* cursor, int* tiles, int2* inc,
+                      long long inc_cap, int* err) {
+  const int n_own = S.nf + S.nab;
+  const int n = n_own + 1;
+  cudaMemsetAsync(inc_ptr, 0, sizeof(int) * n, st);
+  int grid = std::max(1, std::min((4 * (cap + n_fric) + 255) / 256, 148 * 8));
+  k_incidence<false><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, inc_ptr, nullptr, 0, err);
+  int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<ntiles, 1024, 0, st>>>(n, inc_ptr, tiles);
+  k_scan_totals<<<1, 1024, 0, st>>>(ntiles, tiles);
+  k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(n, inc_ptr, tiles);
+  cudaMemcpyAsync(cursor, inc_ptr, sizeof(int) * n_own, cudaMemcpyDeviceToDevice, st);
+  k_incidence<true><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, cursor, inc, inc_cap, err);
+  for (int k = 0; k < 5; ++k) count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// ABD bodies in contact.  For each pair, the part of J^T H J that couples the
+// pseudo-nodes of one body with themselves is added into that body's 4x4 BSR
+// grid, and the part that couples them with any other node becomes a list of
+// 3x3 blocks per body (entry code = column node << 2 | pseudo-node row t), so
+// that the ABD rows of the PCG need one gather per block.  Once per Newton
+// iteration, after the pair Hessians and before the preconditioner.
+// ---------------------------------------------------------------------------
+struct PairSlots {
+  int n;          // slots (4)
+  int kind[4];    // VK_FEM / VK_ABD / VK_KIN, or -1 for a zero-weight friction slot
+  int node[4];    // FEM node, or first pseudo-node of the ABD body
+  int body[4];    // ABD body or -1
+  double w[4][4]; // pseudo-node weights (1, xbar) of ABD slots
+};
+
+__device__ inline void pair_slots(const DevScene& S, const int* ids, const double* fw, PairSlots& P) {
+  P.n = 4;
+  for (int q = 0; q < 4; ++q) {
+    const int v = ids[q];
+    P.body[q] = -1;
+    P.node[q] = -1;
+    if (fw && fw[q] == 0.0) { P.kind[q] = -1; continue; }
+    const int k = S.vkind[v];
+    P.kind[q] = k;
+    if (k == VK_FEM) {
+      P.node[q] = v;
+    } else if (k == VK_ABD) {
+      const int b = S.vabd[v];
+      P.body[q] = b;
+      P.node[q] = S.nf + 4 * b;
+      P.w[q][0] = 1.0;
+      P.w[q][1] = S.xbar[3 * v];
+      P.w[q][2] = S.xbar[3 * v + 1];
+      P.w[q][3] = S.xbar[3 * v + 2];
+    }
+  }
+}
+
+// 3x3 block (q, j) of a pair: rows 3q.., columns 3j.. of its 12x12 (barrier) or w_q w_j Hu (friction)
+__device__ inline void pair_block(const double* H, const double* fw, const double* Hu, int q, int j, double B[9]) {
+  if (H) {
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) B[3 * r + c] = H[(3 * q + r) * 12 + 3 * j + c];
+  } else {
+    const double ww = fw[q] * fw[j];
+    for (int i = 0; i < 9; ++i) B[i] = ww * Hu[i];
+  }
+}
+
+template <bool FILL>
+__global__ void k_abd_contact(DevScene S, const int* __restrict__ rec, const int* __restrict__ n_pairs, int cap,
+                              const double* __restrict__ pairH, int n_fric, const int* __restrict__ f_ids,
+                              const double* __restrict__ f_w, const double* __restrict__ f_Hu,
+                              int* __restrict__ cnt_or_cursor, int* __restrict__ ent, double* __restrict__ entv,
+                              long long ent_cap, double* __restrict__ Hval, int* __restrict__ err) {
+  const int np = min(*n_pairs, cap);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np + n_fric; e += gridDim.x * blockDim.x) {
+    const bool fric = e >= np;
+    const int k = fric ? e - np : e;
+    const int* ids = fric ? f_ids + 4 * (size_t)k : rec + 8 * (size_t)k + 4;
+    const double* fw = fric ? f_w + 4 * (size_t)k : nullptr;
+    const double* H = fric ? nullptr : pairH + 144 * (size_t)k;
+    const double* Hu = fric ? f_Hu + 9 * (size_t)k : nullptr;
+    PairSlots P;
+    pair_slots(S, ids, fw, P);
+    for (int q0 = 0; q0 < 4; ++q0) {
+      const int b = P.body[q0];
+      if (b < 0) continue;
+      bool first = true;
+      for (int q = 0; q < q0; ++q) first = first && P.body[q] != b;
+      if (!first) continue;  // body b handled at its first slot
+      // columns of the list: FEM slots (one node each) and other ABD bodies (four pseudo-nodes each)
+      int count = 0;
+      for (int j = 0; j < 4; ++j) {
+        if (P.kind[j] == VK_FEM) count += 4;
+        if (P.kind[j] == VK_ABD && P.body[j] != b) {
+          bool fb = true;
+          for (int jj = 0; jj < j; ++jj) fb = fb && P.body[jj] != P.body[j];
+          if (fb) count += 16;
         }
-      u[3 * q] = ux; u[3 * q + 1] = uy; u[3 * q + 2] = uz;
-    }
-    for (int q = 0; q < 4; ++q) {
-      if (kin[q]) continue;
-      M w0 = M(0), w1 = M(0), w2 = M(0);
-      const M* H0 = H + 12 * (3 * q);
-      for (int j = 0; j < 12; ++j) {
-        w0 += H0[j] * u[j];
-        w1 += H0[12 + j] * u[j];
-        w2 += H0[24 + j] * u[j];
       }
-      node_scatter(S, y, r[4 + q], mk((double)w0, (double)w1, (double)w2));
-      acc += (double)u[3 * q] * (double)w0 + (double)u[3 * q + 1] * (double)w1 + (double)u[3 * q + 2] * (double)w2;
-    }
-  }
-  for (int k = tid; k < a.n_fric; k += nthr) {
-    const int* ids = a.f_ids + 4 * k;
-    const double* w = a.f_w + 4 * k;
-    const M* Hu = fHu + 9 * k;
-    M U0 = M(0), U1 = M(0), U2 = M(0);
-    bool kin[4];
-    for (int q = 0; q < 4; ++q) {
-      kin[q] = S.vkind[ids[q]] == VK_KIN;
-      if (kin[q] || w[q] == 0.0) continue;
-      NodeMap m = vertex_nodes(S, ids[q]);
-      for (int t = 0; t < m.n; ++t) {
-        M ww = (M)(w[q] * m.w[t]);
-        U0 += ww * (M)p[3 * m.node[t]];
-        U1 += ww * (M)p[3 * m.node[t] + 1];
-        U2 += ww * (M)p[3 * m.node[t] + 2];
-      }
-    }
-    M t0 = Hu[0] * U0 + Hu[1] * U1 + Hu[2] * U2, t1 = Hu[3] * U0 + Hu[4] * U1 + Hu[5] * U2,
-      t2 = Hu[6] * U0 + Hu[7] * U1 + Hu[8] * U2;
-    d3 t = mk((double)t0, (double)t1, (double)t2);
-    for (int q = 0; q < 4; ++q)
-      if (!kin[q] && w[q] != 0.0) node_scatter(S, y, ids[q], w[q] * t);
-    acc += (double)U0 * t.x + (double)U1 * t.y + (double)U2 * t.z;
-  }
-  return acc;
-}
-
-// z = Dinv r for node i (Dinv of type M, z stored as V); returns r.z and r.r shares
-template <typename M, typename V>
-__device__ inline void precond_node(const M* Dinv, const double* r, V* z, int i, double& rz, double& rr) {
-  const M* D = Dinv + 9 * i;
-  M r0 = (M)r[3 * i], r1 = (M)r[3 * i + 1], r2 = (M)r[3 * i + 2];
-  M z0 = D[0] * r0 + D[1] * r1 + D[2] * r2, z1 = D[3] * r0 + D[4] * r1 + D[5] * r2, z2 = D[6] * r0 + D[7] * r1 + D[8] * r2;
-  z[3 * i] = (V)z0; z[3 * i + 1] = (V)z1; z[3 * i + 2] = (V)z2;
-  rz += r[3 * i] * (double)z[3 * i] + r[3 * i + 1] * (double)z[3 * i + 1] + r[3 * i + 2] * (double)z[3 * i + 2];
-  rr += r[3 * i] * r[3 * i] + r[3 * i + 1] * r[3 * i + 1] + r[3 * i + 2] * r[3 * i + 2];
-}
-
-// w += A u over the BSR rows, ROWG threads per row (row blocks strided among
-// them, partial sums combined by shuffles); returns this thread's share of
-// u^T (A_bsr u).  Every thread of the grid must call it (whole warps shuffle).
-template <typename M, typename V, int ROWG>
-__device__ inline double spmv_bsr(const PcgArgs& a, const M* val, const V* u, double* w, int tid, int nthr) {
-  double acc = 0.0;
-  int gl = threadIdx.x & (ROWG - 1);
-  int group = tid / ROWG, ngroups = nthr / ROWG;
-  int n_pad = ((a.n_nodes + ngroups - 1) / ngroups) * ngroups;
-  for (int i = group; i < n_pad; i += ngroups) {
-    M s0 = M(0), s1 = M(0), s2 = M(0);
-    if (i < a.n_nodes) {
-      int k1 = a.row[i + 1];
-      for (int k = a.row[i] + gl; k < k1; k += ROWG) {
-        const M* A = val + 9 * (size_t)k;
-        int j = a.col[k];
-        M p0 = (M)u[3 * j], p1 = (M)u[3 * j + 1], p2 = (M)u[3 * j + 2];
-        s0 += A[0] * p0 + A[1] * p1 + A[2] * p2;
-        s1 += A[3] * p0 + A[4] * p1 + A[5] * p2;
-        s2 += A[6] * p0 + A[7] * p1 + A[8] * p2;
-      }
-    }
-    for (int o = ROWG / 2; o > 0; o >>= 1) {
-      s0 += __shfl_down_sync(0xffffffffu, s0, o, ROWG);
-      s1 += __shfl_down_sync(0xffffffffu, s1, o, ROWG);
-      s2 += __shfl_down_sync(0xffffffffu, s2, o, ROWG);
-    }
-    if (gl == 0 && i < a.n_nodes) {
-      atomicAdd(w + 3 * i, (double)s0);
-      atomicAdd(w + 3 * i + 1, (double)s1);
-      atomicAdd(w + 3 * i + 2, (double)s2);
-      acc += (double)u[3 * i] * (double)s0 + (double)u[3 * i + 1] * (double)s1 + (double)u[3 * i + 2] * (double)s2;
-    }
-  }
-  return acc;
-}
-
-// Contact terms of w += A u, one warp per barrier pair and per friction pair:
-// lane j < 12 gathers u for DOF j of the stencil (slot j / 3, component j % 3),
-// lane r < 12 forms row r of the 12x12 block product and scatters it.
-// Returns this lane's share of u^T (A_contact u).  Whole warps must call it.
-template <typename M, typename V>
-__device__ inline double apply_contact_warp(const PcgArgs& a, const M* pairH, const M* fHu, const V* u, double* w,
-                                            int tid, int nthr) {
-  const DevScene& S = a.S;
-  int lane = threadIdx.x & 31;
-  int warp = tid >> 5, nwarps = nthr >> 5;
-  double acc = 0.0;
-  int np = min(*a.n_pairs, a.cap);
-  int slot = lane / 3, comp = lane % 3;
-  for (int k = warp; k < np; k += nwarps) {
-    const int* r = a.rec + 8 * k;
-    int v = lane < 12 ? r[4 + slot] : 0;
-    bool active = lane < 12 && S.vkind[v] != VK_KIN;
-    M uj = M(0);
-    if (active) {
-      NodeMap m = vertex_nodes(S, v);
-      for (int t = 0; t < m.n; ++t) uj += (M)m.w[t] * (M)u[3 * m.node[t] + comp];
-    }
-    const M* H = pairH + 144 * (size_t)k + 12 * (lane < 12 ? lane : 0);
-    M wr = M(0);
-    for (int j = 0; j < 12; ++j) {
-      M uv = __shfl_sync(0xffffffffu, uj, j);
-      if (lane < 12) wr += H[j] * uv;
-    }
-    if (active) {
-      NodeMap m = vertex_nodes(S, v);
-      for (int t = 0; t < m.n; ++t) atomicAdd(w + 3 * m.node[t] + comp, m.w[t] * (double)wr);
-      acc += (double)uj * (double)wr;
-    }
-  }
-  for (int k = warp; k < a.n_fric; k += nwarps) {
-    const int* ids = a.f_ids + 4 * k;
-    const double* wk = a.f_w + 4 * k;
-    const M* Hu = fHu + 9 * k;
-    int v = lane < 12 ? ids[slot] : 0;
-    double wgt = lane < 12 ? wk[slot] : 0.0;
-    bool active = lane < 12 && wgt != 0.0 && S.vkind[v] != VK_KIN;
-    M uj = M(0);
-    if (active) {
-      NodeMap m = vertex_nodes(S, v);
-      for (int t = 0; t < m.n; ++t) uj += (M)m.w[t] * (M)u[3 * m.node[t] + comp];
-    }
-    // U_c = sum over slots of w_k u_{k,c}: lanes c, c+3, c+6, c+9
-    M contrib = (M)wgt * uj;
-    M U0 = M(0), U1 = M(0), U2 = M(0);
-    for (int q = 0; q < 4; ++q) {
-      U0 += __shfl_sync(0xffffffffu, contrib, 3 * q);
-      U1 += __shfl_sync(0xffffffffu, contrib, 3 * q + 1);
-      U2 += __shfl_sync(0xffffffffu, contrib, 3 * q + 2);
-    }
-    M tc = M(0);
-    if (lane < 12) tc = Hu[3 * comp] * U0 + Hu[3 * comp + 1] * U1 + Hu[3 * comp + 2] * U2;
-    if (active) {
-      NodeMap m = vertex_nodes(S, v);
-      double y = wgt * (double)tc;
-      for (int t = 0; t < m.n; ++t) atomicAdd(w + 3 * m.node[t] + comp, m.w[t] * y);
-      acc += (double)uj * y;
-    }
-  }
-  return acc;
-}
-
-// w += A u for the whole operator (BSR + barrier pairs + friction pairs); returns this thread's share of u^T A u.
-template <typename M, typename V, int ROWG>
-__device__ inline double apply_full(const PcgArgs& a, const M* val, const M* pairH, const M* fHu, const V* u, double* w,
-                                    int tid, int nthr) {
-  double acc = spmv_bsr<M, V, ROWG>(a, val, u, w, tid, nthr);
-  acc += apply_contact_warp<M, V>(a, pairH, fHu, u, w, tid, nthr);
-  return acc;
-}
-
-// Sums of up to three per-thread values over the block (result in every thread).
-__device__ inline void block_sum3(double& a0, double& a1, double& a2) {
-  __shared__ double sh3[3][32];
-  __shared__ double tot3[3];
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_down_sync(0xffffffffu, a0, o);
-    a1 += __shfl_down_sync(0xffffffffu, a1, o);
-    a2 += __shfl_down_sync(0xffffffffu, a2, o);
-  }
-  int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (lane == 0) { sh3[0][wi] = a0; sh3[1][wi] = a1; sh3[2][wi] = a2; }
-  __syncthreads();
-  if (wi == 0) {
-    double b0 = lane < nw ? sh3[0][lane] : 0.0, b1 = lane < nw ? sh3[1][lane] : 0.0, b2 = lane < nw ? sh3[2][lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      b0 += __shfl_down_sync(0xffffffffu, b0, o);
-      b1 += __shfl_down_sync(0xffffffffu, b1, o);
-      b2 += __shfl_down_sync(0xffffffffu, b2, o);
-    }
-    if (lane == 0) { tot3[0] = b0; tot3[1] = b1; tot3[2] = b2; }
-  }
-  __syncthreads();
-  a0 = tot3[0]; a1 = tot3[1]; a2 = tot3[2];
-  __syncthreads();
-}
-
-// Totals of three partial arrays (one entry per block), identical in every block.
-__device__ inline void grid_total3(const double* p0, const double* p1, const double* p2, int nblk, double& t0,
-                                   double& t1, double& t2) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    a0 += p0[b];
-    a1 += p1[b];
-    a2 += p2[b];
-  }
-  block_sum3(a0, a1, a2);
-  t0 = a0; t1 = a1; t2 = a2;
-}
-
-// One PCG solve in the Chronopoulos-Gear form: both dot products of an
-// iteration come from one reduction point, so an iteration costs two grid
-// barriers (vector update | operator application).
-//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,  u = M^-1 r,
-//   w = A u,  gamma = r.u,  delta = u.w,
-//   beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old).
-// T = double: all FP64.  T = float: FP32 operator, preconditioner, u and p;
-// x, r, w, s and every dot product FP64; at FP32 convergence up to 3
-// replacements r <- b - A x with the FP64 operator.
-template <typename T, int ROWG>
-__global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
-  cg::grid_group grid = cg::this_grid();
-  int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-  int nblk = gridDim.x;
-  int n3 = 3 * a.n_nodes;
-  constexpr bool F32 = sizeof(T) == 4;
-  const T* val = F32 ? (const T*)a.val32 : (const T*)a.val;
-  const T* pairH = F32 ? (const T*)a.pairH32 : (const T*)a.pairH;
-  const T* fHu = F32 ? (const T*)a.f_Hu32 : (const T*)a.f_Hu;
-  const T* Dinv = F32 ? (const T*)a.Dinv32 : (const T*)a.Dinv;
-  T* pv = F32 ? (T*)a.p32 : (T*)a.p;
-  T* uv = F32 ? (T*)a.z32 : (T*)a.z;
-  double* w = a.y;
-  double* sv = a.s;
-  // partial sums: A (u.Au) is rewritten one barrier after its last read; B (r.u) and C (r.r)
-  // are written in the vector phase right after the reads, so they alternate between two
-  // buffers by iteration parity (a buffer is rewritten two barriers after its last read)
-  double* partA = a.partial;
-  auto partB = [&](int par) { return a.partial + (1 + par) * nblk; };
-  auto partC = [&](int par) { return a.partial + (3 + par) * nblk; };
-  // x = 0, r = b, u = M^-1 r, p = s = w = 0
-  double g_l = 0.0, rr_l = 0.0;
-  for (int i = tid; i < a.n_nodes; i += nthr) {
-    for (int d = 0; d < 3; ++d) {
-      a.x[3 * i + d] = 0.0;
-      a.r[3 * i + d] = a.b[3 * i + d];
-      w[3 * i + d] = 0.0;
-      sv[3 * i + d] = 0.0;
-      pv[3 * i + d] = T(0);
-    }
-    precond_node<T, T>(Dinv, a.r, uv, i, g_l, rr_l);
-  }
-  double zero = 0.0;
-  block_sum3(g_l, rr_l, zero);
-  if (threadIdx.x == 0) { partB(1)[blockIdx.x] = g_l; partC(1)[blockIdx.x] = rr_l; }
-  grid.sync();
-  double d_l = apply_full<T, T, ROWG>(a, val, pairH, fHu, uv, w, tid, nthr);
-  double v = block_sum(d_l);
-  if (threadIdx.x == 0) partA[blockIdx.x] = v;
-  grid.sync();
-  double gamma, rr, delta;
-  grid_total3(partB(1), partC(1), partA, nblk, gamma, rr, delta);
-  double bb = rr;
-  double tol2 = a.rtol * a.rtol * bb;
-  int it = 0, status = 0, replaced = 0;
-  double alpha = 0.0, beta = 0.0;
-  if (bb > 0.0) {
-    if (!(delta > 0.0)) status = isfinite(delta) ? 1 : 2;
-    alpha = gamma / delta;
-    for (it = 0; status == 0 && it < a.max_iter; ++it) {
-      // V: vector updates (node-local); w is consumed into s and cleared for the next product
-      g_l = 0.0;
-      rr_l = 0.0;
-      for (int i = tid; i < a.n_nodes; i += nthr) {
-        for (int d = 0; d < 3; ++d) {
-          int q = 3 * i + d;
-          double pq = (double)uv[q] + beta * (double)pv[q];
-          double sq = w[q] + beta * sv[q];
-          pv[q] = (T)pq;
-          sv[q] = sq;
-          a.x[q] += alpha * pq;
-          a.r[q] -= alpha * sq;
-          w[q] = 0.0;
-        }
-        precond_node<T, T>(Dinv, a.r, uv, i, g_l, rr_l);
-      }
-      const int par = it & 1;
-      zero = 0.0;
-      block_sum3(g_l, rr_l, zero);
-      if (threadIdx.x == 0) { partB(par)[blockIdx.x] = g_l; partC(par)[blockIdx.x] = rr_l; }
-      grid.sync();
-      // W: w = A u and u.w
-      d_l = apply_full<T, T, ROWG>(a, val, pairH, fHu, uv, w, tid, nthr);
-      v = block_sum(d_l);
-      if (threadIdx.x == 0) partA[blockIdx.x] = v;
-      grid.sync();
-      double gamma_new;
-      grid_total3(partB(par), partC(par), partA, nblk, gamma_new, rr, delta);
-      if (!isfinite(rr) || !isfinite(delta)) { status = 2; ++it; break; }
-      if (rr <= tol2) {
-        if (!F32 || replaced >= 3) { ++it; break; }
-        // FP64 residual replacement and restart: r = b - A64 x
-        ++replaced;
-        for (int q = tid; q < n3; q += nthr) sv[q] = 0.0;
-        grid.sync();
-        apply_full<double, double, ROWG>(a, a.val, a.pairH, a.f_Hu, a.x, sv, tid, nthr);
-        grid.sync();
-        g_l = 0.0;
-        rr_l = 0.0;
-        for (int i = tid; i < a.n_nodes; i += nthr) {
-          for (int d = 0; d < 3; ++d) {
-            int q = 3 * i + d;
-            a.r[q] = a.b[q] - sv[q];
-            w[q] = 0.0;
-            sv[q] = 0.0;
-            pv[q] = T(0);
-          }
-          precond_node<T, T>(Dinv, a.r, uv, i, g_l, rr_l);
-        }
-        // this iteration's buffer: read before the two barriers above, rewritten next at it + 2
-        zero = 0.0;
-        block_sum3(g_l, rr_l, zero);
-        if (threadIdx.x == 0) { partB(par)[blockIdx.x] = g_l; partC(par)[blockIdx.x] = rr_l; }
-        grid.sync();
-        d_l = apply_full<T, T, ROWG>(a, val, pairH, fHu, uv, w, tid, nthr);
-        v = block_sum(d_l);
-        if (threadIdx.x == 0) partA[blockIdx.x] = v;
-        grid.sync();
-        grid_total3(partB(par), partC(par), partA, nblk, gamma, rr, delta);
-        if (rr <= tol2) { ++it; break; }
-        if (!(delta > 0.0)) { status = isfinite(delta) ? 1 : 2; ++it; break; }
-        beta = 0.0;
-        alpha = gamma / delta;
+      if (!FILL) {
+        if (count) atomicAdd(cnt_or_cursor + b, count);
         continue;
       }
-      beta = gamma_new / gamma;
-      double den = delta - beta * gamma_new / alpha;
-      if (!(den > 0.0)) { status = isfinite(den) ? 1 : 2; ++it; break; }
-      alpha = gamma_new / den;
-      gamma = gamma_new;
+      double B[9];
+      // same-body part into the BSR grid
+      for (int t = 0; t < 4; ++t)
+        for (int u = 0; u < 4; ++u) {
+          double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+          for (int q = 0; q < 4; ++q) {
+            if (P.body[q] != b) continue;
+            for (int j = 0; j < 4; ++j) {
+              if (P.body[j] != b) continue;
+              pair_block(H, fw, Hu, q, j, B);
+              const double ww = P.w[q][t] * P.w[j][u];
+              for (int i = 0; i < 9; ++i) acc[i] += ww * B[i];
+            }
+          }
+          double* dst = Hval + 9 * (size_t)S.abd_blk[16 * b + 4 * t + u];
+          for (int i = 0; i < 9; ++i) atomicAdd(dst + i, acc[i]);
+        }
+      if (!count) continue;
+      int pos = atomicAdd(cnt_or_cursor + b, count);
+      if (pos < 0 || pos + count > ent_cap) { atomicOr(err, ERRF_ABD); continue; }
+      for (int j = 0; j < 4; ++j) {
+        if (P.kind[j] == VK_FEM) {
+          for (int t = 0; t < 4; ++t) {
+            double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int q = 0; q < 4; ++q) {
+              if (P.body[q] != b) continue;
+              pair_block(H, fw, Hu, q, j, B);
+              for (int i = 0; i < 9; ++i) acc[i] += P.w[q][t] * B[i];
+            }
+            ent[pos] = (P.node[j] << 2) | t;
+            for (int i = 0; i < 9; ++i) entv[9 * (size_t)pos + i] = acc[i];
+            ++pos;
+          }
+        } else if (P.kind[j] == VK_ABD && P.body[j] != b) {
+          bool fb = true;
+          for (int jj = 0; jj < j; ++jj) fb = fb && P.body[jj] != P.body[j];
+          if (!fb) continue;
+          const int b2 = P.body[j];
+          for (int t = 0; t < 4; ++t)
+            for (int u = 0; u < 4; ++u) {
+              double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+              for (int q = 0; q < 4; ++q) {
+                if (P.body[q] != b) continue;
+                for (int jj = 0; jj < 4; ++jj) {
+                  if (P.body[jj] != b2) continue;
+                  pair_block(H, fw, Hu, q, jj, B);
+                  const double ww = P.w[q][t] * P.w[jj][u];
+                  for (int i = 0; i < 9; ++i) acc[i] += ww * B[i];
+                }
+              }
+              ent[pos] = ((S.nf + 4 * b2 + u) << 2) | t;
+              for (int i = 0; i < 9; ++i) entv[9 * (size_t)pos + i] = acc[i];
+              ++pos;
+            }
+        }
+      }
     }
-  } else {
-    for (int i = tid; i < n3; i += nthr) a.x[i] = 0.0;
   }
-  if (tid == 0) {
+}
+
+void launch_abd_contact(cudaStream_t st, const DevScene& S, const int* rec, const int* n_pairs, int cap,
+                        const double* pairH, int n_fric, const int* f_ids, const double* f_w, const double* f_Hu,
+                        int* abd_ptr, int* cursor, int* ent, double* entv, long long ent_cap, double* Hval,
+                        double* Dc, int* err) {
+  if (S.nab == 0) return;
+  // the diagonal contact blocks of the pseudo-nodes go into the BSR grid with the rest of the same-body part
+  cudaMemsetAsync(Dc + 9 * (size_t)S.nf, 0, sizeof(double) * 36 * (size_t)S.nab, st);
+  cudaMemsetAsync(abd_ptr, 0, sizeof(int) * (S.nab + 1), st);
+  int grid = std::max(1, std::min((cap + n_fric + 127) / 128, 148 * 8));
+  k_abd_contact<false><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, abd_ptr,
+                                             nullptr, nullptr, 0, nullptr, err);
+  k_scan_totals<<<1, 1024, 0, st>>>(S.nab + 1, abd_ptr);
+  cudaMemcpyAsync(cursor, abd_ptr, sizeof(int) * S.nab, cudaMemcpyDeviceToDevice, st);
+  k_abd_contact<true><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, cursor, ent,
+                                            entv, ent_cap, Hval, err);
+  count_launch(3);
+}
+
+// ---------------------------------------------------------------------------
+// operator in the CTA-major layout: the blocks of segment s (rows seg[s] ..
+// seg[s+1]) are stored from 9 k0 on as nine planes of nloc values (value q of
+// block k0 + kk at 9 k0 + q nloc + kk), so that consecutive threads read
+// consecutive addresses and a CTA's rows form one contiguous range.
+// ---------------------------------------------------------------------------
+template <typename M>
+__global__ void k_layout(const int* __restrict__ seg, const int* __restrict__ row, const double* __restrict__ src,
+                         M* __restrict__ dst) {
+  int s = blockIdx.x;
+  int k0 = row[seg[s]], k1 = row[seg[s + 1]];
+  int nloc = k1 - k0;
+  const double* in = src + 9 * (size_t)k0;
+  M* out = dst + 9 * (size_t)k0;
+  for (int idx = threadIdx.x; idx < 9 * nloc; idx += blockDim.x) {
+    int q = idx / nloc, kk = idx - q * nloc;
+    out[idx] = (M)in[9 * kk + q];
+  }
+}
+
+void launch_layout(cudaStream_t st, int n_seg, const int* seg, const int* row, const double* src, void* dst, int fp32) {
+  if (n_seg <= 0) return;
+  if (fp32) k_layout<float><<<n_seg, 256, 0, st>>>(seg, row, src, (float*)dst);
+  else k_layout<double><<<n_seg, 256, 0, st>>>(seg, row, src, (double*)dst);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// the solver kernel
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Vecs {
+  T *r, *u, *w, *m0, *m1, *z, *q, *s, *p;
+};
+
+// value q of local block kk: base[q * sq + kk * sk]
+template <typename M>
+struct OpView {
+  const M* base;
+  int sq, sk;
+};
+
+// Index validation (PcgArgs::check): records the first failing site and
+// tells the caller to skip the access.
+__device__ inline bool pcg_ok(const PcgArgs& a, bool cond, int site) {
+  if (a.check == nullptr || cond) return true;
+  atomicCAS(a.check, 0, site);
+  return false;
+}
+
+// v gathered at a vertex through x = J z (zero for kinematic vertices), in FP64
+template <typename V>
+__device__ inline void gather_vertex(const PcgArgs& a, const V* v, int vert, double& g0, double& g1, double& g2) {
+  const DevScene& S = a.S;
+  if (!pcg_ok(a, vert >= 0 && vert < S.nv, 4)) { g0 = g1 = g2 = 0.0; return; }
+  int kind = S.vkind[vert];
+  if (kind == VK_ABD && !pcg_ok(a, S.vabd[vert] >= 0 && S.vabd[vert] < S.nab, 7)) { g0 = g1 = g2 = 0.0; return; }
+  if (kind == VK_FEM) {
+    g0 = v[3 * vert]; g1 = v[3 * vert + 1]; g2 = v[3 * vert + 2];
+  } else if (kind == VK_ABD) {
+    int n = S.nf + 4 * S.vabd[vert];
+    const double x0 = S.xbar[3 * vert], x1 = S.xbar[3 * vert + 1], x2 = S.xbar[3 * vert + 2];
+    const V* b = v + 3 * n;
+    g0 = b[0] + x0 * b[3] + x1 * b[6] + x2 * b[9];
+    g1 = b[1] + x0 * b[4] + x1 * b[7] + x2 * b[10];
+    g2 = b[2] + x0 * b[5] + x1 * b[8] + x2 * b[11];
+  } else {
+    g0 = g1 = g2 = 0.0;
+  }
+}
+
+// rows (3 slot .. 3 slot + 2) of one contact block applied to v (block values
+// stored as M, products and sums in FP64); returns the pair's vertex in that slot
+template <typename M, typename V>
+__device__ inline int contact_rows(const PcgArgs& a, const M* pairH, const M* fHu, const V* v, int code, double& y0,
+                                   double& y1, double& y2) {
+  const int k = code >> 3, q = code & 3;
+  if (!pcg_ok(a, (code & 4) ? (k >= 0 && k < a.n_fric) : (k >= 0 && k < a.cap), (code & 4) ? 5 : 3)) {
+    y0 = y1 = y2 = 0.0;
+    return -1;
+  }
+  if (!(code & 4)) {
+    const int* r = a.rec + 8 * (size_t)k;
+    const M* H = pairH + 144 * (size_t)k + 36 * q;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double g0, g1, g2;
+      gather_vertex<V>(a, v, r[4 + j], g0, g1, g2);
+      t0 += (double)H[3 * j] * g0 + (double)H[3 * j + 1] * g1 + (double)H[3 * j + 2] * g2;
+      t1 += (double)H[12 + 3 * j] * g0 + (double)H[12 + 3 * j + 1] * g1 + (double)H[12 + 3 * j + 2] * g2;
+      t2 += (double)H[24 + 3 * j] * g0 + (double)H[24 + 3 * j + 1] * g1 + (double)H[24 + 3 * j + 2] * g2;
+    }
+    y0 = t0; y1 = t1; y2 = t2;
+    return r[4 + q];
+  }
+  const int* ids = a.f_ids + 4 * (size_t)k;
+  const double* w = a.f_w + 4 * (size_t)k;
+  const M* Hu = fHu + 9 * (size_t)k;
+  double U0 = 0.0, U1 = 0.0, U2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (w[j] == 0.0) continue;
+    double g0, g1, g2;
+    gather_vertex<V>(a, v, ids[j], g0, g1, g2);
+    U0 += w[j] * g0; U1 += w[j] * g1; U2 += w[j] * g2;
+  }
+  const double wq = w[q];
+  y0 = wq * ((double)Hu[0] * U0 + (double)Hu[1] * U1 + (double)Hu[2] * U2);
+  y1 = wq * ((double)Hu[3] * U0 + (double)Hu[4] * U1 + (double)Hu[5] * U2);
+  y2 = wq * ((double)Hu[6] * U0 + (double)Hu[7] * U1 + (double)Hu[8] * U2);
+  return ids[q];
+}
+
+// Sum of N per-thread values over the CTA, left in out[0..N) (shared) for every thread.
+template <typename M, int N>
+__device__ inline void block_sum_n(M (&v)[N], M* red /* shared, 32 * N */, M* out /* shared, N */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < N; ++j) red[32 * j + wi] = v[j];
+  __syncthreads();
+  if (wi == 0) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      M b = lane < nw ? red[32 * j + lane] : M(0);
+      for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+      if (lane == 0) out[j] = b;
+    }
+  }
+  __syncthreads();
+}
+
+constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
+
+struct Shared {
+  double red[32 * 12];
+  double out[12];
+};
+
+// Contact rows of the FEM segment [r0, r1): every incidence of the segment
+// (a contiguous range of the incidence list, ordered by owner) is handled by
+// one thread of the CTA and added to acc[3 (owner - r0) + c] in shared memory.
+// Every thread of the CTA must call it; acc is complete on return.
+template <typename M, typename V>
+__device__ inline void fem_contact(const PcgArgs& a, int r0, int r1, const M* pairH, const M* fHu, const V* v,
+                                   double* acc) {
+  for (int j = threadIdx.x; j < 3 * (r1 - r0); j += blockDim.x) acc[j] = 0.0;
+  __syncthreads();
+  const int e0 = a.inc_ptr[r0], e1 = a.inc_ptr[r1];
+#pragma unroll 2
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    if (!pcg_ok(a, e >= 0 && e < a.inc_cap, 2)) break;
+    const int2 ie = a.inc[e];
+    if (!pcg_ok(a, ie.y >= r0 && ie.y < r1, 12)) continue;
+    double y0, y1, y2;
+    contact_rows<M, V>(a, pairH, fHu, v, ie.x, y0, y1, y2);
+    double* t = acc + 3 * (ie.y - r0);
+    atomicAdd(t, y0);
+    atomicAdd(t + 1, y1);
+    atomicAdd(t + 2, y2);
+  }
+  __syncthreads();
+}
+
+// Rows of the FEM segment [r0, r1) of this CTA: y = (A v)_i for each row i,
+// the BSR part formed by a group of ROWG threads, plus the row's contact sum
+// from fem_contact, handed to fn(i, y0, y1, y2) on the group's first lane.
+// Every thread of the CTA must call it.
+template <typename M, typename V, int ROWG, typename F>
+__device__ inline void fem_rows(const PcgArgs& a, int r0, int r1, int k0, OpView<M> op, const int* colp,
+                                const int* rowp /* relative to k0, indexed from r0; null: global row */,
+                                const double* acc, const V* v, F&& fn) {
+  const int groups = blockDim.x / ROWG, g = threadIdx.x / ROWG, gl = threadIdx.x & (ROWG - 1);
+  for (int base = r0; base < r1; base += groups) {
+    const int i = base + g;
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    if (i < r1) {
+      int kb, ke;
+      if (rowp) { kb = rowp[i - r0]; ke = rowp[i - r0 + 1]; }
+      else { kb = a.row[i] - k0; ke = a.row[i + 1] - k0; }
+#pragma unroll 2
+      for (int kk = kb + gl; kk < ke; kk += ROWG) {
+        const int j = colp[kk];
+        if (!pcg_ok(a, j >= 0 && j < a.n_nodes, 1)) continue;
+        const double v0 = v[3 * j], v1 = v[3 * j + 1], v2 = v[3 * j + 2];
+        const M* A = op.base + (size_t)kk * op.sk;
+        const int sq = op.sq;
+        y0 += (double)A[0] * v0 + (double)A[sq] * v1 + (double)A[2 * sq] * v2;
+        y1 += (double)A[3 * sq] * v0 + (double)A[4 * sq] * v1 + (double)A[5 * sq] * v2;
+        y2 += (double)A[6 * sq] * v0 + (double)A[7 * sq] * v1 + (double)A[8 * sq] * v2;
+      }
+    }
+#pragma unroll
+    for (int o = ROWG / 2; o > 0; o >>= 1) {
+      y0 += __shfl_down_sync(0xffffffffu, y0, o, ROWG);
+      y1 += __shfl_down_sync(0xffffffffu, y1, o, ROWG);
+      y2 += __shfl_down_sync(0xffffffffu, y2, o, ROWG);
+    }
+    if (i < r1 && gl == 0) {
+      const double* c = acc + 3 * (i - r0);
+      fn(i, y0 + c[0], y1 + c[1], y2 + c[2]);
+    }
+  }
+}
+
+// Rows of the four pseudo-nodes of ABD body b, formed by the whole CTA (BSR
+// grid including the body's own contact, then its list of contact coupling
+// blocks) and handed to fn(node, y0, y1, y2) on threads 0..3.  Every thread
+// must call it.
+template <typename M, typename V, typename F>
+__device__ inline void abd_rows(const PcgArgs& a, int b, OpView<M> op, const int* colp, int nloc, const V* v,
+                                Shared& sh, F&& fn) {
+  const DevScene& S = a.S;
+  const int r = S.nf + 4 * b, k0 = a.row[r];
+  const int rb1 = a.row[r + 1] - k0, rb2 = a.row[r + 2] - k0, rb3 = a.row[r + 3] - k0;
+  double acc[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) acc[j] = 0.0;
+  for (int kk = threadIdx.x; kk < nloc; kk += blockDim.x) {
+    const int t = (kk >= rb1) + (kk >= rb2) + (kk >= rb3);
+    const int j = colp[kk];
+    if (!pcg_ok(a, j >= 0 && j < a.n_nodes, 8)) continue;
+    const double v0 = v[3 * j], v1 = v[3 * j + 1], v2 = v[3 * j + 2];
+    const M* A = op.base + (size_t)kk * op.sk;
+    const int sq = op.sq;
+    const double y0 = (double)A[0] * v0 + (double)A[sq] * v1 + (double)A[2 * sq] * v2;
+    const double y1 = (double)A[3 * sq] * v0 + (double)A[4 * sq] * v1 + (double)A[5 * sq] * v2;
+    const double y2 = (double)A[6 * sq] * v0 + (double)A[7 * sq] * v1 + (double)A[8 * sq] * v2;
+#pragma unroll
+    for (int tt = 0; tt < 4; ++tt)
+      if (tt == t) { acc[3 * tt] += y0; acc[3 * tt + 1] += y1; acc[3 * tt + 2] += y2; }
+  }
+  const int e1 = a.abd_ptr[b + 1];
+#pragma unroll 2
+  for (int e = a.abd_ptr[b] + threadIdx.x; e < e1; e += blockDim.x) {
+    if (!pcg_ok(a, e >= 0 && e < a.abd_cap, 9)) break;
+    const int code = a.abd_ent[e], t = code & 3, j = code >> 2;
+    if (!pcg_ok(a, j >= 0 && j < a.n_nodes, 10)) continue;
+    const double v0 = v[3 * j], v1 = v[3 * j + 1], v2 = v[3 * j + 2];
+    const double* B = a.abd_val + 9 * (size_t)e;
+    const double y0 = B[0] * v0 + B[1] * v1 + B[2] * v2;
+    const double y1 = B[3] * v0 + B[4] * v1 + B[5] * v2;
+    const double y2 = B[6] * v0 + B[7] * v1 + B[8] * v2;
+#pragma unroll
+    for (int tt = 0; tt < 4; ++tt)
+      if (tt == t) { acc[3 * tt] += y0; acc[3 * tt + 1] += y1; acc[3 * tt + 2] += y2; }
+  }
+  block_sum_n<double, 12>(acc, sh.red, sh.out);
+  if (threadIdx.x < 4) {
+    const int t = threadIdx.x;
+    fn(r + t, sh.out[3 * t], sh.out[3 * t + 1], sh.out[3 * t + 2]);
+  }
+  __syncthreads();
+}
+
+// z = D v for one node's 3x3 block (D in the operator type, v and z in the vector type)
+template <typename M, typename T>
+__device__ inline void apply3(const M* D, T v0, T v1, T v2, T& z0, T& z1, T& z2) {
+  const M w0 = (M)v0, w1 = (M)v1, w2 = (M)v2;
+  z0 = (T)(D[0] * w0 + D[1] * w1 + D[2] * w2);
+  z1 = (T)(D[3] * w0 + D[4] * w1 + D[5] * w2);
+  z2 = (T)(D[6] * w0 + D[7] * w1 + D[8] * w2);
+}
+
+// Totals of the three per-CTA partial sums (one replica, summed in CTA order by
+// every CTA): the loads are issued by load_partials, the sums by totals3.
+struct Partials {
+  double v[3][2];
+};
+__device__ inline void load_partials(const double* rep /* [3][grid] */, int nblk, Partials& P) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int b = threadIdx.x + j * blockDim.x;
+    const bool in = b < nblk;
+    P.v[0][j] = in ? rep[b] : 0.0;
+    P.v[1][j] = in ? rep[nblk + b] : 0.0;
+    P.v[2][j] = in ? rep[2 * nblk + b] : 0.0;
+  }
+}
+__device__ inline void totals3(const double* rep, int nblk, const Partials& P, Shared& sh, double& t0, double& t1,
+                               double& t2) {
+  double v[3] = {P.v[0][0] + P.v[0][1], P.v[1][0] + P.v[1][1], P.v[2][0] + P.v[2][1]};
+  for (int b = threadIdx.x + 2 * blockDim.x; b < nblk; b += blockDim.x) {
+    v[0] += rep[b];
+    v[1] += rep[nblk + b];
+    v[2] += rep[2 * nblk + b];
+  }
+  block_sum_n<double, 3>(v, sh.red, sh.out);
+  t0 = sh.out[0]; t1 = sh.out[1]; t2 = sh.out[2];
+  __syncthreads();
+}
+
+__device__ inline void write_partials(double* rep0 /* replica 0 of this parity, [3][grid] */, size_t rep_stride,
+                                      int nblk, Shared& sh, double (&v)[3]) {
+  block_sum_n<double, 3>(v, sh.red, sh.out);
+  if (threadIdx.x < 3 * PCG_REPLICAS) {
+    int rep = threadIdx.x / 3, j = threadIdx.x % 3;
+    rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = sh.out[j];
+  }
+  __syncthreads();
+}
+
+__device__ inline double total_fp64(const double* rep /* [grid] */, int nblk, double* red, double* out) {
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v[0] += rep[b];
+  block_sum_n<double, 1>(v, red, out);
+  double t = out[0];
+  __syncthreads();
+  return t;
+}
+
+// One solve.  M = double: every operation in FP64.  M = float (mixed
+// precision): the operator, the contact blocks and the preconditioner are
+// applied in FP32; the iteration vectors, the scalars and every dot product
+// stay FP64, and the FP64 residual b - A x is recomputed with the FP64
+// operator whenever the recurrence has converged, restarting the iteration
+// on it (iterative refinement).  Both forms restart the same way when the
+// recursive residual of the pipelined recurrences stagnates.
+template <typename M, int ROWG>
+__global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
+  using T = double;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ Shared sh;
+  constexpr bool F32 = sizeof(M) == 4;
+  const DevScene& S = a.S;
+  const int nblk = gridDim.x, cta = blockIdx.x;
+  const bool fem_cta = cta < a.n_fem_ctas;
+  const int nf = S.nf;
+  const int n3 = 3 * a.n_nodes;
+
+  // ---- this CTA's rows and their operator view; shared memory: contact sums
+  //      of the rows, then (resident) operator planes, preconditioner, columns, row offsets
+  int r0 = 0, r1 = 0, k0 = 0, nloc = 0;
+  OpView<M> op{nullptr, 0, 1};
+  const int* colp = nullptr;
+  const int* rowp = nullptr;
+  const M* dinv_loc = nullptr;
+  const M* opM = (const M*)a.op;
+  const M* dinvM = (const M*)a.dinv;
+  double* acc = (double*)dyn;
+  if (fem_cta) {
+    r0 = a.seg_row[cta]; r1 = a.seg_row[cta + 1];
+    if (!pcg_ok(a, r0 >= 0 && r0 <= r1 && r1 <= nf, 11)) r0 = r1 = 0;
+    k0 = a.row[r0]; nloc = a.row[r1] - k0;
+    if (a.resident) {
+      M* s_op = (M*)(acc + 3 * (size_t)a.max_rows);
+      M* s_dinv = s_op + 9 * (size_t)nloc;
+      int* s_col = (int*)(s_dinv + 9 * (size_t)(r1 - r0));
+      int* s_row = s_col + nloc;
+      const M* g_op = opM + 9 * (size_t)k0;
+      for (int idx = threadIdx.x; idx < 9 * nloc; idx += blockDim.x) s_op[idx] = g_op[idx];
+      for (int idx = threadIdx.x; idx < 9 * (r1 - r0); idx += blockDim.x) s_dinv[idx] = dinvM[9 * (size_t)r0 + idx];
+      for (int idx = threadIdx.x; idx < nloc; idx += blockDim.x) s_col[idx] = a.col[k0 + idx];
+      for (int idx = threadIdx.x; idx <= r1 - r0; idx += blockDim.x) s_row[idx] = a.row[r0 + idx] - k0;
+      __syncthreads();
+      op = OpView<M>{s_op, nloc, 1};
+      colp = s_col; rowp = s_row; dinv_loc = s_dinv;
+    } else {
+      op = OpView<M>{opM + 9 * (size_t)k0, nloc, 1};
+      colp = a.col + k0; dinv_loc = dinvM + 9 * (size_t)r0;
+    }
+  }
+  // preconditioner block of node i (owned by this CTA)
+  auto Dof = [&](int i) -> const M* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvM + 9 * (size_t)i); };
+
+  Vecs<T> V;
+  {
+    T* base = (T*)a.vec;
+    V.r = base; V.u = base + n3; V.w = base + 2 * (size_t)n3; V.m0 = base + 3 * (size_t)n3;
+    V.m1 = base + 4 * (size_t)n3; V.z = base + 5 * (size_t)n3; V.q = base + 6 * (size_t)n3;
+    V.s = base + 7 * (size_t)n3; V.p = base + 8 * (size_t)n3;
+  }
+  const M* pairH = (const M*)a.pairH;
+  const M* fHu = (const M*)a.fHu;
+  double* x = a.x;
+  double* t64 = a.t64;
+  // partial sums: [R][2 parities][3][grid], then the residual norms [R][grid]
+  double* partT = (double*)a.partial;
+  const size_t repT = 2 * 3 * (size_t)nblk;
+  double* partD = partT + PCG_REPLICAS * repT;
+  const int myrep = cta % PCG_REPLICAS;
+
+  // every row-forming pass over this CTA's owned rows: the iteration operator
+  // (assembled = false: layout copy of type M) or the assembled FP64 one
+  auto for_rows = [&](bool assembled, auto&& op_view_fem, const int* colp_fem, const int* rowp_fem, auto mtag,
+                      const auto* mat_pairH, const auto* mat_fHu, const auto* vin, auto&& fn) {
+    using MM = decltype(mtag);
+    using VV = typename std::remove_cv<typename std::remove_pointer<decltype(vin)>::type>::type;
+    if (fem_cta) {
+      fem_contact<MM, VV>(a, r0, r1, mat_pairH, mat_fHu, vin, acc);
+      fem_rows<MM, VV, ROWG>(a, r0, r1, k0, op_view_fem, colp_fem, rowp_fem, acc, vin, fn);
+    } else {
+      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas) {
+        const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
+        OpView<MM> ov = assembled ? OpView<MM>{(const MM*)a.val64 + 9 * (size_t)kb0, 1, 9}
+                                  : OpView<MM>{(const MM*)a.op + 9 * (size_t)kb0, nl, 1};
+        abd_rows<MM, VV>(a, b, ov, a.col + kb0, nl, vin, sh, fn);
+      }
+    }
+  };
+  // node-local pass over the nodes this CTA owns
+  auto for_nodes = [&](auto&& fn) {
+    if (fem_cta) {
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) fn(i);
+    } else {
+      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas)
+        if (threadIdx.x < 4) fn(nf + 4 * b + threadIdx.x);
+    }
+  };
+  // the FP64 operator (assembled layout) for the true residual
+  OpView<double> op64{a.val64 + 9 * (size_t)k0, 1, 9};
+  const int* col64 = a.col + k0;
+
+  // ---- x = 0, t64 = b, |b|^2
+  {
+    double v[1] = {0.0};
+    for_nodes([&](int i) {
+      for (int c = 0; c < 3; ++c) {
+        double bv = a.b[3 * i + c];
+        x[3 * i + c] = 0.0;
+        t64[3 * i + c] = bv;
+        v[0] += bv * bv;
+      }
+    });
+    block_sum_n<double, 1>(v, sh.red, sh.out);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
+  }
+  grid.sync();
+  const double bb = total_fp64(partD + myrep * (size_t)nblk, nblk, sh.red, sh.out);
+  int it = 0, status = 0, replaced = 0;
+  if (!(bb > 0.0) || !isfinite(bb)) {
+    if (threadIdx.x == 0 && cta == 0) {
+      a.out[0] = 0; a.out[1] = isfinite(bb) ? 0 : 2; a.out[2] = 0; a.res[0] = 0.0;
+    }
+    return;
+  }
+  const double tol2_true = a.rtol * a.rtol * bb;
+  const int max_replace = 10;
+  double sigma = 1.0 / sqrt(bb);  // scale of the current restart: iteration vectors hold sigma * (b - A x)
+  double tt = bb;
+
+  // ---- (re)start from t64 = b - A x: r = sigma t64, u = M^-1 r, w = A u, m = M^-1 w
+  auto restart = [&](int par) {
+    for_nodes([&](int i) {
+      T rv[3];
+      for (int c = 0; c < 3; ++c) {
+        const int q = 3 * i + c;
+        rv[c] = sigma * t64[q];
+        V.r[q] = rv[c];
+        V.z[q] = T(0); V.q[q] = T(0); V.s[q] = T(0); V.p[q] = T(0);
+      }
+      T u0, u1, u2;
+      apply3<M, T>(Dof(i), rv[0], rv[1], rv[2], u0, u1, u2);
+      V.u[3 * i] = u0; V.u[3 * i + 1] = u1; V.u[3 * i + 2] = u2;
+    });
+    grid.sync();
+    double pv[3] = {0.0, 0.0, 0.0};
+    T* mcur = par ? V.m1 : V.m0;
+    for_rows(false, op, colp, rowp, M(0), pairH, fHu, (const T*)V.u, [&](int i, double y0, double y1, double y2) {
+      const int q = 3 * i;
+      V.w[q] = y0; V.w[q + 1] = y1; V.w[q + 2] = y2;
+      T m0, m1, m2;
+      apply3<M, T>(Dof(i), y0, y1, y2, m0, m1, m2);
+      mcur[q] = m0; mcur[q + 1] = m1; mcur[q + 2] = m2;
+      const T u0 = V.u[q], u1 = V.u[q + 1], u2 = V.u[q + 2];
+      const T rr0 = V.r[q], rr1 = V.r[q + 1], rr2 = V.r[q + 2];
+      pv[0] += rr0 * u0 + rr1 * u1 + rr2 * u2;
+      pv[1] += y0 * u0 + y1 * u1 + y2 * u2;
+      pv[2] += rr0 * rr0 + rr1 * rr1 + rr2 * rr2;
+    });
+    write_partials(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv);
+    grid.sync();
+  };
+  // ---- the FP64 residual t64 = b - A64 x and its squared norm
+  auto true_residual = [&]() -> double {
+    double v[1] = {0.0};
+    for_rows(true, op64, col64, (const int*)nullptr, 0.0, a.pairH64, a.fHu64, (const double*)x,
+             [&](int i, double y0, double y1, double y2) {
+               const int q = 3 * i;
+               const double t0 = a.b[q] - y0, t1 = a.b[q + 1] - y1, t2 = a.b[q + 2] - y2;
+               t64[q] = t0; t64[q + 1] = t1; t64[q + 2] = t2;
+               v[0] += t0 * t0 + t1 * t1 + t2 * t2;
+             });
+    block_sum_n<double, 1>(v, sh.red, sh.out);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
+    grid.sync();
+    return total_fp64(partD + myrep * (size_t)nblk, nblk, sh.red, sh.out);
+  };
+
+  // inner target in the scaled units of the current restart: the requested
+  // reduction, but not below what the FP32 operator resolves
+  auto inner_tol2 = [&]() -> double {
+    double t = tol2_true * sigma * sigma;
+    if (F32) t = fmax(t, 1e-12);
+    return t;
+  };
+  restart(0);
+  double tol_in2 = inner_tol2();
+  double unscale = sqrt(bb);  // 1 / sigma
+  bool fresh = true;
+  double alpha_old = 1.0, gamma_old = 1.0;
+  // stagnation: the recursive residual of the pipelined recurrences can level
+  // off above the target (its rounding drifts from b - A x); when it has not
+  // reached a new minimum for STALL iterations the true residual is formed
+  constexpr int STALL = 80;
+  double rr_best = 0.0;
+  int it_best = 0;
+  for (;;) {
+    const int par = it & 1;
+    const double* rep = partT + (size_t)par * 3 * nblk + myrep * repT;
+    Partials P;
+    load_partials(rep, nblk, P);
+    double gamma, delta, rr;
+    totals3(rep, nblk, P, sh, gamma, delta, rr);
+    if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) { status = 2; break; }
+    if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
+    double alpha = 0.0, beta = 0.0;
+    bool stop_inner = rr <= tol_in2 || it - it_best > STALL;
+    if (!stop_inner) {
+      if (fresh) {
+        if (!(delta > 0.0)) { status = 1; break; }
+        alpha = gamma / delta;
+      } else {
+        beta = gamma / gamma_old;
+        const double den = delta - beta * gamma / alpha_old;
+        if (!(den > 0.0)) stop_inner = true;  // lost conjugacy: refresh from the true residual
+        else alpha = gamma / den;
+      }
+    }
+    if (stop_inner || it >= a.max_iter) {
+      tt = true_residual();
+      if (!isfinite(tt)) { status = 2; break; }
+      if (tt <= tol2_true || it >= a.max_iter || replaced >= max_replace) break;
+      ++replaced;
+      unscale = sqrt(tt);
+      sigma = 1.0 / unscale;
+      tol_in2 = inner_tol2();
+      restart(par);
+      fresh = true;
+      continue;
+    }
+    // iteration: n = A m, then every recurrence of the owned nodes
+    const double ax = alpha * unscale;
+    T* mcur = par ? V.m1 : V.m0;
+    T* mnext = par ? V.m0 : V.m1;
+    double pv[3] = {0.0, 0.0, 0.0};
+    for_rows(false, op, colp, rowp, M(0), pairH, fHu, (const T*)mcur, [&](int i, double n0, double n1, double n2) {
+      const T nn[3] = {n0, n1, n2};
+      T rn[3], un[3], wn[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int q = 3 * i + c;
+        const T z = nn[c] + beta * V.z[q];
+        const T qq = mcur[q] + beta * V.q[q];
+        const T s = V.w[q] + beta * V.s[q];
+        const T p = V.u[q] + beta * V.p[q];
+        V.z[q] = z; V.q[q] = qq; V.s[q] = s; V.p[q] = p;
+        x[q] += ax * p;
+        rn[c] = V.r[q] - alpha * s;
+        un[c] = V.u[q] - alpha * qq;
+        wn[c] = V.w[q] - alpha * z;
+        V.r[q] = rn[c]; V.u[q] = un[c]; V.w[q] = wn[c];
+      }
+      T m0, m1, m2;
+      apply3<M, T>(Dof(i), wn[0], wn[1], wn[2], m0, m1, m2);
+      mnext[3 * i] = m0; mnext[3 * i + 1] = m1; mnext[3 * i + 2] = m2;
+      pv[0] += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
+      pv[1] += wn[0] * un[0] + wn[1] * un[1] + wn[2] * un[2];
+      pv[2] += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
+    });
+    write_partials(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv);
+    grid.sync();
+    gamma_old = gamma;
+    alpha_old = alpha;
+    fresh = false;
+    ++it;
+  }
+  const double res = sqrt(fmax(tt, 0.0) / bb);
+  if (status == 0 && !(tt <= tol2_true)) status = 3;  // iteration or restart budget spent before the tolerance
+  if (threadIdx.x == 0 && cta == 0) {
     a.out[0] = it;
     a.out[1] = status;
     a.out[2] = replaced;
-    a.res[0] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    a.res[0] = res;
   }
 }
 
@@ -472,37 +943,44 @@ void launch_rhs(cudaStream_t st, int n, const double* g, const double* gdir, dou
   if (n) { k_rhs<<<(n + 255) / 256, 256, 0, st>>>(n, g, gdir, rhs); count_launch(); }
 }
 
-int pcg_max_blocks(int threads) {
-  int dev, sms, per_sm;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double, 4>, threads, 0);
-  return sms * (per_sm > 0 ? per_sm : 1);
-}
-
-int pcg_max_blocks_fp32(int threads) {
-  int dev, sms, per_sm;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float, 4>, threads, 0);
-  return sms * (per_sm > 0 ? per_sm : 1);
-}
-
-template <typename T>
+template <typename M>
 static void* pcg_kernel(int rowg) {
   switch (rowg) {
-    case 2: return (void*)k_pcg<T, 2>;
-    case 8: return (void*)k_pcg<T, 8>;
-    case 16: return (void*)k_pcg<T, 16>;
-    default: return (void*)k_pcg<T, 4>;
+    case 1: return (void*)k_pcg<M, 1>;
+    case 2: return (void*)k_pcg<M, 2>;
+    case 8: return (void*)k_pcg<M, 8>;
+    default: return (void*)k_pcg<M, 4>;
   }
 }
 
-cudaError_t launch_pcg(cudaStream_t st, int grid, int threads, const PcgArgs& a, int rowg) {
+static void* pcg_fn(int fp32, int rowg) { return fp32 ? pcg_kernel<float>(rowg) : pcg_kernel<double>(rowg); }
+
+int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem) {
+  int dev, sms, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  void* f = pcg_fn(fp32, rowg);
+  if (dyn_smem) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, dyn_smem);
+  return sms * per_sm;
+}
+
+size_t pcg_smem_limit() {
+  int dev, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return (size_t)optin;
+}
+
+cudaError_t launch_pcg(cudaStream_t st, int grid, int threads, const PcgArgs& a, int rowg, size_t dyn_smem) {
   void* args[] = {(void*)&a};
   count_launch();
-  void* f = a.fp32 ? pcg_kernel<float>(rowg) : pcg_kernel<double>(rowg);
-  return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, 0, st);
+  void* f = pcg_fn(a.fp32, rowg);
+  if (dyn_smem) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, dyn_smem, st);
 }
 
 void launch_to_float(cudaStream_t st, size_t n, const double* src, float* dst, const int* n_dev, int stride) {
@@ -510,6 +988,42 @@ void launch_to_float(cudaStream_t st, size_t n, const double* src, float* dst, c
   int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
   k_to_float<<<grid, 256, 0, st>>>(n, src, dst, n_dev, stride);
   count_launch();
+}
+
+// Partition of the rows among the CTAs of a PCG launch (see PcgPlan).
+void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, PcgPlan& P) {
+  P.grid = grid;
+  P.n_abd_ctas = nab > 0 ? std::min(nab, std::max(1, grid / 8)) : 0;
+  P.n_fem_ctas = std::max(1, grid - P.n_abd_ctas);
+  if (P.n_fem_ctas + P.n_abd_ctas > grid) P.n_abd_ctas = grid - P.n_fem_ctas;
+  // balance FEM rows by stored blocks plus a per-row cost
+  const int nc = P.n_fem_ctas;
+  std::vector<long long> pre(nf + 1, 0);
+  for (int i = 0; i < nf; ++i) pre[i + 1] = pre[i] + (row[i + 1] - row[i]) + 2;
+  P.seg.assign(1, 0);
+  int cur = 0;
+  for (int c = 1; c < nc; ++c) {
+    long long target = pre[nf] * c / nc;
+    while (cur < nf && pre[cur] < target) ++cur;
+    P.seg.push_back(cur);
+  }
+  P.seg.push_back(nf);
+  for (int b = 1; b <= nab; ++b) P.seg.push_back(nf + 4 * b);
+  P.max_rows = 0;
+  P.max_blocks = 0;
+  for (int c = 0; c < nc; ++c) {
+    P.max_rows = std::max(P.max_rows, P.seg[c + 1] - P.seg[c]);
+    P.max_blocks = std::max(P.max_blocks, row[P.seg[c + 1]] - row[P.seg[c]]);
+  }
+}
+
+size_t pcg_contact_bytes(const PcgPlan& P) { return (24 * (size_t)P.max_rows + 127) & ~(size_t)127; }
+
+size_t pcg_resident_bytes(const PcgPlan& P, int fp32) {
+  size_t e = fp32 ? 4 : 8;
+  size_t b = 24 * (size_t)P.max_rows + 9 * (size_t)P.max_blocks * e + 9 * (size_t)P.max_rows * e +
+             4 * (size_t)P.max_blocks + 4 * ((size_t)P.max_rows + 1);
+  return (b + 127) & ~(size_t)127;
 }
 
 }  // namespace ipc

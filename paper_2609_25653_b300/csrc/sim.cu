@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <tuple>
@@ -60,10 +61,30 @@ struct ipcsim {
   double *xv = nullptr, *xv_t = nullptr, *xv_trial = nullptr, *z_trial = nullptr, *xk_trial = nullptr;
   double *g = nullptr, *gdir = nullptr, *rhs = nullptr, *p = nullptr, *pD = nullptr, *pv = nullptr;
   double *Hconst = nullptr, *Hval = nullptr, *Dc = nullptr, *Dinv = nullptr;
-  double *r = nullptr, *zz = nullptr, *pp = nullptr, *y = nullptr, *svec = nullptr, *partial = nullptr;
+  double *y = nullptr, *partial = nullptr;
   double* T_dev = nullptr;
+  // PCG: operator in the CTA-major layout (iteration type), nine iteration vectors, row partition
+  double* pcg_op = nullptr;
+  double* pcg_vec = nullptr;
+  std::vector<int> h_row;      // BSR row offsets (host copy)
+  PcgPlan plan;
+  int plan_fp32 = -1;
+  int* d_seg = nullptr;
+  int d_seg_cap = 0;
+  bool plan_resident = false;
+  size_t plan_smem = 0;
+  int plan_want_grid = 0, plan_rowg = 0;
+  // contact incidences per owner (FEM node or ABD body)
+  int *inc_ptr = nullptr, *inc_cursor = nullptr, *inc_tiles = nullptr;
+  int2* inc = nullptr;
+  long long inc_cap = 0;
+  // contact coupling blocks of the ABD pseudo-node rows
+  int *abd_ptr = nullptr, *abd_cursor = nullptr, *abd_ent = nullptr;
+  double* abd_val = nullptr;
+  long long abd_cap = 0;
+  int* pcg_check = nullptr;    // diagnostic index-check flag of the PCG
   // mixed precision copies
-  float *val32 = nullptr, *pairH32 = nullptr, *fHu32 = nullptr, *Dinv32 = nullptr, *z32 = nullptr, *p32 = nullptr;
+  float *pairH32 = nullptr, *fHu32 = nullptr, *Dinv32 = nullptr;
   // contact
   int cap = 0;
   int* rec = nullptr;
@@ -94,9 +115,9 @@ struct ipcsim {
   };
   Scal* sc_dev = nullptr;
   Scal* sc_host = nullptr;
-  int pcg_grid_max = 1, pcg_grid_max_d = 1, pcg_grid_max_f = 1;
-  // PCG launch shape: threads per BSR row and blocks per SM (0: as many as the work needs, up to occupancy)
-  int tune_rowg = PCG_ROW_GROUP, tune_bps = 0;
+  int pcg_grid_max = 1;
+  // PCG launch shape: threads per FEM row and CTAs per SM
+  int tune_rowg = PCG_ROW_GROUP, tune_bps = 2;
   bool autotune_pending = false;
   float tune_ms[8] = {0};
   // optional per-stage CUDA-event timing on the simulator's stream
@@ -174,8 +195,43 @@ void inv3(const double* m, double* o, double& det) {
   o[6] = c02 * id; o[7] = (m[1] * m[6] - m[0] * m[7]) * id; o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
 }
 
+// incidence entries: four per barrier pair and per friction pair
+ipc_status grow_inc(ipcsim* sim) {
+  long long need = 4LL * ((long long)sim->cap + sim->fcap);
+  if (need <= sim->inc_cap) return IPC_OK;
+  dfree(sim, sim->inc);
+  sim->inc = nullptr;
+  ipc_status s = dalloc(sim, &sim->inc, (size_t)need);  // int2 entries
+  if (s) return s;
+  sim->inc_cap = need;
+  return IPC_OK;
+}
+
+// Largest pair and candidate buffers the simulator grows to (records of 32 B,
+// pair blocks of 1152 B): beyond them a step fails with IPC_ERR_CAPACITY.
+constexpr long long MAX_PAIRS = 1LL << 23;
+constexpr long long MAX_CANDIDATES = 1LL << 26;
+
+// ABD coupling blocks: a few per pair touching an ABD body; grown when a Newton iteration overflows them
+ipc_status grow_abd_list(ipcsim* sim, long long need) {
+  if (sim->nab == 0 || need <= sim->abd_cap) return IPC_OK;
+  dfree(sim, sim->abd_ent);
+  dfree(sim, sim->abd_val);
+  sim->abd_ent = nullptr;
+  sim->abd_val = nullptr;
+  ipc_status s;
+  if ((s = dalloc(sim, &sim->abd_ent, (size_t)need))) return s;
+  if ((s = dalloc(sim, &sim->abd_val, 9 * (size_t)need))) return s;
+  sim->abd_cap = need;
+  return IPC_OK;
+}
+
 ipc_status grow_pairs(ipcsim* sim, int need) {
-  int ncap = std::max(need + need / 2, 1024);
+  if (need < 0 || need > MAX_PAIRS) {
+    sim->err = "active-pair count " + std::to_string(need) + " exceeds the pair buffer limit";
+    return IPC_ERR_CAPACITY;
+  }
+  int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 1024), MAX_PAIRS);
   dfree(sim, sim->rec);
   dfree(sim, sim->rec_s);
   dfree(sim, sim->pairH);
@@ -190,11 +246,15 @@ ipc_status grow_pairs(ipcsim* sim, int need) {
     if ((s = dalloc(sim, &sim->pairH32, (size_t)144 * ncap))) return s;
   }
   sim->cap = ncap;
-  return IPC_OK;
+  return grow_inc(sim);
 }
 
 ipc_status grow_cand(ipcsim* sim, int need) {
-  int ncap = std::max(need + need / 2, 4096);
+  if (need < 0 || need > MAX_CANDIDATES) {
+    sim->err = "CCD candidate count " + std::to_string(need) + " exceeds the candidate buffer limit";
+    return IPC_ERR_CAPACITY;
+  }
+  int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 4096), MAX_CANDIDATES);
   dfree(sim, sim->cand);
   sim->cand = nullptr;
   ipc_status s = dalloc(sim, &sim->cand, (size_t)8 * ncap);
@@ -205,7 +265,11 @@ ipc_status grow_cand(ipcsim* sim, int need) {
 }
 
 ipc_status grow_fric(ipcsim* sim, int need) {
-  int ncap = std::max(need + need / 2, 1024);
+  if (need < 0 || need > MAX_PAIRS) {
+    sim->err = "friction-pair count " + std::to_string(need) + " exceeds the pair buffer limit";
+    return IPC_ERR_CAPACITY;
+  }
+  int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 1024), MAX_PAIRS);
   dfree(sim, sim->f_ids); dfree(sim, sim->f_w); dfree(sim, sim->f_n); dfree(sim, sim->f_lam); dfree(sim, sim->f_Hu);
   ipc_status s;
   if ((s = dalloc(sim, &sim->f_ids, (size_t)4 * ncap))) return s;
@@ -219,11 +283,11 @@ ipc_status grow_fric(ipcsim* sim, int need) {
     if ((s = dalloc(sim, &sim->fHu32, (size_t)9 * ncap))) return s;
   }
   sim->fcap = ncap;
-  return IPC_OK;
+  return grow_inc(sim);
 }
 
 enum { PROF_PCG = 0, PROF_ELASTIC = 1, PROF_BARRIER = 2, PROF_CULL = 3, PROF_CCD = 4, PROF_FRICTION = 5,
-       PROF_OTHER = 6 };
+       PROF_OTHER = 6, PROF_PCG_SETUP = 7 };
 
 inline void prof_begin(ipcsim* sim, int k) {
   if (!sim->prof) return;
@@ -252,18 +316,127 @@ inline void prof_collect(ipcsim* sim) {
     }
 }
 
-// Cooperative PCG grid: PCG_ROW_GROUP threads per BSR row, capped by co-residency.
-int pcg_grid(const ipcsim* sim, bool fp32) {
-  int cap = fp32 ? sim->pcg_grid_max_f : sim->pcg_grid_max_d;
-  if (sim->tune_bps > 0) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(1, std::min(cap, sms * sim->tune_bps));
+// Row partition, shared-memory residency and operator layout of the PCG for
+// the current launch shape (tune_rowg threads per FEM row, tune_bps CTAs per SM).
+ipc_status pcg_prepare(ipcsim* sim, int fp32) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int rowg = sim->tune_rowg;
+  const int want = std::min(std::max(1, sms * std::max(1, sim->tune_bps)), sim->pcg_grid_max);
+  if (!(sim->plan.grid > 0 && sim->plan_want_grid == want && sim->plan_fp32 == fp32 && sim->plan_rowg == rowg)) {
+    int grid = want;
+    bool resident = false;
+    size_t smem = 0;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      if (sim->nab > 0 && grid < 2) { sim->err = "PCG needs two co-resident CTAs"; return IPC_ERR_CUDA; }
+      pcg_plan_rows(sim->h_row, sim->nf, sim->nab, grid, sim->plan);
+      const size_t bytes = pcg_resident_bytes(sim->plan, fp32);
+      const int cap_res = bytes <= pcg_smem_limit() ? pcg_max_blocks(PCG_THREADS, fp32, rowg, bytes) : 0;
+      if (cap_res >= grid) { resident = true; smem = bytes; break; }
+      smem = pcg_contact_bytes(sim->plan);
+      const int cap = smem <= pcg_smem_limit() ? pcg_max_blocks(PCG_THREADS, fp32, rowg, smem) : 0;
+      if (cap <= 0) { sim->err = "PCG kernel cannot be made resident"; return IPC_ERR_CUDA; }
+      if (cap >= grid) break;
+      grid = cap;
+    }
+    const int n = (int)sim->plan.seg.size();
+    if (n > sim->d_seg_cap) {
+      dfree(sim, sim->d_seg);
+      sim->d_seg = nullptr;
+      ipc_status s = dalloc(sim, &sim->d_seg, (size_t)n);
+      if (s) return s;
+      sim->d_seg_cap = n;
+    }
+    CUDA_TRY(cudaMemcpyAsync(sim->d_seg, sim->plan.seg.data(), sizeof(int) * n, cudaMemcpyHostToDevice, sim->st));
+    sim->plan_want_grid = want;
+    sim->plan_fp32 = fp32;
+    sim->plan_rowg = rowg;
+    sim->plan_resident = resident;
+    sim->plan_smem = smem;
   }
-  long long threads = (long long)sim->n_nodes * sim->tune_rowg;
-  int want = (int)std::max(1LL, (threads + PCG_THREADS - 1) / PCG_THREADS);
-  return std::max(1, std::min(cap, want));
+  launch_layout(sim->st, sim->plan.n_fem_ctas + sim->nab, sim->d_seg, sim->S.bsr_row, sim->Hval, sim->pcg_op,
+                fp32);
+  return IPC_OK;
+}
+
+// One PCG solve of H_FF p = rhs on the assembled system (Hval, pairH, f_Hu,
+// Dinv and, for FP32 iterations, their FP32 copies); the incidence lists
+// must describe the current pairs and pcg_prepare must have run on this Hval.
+ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric) {
+  const DevScene& S = sim->S;
+  PcgArgs a{};
+  a.S = S;
+  a.n_nodes = sim->n_nodes;
+  a.n_fem_ctas = sim->plan.n_fem_ctas;
+  a.n_abd_ctas = sim->plan.n_abd_ctas;
+  a.seg_row = sim->d_seg;
+  a.resident = sim->plan_resident ? 1 : 0;
+  a.row = S.bsr_row;
+  a.col = S.bsr_col;
+  a.op = sim->pcg_op;
+  a.dinv = fp32 ? (const void*)sim->Dinv32 : (const void*)sim->Dinv;
+  a.val64 = sim->Hval;
+  a.pairH = fp32 ? (const void*)sim->pairH32 : (const void*)sim->pairH;
+  a.fHu = fp32 ? (const void*)sim->fHu32 : (const void*)sim->f_Hu;
+  a.pairH64 = sim->pairH;
+  a.fHu64 = sim->f_Hu;
+  a.rec = sim->rec;
+  a.n_pairs = &sim->sc_dev->n_pairs;
+  a.cap = sim->cap;
+  a.n_fric = n_fric;
+  a.f_ids = sim->f_ids;
+  a.f_w = sim->f_w;
+  a.inc_ptr = sim->inc_ptr;
+  a.inc = sim->inc;
+  a.b = sim->rhs;
+  a.x = sim->p;
+  a.vec = sim->pcg_vec;
+  a.t64 = sim->y;
+  a.partial = sim->partial;
+  a.rtol = rtol;
+  a.max_iter = max_iter;
+  a.fp32 = fp32;
+  a.out = sim->sc_dev->pcg_out;
+  a.res = &sim->sc_dev->pcg_res;
+  a.inc_cap = sim->inc_cap;
+  // IPCSIM_PCG_CHECK=1: the solver validates every gathered index (diagnostic mode)
+  static const bool check = [] { const char* e = std::getenv("IPCSIM_PCG_CHECK"); return e && e[0] == '1'; }();
+  if (check && !sim->pcg_check) {
+    ipc_status s = dalloc(sim, &sim->pcg_check, 1);
+    if (s) return s;
+  }
+  a.check = check ? sim->pcg_check : nullptr;
+  a.max_rows = sim->plan.max_rows;
+  a.abd_ptr = sim->abd_ptr;
+  a.abd_ent = sim->abd_ent;
+  a.abd_val = sim->abd_val;
+  a.abd_cap = sim->abd_cap;
+  CUDA_TRY(launch_pcg(sim->st, sim->plan.grid, PCG_THREADS, a, sim->tune_rowg, sim->plan_smem));
+  if (check) {
+    int site = 0;
+    CUDA_TRY(cudaMemcpyAsync(&site, sim->pcg_check, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+    CUDA_TRY(cudaStreamSynchronize(sim->st));
+    if (site) {
+      sim->err = "PCG index check failed at site " + std::to_string(site);
+      return IPC_ERR_CUDA;
+    }
+  }
+  return IPC_OK;
+}
+
+// ABD contact: same-body blocks into the BSR grid, coupling blocks into the per-body lists.
+void build_abd_contact(ipcsim* sim, int n_fric) {
+  if (!sim->nab) return;
+  launch_abd_contact(sim->st, sim->S, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->pairH, n_fric, sim->f_ids,
+                     sim->f_w, sim->f_Hu, sim->abd_ptr, sim->abd_cursor, sim->abd_ent, sim->abd_val, sim->abd_cap,
+                     sim->Hval, sim->Dc, &sim->sc_dev->flags);
+}
+
+// Contact incidences of the current pairs (and friction pairs) per owner.
+void build_incidence(ipcsim* sim, int n_fric) {
+  launch_incidence(sim->st, sim->S, sim->rec, &sim->sc_dev->n_pairs, sim->cap, n_fric, sim->f_ids, sim->f_w,
+                   sim->inc_ptr, sim->inc_cursor, sim->inc_tiles, sim->inc, sim->inc_cap, &sim->sc_dev->flags);
 }
 
 int pair_grid(int cap) { return std::max(1, std::min((cap + 127) / 128, 148 * 8)); }
@@ -751,6 +924,7 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     if ((s = upload(sim, &ip, stb))) return fail(s, ""); S.stitch_b = ip;
     if ((s = upload(sim, &dp, stx))) return fail(s, ""); S.stitch_X = dp;
     if ((s = upload(sim, &ip, row_ptr))) return fail(s, ""); S.bsr_row = ip;
+    sim->h_row = row_ptr;
     if ((s = upload(sim, &ip, col))) return fail(s, ""); S.bsr_col = ip;
     if ((s = upload(sim, &ip, diag))) return fail(s, ""); S.bsr_diag = ip;
     if ((s = upload(sim, &sim->Hconst, Hc))) return fail(s, "");
@@ -780,8 +954,7 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     }
     if ((s = upload(sim, &sim->xk, xk))) return fail(s, "");
   }
-  double** bufs3n[] = {&sim->z_t, &sim->z_tilde, &sim->z_trial, &sim->g, &sim->gdir, &sim->rhs, &sim->p,
-                       &sim->r, &sim->zz, &sim->pp, &sim->y, &sim->svec};
+  double** bufs3n[] = {&sim->z_t, &sim->z_tilde, &sim->z_trial, &sim->g, &sim->gdir, &sim->rhs, &sim->p, &sim->y};
   for (auto b : bufs3n)
     if ((s = dalloc(sim, b, ndof))) return fail(s, "");
   double** bufsk[] = {&sim->xk_t, &sim->xk_hat, &sim->xk_trial, &sim->pD};
@@ -796,16 +969,25 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   if ((s = dalloc(sim, &sim->Dinv, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->T_dev, 12 * (size_t)std::max(nkb, 1)))) return fail(s, "");
   if (P.precision != IPC_PREC_FP64 && P.precision != IPC_PREC_MIXED) return fail(IPC_ERR_ARG, "unknown precision");
-  sim->pcg_grid_max_d = pcg_max_blocks(PCG_THREADS);
-  sim->pcg_grid_max_f = pcg_max_blocks_fp32(PCG_THREADS);
-  sim->pcg_grid_max = std::max(sim->pcg_grid_max_d, sim->pcg_grid_max_f);  // sizes the partial-sum buffer
-  if (P.precision == IPC_PREC_MIXED) {
-    if ((s = dalloc(sim, &sim->val32, 9 * (size_t)nnzb))) return fail(s, "");
-    if ((s = dalloc(sim, &sim->Dinv32, 9 * (size_t)n_nodes))) return fail(s, "");
-    if ((s = dalloc(sim, &sim->z32, (size_t)ndof))) return fail(s, "");
-    if ((s = dalloc(sim, &sim->p32, (size_t)ndof))) return fail(s, "");
+  {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sim->pcg_grid_max = 4 * sms;  // sizes the partial-sum buffer: up to four CTAs per SM
   }
-  if ((s = dalloc(sim, &sim->partial, 5 * (size_t)sim->pcg_grid_max))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->pcg_op, 9 * (size_t)nnzb))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->pcg_vec, 9 * (size_t)ndof))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->inc_ptr, (size_t)nf + nab + 1))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->inc_cursor, (size_t)nf + nab + 1))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->inc_tiles, (size_t)(nf + nab + 1) / 4096 + 1))) return fail(s, "");
+  if (nab) {
+    if ((s = dalloc(sim, &sim->abd_ptr, (size_t)nab + 1))) return fail(s, "");
+    if ((s = dalloc(sim, &sim->abd_cursor, (size_t)nab + 1))) return fail(s, "");
+    if ((s = grow_abd_list(sim, 4096))) return fail(s, "");
+  }
+  if (P.precision == IPC_PREC_MIXED)
+    if ((s = dalloc(sim, &sim->Dinv32, 9 * (size_t)n_nodes))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->partial, pcg_partial_doubles(sim->pcg_grid_max)))) return fail(s, "");
   if ((s = dalloc(sim, &sim->sc_dev, 1))) return fail(s, "");
   if (cudaMallocHost((void**)&sim->sc_host, sizeof(ipcsim::Scal)) != cudaSuccess) return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
   std::memset(sim->sc_host, 0, sizeof(ipcsim::Scal));
@@ -1052,29 +1234,22 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
                       P.eps_v * dt, dt2, 2, sim->g, sim->f_Hu, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[3]);
       prof_end(sim, PROF_FRICTION);
     }
+    build_abd_contact(sim, P.mu > 0 ? sim->n_fric : 0);
     launch_rhs(cs, ndof, sim->g, sim->gdir, sim->rhs);
     launch_dinv(cs, sim->n_nodes, S.bsr_diag, sim->Hval, sim->Dc, sim->Dinv);
     // ---- PCG
-    PcgArgs a{};
-    a.S = S; a.n_nodes = sim->n_nodes; a.row = S.bsr_row; a.col = S.bsr_col; a.val = sim->Hval;
-    a.rec = sim->rec; a.n_pairs = &sim->sc_dev->n_pairs; a.cap = sim->cap; a.pairH = sim->pairH;
-    a.n_fric = P.mu > 0 ? sim->n_fric : 0; a.f_ids = sim->f_ids; a.f_w = sim->f_w; a.f_Hu = sim->f_Hu;
-    a.Dinv = sim->Dinv; a.b = sim->rhs; a.x = sim->p; a.r = sim->r; a.z = sim->zz; a.p = sim->pp; a.y = sim->y;
-    a.s = sim->svec;
-    a.partial = sim->partial; a.rtol = P.pcg_rtol; a.max_iter = max_pcg;
-    a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
-    if (P.precision == IPC_PREC_MIXED) {
-      a.fp32 = 1;
-      a.val32 = sim->val32; a.pairH32 = sim->pairH32; a.f_Hu32 = sim->fHu32; a.Dinv32 = sim->Dinv32;
-      a.z32 = sim->z32; a.p32 = sim->p32;
-      launch_to_float(cs, 9 * (size_t)sim->nnzb, sim->Hval, sim->val32);
+    const int fp32 = P.precision == IPC_PREC_MIXED ? 1 : 0;
+    const int n_fric_it = P.mu > 0 ? sim->n_fric : 0;
+    prof_begin(sim, PROF_PCG_SETUP);
+    build_incidence(sim, n_fric_it);
+    if (fp32) {
       launch_to_float(cs, 144 * (size_t)sim->cap, sim->pairH, sim->pairH32, &sim->sc_dev->n_pairs, 144);
-      if (a.n_fric) launch_to_float(cs, 9 * (size_t)a.n_fric, sim->f_Hu, sim->fHu32);
+      if (n_fric_it) launch_to_float(cs, 9 * (size_t)n_fric_it, sim->f_Hu, sim->fHu32);
       launch_to_float(cs, 9 * (size_t)sim->n_nodes, sim->Dinv, sim->Dinv32);
     }
     if (sim->autotune_pending) {
       // time every launch shape on this system (same right-hand side, same tolerance) and keep the fastest
-      const int rowgs[4] = {2, 4, 8, 16};
+      const int rowgs[4] = {1, 2, 4, 8};
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
@@ -1084,11 +1259,11 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
         for (int ri = 0; ri < 4; ++ri) {
           sim->tune_rowg = rowgs[ri];
           sim->tune_bps = bi + 1;
-          int g = pcg_grid(sim, P.precision == IPC_PREC_MIXED);
           float ms = 0.f;
+          if ((s = pcg_prepare(sim, fp32))) return s;
           for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, cs);
-            CUDA_TRY(launch_pcg(cs, g, PCG_THREADS, a, sim->tune_rowg));
+            if ((s = pcg_run(sim, fp32, P.pcg_rtol, max_pcg, n_fric_it))) return s;
             cudaEventRecord(e1, cs);
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms, e0, e1);
@@ -1102,9 +1277,10 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
       sim->tune_bps = best_b;
       sim->autotune_pending = false;
     }
-    int grid = pcg_grid(sim, P.precision == IPC_PREC_MIXED);
+    if ((s = pcg_prepare(sim, fp32))) return s;
+    prof_end(sim, PROF_PCG_SETUP);
     prof_begin(sim, PROF_PCG);
-    CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a, sim->tune_rowg));
+    if ((s = pcg_run(sim, fp32, P.pcg_rtol, max_pcg, n_fric_it))) return s;
     prof_end(sim, PROF_PCG);
     // ---- direction norms and CCD bound
     launch_pnorm(cs, ndof, sim->p, nk3, sim->pD, sim->sc_dev->pn);
@@ -1124,13 +1300,25 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     CUDA_TRY(cudaGetLastError());
     const ipcsim::Scal& h = *sim->sc_host;
     if (h.flags & ERRF_BVH) return finish(IPC_ERR_BVH_OVERFLOW, "BVH traversal stack overflow");
+    if (h.flags & ERRF_INC) return finish(IPC_ERR_CUDA, "contact incidence list overflow");
+    if (h.flags & ERRF_ABD) {
+      // the ABD coupling list overflowed: grow it and redo this iteration
+      if ((s = grow_abd_list(sim, 4 * sim->abd_cap))) return finish(s, "ABD coupling list growth failed");
+      continue;
+    }
     if (h.n_pairs > sim->cap) {
-      if ((s = grow_pairs(sim, h.n_pairs))) return finish(s, "pair buffer growth failed");
+      if ((s = grow_pairs(sim, h.n_pairs))) {
+        const std::string m = sim->err;
+        return finish(s, m.c_str());
+      }
       rec_current = false;
       continue;
     }
     if (sweep && h.n_cand > sim->ccap) {
-      if ((s = grow_cand(sim, h.n_cand))) return finish(s, "candidate buffer growth failed");
+      if ((s = grow_cand(sim, h.n_cand))) {
+        const std::string m = sim->err;
+        return finish(s, m.c_str());
+      }
       continue;
     }
     sim->cand_valid = sweep;
@@ -1315,18 +1503,28 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     if (sim->sc_host->n_pairs > sim->cap) { if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s; continue; }
     break;
   }
+  for (int tries = 0;; ++tries) {
+    // the ABD coupling list of the unprojected Hessian (grown until it fits)
+    CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), cs));
+    if (tries > 0) {
+      // a retry: rebuild the BSR values without the partial contact blocks of the overflowed pass
+      CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
+      launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
+      launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g, sim->Hval, &sim->sc_dev->E[5]);
+    }
+    build_abd_contact(sim, P.mu > 0 ? sim->n_fric : 0);
+    if ((s = sync_scalars(sim))) return s;
+    if (!(sim->sc_host->flags & ERRF_ABD)) break;
+    if (tries > 8 || (s = grow_abd_list(sim, 4 * sim->abd_cap))) { sim->err = "ABD coupling list growth failed"; return IPC_ERR_CAPACITY; }
+  }
   launch_dinv(cs, sim->n_nodes, S.bsr_diag, sim->Hval, sim->Dc, sim->Dinv);
   launch_axpy(cs, ndof, gz_next, 1.0 / dt, gzd_next, sim->rhs);
-  PcgArgs a{};
-  a.S = S; a.n_nodes = sim->n_nodes; a.row = S.bsr_row; a.col = S.bsr_col; a.val = sim->Hval;
-  a.rec = sim->rec; a.n_pairs = &sim->sc_dev->n_pairs; a.cap = sim->cap; a.pairH = sim->pairH;
-  a.n_fric = P.mu > 0 ? sim->n_fric : 0; a.f_ids = sim->f_ids; a.f_w = sim->f_w; a.f_Hu = sim->f_Hu;
-  a.Dinv = sim->Dinv; a.b = sim->rhs; a.x = sim->p; a.r = sim->r; a.z = sim->zz; a.p = sim->pp; a.y = sim->y;
-  a.s = sim->svec;
-  a.partial = sim->partial; a.rtol = 1e-12; a.max_iter = 10 * ndof + 1000;
-  a.out = sim->sc_dev->pcg_out; a.res = &sim->sc_dev->pcg_res;
-  int grid = pcg_grid(sim, false);
-  CUDA_TRY(launch_pcg(cs, grid, PCG_THREADS, a, sim->tune_rowg));
+  {
+    const int n_fric_adj = P.mu > 0 ? sim->n_fric : 0;
+    build_incidence(sim, n_fric_adj);
+    if ((s = pcg_prepare(sim, 0))) return s;
+    if ((s = pcg_run(sim, 0, 1e-12, 10 * ndof + 1000, n_fric_adj))) return s;
+  }
   // contractions with lam (= sim->p)
   if (glogE) launch_theta_grad(cs, S, sim->xv, sim->p, dt2, glogE);
   double* tmp = sim->y;  // scratch: friction gradient, then M lam
@@ -1342,20 +1540,30 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   if (P.mu > 0) launch_friction_apply(cs, S, sim->n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->p, gz_t);
   if ((s = sync_scalars(sim))) return s;
   CUDA_TRY(cudaGetLastError());
+  if (sim->sc_host->pcg_out[1] == 3 && !(sim->sc_host->pcg_res <= 1e-10)) {
+    sim->err = "adjoint PCG stopped at relative residual " + std::to_string(sim->sc_host->pcg_res);
+    return IPC_ERR_PCG;
+  }
+  if (sim->sc_host->pcg_out[1] == 3) sim->sc_host->pcg_out[1] = 0;
   if (sim->sc_host->pcg_out[1]) { sim->err = "adjoint PCG breakdown (Hessian not positive definite)"; return IPC_ERR_PCG; }
   if (gmu_host && P.mu > 0) *gmu_host += -sim->sc_host->E[6] / P.mu;
   return IPC_OK;
 }
 
-ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out2, float* ms8) {
+ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out4, float* ms8) {
   if (!sim) return IPC_ERR_ARG;
   if (rowg > 0) {
-    if (rowg != 2 && rowg != 4 && rowg != 8 && rowg != 16) { sim->err = "rowg must be 2, 4, 8 or 16"; return IPC_ERR_ARG; }
+    if (rowg != 1 && rowg != 2 && rowg != 4 && rowg != 8) { sim->err = "rowg must be 1, 2, 4 or 8"; return IPC_ERR_ARG; }
     sim->tune_rowg = rowg;
   }
-  if (blocks_per_sm >= 0) sim->tune_bps = std::min(blocks_per_sm, 2);
+  if (blocks_per_sm > 0) sim->tune_bps = std::min(blocks_per_sm, 4);
   if (autotune_next_step) sim->autotune_pending = true;
-  if (out2) { out2[0] = sim->tune_rowg; out2[1] = sim->tune_bps; }
+  if (out4) {
+    out4[0] = sim->tune_rowg;
+    out4[1] = sim->tune_bps;
+    out4[2] = sim->plan.grid;
+    out4[3] = sim->plan_resident ? 1 : 0;
+  }
   if (ms8) std::memcpy(ms8, sim->tune_ms, sizeof(sim->tune_ms));
   return IPC_OK;
 }

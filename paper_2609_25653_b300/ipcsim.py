@@ -86,7 +86,7 @@ SIGNATURES = {
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
 }
 
-PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "unused"]
+PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "pcg_setup"]
 
 
 def load():
@@ -339,12 +339,18 @@ class Simulator:
                                        _ptr(glogE), C.byref(gmu)))
         return gz_t, gzd_t, glogE, gmu.value
 
-    def tuning(self, rowg=0, blocks_per_sm=-1, autotune_next_step=False):
+    def tuning(self, rowg=0, blocks_per_sm=0, autotune_next_step=False):
         """Set / read the PCG launch shape; returns ((rowg, blocks_per_sm), last autotuning times in ms)."""
-        out = (C.c_int * 2)()
+        out = (C.c_int * 4)()
         ms = (C.c_float * 8)()
         self._check(load().sim_tuning(self.h, int(rowg), int(blocks_per_sm), int(bool(autotune_next_step)), out, ms))
         return (out[0], out[1]), list(ms)
+
+    def pcg_layout(self):
+        """(CTAs, operator resident in shared memory) of the last PCG launch."""
+        out = (C.c_int * 4)()
+        self._check(load().sim_tuning(self.h, 0, 0, 0, out, None))
+        return out[2], bool(out[3])
 
     def profile(self, enable=True):
         self._check(load().sim_profile(self.h, int(enable)))

@@ -647,3 +647,62 @@ def batched_grasps(n_scenes: int = 64, seed0: int = 0, n_steps: int = 200, tets_
         # scenes sit on an 8-wide grid, `spacing` apart, so that their ground quads do not overlap
         out.append(translate_scene(sc, ((k % 8) * spacing, (k // 8) * spacing, 0.0)) if spacing else sc)
     return out
+
+
+def voxel_cylinder(r, h, cell, z0=0.0):
+    """Tet mesh of a vertical cylinder (radius r, height h, bottom at z0): the
+    cells of a regular grid that lie wholly inside the circle, 6 tets each."""
+    n = int(math.ceil(2 * r / cell))
+    nz = int(round(h / cell))
+    X, T = grid_tets((-0.5 * n * cell, -0.5 * n * cell, z0), cell, n, n, nz)
+    ci = np.arange(n * n * nz)
+    ii, jj = ci % n, (ci // n) % n
+    xc = (ii + 0.5) * cell - 0.5 * n * cell
+    yc = (jj + 0.5) * cell - 0.5 * n * cell
+    ax, ay = np.abs(xc) + 0.5 * cell, np.abs(yc) + 0.5 * cell
+    keep = ax * ax + ay * ay <= r * r
+    T = T[np.repeat(keep, 6)]
+    used = np.unique(T)
+    remap = -np.ones(len(X), np.int64)
+    remap[used] = np.arange(len(used))
+    return X[used], remap[T].astype(np.int32)
+
+
+def soft_gripper_cylinder(seed: int = 0, n_steps: int = 300, tip_cell=1.25e-3, cyl_cell=2.15e-3,
+                          close_per_step=0.05e-3, **param_overrides) -> dict:
+    """The two fin-ray fingertips of the arm-gripper grasp squeeze a deformable
+    Neo-Hookean cylinder (r = 25 mm, h = 60 mm, about 60k tets, E = 5e4 Pa,
+    nu = 0.4, rho = 1100 assumed) resting on the ground quad; no arm links and
+    no rigid object.  The fingertips start 0.8 mm from the cylinder; the
+    finger bases close `close_per_step` (0.05 mm) per step for 200 steps
+    (10 mm in all), then hold.  dt = 5 ms, dhat = 0.5 mm, mu = 0.6."""
+    mm = 1e-3
+    sc = arm_gripper_grasp(seed, n_steps=n_steps, tip_cell=tip_cell, link_tris=8, obj_tris=1000, **param_overrides)
+    cX, cT = voxel_cylinder(25 * mm, 60 * mm, cyl_cell, z0=0.3 * mm)
+    n_tip_v, n_tip_t = len(sc["fem_X"]), len(sc["fem_tets"])
+    # move the fingertips (and their bases) in to 0.8 mm from the voxel surface
+    shift = 25 * mm - float(np.abs(cX[:, 1]).max())
+    tX = sc["fem_X"].copy()
+    tX[:, 1] -= np.sign(tX[:, 1]) * shift
+    X = np.concatenate([tX, cX])
+    tets = np.concatenate([sc["fem_tets"], cT + n_tip_v])
+    nt_c = len(cT)
+    sc["fem_X"] = X
+    sc["fem_tets"] = tets
+    sc["fem_logE"] = np.concatenate([sc["fem_logE"], np.full(nt_c, math.log(5e4))])
+    sc["fem_nu"] = np.concatenate([sc["fem_nu"], np.full(nt_c, 0.4)])
+    sc["fem_rho"] = np.concatenate([sc["fem_rho"], np.full(nt_c, 1100.0)])
+    sc["fem_body"] = np.concatenate([sc["fem_body"], np.full(nt_c, 2, np.int32)])
+    sc["abd"] = []
+    sc["kin"] = sc["kin"][:3]
+    kin_T = sc["kin_T"][:, :3].copy()
+    b, gap = 25 * mm - shift, 0.8 * mm
+    z_top = kin_T[0, 1, 2, 3]
+    for s in range(n_steps + 1):
+        close = min(s, 200) * close_per_step
+        kin_T[s, 1, :, 3] = (0.0, b + gap - close, z_top)
+        kin_T[s, 2, :, 3] = (0.0, -(b + gap - close), z_top)
+    sc["kin_T"] = kin_T
+    sc["name"] = f"soft_gripper_cylinder_{len(tets)}tet"
+    assert n_tip_t + nt_c == len(tets)
+    return sc

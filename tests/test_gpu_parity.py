@@ -342,3 +342,20 @@ def test_sweep_candidates_match_all_pairs_steps(name):
         xa, _, qa, _ = a.get_state()
         xb, _, qb, _ = b.get_state()
         assert np.max(np.abs(xa - xb)) <= 1e-8 * a.L
+
+
+def test_soft_cylinder_mixed_within_1e5():
+    """Two fingertips squeezing a deformable cylinder (about 110k tets in all): the FP32-iteration path
+    stays within 1e-5 of the bbox diagonal of the FP64 path while contact builds up."""
+    from paper_2609_25653_b300 import ipcsim
+    sc = scenes.soft_gripper_cylinder(0, n_steps=8, close_per_step=0.25e-3)
+    a = _sim(sc)
+    b = _sim(sc, precision=ipcsim.PREC_MIXED)
+    for k in range(8):
+        sa = a.step()
+        sb = b.step()
+        assert sa["status"] == 0 and sb["status"] == 0
+        xa = a.get_state()[0]
+        xb = b.get_state()[0]
+        assert np.max(np.abs(xa - xb)) / a.L < 1e-5
+    assert sa["n_pairs_max"] > 0 and sa["min_dist"] > 0 and sb["min_dist"] > 0
