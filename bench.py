@@ -8,9 +8,10 @@ the timed events.  Each step is timed with CUDA events on the simulator's
 stream; `value` = steps / sum of step times (max over ranks for N > 1, each
 rank running its own replica: a single scene does not shard).
 
-`e2e` times the same steps through the public API with host buffers: the
-kinematic transforms go host -> device and the positions come back to host
-memory every step, inside the timed region.
+`e2e` replays the same steps (from the state saved before the timed steps)
+through the public API with host buffers: the kinematic transforms go host ->
+device and the positions come back to host memory every step, inside the
+timed region.
 
 `--impl reference` times the plain FP64 CPU oracle on the same workload.
 """
@@ -126,17 +127,20 @@ class ClockSampler:
 def pcg_bytes(work, sim, fp32, resident, launches):
     """Algorithmic bytes the PCG kernel has to move, summed over the recorded launches.
 
-    Per iteration and node: the seven node-local iteration vectors (z, q, s, p,
-    r, u, w) read and written, m read and the next m written, and x (FP64)
-    read and written: 48 elements of the iteration type + 48 B.  The operator
-    (9 elements + 4 B column index per BSR block) and the 3x3 preconditioner
-    blocks (9 elements per node) once per iteration when they stream from
-    memory, once per launch when every CTA keeps its rows in shared memory.
-    Per barrier pair and iteration its 144-element block and 32 B record; per
-    friction pair its 9-element block, ids and weights (48 B)."""
+    FP64 (pipelined CG, one barrier per iteration), per iteration and node: the
+    seven node-local vectors (z, q, s, p, r, u, w) and m read and written, x
+    read and written: 54 doubles = 432 B.  Mixed precision (FP32 CG inside FP64
+    refinement), per iteration and node: u read and w written in the product
+    phase, u, w, p, s, d, r read and p, s, d, r, u written in the update phase:
+    39 floats = 156 B.  The operator (9 elements + 4 B column index per BSR
+    block) and the 3x3 preconditioner blocks (9 elements per node) once per
+    iteration when they stream from memory, once per launch when every CTA
+    keeps its rows in shared memory.  Per barrier pair and iteration its
+    144-element block and 32 B record; per friction pair its 9-element block,
+    ids and weights (48 B)."""
     e = 4 if fp32 else 8
     n = sim.n_nodes
-    nodes = n * (48 * e + 48)
+    nodes = n * (156 if fp32 else 432)
     op = work["bsr_blocks"] * (9 * e + 4) + 9 * n * e
     per_iter = nodes + (0 if resident else op)
     return (work["pcg_iters"] * per_iter + (launches * op if resident else 0)
@@ -167,7 +171,7 @@ def run_ours(args):
         sc = wl
         sim = ipcsim.Simulator(sc, precision=prec, stream=stream)
     n_sc = len(wl) if batched else 1
-    n_total = args.warmup + args.steps + args.steps + 1
+    n_total = args.warmup + args.steps + 1
     if sc["kin_T"].shape[0] < n_total + 1 and len(sc.get("kin", [])):
         raise SystemExit("workload trajectory too short for the requested steps")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -181,6 +185,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    # state at the start of the timed steps: the end-to-end leg replays the same steps from it
+    snap = sim.get_state()
+    snap_index = sim.step_index
     sim.profile(True)
     launches0 = ipcsim.kernel_launches()
     times = []
@@ -210,15 +217,23 @@ def run_ours(args):
         total_ms = float(t.item())
     value = world * args.steps * n_sc / (total_ms / 1e3)
 
-    # e2e through the public API with host buffers (transforms in, positions out)
+    # e2e through the public API with host buffers (transforms in, positions out), over the same steps
+    sim.set_state(*snap)
+    if sim.nkb:
+        sim.set_kinematic(sc["kin_T"][snap_index])
+    sim.step_index = snap_index
     x_host = np.zeros((sim.nf, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    e2e_steps_ms = []
     for _ in range(args.steps):
+        t1 = time.perf_counter()
         sim.step()
         x_host[:] = sim.get_state()[0]
+        e2e_steps_ms.append(round((time.perf_counter() - t1) * 1e3, 2))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    print("e2e step ms:", e2e_steps_ms, file=sys.stderr)
     if world > 1:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -38,10 +38,12 @@ struct PcgArgs {
   const double* f_w;
   const int* inc_ptr;        // (nf + nab + 1) contact incidences per owner
   const int2* inc;           // (code, owner) ordered by owner; code = pair << 3 | friction << 2 | slot
-  int max_rows;              // most FEM rows of one CTA (sizes the shared contact sums)
+  int max_rows;              // most FEM rows of one CTA
+  int acc_doubles;           // doubles of shared memory reserved for the row products
   const int* abd_ptr;        // (nab + 1) contact coupling blocks per ABD body
   const int* abd_ent;        // column node << 2 | pseudo-node row
   const double* abd_val;     // (entries, 9)
+  const float* abd_val32;    // FP32 copy (mixed precision)
   long long abd_cap;
   const double* b;
   double* x;
@@ -62,6 +64,7 @@ struct PcgPlan {
   int grid = 0, n_fem_ctas = 0, n_abd_ctas = 0;
   std::vector<int> seg;      // FEM CTA row boundaries, then nf + 4 b for every ABD body
   int max_rows = 0, max_blocks = 0;
+  int acc_doubles = 0;       // row products in shared memory: 3 per FEM row, 12 per ABD body of a CTA
 };
 
 

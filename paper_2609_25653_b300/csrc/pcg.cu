@@ -172,8 +172,9 @@ void launch_incidence(cudaStream_t st, const DevScene& S, const int* rec, const 
 // ABD bodies in contact.  For each pair, the part of J^T H J that couples the
 // pseudo-nodes of one body with themselves is added into that body's 4x4 BSR
 // grid, and the part that couples them with any other node becomes a list of
-// 3x3 blocks per body (entry code = column node << 2 | pseudo-node row t), so
-// that the ABD rows of the PCG need one gather per block.  Once per Newton
+// 3x3 blocks per body (entry code = column node << 2 | pseudo-node row t; the
+// rows t = 0..3 of one column are consecutive, so t = (entry - first entry of
+// the body) mod 4), so that the ABD rows of the PCG need one gather per block.  Once per Newton
 // iteration, after the pair Hessians and before the preconditioner.
 // ---------------------------------------------------------------------------
 struct PairSlots {
@@ -292,8 +293,8 @@ __global__ void k_abd_contact(DevScene S, const int* __restrict__ rec, const int
           for (int jj = 0; jj < j; ++jj) fb = fb && P.body[jj] != P.body[j];
           if (!fb) continue;
           const int b2 = P.body[j];
-          for (int t = 0; t < 4; ++t)
-            for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 4; ++u)
+            for (int t = 0; t < 4; ++t) {  // t innermost: entry e of body b has t = (e - ptr[b]) & 3
               double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
               for (int q = 0; q < 4; ++q) {
                 if (P.body[q] != b) continue;
@@ -382,48 +383,48 @@ __device__ inline bool pcg_ok(const PcgArgs& a, bool cond, int site) {
   return false;
 }
 
-// v gathered at a vertex through x = J z (zero for kinematic vertices), in FP64
-template <typename V>
-__device__ inline void gather_vertex(const PcgArgs& a, const V* v, int vert, double& g0, double& g1, double& g2) {
+// v gathered at a vertex through x = J z (zero for kinematic vertices), in the accumulation type A
+template <typename V, typename A>
+__device__ inline void gather_vertex(const PcgArgs& a, const V* v, int vert, A& g0, A& g1, A& g2) {
   const DevScene& S = a.S;
-  if (!pcg_ok(a, vert >= 0 && vert < S.nv, 4)) { g0 = g1 = g2 = 0.0; return; }
+  if (!pcg_ok(a, vert >= 0 && vert < S.nv, 4)) { g0 = g1 = g2 = A(0); return; }
   int kind = S.vkind[vert];
-  if (kind == VK_ABD && !pcg_ok(a, S.vabd[vert] >= 0 && S.vabd[vert] < S.nab, 7)) { g0 = g1 = g2 = 0.0; return; }
+  if (kind == VK_ABD && !pcg_ok(a, S.vabd[vert] >= 0 && S.vabd[vert] < S.nab, 7)) { g0 = g1 = g2 = A(0); return; }
   if (kind == VK_FEM) {
-    g0 = v[3 * vert]; g1 = v[3 * vert + 1]; g2 = v[3 * vert + 2];
+    g0 = (A)v[3 * vert]; g1 = (A)v[3 * vert + 1]; g2 = (A)v[3 * vert + 2];
   } else if (kind == VK_ABD) {
     int n = S.nf + 4 * S.vabd[vert];
-    const double x0 = S.xbar[3 * vert], x1 = S.xbar[3 * vert + 1], x2 = S.xbar[3 * vert + 2];
+    const A x0 = (A)S.xbar[3 * vert], x1 = (A)S.xbar[3 * vert + 1], x2 = (A)S.xbar[3 * vert + 2];
     const V* b = v + 3 * n;
-    g0 = b[0] + x0 * b[3] + x1 * b[6] + x2 * b[9];
-    g1 = b[1] + x0 * b[4] + x1 * b[7] + x2 * b[10];
-    g2 = b[2] + x0 * b[5] + x1 * b[8] + x2 * b[11];
+    g0 = (A)b[0] + x0 * (A)b[3] + x1 * (A)b[6] + x2 * (A)b[9];
+    g1 = (A)b[1] + x0 * (A)b[4] + x1 * (A)b[7] + x2 * (A)b[10];
+    g2 = (A)b[2] + x0 * (A)b[5] + x1 * (A)b[8] + x2 * (A)b[11];
   } else {
-    g0 = g1 = g2 = 0.0;
+    g0 = g1 = g2 = A(0);
   }
 }
 
 // rows (3 slot .. 3 slot + 2) of one contact block applied to v (block values
-// stored as M, products and sums in FP64); returns the pair's vertex in that slot
-template <typename M, typename V>
-__device__ inline int contact_rows(const PcgArgs& a, const M* pairH, const M* fHu, const V* v, int code, double& y0,
-                                   double& y1, double& y2) {
+// stored as M, products and sums in A); returns the pair's vertex in that slot
+template <typename M, typename V, typename A>
+__device__ inline int contact_rows(const PcgArgs& a, const M* pairH, const M* fHu, const V* v, int code, A& y0, A& y1,
+                                   A& y2) {
   const int k = code >> 3, q = code & 3;
   if (!pcg_ok(a, (code & 4) ? (k >= 0 && k < a.n_fric) : (k >= 0 && k < a.cap), (code & 4) ? 5 : 3)) {
-    y0 = y1 = y2 = 0.0;
+    y0 = y1 = y2 = A(0);
     return -1;
   }
   if (!(code & 4)) {
     const int* r = a.rec + 8 * (size_t)k;
     const M* H = pairH + 144 * (size_t)k + 36 * q;
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    A t0 = A(0), t1 = A(0), t2 = A(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      double g0, g1, g2;
-      gather_vertex<V>(a, v, r[4 + j], g0, g1, g2);
-      t0 += (double)H[3 * j] * g0 + (double)H[3 * j + 1] * g1 + (double)H[3 * j + 2] * g2;
-      t1 += (double)H[12 + 3 * j] * g0 + (double)H[12 + 3 * j + 1] * g1 + (double)H[12 + 3 * j + 2] * g2;
-      t2 += (double)H[24 + 3 * j] * g0 + (double)H[24 + 3 * j + 1] * g1 + (double)H[24 + 3 * j + 2] * g2;
+      A g0, g1, g2;
+      gather_vertex<V, A>(a, v, r[4 + j], g0, g1, g2);
+      t0 = fma((A)H[3 * j], g0, fma((A)H[3 * j + 1], g1, fma((A)H[3 * j + 2], g2, t0)));
+      t1 = fma((A)H[12 + 3 * j], g0, fma((A)H[12 + 3 * j + 1], g1, fma((A)H[12 + 3 * j + 2], g2, t1)));
+      t2 = fma((A)H[24 + 3 * j], g0, fma((A)H[24 + 3 * j + 1], g1, fma((A)H[24 + 3 * j + 2], g2, t2)));
     }
     y0 = t0; y1 = t1; y2 = t2;
     return r[4 + q];
@@ -431,60 +432,126 @@ __device__ inline int contact_rows(const PcgArgs& a, const M* pairH, const M* fH
   const int* ids = a.f_ids + 4 * (size_t)k;
   const double* w = a.f_w + 4 * (size_t)k;
   const M* Hu = fHu + 9 * (size_t)k;
-  double U0 = 0.0, U1 = 0.0, U2 = 0.0;
+  A U0 = A(0), U1 = A(0), U2 = A(0);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (w[j] == 0.0) continue;
-    double g0, g1, g2;
-    gather_vertex<V>(a, v, ids[j], g0, g1, g2);
-    U0 += w[j] * g0; U1 += w[j] * g1; U2 += w[j] * g2;
+    A g0, g1, g2;
+    gather_vertex<V, A>(a, v, ids[j], g0, g1, g2);
+    const A wj = (A)w[j];
+    U0 = fma(wj, g0, U0); U1 = fma(wj, g1, U1); U2 = fma(wj, g2, U2);
   }
-  const double wq = w[q];
-  y0 = wq * ((double)Hu[0] * U0 + (double)Hu[1] * U1 + (double)Hu[2] * U2);
-  y1 = wq * ((double)Hu[3] * U0 + (double)Hu[4] * U1 + (double)Hu[5] * U2);
-  y2 = wq * ((double)Hu[6] * U0 + (double)Hu[7] * U1 + (double)Hu[8] * U2);
+  const A wq = (A)w[q];
+  y0 = wq * fma((A)Hu[0], U0, fma((A)Hu[1], U1, (A)Hu[2] * U2));
+  y1 = wq * fma((A)Hu[3], U0, fma((A)Hu[4], U1, (A)Hu[5] * U2));
+  y2 = wq * fma((A)Hu[6], U0, fma((A)Hu[7], U1, (A)Hu[8] * U2));
   return ids[q];
 }
 
-// Sum of N per-thread values over the CTA, left in out[0..N) (shared) for every thread.
-template <typename M, int N>
-__device__ inline void block_sum_n(M (&v)[N], M* red /* shared, 32 * N */, M* out /* shared, N */) {
+// ---------------------------------------------------------------------------
+// Reductions.  FP64 issue slots are scarce on this part (2 FMA / clock / SM),
+// so every sum over the CTA goes through shared memory and one warp: each
+// thread stores its values, warp 0 adds them in a fixed order (8 per lane and
+// value), then 5 shuffle levels.
+// ---------------------------------------------------------------------------
+constexpr int PCG_THREADS_MAX = 256;
+constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
+
+struct Shared {
+  double vals[3][PCG_THREADS_MAX];  // per-thread values of a CTA sum
+  double red[8][12];                // per-warp sums of the ABD rows
+  double out[12];                   // results, read by every thread
+  double scal[4];                   // scalars of an iteration (thread 0 -> all)
+  int action;
+};
+
+// Sum over the CTA of N <= 3 per-thread values of type T; results in
+// sh.out[0..N) (as FP64) for every thread.
+template <int N, typename T>
+__device__ inline void cta_sum(const T (&v)[N], Shared& sh) {
+  T (*vals)[PCG_THREADS_MAX] = reinterpret_cast<T (*)[PCG_THREADS_MAX]>(&sh.vals[0][0]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int j = 0; j < N; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
-  int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int j = 0; j < N; ++j) vals[j][threadIdx.x] = v[j];
   __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int j = 0; j < N; ++j) red[32 * j + wi] = v[j];
-  __syncthreads();
-  if (wi == 0) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      M b = lane < nw ? red[32 * j + lane] : M(0);
-      for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
-      if (lane == 0) out[j] = b;
+      T t = T(0);
+      for (int k = lane; k < (int)blockDim.x; k += 32) t += vals[j][k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) sh.out[j] = (double)t;
     }
   }
   __syncthreads();
 }
 
-constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
-
-struct Shared {
-  double red[32 * 12];
-  double out[12];
+// Sum over the CTAs of 3 partial sums of type T (one replica [3][grid]):
+// every CTA adds them in the same order, so all CTAs hold bit-identical
+// totals.  The loads of the first 2 x blockDim partials are issued early.
+template <typename T>
+struct Partials {
+  T v[3][2];
 };
+template <typename T>
+__device__ inline void load_partials(const T* rep, int nblk, Partials<T>& P) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int b = threadIdx.x + j * blockDim.x;
+    const bool in = b < nblk;
+    P.v[0][j] = in ? rep[b] : T(0);
+    P.v[1][j] = in ? rep[nblk + b] : T(0);
+    P.v[2][j] = in ? rep[2 * nblk + b] : T(0);
+  }
+}
+template <typename T>
+__device__ inline void totals3(const T* rep, int nblk, const Partials<T>& P, Shared& sh, double& t0, double& t1,
+                               double& t2) {
+  T v[3] = {P.v[0][0] + P.v[0][1], P.v[1][0] + P.v[1][1], P.v[2][0] + P.v[2][1]};
+  for (int b = threadIdx.x + 2 * blockDim.x; b < nblk; b += blockDim.x) {
+    v[0] += rep[b];
+    v[1] += rep[nblk + b];
+    v[2] += rep[2 * nblk + b];
+  }
+  cta_sum<3, T>(v, sh);
+  t0 = sh.out[0]; t1 = sh.out[1]; t2 = sh.out[2];
+  __syncthreads();
+}
 
-// Contact rows of the FEM segment [r0, r1): every incidence of the segment
-// (a contiguous range of the incidence list, ordered by owner) is handled by
-// one thread of the CTA and added to acc[3 (owner - r0) + c] in shared memory.
-// Every thread of the CTA must call it; acc is complete on return.
-template <typename M, typename V>
-__device__ inline void fem_contact(const PcgArgs& a, int r0, int r1, const M* pairH, const M* fHu, const V* v,
-                                   double* acc) {
-  for (int j = threadIdx.x; j < 3 * (r1 - r0); j += blockDim.x) acc[j] = 0.0;
+// This CTA's 3 partial sums, written to every replica.
+template <typename T>
+__device__ inline void write_partials(T* rep0 /* replica 0 of this parity, [3][grid] */, size_t rep_stride, int nblk,
+                                      Shared& sh, const T (&v)[3]) {
+  cta_sum<3, T>(v, sh);
+  if (threadIdx.x < 3 * PCG_REPLICAS) {
+    int rep = threadIdx.x / 3, j = threadIdx.x % 3;
+    rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = (T)sh.out[j];
+  }
+  __syncthreads();
+}
+
+__device__ inline double total_fp64(const double* rep /* [grid] */, int nblk, Shared& sh) {
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v[0] += rep[b];
+  cta_sum<1, double>(v, sh);
+  double t = sh.out[0];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Row products y = A v of the rows a CTA owns, left in shared memory.
+// ---------------------------------------------------------------------------
+// FEM segment [r0, r1): acc[3 (i - r0) + c].  The contact incidences of the
+// segment (a contiguous range of the owner-ordered incidence list) are spread
+// over all threads and added with shared-memory atomics; the BSR part of a
+// row is formed by a group of ROWG threads.  Every thread must call it.
+template <typename M, typename V, typename A, int ROWG>
+__device__ inline void fem_products(const PcgArgs& a, int r0, int r1, int k0, OpView<M> op, const int* colp,
+                                    const int* rowp /* relative to k0, indexed from r0; null: global row */,
+                                    const M* pairH, const M* fHu, const V* v, A* acc) {
+  for (int j = threadIdx.x; j < 3 * (r1 - r0); j += blockDim.x) acc[j] = A(0);
   __syncthreads();
   const int e0 = a.inc_ptr[r0], e1 = a.inc_ptr[r1];
 #pragma unroll 2
@@ -492,28 +559,18 @@ __device__ inline void fem_contact(const PcgArgs& a, int r0, int r1, const M* pa
     if (!pcg_ok(a, e >= 0 && e < a.inc_cap, 2)) break;
     const int2 ie = a.inc[e];
     if (!pcg_ok(a, ie.y >= r0 && ie.y < r1, 12)) continue;
-    double y0, y1, y2;
-    contact_rows<M, V>(a, pairH, fHu, v, ie.x, y0, y1, y2);
-    double* t = acc + 3 * (ie.y - r0);
+    A y0, y1, y2;
+    contact_rows<M, V, A>(a, pairH, fHu, v, ie.x, y0, y1, y2);
+    A* t = acc + 3 * (ie.y - r0);
     atomicAdd(t, y0);
     atomicAdd(t + 1, y1);
     atomicAdd(t + 2, y2);
   }
   __syncthreads();
-}
-
-// Rows of the FEM segment [r0, r1) of this CTA: y = (A v)_i for each row i,
-// the BSR part formed by a group of ROWG threads, plus the row's contact sum
-// from fem_contact, handed to fn(i, y0, y1, y2) on the group's first lane.
-// Every thread of the CTA must call it.
-template <typename M, typename V, int ROWG, typename F>
-__device__ inline void fem_rows(const PcgArgs& a, int r0, int r1, int k0, OpView<M> op, const int* colp,
-                                const int* rowp /* relative to k0, indexed from r0; null: global row */,
-                                const double* acc, const V* v, F&& fn) {
   const int groups = blockDim.x / ROWG, g = threadIdx.x / ROWG, gl = threadIdx.x & (ROWG - 1);
   for (int base = r0; base < r1; base += groups) {
     const int i = base + g;
-    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    A y0 = A(0), y1 = A(0), y2 = A(0);
     if (i < r1) {
       int kb, ke;
       if (rowp) { kb = rowp[i - r0]; ke = rowp[i - r0 + 1]; }
@@ -522,12 +579,12 @@ __device__ inline void fem_rows(const PcgArgs& a, int r0, int r1, int k0, OpView
       for (int kk = kb + gl; kk < ke; kk += ROWG) {
         const int j = colp[kk];
         if (!pcg_ok(a, j >= 0 && j < a.n_nodes, 1)) continue;
-        const double v0 = v[3 * j], v1 = v[3 * j + 1], v2 = v[3 * j + 2];
-        const M* A = op.base + (size_t)kk * op.sk;
+        const A v0 = (A)v[3 * j], v1 = (A)v[3 * j + 1], v2 = (A)v[3 * j + 2];
+        const M* H = op.base + (size_t)kk * op.sk;
         const int sq = op.sq;
-        y0 += (double)A[0] * v0 + (double)A[sq] * v1 + (double)A[2 * sq] * v2;
-        y1 += (double)A[3 * sq] * v0 + (double)A[4 * sq] * v1 + (double)A[5 * sq] * v2;
-        y2 += (double)A[6 * sq] * v0 + (double)A[7 * sq] * v1 + (double)A[8 * sq] * v2;
+        y0 = fma((A)H[0], v0, fma((A)H[sq], v1, fma((A)H[2 * sq], v2, y0)));
+        y1 = fma((A)H[3 * sq], v0, fma((A)H[4 * sq], v1, fma((A)H[5 * sq], v2, y1)));
+        y2 = fma((A)H[6 * sq], v0, fma((A)H[7 * sq], v1, fma((A)H[8 * sq], v2, y2)));
       }
     }
 #pragma unroll
@@ -537,140 +594,91 @@ __device__ inline void fem_rows(const PcgArgs& a, int r0, int r1, int k0, OpView
       y2 += __shfl_down_sync(0xffffffffu, y2, o, ROWG);
     }
     if (i < r1 && gl == 0) {
-      const double* c = acc + 3 * (i - r0);
-      fn(i, y0 + c[0], y1 + c[1], y2 + c[2]);
+      A* c = acc + 3 * (i - r0);
+      c[0] += y0; c[1] += y1; c[2] += y2;
     }
   }
+  __syncthreads();
 }
 
-// Rows of the four pseudo-nodes of ABD body b, formed by the whole CTA (BSR
-// grid including the body's own contact, then its list of contact coupling
-// blocks) and handed to fn(node, y0, y1, y2) on threads 0..3.  Every thread
-// must call it.
-template <typename M, typename V, typename F>
-__device__ inline void abd_rows(const PcgArgs& a, int b, OpView<M> op, const int* colp, int nloc, const V* v,
-                                Shared& sh, F&& fn) {
+// The four pseudo-nodes of ABD body b: y into out12[3 t + c].  Thread tid
+// serves row t = tid mod 4 (BSR blocks of that row and coupling entries of
+// that row, strided by blockDim / 4), then lanes of equal t combine by three
+// shuffle levels and warps through shared memory.  Every thread must call it.
+template <typename M, typename V, typename A, typename L>
+__device__ inline void abd_products(const PcgArgs& a, int b, OpView<M> op, const int* colp, int nloc, const V* v,
+                                    const L* list_val, Shared& sh, A* out12) {
   const DevScene& S = a.S;
   const int r = S.nf + 4 * b, k0 = a.row[r];
-  const int rb1 = a.row[r + 1] - k0, rb2 = a.row[r + 2] - k0, rb3 = a.row[r + 3] - k0;
-  double acc[12];
-#pragma unroll
-  for (int j = 0; j < 12; ++j) acc[j] = 0.0;
-  for (int kk = threadIdx.x; kk < nloc; kk += blockDim.x) {
-    const int t = (kk >= rb1) + (kk >= rb2) + (kk >= rb3);
+  const int t = threadIdx.x & 3, slot = threadIdx.x >> 2, nslot = blockDim.x >> 2;
+  A y0 = A(0), y1 = A(0), y2 = A(0);
+  const int kb = a.row[r + t] - k0, ke = a.row[r + t + 1] - k0;
+  for (int kk = kb + slot; kk < ke; kk += nslot) {
     const int j = colp[kk];
     if (!pcg_ok(a, j >= 0 && j < a.n_nodes, 8)) continue;
-    const double v0 = v[3 * j], v1 = v[3 * j + 1], v2 = v[3 * j + 2];
-    const M* A = op.base + (size_t)kk * op.sk;
+    const A v0 = (A)v[3 * j], v1 = (A)v[3 * j + 1], v2 = (A)v[3 * j + 2];
+    const M* H = op.base + (size_t)kk * op.sk;
     const int sq = op.sq;
-    const double y0 = (double)A[0] * v0 + (double)A[sq] * v1 + (double)A[2 * sq] * v2;
-    const double y1 = (double)A[3 * sq] * v0 + (double)A[4 * sq] * v1 + (double)A[5 * sq] * v2;
-    const double y2 = (double)A[6 * sq] * v0 + (double)A[7 * sq] * v1 + (double)A[8 * sq] * v2;
-#pragma unroll
-    for (int tt = 0; tt < 4; ++tt)
-      if (tt == t) { acc[3 * tt] += y0; acc[3 * tt + 1] += y1; acc[3 * tt + 2] += y2; }
+    y0 = fma((A)H[0], v0, fma((A)H[sq], v1, fma((A)H[2 * sq], v2, y0)));
+    y1 = fma((A)H[3 * sq], v0, fma((A)H[4 * sq], v1, fma((A)H[5 * sq], v2, y1)));
+    y2 = fma((A)H[6 * sq], v0, fma((A)H[7 * sq], v1, fma((A)H[8 * sq], v2, y2)));
   }
-  const int e1 = a.abd_ptr[b + 1];
-#pragma unroll 2
-  for (int e = a.abd_ptr[b] + threadIdx.x; e < e1; e += blockDim.x) {
+  const int e0 = a.abd_ptr[b], e1 = a.abd_ptr[b + 1];
+#pragma unroll 4
+  for (int e = e0 + 4 * slot + t; e < e1; e += 4 * nslot) {
     if (!pcg_ok(a, e >= 0 && e < a.abd_cap, 9)) break;
-    const int code = a.abd_ent[e], t = code & 3, j = code >> 2;
-    if (!pcg_ok(a, j >= 0 && j < a.n_nodes, 10)) continue;
-    const double v0 = v[3 * j], v1 = v[3 * j + 1], v2 = v[3 * j + 2];
-    const double* B = a.abd_val + 9 * (size_t)e;
-    const double y0 = B[0] * v0 + B[1] * v1 + B[2] * v2;
-    const double y1 = B[3] * v0 + B[4] * v1 + B[5] * v2;
-    const double y2 = B[6] * v0 + B[7] * v1 + B[8] * v2;
+    const int code = a.abd_ent[e], j = code >> 2;
+    if (!pcg_ok(a, j >= 0 && j < a.n_nodes && (code & 3) == t, 10)) continue;
+    const A v0 = (A)v[3 * j], v1 = (A)v[3 * j + 1], v2 = (A)v[3 * j + 2];
+    const L* B = list_val + 9 * (size_t)e;
+    y0 = fma((A)B[0], v0, fma((A)B[1], v1, fma((A)B[2], v2, y0)));
+    y1 = fma((A)B[3], v0, fma((A)B[4], v1, fma((A)B[5], v2, y1)));
+    y2 = fma((A)B[6], v0, fma((A)B[7], v1, fma((A)B[8], v2, y2)));
+  }
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt)
-      if (tt == t) { acc[3 * tt] += y0; acc[3 * tt + 1] += y1; acc[3 * tt + 2] += y2; }
+  for (int o = 4; o < 32; o <<= 1) {
+    y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
   }
-  block_sum_n<double, 12>(acc, sh.red, sh.out);
-  if (threadIdx.x < 4) {
-    const int t = threadIdx.x;
-    fn(r + t, sh.out[3 * t], sh.out[3 * t + 1], sh.out[3 * t + 2]);
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane < 4) { sh.red[wi][3 * lane] = y0; sh.red[wi][3 * lane + 1] = y1; sh.red[wi][3 * lane + 2] = y2; }
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    A sum = A(0);
+    for (int w = 0; w < nw; ++w) sum += (A)sh.red[w][threadIdx.x];
+    out12[threadIdx.x] = sum;
   }
   __syncthreads();
 }
 
-// z = D v for one node's 3x3 block (D in the operator type, v and z in the vector type)
-template <typename M, typename T>
-__device__ inline void apply3(const M* D, T v0, T v1, T v2, T& z0, T& z1, T& z2) {
-  const M w0 = (M)v0, w1 = (M)v1, w2 = (M)v2;
-  z0 = (T)(D[0] * w0 + D[1] * w1 + D[2] * w2);
-  z1 = (T)(D[3] * w0 + D[4] * w1 + D[5] * w2);
-  z2 = (T)(D[6] * w0 + D[7] * w1 + D[8] * w2);
-}
-
-// Totals of the three per-CTA partial sums (one replica, summed in CTA order by
-// every CTA): the loads are issued by load_partials, the sums by totals3.
-struct Partials {
-  double v[3][2];
-};
-__device__ inline void load_partials(const double* rep /* [3][grid] */, int nblk, Partials& P) {
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int b = threadIdx.x + j * blockDim.x;
-    const bool in = b < nblk;
-    P.v[0][j] = in ? rep[b] : 0.0;
-    P.v[1][j] = in ? rep[nblk + b] : 0.0;
-    P.v[2][j] = in ? rep[2 * nblk + b] : 0.0;
-  }
-}
-__device__ inline void totals3(const double* rep, int nblk, const Partials& P, Shared& sh, double& t0, double& t1,
-                               double& t2) {
-  double v[3] = {P.v[0][0] + P.v[0][1], P.v[1][0] + P.v[1][1], P.v[2][0] + P.v[2][1]};
-  for (int b = threadIdx.x + 2 * blockDim.x; b < nblk; b += blockDim.x) {
-    v[0] += rep[b];
-    v[1] += rep[nblk + b];
-    v[2] += rep[2 * nblk + b];
-  }
-  block_sum_n<double, 3>(v, sh.red, sh.out);
-  t0 = sh.out[0]; t1 = sh.out[1]; t2 = sh.out[2];
-  __syncthreads();
-}
-
-__device__ inline void write_partials(double* rep0 /* replica 0 of this parity, [3][grid] */, size_t rep_stride,
-                                      int nblk, Shared& sh, double (&v)[3]) {
-  block_sum_n<double, 3>(v, sh.red, sh.out);
-  if (threadIdx.x < 3 * PCG_REPLICAS) {
-    int rep = threadIdx.x / 3, j = threadIdx.x % 3;
-    rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = sh.out[j];
-  }
-  __syncthreads();
-}
-
-__device__ inline double total_fp64(const double* rep /* [grid] */, int nblk, double* red, double* out) {
-  double v[1] = {0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v[0] += rep[b];
-  block_sum_n<double, 1>(v, red, out);
-  double t = out[0];
-  __syncthreads();
-  return t;
+// z = D v for one node's 3x3 block (D stored as M, arithmetic in A)
+template <typename M, typename A>
+__device__ inline void apply3(const M* D, A v0, A v1, A v2, A& z0, A& z1, A& z2) {
+  z0 = fma((A)D[0], v0, fma((A)D[1], v1, (A)D[2] * v2));
+  z1 = fma((A)D[3], v0, fma((A)D[4], v1, (A)D[5] * v2));
+  z2 = fma((A)D[6], v0, fma((A)D[7], v1, (A)D[8] * v2));
 }
 
 // One solve.  M = double: every operation in FP64.  M = float (mixed
 // precision): the operator, the contact blocks and the preconditioner are
-// applied in FP32; the iteration vectors, the scalars and every dot product
-// stay FP64, and the FP64 residual b - A x is recomputed with the FP64
-// operator whenever the recurrence has converged, restarting the iteration
-// on it (iterative refinement).  Both forms restart the same way when the
-// recursive residual of the pipelined recurrences stagnates.
+// stored in FP32 and applied in FP64 arithmetic, so the recurrences see one
+// fixed linear operator; the vectors, scalars and dot products are FP64, and
+// the FP64 residual b - A x with the FP64 operator is formed whenever the
+// recurrence has converged or stagnates, restarting the iteration on it.
 template <typename M, int ROWG>
 __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
-  using T = double;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Shared sh;
-  constexpr bool F32 = sizeof(M) == 4;
   const DevScene& S = a.S;
   const int nblk = gridDim.x, cta = blockIdx.x;
   const bool fem_cta = cta < a.n_fem_ctas;
   const int nf = S.nf;
   const int n3 = 3 * a.n_nodes;
 
-  // ---- this CTA's rows and their operator view; shared memory: contact sums
-  //      of the rows, then (resident) operator planes, preconditioner, columns, row offsets
+  // ---- this CTA's rows; shared memory: row products (FEM: 3 per row, ABD: 12
+  //      per owned body), then (resident) operator planes, preconditioner, columns, row offsets
   int r0 = 0, r1 = 0, k0 = 0, nloc = 0;
   OpView<M> op{nullptr, 0, 1};
   const int* colp = nullptr;
@@ -684,7 +692,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     if (!pcg_ok(a, r0 >= 0 && r0 <= r1 && r1 <= nf, 11)) r0 = r1 = 0;
     k0 = a.row[r0]; nloc = a.row[r1] - k0;
     if (a.resident) {
-      M* s_op = (M*)(acc + 3 * (size_t)a.max_rows);
+      M* s_op = (M*)(acc + a.acc_doubles);
       M* s_dinv = s_op + 9 * (size_t)nloc;
       int* s_col = (int*)(s_dinv + 9 * (size_t)(r1 - r0));
       int* s_row = s_col + nloc;
@@ -704,9 +712,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   // preconditioner block of node i (owned by this CTA)
   auto Dof = [&](int i) -> const M* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvM + 9 * (size_t)i); };
 
-  Vecs<T> V;
+  Vecs<double> V;
   {
-    T* base = (T*)a.vec;
+    double* base = (double*)a.vec;
     V.r = base; V.u = base + n3; V.w = base + 2 * (size_t)n3; V.m0 = base + 3 * (size_t)n3;
     V.m1 = base + 4 * (size_t)n3; V.z = base + 5 * (size_t)n3; V.q = base + 6 * (size_t)n3;
     V.s = base + 7 * (size_t)n3; V.p = base + 8 * (size_t)n3;
@@ -721,31 +729,33 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   double* partD = partT + PCG_REPLICAS * repT;
   const int myrep = cta % PCG_REPLICAS;
 
-  // every row-forming pass over this CTA's owned rows: the iteration operator
-  // (assembled = false: layout copy of type M) or the assembled FP64 one
-  auto for_rows = [&](bool assembled, auto&& op_view_fem, const int* colp_fem, const int* rowp_fem, auto mtag,
-                      const auto* mat_pairH, const auto* mat_fHu, const auto* vin, auto&& fn) {
+  // y = A v for every owned row, left in shared memory (see row_y): the
+  // iteration operator (assembled = false: layout copy of type M) or the
+  // assembled FP64 one.  Every thread must call it.
+  auto products = [&](bool assembled, auto&& op_view_fem, const int* colp_fem, const int* rowp_fem, auto mtag,
+                      const auto* mat_pairH, const auto* mat_fHu, const double* vin) {
     using MM = decltype(mtag);
-    using VV = typename std::remove_cv<typename std::remove_pointer<decltype(vin)>::type>::type;
     if (fem_cta) {
-      fem_contact<MM, VV>(a, r0, r1, mat_pairH, mat_fHu, vin, acc);
-      fem_rows<MM, VV, ROWG>(a, r0, r1, k0, op_view_fem, colp_fem, rowp_fem, acc, vin, fn);
+      fem_products<MM, double, double, ROWG>(a, r0, r1, k0, op_view_fem, colp_fem, rowp_fem, mat_pairH, mat_fHu,
+                                             vin, acc);
     } else {
-      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas) {
+      int j = 0;
+      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j) {
         const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
         OpView<MM> ov = assembled ? OpView<MM>{(const MM*)a.val64 + 9 * (size_t)kb0, 1, 9}
                                   : OpView<MM>{(const MM*)a.op + 9 * (size_t)kb0, nl, 1};
-        abd_rows<MM, VV>(a, b, ov, a.col + kb0, nl, vin, sh, fn);
+        abd_products<MM, double, double, double>(a, b, ov, a.col + kb0, nl, vin, a.abd_val, sh, acc + 12 * j);
       }
     }
   };
-  // node-local pass over the nodes this CTA owns
+  // node-local pass over the owned nodes, with the node's row product from `products`
   auto for_nodes = [&](auto&& fn) {
     if (fem_cta) {
-      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) fn(i);
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) fn(i, acc + 3 * (i - r0));
     } else {
-      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas)
-        if (threadIdx.x < 4) fn(nf + 4 * b + threadIdx.x);
+      int j = 0;
+      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j)
+        if (threadIdx.x < 4) fn(nf + 4 * b + threadIdx.x, acc + 12 * j + 3 * threadIdx.x);
     }
   };
   // the FP64 operator (assembled layout) for the true residual
@@ -755,7 +765,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   // ---- x = 0, t64 = b, |b|^2
   {
     double v[1] = {0.0};
-    for_nodes([&](int i) {
+    for_nodes([&](int i, const double*) {
       for (int c = 0; c < 3; ++c) {
         double bv = a.b[3 * i + c];
         x[3 * i + c] = 0.0;
@@ -763,12 +773,12 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         v[0] += bv * bv;
       }
     });
-    block_sum_n<double, 1>(v, sh.red, sh.out);
+    cta_sum<1, double>(v, sh);
     if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
     __syncthreads();
   }
   grid.sync();
-  const double bb = total_fp64(partD + myrep * (size_t)nblk, nblk, sh.red, sh.out);
+  const double bb = total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
   int it = 0, status = 0, replaced = 0;
   if (!(bb > 0.0) || !isfinite(bb)) {
     if (threadIdx.x == 0 && cta == 0) {
@@ -783,55 +793,57 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
 
   // ---- (re)start from t64 = b - A x: r = sigma t64, u = M^-1 r, w = A u, m = M^-1 w
   auto restart = [&](int par) {
-    for_nodes([&](int i) {
-      T rv[3];
+    for_nodes([&](int i, const double*) {
+      double rv[3];
       for (int c = 0; c < 3; ++c) {
         const int q = 3 * i + c;
         rv[c] = sigma * t64[q];
         V.r[q] = rv[c];
-        V.z[q] = T(0); V.q[q] = T(0); V.s[q] = T(0); V.p[q] = T(0);
+        V.z[q] = 0.0; V.q[q] = 0.0; V.s[q] = 0.0; V.p[q] = 0.0;
       }
-      T u0, u1, u2;
-      apply3<M, T>(Dof(i), rv[0], rv[1], rv[2], u0, u1, u2);
+      double u0, u1, u2;
+      apply3<M, double>(Dof(i), rv[0], rv[1], rv[2], u0, u1, u2);
       V.u[3 * i] = u0; V.u[3 * i + 1] = u1; V.u[3 * i + 2] = u2;
     });
     grid.sync();
+    double* mcur = par ? V.m1 : V.m0;
+    products(false, op, colp, rowp, M(0), pairH, fHu, V.u);
     double pv[3] = {0.0, 0.0, 0.0};
-    T* mcur = par ? V.m1 : V.m0;
-    for_rows(false, op, colp, rowp, M(0), pairH, fHu, (const T*)V.u, [&](int i, double y0, double y1, double y2) {
+    for_nodes([&](int i, const double* y) {
       const int q = 3 * i;
-      V.w[q] = y0; V.w[q + 1] = y1; V.w[q + 2] = y2;
-      T m0, m1, m2;
-      apply3<M, T>(Dof(i), y0, y1, y2, m0, m1, m2);
+      V.w[q] = y[0]; V.w[q + 1] = y[1]; V.w[q + 2] = y[2];
+      double m0, m1, m2;
+      apply3<M, double>(Dof(i), y[0], y[1], y[2], m0, m1, m2);
       mcur[q] = m0; mcur[q + 1] = m1; mcur[q + 2] = m2;
-      const T u0 = V.u[q], u1 = V.u[q + 1], u2 = V.u[q + 2];
-      const T rr0 = V.r[q], rr1 = V.r[q + 1], rr2 = V.r[q + 2];
+      const double u0 = V.u[q], u1 = V.u[q + 1], u2 = V.u[q + 2];
+      const double rr0 = V.r[q], rr1 = V.r[q + 1], rr2 = V.r[q + 2];
       pv[0] += rr0 * u0 + rr1 * u1 + rr2 * u2;
-      pv[1] += y0 * u0 + y1 * u1 + y2 * u2;
+      pv[1] += y[0] * u0 + y[1] * u1 + y[2] * u2;
       pv[2] += rr0 * rr0 + rr1 * rr1 + rr2 * rr2;
     });
-    write_partials(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv);
+    write_partials<double>(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv);
     grid.sync();
   };
   // ---- the FP64 residual t64 = b - A64 x and its squared norm
   auto true_residual = [&]() -> double {
+    products(true, op64, col64, (const int*)nullptr, 0.0, a.pairH64, a.fHu64, x);
     double v[1] = {0.0};
-    for_rows(true, op64, col64, (const int*)nullptr, 0.0, a.pairH64, a.fHu64, (const double*)x,
-             [&](int i, double y0, double y1, double y2) {
-               const int q = 3 * i;
-               const double t0 = a.b[q] - y0, t1 = a.b[q + 1] - y1, t2 = a.b[q + 2] - y2;
-               t64[q] = t0; t64[q + 1] = t1; t64[q + 2] = t2;
-               v[0] += t0 * t0 + t1 * t1 + t2 * t2;
-             });
-    block_sum_n<double, 1>(v, sh.red, sh.out);
+    for_nodes([&](int i, const double* y) {
+      const int q = 3 * i;
+      const double t0 = a.b[q] - y[0], t1 = a.b[q + 1] - y[1], t2 = a.b[q + 2] - y[2];
+      t64[q] = t0; t64[q + 1] = t1; t64[q + 2] = t2;
+      v[0] += t0 * t0 + t1 * t1 + t2 * t2;
+    });
+    cta_sum<1, double>(v, sh);
     if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
     __syncthreads();
     grid.sync();
-    return total_fp64(partD + myrep * (size_t)nblk, nblk, sh.red, sh.out);
+    return total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
   };
 
   // inner target in the scaled units of the current restart: the requested
-  // reduction, but not below what the FP32 operator resolves
+  // reduction, but not below what the FP32-stored operator resolves
+  constexpr bool F32 = sizeof(M) == 4;
   auto inner_tol2 = [&]() -> double {
     double t = tol2_true * sigma * sigma;
     if (F32) t = fmax(t, 1e-12);
@@ -851,26 +863,46 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   for (;;) {
     const int par = it & 1;
     const double* rep = partT + (size_t)par * 3 * nblk + myrep * repT;
-    Partials P;
-    load_partials(rep, nblk, P);
+    double* mcur = par ? V.m1 : V.m0;
+    double* mnext = par ? V.m0 : V.m1;
+    // the partial sums are loaded first, the product n = A m is formed while they arrive
+    Partials<double> P;
+    load_partials<double>(rep, nblk, P);
+    products(false, op, colp, rowp, M(0), pairH, fHu, mcur);
     double gamma, delta, rr;
-    totals3(rep, nblk, P, sh, gamma, delta, rr);
-    if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) { status = 2; break; }
-    if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
-    double alpha = 0.0, beta = 0.0;
-    bool stop_inner = rr <= tol_in2 || it - it_best > STALL;
-    if (!stop_inner) {
-      if (fresh) {
-        if (!(delta > 0.0)) { status = 1; break; }
-        alpha = gamma / delta;
-      } else {
-        beta = gamma / gamma_old;
-        const double den = delta - beta * gamma / alpha_old;
-        if (!(den > 0.0)) stop_inner = true;  // lost conjugacy: refresh from the true residual
-        else alpha = gamma / den;
+    totals3<double>(rep, nblk, P, sh, gamma, delta, rr);
+    // the scalar recurrences run on thread 0 of every CTA (identical inputs,
+    // identical results) and reach the other threads through shared memory
+    enum { ACT_STEP = 0, ACT_REFRESH = 1, ACT_BREAKDOWN = 2, ACT_NAN = 3 };
+    if (threadIdx.x == 0) {
+      int act = ACT_STEP;
+      double al = 0.0, be = 0.0;
+      if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) act = ACT_NAN;
+      else {
+        if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
+        if (rr <= tol_in2 || it - it_best > STALL || it >= a.max_iter) act = ACT_REFRESH;
+        else if (fresh) {
+          if (!(delta > 0.0)) act = ACT_BREAKDOWN;
+          else al = gamma / delta;
+        } else {
+          be = gamma / gamma_old;
+          const double den = delta - be * gamma / alpha_old;
+          if (!(den > 0.0)) act = ACT_REFRESH;  // lost conjugacy: refresh from the true residual
+          else al = gamma / den;
+        }
       }
+      sh.action = act;
+      sh.scal[0] = al;
+      sh.scal[1] = be;
+      sh.scal[2] = al * unscale;
     }
-    if (stop_inner || it >= a.max_iter) {
+    __syncthreads();
+    const int action = sh.action;
+    const double alpha = sh.scal[0], beta = sh.scal[1], ax = sh.scal[2];
+    __syncthreads();
+    if (action == ACT_NAN) { status = 2; break; }
+    if (action == ACT_BREAKDOWN) { status = 1; break; }
+    if (action == ACT_REFRESH) {
       tt = true_residual();
       if (!isfinite(tt)) { status = 2; break; }
       if (tt <= tol2_true || it >= a.max_iter || replaced >= max_replace) break;
@@ -882,21 +914,17 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
       fresh = true;
       continue;
     }
-    // iteration: n = A m, then every recurrence of the owned nodes
-    const double ax = alpha * unscale;
-    T* mcur = par ? V.m1 : V.m0;
-    T* mnext = par ? V.m0 : V.m1;
+    // every recurrence of the owned nodes, one thread per node
     double pv[3] = {0.0, 0.0, 0.0};
-    for_rows(false, op, colp, rowp, M(0), pairH, fHu, (const T*)mcur, [&](int i, double n0, double n1, double n2) {
-      const T nn[3] = {n0, n1, n2};
-      T rn[3], un[3], wn[3];
+    for_nodes([&](int i, const double* n) {
+      double rn[3], un[3], wn[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int q = 3 * i + c;
-        const T z = nn[c] + beta * V.z[q];
-        const T qq = mcur[q] + beta * V.q[q];
-        const T s = V.w[q] + beta * V.s[q];
-        const T p = V.u[q] + beta * V.p[q];
+        const double z = n[c] + beta * V.z[q];
+        const double qq = mcur[q] + beta * V.q[q];
+        const double s = V.w[q] + beta * V.s[q];
+        const double p = V.u[q] + beta * V.p[q];
         V.z[q] = z; V.q[q] = qq; V.s[q] = s; V.p[q] = p;
         x[q] += ax * p;
         rn[c] = V.r[q] - alpha * s;
@@ -904,14 +932,14 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         wn[c] = V.w[q] - alpha * z;
         V.r[q] = rn[c]; V.u[q] = un[c]; V.w[q] = wn[c];
       }
-      T m0, m1, m2;
-      apply3<M, T>(Dof(i), wn[0], wn[1], wn[2], m0, m1, m2);
+      double m0, m1, m2;
+      apply3<M, double>(Dof(i), wn[0], wn[1], wn[2], m0, m1, m2);
       mnext[3 * i] = m0; mnext[3 * i + 1] = m1; mnext[3 * i + 2] = m2;
       pv[0] += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
       pv[1] += wn[0] * un[0] + wn[1] * un[1] + wn[2] * un[2];
       pv[2] += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
     });
-    write_partials(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv);
+    write_partials<double>(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv);
     grid.sync();
     gamma_old = gamma;
     alpha_old = alpha;
@@ -925,6 +953,274 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     a.out[1] = status;
     a.out[2] = replaced;
     a.res[0] = res;
+  }
+}
+
+// Mixed-precision solve: iterative refinement around an FP32 conjugate-
+// gradient solve.  The inner solve runs entirely in FP32 (operator,
+// preconditioner, contact blocks, vectors, dot products) in the
+// Chronopoulos-Gear form of CG, which tolerates the rounding of FP32 matrix
+// products (the pipelined recurrences do not): two grid barriers per
+// iteration, one reduction point.  Its solution d of A32 d = sigma (b - A x)
+// is accumulated into x in FP64 and the FP64 residual b - A x is recomputed
+// with the FP64 operator until it meets the tolerance.
+template <int ROWG>
+__global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
+  using F = float;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ Shared sh;
+  const DevScene& S = a.S;
+  const int nblk = gridDim.x, cta = blockIdx.x;
+  const bool fem_cta = cta < a.n_fem_ctas;
+  const int nf = S.nf;
+  const int n3 = 3 * a.n_nodes;
+
+  int r0 = 0, r1 = 0, k0 = 0, nloc = 0;
+  OpView<F> op{nullptr, 0, 1};
+  const int* colp = nullptr;
+  const int* rowp = nullptr;
+  const F* dinv_loc = nullptr;
+  const F* opF = (const F*)a.op;
+  const F* dinvF = (const F*)a.dinv;
+  double* acc = (double*)dyn;  // row products: FP64 for the residual, FP32 for the iteration
+  F* accf = (F*)dyn;
+  if (fem_cta) {
+    r0 = a.seg_row[cta]; r1 = a.seg_row[cta + 1];
+    if (!pcg_ok(a, r0 >= 0 && r0 <= r1 && r1 <= nf, 11)) r0 = r1 = 0;
+    k0 = a.row[r0]; nloc = a.row[r1] - k0;
+    if (a.resident) {
+      F* s_op = (F*)(acc + a.acc_doubles);
+      F* s_dinv = s_op + 9 * (size_t)nloc;
+      int* s_col = (int*)(s_dinv + 9 * (size_t)(r1 - r0));
+      int* s_row = s_col + nloc;
+      const F* g_op = opF + 9 * (size_t)k0;
+      for (int idx = threadIdx.x; idx < 9 * nloc; idx += blockDim.x) s_op[idx] = g_op[idx];
+      for (int idx = threadIdx.x; idx < 9 * (r1 - r0); idx += blockDim.x) s_dinv[idx] = dinvF[9 * (size_t)r0 + idx];
+      for (int idx = threadIdx.x; idx < nloc; idx += blockDim.x) s_col[idx] = a.col[k0 + idx];
+      for (int idx = threadIdx.x; idx <= r1 - r0; idx += blockDim.x) s_row[idx] = a.row[r0 + idx] - k0;
+      __syncthreads();
+      op = OpView<F>{s_op, nloc, 1};
+      colp = s_col; rowp = s_row; dinv_loc = s_dinv;
+    } else {
+      op = OpView<F>{opF + 9 * (size_t)k0, nloc, 1};
+      colp = a.col + k0; dinv_loc = dinvF + 9 * (size_t)r0;
+    }
+  }
+  auto Dof = [&](int i) -> const F* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvF + 9 * (size_t)i); };
+
+  F* base = (F*)a.vec;
+  F* r = base;
+  F* u = base + n3;
+  F* w = base + 2 * (size_t)n3;
+  F* pv_ = base + 3 * (size_t)n3;
+  F* sv = base + 4 * (size_t)n3;
+  F* xi = base + 5 * (size_t)n3;
+  const F* pairH = (const F*)a.pairH;
+  const F* fHu = (const F*)a.fHu;
+  double* x = a.x;
+  double* t64 = a.t64;
+  // partial sums: FP32 [R][2][3][grid], then FP64 [R][grid] (norms of b and of the true residual)
+  F* partF = (F*)a.partial;
+  const size_t repT = 2 * 3 * (size_t)nblk;
+  double* partD = (double*)a.partial + PCG_REPLICAS * repT;
+  const int myrep = cta % PCG_REPLICAS;
+
+  // FP32 products of the iteration operator, FP64 products of the assembled one
+  auto products32 = [&](const F* vin) {
+    if (fem_cta) {
+      fem_products<F, F, F, ROWG>(a, r0, r1, k0, op, colp, rowp, pairH, fHu, vin, accf);
+    } else {
+      int j = 0;
+      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j) {
+        const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
+        abd_products<F, F, F, F>(a, b, OpView<F>{opF + 9 * (size_t)kb0, nl, 1}, a.col + kb0, nl, vin, a.abd_val32, sh,
+                                 accf + 12 * j);
+      }
+    }
+  };
+  auto products64 = [&](const double* vin) {
+    if (fem_cta) {
+      fem_products<double, double, double, ROWG>(a, r0, r1, k0, OpView<double>{a.val64 + 9 * (size_t)k0, 1, 9},
+                                                 a.col + k0, nullptr, a.pairH64, a.fHu64, vin, acc);
+    } else {
+      int j = 0;
+      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j) {
+        const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
+        abd_products<double, double, double, double>(a, b, OpView<double>{a.val64 + 9 * (size_t)kb0, 1, 9},
+                                                     a.col + kb0, nl, vin, a.abd_val, sh, acc + 12 * j);
+      }
+    }
+  };
+  // node-local pass; the row product of the node (from the last products call) is at prod(i)
+  auto for_nodes = [&](auto&& fn) {
+    if (fem_cta) {
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) fn(i, 3 * (i - r0));
+    } else {
+      int j = 0;
+      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j)
+        if (threadIdx.x < 4) fn(nf + 4 * b + threadIdx.x, 12 * j + 3 * threadIdx.x);
+    }
+  };
+
+  // ---- x = 0, t64 = b, |b|^2
+  {
+    double v[1] = {0.0};
+    for_nodes([&](int i, int) {
+      for (int c = 0; c < 3; ++c) {
+        const double bv = a.b[3 * i + c];
+        x[3 * i + c] = 0.0;
+        t64[3 * i + c] = bv;
+        v[0] += bv * bv;
+      }
+    });
+    cta_sum<1, double>(v, sh);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
+  }
+  grid.sync();
+  const double bb = total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
+  int it = 0, status = 0, refine = 0;
+  if (!(bb > 0.0) || !isfinite(bb)) {
+    if (threadIdx.x == 0 && cta == 0) {
+      a.out[0] = 0; a.out[1] = isfinite(bb) ? 0 : 2; a.out[2] = 0; a.res[0] = 0.0;
+    }
+    return;
+  }
+  const double tol2_true = a.rtol * a.rtol * bb;
+  double tt = bb;
+  constexpr int STALL = 80;
+  constexpr int MAX_REFINE = 10;
+  for (;;) {
+    // ---- inner solve of A32 d = sigma t64 from d = 0
+    const double unscale = sqrt(tt);
+    const double sigma = 1.0 / unscale;
+    // inner target: the remaining reduction, not below what FP32 CG resolves
+    const F tol_in2 = (F)fmax(tol2_true / tt, 1e-10);
+    F g_l = F(0), rr_l = F(0);
+    for_nodes([&](int i, int) {
+      F rv[3], uv[3];
+      for (int c = 0; c < 3; ++c) {
+        const int q = 3 * i + c;
+        rv[c] = (F)(sigma * t64[q]);
+        r[q] = rv[c];
+        pv_[q] = F(0); sv[q] = F(0); xi[q] = F(0);
+      }
+      apply3<F, F>(Dof(i), rv[0], rv[1], rv[2], uv[0], uv[1], uv[2]);
+      for (int c = 0; c < 3; ++c) u[3 * i + c] = uv[c];
+      g_l += rv[0] * uv[0] + rv[1] * uv[1] + rv[2] * uv[2];
+      rr_l += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+    });
+    grid.sync();
+    bool fresh = true;
+    F alpha_old = F(1), gamma_old = F(1), rr_best = F(0);
+    int it_best = it;
+    for (;;) {
+      const int par = it & 1;
+      // phase A: w = A u, partial sums of (r, u), (w, u), (r, r)
+      products32(u);
+      F d_l = F(0);
+      for_nodes([&](int i, int o) {
+        const int q = 3 * i;
+        const F w0 = accf[o], w1 = accf[o + 1], w2 = accf[o + 2];
+        w[q] = w0; w[q + 1] = w1; w[q + 2] = w2;
+        d_l += w0 * u[q] + w1 * u[q + 1] + w2 * u[q + 2];
+      });
+      const F pl[3] = {g_l, d_l, rr_l};
+      write_partials<F>(partF + (size_t)par * 3 * nblk, repT, nblk, sh, pl);
+      grid.sync();
+      // phase B: totals, scalars on thread 0, vector updates
+      Partials<F> P;
+      const F* rep = partF + (size_t)par * 3 * nblk + myrep * repT;
+      load_partials<F>(rep, nblk, P);
+      double gd, dd, rd;
+      totals3<F>(rep, nblk, P, sh, gd, dd, rd);
+      enum { ACT_STEP = 0, ACT_DONE = 1, ACT_BREAKDOWN = 2, ACT_NAN = 3 };
+      if (threadIdx.x == 0) {
+        const F gamma = (F)gd, delta = (F)dd, rr = (F)rd;
+        int act = ACT_STEP;
+        F al = F(0), be = F(0);
+        if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) act = ACT_NAN;
+        else {
+          if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
+          if (rr <= tol_in2 || it - it_best > STALL || it >= a.max_iter) act = ACT_DONE;
+          else if (fresh) {
+            if (!(delta > F(0))) act = ACT_BREAKDOWN;
+            else al = gamma / delta;
+          } else {
+            be = gamma / gamma_old;
+            const F den = delta - be * gamma / alpha_old;
+            if (!(den > F(0))) act = ACT_DONE;  // lost conjugacy: refine from the true residual
+            else al = gamma / den;
+          }
+          gamma_old = gamma;
+          alpha_old = al;
+        }
+        sh.action = act;
+        sh.scal[0] = al;
+        sh.scal[1] = be;
+      }
+      __syncthreads();
+      const int action = sh.action;
+      const F alpha = (F)sh.scal[0], beta = (F)sh.scal[1];
+      __syncthreads();
+      if (action == ACT_NAN) { status = 2; break; }
+      if (action == ACT_BREAKDOWN) { if (fresh) status = 1; break; }
+      if (action == ACT_DONE) break;
+      g_l = F(0);
+      rr_l = F(0);
+      for_nodes([&](int i, int) {
+        F rn[3];
+        for (int c = 0; c < 3; ++c) {
+          const int q = 3 * i + c;
+          const F p = u[q] + beta * pv_[q];
+          const F sq = w[q] + beta * sv[q];
+          pv_[q] = p;
+          sv[q] = sq;
+          xi[q] += alpha * p;
+          rn[c] = r[q] - alpha * sq;
+          r[q] = rn[c];
+        }
+        F un[3];
+        apply3<F, F>(Dof(i), rn[0], rn[1], rn[2], un[0], un[1], un[2]);
+        for (int c = 0; c < 3; ++c) u[3 * i + c] = un[c];
+        g_l += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
+        rr_l += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
+      });
+      fresh = false;
+      ++it;
+      grid.sync();
+    }
+    if (status) break;
+    // ---- x += d / sigma in FP64, then the FP64 residual
+    for_nodes([&](int i, int) {
+      for (int c = 0; c < 3; ++c) x[3 * i + c] += unscale * (double)xi[3 * i + c];
+    });
+    grid.sync();
+    products64(x);
+    double v[1] = {0.0};
+    for_nodes([&](int i, int o) {
+      for (int c = 0; c < 3; ++c) {
+        const double t = a.b[3 * i + c] - acc[o + c];
+        t64[3 * i + c] = t;
+        v[0] += t * t;
+      }
+    });
+    cta_sum<1, double>(v, sh);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
+    grid.sync();
+    tt = total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
+    if (!isfinite(tt)) { status = 2; break; }
+    if (tt <= tol2_true || it >= a.max_iter || refine >= MAX_REFINE || !(tt > 0.0)) break;
+    ++refine;
+  }
+  if (status == 0 && !(tt <= tol2_true)) status = 3;
+  if (threadIdx.x == 0 && cta == 0) {
+    a.out[0] = it;
+    a.out[1] = status;
+    a.out[2] = refine;
+    a.res[0] = sqrt(fmax(tt, 0.0) / bb);
   }
 }
 
@@ -953,7 +1249,17 @@ static void* pcg_kernel(int rowg) {
   }
 }
 
-static void* pcg_fn(int fp32, int rowg) { return fp32 ? pcg_kernel<float>(rowg) : pcg_kernel<double>(rowg); }
+static void* pcg32_kernel(int rowg) {
+  switch (rowg) {
+    case 1: return (void*)k_pcg32<1>;
+    case 2: return (void*)k_pcg32<2>;
+    case 8: return (void*)k_pcg32<8>;
+    default: return (void*)k_pcg32<4>;
+  }
+}
+
+// fp32: the mixed-precision refinement solver; otherwise the FP64 pipelined solver
+static void* pcg_fn(int fp32, int rowg) { return fp32 ? pcg32_kernel(rowg) : pcg_kernel<double>(rowg); }
 
 int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem) {
   int dev, sms, per_sm = 0;
@@ -1015,13 +1321,16 @@ void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, PcgPl
     P.max_rows = std::max(P.max_rows, P.seg[c + 1] - P.seg[c]);
     P.max_blocks = std::max(P.max_blocks, row[P.seg[c + 1]] - row[P.seg[c]]);
   }
+  const int bodies_per_cta = P.n_abd_ctas ? (nab + P.n_abd_ctas - 1) / P.n_abd_ctas : 0;
+  P.acc_doubles = std::max(1, std::max(3 * P.max_rows, 12 * bodies_per_cta));
+  P.acc_doubles = (P.acc_doubles + 1) & ~1;  // keeps what follows 16-byte aligned
 }
 
-size_t pcg_contact_bytes(const PcgPlan& P) { return (24 * (size_t)P.max_rows + 127) & ~(size_t)127; }
+size_t pcg_contact_bytes(const PcgPlan& P) { return (8 * (size_t)P.acc_doubles + 127) & ~(size_t)127; }
 
 size_t pcg_resident_bytes(const PcgPlan& P, int fp32) {
   size_t e = fp32 ? 4 : 8;
-  size_t b = 24 * (size_t)P.max_rows + 9 * (size_t)P.max_blocks * e + 9 * (size_t)P.max_rows * e +
+  size_t b = 8 * (size_t)P.acc_doubles + 9 * (size_t)P.max_blocks * e + 9 * (size_t)P.max_rows * e +
              4 * (size_t)P.max_blocks + 4 * ((size_t)P.max_rows + 1);
   return (b + 127) & ~(size_t)127;
 }

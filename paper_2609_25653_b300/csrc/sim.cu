@@ -81,6 +81,7 @@ struct ipcsim {
   // contact coupling blocks of the ABD pseudo-node rows
   int *abd_ptr = nullptr, *abd_cursor = nullptr, *abd_ent = nullptr;
   double* abd_val = nullptr;
+  float* abd_val32 = nullptr;
   long long abd_cap = 0;
   int* pcg_check = nullptr;    // diagnostic index-check flag of the PCG
   // mixed precision copies
@@ -217,11 +218,14 @@ ipc_status grow_abd_list(ipcsim* sim, long long need) {
   if (sim->nab == 0 || need <= sim->abd_cap) return IPC_OK;
   dfree(sim, sim->abd_ent);
   dfree(sim, sim->abd_val);
+  dfree(sim, sim->abd_val32);
   sim->abd_ent = nullptr;
   sim->abd_val = nullptr;
+  sim->abd_val32 = nullptr;
   ipc_status s;
   if ((s = dalloc(sim, &sim->abd_ent, (size_t)need))) return s;
   if ((s = dalloc(sim, &sim->abd_val, 9 * (size_t)need))) return s;
+  if (sim->P.precision == IPC_PREC_MIXED && (s = dalloc(sim, &sim->abd_val32, 9 * (size_t)need))) return s;
   sim->abd_cap = need;
   return IPC_OK;
 }
@@ -408,9 +412,11 @@ ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric)
   }
   a.check = check ? sim->pcg_check : nullptr;
   a.max_rows = sim->plan.max_rows;
+  a.acc_doubles = sim->plan.acc_doubles;
   a.abd_ptr = sim->abd_ptr;
   a.abd_ent = sim->abd_ent;
   a.abd_val = sim->abd_val;
+  a.abd_val32 = sim->abd_val32;
   a.abd_cap = sim->abd_cap;
   CUDA_TRY(launch_pcg(sim->st, sim->plan.grid, PCG_THREADS, a, sim->tune_rowg, sim->plan_smem));
   if (check) {
@@ -1246,6 +1252,7 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
       launch_to_float(cs, 144 * (size_t)sim->cap, sim->pairH, sim->pairH32, &sim->sc_dev->n_pairs, 144);
       if (n_fric_it) launch_to_float(cs, 9 * (size_t)n_fric_it, sim->f_Hu, sim->fHu32);
       launch_to_float(cs, 9 * (size_t)sim->n_nodes, sim->Dinv, sim->Dinv32);
+      if (sim->nab) launch_to_float(cs, 9 * (size_t)sim->abd_cap, sim->abd_val, sim->abd_val32, sim->abd_ptr + sim->nab, 9);
     }
     if (sim->autotune_pending) {
       // time every launch shape on this system (same right-hand side, same tolerance) and keep the fastest
