@@ -11,6 +11,17 @@ namespace ipc {
 extern unsigned long long g_kernel_launches;
 inline void count_launch(int n = 1) { __atomic_fetch_add(&g_kernel_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
 
+// Gather descriptor of one contact pair (barrier pairs at [0, cap), friction
+// pairs at [cap, cap + fcap)): for every slot the first node of its vertex (-1:
+// kinematic or zero weight) and, for ABD vertices (bit j of abd), the rest
+// position that weights the body's pseudo-nodes 1..3.
+struct __align__(16) PairDesc {
+  int node[4];
+  int abd;
+  int pad[3];
+  double xb[4][3];
+};
+
 // Arguments of one PCG solve (see pcg.cu).  CTAs [0, n_fem_ctas) own the FEM
 // rows seg_row[c] .. seg_row[c + 1]; the others own ABD bodies
 // b = cta - n_fem_ctas (mod n_abd_ctas).  Pointers of the operator type
@@ -36,6 +47,7 @@ struct PcgArgs {
   int n_fric;
   const int* f_ids;
   const double* f_w;
+  const PairDesc* desc;      // (cap + fcap) gather descriptors of the pairs
   const int* inc_ptr;        // (nf + nab + 1) contact incidences per owner
   const int2* inc;           // (code, owner) ordered by owner; code = pair << 3 | friction << 2 | slot
   int max_rows;              // most FEM rows of one CTA
@@ -146,7 +158,7 @@ cudaError_t launch_pcg(cudaStream_t, int grid, int threads, const PcgArgs& a, in
 void launch_layout(cudaStream_t, int n_seg, const int* seg, const int* row, const double* src, void* dst, int fp32);
 void launch_incidence(cudaStream_t, const DevScene& S, const int* rec, const int* n_pairs, int cap, int n_fric,
                       const int* f_ids, const double* f_w, int* inc_ptr, int* cursor, int* tiles, int2* inc,
-                      long long inc_cap, int* err);
+                      long long inc_cap, PairDesc* desc, int* err);
 void launch_abd_contact(cudaStream_t, const DevScene& S, const int* rec, const int* n_pairs, int cap,
                         const double* pairH, int n_fric, const int* f_ids, const double* f_w, const double* f_Hu,
                         int* abd_ptr, int* cursor, int* ent, double* entv, long long ent_cap, double* Hval,

@@ -67,20 +67,39 @@ template <bool FILL>
 __global__ void k_incidence(DevScene S, const int* __restrict__ rec, const int* __restrict__ n_pairs, int cap,
                             int n_fric, const int* __restrict__ f_ids, const double* __restrict__ f_w,
                             int* __restrict__ cnt_or_cursor, int2* __restrict__ inc, long long inc_cap,
-                            int* __restrict__ err) {
+                            PairDesc* __restrict__ desc, int* __restrict__ err) {
   const int np = min(*n_pairs, cap);
   const long long tot = 4LL * (np + n_fric);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     int k = (int)(e >> 2), q = (int)(e & 3), v, code;
+    bool zero = false;
+    int di;
     if (k < np) {
-      v = rec[8 * k + 4 + q];
+      v = rec[8 * (size_t)k + 4 + q];
       code = (k << 3) | q;
+      di = k;
     } else {
       k -= np;
-      if (f_w[4 * k + q] == 0.0) continue;
-      v = f_ids[4 * k + q];
+      zero = f_w[4 * (size_t)k + q] == 0.0;
+      v = f_ids[4 * (size_t)k + q];
       code = (k << 3) | 4 | q;
+      di = cap + k;
     }
+    if (!FILL) {
+      // the slot's part of the pair's gather descriptor
+      PairDesc& D = desc[di];
+      const int kind = zero ? VK_KIN : S.vkind[v];
+      D.node[q] = kind == VK_FEM ? v : (kind == VK_ABD ? S.nf + 4 * S.vabd[v] : -1);
+      if (kind == VK_ABD) {
+        D.xb[q][0] = S.xbar[3 * v];
+        D.xb[q][1] = S.xbar[3 * v + 1];
+        D.xb[q][2] = S.xbar[3 * v + 2];
+        atomicOr(&D.abd, 1 << q);
+      } else {
+        atomicAnd(&D.abd, ~(1 << q));
+      }
+    }
+    if (zero) continue;
     int o = owner_of(S, v);
     if (o < 0) continue;
     int slot = atomicAdd(cnt_or_cursor + o, 1);
@@ -153,18 +172,18 @@ __global__ void k_scan_add(int n, int* __restrict__ a, const int* __restrict__ t
 
 void launch_incidence(cudaStream_t st, const DevScene& S, const int* rec, const int* n_pairs, int cap, int n_fric,
                       const int* f_ids, const double* f_w, int* inc_ptr, int* cursor, int* tiles, int2* inc,
-                      long long inc_cap, int* err) {
+                      long long inc_cap, PairDesc* desc, int* err) {
   const int n_own = S.nf + S.nab;
   const int n = n_own + 1;
   cudaMemsetAsync(inc_ptr, 0, sizeof(int) * n, st);
   int grid = std::max(1, std::min((4 * (cap + n_fric) + 255) / 256, 148 * 8));
-  k_incidence<false><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, inc_ptr, nullptr, 0, err);
+  k_incidence<false><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, inc_ptr, nullptr, 0, desc, err);
   int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   k_scan_tiles<<<ntiles, 1024, 0, st>>>(n, inc_ptr, tiles);
   k_scan_totals<<<1, 1024, 0, st>>>(ntiles, tiles);
   k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(n, inc_ptr, tiles);
   cudaMemcpyAsync(cursor, inc_ptr, sizeof(int) * n_own, cudaMemcpyDeviceToDevice, st);
-  k_incidence<true><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, cursor, inc, inc_cap, err);
+  k_incidence<true><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, cursor, inc, inc_cap, desc, err);
   for (int k = 0; k < 5; ++k) count_launch();
 }
 
@@ -383,69 +402,63 @@ __device__ inline bool pcg_ok(const PcgArgs& a, bool cond, int site) {
   return false;
 }
 
-// v gathered at a vertex through x = J z (zero for kinematic vertices), in the accumulation type A
+// v at a pair slot through its gather descriptor (x = J z; zero for kinematic slots)
 template <typename V, typename A>
-__device__ inline void gather_vertex(const PcgArgs& a, const V* v, int vert, A& g0, A& g1, A& g2) {
-  const DevScene& S = a.S;
-  if (!pcg_ok(a, vert >= 0 && vert < S.nv, 4)) { g0 = g1 = g2 = A(0); return; }
-  int kind = S.vkind[vert];
-  if (kind == VK_ABD && !pcg_ok(a, S.vabd[vert] >= 0 && S.vabd[vert] < S.nab, 7)) { g0 = g1 = g2 = A(0); return; }
-  if (kind == VK_FEM) {
-    g0 = (A)v[3 * vert]; g1 = (A)v[3 * vert + 1]; g2 = (A)v[3 * vert + 2];
-  } else if (kind == VK_ABD) {
-    int n = S.nf + 4 * S.vabd[vert];
-    const A x0 = (A)S.xbar[3 * vert], x1 = (A)S.xbar[3 * vert + 1], x2 = (A)S.xbar[3 * vert + 2];
-    const V* b = v + 3 * n;
-    g0 = (A)b[0] + x0 * (A)b[3] + x1 * (A)b[6] + x2 * (A)b[9];
-    g1 = (A)b[1] + x0 * (A)b[4] + x1 * (A)b[7] + x2 * (A)b[10];
-    g2 = (A)b[2] + x0 * (A)b[5] + x1 * (A)b[8] + x2 * (A)b[11];
-  } else {
-    g0 = g1 = g2 = A(0);
+__device__ inline void gather_slot(const PairDesc& D, int j, const V* v, A& g0, A& g1, A& g2) {
+  const int n = D.node[j];
+  if (n < 0) { g0 = g1 = g2 = A(0); return; }
+  const V* b = v + 3 * (size_t)n;
+  g0 = (A)b[0]; g1 = (A)b[1]; g2 = (A)b[2];
+  if (D.abd & (1 << j)) {
+    const A x0 = (A)D.xb[j][0], x1 = (A)D.xb[j][1], x2 = (A)D.xb[j][2];
+    g0 = fma(x0, (A)b[3], fma(x1, (A)b[6], fma(x2, (A)b[9], g0)));
+    g1 = fma(x0, (A)b[4], fma(x1, (A)b[7], fma(x2, (A)b[10], g1)));
+    g2 = fma(x0, (A)b[5], fma(x1, (A)b[8], fma(x2, (A)b[11], g2)));
   }
 }
 
 // rows (3 slot .. 3 slot + 2) of one contact block applied to v (block values
-// stored as M, products and sums in A); returns the pair's vertex in that slot
+// stored as M, products and sums in A)
 template <typename M, typename V, typename A>
-__device__ inline int contact_rows(const PcgArgs& a, const M* pairH, const M* fHu, const V* v, int code, A& y0, A& y1,
-                                   A& y2) {
+__device__ inline void contact_rows(const PcgArgs& a, const M* pairH, const M* fHu, const V* v, int code, A& y0, A& y1,
+                                    A& y2) {
   const int k = code >> 3, q = code & 3;
-  if (!pcg_ok(a, (code & 4) ? (k >= 0 && k < a.n_fric) : (k >= 0 && k < a.cap), (code & 4) ? 5 : 3)) {
+  const bool fric = code & 4;
+  if (!pcg_ok(a, fric ? (k >= 0 && k < a.n_fric) : (k >= 0 && k < a.cap), fric ? 5 : 3)) {
     y0 = y1 = y2 = A(0);
-    return -1;
+    return;
   }
-  if (!(code & 4)) {
-    const int* r = a.rec + 8 * (size_t)k;
+  const PairDesc& D = a.desc[fric ? (size_t)a.cap + k : (size_t)k];
+  A g[4][3];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!pcg_ok(a, D.node[j] < a.n_nodes, 4)) { g[j][0] = g[j][1] = g[j][2] = A(0); continue; }
+    gather_slot<V, A>(D, j, v, g[j][0], g[j][1], g[j][2]);
+  }
+  if (!fric) {
     const M* H = pairH + 144 * (size_t)k + 36 * q;
     A t0 = A(0), t1 = A(0), t2 = A(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      A g0, g1, g2;
-      gather_vertex<V, A>(a, v, r[4 + j], g0, g1, g2);
-      t0 = fma((A)H[3 * j], g0, fma((A)H[3 * j + 1], g1, fma((A)H[3 * j + 2], g2, t0)));
-      t1 = fma((A)H[12 + 3 * j], g0, fma((A)H[12 + 3 * j + 1], g1, fma((A)H[12 + 3 * j + 2], g2, t1)));
-      t2 = fma((A)H[24 + 3 * j], g0, fma((A)H[24 + 3 * j + 1], g1, fma((A)H[24 + 3 * j + 2], g2, t2)));
+      t0 = fma((A)H[3 * j], g[j][0], fma((A)H[3 * j + 1], g[j][1], fma((A)H[3 * j + 2], g[j][2], t0)));
+      t1 = fma((A)H[12 + 3 * j], g[j][0], fma((A)H[12 + 3 * j + 1], g[j][1], fma((A)H[12 + 3 * j + 2], g[j][2], t1)));
+      t2 = fma((A)H[24 + 3 * j], g[j][0], fma((A)H[24 + 3 * j + 1], g[j][1], fma((A)H[24 + 3 * j + 2], g[j][2], t2)));
     }
     y0 = t0; y1 = t1; y2 = t2;
-    return r[4 + q];
+    return;
   }
-  const int* ids = a.f_ids + 4 * (size_t)k;
   const double* w = a.f_w + 4 * (size_t)k;
   const M* Hu = fHu + 9 * (size_t)k;
   A U0 = A(0), U1 = A(0), U2 = A(0);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    if (w[j] == 0.0) continue;
-    A g0, g1, g2;
-    gather_vertex<V, A>(a, v, ids[j], g0, g1, g2);
     const A wj = (A)w[j];
-    U0 = fma(wj, g0, U0); U1 = fma(wj, g1, U1); U2 = fma(wj, g2, U2);
+    U0 = fma(wj, g[j][0], U0); U1 = fma(wj, g[j][1], U1); U2 = fma(wj, g[j][2], U2);
   }
   const A wq = (A)w[q];
   y0 = wq * fma((A)Hu[0], U0, fma((A)Hu[1], U1, (A)Hu[2] * U2));
   y1 = wq * fma((A)Hu[3], U0, fma((A)Hu[4], U1, (A)Hu[5] * U2));
   y2 = wq * fma((A)Hu[6], U0, fma((A)Hu[7], U1, (A)Hu[8] * U2));
-  return ids[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -553,18 +566,35 @@ __device__ inline void fem_products(const PcgArgs& a, int r0, int r1, int k0, Op
                                     const M* pairH, const M* fHu, const V* v, A* acc) {
   for (int j = threadIdx.x; j < 3 * (r1 - r0); j += blockDim.x) acc[j] = A(0);
   __syncthreads();
+  // incidences e of the segment, consecutive per lane; their owners are non-decreasing, so the
+  // contributions of one owner are summed by a segmented warp scan and added once per run
   const int e0 = a.inc_ptr[r0], e1 = a.inc_ptr[r1];
-#pragma unroll 2
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    if (!pcg_ok(a, e >= 0 && e < a.inc_cap, 2)) break;
-    const int2 ie = a.inc[e];
-    if (!pcg_ok(a, ie.y >= r0 && ie.y < r1, 12)) continue;
-    A y0, y1, y2;
-    contact_rows<M, V, A>(a, pairH, fHu, v, ie.x, y0, y1, y2);
-    A* t = acc + 3 * (ie.y - r0);
-    atomicAdd(t, y0);
-    atomicAdd(t + 1, y1);
-    atomicAdd(t + 2, y2);
+  const int lane = threadIdx.x & 31;
+  for (int eb = e0; eb < e1; eb += blockDim.x) {
+    const int e = eb + threadIdx.x;
+    int own = -1;
+    A y0 = A(0), y1 = A(0), y2 = A(0);
+    if (e < e1 && pcg_ok(a, e >= 0 && e < a.inc_cap, 2)) {
+      const int2 ie = a.inc[e];
+      if (pcg_ok(a, ie.y >= r0 && ie.y < r1, 12)) {
+        own = ie.y;
+        contact_rows<M, V, A>(a, pairH, fHu, v, ie.x, y0, y1, y2);
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const A t0 = __shfl_up_sync(0xffffffffu, y0, o), t1 = __shfl_up_sync(0xffffffffu, y1, o),
+              t2 = __shfl_up_sync(0xffffffffu, y2, o);
+      const int ow = __shfl_up_sync(0xffffffffu, own, o);
+      if (lane >= o && ow == own) { y0 += t0; y1 += t1; y2 += t2; }
+    }
+    const int next = __shfl_down_sync(0xffffffffu, own, 1);
+    if (own >= 0 && (lane == 31 || next != own)) {
+      A* t = acc + 3 * (own - r0);
+      atomicAdd(t, y0);
+      atomicAdd(t + 1, y1);
+      atomicAdd(t + 2, y2);
+    }
   }
   __syncthreads();
   const int groups = blockDim.x / ROWG, g = threadIdx.x / ROWG, gl = threadIdx.x & (ROWG - 1);
@@ -917,19 +947,28 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     // every recurrence of the owned nodes, one thread per node
     double pv[3] = {0.0, 0.0, 0.0};
     for_nodes([&](int i, const double* n) {
+      // every value of the node is loaded before anything is stored (the vectors may alias as far as
+      // the compiler knows, which would otherwise serialise the loads behind the stores)
+      double oz[3], oq[3], os[3], op_[3], ou[3], ow[3], orr[3], om[3], ox[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int q = 3 * i + c;
+        oz[c] = V.z[q]; oq[c] = V.q[q]; os[c] = V.s[q]; op_[c] = V.p[q]; ou[c] = V.u[q];
+        ow[c] = V.w[q]; orr[c] = V.r[q]; om[c] = mcur[q]; ox[c] = x[q];
+      }
       double rn[3], un[3], wn[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int q = 3 * i + c;
-        const double z = n[c] + beta * V.z[q];
-        const double qq = mcur[q] + beta * V.q[q];
-        const double s = V.w[q] + beta * V.s[q];
-        const double p = V.u[q] + beta * V.p[q];
+        const double z = fma(beta, oz[c], n[c]);
+        const double qq = fma(beta, oq[c], om[c]);
+        const double s = fma(beta, os[c], ow[c]);
+        const double p = fma(beta, op_[c], ou[c]);
         V.z[q] = z; V.q[q] = qq; V.s[q] = s; V.p[q] = p;
-        x[q] += ax * p;
-        rn[c] = V.r[q] - alpha * s;
-        un[c] = V.u[q] - alpha * qq;
-        wn[c] = V.w[q] - alpha * z;
+        x[q] = fma(ax, p, ox[c]);
+        rn[c] = fma(-alpha, s, orr[c]);
+        un[c] = fma(-alpha, qq, ou[c]);
+        wn[c] = fma(-alpha, z, ow[c]);
         V.r[q] = rn[c]; V.u[q] = un[c]; V.w[q] = wn[c];
       }
       double m0, m1, m2;
@@ -1170,15 +1209,21 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       g_l = F(0);
       rr_l = F(0);
       for_nodes([&](int i, int) {
-        F rn[3];
+        F ou[3], opv[3], ow[3], osv[3], oxi[3], orr[3], rn[3];
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           const int q = 3 * i + c;
-          const F p = u[q] + beta * pv_[q];
-          const F sq = w[q] + beta * sv[q];
+          ou[c] = u[q]; opv[c] = pv_[q]; ow[c] = w[q]; osv[c] = sv[q]; oxi[c] = xi[q]; orr[c] = r[q];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int q = 3 * i + c;
+          const F p = fmaf(beta, opv[c], ou[c]);
+          const F sq = fmaf(beta, osv[c], ow[c]);
           pv_[q] = p;
           sv[q] = sq;
-          xi[q] += alpha * p;
-          rn[c] = r[q] - alpha * sq;
+          xi[q] = fmaf(alpha, p, oxi[c]);
+          rn[c] = fmaf(-alpha, sq, orr[c]);
           r[q] = rn[c];
         }
         F un[3];

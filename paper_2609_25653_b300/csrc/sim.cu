@@ -77,6 +77,8 @@ struct ipcsim {
   // contact incidences per owner (FEM node or ABD body)
   int *inc_ptr = nullptr, *inc_cursor = nullptr, *inc_tiles = nullptr;
   int2* inc = nullptr;
+  PairDesc* desc = nullptr;    // (cap + fcap) gather descriptors of the pairs
+  long long desc_cap = 0;
   long long inc_cap = 0;
   // contact coupling blocks of the ABD pseudo-node rows
   int *abd_ptr = nullptr, *abd_cursor = nullptr, *abd_ent = nullptr;
@@ -198,6 +200,14 @@ void inv3(const double* m, double* o, double& det) {
 
 // incidence entries: four per barrier pair and per friction pair
 ipc_status grow_inc(ipcsim* sim) {
+  const long long nd = (long long)sim->cap + sim->fcap;
+  if (nd > sim->desc_cap) {
+    dfree(sim, sim->desc);
+    sim->desc = nullptr;
+    ipc_status s = dalloc(sim, &sim->desc, (size_t)nd);
+    if (s) return s;
+    sim->desc_cap = nd;
+  }
   long long need = 4LL * ((long long)sim->cap + sim->fcap);
   if (need <= sim->inc_cap) return IPC_OK;
   dfree(sim, sim->inc);
@@ -391,6 +401,7 @@ ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric)
   a.n_fric = n_fric;
   a.f_ids = sim->f_ids;
   a.f_w = sim->f_w;
+  a.desc = sim->desc;
   a.inc_ptr = sim->inc_ptr;
   a.inc = sim->inc;
   a.b = sim->rhs;
@@ -442,7 +453,8 @@ void build_abd_contact(ipcsim* sim, int n_fric) {
 // Contact incidences of the current pairs (and friction pairs) per owner.
 void build_incidence(ipcsim* sim, int n_fric) {
   launch_incidence(sim->st, sim->S, sim->rec, &sim->sc_dev->n_pairs, sim->cap, n_fric, sim->f_ids, sim->f_w,
-                   sim->inc_ptr, sim->inc_cursor, sim->inc_tiles, sim->inc, sim->inc_cap, &sim->sc_dev->flags);
+                   sim->inc_ptr, sim->inc_cursor, sim->inc_tiles, sim->inc, sim->inc_cap, sim->desc,
+                   &sim->sc_dev->flags);
 }
 
 int pair_grid(int cap) { return std::max(1, std::min((cap + 127) / 128, 148 * 8)); }
