@@ -234,6 +234,38 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     print("e2e step ms:", e2e_steps_ms, file=sys.stderr)
+
+    # adjoint ms/step: the backward of the same steps (unprojected Hessian re-assembly at the
+    # checkpointed end state, FP64 adjoint solve, parameter contractions), replayed from checkpoints
+    adjoint = None
+    if not batched and not args.no_adjoint:
+        sim.set_state(*snap)
+        if sim.nkb:
+            sim.set_kinematic(sc["kin_T"][snap_index])
+        sim.step_index = snap_index
+        ckpt = []
+        for _ in range(args.steps):
+            z0, zd0 = sim.get_dofs()
+            k0 = sim.step_index
+            sim.step()
+            z1, _ = sim.get_dofs()
+            ckpt.append((z0, zd0, z1, k0))
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        glogE = torch.zeros(sim.nt, dtype=torch.float64, device="cuda")
+        adj_ms = []
+        for z0, zd0, z1, k0 in ckpt:
+            gz = torch.randn(sim.ndof, dtype=torch.float64, device="cuda", generator=gen)
+            gzd = 1e-2 * torch.randn(sim.ndof, dtype=torch.float64, device="cuda", generator=gen)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            sim.adjoint(z0, zd0, z1, sc["kin_T"][k0], sc["kin_T"][k0 + 1], gz, gzd, glogE)
+            a1.record(stream)
+            a1.synchronize()
+            adj_ms.append(a0.elapsed_time(a1))
+        adjoint = {"ms_per_step": round(sum(adj_ms) / len(adj_ms), 3), "steps": len(adj_ms),
+                   "solve": "FP64 PCG on the unprojected Hessian, rtol 1e-12"}
     if world > 1:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -276,6 +308,7 @@ def run_ours(args):
                                                           "active_pairs_max": max(s["n_pairs_max"] for s in stats)}),
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "adjoint": adjoint,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 96 * sim.nkb,
                     "d2h_bytes_per_step": 24 * sim.nf},
             "gpu_launches": int(launches),
@@ -420,6 +453,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default PCG launch shape")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ms/step measurement")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
                     help="default: fp64 for single scenes, mixed (FP32 PCG, FP64 residuals) for batches")
     args = ap.parse_args()

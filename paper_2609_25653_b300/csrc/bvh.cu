@@ -235,24 +235,22 @@ __global__ void k_hierarchy(int n, const unsigned* __restrict__ codes, int* __re
 // leaf boxes to nodes, then up the tree: the second child to arrive merges
 __global__ void k_refit(int n, const int* __restrict__ prim, const double* __restrict__ leaf,
                         const int* __restrict__ left, const int* __restrict__ right, const int* __restrict__ parent,
-                        int* __restrict__ flag, double* __restrict__ box) {
+                        int* __restrict__ flag, float* __restrict__ box) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int node = n - 1 + k;
-  const double* src = leaf + 6 * (size_t)prim[k];
-  double* dst = box + 6 * (size_t)node;
-  for (int q = 0; q < 6; ++q) dst[q] = src[q];
+  box_outward(leaf + 6 * (size_t)prim[k], box + 6 * (size_t)node);
   if (n == 1) return;
   int p = parent[node];
   while (p >= 0) {
     __threadfence();
     if (atomicAdd(flag + p, 1) == 0) return;
     __threadfence();
-    const volatile double* a = box + 6 * (size_t)left[p];
-    const volatile double* b = box + 6 * (size_t)right[p];
-    double* o = box + 6 * (size_t)p;
-    o[0] = fmin(a[0], b[0]); o[1] = fmin(a[1], b[1]); o[2] = fmin(a[2], b[2]);
-    o[3] = fmax(a[3], b[3]); o[4] = fmax(a[4], b[4]); o[5] = fmax(a[5], b[5]);
+    const volatile float* a = box + 6 * (size_t)left[p];
+    const volatile float* b = box + 6 * (size_t)right[p];
+    float* o = box + 6 * (size_t)p;
+    o[0] = fminf(a[0], b[0]); o[1] = fminf(a[1], b[1]); o[2] = fminf(a[2], b[2]);
+    o[3] = fmaxf(a[3], b[3]); o[4] = fmaxf(a[4], b[4]); o[5] = fmaxf(a[5], b[5]);
     p = parent[p];
   }
 }
@@ -280,7 +278,7 @@ cudaError_t bvh_alloc(Bvh& B, int n) {
   A((void**)&B.right, sizeof(int) * c);
   A((void**)&B.parent, sizeof(int) * 2 * c);
   A((void**)&B.flag, sizeof(int) * c);
-  A((void**)&B.box, sizeof(double) * 6 * 2 * c);
+  A((void**)&B.box, sizeof(float) * 6 * 2 * c);
   A((void**)&B.leafbox, sizeof(double) * 6 * c);
   A((void**)&B.hist, sizeof(int) * 256 * nblk);
   A((void**)&B.bounds, sizeof(double) * 6 * (BOUND_BLOCKS + 1));

@@ -18,7 +18,7 @@ struct Bvh {
   int* right = nullptr;
   int* parent = nullptr;     // (2 cap)
   int* flag = nullptr;       // (cap) refit arrival counters
-  double* box = nullptr;     // (2 cap, 6) lo.xyz, hi.xyz
+  float* box = nullptr;      // (2 cap, 6) node boxes lo.xyz, hi.xyz, rounded outward to FP32
   double* leafbox = nullptr; // (cap, 6) primitive boxes in primitive order
   int* hist = nullptr;       // radix histograms
   int hist_cap = 0;
@@ -27,6 +27,19 @@ struct Bvh {
 
 __device__ inline bool box_overlap(const double* a, const double* b) {
   return !(a[0] > b[3] || b[0] > a[3] || a[1] > b[4] || b[1] > a[4] || a[2] > b[5] || b[2] > a[5]);
+}
+
+// The tree's node boxes are FP32 with lower bounds rounded down and upper bounds
+// rounded up, so they contain the exact FP64 boxes: a traversal with an
+// outward-rounded query visits every leaf the FP64 test would (and possibly a
+// few more, which the exact tests after it reject).  FP32 compares issue at
+// full rate on this part; FP64 ones do not.
+__device__ inline bool box_overlap(const float* a, const float* b) {
+  return !(a[0] > b[3] || b[0] > a[3] || a[1] > b[4] || b[1] > a[4] || a[2] > b[5] || b[2] > a[5]);
+}
+__device__ inline void box_outward(const double* d, float* f) {
+  f[0] = __double2float_rd(d[0]); f[1] = __double2float_rd(d[1]); f[2] = __double2float_rd(d[2]);
+  f[3] = __double2float_ru(d[3]); f[4] = __double2float_ru(d[4]); f[5] = __double2float_ru(d[5]);
 }
 
 }  // namespace ipc

@@ -98,9 +98,34 @@ __device__ double accd(int kind, const d3* x0, const d3* p0, double s_frac, doub
   }
   double lp = (kind == 0) ? nrm[0] + fmax(nrm[1], fmax(nrm[2], nrm[3])) : fmax(nrm[0], nrm[1]) + fmax(nrm[2], nrm[3]);
   if (lp == 0.0) return tmax;
+  // A cheap lower bound of the distance (point or edge against the other primitive's bounding
+  // sphere): when even it allows a first advance (1 - s) d0 / lp past tmax, the result is tmax.
+  // The margin keeps the bound's own rounding from deciding a borderline pair.
+  {
+    d3 ca, cb;
+    double ra, rb;
+    if (kind == 0) {
+      ca = x0[0];
+      ra = 0.0;
+      cb = (1.0 / 3.0) * (x0[1] + x0[2] + x0[3]);
+      rb = 0.0;
+      for (int k = 1; k < 4; ++k) { d3 e = x0[k] - cb; rb = fmax(rb, sqrt(dot(e, e))); }
+    } else {
+      ca = 0.5 * (x0[0] + x0[1]);
+      cb = 0.5 * (x0[2] + x0[3]);
+      d3 ea = x0[0] - ca, eb = x0[2] - cb;
+      ra = sqrt(dot(ea, ea));
+      rb = sqrt(dot(eb, eb));
+    }
+    d3 dc = ca - cb;
+    const double lb = sqrt(dot(dc, dc)) - ra - rb;
+    if (lb > 0.0 && (1.0 - s_frac) * lb >= tmax * lp * (1.0 + 1e-9)) return tmax;
+  }
   double d0 = sqrt(pair_s(kind, x0));
   double target = s_frac * d0;
   double t = 0.0, tl = (1.0 - s_frac) * d0 / lp;
+  // the distance at the first advance only sets the next step: not needed when it already reaches tmax
+  if (tl >= tmax) return tmax;
   d3 xt[4];
   for (int it = 0; it < max_iter; ++it) {
     double tn = t + tl;
@@ -184,14 +209,18 @@ struct TreeView {
   const int* prim;
   const int* left;
   const int* right;
-  const double* box;
+  const float* box;
 };
 __host__ inline TreeView view(const Bvh& B) { return TreeView{B.n, B.prim, B.left, B.right, B.box}; }
 
-// Visit every leaf whose box overlaps q; f(primitive) per leaf.  Returns false on stack overflow.
+// Visit every leaf whose box overlaps q (in the outward-rounded FP32 boxes of
+// the tree, a superset of the exact overlaps); f(primitive) per leaf.  Returns
+// false on stack overflow.
 template <typename F>
-__device__ inline bool traverse(const TreeView& T, const double* q, F f) {
+__device__ inline bool traverse(const TreeView& T, const double* q64, F f) {
   if (T.n <= 0) return true;
+  float q[6];
+  box_outward(q64, q);
   int stack[STACK];
   int sp = 0;
   stack[sp++] = 0;
@@ -271,6 +300,12 @@ __global__ void k_ccd_pt_bvh(DevScene S, const double* __restrict__ xv, const do
     int3 tv = S.tris[t];
     int tvv[3] = {tv.x, tv.y, tv.z};
     if (excluded(S, &p, 1, tvv, 3)) return;
+    // the exact FP64 swept-box test (the tree's FP32 boxes are a conservative superset)
+    d3 lb = mk(inf, inf, inf), hb = mk(-inf, -inf, -inf);
+    swept(xv, pv, tv.x, lb, hb);
+    swept(xv, pv, tv.y, lb, hb);
+    swept(xv, pv, tv.z, lb, hb);
+    if (!overlap(la, ha, lb, hb)) return;
     int ids[4] = {p, tv.x, tv.y, tv.z};
     d3 x[4], pp[4];
     for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
@@ -300,6 +335,10 @@ __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const do
     int2 B = S.edges[eb];
     int va[2] = {A.x, A.y}, vb[2] = {B.x, B.y};
     if (excluded(S, va, 2, vb, 2)) return;
+    d3 lb = mk(inf, inf, inf), hb = mk(-inf, -inf, -inf);
+    swept(xv, pv, B.x, lb, hb);
+    swept(xv, pv, B.y, lb, hb);
+    if (!overlap(la, ha, lb, hb)) return;
     int ids[4] = {A.x, A.y, B.x, B.y};
     d3 x[4], pp[4];
     for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }

@@ -85,4 +85,101 @@ __device__ void project_psd(T* H) {
     }
 }
 
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Parallel cyclic Jacobi PSD projection of the symmetric n x n matrix A (n
+// even <= 12, row stride 12, shared memory) by one warp: n / 2 disjoint
+// rotations per round (round-robin pairing), n - 1 rounds per sweep, then
+// A <- V max(lambda, 0) V^T.  V (12 x 12), lam (12), rp/rq/rc/rs (6 each) are
+// shared-memory workspace.  Every lane of the warp must call it.
+__device__ inline void warp_project_psd(double* A, double* V, double* lam, int* rp, int* rq, double* rc, double* rs,
+                                        int n, int lane) {
+  for (int e = lane; e < 144; e += 32) V[e] = ((e / 12) == (e % 12)) ? 1.0 : 0.0;
+  // Gershgorin: skip when diagonally dominant with non-negative diagonal
+  bool dom = true;
+  if (lane < n) {
+    double off = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (j != lane) off += fabs(A[12 * lane + j]);
+    dom = A[13 * lane] >= off;
+  }
+  if (__all_sync(0xffffffffu, dom)) return;
+  __syncwarp();
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = lane; e < 144; e += 32) {
+      int i = e / 12, j = e % 12;
+      if (i < n && j < n) {
+        double a2 = A[e] * A[e];
+        tot += a2;
+        if (i != j) off += a2;
+      }
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if (off <= 1e-30 * tot || tot == 0.0) break;
+    for (int r = 0; r < n - 1; ++r) {
+      if (lane < n / 2) {
+        int k = lane;
+        int pa = k, pb = n - 1 - k;
+        int p = pa == 0 ? 0 : 1 + (pa - 1 + r) % (n - 1);
+        int q = 1 + (pb - 1 + r) % (n - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        double apq = A[12 * p + q];
+        double c = 1.0, sn = 0.0;
+        if (apq != 0.0) {
+          double theta = (A[12 * q + q] - A[12 * p + p]) / (2.0 * apq);
+          double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          sn = t * c;
+        }
+        rp[k] = p; rq[k] = q; rc[k] = c; rs[k] = sn;
+      }
+      __syncwarp();
+      int items = (n / 2) * n;
+      for (int it = lane; it < items; it += 32) {  // rows: A <- J^T A
+        int k = it / n, j = it % n;
+        int p = rp[k], q = rq[k];
+        double c = rc[k], sn = rs[k];
+        double apj = A[12 * p + j], aqj = A[12 * q + j];
+        A[12 * p + j] = c * apj - sn * aqj;
+        A[12 * q + j] = sn * apj + c * aqj;
+      }
+      __syncwarp();
+      for (int it = lane; it < items; it += 32) {  // columns: A <- A J, V <- V J
+        int k = it / n, i = it % n;
+        int p = rp[k], q = rq[k];
+        double c = rc[k], sn = rs[k];
+        double aip = A[12 * i + p], aiq = A[12 * i + q];
+        A[12 * i + p] = c * aip - sn * aiq;
+        A[12 * i + q] = sn * aip + c * aiq;
+        double vip = V[12 * i + p], viq = V[12 * i + q];
+        V[12 * i + p] = c * vip - sn * viq;
+        V[12 * i + q] = sn * vip + c * viq;
+      }
+      __syncwarp();
+    }
+  }
+  // A <- V max(diag, 0) V^T (eigenvalues staged in shared memory)
+  if (lane < n) lam[lane] = fmax(A[13 * lane], 0.0);
+  __syncwarp();
+  double out[5] = {0, 0, 0, 0, 0};
+  int cnt = 0;
+  for (int e = lane; e < 144; e += 32, ++cnt) {
+    int i = e / 12, j = e % 12;
+    double sacc = 0.0;
+    if (i < n && j < n)
+      for (int k = 0; k < n; ++k) sacc += V[12 * i + k] * lam[k] * V[12 * j + k];
+    out[cnt] = sacc;
+  }
+  __syncwarp();
+  cnt = 0;
+  for (int e = lane; e < 144; e += 32, ++cnt) A[e] = out[cnt];
+  __syncwarp();
+}
+
 }  // namespace ipc

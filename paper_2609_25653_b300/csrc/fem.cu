@@ -403,6 +403,67 @@ __global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kapp
   if (threadIdx.x == 0) atomicAdd(E, s);
 }
 
+// The same energy, gradient and projected Hessian with one warp per body: the
+// 9x9 Hessian is built by the lanes in shared memory (padded to 10 x 10 with a
+// zero row and column, which keeps eigenvalue 0) and projected by the warp's
+// parallel Jacobi, so a body costs microseconds instead of a serial 9x9 sweep.
+constexpr int ORTH_WARPS = 4;
+struct OrthWork {
+  double H[144];
+  double V[144];
+  double lam[12];
+  double rc[6], rs[6];
+  int rp[6], rq[6];
+};
+
+__global__ void __launch_bounds__(32 * ORTH_WARPS) k_abd_orth_warp(DevScene S, const double* __restrict__ z,
+                                                                    double kappa_A, double scale, int mode, int project,
+                                                                    double* __restrict__ g, double* __restrict__ Hval,
+                                                                    double* __restrict__ E) {
+  __shared__ OrthWork work[ORTH_WARPS];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * ORTH_WARPS + wid;
+  if (b >= S.nab) return;  // whole warps leave together
+  OrthWork& W = work[wid];
+  const int base = S.nf + 4 * b;
+  const d3 a[3] = {ld3(z, base + 1), ld3(z, base + 2), ld3(z, base + 3)};
+  const double k = kappa_A * S.abd_vol[b];
+  double G[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) G[i][j] = dot(a[i], a[j]) - (i == j ? 1.0 : 0.0);
+  if (lane == 0) {
+    double e = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) e += G[i][j] * G[i][j];
+    atomicAdd(E, k * e);
+  }
+  if (mode >= 1 && lane < 9) {
+    const int i = lane / 3, c = lane % 3;
+    const double gi = 4.0 * k * (G[i][0] * comp(a[0], c) + G[i][1] * comp(a[1], c) + G[i][2] * comp(a[2], c));
+    atomicAdd(g + 3 * (base + 1 + i) + c, scale * gi);
+  }
+  if (mode < 2) return;
+  for (int e = lane; e < 144; e += 32) {
+    const int row = e / 12, col = e % 12;
+    double h = 0.0;
+    if (row < 9 && col < 9) {
+      const int ki = row / 3, r = row % 3, li = col / 3, c = col % 3;
+      h = comp(a[li], r) * comp(a[ki], c) + (r == c ? G[ki][li] : 0.0);
+      if (ki == li) h += comp(a[0], r) * comp(a[0], c) + comp(a[1], r) * comp(a[1], c) + comp(a[2], r) * comp(a[2], c);
+      h *= 4.0 * k;
+    }
+    W.H[e] = h;
+  }
+  __syncwarp();
+  if (project) warp_project_psd(W.H, W.V, W.lam, W.rp, W.rq, W.rc, W.rs, 10, lane);
+  for (int e = lane; e < 81; e += 32) {
+    const int row = e / 9, col = e % 9;
+    const int ki = row / 3, r = row % 3, li = col / 3, c = col % 3;
+    double* dst = Hval + 9 * (size_t)S.abd_blk[16 * b + 4 * (1 + ki) + (1 + li)];
+    atomicAdd(dst + 3 * r + c, scale * W.H[12 * row + col]);
+  }
+}
+
 // z_out = z + alpha p ; xk_out = alpha == 1 ? xk_hat : xk + alpha pD
 __global__ void k_trial(int ndof, int nk3, const double* __restrict__ z, const double* __restrict__ p, double alpha,
                         double* __restrict__ z_out, const double* __restrict__ xk, const double* __restrict__ pD,
@@ -470,7 +531,13 @@ void launch_stitch(cudaStream_t st, const DevScene& S, const double* xv, const d
 }
 void launch_abd_orth(cudaStream_t st, const DevScene& S, const double* z, double kappa_A, double scale, int mode,
                      int project, double* g, double* Hval, double* E) {
-  if (S.nab) { k_abd_orth<<<nb(S.nab, 64), 64, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E); count_launch(); }
+  if (S.nab) {
+    if (mode >= 2)
+      k_abd_orth_warp<<<nb(S.nab, ORTH_WARPS), 32 * ORTH_WARPS, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E);
+    else
+      k_abd_orth<<<nb(S.nab, 64), 64, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E);
+    count_launch();
+  }
 }
 void launch_trial(cudaStream_t st, int ndof, int nk3, const double* z, const double* p, double alpha, double* z_out,
                   const double* xk, const double* pD, const double* xk_hat, double* xk_out) {

@@ -568,7 +568,7 @@ __device__ inline void fem_products(const PcgArgs& a, int r0, int r1, int k0, Op
   __syncthreads();
   // incidences e of the segment, consecutive per lane; their owners are non-decreasing, so the
   // contributions of one owner are summed by a segmented warp scan and added once per run
-  const int e0 = a.inc_ptr[r0], e1 = a.inc_ptr[r1];
+  const int e0 = a.inc_ptr[r0], e1 = (int)min((long long)a.inc_ptr[r1], a.inc_cap);
   const int lane = threadIdx.x & 31;
   for (int eb = e0; eb < e1; eb += blockDim.x) {
     const int e = eb + threadIdx.x;
@@ -653,7 +653,8 @@ __device__ inline void abd_products(const PcgArgs& a, int b, OpView<M> op, const
     y1 = fma((A)H[3 * sq], v0, fma((A)H[4 * sq], v1, fma((A)H[5 * sq], v2, y1)));
     y2 = fma((A)H[6 * sq], v0, fma((A)H[7 * sq], v1, fma((A)H[8 * sq], v2, y2)));
   }
-  const int e0 = a.abd_ptr[b], e1 = a.abd_ptr[b + 1];
+  // an overflowed list (the Newton iteration is then redone with a larger one) is read only up to its capacity
+  const int e0 = a.abd_ptr[b], e1 = (int)min((long long)a.abd_ptr[b + 1], a.abd_cap);
 #pragma unroll 4
   for (int e = e0 + 4 * slot + t; e < e1; e += 4 * nslot) {
     if (!pcg_ok(a, e >= 0 && e < a.abd_cap, 9)) break;

@@ -199,6 +199,8 @@ void inv3(const double* m, double* o, double& det) {
 }
 
 // incidence entries: four per barrier pair and per friction pair
+ipc_status grow_abd_list(ipcsim* sim, long long need);
+
 ipc_status grow_inc(ipcsim* sim) {
   const long long nd = (long long)sim->cap + sim->fcap;
   if (nd > sim->desc_cap) {
@@ -207,6 +209,11 @@ ipc_status grow_inc(ipcsim* sim) {
     ipc_status s = dalloc(sim, &sim->desc, (size_t)nd);
     if (s) return s;
     sim->desc_cap = nd;
+  }
+  // ABD coupling blocks: twelve per pair cover a pair with one ABD body and three other vertices
+  if (sim->nab) {
+    ipc_status s = grow_abd_list(sim, 12 * nd);
+    if (s) return s;
   }
   long long need = 4LL * ((long long)sim->cap + sim->fcap);
   if (need <= sim->inc_cap) return IPC_OK;
@@ -1001,7 +1008,7 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   if (nab) {
     if ((s = dalloc(sim, &sim->abd_ptr, (size_t)nab + 1))) return fail(s, "");
     if ((s = dalloc(sim, &sim->abd_cursor, (size_t)nab + 1))) return fail(s, "");
-    if ((s = grow_abd_list(sim, 4096))) return fail(s, "");
+    if ((s = grow_abd_list(sim, std::max<long long>(4096, 12LL * (sim->cap + sim->fcap))))) return fail(s, "");
   }
   if (P.precision == IPC_PREC_MIXED)
     if ((s = dalloc(sim, &sim->Dinv32, 9 * (size_t)n_nodes))) return fail(s, "");
