@@ -2,6 +2,7 @@
 // predictor, kinematic targets, vertex positions, inertia, Neo-Hookean
 // elasticity (§III-C.1), stitch springs (Eq. 2), affine-body orthogonality,
 // step update and velocities.
+#include <type_traits>
 #include "common.cuh"
 #include "eig.cuh"
 #include "kernels.h"
@@ -234,10 +235,144 @@ __device__ inline void snh_projected_hessian(const d3* f, double mu, double lam,
   }
 }
 
+// The same projection in FP32, for the mixed-precision path (whose operator is
+// applied in FP32 anyway): the FP64 pipe of this part issues 2 FMA per clock
+// per SM and this projection is ~3k FMA per tet; the FP32 pipe issues 128.
+__device__ inline void jacobi3f(float* A, float* V) {
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.f : 0.f;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    float off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    float tot = A[0] * A[0] + A[4] * A[4] + A[8] * A[8] + 2.f * off;
+    if (off <= 1e-14f * tot || tot == 0.f) break;
+    const int P[3] = {0, 0, 1}, Q[3] = {1, 2, 2};
+    for (int r = 0; r < 3; ++r) {
+      int p = P[r], q = Q[r];
+      float apq = A[3 * p + q];
+      if (apq == 0.f) continue;
+      float theta = (A[3 * q + q] - A[3 * p + p]) / (2.f * apq);
+      float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+      float c = 1.f / sqrtf(t * t + 1.f), sn = t * c;
+      for (int k = 0; k < 3; ++k) {
+        float akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = c * akp - sn * akq;
+        A[3 * k + q] = sn * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        float apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = c * apk - sn * aqk;
+        A[3 * q + k] = sn * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        float vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - sn * vkq;
+        V[3 * k + q] = sn * vkp + c * vkq;
+      }
+    }
+  }
+}
+
+__device__ inline float dotf3(const float* a, const float* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ inline void crossf3(const float* a, const float* b, float* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// FP32 counterpart of snh_projected_hessian (same modes and eigenvalues).
+__device__ inline void snh_projected_hessian_f32(const d3* fd, double mu_d, double lam_d, const double Cc_d[4][3],
+                                                 double sv_d, float* H12) {
+  float f[3][3];
+  for (int j = 0; j < 3; ++j) { f[j][0] = (float)fd[j].x; f[j][1] = (float)fd[j].y; f[j][2] = (float)fd[j].z; }
+  const float mu = (float)mu_d, lam = (float)lam_d, sv = (float)sv_d;
+  float Cc[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int j = 0; j < 3; ++j) Cc[a][j] = (float)Cc_d[a][j];
+  // rotation-variant SVD F = U diag(s) V^T from the eigen-decomposition of F^T F
+  float A[9], Vm[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[3 * i + j] = dotf3(f[i], f[j]);
+  jacobi3f(A, Vm);
+  float e[3] = {A[0], A[4], A[8]};
+  int ord[3] = {0, 1, 2};
+  for (int a = 0; a < 2; ++a)
+    for (int b = a + 1; b < 3; ++b)
+      if (e[ord[b]] > e[ord[a]]) { int t = ord[a]; ord[a] = ord[b]; ord[b] = t; }
+  float V[3][3];
+  for (int m = 0; m < 3; ++m) { V[m][0] = Vm[ord[m]]; V[m][1] = Vm[3 + ord[m]]; V[m][2] = Vm[6 + ord[m]]; }
+  float c01[3];
+  crossf3(V[0], V[1], c01);
+  if (dotf3(c01, V[2]) < 0.f) { V[2][0] = -V[2][0]; V[2][1] = -V[2][1]; V[2][2] = -V[2][2]; }
+  float bvec[3][3];
+  for (int m = 0; m < 3; ++m)
+    for (int d = 0; d < 3; ++d) bvec[m][d] = V[m][0] * f[0][d] + V[m][1] * f[1][d] + V[m][2] * f[2][d];
+  float U[3][3];
+  const float n0 = sqrtf(dotf3(bvec[0], bvec[0]));
+  for (int d = 0; d < 3; ++d) U[0][d] = n0 > 1e-30f ? bvec[0][d] / n0 : (d == 0 ? 1.f : 0.f);
+  float u1[3];
+  const float pr = dotf3(U[0], bvec[1]);
+  for (int d = 0; d < 3; ++d) u1[d] = bvec[1][d] - pr * U[0][d];
+  const float n1 = sqrtf(dotf3(u1, u1));
+  if (n1 > 1e-6f * (n0 + 1e-30f)) {
+    for (int d = 0; d < 3; ++d) u1[d] /= n1;
+  } else {
+    float t[3] = {fabsf(U[0][0]) < 0.9f ? 1.f : 0.f, fabsf(U[0][0]) < 0.9f ? 0.f : 1.f, 0.f};
+    crossf3(U[0], t, u1);
+    const float nn = sqrtf(dotf3(u1, u1));
+    for (int d = 0; d < 3; ++d) u1[d] /= nn;
+  }
+  for (int d = 0; d < 3; ++d) U[1][d] = u1[d];
+  crossf3(U[0], U[1], U[2]);
+  const float s[3] = {dotf3(U[0], bvec[0]), dotf3(U[1], bvec[1]), dotf3(U[2], bvec[2])};
+  const float J = s[0] * s[1] * s[2];
+  const float kJ = lam * (J - 1.f) - mu;
+  for (int i = 0; i < 144; ++i) H12[i] = 0.f;
+  float Vt_c[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int m = 0; m < 3; ++m) Vt_c[a][m] = V[m][0] * Cc[a][0] + V[m][1] * Cc[a][1] + V[m][2] * Cc[a][2];
+  auto add_mode = [&](const float* B, float lamb) {
+    if (!(lamb > 0.f)) return;
+    float w[12];
+    for (int a = 0; a < 4; ++a) {
+      const float y0 = B[0] * Vt_c[a][0] + B[1] * Vt_c[a][1] + B[2] * Vt_c[a][2];
+      const float y1 = B[3] * Vt_c[a][0] + B[4] * Vt_c[a][1] + B[5] * Vt_c[a][2];
+      const float y2 = B[6] * Vt_c[a][0] + B[7] * Vt_c[a][1] + B[8] * Vt_c[a][2];
+      for (int d = 0; d < 3; ++d) w[3 * a + d] = y0 * U[0][d] + y1 * U[1][d] + y2 * U[2][d];
+    }
+    const float c = sv * lamb;
+    for (int i = 0; i < 12; ++i) {
+      const float ci = c * w[i];
+      for (int j = 0; j < 12; ++j) H12[12 * i + j] += ci * w[j];
+    }
+  };
+  const float r2 = 0.70710678f;
+  const int PI[3] = {1, 0, 0}, PJ[3] = {2, 2, 1};
+  for (int k = 0; k < 3; ++k) {
+    const int i = PI[k], j = PJ[k];
+    float B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    B[3 * i + j] = r2; B[3 * j + i] = -r2;
+    add_mode(B, mu + kJ * s[k]);
+    B[3 * j + i] = r2;
+    add_mode(B, mu - kJ * s[k]);
+  }
+  const float c3[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+  float Am[9], Y[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Am[3 * i + j] = (i == j ? mu : 0.f) + lam * c3[i] * c3[j];
+  Am[1] += kJ * s[2]; Am[3] += kJ * s[2];
+  Am[2] += kJ * s[1]; Am[6] += kJ * s[1];
+  Am[5] += kJ * s[0]; Am[7] += kJ * s[0];
+  jacobi3f(Am, Y);
+  for (int q = 0; q < 3; ++q) {
+    const float B[9] = {Y[q], 0, 0, 0, Y[3 + q], 0, 0, 0, Y[6 + q]};
+    add_mode(B, Am[4 * q]);
+  }
+}
+
 // Neo-Hookean energy Psi = mu/2 (|F|^2 - 3) - mu (J - 1) + lam/2 (J - 1)^2 per tet (§III-C.1),
 // its gradient and PSD-projected Hessian scattered into the BSR matrix.
 // scale = dt^2 for the incremental potential; mode: 0 energy only, 1 + gradient, 2 + Hessian.
-template <typename HT>
+// F32H: the projected Hessian in FP32 (mixed precision); energy and gradient always FP64.
+template <typename HT, bool F32H>
 __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __restrict__ xv, double scale, int mode,
                                                  int project, double* __restrict__ g, HT* __restrict__ Hval,
                                                  double* __restrict__ tetH, double* __restrict__ E) {
@@ -276,8 +411,10 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
         atomicAdd(g + 3 * id[a] + 2, sv * ga.z);
       }
       if (mode >= 2 && project) {
-        double H12[144];
-        snh_projected_hessian(f, mu, lam, Cc, sv, H12);
+        using HC = typename std::conditional<F32H, float, double>::type;
+        HC H12[144];
+        if constexpr (F32H) snh_projected_hessian_f32(f, mu, lam, Cc, sv, H12);
+        else snh_projected_hessian(f, mu, lam, Cc, sv, H12);
         for (int a = 0; a < 4; ++a)
           for (int b = 0; b < 4; ++b) {
             if (Hval) {
@@ -522,8 +659,13 @@ void launch_inertia(cudaStream_t st, const DevScene& S, const double* z, const d
   if (S.n_nodes) { k_inertia<<<nb(S.n_nodes, 256), 256, 0, st>>>(S, z, z_tilde, g, E, want_grad); count_launch(); }
 }
 void launch_elastic(cudaStream_t st, const DevScene& S, const double* xv, double scale, int mode, int project,
-                    double* g, double* Hval, double* tetH, double* E) {
-  if (S.nt) { k_elastic<double><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E); count_launch(); }
+                    double* g, double* Hval, double* tetH, double* E, int hess_fp32) {
+  if (!S.nt) return;
+  if (hess_fp32 && mode >= 2 && project)
+    k_elastic<double, true><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+  else
+    k_elastic<double, false><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+  count_launch();
 }
 void launch_stitch(cudaStream_t st, const DevScene& S, const double* xv, const double* stitch_hat, double k_c,
                    double scale, int mode, double* g, double* E) {

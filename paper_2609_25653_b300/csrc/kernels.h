@@ -88,8 +88,9 @@ void launch_vertex_positions(cudaStream_t, const DevScene&, const double* z, con
 void launch_vertex_disp(cudaStream_t, const DevScene&, const double* p, const double* pD, double* pv);
 void launch_inertia(cudaStream_t, const DevScene&, const double* z, const double* z_tilde, double* g, double* E,
                     int want_grad);
+// hess_fp32: the projected Hessian in FP32 (mixed precision); energy and gradient stay FP64
 void launch_elastic(cudaStream_t, const DevScene&, const double* xv, double scale, int mode, int project, double* g,
-                    double* Hval, double* tetH, double* E);
+                    double* Hval, double* tetH, double* E, int hess_fp32 = 0);
 void launch_stitch(cudaStream_t, const DevScene&, const double* xv, const double* stitch_hat, double k_c, double scale,
                    int mode, double* g, double* E);
 void launch_abd_orth(cudaStream_t, const DevScene&, const double* z, double kappa_A, double scale, int mode, int project,

@@ -1245,7 +1245,8 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     }
     launch_inertia(cs, S, sim->z, sim->z_tilde, sim->g, &sim->sc_dev->E[0], 1);
     prof_begin(sim, PROF_ELASTIC);
-    launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
+    launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1],
+                   P.precision == IPC_PREC_MIXED);
     prof_end(sim, PROF_ELASTIC);
     launch_stitch(cs, S, sim->xv, sim->stitch_hat, sim->k_c, dt2, 1, sim->g, &sim->sc_dev->E[4]);
     launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g, sim->Hval, &sim->sc_dev->E[5]);
