@@ -53,9 +53,22 @@ struct DevScene {
   const int* body_scene;     // (nbody)
   const double* scene_kappa; // (n_scenes)
   const double* scene_kc;    // (n_scenes)
+  // per-scene Newton control of a batch (null for a single scene): scene of every
+  // node, energy terms per scene (n_scenes, 8), CCD bound per scene (double bits),
+  // max |p_F| and max |p_D| per scene (double bits), line-search step per scene
+  const int* node_scene;
+  double* E_sc;
+  unsigned long long* alpha_sc;
+  unsigned long long* pn_sc;
+  const double* alpha_trial;
 };
 
 __device__ inline int scene_of_vertex(const DevScene& S, int v) { return S.body_scene[S.vbody[v]]; }
+
+// energy term comp of one element of scene sc (batches only)
+__device__ inline void scene_energy(const DevScene& S, int sc, int comp, double e) {
+  if (S.E_sc && e != 0.0) atomicAdd(S.E_sc + 8 * sc + comp, e);
+}
 
 // ---------------------------------------------------------------------------
 // small vector helpers

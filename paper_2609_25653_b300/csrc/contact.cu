@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
       if (mode == 0) {
         double m = kind == 1 ? moll_value(x, eps_x) : 1.0;
         e_acc += kappa * m * b;
+        if (S.E_sc) scene_energy(S, scene_of_vertex(S, ids[0]), 2, kappa * m * b);
       } else if (b != 0.0 || b1 != 0.0) {
         double gs[12], Hs[144];
         red_expand(R, gs, Hs);
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
           if (dot(nn, nn) < eps_x) { m = mollifier(x, eps_x, gm, Hm); moll = true; }
         }
         e_acc += kappa * m * b;
+        if (S.E_sc) scene_energy(S, scene_of_vertex(S, ids[0]), 2, kappa * m * b);
         double grad[12];
         for (int i = 0; i < 12; ++i) grad[i] = kappa * (m * b1 * gs[i] + (moll ? b * gm[i] : 0.0));
         double* H = pairH + 144 * (size_t)k;
@@ -328,6 +330,7 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
       W.sc[0] = sd; W.sc[1] = b; W.sc[2] = b1; W.sc[3] = b2; W.sc[4] = mval; W.sc[5] = m1; W.sc[6] = m2;
       smin = fmin(smin, sd);
       e_acc += kappa * mval * b;
+      if (S.E_sc) scene_energy(S, scene_of_vertex(S, W.ids[0]), 2, kappa * mval * b);
     }
     __syncwarp();
     double b = W.sc[1], b1 = W.sc[2], b2 = W.sc[3], mval = W.sc[4], m1 = W.sc[5], m2 = W.sc[6];
@@ -504,6 +507,7 @@ __global__ void k_friction(DevScene S, const double* __restrict__ xv, const doub
     double c = mu * f_lam[k];
     double f0 = y < eps ? -y * y * y / (3.0 * eps * eps) + y * y / eps + eps / 3.0 : y;
     e_acc = c * f0;
+    if (S.E_sc) scene_energy(S, scene_of_vertex(S, ids[0]), 3, e_acc);
     if (mode >= 1) {
       double a = y < eps ? (-y / (eps * eps) + 2.0 / eps) : 1.0 / y;
       d3 gu = (c * a) * t;

@@ -171,7 +171,10 @@ __global__ void k_ccd_pt_brute(DevScene S, const double* __restrict__ xv, const 
   for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
   atomicAdd(n_cand, 1);
   double toi = accd(0, x, pp, s_frac, 1.0, max_iter);
-  if (toi < 1.0) atomicMin(alpha_bits, dbits(toi));
+  if (toi < 1.0) {
+    atomicMin(alpha_bits, dbits(toi));
+    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, p), dbits(toi));
+  }
 }
 
 __global__ void k_ccd_ee_brute(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
@@ -196,7 +199,10 @@ __global__ void k_ccd_ee_brute(DevScene S, const double* __restrict__ xv, const 
   for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
   atomicAdd(n_cand, 1);
   double toi = accd(1, x, pp, s_frac, 1.0, max_iter);
-  if (toi < 1.0) atomicMin(alpha_bits, dbits(toi));
+  if (toi < 1.0) {
+    atomicMin(alpha_bits, dbits(toi));
+    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, ids[0]), dbits(toi));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -314,7 +320,10 @@ __global__ void k_ccd_pt_bvh(DevScene S, const double* __restrict__ xv, const do
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_cand, nc);
-  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+  if (amin < 1.0) {
+    atomicMin(alpha_bits, dbits(amin));
+    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, p), dbits(amin));
+  }
 }
 
 __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
@@ -347,7 +356,10 @@ __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const do
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_cand, nc);
-  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+  if (amin < 1.0) {
+    atomicMin(alpha_bits, dbits(amin));
+    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, A.x), dbits(amin));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -400,7 +412,10 @@ __global__ void k_sweep_pt_bvh(DevScene S, const double* __restrict__ xv, const 
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_ccd, nc);
-  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+  if (amin < 1.0) {
+    atomicMin(alpha_bits, dbits(amin));
+    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, p), dbits(amin));
+  }
 }
 
 __global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
@@ -435,7 +450,10 @@ __global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const 
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_ccd, nc);
-  if (amin < 1.0) atomicMin(alpha_bits, dbits(amin));
+  if (amin < 1.0) {
+    atomicMin(alpha_bits, dbits(amin));
+    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, A.x), dbits(amin));
+  }
 }
 
 // Active pairs among the candidates: the exact classification and s < dhat^2 at xv.

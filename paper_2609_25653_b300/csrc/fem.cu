@@ -83,6 +83,7 @@ __global__ void k_inertia(DevScene S, const double* __restrict__ z, const double
     d3 dz = ld3(z, i) - ld3(z_tilde, i);
     double m = S.node_mass[i];
     e = 0.5 * m * dot(dz, dz);
+    if (S.E_sc) scene_energy(S, S.node_scene[i], 0, e);
     if (want_grad) st3(g, i, m * dz);
   } else if (i < S.n_nodes) {
     int b = (i - S.nf) / 4, r = (i - S.nf) % 4;
@@ -91,6 +92,7 @@ __global__ void k_inertia(DevScene S, const double* __restrict__ z, const double
     d3 acc = mk(0, 0, 0);
     for (int s = 0; s < 4; ++s) acc = acc + Sm[4 * r + s] * (ld3(z, base + s) - ld3(z_tilde, base + s));
     e = 0.5 * dot(ld3(z, i) - ld3(z_tilde, i), acc);
+    if (S.E_sc) scene_energy(S, S.node_scene[i], 0, e);
     if (want_grad) st3(g, i, acc);
   }
   double s = block_sum(e);
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
     double Ic = dot(f[0], f[0]) + dot(f[1], f[1]) + dot(f[2], f[2]);
     double mu = S.mu[e], lam = S.lam[e], V = S.vol[e];
     energy = V * (0.5 * mu * (Ic - 3.0) - mu * (J - 1.0) + 0.5 * lam * (J - 1.0) * (J - 1.0));
+    if (S.E_sc) scene_energy(S, scene_of_vertex(S, id[0]), 1, energy);
     if (mode >= 1) {
       double kJ = lam * (J - 1.0) - mu;
       d3 Pc[3];  // columns of P
@@ -480,6 +483,7 @@ __global__ void k_stitch(DevScene S, const double* __restrict__ xv, const double
     const double k_c = S.scene_kc[scene_of_vertex(S, v)];
     d3 d = ld3(xv, v) - ld3(stitch_hat, i);
     e = 0.5 * k_c * dot(d, d);
+    if (S.E_sc) scene_energy(S, scene_of_vertex(S, v), 4, e);
     if (mode >= 1) {
       atomicAdd(g + 3 * v, scale * k_c * d.x);
       atomicAdd(g + 3 * v + 1, scale * k_c * d.y);
@@ -505,6 +509,7 @@ __global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kapp
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) e += G[i][j] * G[i][j];
     e *= k;
+    if (S.E_sc) scene_energy(S, S.node_scene[base], 5, e);
     if (mode >= 1) {
       for (int i = 0; i < 3; ++i) {
         d3 gi = 4.0 * k * (G[i][0] * a[0] + G[i][1] * a[1] + G[i][2] * a[2]);
@@ -573,6 +578,7 @@ __global__ void __launch_bounds__(32 * ORTH_WARPS) k_abd_orth_warp(DevScene S, c
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) e += G[i][j] * G[i][j];
     atomicAdd(E, k * e);
+    if (S.E_sc) scene_energy(S, S.node_scene[base], 5, k * e);
   }
   if (mode >= 1 && lane < 9) {
     const int i = lane / 3, c = lane % 3;
@@ -627,6 +633,32 @@ __global__ void k_pnorm(int ndof, const double* __restrict__ p, int nk3, const d
   if (threadIdx.x == 0) atomicMax(out, dbits(a));
   b = block_max(b);
   if (threadIdx.x == 0) atomicMax(out + 1, dbits(b));
+}
+
+// Batches: max |p_F| and max |p_D| per scene.
+__global__ void k_pnorm_scenes(DevScene S, int ndof, const double* __restrict__ p, int nk3,
+                               const double* __restrict__ pD) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ndof) {
+    const double a = isfinite(p[i]) ? fabs(p[i]) : 1e300;
+    if (a > 0.0) atomicMax(S.pn_sc + 2 * S.node_scene[i / 3], dbits(a));
+  }
+  if (i < nk3 && pD[i] != 0.0) {
+    const int v = S.nf + S.na_v + i / 3;
+    atomicMax(S.pn_sc + 2 * scene_of_vertex(S, v) + 1, dbits(fabs(pD[i])));
+  }
+}
+
+// Batches: z_out = z + alpha_s p and xk_out = (alpha_s == 1 ? xk_hat : xk + alpha_s pD) with the step of each scene.
+__global__ void k_trial_scenes(DevScene S, int ndof, int nk3, const double* __restrict__ z, const double* __restrict__ p,
+                               double* __restrict__ z_out, const double* __restrict__ xk, const double* __restrict__ pD,
+                               const double* __restrict__ xk_hat, double* __restrict__ xk_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ndof) z_out[i] = z[i] + S.alpha_trial[S.node_scene[i / 3]] * p[i];
+  if (i < nk3) {
+    const double al = S.alpha_trial[scene_of_vertex(S, S.nf + S.na_v + i / 3)];
+    xk_out[i] = (al == 1.0) ? xk_hat[i] : xk[i] + al * pD[i];
+  }
 }
 
 // p_D = xk_hat - xk
@@ -692,6 +724,18 @@ void launch_velocity(cudaStream_t st, int ndof, const double* z, const double* z
 void launch_pnorm(cudaStream_t st, int ndof, const double* p, int nk3, const double* pD, unsigned long long* out) {
   int n = ndof > nk3 ? ndof : nk3;
   if (n) { k_pnorm<<<nb(n, 256), 256, 0, st>>>(ndof, p, nk3, pD, out); count_launch(); }
+}
+void launch_pnorm_scenes(cudaStream_t st, const DevScene& S, int ndof, const double* p, int nk3, const double* pD) {
+  int n = ndof > nk3 ? ndof : nk3;
+  if (n) { k_pnorm_scenes<<<nb(n, 256), 256, 0, st>>>(S, ndof, p, nk3, pD); count_launch(); }
+}
+void launch_trial_scenes(cudaStream_t st, const DevScene& S, int ndof, int nk3, const double* z, const double* p,
+                         double* z_out, const double* xk, const double* pD, const double* xk_hat, double* xk_out) {
+  int n = ndof > nk3 ? ndof : nk3;
+  if (n) {
+    k_trial_scenes<<<nb(n, 256), 256, 0, st>>>(S, ndof, nk3, z, p, z_out, xk, pD, xk_hat, xk_out);
+    count_launch();
+  }
 }
 void launch_sub(cudaStream_t st, int n, const double* a, const double* b, double* o) {
   if (n) { k_sub<<<nb(n, 256), 256, 0, st>>>(n, a, b, o); count_launch(); }

@@ -99,6 +99,10 @@ void launch_trial(cudaStream_t, int ndof, int nk3, const double* z, const double
                   const double* xk, const double* pD, const double* xk_hat, double* xk_out);
 void launch_velocity(cudaStream_t, int ndof, const double* z, const double* z_t, double inv_dt, double* zd);
 void launch_pnorm(cudaStream_t, int ndof, const double* p, int nk3, const double* pD, unsigned long long* out);
+// batches: per-scene max |p_F|, |p_D| into S.pn_sc; trial step with the step of each scene (S.alpha_trial)
+void launch_pnorm_scenes(cudaStream_t, const DevScene& S, int ndof, const double* p, int nk3, const double* pD);
+void launch_trial_scenes(cudaStream_t, const DevScene& S, int ndof, int nk3, const double* z, const double* p,
+                         double* z_out, const double* xk, const double* pD, const double* xk_hat, double* xk_out);
 void launch_sub(cudaStream_t, int n, const double* a, const double* b, double* o);
 
 // contact.cu

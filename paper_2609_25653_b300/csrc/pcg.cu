@@ -1343,31 +1343,145 @@ void launch_to_float(cudaStream_t st, size_t n, const double* src, float* dst, c
 }
 
 // Partition of the rows among the CTAs of a PCG launch (see PcgPlan).
-void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, PcgPlan& P) {
+namespace {
+// n_parts contiguous cuts of [lo, hi) balanced by the prefix cost pre (pre[i] = cost of [0, i)); appends the
+// n_parts - 1 inner boundaries and hi
+void cut_balanced(const std::vector<long long>& pre, int lo, int hi, int n_parts, std::vector<int>& out) {
+  int cur = lo;
+  const long long c0 = pre[lo], tot = pre[hi] - c0;
+  for (int c = 1; c < n_parts; ++c) {
+    const long long target = c0 + tot * c / n_parts;
+    while (cur < hi && pre[cur] < target) ++cur;
+    out.push_back(cur);
+  }
+  out.push_back(hi);
+}
+// at least one part for every item of nonzero cost, the rest in proportion to the cost (largest remainders)
+std::vector<int> share_parts(const std::vector<long long>& cost, int n_parts) {
+  const int n = (int)cost.size();
+  std::vector<int> k(n, 0);
+  long long tot = 0;
+  int used = 0;
+  for (int s = 0; s < n; ++s)
+    if (cost[s] > 0) { k[s] = 1; ++used; tot += cost[s]; }
+  const int rest = n_parts - used;
+  if (rest <= 0 || tot == 0) return k;
+  std::vector<std::pair<long long, int>> frac;
+  int given = 0;
+  for (int s = 0; s < n; ++s) {
+    if (!cost[s]) continue;
+    const long long q = (long long)rest * cost[s];
+    k[s] += (int)(q / tot);
+    given += (int)(q / tot);
+    frac.push_back({q % tot, s});
+  }
+  std::sort(frac.begin(), frac.end(), [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) {
+    return x.first != y.first ? x.first > y.first : x.second < y.second;
+  });
+  for (int j = 0; given < rest && j < (int)frac.size(); ++j, ++given) ++k[frac[j].second];
+  return k;
+}
+}  // namespace
+
+void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, const std::vector<int>& node_scene,
+                   int n_scenes, PcgPlan& P) {
   P.grid = grid;
-  P.n_abd_ctas = nab > 0 ? std::min(nab, std::max(1, grid / 8)) : 0;
-  P.n_fem_ctas = std::max(1, grid - P.n_abd_ctas);
-  if (P.n_fem_ctas + P.n_abd_ctas > grid) P.n_abd_ctas = grid - P.n_fem_ctas;
-  // balance FEM rows by stored blocks plus a per-row cost
-  const int nc = P.n_fem_ctas;
+  // FEM rows balanced by stored blocks plus a per-row cost; ABD bodies by count
   std::vector<long long> pre(nf + 1, 0);
   for (int i = 0; i < nf; ++i) pre[i + 1] = pre[i] + (row[i + 1] - row[i]) + 2;
-  P.seg.assign(1, 0);
-  int cur = 0;
-  for (int c = 1; c < nc; ++c) {
-    long long target = pre[nf] * c / nc;
-    while (cur < nf && pre[cur] < target) ++cur;
-    P.seg.push_back(cur);
+  std::vector<long long> bpre(nab + 1);
+  for (int b = 0; b <= nab; ++b) bpre[b] = b;
+
+  // per-scene solves need the rows of every scene contiguous, a CTA of their own for each scene's FEM rows
+  // and ABD bodies, and at most PCG_SCENES_MAX scenes
+  std::vector<int> fem_lo, abd_lo;  // first row / body of every scene, then the end
+  bool per_scene = n_scenes > 1 && n_scenes <= PCG_SCENES_MAX && (int)node_scene.size() >= nf + 4 * nab;
+  if (per_scene) {
+    fem_lo.assign(n_scenes + 1, nf);
+    abd_lo.assign(n_scenes + 1, nab);
+    int last = 0;
+    for (int i = 0; i < nf && per_scene; ++i) {
+      const int s = node_scene[i];
+      if (s < last || s >= n_scenes) per_scene = false;
+      else for (; last < s; ++last) fem_lo[last + 1] = i;
+    }
+    for (int s = 0; s <= n_scenes; ++s) if (s > last) fem_lo[s] = nf;
+    fem_lo[0] = 0;
+    last = 0;
+    for (int b = 0; b < nab && per_scene; ++b) {
+      const int s = node_scene[nf + 4 * b];
+      if (s < last || s >= n_scenes) per_scene = false;
+      else for (; last < s; ++last) abd_lo[last + 1] = b;
+    }
+    for (int s = 0; s <= n_scenes; ++s) if (s > last) abd_lo[s] = nab;
+    abd_lo[0] = 0;
   }
-  P.seg.push_back(nf);
+  std::vector<long long> fcost, acost;
+  int fem_scenes = 0, abd_scenes = 0;
+  if (per_scene) {
+    fcost.resize(n_scenes);
+    acost.resize(n_scenes);
+    for (int s = 0; s < n_scenes; ++s) {
+      fcost[s] = pre[fem_lo[s + 1]] - pre[fem_lo[s]];
+      acost[s] = abd_lo[s + 1] - abd_lo[s];
+      fem_scenes += fcost[s] > 0;
+      abd_scenes += acost[s] > 0;
+    }
+    P.n_abd_ctas = nab > 0 ? std::min(nab, std::max(abd_scenes, grid / 8)) : 0;
+    P.n_fem_ctas = grid - P.n_abd_ctas;
+    if (P.n_fem_ctas < std::max(1, fem_scenes)) per_scene = false;
+  }
+  if (!per_scene) {
+    P.n_abd_ctas = nab > 0 ? std::min(nab, std::max(1, grid / 8)) : 0;
+    P.n_fem_ctas = std::max(1, grid - P.n_abd_ctas);
+    if (P.n_fem_ctas + P.n_abd_ctas > grid) P.n_abd_ctas = grid - P.n_fem_ctas;
+  }
+  P.seg.assign(1, 0);
+  P.abd_seg.assign(1, 0);
+  P.cta_scene.assign(grid, -1);
+  if (per_scene) {
+    P.n_psc = n_scenes;
+    const std::vector<int> kf = share_parts(fcost, P.n_fem_ctas), ka = share_parts(acost, P.n_abd_ctas);
+    int c = 0;
+    for (int s = 0; s < n_scenes; ++s) {
+      if (!kf[s]) continue;
+      cut_balanced(pre, fem_lo[s], fem_lo[s + 1], kf[s], P.seg);
+      for (int j = 0; j < kf[s]; ++j) P.cta_scene[c++] = s;
+    }
+    while (c < P.n_fem_ctas) { P.seg.push_back(nf); ++c; }  // spare CTAs: no rows, no scene
+    c = 0;
+    for (int s = 0; s < n_scenes; ++s) {
+      if (!ka[s]) continue;
+      cut_balanced(bpre, abd_lo[s], abd_lo[s + 1], ka[s], P.abd_seg);
+      for (int j = 0; j < ka[s]; ++j) P.cta_scene[P.n_fem_ctas + c++] = s;
+    }
+    while (c < P.n_abd_ctas) { P.abd_seg.push_back(nab); ++c; }
+  } else {
+    P.n_psc = 1;
+    cut_balanced(pre, 0, nf, P.n_fem_ctas, P.seg);
+    if (P.n_abd_ctas) cut_balanced(bpre, 0, nab, P.n_abd_ctas, P.abd_seg);
+    for (int c = 0; c < grid; ++c) P.cta_scene[c] = 0;  // every CTA takes part in the one solve
+  }
+  // CTAs of every scene, in CTA order
+  P.sc_ptr.assign(P.n_psc + 1, 0);
+  for (int c = 0; c < grid; ++c)
+    if (P.cta_scene[c] >= 0) ++P.sc_ptr[P.cta_scene[c] + 1];
+  for (int s = 0; s < P.n_psc; ++s) P.sc_ptr[s + 1] += P.sc_ptr[s];
+  P.sc_cta.assign(P.sc_ptr[P.n_psc], 0);
+  {
+    std::vector<int> fill(P.sc_ptr.begin(), P.sc_ptr.end() - 1);
+    for (int c = 0; c < grid; ++c)
+      if (P.cta_scene[c] >= 0) P.sc_cta[fill[P.cta_scene[c]]++] = c;
+  }
   for (int b = 1; b <= nab; ++b) P.seg.push_back(nf + 4 * b);
   P.max_rows = 0;
   P.max_blocks = 0;
-  for (int c = 0; c < nc; ++c) {
+  for (int c = 0; c < P.n_fem_ctas; ++c) {
     P.max_rows = std::max(P.max_rows, P.seg[c + 1] - P.seg[c]);
     P.max_blocks = std::max(P.max_blocks, row[P.seg[c + 1]] - row[P.seg[c]]);
   }
-  const int bodies_per_cta = P.n_abd_ctas ? (nab + P.n_abd_ctas - 1) / P.n_abd_ctas : 0;
+  int bodies_per_cta = 0;
+  for (int c = 0; c < P.n_abd_ctas; ++c) bodies_per_cta = std::max(bodies_per_cta, P.abd_seg[c + 1] - P.abd_seg[c]);
   P.acc_doubles = std::max(1, std::max(3 * P.max_rows, 12 * bodies_per_cta));
   P.acc_doubles = (P.acc_doubles + 1) & ~1;  // keeps what follows 16-byte aligned
 }

@@ -119,6 +119,14 @@ struct ipcsim {
   Scal* sc_dev = nullptr;
   Scal* sc_host = nullptr;
   int pcg_grid_max = 1;
+  // per-scene Newton control of a batch (n_scenes > 1): device accumulators and pinned host mirrors
+  double* E_sc_dev = nullptr;
+  unsigned long long* alpha_sc_dev = nullptr;
+  unsigned long long* pn_sc_dev = nullptr;
+  double* alpha_trial_dev = nullptr;
+  double* E_sc_h = nullptr;
+  unsigned long long* alpha_sc_h = nullptr;
+  unsigned long long* pn_sc_h = nullptr;
   // PCG launch shape: threads per FEM row and CTAs per SM
   int tune_rowg = PCG_ROW_GROUP, tune_bps = 2;
   bool autotune_pending = false;
@@ -497,6 +505,14 @@ ipc_status reset_iteration_scalars(ipcsim* sim) {
   CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, offsetof(ipcsim::Scal, alpha), sim->st));
   unsigned long long init[2] = {double_bits(1.0), double_bits(1e300)};
   CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, init, sizeof(init), cudaMemcpyHostToDevice, sim->st));
+  if (sim->n_scenes > 1) {
+    const int ns = sim->n_scenes;
+    CUDA_TRY(cudaMemsetAsync(sim->E_sc_dev, 0, sizeof(double) * 8 * ns, sim->st));
+    CUDA_TRY(cudaMemsetAsync(sim->pn_sc_dev, 0, sizeof(unsigned long long) * 2 * ns, sim->st));
+    for (int k = 0; k < ns; ++k) sim->alpha_sc_h[k] = double_bits(1.0);
+    CUDA_TRY(cudaMemcpyAsync(sim->alpha_sc_dev, sim->alpha_sc_h, sizeof(unsigned long long) * ns,
+                             cudaMemcpyHostToDevice, sim->st));
+  }
   return IPC_OK;
 }
 
@@ -515,6 +531,14 @@ void rebuild_trees(ipcsim* sim, const double* xv) {
 
 ipc_status sync_scalars(ipcsim* sim) {
   CUDA_TRY(cudaMemcpyAsync(sim->sc_host, sim->sc_dev, sizeof(ipcsim::Scal), cudaMemcpyDeviceToHost, sim->st));
+  if (sim->n_scenes > 1) {
+    const int ns = sim->n_scenes;
+    CUDA_TRY(cudaMemcpyAsync(sim->E_sc_h, sim->E_sc_dev, sizeof(double) * 8 * ns, cudaMemcpyDeviceToHost, sim->st));
+    CUDA_TRY(cudaMemcpyAsync(sim->alpha_sc_h, sim->alpha_sc_dev, sizeof(unsigned long long) * ns,
+                             cudaMemcpyDeviceToHost, sim->st));
+    CUDA_TRY(cudaMemcpyAsync(sim->pn_sc_h, sim->pn_sc_dev, sizeof(unsigned long long) * 2 * ns,
+                             cudaMemcpyDeviceToHost, sim->st));
+  }
   CUDA_TRY(cudaStreamSynchronize(sim->st));
   prof_collect(sim);
   return IPC_OK;
@@ -543,6 +567,7 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
   launch_vertex_positions(sim->st, S, zq, xkq, xvq);
   for (;;) {
     CUDA_TRY(cudaMemsetAsync(sim->sc_dev->E, 0, sizeof(double) * 8, sim->st));
+    if (sim->n_scenes > 1) CUDA_TRY(cudaMemsetAsync(sim->E_sc_dev, 0, sizeof(double) * 8 * sim->n_scenes, sim->st));
     unsigned long long big = double_bits(1e300);
     CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->min_s, &big, sizeof(big), cudaMemcpyHostToDevice, sim->st));
     active_set(sim, xvq);
@@ -600,6 +625,7 @@ void sim_destroy(ipcsim* sim) {
   for (auto& e : sim->ev)
     if (e) cudaEventDestroy(e);
   if (sim->sc_host) cudaFreeHost(sim->sc_host);
+  if (sim->E_sc_h) cudaFreeHost(sim->E_sc_h);
   delete sim;
 }
 
@@ -957,6 +983,25 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     if ((s = upload(sim, &dp, scene_kappa))) return fail(s, ""); S.scene_kappa = dp;
     if ((s = upload(sim, &dp, scene_kc))) return fail(s, ""); S.scene_kc = dp;
     S.n_scenes = n_scenes;
+    if (n_scenes > 1) {
+      // scene of every node: FEM vertices through their body, ABD pseudo-nodes through their body
+      std::vector<int> node_scene(n_nodes);
+      for (int i = 0; i < nf; ++i) node_scene[i] = body_scene[vbody[i]];
+      for (int v = nf; v < nf + na_v; ++v)
+        for (int t = 0; t < 4; ++t) node_scene[nf + 4 * vabd[v] + t] = body_scene[vbody[v]];
+      if ((s = upload(sim, &ip, node_scene))) return fail(s, ""); S.node_scene = ip;
+      if ((s = dalloc(sim, &sim->E_sc_dev, 8 * (size_t)n_scenes))) return fail(s, ""); S.E_sc = sim->E_sc_dev;
+      if ((s = dalloc(sim, &sim->alpha_sc_dev, (size_t)n_scenes))) return fail(s, ""); S.alpha_sc = sim->alpha_sc_dev;
+      if ((s = dalloc(sim, &sim->pn_sc_dev, 2 * (size_t)n_scenes))) return fail(s, ""); S.pn_sc = sim->pn_sc_dev;
+      if ((s = dalloc(sim, &sim->alpha_trial_dev, (size_t)n_scenes))) return fail(s, "");
+      S.alpha_trial = sim->alpha_trial_dev;
+      void* hb = nullptr;
+      if (cudaMallocHost(&hb, sizeof(double) * 11 * (size_t)n_scenes) != cudaSuccess)
+        return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
+      sim->E_sc_h = static_cast<double*>(hb);
+      sim->alpha_sc_h = reinterpret_cast<unsigned long long*>(sim->E_sc_h + 8 * (size_t)n_scenes);
+      sim->pn_sc_h = sim->alpha_sc_h + n_scenes;
+    }
   }
   // state
   const int ndof = 3 * n_nodes;
@@ -1216,6 +1261,7 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   const int max_pcg = P.max_pcg > 0 ? P.max_pcg : (int)(10.0 * std::sqrt((double)ndof)) + 100;
   bool converged = false;
   int it = 0;
+  std::vector<char> scene_done;  // batches: scenes whose Newton iteration has converged
   auto restore = [&]() {
     cudaMemcpyAsync(sim->z, sim->z_t, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, cs);
     if (nk3) cudaMemcpyAsync(sim->xk, sim->xk_t, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, cs);
@@ -1311,6 +1357,7 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     prof_end(sim, PROF_PCG);
     // ---- direction norms and CCD bound
     launch_pnorm(cs, ndof, sim->p, nk3, sim->pD, sim->sc_dev->pn);
+    if (sim->n_scenes > 1) launch_pnorm_scenes(cs, S, ndof, sim->p, nk3, sim->pD);
     launch_vertex_disp(cs, S, sim->p, sim->pD, sim->pv);
     prof_begin(sim, PROF_CCD);
     if (sweep) {
@@ -1370,6 +1417,69 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     if (min_s_it < 1e299) st.min_dist = std::min(st.min_dist, std::sqrt(min_s_it));
     st.pnorm_end = pn / (dt * sim->L);
     st.energy_end = E;
+    if (sim->n_scenes > 1) {
+      // ---- batches: every scene has its own convergence test, CCD bound and line search, so each
+      //      advances as it would alone (pairs never cross scenes, the energy is a sum over scenes)
+      const int ns = sim->n_scenes;
+      if (scene_done.empty()) scene_done.assign(ns, 0);
+      std::vector<double> al(ns, 0.0), E0(ns), pns(ns), pds(ns);
+      std::vector<char> need_test(ns, 0);
+      bool all_done = true;
+      for (int k = 0; k < ns; ++k) {
+        E0[k] = total_energy(sim, sim->E_sc_h + 8 * k);
+        pns[k] = bits_to_double(sim->pn_sc_h[2 * k]);
+        pds[k] = bits_to_double(sim->pn_sc_h[2 * k + 1]);
+        if (!scene_done[k] && pds[k] == 0.0 && pns[k] <= tol_abs) scene_done[k] = 1;
+        if (scene_done[k]) continue;
+        all_done = false;
+        al[k] = std::min(1.0, bits_to_double(sim->alpha_sc_h[k]));
+        need_test[k] = pds[k] == 0.0;  // while kinematic targets are not reached the CCD-feasible step is taken
+      }
+      if (all_done) { converged = true; break; }
+      int halv = 0;
+      for (;;) {
+        CUDA_TRY(cudaMemcpyAsync(sim->alpha_trial_dev, al.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, cs));
+        launch_trial_scenes(cs, S, ndof, nk3, sim->z, sim->p, sim->z_trial, sim->xk, sim->pD, sim->xk_hat,
+                            sim->xk_trial);
+        double E_tot = 0;
+        if ((s = energy_at(sim, sim->z_trial, sim->xk_trial, sim->xv_trial, &E_tot, nullptr))) return s;
+        bool changed = false, pending = false;
+        for (int k = 0; k < ns; ++k) {
+          if (!need_test[k]) continue;
+          const double Ek = total_energy(sim, sim->E_sc_h + 8 * k);
+          if (Ek <= E0[k] + 1e-13 * std::fabs(E0[k])) { need_test[k] = 0; continue; }
+          al[k] *= 0.5;
+          changed = true;
+          // no decrease resolvable above rounding within the tolerance: this scene is stationary
+          if (al[k] * pns[k] <= tol_abs) { al[k] = 0.0; need_test[k] = 0; scene_done[k] = 1; continue; }
+          pending = true;
+        }
+        if (changed) ++halv;
+        if (!pending) {
+          if (changed) {
+            // steps changed after the last evaluation: place every scene at its final step
+            CUDA_TRY(cudaMemcpyAsync(sim->alpha_trial_dev, al.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, cs));
+            launch_trial_scenes(cs, S, ndof, nk3, sim->z, sim->p, sim->z_trial, sim->xk, sim->pD, sim->xk_hat,
+                                sim->xk_trial);
+            launch_vertex_positions(cs, S, sim->z_trial, sim->xk_trial, sim->xv_trial);
+            active_set(sim, sim->xv_trial);
+          }
+          break;
+        }
+        if (halv > 40) return finish(IPC_ERR_LS_STALL, "line search stalled");
+      }
+      st.ls_halvings += halv;
+      for (int k = 0; k < ns; ++k)
+        if (!scene_done[k] || al[k] > 0.0) st.alpha_min = std::min(st.alpha_min, al[k]);
+      rec_current = true;  // the active set at the accepted trial
+      std::swap(sim->z, sim->z_trial);
+      std::swap(sim->xk, sim->xk_trial);
+      sim->cand_valid = false;
+      bool all = true;
+      for (int k = 0; k < ns; ++k) all = all && scene_done[k];
+      if (all) { converged = true; break; }
+      continue;
+    }
     bool dirichlet_done = (pdn == 0.0);
     if (dirichlet_done && pn <= tol_abs) { converged = true; break; }
     double alpha = std::min(1.0, bits_to_double(h.alpha));
