@@ -69,12 +69,25 @@ struct PcgArgs {
   double* res;               // [relative residual]
   long long inc_cap;         // entries of inc
   int* check;                // non-null: validate every gathered index, record the first bad site here, skip it
+  // independent solves (a batch of scenes): every CTA serves the rows of one scene, each scene runs
+  // its own recurrences, tolerance and stop; n_psc = 1 is one solve over all CTAs
+  int n_psc;
+  const int* abd_seg;        // (n_abd_ctas + 1) ABD bodies of every ABD CTA
+  const int* cta_scene;      // (grid) scene of every CTA, -1 for a CTA without rows
+  const int* sc_ptr;         // (n_psc + 1) CTAs of every scene, in sc_cta
+  const int* sc_cta;
+  const int* scene_skip;     // (n_psc) or null: nonzero = scene not solved (x = 0)
+  double* sc_res;            // (n_psc) or null: relative residual of every scene
+  int* sc_it;                // (n_psc) or null: iterations of every scene
 };
 
 // Row partition of one PCG launch shape.
 struct PcgPlan {
   int grid = 0, n_fem_ctas = 0, n_abd_ctas = 0;
   std::vector<int> seg;      // FEM CTA row boundaries, then nf + 4 b for every ABD body
+  std::vector<int> abd_seg;  // ABD body boundaries of the ABD CTAs
+  int n_psc = 1;             // independent solves
+  std::vector<int> cta_scene, sc_ptr, sc_cta;
   int max_rows = 0, max_blocks = 0;
   int acc_doubles = 0;       // row products in shared memory: 3 per FEM row, 12 per ABD body of a CTA
 };
@@ -151,11 +164,15 @@ void launch_dinv(cudaStream_t, int n_nodes, const int* diag, const double* val, 
 void launch_rhs(cudaStream_t, int n, const double* g, const double* gdir, double* rhs);
 constexpr int PCG_ROW_GROUP = 4;  // default threads per FEM row in the PCG
 constexpr int PCG_REPLICA_COUNT = 8;
+constexpr int PCG_SCENES_MAX = 256;  // independent solves of one launch (one decision thread each)
 inline size_t pcg_partial_doubles(int grid) { return (size_t)PCG_REPLICA_COUNT * 7 * grid; }
 // co-resident CTAs of the PCG kernel for this shape (rowg: threads per FEM row, 1, 2, 4 or 8)
 int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem);
 size_t pcg_smem_limit();
-void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, PcgPlan& P);
+// node_scene (empty: one solve) gives the scene of every row; scenes get CTAs of their own when their rows
+// are contiguous and the grid has room, else the plan is one solve
+void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, const std::vector<int>& node_scene,
+                   int n_scenes, PcgPlan& P);
 // dynamic shared memory of a PCG CTA: contact sums of its rows, plus the operator rows when resident
 size_t pcg_contact_bytes(const PcgPlan& P);
 size_t pcg_resident_bytes(const PcgPlan& P, int fp32);

@@ -470,12 +470,17 @@ __device__ inline void contact_rows(const PcgArgs& a, const M* pairH, const M* f
 constexpr int PCG_THREADS_MAX = 256;
 constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
 
+static_assert(PCG_SCENES_MAX <= PCG_THREADS_MAX, "one decision thread per scene");
 struct Shared {
-  double vals[3][PCG_THREADS_MAX];  // per-thread values of a CTA sum
+  union {
+    double vals[3][PCG_THREADS_MAX];  // per-thread values of a CTA sum
+    double tot[3][PCG_SCENES_MAX];    // per-scene totals (several solves)
+  };
   double red[8][12];                // per-warp sums of the ABD rows
   double out[12];                   // results, read by every thread
-  double scal[4];                   // scalars of an iteration (thread 0 -> all)
+  double scal[4];                   // scalars of an iteration (the scene's decision thread -> all)
   int action;
+  unsigned long long agg[4];        // end of the solve: maxima over the scenes
 };
 
 // Sum over the CTA of N <= 3 per-thread values of type T; results in
@@ -542,6 +547,85 @@ __device__ inline void write_partials(T* rep0 /* replica 0 of this parity, [3][g
     rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = (T)sh.out[j];
   }
   __syncthreads();
+}
+
+// Totals of N per-CTA values for every solve, in a fixed order so that every
+// CTA holds bit-identical totals.  One solve: the CTA sum over all CTAs into
+// sh.out (the first 2 x blockDim values may already be in P); several: one
+// warp per scene over that scene's CTAs into sh.tot[j][s].  Every thread must
+// call it; read the results with scene_total.
+template <int N, typename T>
+__device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] */, int nblk, Shared& sh,
+                                    const Partials<T>* P) {
+  if (a.n_psc == 1) {
+    T v[N];
+    int start = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = T(0);
+    if (P) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = P->v[j][0] + P->v[j][1];
+      start = 2 * blockDim.x;
+    }
+    for (int b = threadIdx.x + start; b < nblk; b += blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] += rep[(size_t)j * nblk + b];
+    }
+    cta_sum<N, T>(v, sh);
+    return;
+  }
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int sc = threadIdx.x >> 5; sc < a.n_psc; sc += nw) {
+    const int k0 = a.sc_ptr[sc], k1 = a.sc_ptr[sc + 1];
+    T v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = T(0);
+    for (int k = k0 + lane; k < k1; k += 32) {
+      const int c = a.sc_cta[k];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] += rep[(size_t)j * nblk + c];
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) sh.tot[j][sc] = (double)v[j];
+    }
+  }
+  __syncthreads();
+}
+__device__ inline double scene_total(const PcgArgs& a, const Shared& sh, int j, int sc) {
+  return a.n_psc == 1 ? sh.out[j] : sh.tot[j][sc];
+}
+
+// End of a solve: CTA 0 reports the iterations, worst status, restarts and
+// largest relative residual over the scenes (and every scene's residual and
+// iterations when asked).  Status ranks: 0 converged < 3 budget spent <
+// 1 breakdown < 2 non-finite.  Every thread of every CTA must call it.
+__device__ inline void report_solve(const PcgArgs& a, Shared& sh, bool decider, int sc, int it, int status,
+                                    int restarts, double res) {
+  if (blockIdx.x != 0) return;
+  if (threadIdx.x < 4) sh.agg[threadIdx.x] = 0ull;
+  __syncthreads();
+  if (decider) {
+    const int rank = status == 0 ? 0 : status == 3 ? 1 : status == 1 ? 2 : 3;
+    atomicMax(&sh.agg[0], (unsigned long long)it);
+    atomicMax(&sh.agg[1], (unsigned long long)rank);
+    atomicMax(&sh.agg[2], (unsigned long long)restarts);
+    atomicMax(&sh.agg[3], (unsigned long long)__double_as_longlong(fmax(res, 0.0)));
+    if (a.sc_res) a.sc_res[sc] = res;
+    if (a.sc_it) a.sc_it[sc] = it;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int rank = (int)sh.agg[1];
+    a.out[0] = (int)sh.agg[0];
+    a.out[1] = rank == 0 ? 0 : rank == 1 ? 3 : rank == 2 ? 1 : 2;
+    a.out[2] = (int)sh.agg[2];
+    a.res[0] = __longlong_as_double((long long)sh.agg[3]);
+  }
 }
 
 __device__ inline double total_fp64(const double* rep /* [grid] */, int nblk, Shared& sh) {
@@ -691,12 +775,18 @@ __device__ inline void apply3(const M* D, A v0, A v1, A v2, A& z0, A& z1, A& z2)
   z2 = fma((A)D[6], v0, fma((A)D[7], v1, (A)D[8] * v2));
 }
 
-// One solve.  M = double: every operation in FP64.  M = float (mixed
-// precision): the operator, the contact blocks and the preconditioner are
-// stored in FP32 and applied in FP64 arithmetic, so the recurrences see one
-// fixed linear operator; the vectors, scalars and dot products are FP64, and
-// the FP64 residual b - A x with the FP64 operator is formed whenever the
+// One solve (or one per scene of a batch).  M = double: every operation in
+// FP64.  M = float: the operator, the contact blocks and the preconditioner
+// are stored in FP32 and applied in FP64 arithmetic, so the recurrences see
+// one fixed linear operator; the vectors, scalars and dot products are FP64,
+// and the FP64 residual b - A x with the FP64 operator is formed whenever the
 // recurrence has converged or stagnates, restarting the iteration on it.
+//
+// Several scenes: each CTA serves the rows of one scene; thread s of every CTA
+// runs the scalar recurrences of scene s on that scene's totals (so every CTA
+// knows every scene's next action), a scene that has met its tolerance stops
+// forming products, and the grid barriers stay common: a loop with a refresh
+// anywhere takes the refresh barriers everywhere.
 template <typename M, int ROWG>
 __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   cg::grid_group grid = cg::this_grid();
@@ -707,10 +797,13 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   const bool fem_cta = cta < a.n_fem_ctas;
   const int nf = S.nf;
   const int n3 = 3 * a.n_nodes;
+  const int my_sc = a.cta_scene[cta];
+  const bool decider = (int)threadIdx.x < a.n_psc;  // runs the recurrences of scene threadIdx.x
+  const int dsc = threadIdx.x;
 
   // ---- this CTA's rows; shared memory: row products (FEM: 3 per row, ABD: 12
   //      per owned body), then (resident) operator planes, preconditioner, columns, row offsets
-  int r0 = 0, r1 = 0, k0 = 0, nloc = 0;
+  int r0 = 0, r1 = 0, k0 = 0, nloc = 0, ab0 = 0, ab1 = 0;
   OpView<M> op{nullptr, 0, 1};
   const int* colp = nullptr;
   const int* rowp = nullptr;
@@ -739,6 +832,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
       op = OpView<M>{opM + 9 * (size_t)k0, nloc, 1};
       colp = a.col + k0; dinv_loc = dinvM + 9 * (size_t)r0;
     }
+  } else {
+    ab0 = a.abd_seg[cta - a.n_fem_ctas]; ab1 = a.abd_seg[cta - a.n_fem_ctas + 1];
+    if (!pcg_ok(a, ab0 >= 0 && ab0 <= ab1 && ab1 <= S.nab, 13)) ab0 = ab1 = 0;
   }
   // preconditioner block of node i (owned by this CTA)
   auto Dof = [&](int i) -> const M* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvM + 9 * (size_t)i); };
@@ -760,9 +856,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   double* partD = partT + PCG_REPLICAS * repT;
   const int myrep = cta % PCG_REPLICAS;
 
-  // y = A v for every owned row, left in shared memory (see row_y): the
-  // iteration operator (assembled = false: layout copy of type M) or the
-  // assembled FP64 one.  Every thread must call it.
+  // y = A v for every owned row, left in shared memory: the iteration
+  // operator (assembled = false: layout copy of type M) or the assembled FP64
+  // one.  Every thread of the CTA must call it.
   auto products = [&](bool assembled, auto&& op_view_fem, const int* colp_fem, const int* rowp_fem, auto mtag,
                       const auto* mat_pairH, const auto* mat_fHu, const double* vin) {
     using MM = decltype(mtag);
@@ -770,8 +866,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
       fem_products<MM, double, double, ROWG>(a, r0, r1, k0, op_view_fem, colp_fem, rowp_fem, mat_pairH, mat_fHu,
                                              vin, acc);
     } else {
-      int j = 0;
-      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j) {
+      for (int b = ab0, j = 0; b < ab1; ++b, ++j) {
         const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
         OpView<MM> ov = assembled ? OpView<MM>{(const MM*)a.val64 + 9 * (size_t)kb0, 1, 9}
                                   : OpView<MM>{(const MM*)a.op + 9 * (size_t)kb0, nl, 1};
@@ -784,136 +879,136 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     if (fem_cta) {
       for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) fn(i, acc + 3 * (i - r0));
     } else {
-      int j = 0;
-      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j)
+      for (int b = ab0, j = 0; b < ab1; ++b, ++j)
         if (threadIdx.x < 4) fn(nf + 4 * b + threadIdx.x, acc + 12 * j + 3 * threadIdx.x);
     }
+  };
+  // this CTA's part of a norm, to partD (every replica)
+  auto write_norm = [&](double v) {
+    double w[1] = {v};
+    cta_sum<1, double>(w, sh);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
   };
   // the FP64 operator (assembled layout) for the true residual
   OpView<double> op64{a.val64 + 9 * (size_t)k0, 1, 9};
   const int* col64 = a.col + k0;
 
-  // ---- x = 0, t64 = b, |b|^2
+  // ---- x = 0, t64 = b, |b|^2 of every scene
   {
-    double v[1] = {0.0};
+    double v = 0.0;
     for_nodes([&](int i, const double*) {
       for (int c = 0; c < 3; ++c) {
         double bv = a.b[3 * i + c];
         x[3 * i + c] = 0.0;
         t64[3 * i + c] = bv;
-        v[0] += bv * bv;
+        v += bv * bv;
       }
     });
-    cta_sum<1, double>(v, sh);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
-    __syncthreads();
+    write_norm(v);
   }
   grid.sync();
-  const double bb = total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
-  int it = 0, status = 0, replaced = 0;
-  if (!(bb > 0.0) || !isfinite(bb)) {
-    if (threadIdx.x == 0 && cta == 0) {
-      a.out[0] = 0; a.out[1] = isfinite(bb) ? 0 : 2; a.out[2] = 0; a.res[0] = 0.0;
-    }
-    return;
-  }
-  const double tol2_true = a.rtol * a.rtol * bb;
+  scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
+
+  // ---- per-scene state, held by the scene's decision thread
+  constexpr bool F32 = sizeof(M) == 4;
+  constexpr int STALL = 80;  // iterations without a new minimum of the recursive residual before a refresh
   const int max_replace = 10;
-  double sigma = 1.0 / sqrt(bb);  // scale of the current restart: iteration vectors hold sigma * (b - A x)
-  double tt = bb;
-
-  // ---- (re)start from t64 = b - A x: r = sigma t64, u = M^-1 r, w = A u, m = M^-1 w
-  auto restart = [&](int par) {
-    for_nodes([&](int i, const double*) {
-      double rv[3];
-      for (int c = 0; c < 3; ++c) {
-        const int q = 3 * i + c;
-        rv[c] = sigma * t64[q];
-        V.r[q] = rv[c];
-        V.z[q] = 0.0; V.q[q] = 0.0; V.s[q] = 0.0; V.p[q] = 0.0;
-      }
-      double u0, u1, u2;
-      apply3<M, double>(Dof(i), rv[0], rv[1], rv[2], u0, u1, u2);
-      V.u[3 * i] = u0; V.u[3 * i + 1] = u1; V.u[3 * i + 2] = u2;
-    });
-    grid.sync();
-    double* mcur = par ? V.m1 : V.m0;
-    products(false, op, colp, rowp, M(0), pairH, fHu, V.u);
-    double pv[3] = {0.0, 0.0, 0.0};
-    for_nodes([&](int i, const double* y) {
-      const int q = 3 * i;
-      V.w[q] = y[0]; V.w[q + 1] = y[1]; V.w[q + 2] = y[2];
-      double m0, m1, m2;
-      apply3<M, double>(Dof(i), y[0], y[1], y[2], m0, m1, m2);
-      mcur[q] = m0; mcur[q + 1] = m1; mcur[q + 2] = m2;
-      const double u0 = V.u[q], u1 = V.u[q + 1], u2 = V.u[q + 2];
-      const double rr0 = V.r[q], rr1 = V.r[q + 1], rr2 = V.r[q + 2];
-      pv[0] += rr0 * u0 + rr1 * u1 + rr2 * u2;
-      pv[1] += y[0] * u0 + y[1] * u1 + y[2] * u2;
-      pv[2] += rr0 * rr0 + rr1 * rr1 + rr2 * rr2;
-    });
-    write_partials<double>(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv);
-    grid.sync();
-  };
-  // ---- the FP64 residual t64 = b - A64 x and its squared norm
-  auto true_residual = [&]() -> double {
-    products(true, op64, col64, (const int*)nullptr, 0.0, a.pairH64, a.fHu64, x);
-    double v[1] = {0.0};
-    for_nodes([&](int i, const double* y) {
-      const int q = 3 * i;
-      const double t0 = a.b[q] - y[0], t1 = a.b[q + 1] - y[1], t2 = a.b[q + 2] - y[2];
-      t64[q] = t0; t64[q + 1] = t1; t64[q + 2] = t2;
-      v[0] += t0 * t0 + t1 * t1 + t2 * t2;
-    });
-    cta_sum<1, double>(v, sh);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
-    __syncthreads();
-    grid.sync();
-    return total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
-  };
-
+  double bb = 0.0, tol2_true = 0.0, sigma = 1.0, unscale = 1.0, tt = 0.0, tol_in2 = 0.0;
+  double alpha_old = 1.0, gamma_old = 1.0, rr_best = 0.0;
+  int it = 0, it_best = 0, replaced = 0, status = 0;
+  bool fresh = true, done = true;
   // inner target in the scaled units of the current restart: the requested
   // reduction, but not below what the FP32-stored operator resolves
-  constexpr bool F32 = sizeof(M) == 4;
   auto inner_tol2 = [&]() -> double {
     double t = tol2_true * sigma * sigma;
     if (F32) t = fmax(t, 1e-12);
     return t;
   };
-  restart(0);
-  double tol_in2 = inner_tol2();
-  double unscale = sqrt(bb);  // 1 / sigma
-  bool fresh = true;
-  double alpha_old = 1.0, gamma_old = 1.0;
-  // stagnation: the recursive residual of the pipelined recurrences can level
-  // off above the target (its rounding drifts from b - A x); when it has not
-  // reached a new minimum for STALL iterations the true residual is formed
-  constexpr int STALL = 80;
-  double rr_best = 0.0;
-  int it_best = 0;
-  for (;;) {
-    const int par = it & 1;
+  if (decider) {
+    bb = scene_total(a, sh, 0, dsc);
+    const bool skip = a.scene_skip && a.scene_skip[dsc];
+    done = skip || !(bb > 0.0) || !isfinite(bb);
+    status = (skip || isfinite(bb)) ? 0 : 2;
+    if (skip) bb = 0.0;
+    tt = bb;
+    tol2_true = a.rtol * a.rtol * bb;
+    unscale = sqrt(bb);
+    sigma = done ? 1.0 : 1.0 / unscale;
+    tol_in2 = inner_tol2();
+    if (dsc == my_sc) { sh.action = done ? 0 : 1; sh.scal[3] = sigma; }
+  }
+  __syncthreads();
+  bool my_run = my_sc >= 0 && sh.action;  // this CTA's scene forms products in the next loop
+  __syncthreads();
+
+  // ---- (re)start of the scenes whose CTAs have on = true, from t64 = b - A x:
+  //      r = sigma t64, u = M^-1 r, w = A u, m = M^-1 w, partial sums into parity par.
+  //      Two grid barriers, taken by every CTA.
+  auto restart = [&](int par, bool on) {
+    if (on) {
+      const double sg = sh.scal[3];
+      for_nodes([&](int i, const double*) {
+        double rv[3];
+        for (int c = 0; c < 3; ++c) {
+          const int q = 3 * i + c;
+          rv[c] = sg * t64[q];
+          V.r[q] = rv[c];
+          V.z[q] = 0.0; V.q[q] = 0.0; V.s[q] = 0.0; V.p[q] = 0.0;
+        }
+        double u0, u1, u2;
+        apply3<M, double>(Dof(i), rv[0], rv[1], rv[2], u0, u1, u2);
+        V.u[3 * i] = u0; V.u[3 * i + 1] = u1; V.u[3 * i + 2] = u2;
+      });
+    }
+    grid.sync();
+    if (on) {
+      double* mdst = par ? V.m1 : V.m0;
+      products(false, op, colp, rowp, M(0), pairH, fHu, V.u);
+      double pv[3] = {0.0, 0.0, 0.0};
+      for_nodes([&](int i, const double* y) {
+        const int q = 3 * i;
+        V.w[q] = y[0]; V.w[q + 1] = y[1]; V.w[q + 2] = y[2];
+        double m0, m1, m2;
+        apply3<M, double>(Dof(i), y[0], y[1], y[2], m0, m1, m2);
+        mdst[q] = m0; mdst[q + 1] = m1; mdst[q + 2] = m2;
+        const double u0 = V.u[q], u1 = V.u[q + 1], u2 = V.u[q + 2];
+        const double rr0 = V.r[q], rr1 = V.r[q + 1], rr2 = V.r[q + 2];
+        pv[0] += rr0 * u0 + rr1 * u1 + rr2 * u2;
+        pv[1] += y[0] * u0 + y[1] * u1 + y[2] * u2;
+        pv[2] += rr0 * rr0 + rr1 * rr1 + rr2 * rr2;
+      });
+      write_partials<double>(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv);
+    }
+    grid.sync();
+  };
+  restart(0, my_run);
+
+  enum { ACT_IDLE = 0, ACT_STEP = 1, ACT_REFRESH = 2 };
+  for (int L = 0;; ++L) {
+    const int par = L & 1;
     const double* rep = partT + (size_t)par * 3 * nblk + myrep * repT;
     double* mcur = par ? V.m1 : V.m0;
     double* mnext = par ? V.m0 : V.m1;
-    // the partial sums are loaded first, the product n = A m is formed while they arrive
+    // one solve: the partial sums are loaded first, the product n = A m is formed while they arrive
     Partials<double> P;
-    load_partials<double>(rep, nblk, P);
-    products(false, op, colp, rowp, M(0), pairH, fHu, mcur);
-    double gamma, delta, rr;
-    totals3<double>(rep, nblk, P, sh, gamma, delta, rr);
-    // the scalar recurrences run on thread 0 of every CTA (identical inputs,
-    // identical results) and reach the other threads through shared memory
-    enum { ACT_STEP = 0, ACT_REFRESH = 1, ACT_BREAKDOWN = 2, ACT_NAN = 3 };
-    if (threadIdx.x == 0) {
-      int act = ACT_STEP;
+    if (a.n_psc == 1) load_partials<double>(rep, nblk, P);
+    if (my_run) products(false, op, colp, rowp, M(0), pairH, fHu, mcur);
+    scene_totals<3, double>(a, rep, nblk, sh, a.n_psc == 1 ? &P : nullptr);
+    // the scalar recurrences of every scene (identical inputs in every CTA, identical results); the
+    // CTA's own scene reaches its threads through shared memory
+    int act = ACT_IDLE;
+    if (decider && !done) {
+      const double gamma = scene_total(a, sh, 0, dsc), delta = scene_total(a, sh, 1, dsc),
+                   rr = scene_total(a, sh, 2, dsc);
       double al = 0.0, be = 0.0;
-      if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) act = ACT_NAN;
+      act = ACT_STEP;
+      if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) { status = 2; done = true; act = ACT_IDLE; }
       else {
         if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
         if (rr <= tol_in2 || it - it_best > STALL || it >= a.max_iter) act = ACT_REFRESH;
         else if (fresh) {
-          if (!(delta > 0.0)) act = ACT_BREAKDOWN;
+          if (!(delta > 0.0)) { status = 1; done = true; act = ACT_IDLE; }
           else al = gamma / delta;
         } else {
           be = gamma / gamma_old;
@@ -922,78 +1017,104 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
           else al = gamma / den;
         }
       }
-      sh.action = act;
-      sh.scal[0] = al;
-      sh.scal[1] = be;
-      sh.scal[2] = al * unscale;
+      if (act == ACT_STEP) {
+        gamma_old = gamma;
+        alpha_old = al;
+        fresh = false;
+        ++it;
+      }
+      if (dsc == my_sc) {
+        sh.scal[0] = al;
+        sh.scal[1] = be;
+        sh.scal[2] = al * unscale;
+      }
     }
-    __syncthreads();
-    const int action = sh.action;
+    if (decider && dsc == my_sc) sh.action = act;
+    const bool any_refresh = __syncthreads_or(act == ACT_REFRESH);
+    const bool any_live = __syncthreads_or(act != ACT_IDLE);
+    const int my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
     const double alpha = sh.scal[0], beta = sh.scal[1], ax = sh.scal[2];
-    __syncthreads();
-    if (action == ACT_NAN) { status = 2; break; }
-    if (action == ACT_BREAKDOWN) { status = 1; break; }
-    if (action == ACT_REFRESH) {
-      tt = true_residual();
-      if (!isfinite(tt)) { status = 2; break; }
-      if (tt <= tol2_true || it >= a.max_iter || replaced >= max_replace) break;
-      ++replaced;
-      unscale = sqrt(tt);
-      sigma = 1.0 / unscale;
-      tol_in2 = inner_tol2();
-      restart(par);
-      fresh = true;
-      continue;
+    if (!any_live) break;
+    if (my_act == ACT_STEP) {
+      // every recurrence of the owned nodes, one thread per node
+      double pv[3] = {0.0, 0.0, 0.0};
+      for_nodes([&](int i, const double* n) {
+        // every value of the node is loaded before anything is stored (the vectors may alias as far as
+        // the compiler knows, which would otherwise serialise the loads behind the stores)
+        double oz[3], oq[3], os[3], op_[3], ou[3], ow[3], orr[3], om[3], ox[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int q = 3 * i + c;
+          oz[c] = V.z[q]; oq[c] = V.q[q]; os[c] = V.s[q]; op_[c] = V.p[q]; ou[c] = V.u[q];
+          ow[c] = V.w[q]; orr[c] = V.r[q]; om[c] = mcur[q]; ox[c] = x[q];
+        }
+        double rn[3], un[3], wn[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int q = 3 * i + c;
+          const double z = fma(beta, oz[c], n[c]);
+          const double qq = fma(beta, oq[c], om[c]);
+          const double s = fma(beta, os[c], ow[c]);
+          const double p = fma(beta, op_[c], ou[c]);
+          V.z[q] = z; V.q[q] = qq; V.s[q] = s; V.p[q] = p;
+          x[q] = fma(ax, p, ox[c]);
+          rn[c] = fma(-alpha, s, orr[c]);
+          un[c] = fma(-alpha, qq, ou[c]);
+          wn[c] = fma(-alpha, z, ow[c]);
+          V.r[q] = rn[c]; V.u[q] = un[c]; V.w[q] = wn[c];
+        }
+        double m0, m1, m2;
+        apply3<M, double>(Dof(i), wn[0], wn[1], wn[2], m0, m1, m2);
+        mnext[3 * i] = m0; mnext[3 * i + 1] = m1; mnext[3 * i + 2] = m2;
+        pv[0] += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
+        pv[1] += wn[0] * un[0] + wn[1] * un[1] + wn[2] * un[2];
+        pv[2] += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
+      });
+      write_partials<double>(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv);
     }
-    // every recurrence of the owned nodes, one thread per node
-    double pv[3] = {0.0, 0.0, 0.0};
-    for_nodes([&](int i, const double* n) {
-      // every value of the node is loaded before anything is stored (the vectors may alias as far as
-      // the compiler knows, which would otherwise serialise the loads behind the stores)
-      double oz[3], oq[3], os[3], op_[3], ou[3], ow[3], orr[3], om[3], ox[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int q = 3 * i + c;
-        oz[c] = V.z[q]; oq[c] = V.q[q]; os[c] = V.s[q]; op_[c] = V.p[q]; ou[c] = V.u[q];
-        ow[c] = V.w[q]; orr[c] = V.r[q]; om[c] = mcur[q]; ox[c] = x[q];
+    bool my_restart = false;
+    if (any_refresh) {
+      // ---- the FP64 residual t64 = b - A64 x of the refreshing scenes (their x is unchanged in this loop)
+      const bool ref = my_act == ACT_REFRESH;
+      if (ref) {
+        products(true, op64, col64, (const int*)nullptr, 0.0, a.pairH64, a.fHu64, x);
+        double v = 0.0;
+        for_nodes([&](int i, const double* y) {
+          const int q = 3 * i;
+          const double t0 = a.b[q] - y[0], t1 = a.b[q + 1] - y[1], t2 = a.b[q + 2] - y[2];
+          t64[q] = t0; t64[q + 1] = t1; t64[q + 2] = t2;
+          v += t0 * t0 + t1 * t1 + t2 * t2;
+        });
+        write_norm(v);
       }
-      double rn[3], un[3], wn[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int q = 3 * i + c;
-        const double z = fma(beta, oz[c], n[c]);
-        const double qq = fma(beta, oq[c], om[c]);
-        const double s = fma(beta, os[c], ow[c]);
-        const double p = fma(beta, op_[c], ou[c]);
-        V.z[q] = z; V.q[q] = qq; V.s[q] = s; V.p[q] = p;
-        x[q] = fma(ax, p, ox[c]);
-        rn[c] = fma(-alpha, s, orr[c]);
-        un[c] = fma(-alpha, qq, ou[c]);
-        wn[c] = fma(-alpha, z, ow[c]);
-        V.r[q] = rn[c]; V.u[q] = un[c]; V.w[q] = wn[c];
+      grid.sync();
+      scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
+      if (act == ACT_REFRESH) {  // decision threads of the refreshing scenes
+        tt = scene_total(a, sh, 0, dsc);
+        bool again = false;
+        if (!isfinite(tt)) { status = 2; done = true; }
+        else if (tt <= tol2_true || it >= a.max_iter || replaced >= max_replace) done = true;
+        else {
+          ++replaced;
+          unscale = sqrt(tt);
+          sigma = 1.0 / unscale;
+          tol_in2 = inner_tol2();
+          fresh = true;
+          again = true;
+        }
+        if (dsc == my_sc) { sh.action = again ? 1 : 0; sh.scal[3] = sigma; }
       }
-      double m0, m1, m2;
-      apply3<M, double>(Dof(i), wn[0], wn[1], wn[2], m0, m1, m2);
-      mnext[3 * i] = m0; mnext[3 * i + 1] = m1; mnext[3 * i + 2] = m2;
-      pv[0] += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
-      pv[1] += wn[0] * un[0] + wn[1] * un[1] + wn[2] * un[2];
-      pv[2] += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
-    });
-    write_partials<double>(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv);
-    grid.sync();
-    gamma_old = gamma;
-    alpha_old = alpha;
-    fresh = false;
-    ++it;
+      __syncthreads();
+      my_restart = ref && sh.action;
+      __syncthreads();
+      restart(par ^ 1, my_restart);
+    } else {
+      grid.sync();
+    }
+    my_run = my_act == ACT_STEP || my_restart;
   }
-  const double res = sqrt(fmax(tt, 0.0) / bb);
-  if (status == 0 && !(tt <= tol2_true)) status = 3;  // iteration or restart budget spent before the tolerance
-  if (threadIdx.x == 0 && cta == 0) {
-    a.out[0] = it;
-    a.out[1] = status;
-    a.out[2] = replaced;
-    a.res[0] = res;
-  }
+  if (decider && status == 0 && !(tt <= tol2_true)) status = 3;  // budget spent before the tolerance
+  report_solve(a, sh, decider, dsc, it, status, replaced, decider && bb > 0.0 ? sqrt(fmax(tt, 0.0) / bb) : 0.0);
 }
 
 // Mixed-precision solve: iterative refinement around an FP32 conjugate-
@@ -1003,7 +1124,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
 // products (the pipelined recurrences do not): two grid barriers per
 // iteration, one reduction point.  Its solution d of A32 d = sigma (b - A x)
 // is accumulated into x in FP64 and the FP64 residual b - A x is recomputed
-// with the FP64 operator until it meets the tolerance.
+// with the FP64 operator until it meets the tolerance.  Several scenes: as in
+// k_pcg, every scene has its own recurrences, refinements and stop, and a loop
+// in which any scene ends an inner solve takes the refinement barriers
+// everywhere.
 template <int ROWG>
 __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   using F = float;
@@ -1015,8 +1139,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   const bool fem_cta = cta < a.n_fem_ctas;
   const int nf = S.nf;
   const int n3 = 3 * a.n_nodes;
+  const int my_sc = a.cta_scene[cta];
+  const bool decider = (int)threadIdx.x < a.n_psc;  // runs the recurrences of scene threadIdx.x
+  const int dsc = threadIdx.x;
 
-  int r0 = 0, r1 = 0, k0 = 0, nloc = 0;
+  int r0 = 0, r1 = 0, k0 = 0, nloc = 0, ab0 = 0, ab1 = 0;
   OpView<F> op{nullptr, 0, 1};
   const int* colp = nullptr;
   const int* rowp = nullptr;
@@ -1046,6 +1173,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       op = OpView<F>{opF + 9 * (size_t)k0, nloc, 1};
       colp = a.col + k0; dinv_loc = dinvF + 9 * (size_t)r0;
     }
+  } else {
+    ab0 = a.abd_seg[cta - a.n_fem_ctas]; ab1 = a.abd_seg[cta - a.n_fem_ctas + 1];
+    if (!pcg_ok(a, ab0 >= 0 && ab0 <= ab1 && ab1 <= S.nab, 13)) ab0 = ab1 = 0;
   }
   auto Dof = [&](int i) -> const F* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvF + 9 * (size_t)i); };
 
@@ -1071,8 +1201,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     if (fem_cta) {
       fem_products<F, F, F, ROWG>(a, r0, r1, k0, op, colp, rowp, pairH, fHu, vin, accf);
     } else {
-      int j = 0;
-      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j) {
+      for (int b = ab0, j = 0; b < ab1; ++b, ++j) {
         const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
         abd_products<F, F, F, F>(a, b, OpView<F>{opF + 9 * (size_t)kb0, nl, 1}, a.col + kb0, nl, vin, a.abd_val32, sh,
                                  accf + 12 * j);
@@ -1084,60 +1213,86 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       fem_products<double, double, double, ROWG>(a, r0, r1, k0, OpView<double>{a.val64 + 9 * (size_t)k0, 1, 9},
                                                  a.col + k0, nullptr, a.pairH64, a.fHu64, vin, acc);
     } else {
-      int j = 0;
-      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j) {
+      for (int b = ab0, j = 0; b < ab1; ++b, ++j) {
         const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
         abd_products<double, double, double, double>(a, b, OpView<double>{a.val64 + 9 * (size_t)kb0, 1, 9},
                                                      a.col + kb0, nl, vin, a.abd_val, sh, acc + 12 * j);
       }
     }
   };
-  // node-local pass; the row product of the node (from the last products call) is at prod(i)
+  // node-local pass; the row product of the node (from the last products call) is at offset o
   auto for_nodes = [&](auto&& fn) {
     if (fem_cta) {
       for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) fn(i, 3 * (i - r0));
     } else {
-      int j = 0;
-      for (int b = cta - a.n_fem_ctas; b < S.nab; b += a.n_abd_ctas, ++j)
+      for (int b = ab0, j = 0; b < ab1; ++b, ++j)
         if (threadIdx.x < 4) fn(nf + 4 * b + threadIdx.x, 12 * j + 3 * threadIdx.x);
     }
   };
+  auto write_norm = [&](double v) {
+    double wv[1] = {v};
+    cta_sum<1, double>(wv, sh);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
+  };
 
-  // ---- x = 0, t64 = b, |b|^2
+  // ---- x = 0, t64 = b, |b|^2 of every scene
   {
-    double v[1] = {0.0};
+    double v = 0.0;
     for_nodes([&](int i, int) {
       for (int c = 0; c < 3; ++c) {
         const double bv = a.b[3 * i + c];
         x[3 * i + c] = 0.0;
         t64[3 * i + c] = bv;
-        v[0] += bv * bv;
+        v += bv * bv;
       }
     });
-    cta_sum<1, double>(v, sh);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
-    __syncthreads();
+    write_norm(v);
   }
   grid.sync();
-  const double bb = total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
-  int it = 0, status = 0, refine = 0;
-  if (!(bb > 0.0) || !isfinite(bb)) {
-    if (threadIdx.x == 0 && cta == 0) {
-      a.out[0] = 0; a.out[1] = isfinite(bb) ? 0 : 2; a.out[2] = 0; a.res[0] = 0.0;
-    }
-    return;
-  }
-  const double tol2_true = a.rtol * a.rtol * bb;
-  double tt = bb;
+  scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
+
+  // ---- per-scene state, held by the scene's decision thread
   constexpr int STALL = 80;
   constexpr int MAX_REFINE = 10;
-  for (;;) {
-    // ---- inner solve of A32 d = sigma t64 from d = 0
-    const double unscale = sqrt(tt);
-    const double sigma = 1.0 / unscale;
-    // inner target: the remaining reduction, not below what FP32 CG resolves
-    const F tol_in2 = (F)fmax(tol2_true / tt, 1e-10);
-    F g_l = F(0), rr_l = F(0);
+  double bb = 0.0, tol2_true = 0.0, tt = 0.0, unscale = 1.0;
+  F tol_in2 = F(0), alpha_old = F(1), gamma_old = F(1), rr_best = F(0);
+  int it = 0, it_best = 0, refine = 0, status = 0;
+  bool fresh = true, done = true;
+  // a new inner solve of A32 d = sigma t64 from d = 0; its target is the
+  // remaining reduction, not below what FP32 CG resolves
+  auto begin_inner = [&]() {
+    unscale = sqrt(tt);
+    tol_in2 = (F)fmax(tol2_true / tt, 1e-10);
+    fresh = true;
+    alpha_old = F(1);
+    gamma_old = F(1);
+    rr_best = F(0);
+    it_best = it;
+    if (dsc == my_sc) { sh.scal[2] = unscale; sh.scal[3] = 1.0 / unscale; }
+  };
+  if (decider) {
+    bb = scene_total(a, sh, 0, dsc);
+    const bool skip = a.scene_skip && a.scene_skip[dsc];
+    done = skip || !(bb > 0.0) || !isfinite(bb);
+    status = (skip || isfinite(bb)) ? 0 : 2;
+    if (skip) bb = 0.0;
+    tt = bb;
+    tol2_true = a.rtol * a.rtol * bb;
+    if (!done) begin_inner();
+    if (dsc == my_sc) sh.action = done ? 0 : 1;
+  }
+  __syncthreads();
+  bool my_run = my_sc >= 0 && sh.action;  // this CTA's scene is inside an inner solve
+  __syncthreads();
+
+  // inner solve start of this CTA's scene: r = sigma t64, u = M^-1 r, p = s = d = 0, and the
+  // CTA's parts of (r, u), (r, r)
+  F g_l = F(0), rr_l = F(0);
+  auto init_inner = [&]() {
+    const double sigma = sh.scal[3];
+    g_l = F(0);
+    rr_l = F(0);
     for_nodes([&](int i, int) {
       F rv[3], uv[3];
       for (int c = 0; c < 3; ++c) {
@@ -1151,13 +1306,15 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       g_l += rv[0] * uv[0] + rv[1] * uv[1] + rv[2] * uv[2];
       rr_l += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
     });
-    grid.sync();
-    bool fresh = true;
-    F alpha_old = F(1), gamma_old = F(1), rr_best = F(0);
-    int it_best = it;
-    for (;;) {
-      const int par = it & 1;
-      // phase A: w = A u, partial sums of (r, u), (w, u), (r, r)
+  };
+  if (my_run) init_inner();
+  grid.sync();
+
+  enum { ACT_IDLE = 0, ACT_STEP = 1, ACT_END = 2 };
+  for (int L = 0;; ++L) {
+    const int par = L & 1;
+    // phase A: w = A u, partial sums of (r, u), (w, u), (r, r)
+    if (my_run) {
       products32(u);
       F d_l = F(0);
       for_nodes([&](int i, int o) {
@@ -1168,45 +1325,47 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       });
       const F pl[3] = {g_l, d_l, rr_l};
       write_partials<F>(partF + (size_t)par * 3 * nblk, repT, nblk, sh, pl);
-      grid.sync();
-      // phase B: totals, scalars on thread 0, vector updates
-      Partials<F> P;
+    }
+    grid.sync();
+    // phase B: totals, the scalars of every scene, vector updates
+    {
       const F* rep = partF + (size_t)par * 3 * nblk + myrep * repT;
-      load_partials<F>(rep, nblk, P);
-      double gd, dd, rd;
-      totals3<F>(rep, nblk, P, sh, gd, dd, rd);
-      enum { ACT_STEP = 0, ACT_DONE = 1, ACT_BREAKDOWN = 2, ACT_NAN = 3 };
-      if (threadIdx.x == 0) {
-        const F gamma = (F)gd, delta = (F)dd, rr = (F)rd;
-        int act = ACT_STEP;
-        F al = F(0), be = F(0);
-        if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) act = ACT_NAN;
-        else {
-          if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
-          if (rr <= tol_in2 || it - it_best > STALL || it >= a.max_iter) act = ACT_DONE;
-          else if (fresh) {
-            if (!(delta > F(0))) act = ACT_BREAKDOWN;
-            else al = gamma / delta;
-          } else {
-            be = gamma / gamma_old;
-            const F den = delta - be * gamma / alpha_old;
-            if (!(den > F(0))) act = ACT_DONE;  // lost conjugacy: refine from the true residual
-            else al = gamma / den;
-          }
-          gamma_old = gamma;
-          alpha_old = al;
+      Partials<F> P;
+      if (a.n_psc == 1) load_partials<F>(rep, nblk, P);
+      scene_totals<3, F>(a, rep, nblk, sh, a.n_psc == 1 ? &P : nullptr);
+    }
+    int act = ACT_IDLE;
+    if (decider && !done) {
+      const F gamma = (F)scene_total(a, sh, 0, dsc), delta = (F)scene_total(a, sh, 1, dsc),
+              rr = (F)scene_total(a, sh, 2, dsc);
+      F al = F(0), be = F(0);
+      act = ACT_STEP;
+      if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) { status = 2; done = true; act = ACT_IDLE; }
+      else {
+        if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
+        if (rr <= tol_in2 || it - it_best > STALL || it >= a.max_iter) act = ACT_END;
+        else if (fresh) {
+          if (!(delta > F(0))) { status = 1; done = true; act = ACT_IDLE; }
+          else al = gamma / delta;
+        } else {
+          be = gamma / gamma_old;
+          const F den = delta - be * gamma / alpha_old;
+          if (!(den > F(0))) act = ACT_END;  // lost conjugacy: refine from the true residual
+          else al = gamma / den;
         }
-        sh.action = act;
-        sh.scal[0] = al;
-        sh.scal[1] = be;
+        gamma_old = gamma;
+        alpha_old = al;
       }
-      __syncthreads();
-      const int action = sh.action;
-      const F alpha = (F)sh.scal[0], beta = (F)sh.scal[1];
-      __syncthreads();
-      if (action == ACT_NAN) { status = 2; break; }
-      if (action == ACT_BREAKDOWN) { if (fresh) status = 1; break; }
-      if (action == ACT_DONE) break;
+      if (act == ACT_STEP) { fresh = false; ++it; }
+      if (dsc == my_sc) { sh.scal[0] = al; sh.scal[1] = be; }
+    }
+    if (decider && dsc == my_sc) sh.action = act;
+    const bool any_end = __syncthreads_or(act == ACT_END);
+    const bool any_live = __syncthreads_or(act != ACT_IDLE);
+    const int my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
+    const F alpha = (F)sh.scal[0], beta = (F)sh.scal[1];
+    if (!any_live) break;
+    if (my_act == ACT_STEP) {
       g_l = F(0);
       rr_l = F(0);
       for_nodes([&](int i, int) {
@@ -1233,41 +1392,54 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
         g_l += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
         rr_l += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
       });
-      fresh = false;
-      ++it;
-      grid.sync();
     }
-    if (status) break;
-    // ---- x += d / sigma in FP64, then the FP64 residual
-    for_nodes([&](int i, int) {
-      for (int c = 0; c < 3; ++c) x[3 * i + c] += unscale * (double)xi[3 * i + c];
-    });
-    grid.sync();
-    products64(x);
-    double v[1] = {0.0};
-    for_nodes([&](int i, int o) {
-      for (int c = 0; c < 3; ++c) {
-        const double t = a.b[3 * i + c] - acc[o + c];
-        t64[3 * i + c] = t;
-        v[0] += t * t;
+    bool my_again = false;
+    if (any_end) {
+      // ---- scenes that ended an inner solve: x += d / sigma in FP64, then the FP64 residual
+      const bool fin = my_act == ACT_END;
+      if (fin) {
+        const double us = sh.scal[2];
+        for_nodes([&](int i, int) {
+          for (int c = 0; c < 3; ++c) x[3 * i + c] += us * (double)xi[3 * i + c];
+        });
       }
-    });
-    cta_sum<1, double>(v, sh);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
-    __syncthreads();
+      grid.sync();
+      if (fin) {
+        products64(x);
+        double v = 0.0;
+        for_nodes([&](int i, int o) {
+          for (int c = 0; c < 3; ++c) {
+            const double t = a.b[3 * i + c] - acc[o + c];
+            t64[3 * i + c] = t;
+            v += t * t;
+          }
+        });
+        write_norm(v);
+      }
+      grid.sync();
+      scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
+      if (act == ACT_END) {  // decision threads of those scenes
+        tt = scene_total(a, sh, 0, dsc);
+        bool again = false;
+        if (!isfinite(tt)) { status = 2; done = true; }
+        else if (tt <= tol2_true || it >= a.max_iter || refine >= MAX_REFINE || !(tt > 0.0)) done = true;
+        else {
+          ++refine;
+          begin_inner();
+          again = true;
+        }
+        if (dsc == my_sc) sh.action = again ? 1 : 0;
+      }
+      __syncthreads();
+      my_again = fin && sh.action;
+      __syncthreads();
+      if (my_again) init_inner();
+    }
     grid.sync();
-    tt = total_fp64(partD + myrep * (size_t)nblk, nblk, sh);
-    if (!isfinite(tt)) { status = 2; break; }
-    if (tt <= tol2_true || it >= a.max_iter || refine >= MAX_REFINE || !(tt > 0.0)) break;
-    ++refine;
+    my_run = my_act == ACT_STEP || my_again;
   }
-  if (status == 0 && !(tt <= tol2_true)) status = 3;
-  if (threadIdx.x == 0 && cta == 0) {
-    a.out[0] = it;
-    a.out[1] = status;
-    a.out[2] = refine;
-    a.res[0] = sqrt(fmax(tt, 0.0) / bb);
-  }
+  if (decider && status == 0 && !(tt <= tol2_true)) status = 3;
+  report_solve(a, sh, decider, dsc, it, status, refine, decider && bb > 0.0 ? sqrt(fmax(tt, 0.0) / bb) : 0.0);
 }
 
 __global__ void k_to_float(size_t n, const double* __restrict__ src, float* __restrict__ dst, const int* n_dev,

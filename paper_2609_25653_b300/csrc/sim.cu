@@ -69,8 +69,14 @@ struct ipcsim {
   std::vector<int> h_row;      // BSR row offsets (host copy)
   PcgPlan plan;
   int plan_fp32 = -1;
-  int* d_seg = nullptr;
+  int* d_seg = nullptr;         // PCG plan: FEM/body segments, ABD CTA ranges, scene of every CTA, CTAs of every scene
   int d_seg_cap = 0;
+  std::vector<int> h_plan_buf;  // host staging of d_seg
+  std::vector<int> h_node_scene;  // scene of every node (batches)
+  int* d_pcg_skip = nullptr;     // (n_scenes) scenes the next PCG leaves out (their Newton iteration has converged)
+  int* pcg_skip_h = nullptr;     // pinned staging of d_pcg_skip
+  bool pcg_skip_on = false;
+  double* d_pcg_sc_res = nullptr;  // (n_scenes) relative residual of every scene's last solve
   bool plan_resident = false;
   size_t plan_smem = 0;
   int plan_want_grid = 0, plan_rowg = 0;
@@ -359,7 +365,7 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
     size_t smem = 0;
     for (int attempt = 0; attempt < 4; ++attempt) {
       if (sim->nab > 0 && grid < 2) { sim->err = "PCG needs two co-resident CTAs"; return IPC_ERR_CUDA; }
-      pcg_plan_rows(sim->h_row, sim->nf, sim->nab, grid, sim->plan);
+      pcg_plan_rows(sim->h_row, sim->nf, sim->nab, grid, sim->h_node_scene, sim->n_scenes, sim->plan);
       const size_t bytes = pcg_resident_bytes(sim->plan, fp32);
       const int cap_res = bytes <= pcg_smem_limit() ? pcg_max_blocks(PCG_THREADS, fp32, rowg, bytes) : 0;
       if (cap_res >= grid) { resident = true; smem = bytes; break; }
@@ -369,7 +375,14 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
       if (cap >= grid) break;
       grid = cap;
     }
-    const int n = (int)sim->plan.seg.size();
+    // one device buffer: seg | abd_seg | cta_scene | sc_ptr | sc_cta
+    const PcgPlan& pl = sim->plan;
+    std::vector<int>& buf = sim->h_plan_buf;
+    CUDA_TRY(cudaStreamSynchronize(sim->st));  // the previous upload from buf has completed
+    buf.clear();
+    for (const std::vector<int>* v : {&pl.seg, &pl.abd_seg, &pl.cta_scene, &pl.sc_ptr, &pl.sc_cta})
+      buf.insert(buf.end(), v->begin(), v->end());
+    const int n = (int)buf.size();
     if (n > sim->d_seg_cap) {
       dfree(sim, sim->d_seg);
       sim->d_seg = nullptr;
@@ -377,7 +390,7 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
       if (s) return s;
       sim->d_seg_cap = n;
     }
-    CUDA_TRY(cudaMemcpyAsync(sim->d_seg, sim->plan.seg.data(), sizeof(int) * n, cudaMemcpyHostToDevice, sim->st));
+    CUDA_TRY(cudaMemcpyAsync(sim->d_seg, buf.data(), sizeof(int) * n, cudaMemcpyHostToDevice, sim->st));
     sim->plan_want_grid = want;
     sim->plan_fp32 = fp32;
     sim->plan_rowg = rowg;
@@ -400,6 +413,20 @@ ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric)
   a.n_fem_ctas = sim->plan.n_fem_ctas;
   a.n_abd_ctas = sim->plan.n_abd_ctas;
   a.seg_row = sim->d_seg;
+  {
+    const PcgPlan& pl = sim->plan;
+    const int* d = sim->d_seg + pl.seg.size();
+    a.abd_seg = d; d += pl.abd_seg.size();
+    a.cta_scene = d; d += pl.cta_scene.size();
+    a.sc_ptr = d; d += pl.sc_ptr.size();
+    a.sc_cta = d;
+    a.n_psc = pl.n_psc;
+    // the per-scene plan's solves are the scenes of the batch
+    const bool per_scene = pl.n_psc > 1 && pl.n_psc == sim->n_scenes;
+    a.scene_skip = per_scene && sim->pcg_skip_on ? sim->d_pcg_skip : nullptr;
+    a.sc_res = per_scene ? sim->d_pcg_sc_res : nullptr;
+    a.sc_it = nullptr;
+  }
   a.resident = sim->plan_resident ? 1 : 0;
   a.row = S.bsr_row;
   a.col = S.bsr_col;
@@ -626,6 +653,7 @@ void sim_destroy(ipcsim* sim) {
     if (e) cudaEventDestroy(e);
   if (sim->sc_host) cudaFreeHost(sim->sc_host);
   if (sim->E_sc_h) cudaFreeHost(sim->E_sc_h);
+  if (sim->pcg_skip_h) cudaFreeHost(sim->pcg_skip_h);
   delete sim;
 }
 
@@ -990,6 +1018,11 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
       for (int v = nf; v < nf + na_v; ++v)
         for (int t = 0; t < 4; ++t) node_scene[nf + 4 * vabd[v] + t] = body_scene[vbody[v]];
       if ((s = upload(sim, &ip, node_scene))) return fail(s, ""); S.node_scene = ip;
+      sim->h_node_scene = node_scene;
+      if ((s = dalloc(sim, &sim->d_pcg_skip, (size_t)n_scenes))) return fail(s, "");
+      if ((s = dalloc(sim, &sim->d_pcg_sc_res, (size_t)n_scenes))) return fail(s, "");
+      if (cudaMallocHost(&sim->pcg_skip_h, sizeof(int) * (size_t)n_scenes) != cudaSuccess)
+        return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
       if ((s = dalloc(sim, &sim->E_sc_dev, 8 * (size_t)n_scenes))) return fail(s, ""); S.E_sc = sim->E_sc_dev;
       if ((s = dalloc(sim, &sim->alpha_sc_dev, (size_t)n_scenes))) return fail(s, ""); S.alpha_sc = sim->alpha_sc_dev;
       if ((s = dalloc(sim, &sim->pn_sc_dev, 2 * (size_t)n_scenes))) return fail(s, ""); S.pn_sc = sim->pn_sc_dev;
@@ -1312,6 +1345,14 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     // ---- PCG
     const int fp32 = P.precision == IPC_PREC_MIXED ? 1 : 0;
     const int n_fric_it = P.mu > 0 ? sim->n_fric : 0;
+    // batches: scenes whose Newton iteration has converged are left out of the solve (direction 0)
+    sim->pcg_skip_on = false;
+    if (sim->n_scenes > 1 && !scene_done.empty()) {
+      for (int k = 0; k < sim->n_scenes; ++k) sim->pcg_skip_h[k] = scene_done[k] ? 1 : 0;
+      CUDA_TRY(cudaMemcpyAsync(sim->d_pcg_skip, sim->pcg_skip_h, sizeof(int) * sim->n_scenes, cudaMemcpyHostToDevice,
+                               cs));
+      sim->pcg_skip_on = true;
+    }
     prof_begin(sim, PROF_PCG_SETUP);
     build_incidence(sim, n_fric_it);
     if (fp32) {
@@ -1354,6 +1395,7 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     prof_end(sim, PROF_PCG_SETUP);
     prof_begin(sim, PROF_PCG);
     if ((s = pcg_run(sim, fp32, P.pcg_rtol, max_pcg, n_fric_it))) return s;
+    sim->pcg_skip_on = false;
     prof_end(sim, PROF_PCG);
     // ---- direction norms and CCD bound
     launch_pnorm(cs, ndof, sim->p, nk3, sim->pD, sim->sc_dev->pn);
