@@ -265,7 +265,28 @@ struct PairWork {
 
 // PSD projection of W.H (n x n, n even <= 12, row stride 12) in place (eig.cuh)
 __device__ inline void warp_project(PairWork& W, int n, int lane) {
-  warp_project_psd(W.H, W.V, W.lam, W.rp, W.rq, W.rc, W.rs, n, lane);
+  warp_project_psd<double>(W.H, W.V, W.lam, W.rp, W.rq, W.rc, W.rs, n, lane);
+}
+// The same projection in FP32 (mixed precision, where the solve stores the pair blocks in FP32): the
+// diagonal-dominance test on the FP64 matrix, then the rotations in FP32 in the storage of W.V (free until
+// the scatter), widened back into W.H.  The barrier value, its derivatives and the gradient stay FP64.
+__device__ inline void warp_project_f32(PairWork& W, int n, int lane) {
+  bool dom = true;
+  if (lane < n) {
+    double off = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (j != lane) off += fabs(W.H[12 * lane + j]);
+    dom = W.H[13 * lane] >= off;
+  }
+  if (__all_sync(0xffffffffu, dom)) return;
+  float* A = reinterpret_cast<float*>(W.V);
+  float* V = A + 144;
+  for (int e = lane; e < 144; e += 32) A[e] = (float)W.H[e];
+  __syncwarp();
+  warp_project_psd<float>(A, V, reinterpret_cast<float*>(W.lam), W.rp, W.rq, reinterpret_cast<float*>(W.rc),
+                          reinterpret_cast<float*>(W.rs), n, lane);
+  for (int e = lane; e < 144; e += 32) W.H[e] = (double)A[e];
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const double* __restrict__ xv,
@@ -274,7 +295,8 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
                                                              int project, double* __restrict__ g,
                                                              double* __restrict__ pairH, double* __restrict__ Dc,
                                                              const double* __restrict__ pD, double* __restrict__ gdir,
-                                                             double* __restrict__ E, unsigned long long* min_s) {
+                                                             double* __restrict__ E, unsigned long long* min_s,
+                                                             int hess_fp32) {
   __shared__ PairWork work[BWARPS];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   PairWork& W = work[wid];
@@ -394,7 +416,8 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
         W.H[e] = v;
       }
       __syncwarp();
-      warp_project(W, nn, lane);
+      if (hess_fp32) warp_project_f32(W, nn, lane);
+      else warp_project(W, nn, lane);
       // scatter H (compact) into a zeroed 12x12 in V
       for (int e = lane; e < 144; e += 32) W.V[e] = 0.0;
       __syncwarp();
@@ -572,12 +595,12 @@ __global__ void k_friction(DevScene S, const double* __restrict__ xv, const doub
 // ---------------------------------------------------------------------------
 void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
                     int cap, double sh, double kappa, double scale, int mode, int project, double* g, double* pairH,
-                    double* Dc, const double* pD, double* gdir, double* E, unsigned long long* min_s) {
+                    double* Dc, const double* pD, double* gdir, double* E, unsigned long long* min_s, int hess_fp32) {
   if (mode >= 2) {
     // one warp per pair: as many warps as the thread-per-pair launch had threads / 32, at least one block
     int wgrid = std::max(1, std::min((cap + BWARPS - 1) / BWARPS, 148 * 16));
     k_barrier_warp<<<wgrid, 32 * BWARPS, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, project, g, pairH, Dc, pD,
-                                                   gdir, E, min_s);
+                                                   gdir, E, min_s, hess_fp32);
   } else {
     k_barrier<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, mode, project, g, pairH, Dc, pD, gdir,
                                     E, min_s);

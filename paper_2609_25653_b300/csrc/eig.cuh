@@ -90,19 +90,28 @@ __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ inline float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // Parallel cyclic Jacobi PSD projection of the symmetric n x n matrix A (n
 // even <= 12, row stride 12, shared memory) by one warp: n / 2 disjoint
 // rotations per round (round-robin pairing), n - 1 rounds per sweep, then
 // A <- V max(lambda, 0) V^T.  V (12 x 12), lam (12), rp/rq/rc/rs (6 each) are
-// shared-memory workspace.  Every lane of the warp must call it.
-__device__ inline void warp_project_psd(double* A, double* V, double* lam, int* rp, int* rq, double* rc, double* rs,
-                                        int n, int lane) {
-  for (int e = lane; e < 144; e += 32) V[e] = ((e / 12) == (e % 12)) ? 1.0 : 0.0;
+// shared-memory workspace.  T = float (mixed precision) stops at a relative
+// off-diagonal mass of 1e-11 and forms every entry of the result and its
+// mirror from the same products, so the result is exactly symmetric.  Every
+// lane of the warp must call it.
+template <typename T>
+__device__ inline void warp_project_psd(T* A, T* V, T* lam, int* rp, int* rq, T* rc, T* rs, int n, int lane) {
+  constexpr bool F32 = sizeof(T) == 4;
+  const T rel_tol = F32 ? T(1e-11) : T(1e-30);
+  for (int e = lane; e < 144; e += 32) V[e] = ((e / 12) == (e % 12)) ? T(1) : T(0);
   // Gershgorin: skip when diagonally dominant with non-negative diagonal
   bool dom = true;
   if (lane < n) {
-    double off = 0.0;
+    T off = T(0);
     for (int j = 0; j < n; ++j)
       if (j != lane) off += fabs(A[12 * lane + j]);
     dom = A[13 * lane] >= off;
@@ -110,18 +119,18 @@ __device__ inline void warp_project_psd(double* A, double* V, double* lam, int* 
   if (__all_sync(0xffffffffu, dom)) return;
   __syncwarp();
   for (int sweep = 0; sweep < 20; ++sweep) {
-    double off = 0.0, tot = 0.0;
+    T off = T(0), tot = T(0);
     for (int e = lane; e < 144; e += 32) {
       int i = e / 12, j = e % 12;
       if (i < n && j < n) {
-        double a2 = A[e] * A[e];
+        T a2 = A[e] * A[e];
         tot += a2;
         if (i != j) off += a2;
       }
     }
     off = warp_sum(off);
     tot = warp_sum(tot);
-    if (off <= 1e-30 * tot || tot == 0.0) break;
+    if (off <= rel_tol * tot || tot == T(0)) break;
     for (int r = 0; r < n - 1; ++r) {
       if (lane < n / 2) {
         int k = lane;
@@ -129,12 +138,12 @@ __device__ inline void warp_project_psd(double* A, double* V, double* lam, int* 
         int p = pa == 0 ? 0 : 1 + (pa - 1 + r) % (n - 1);
         int q = 1 + (pb - 1 + r) % (n - 1);
         if (p > q) { int t = p; p = q; q = t; }
-        double apq = A[12 * p + q];
-        double c = 1.0, sn = 0.0;
-        if (apq != 0.0) {
-          double theta = (A[12 * q + q] - A[12 * p + p]) / (2.0 * apq);
-          double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
+        T apq = A[12 * p + q];
+        T c = T(1), sn = T(0);
+        if (apq != T(0)) {
+          T theta = (A[12 * q + q] - A[12 * p + p]) / (T(2) * apq);
+          T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+          c = T(1) / sqrt(t * t + T(1));
           sn = t * c;
         }
         rp[k] = p; rq[k] = q; rc[k] = c; rs[k] = sn;
@@ -144,8 +153,8 @@ __device__ inline void warp_project_psd(double* A, double* V, double* lam, int* 
       for (int it = lane; it < items; it += 32) {  // rows: A <- J^T A
         int k = it / n, j = it % n;
         int p = rp[k], q = rq[k];
-        double c = rc[k], sn = rs[k];
-        double apj = A[12 * p + j], aqj = A[12 * q + j];
+        T c = rc[k], sn = rs[k];
+        T apj = A[12 * p + j], aqj = A[12 * q + j];
         A[12 * p + j] = c * apj - sn * aqj;
         A[12 * q + j] = sn * apj + c * aqj;
       }
@@ -153,11 +162,11 @@ __device__ inline void warp_project_psd(double* A, double* V, double* lam, int* 
       for (int it = lane; it < items; it += 32) {  // columns: A <- A J, V <- V J
         int k = it / n, i = it % n;
         int p = rp[k], q = rq[k];
-        double c = rc[k], sn = rs[k];
-        double aip = A[12 * i + p], aiq = A[12 * i + q];
+        T c = rc[k], sn = rs[k];
+        T aip = A[12 * i + p], aiq = A[12 * i + q];
         A[12 * i + p] = c * aip - sn * aiq;
         A[12 * i + q] = sn * aip + c * aiq;
-        double vip = V[12 * i + p], viq = V[12 * i + q];
+        T vip = V[12 * i + p], viq = V[12 * i + q];
         V[12 * i + p] = c * vip - sn * viq;
         V[12 * i + q] = sn * vip + c * viq;
       }
@@ -165,13 +174,14 @@ __device__ inline void warp_project_psd(double* A, double* V, double* lam, int* 
     }
   }
   // A <- V max(diag, 0) V^T (eigenvalues staged in shared memory)
-  if (lane < n) lam[lane] = fmax(A[13 * lane], 0.0);
+  if (lane < n) lam[lane] = fmax(A[13 * lane], T(0));
   __syncwarp();
-  double out[5] = {0, 0, 0, 0, 0};
+  T out[5] = {0, 0, 0, 0, 0};
   int cnt = 0;
   for (int e = lane; e < 144; e += 32, ++cnt) {
     int i = e / 12, j = e % 12;
-    double sacc = 0.0;
+    if (F32 && i > j) { int t = i; i = j; j = t; }
+    T sacc = T(0);
     if (i < n && j < n)
       for (int k = 0; k < n; ++k) sacc += V[12 * i + k] * lam[k] * V[12 * j + k];
     out[cnt] = sacc;

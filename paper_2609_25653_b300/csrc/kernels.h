@@ -121,7 +121,7 @@ void launch_sub(cudaStream_t, int n, const double* a, const double* b, double* o
 // contact.cu
 void launch_barrier(cudaStream_t, int grid, const DevScene&, const double* xv, const int* rec, const int* n_dev, int cap,
                     double sh, double kappa, double scale, int mode, int project, double* g, double* pairH, double* Dc,
-                    const double* pD, double* gdir, double* E, unsigned long long* min_s);
+                    const double* pD, double* gdir, double* E, unsigned long long* min_s, int hess_fp32 = 0);
 void launch_friction_lag(cudaStream_t, int grid, const DevScene&, const double* xv, const int* rec, const int* n_dev,
                          int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam);
 void launch_friction(cudaStream_t, const DevScene&, const double* xv, const double* xv_t, int n, const int* f_ids,

@@ -1331,7 +1331,8 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g, sim->Hval, &sim->sc_dev->E[5]);
     prof_begin(sim, PROF_BARRIER);
     launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh, sim->kappa,
-                   dt2, 2, 1, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2], &sim->sc_dev->min_s);
+                   dt2, 2, 1, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2], &sim->sc_dev->min_s,
+                   P.precision == IPC_PREC_MIXED);
     prof_end(sim, PROF_BARRIER);
     if (P.mu > 0) {
       prof_begin(sim, PROF_FRICTION);
