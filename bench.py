@@ -280,7 +280,7 @@ def run_ours(args):
     pcg_grid, pcg_resident = sim.pcg_layout()
     pcg_bytes_per_launch = pcg_bytes(work, sim, prec == ipcsim.PREC_MIXED, pcg_resident, pcg["n"]) / max(pcg["n"], 1)
     achieved = pcg_bytes_per_launch / (pcg_avg_ms / 1e3) / 1e9 if pcg["n"] else 0.0
-    roofline = {"kernel": "k_pcg", "bound": "hbm", "achieved": round(achieved, 2),
+    roofline = {"kernel": "k_pcg32" if precision == "mixed" else "k_pcg", "bound": "hbm", "achieved": round(achieved, 2),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 5),
                 "traffic": None, "peak_source": peak_src,
                 "launch_ms": round(pcg_avg_ms, 5), "algorithmic_bytes_per_launch": int(pcg_bytes_per_launch),
