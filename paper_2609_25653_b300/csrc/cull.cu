@@ -139,6 +139,18 @@ __device__ double accd(int kind, const d3* x0, const d3* p0, double s_frac, doub
   return t;
 }
 
+// Upper bound handed to ACCD by the traversal kernels.  Only a time of impact
+// below the running minimum of the pair's scene can change that minimum, and
+// ACCD with a smaller bound tmax returns min(its result with bound 1, tmax)
+// from the same arithmetic (it stops once its time reaches tmax, and its
+// early-outs only fire when the result would be at least tmax), so the
+// minimum over the pairs is unchanged while more pairs stop early.
+__device__ inline double ccd_tmax(const DevScene& S, const unsigned long long* alpha_bits, int sc, double amin) {
+  const unsigned long long* src = S.alpha_sc ? S.alpha_sc + sc : alpha_bits;
+  const double cur = __longlong_as_double((long long)*(const volatile unsigned long long*)src);
+  return fmin(amin, fmin(cur, 1.0));
+}
+
 __device__ inline void swept(const double* xv, const double* pv, int v, d3& lo, d3& hi) {
   d3 a = ld3(xv, v), p = ld3(pv, v);
   d3 b = a + p;
@@ -301,6 +313,7 @@ __global__ void k_ccd_pt_bvh(DevScene S, const double* __restrict__ xv, const do
   swept(xv, pv, p, la, ha);
   double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
   double amin = 1.0;
+  const int sc = S.alpha_sc ? scene_of_vertex(S, p) : 0;
   int nc = 0;
   bool ok = traverse(T, q, [&](int t) {
     int3 tv = S.tris[t];
@@ -316,7 +329,7 @@ __global__ void k_ccd_pt_bvh(DevScene S, const double* __restrict__ xv, const do
     d3 x[4], pp[4];
     for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
     ++nc;
-    amin = fmin(amin, accd(0, x, pp, s_frac, 1.0, max_iter));
+    amin = fmin(amin, accd(0, x, pp, s_frac, ccd_tmax(S, alpha_bits, sc, amin), max_iter));
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_cand, nc);
@@ -338,6 +351,7 @@ __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const do
   swept(xv, pv, A.y, la, ha);
   double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
   double amin = 1.0;
+  const int sc = S.alpha_sc ? scene_of_vertex(S, A.x) : 0;
   int nc = 0;
   bool ok = traverse(T, q, [&](int eb) {
     if (eb <= ea) return;
@@ -352,7 +366,7 @@ __global__ void k_ccd_ee_bvh(DevScene S, const double* __restrict__ xv, const do
     d3 x[4], pp[4];
     for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
     ++nc;
-    amin = fmin(amin, accd(1, x, pp, s_frac, 1.0, max_iter));
+    amin = fmin(amin, accd(1, x, pp, s_frac, ccd_tmax(S, alpha_bits, sc, amin), max_iter));
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_cand, nc);
@@ -393,6 +407,7 @@ __global__ void k_sweep_pt_bvh(DevScene S, const double* __restrict__ xv, const 
   swept(xv, pv, p, la, ha);
   double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
   double amin = 1.0;
+  const int sc = S.alpha_sc ? scene_of_vertex(S, p) : 0;
   int nc = 0;
   bool ok = traverse(T, q, [&](int t) {
     int3 tv = S.tris[t];
@@ -408,7 +423,7 @@ __global__ void k_sweep_pt_bvh(DevScene S, const double* __restrict__ xv, const 
     d3 x[4], pp[4];
     for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
     ++nc;
-    amin = fmin(amin, accd(0, x, pp, s_frac, 1.0, max_iter));
+    amin = fmin(amin, accd(0, x, pp, s_frac, ccd_tmax(S, alpha_bits, sc, amin), max_iter));
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_ccd, nc);
@@ -431,6 +446,7 @@ __global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const 
   swept(xv, pv, A.y, la, ha);
   double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
   double amin = 1.0;
+  const int sc = S.alpha_sc ? scene_of_vertex(S, A.x) : 0;
   int nc = 0;
   bool ok = traverse(T, q, [&](int eb) {
     if (eb <= ea) return;
@@ -446,7 +462,7 @@ __global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const 
     d3 x[4], pp[4];
     for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
     ++nc;
-    amin = fmin(amin, accd(1, x, pp, s_frac, 1.0, max_iter));
+    amin = fmin(amin, accd(1, x, pp, s_frac, ccd_tmax(S, alpha_bits, sc, amin), max_iter));
   });
   if (!ok) atomicOr(err, ERRF_BVH);
   if (nc) atomicAdd(n_ccd, nc);

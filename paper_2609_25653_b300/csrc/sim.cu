@@ -1849,6 +1849,12 @@ ipc_status sim_ccd_alpha(ipcsim* sim, const double* x_dev, const double* p_dev, 
   if (!sim || !x_dev || !p_dev || !alpha_host) return IPC_ERR_ARG;
   unsigned long long one = double_bits(1.0);
   CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, &one, sizeof(one), cudaMemcpyHostToDevice, sim->st));
+  if (sim->n_scenes > 1) {
+    const std::vector<unsigned long long> ones(sim->n_scenes, one);
+    CUDA_TRY(cudaMemcpyAsync(sim->alpha_sc_dev, ones.data(), sizeof(one) * ones.size(), cudaMemcpyHostToDevice,
+                             sim->st));
+    CUDA_TRY(cudaStreamSynchronize(sim->st));  // the staging vector goes out of scope
+  }
   CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->n_ccd, 0, sizeof(int), sim->st));
   CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), sim->st));
   rebuild_trees(sim, x_dev);
