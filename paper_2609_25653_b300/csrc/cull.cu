@@ -10,6 +10,7 @@
 // This file is compiled with -fmad=false: the classification and the
 // squared distance that decide membership (s < dhat^2) round operation by
 // operation as written, so the active set is exactly reproducible.
+#include <algorithm>
 #include "bvh.cuh"
 #include "common.cuh"
 #include "dist.cuh"
@@ -396,9 +397,14 @@ __device__ inline void emit_cand(int* cand, int* n_cand, int ccap, int kind, int
   }
 }
 
-__global__ void k_sweep_pt_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
-                               int max_iter, TreeView T, int* cand, int* n_cand, int ccap,
-                               unsigned long long* alpha_bits, int* n_ccd, int* err) {
+// Sweep traversal: every (point, triangle) and (edge, edge) pair whose padded
+// swept boxes overlap becomes a candidate (the line search and the next
+// iterate take their active pairs from this list).  The CCD of the
+// candidates runs afterwards in k_ccd_cand: evaluating it inside the
+// traversal left a few lanes of each warp doing FP64 work while the others
+// walked the tree.
+__global__ void k_sweep_pt_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, TreeView T,
+                               int* cand, int* n_cand, int ccap, int* err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.nsv) return;
   int p = S.sv[i];
@@ -406,36 +412,18 @@ __global__ void k_sweep_pt_bvh(DevScene S, const double* __restrict__ xv, const 
   d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf);
   swept(xv, pv, p, la, ha);
   double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
-  double amin = 1.0;
-  const int sc = S.alpha_sc ? scene_of_vertex(S, p) : 0;
-  int nc = 0;
   bool ok = traverse(T, q, [&](int t) {
     int3 tv = S.tris[t];
     int tvv[3] = {tv.x, tv.y, tv.z};
     if (excluded(S, &p, 1, tvv, 3)) return;
     int ids[4] = {p, tv.x, tv.y, tv.z};
     emit_cand(cand, n_cand, ccap, 0, i, t, ids);
-    d3 lb = mk(inf, inf, inf), hb = mk(-inf, -inf, -inf);
-    swept(xv, pv, tv.x, lb, hb);
-    swept(xv, pv, tv.y, lb, hb);
-    swept(xv, pv, tv.z, lb, hb);
-    if (!overlap(la, ha, lb, hb)) return;
-    d3 x[4], pp[4];
-    for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
-    ++nc;
-    amin = fmin(amin, accd(0, x, pp, s_frac, ccd_tmax(S, alpha_bits, sc, amin), max_iter));
   });
   if (!ok) atomicOr(err, ERRF_BVH);
-  if (nc) atomicAdd(n_ccd, nc);
-  if (amin < 1.0) {
-    atomicMin(alpha_bits, dbits(amin));
-    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, p), dbits(amin));
-  }
 }
 
-__global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, double s_frac,
-                               int max_iter, TreeView T, int* cand, int* n_cand, int ccap,
-                               unsigned long long* alpha_bits, int* n_ccd, int* err) {
+__global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const double* __restrict__ pv, TreeView T,
+                               int* cand, int* n_cand, int ccap, int* err) {
   int ea = blockIdx.x * blockDim.x + threadIdx.x;
   if (ea >= S.nedge) return;
   int2 A = S.edges[ea];
@@ -445,9 +433,6 @@ __global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const 
   swept(xv, pv, A.x, la, ha);
   swept(xv, pv, A.y, la, ha);
   double q[6] = {la.x, la.y, la.z, ha.x, ha.y, ha.z};
-  double amin = 1.0;
-  const int sc = S.alpha_sc ? scene_of_vertex(S, A.x) : 0;
-  int nc = 0;
   bool ok = traverse(T, q, [&](int eb) {
     if (eb <= ea) return;
     int2 B = S.edges[eb];
@@ -455,21 +440,47 @@ __global__ void k_sweep_ee_bvh(DevScene S, const double* __restrict__ xv, const 
     if (excluded(S, va, 2, vb, 2)) return;
     int ids[4] = {A.x, A.y, B.x, B.y};
     emit_cand(cand, n_cand, ccap, 1, ea, eb, ids);
-    d3 lb = mk(inf, inf, inf), hb = mk(-inf, -inf, -inf);
-    swept(xv, pv, B.x, lb, hb);
-    swept(xv, pv, B.y, lb, hb);
-    if (!overlap(la, ha, lb, hb)) return;
+  });
+  if (!ok) atomicOr(err, ERRF_BVH);
+}
+
+// CCD of the sweep's candidates, one candidate per thread: the exact FP64
+// swept-box test (the tree's boxes are padded and FP32), then ACCD bounded by
+// the running minimum of the pair's scene; a result below that bound lowers
+// the scene's and the global step bound.  n_ccd counts the ACCD evaluations.
+// Reads at most ccap candidates: when more were found the host enlarges the
+// list and repeats the Newton iteration before it uses the bound.
+__global__ void __launch_bounds__(128) k_ccd_cand(DevScene S, const double* __restrict__ xv,
+                                                  const double* __restrict__ pv, double s_frac, int max_iter,
+                                                  const int* __restrict__ cand, const int* __restrict__ n_cand,
+                                                  int ccap, unsigned long long* alpha_bits, int* n_ccd) {
+  const int n = min(*n_cand, ccap);
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  int nc = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const int* r = cand + 8 * (size_t)c;
+    const int kind = r[0];
+    const int ids[4] = {r[4], r[5], r[6], r[7]};
+    const int na = kind == 0 ? 1 : 2;  // vertices of the first primitive
+    d3 la = mk(inf, inf, inf), ha = mk(-inf, -inf, -inf), lb = la, hb = ha;
+    for (int k = 0; k < 4; ++k) {
+      if (k < na) swept(xv, pv, ids[k], la, ha);
+      else swept(xv, pv, ids[k], lb, hb);
+    }
+    if (!overlap(la, ha, lb, hb)) continue;
     d3 x[4], pp[4];
     for (int k = 0; k < 4; ++k) { x[k] = ld3(xv, ids[k]); pp[k] = ld3(pv, ids[k]); }
     ++nc;
-    amin = fmin(amin, accd(1, x, pp, s_frac, ccd_tmax(S, alpha_bits, sc, amin), max_iter));
-  });
-  if (!ok) atomicOr(err, ERRF_BVH);
-  if (nc) atomicAdd(n_ccd, nc);
-  if (amin < 1.0) {
-    atomicMin(alpha_bits, dbits(amin));
-    if (S.alpha_sc) atomicMin(S.alpha_sc + scene_of_vertex(S, A.x), dbits(amin));
+    const int sc = S.alpha_sc ? scene_of_vertex(S, ids[0]) : 0;
+    const double tmax = ccd_tmax(S, alpha_bits, sc, 1.0);
+    const double t = accd(kind, x, pp, s_frac, tmax, max_iter);
+    if (t < tmax) {
+      atomicMin(alpha_bits, dbits(t));
+      if (S.alpha_sc) atomicMin(S.alpha_sc + sc, dbits(t));
+    }
   }
+  nc = __reduce_add_sync(0xffffffffu, nc);
+  if ((threadIdx.x & 31) == 0 && nc) atomicAdd(n_ccd, nc);
 }
 
 // Active pairs among the candidates: the exact classification and s < dhat^2 at xv.
@@ -548,8 +559,13 @@ void launch_sweep_bvh(cudaStream_t st, const DevScene& S, const double* xv, cons
   bvh_refit(st, tri);
   bvh_leaf_boxes(st, edge, (const int*)S.edges, 2, xv, pv, pad);
   bvh_refit(st, edge);
-  if (S.nsv) { k_sweep_pt_bvh<<<(S.nsv + 127) / 128, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, view(tri), cand, n_cand, ccap, alpha_bits, n_ccd, err); count_launch(); }
-  if (S.nedge) { k_sweep_ee_bvh<<<(S.nedge + 127) / 128, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, view(edge), cand, n_cand, ccap, alpha_bits, n_ccd, err); count_launch(); }
+  if (S.nsv) { k_sweep_pt_bvh<<<(S.nsv + 127) / 128, 128, 0, st>>>(S, xv, pv, view(tri), cand, n_cand, ccap, err); count_launch(); }
+  if (S.nedge) { k_sweep_ee_bvh<<<(S.nedge + 127) / 128, 128, 0, st>>>(S, xv, pv, view(edge), cand, n_cand, ccap, err); count_launch(); }
+  if (ccap > 0) {
+    const int grid = std::max(1, std::min((ccap + 127) / 128, 148 * 16));
+    k_ccd_cand<<<grid, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, cand, n_cand, ccap, alpha_bits, n_ccd);
+    count_launch();
+  }
 }
 
 void launch_filter_active(cudaStream_t st, int grid, const DevScene& S, const double* xv, double sh, const int* cand,
