@@ -462,9 +462,9 @@ __device__ inline void contact_rows(const PcgArgs& a, const M* pairH, const M* f
 }
 
 // ---------------------------------------------------------------------------
-// Reductions.  The solve is bound by barrier latency, and FP64 issue slots
-// are scarce on this part (2 FMA / clock / SM): FP32 sums take one barrier,
-// FP64 sums go through one warp.
+// Reductions.  The solve is bound by barrier latency, so a sum over the CTA
+// takes one barrier: shuffles inside each warp, then every thread adds the
+// per-warp sums (8 values) from shared memory in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int PCG_THREADS_MAX = 256;
 constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
@@ -472,77 +472,40 @@ constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
 static_assert(PCG_SCENES_MAX <= PCG_THREADS_MAX, "one decision thread per scene");
 constexpr int PCG_WARPS_MAX = PCG_THREADS_MAX / 32;
 struct Shared {
-  union {
-    double vals[3][PCG_THREADS_MAX];  // per-thread values of an FP64 CTA sum
-    double tot[3][PCG_SCENES_MAX];    // per-scene totals (several solves)
-  };
-  double out[3];                    // results of an FP64 CTA sum
-  float wsum[2][3][PCG_WARPS_MAX];  // per-warp sums of an FP32 CTA sum, two alternating buffers
+  double tot[3][PCG_SCENES_MAX];    // per-scene totals (several solves)
+  double wsum[2][3][PCG_WARPS_MAX]; // per-warp sums of a CTA sum, two alternating buffers
   double red[8][12];                // per-warp sums of the ABD rows
   double scal[4];                   // scalars of an iteration (the scene's decision thread -> all)
   int action;
   unsigned long long agg[4];        // end of the solve: maxima over the scenes
 };
 
-// Sum over the CTA of N <= 3 per-thread values of type T, into res in every
-// thread, in an order that is the same in every CTA and every thread.
-// FP32: one barrier; each warp adds its lanes by shuffles, lane 0 stores the
-// warp's sums, every thread adds the warps' sums in warp order.  The two
+// Sum over the CTA of N <= 3 per-thread values of type T, as FP64 in res in
+// every thread, behind one barrier: each warp adds its lanes by shuffles,
+// lane 0 stores the warp's sums, and every thread adds the warps' sums in
+// warp order (the same order in every CTA and every thread).  The two
 // staging buffers alternate with tick (one per thread, advanced by every
-// call, so equal in all threads), so a call's stores cannot reach sums that
-// a slower thread is still reading from the call before.  FP64 (2 FMA per
-// clock per SM on this part, so as few lanes as possible add): every thread
-// stores its values, warp 0 adds them (8 per lane and value, then 5 shuffle
-// levels) into sh.out, read after a second barrier (res is not written: read
-// the results with cta_result).  Every thread of the CTA must call it.
+// call, so equal in all threads): a call's stores cannot reach sums that a
+// slower thread is still reading from the call before.  Every thread of the
+// CTA must call it.
 template <int N, typename T>
-__device__ inline void cta_sum(const T (&v)[N], Shared& sh, int& tick, T (&res)[N]) {
-  if constexpr (sizeof(T) == 4) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    float (*buf)[PCG_WARPS_MAX] = sh.wsum[tick & 1];
-    ++tick;
+__device__ inline void cta_sum(const T (&v)[N], Shared& sh, int& tick, double (&res)[N]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double (*buf)[PCG_WARPS_MAX] = sh.wsum[tick & 1];
+  ++tick;
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T t = v[j];
+  for (int j = 0; j < N; ++j) {
+    T t = v[j];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) buf[j][w] = t;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T acc = T(0);
-      for (int k = 0; k < nw; ++k) acc += buf[j][k];
-      res[j] = acc;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < N; ++j) sh.vals[j][threadIdx.x] = v[j];
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        T t = T(0);
-        for (int k = lane; k < (int)blockDim.x; k += 32) t += sh.vals[j][k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) sh.out[j] = t;
-      }
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) buf[j][w] = (double)t;
   }
-}
-template <int N, typename T>
-__device__ inline T cta_result(const Shared& sh, const T (&res)[N], int j) {
-  if constexpr (sizeof(T) == 4) {
-    T x = res[0];  // selected, not indexed: res stays in registers
+  __syncthreads();
 #pragma unroll
-    for (int k = 1; k < N; ++k)
-      if (j == k) x = res[k];
-    return x;
-  } else {
-    return (T)sh.out[j];
+  for (int j = 0; j < N; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += buf[j][k];
+    res[j] = s;
   }
 }
 
@@ -569,11 +532,11 @@ __device__ inline void load_partials(const T* rep, int nblk, Partials<T>& P) {
 template <typename T>
 __device__ inline void write_partials(T* rep0 /* replica 0 of this parity, [3][grid] */, size_t rep_stride, int nblk,
                                       Shared& sh, int& tick, const T (&v)[3]) {
-  T r[3];
+  double r[3];
   cta_sum<3, T>(v, sh, tick, r);
   if (threadIdx.x < 3 * PCG_REPLICAS) {
     const int rep = threadIdx.x / 3, j = threadIdx.x % 3;
-    rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = cta_result(sh, r, j);
+    rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = (T)(j == 0 ? r[0] : j == 1 ? r[1] : r[2]);
   }
 }
 
@@ -584,7 +547,7 @@ __device__ inline void write_partials(T* rep0 /* replica 0 of this parity, [3][g
 // Every thread must call it; read the results with scene_total.
 template <int N, typename T>
 __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] */, int nblk, Shared& sh,
-                                    const Partials<T>* P, int& tick, T (&res)[N]) {
+                                    const Partials<T>* P, int& tick, double (&res)[N]) {
   if (a.n_psc == 1) {
     T v[N];
     int start = 0;
@@ -624,9 +587,9 @@ __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] 
   }
   __syncthreads();
 }
-template <int N, typename T>
-__device__ inline T scene_total(const PcgArgs& a, const Shared& sh, const T (&res)[N], int j, int sc) {
-  return a.n_psc == 1 ? cta_result(sh, res, j) : (T)sh.tot[j][sc];
+template <int N>
+__device__ inline double scene_total(const PcgArgs& a, const Shared& sh, const double (&res)[N], int j, int sc) {
+  return a.n_psc == 1 ? res[j] : sh.tot[j][sc];
 }
 
 // End of a solve: CTA 0 reports the iterations, worst status, restarts and
@@ -819,9 +782,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   const int nf = S.nf;
   const int n3 = 3 * a.n_nodes;
   const int my_sc = a.cta_scene[cta];
-  // thread s runs the FP64 scalar recurrences of scene s and publishes its CTA's scene in shared memory
-  // (FP64 divisions in every thread would cost more issue slots than the broadcast barriers)
-  constexpr bool single = false;
+  // one solve: every thread runs the scalar recurrences (identical inputs, identical results, nothing
+  // to broadcast); several: thread s runs those of scene s and publishes its CTA's scene in shared memory
+  const bool single = a.n_psc == 1;
   const bool decider = single || (int)threadIdx.x < a.n_psc;
   const int dsc = single ? 0 : (int)threadIdx.x;
   const bool writer = decider && dsc == my_sc && (!single || threadIdx.x == 0);
@@ -914,7 +877,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   auto write_norm = [&](double v) {
     double w[1] = {v}, r[1];
     cta_sum<1, double>(w, sh, tick, r);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = r[0];
   };
   // the FP64 operator (assembled layout) for the true residual
   OpView<double> op64{a.val64 + 9 * (size_t)k0, 1, 9};
@@ -1189,8 +1152,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   const int dsc = single ? 0 : (int)threadIdx.x;
   const bool writer = decider && dsc == my_sc && (!single || threadIdx.x == 0);
   int tick = 0;                  // cta_sum staging buffer
-  float tots[3];                 // FP32 totals of the last iteration sums (one solve)
-  double tot1[1];                // FP64 total of the last norm (one solve)
+  double tots[3], tot1[1];       // totals of the last scene_totals call (one solve)
 
   int r0 = 0, r1 = 0, k0 = 0, nloc = 0, ab0 = 0, ab1 = 0;
   OpView<F> op{nullptr, 0, 1};
@@ -1281,7 +1243,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   auto write_norm = [&](double v) {
     double wv[1] = {v}, r[1];
     cta_sum<1, double>(wv, sh, tick, r);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = r[0];
   };
 
   // ---- x = 0, t64 = b, |b|^2 of every scene
@@ -1388,8 +1350,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     int act = ACT_IDLE;
     F al = F(0), be = F(0);
     if (decider && !done) {
-      const F gamma = scene_total(a, sh, tots, 0, dsc), delta = scene_total(a, sh, tots, 1, dsc),
-              rr = scene_total(a, sh, tots, 2, dsc);
+      const F gamma = (F)scene_total(a, sh, tots, 0, dsc), delta = (F)scene_total(a, sh, tots, 1, dsc),
+              rr = (F)scene_total(a, sh, tots, 2, dsc);
       act = ACT_STEP;
       if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) { status = 2; done = true; act = ACT_IDLE; }
       else {
