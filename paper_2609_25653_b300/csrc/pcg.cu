@@ -462,51 +462,47 @@ __device__ inline void contact_rows(const PcgArgs& a, const M* pairH, const M* f
 }
 
 // ---------------------------------------------------------------------------
-// Reductions.  The solve is bound by barrier latency, so a sum over the CTA
-// takes one barrier: shuffles inside each warp, then every thread adds the
-// per-warp sums (8 values) from shared memory in a fixed order.
+// Reductions.  FP64 issue slots are scarce on this part (2 FMA / clock / SM),
+// so every sum over the CTA goes through shared memory and one warp: each
+// thread stores its values, warp 0 adds them in a fixed order (8 per lane and
+// value), then 5 shuffle levels.
 // ---------------------------------------------------------------------------
 constexpr int PCG_THREADS_MAX = 256;
 constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
 
 static_assert(PCG_SCENES_MAX <= PCG_THREADS_MAX, "one decision thread per scene");
-constexpr int PCG_WARPS_MAX = PCG_THREADS_MAX / 32;
 struct Shared {
-  double tot[3][PCG_SCENES_MAX];    // per-scene totals (several solves)
-  double wsum[2][3][PCG_WARPS_MAX]; // per-warp sums of a CTA sum, two alternating buffers
+  union {
+    double vals[3][PCG_THREADS_MAX];  // per-thread values of a CTA sum
+    double tot[3][PCG_SCENES_MAX];    // per-scene totals (several solves)
+  };
   double red[8][12];                // per-warp sums of the ABD rows
+  double out[12];                   // results, read by every thread
   double scal[4];                   // scalars of an iteration (the scene's decision thread -> all)
   int action;
   unsigned long long agg[4];        // end of the solve: maxima over the scenes
 };
 
-// Sum over the CTA of N <= 3 per-thread values of type T, as FP64 in res in
-// every thread, behind one barrier: each warp adds its lanes by shuffles,
-// lane 0 stores the warp's sums, and every thread adds the warps' sums in
-// warp order (the same order in every CTA and every thread).  The two
-// staging buffers alternate with tick (one per thread, advanced by every
-// call, so equal in all threads): a call's stores cannot reach sums that a
-// slower thread is still reading from the call before.  Every thread of the
-// CTA must call it.
+// Sum over the CTA of N <= 3 per-thread values of type T; results in
+// sh.out[0..N) (as FP64) for every thread.
 template <int N, typename T>
-__device__ inline void cta_sum(const T (&v)[N], Shared& sh, int& tick, double (&res)[N]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  double (*buf)[PCG_WARPS_MAX] = sh.wsum[tick & 1];
-  ++tick;
+__device__ inline void cta_sum(const T (&v)[N], Shared& sh) {
+  T (*vals)[PCG_THREADS_MAX] = reinterpret_cast<T (*)[PCG_THREADS_MAX]>(&sh.vals[0][0]);
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    T t = v[j];
+  for (int j = 0; j < N; ++j) vals[j][threadIdx.x] = v[j];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) buf[j][w] = (double)t;
+    for (int j = 0; j < N; ++j) {
+      T t = T(0);
+      for (int k = lane; k < (int)blockDim.x; k += 32) t += vals[j][k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) sh.out[j] = (double)t;
+    }
   }
   __syncthreads();
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    double s = 0.0;
-    for (int k = 0; k < nw; ++k) s += buf[j][k];
-    res[j] = s;
-  }
 }
 
 // Sum over the CTAs of 3 partial sums of type T (one replica [3][grid]):
@@ -527,27 +523,40 @@ __device__ inline void load_partials(const T* rep, int nblk, Partials<T>& P) {
     P.v[2][j] = in ? rep[2 * nblk + b] : T(0);
   }
 }
+template <typename T>
+__device__ inline void totals3(const T* rep, int nblk, const Partials<T>& P, Shared& sh, double& t0, double& t1,
+                               double& t2) {
+  T v[3] = {P.v[0][0] + P.v[0][1], P.v[1][0] + P.v[1][1], P.v[2][0] + P.v[2][1]};
+  for (int b = threadIdx.x + 2 * blockDim.x; b < nblk; b += blockDim.x) {
+    v[0] += rep[b];
+    v[1] += rep[nblk + b];
+    v[2] += rep[2 * nblk + b];
+  }
+  cta_sum<3, T>(v, sh);
+  t0 = sh.out[0]; t1 = sh.out[1]; t2 = sh.out[2];
+  __syncthreads();
+}
 
 // This CTA's 3 partial sums, written to every replica.
 template <typename T>
 __device__ inline void write_partials(T* rep0 /* replica 0 of this parity, [3][grid] */, size_t rep_stride, int nblk,
-                                      Shared& sh, int& tick, const T (&v)[3]) {
-  double r[3];
-  cta_sum<3, T>(v, sh, tick, r);
+                                      Shared& sh, const T (&v)[3]) {
+  cta_sum<3, T>(v, sh);
   if (threadIdx.x < 3 * PCG_REPLICAS) {
-    const int rep = threadIdx.x / 3, j = threadIdx.x % 3;
-    rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = (T)(j == 0 ? r[0] : j == 1 ? r[1] : r[2]);
+    int rep = threadIdx.x / 3, j = threadIdx.x % 3;
+    rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = (T)sh.out[j];
   }
+  __syncthreads();
 }
 
 // Totals of N per-CTA values for every solve, in a fixed order so that every
 // CTA holds bit-identical totals.  One solve: the CTA sum over all CTAs into
-// res of every thread (the first 2 x blockDim values may already be in P);
-// several: one warp per scene over that scene's CTAs into sh.tot[j][s].
-// Every thread must call it; read the results with scene_total.
+// sh.out (the first 2 x blockDim values may already be in P); several: one
+// warp per scene over that scene's CTAs into sh.tot[j][s].  Every thread must
+// call it; read the results with scene_total.
 template <int N, typename T>
 __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] */, int nblk, Shared& sh,
-                                    const Partials<T>* P, int& tick, double (&res)[N]) {
+                                    const Partials<T>* P) {
   if (a.n_psc == 1) {
     T v[N];
     int start = 0;
@@ -562,7 +571,7 @@ __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] 
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] += rep[(size_t)j * nblk + b];
     }
-    cta_sum<N, T>(v, sh, tick, res);
+    cta_sum<N, T>(v, sh);
     return;
   }
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -587,22 +596,20 @@ __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] 
   }
   __syncthreads();
 }
-template <int N>
-__device__ inline double scene_total(const PcgArgs& a, const Shared& sh, const double (&res)[N], int j, int sc) {
-  return a.n_psc == 1 ? res[j] : sh.tot[j][sc];
+__device__ inline double scene_total(const PcgArgs& a, const Shared& sh, int j, int sc) {
+  return a.n_psc == 1 ? sh.out[j] : sh.tot[j][sc];
 }
 
 // End of a solve: CTA 0 reports the iterations, worst status, restarts and
 // largest relative residual over the scenes (and every scene's residual and
-// iterations when asked).  reporter: the thread holds one scene's final state
-// and reports it.  Status ranks: 0 converged < 3 budget spent < 1 breakdown
-// < 2 non-finite.  Every thread of every CTA must call it.
-__device__ inline void report_solve(const PcgArgs& a, Shared& sh, bool reporter, int sc, int it, int status,
+// iterations when asked).  Status ranks: 0 converged < 3 budget spent <
+// 1 breakdown < 2 non-finite.  Every thread of every CTA must call it.
+__device__ inline void report_solve(const PcgArgs& a, Shared& sh, bool decider, int sc, int it, int status,
                                     int restarts, double res) {
   if (blockIdx.x != 0) return;
   if (threadIdx.x < 4) sh.agg[threadIdx.x] = 0ull;
   __syncthreads();
-  if (reporter) {
+  if (decider) {
     const int rank = status == 0 ? 0 : status == 3 ? 1 : status == 1 ? 2 : 3;
     atomicMax(&sh.agg[0], (unsigned long long)it);
     atomicMax(&sh.agg[1], (unsigned long long)rank);
@@ -619,6 +626,15 @@ __device__ inline void report_solve(const PcgArgs& a, Shared& sh, bool reporter,
     a.out[2] = (int)sh.agg[2];
     a.res[0] = __longlong_as_double((long long)sh.agg[3]);
   }
+}
+
+__device__ inline double total_fp64(const double* rep /* [grid] */, int nblk, Shared& sh) {
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v[0] += rep[b];
+  cta_sum<1, double>(v, sh);
+  double t = sh.out[0];
+  __syncthreads();
+  return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -782,14 +798,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   const int nf = S.nf;
   const int n3 = 3 * a.n_nodes;
   const int my_sc = a.cta_scene[cta];
-  // one solve: every thread runs the scalar recurrences (identical inputs, identical results, nothing
-  // to broadcast); several: thread s runs those of scene s and publishes its CTA's scene in shared memory
-  const bool single = a.n_psc == 1;
-  const bool decider = single || (int)threadIdx.x < a.n_psc;
-  const int dsc = single ? 0 : (int)threadIdx.x;
-  const bool writer = decider && dsc == my_sc && (!single || threadIdx.x == 0);
-  int tick = 0;                  // cta_sum staging buffer
-  double tots[3], tot1[1];       // totals of the last scene_totals call (one solve)
+  const bool decider = (int)threadIdx.x < a.n_psc;  // runs the recurrences of scene threadIdx.x
+  const int dsc = threadIdx.x;
 
   // ---- this CTA's rows; shared memory: row products (FEM: 3 per row, ABD: 12
   //      per owned body), then (resident) operator planes, preconditioner, columns, row offsets
@@ -875,9 +885,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   };
   // this CTA's part of a norm, to partD (every replica)
   auto write_norm = [&](double v) {
-    double w[1] = {v}, r[1];
-    cta_sum<1, double>(w, sh, tick, r);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = r[0];
+    double w[1] = {v};
+    cta_sum<1, double>(w, sh);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
   };
   // the FP64 operator (assembled layout) for the true residual
   OpView<double> op64{a.val64 + 9 * (size_t)k0, 1, 9};
@@ -897,7 +908,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     write_norm(v);
   }
   grid.sync();
-  scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr, tick, tot1);
+  scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
 
   // ---- per-scene state, held by the scene's decision thread
   constexpr bool F32 = sizeof(M) == 4;
@@ -915,7 +926,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     return t;
   };
   if (decider) {
-    bb = scene_total(a, sh, tot1, 0, dsc);
+    bb = scene_total(a, sh, 0, dsc);
     const bool skip = a.scene_skip && a.scene_skip[dsc];
     done = skip || !(bb > 0.0) || !isfinite(bb);
     status = (skip || isfinite(bb)) ? 0 : 2;
@@ -925,21 +936,18 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     unscale = sqrt(bb);
     sigma = done ? 1.0 : 1.0 / unscale;
     tol_in2 = inner_tol2();
-    if (writer) { sh.action = done ? 0 : 1; sh.scal[3] = sigma; }
+    if (dsc == my_sc) { sh.action = done ? 0 : 1; sh.scal[3] = sigma; }
   }
-  bool my_run = !done;  // this CTA's scene forms products in the next loop
-  if (!single) {
-    __syncthreads();
-    my_run = my_sc >= 0 && sh.action;
-    __syncthreads();
-  }
+  __syncthreads();
+  bool my_run = my_sc >= 0 && sh.action;  // this CTA's scene forms products in the next loop
+  __syncthreads();
 
   // ---- (re)start of the scenes whose CTAs have on = true, from t64 = b - A x:
   //      r = sigma t64, u = M^-1 r, w = A u, m = M^-1 w, partial sums into parity par.
   //      Two grid barriers, taken by every CTA.
   auto restart = [&](int par, bool on) {
     if (on) {
-      const double sg = single ? sigma : sh.scal[3];
+      const double sg = sh.scal[3];
       for_nodes([&](int i, const double*) {
         double rv[3];
         for (int c = 0; c < 3; ++c) {
@@ -970,7 +978,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         pv[1] += y[0] * u0 + y[1] * u1 + y[2] * u2;
         pv[2] += rr0 * rr0 + rr1 * rr1 + rr2 * rr2;
       });
-      write_partials<double>(partT + (size_t)par * 3 * nblk, repT, nblk, sh, tick, pv);
+      write_partials<double>(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv);
     }
     grid.sync();
   };
@@ -986,14 +994,14 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     Partials<double> P;
     if (a.n_psc == 1) load_partials<double>(rep, nblk, P);
     if (my_run) products(false, op, colp, rowp, M(0), pairH, fHu, mcur);
-    scene_totals<3, double>(a, rep, nblk, sh, a.n_psc == 1 ? &P : nullptr, tick, tots);
+    scene_totals<3, double>(a, rep, nblk, sh, a.n_psc == 1 ? &P : nullptr);
     // the scalar recurrences of every scene (identical inputs in every CTA, identical results); the
     // CTA's own scene reaches its threads through shared memory
     int act = ACT_IDLE;
-    double al = 0.0, be = 0.0;
     if (decider && !done) {
-      const double gamma = scene_total(a, sh, tots, 0, dsc), delta = scene_total(a, sh, tots, 1, dsc),
-                   rr = scene_total(a, sh, tots, 2, dsc);
+      const double gamma = scene_total(a, sh, 0, dsc), delta = scene_total(a, sh, 1, dsc),
+                   rr = scene_total(a, sh, 2, dsc);
+      double al = 0.0, be = 0.0;
       act = ACT_STEP;
       if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) { status = 2; done = true; act = ACT_IDLE; }
       else {
@@ -1015,27 +1023,17 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         fresh = false;
         ++it;
       }
-      if (writer) {
+      if (dsc == my_sc) {
         sh.scal[0] = al;
         sh.scal[1] = be;
         sh.scal[2] = al * unscale;
       }
     }
-    bool any_refresh, any_live;
-    int my_act;
-    double alpha, beta, ax;
-    if (single) {
-      any_refresh = act == ACT_REFRESH;
-      any_live = act != ACT_IDLE;
-      my_act = act;
-      alpha = al; beta = be; ax = al * unscale;
-    } else {
-      if (writer) sh.action = act;
-      any_refresh = __syncthreads_or(act == ACT_REFRESH);
-      any_live = __syncthreads_or(act != ACT_IDLE);
-      my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
-      alpha = sh.scal[0]; beta = sh.scal[1]; ax = sh.scal[2];
-    }
+    if (decider && dsc == my_sc) sh.action = act;
+    const bool any_refresh = __syncthreads_or(act == ACT_REFRESH);
+    const bool any_live = __syncthreads_or(act != ACT_IDLE);
+    const int my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
+    const double alpha = sh.scal[0], beta = sh.scal[1], ax = sh.scal[2];
     if (!any_live) break;
     if (my_act == ACT_STEP) {
       // every recurrence of the owned nodes, one thread per node
@@ -1072,7 +1070,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         pv[1] += wn[0] * un[0] + wn[1] * un[1] + wn[2] * un[2];
         pv[2] += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
       });
-      write_partials<double>(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, tick, pv);
+      write_partials<double>(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv);
     }
     bool my_restart = false;
     if (any_refresh) {
@@ -1090,10 +1088,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         write_norm(v);
       }
       grid.sync();
-      scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr, tick, tot1);
-      bool again = false;
+      scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
       if (act == ACT_REFRESH) {  // decision threads of the refreshing scenes
-        tt = scene_total(a, sh, tot1, 0, dsc);
+        tt = scene_total(a, sh, 0, dsc);
+        bool again = false;
         if (!isfinite(tt)) { status = 2; done = true; }
         else if (tt <= tol2_true || it >= a.max_iter || replaced >= max_replace) done = true;
         else {
@@ -1104,14 +1102,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
           fresh = true;
           again = true;
         }
-        if (writer) { sh.action = again ? 1 : 0; sh.scal[3] = sigma; }
+        if (dsc == my_sc) { sh.action = again ? 1 : 0; sh.scal[3] = sigma; }
       }
-      if (single) my_restart = ref && again;
-      else {
-        __syncthreads();
-        my_restart = ref && sh.action;
-        __syncthreads();
-      }
+      __syncthreads();
+      my_restart = ref && sh.action;
+      __syncthreads();
       restart(par ^ 1, my_restart);
     } else {
       grid.sync();
@@ -1119,7 +1114,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     my_run = my_act == ACT_STEP || my_restart;
   }
   if (decider && status == 0 && !(tt <= tol2_true)) status = 3;  // budget spent before the tolerance
-  report_solve(a, sh, single ? threadIdx.x == 0 : decider, dsc, it, status, replaced, decider && bb > 0.0 ? sqrt(fmax(tt, 0.0) / bb) : 0.0);
+  report_solve(a, sh, decider, dsc, it, status, replaced, decider && bb > 0.0 ? sqrt(fmax(tt, 0.0) / bb) : 0.0);
 }
 
 // Mixed-precision solve: iterative refinement around an FP32 conjugate-
@@ -1145,14 +1140,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   const int nf = S.nf;
   const int n3 = 3 * a.n_nodes;
   const int my_sc = a.cta_scene[cta];
-  // one solve: every thread runs the scalar recurrences (identical inputs, identical results, nothing
-  // to broadcast); several: thread s runs those of scene s and publishes its CTA's scene in shared memory
-  const bool single = a.n_psc == 1;
-  const bool decider = single || (int)threadIdx.x < a.n_psc;
-  const int dsc = single ? 0 : (int)threadIdx.x;
-  const bool writer = decider && dsc == my_sc && (!single || threadIdx.x == 0);
-  int tick = 0;                  // cta_sum staging buffer
-  double tots[3], tot1[1];       // totals of the last scene_totals call (one solve)
+  const bool decider = (int)threadIdx.x < a.n_psc;  // runs the recurrences of scene threadIdx.x
+  const int dsc = threadIdx.x;
 
   int r0 = 0, r1 = 0, k0 = 0, nloc = 0, ab0 = 0, ab1 = 0;
   OpView<F> op{nullptr, 0, 1};
@@ -1241,9 +1230,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     }
   };
   auto write_norm = [&](double v) {
-    double wv[1] = {v}, r[1];
-    cta_sum<1, double>(wv, sh, tick, r);
-    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = r[0];
+    double wv[1] = {v};
+    cta_sum<1, double>(wv, sh);
+    if (threadIdx.x < PCG_REPLICAS) partD[threadIdx.x * (size_t)nblk + cta] = sh.out[0];
+    __syncthreads();
   };
 
   // ---- x = 0, t64 = b, |b|^2 of every scene
@@ -1260,7 +1250,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     write_norm(v);
   }
   grid.sync();
-  scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr, tick, tot1);
+  scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
 
   // ---- per-scene state, held by the scene's decision thread
   constexpr int STALL = 80;
@@ -1279,10 +1269,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     gamma_old = F(1);
     rr_best = F(0);
     it_best = it;
-    if (writer) { sh.scal[2] = unscale; sh.scal[3] = 1.0 / unscale; }
+    if (dsc == my_sc) { sh.scal[2] = unscale; sh.scal[3] = 1.0 / unscale; }
   };
   if (decider) {
-    bb = scene_total(a, sh, tot1, 0, dsc);
+    bb = scene_total(a, sh, 0, dsc);
     const bool skip = a.scene_skip && a.scene_skip[dsc];
     done = skip || !(bb > 0.0) || !isfinite(bb);
     status = (skip || isfinite(bb)) ? 0 : 2;
@@ -1290,20 +1280,17 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     tt = bb;
     tol2_true = a.rtol * a.rtol * bb;
     if (!done) begin_inner();
-    if (writer) sh.action = done ? 0 : 1;
+    if (dsc == my_sc) sh.action = done ? 0 : 1;
   }
-  bool my_run = !done;  // this CTA's scene is inside an inner solve
-  if (!single) {
-    __syncthreads();
-    my_run = my_sc >= 0 && sh.action;
-    __syncthreads();
-  }
+  __syncthreads();
+  bool my_run = my_sc >= 0 && sh.action;  // this CTA's scene is inside an inner solve
+  __syncthreads();
 
   // inner solve start of this CTA's scene: r = sigma t64, u = M^-1 r, p = s = d = 0, and the
   // CTA's parts of (r, u), (r, r)
   F g_l = F(0), rr_l = F(0);
   auto init_inner = [&]() {
-    const double sigma = single ? 1.0 / unscale : sh.scal[3];
+    const double sigma = sh.scal[3];
     g_l = F(0);
     rr_l = F(0);
     for_nodes([&](int i, int) {
@@ -1337,7 +1324,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
         d_l += w0 * u[q] + w1 * u[q + 1] + w2 * u[q + 2];
       });
       const F pl[3] = {g_l, d_l, rr_l};
-      write_partials<F>(partF + (size_t)par * 3 * nblk, repT, nblk, sh, tick, pl);
+      write_partials<F>(partF + (size_t)par * 3 * nblk, repT, nblk, sh, pl);
     }
     grid.sync();
     // phase B: totals, the scalars of every scene, vector updates
@@ -1345,13 +1332,13 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       const F* rep = partF + (size_t)par * 3 * nblk + myrep * repT;
       Partials<F> P;
       if (a.n_psc == 1) load_partials<F>(rep, nblk, P);
-      scene_totals<3, F>(a, rep, nblk, sh, a.n_psc == 1 ? &P : nullptr, tick, tots);
+      scene_totals<3, F>(a, rep, nblk, sh, a.n_psc == 1 ? &P : nullptr);
     }
     int act = ACT_IDLE;
-    F al = F(0), be = F(0);
     if (decider && !done) {
-      const F gamma = (F)scene_total(a, sh, tots, 0, dsc), delta = (F)scene_total(a, sh, tots, 1, dsc),
-              rr = (F)scene_total(a, sh, tots, 2, dsc);
+      const F gamma = (F)scene_total(a, sh, 0, dsc), delta = (F)scene_total(a, sh, 1, dsc),
+              rr = (F)scene_total(a, sh, 2, dsc);
+      F al = F(0), be = F(0);
       act = ACT_STEP;
       if (!isfinite(rr) || !isfinite(delta) || !isfinite(gamma)) { status = 2; done = true; act = ACT_IDLE; }
       else {
@@ -1370,23 +1357,13 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
         alpha_old = al;
       }
       if (act == ACT_STEP) { fresh = false; ++it; }
-      if (writer) { sh.scal[0] = al; sh.scal[1] = be; }
+      if (dsc == my_sc) { sh.scal[0] = al; sh.scal[1] = be; }
     }
-    bool any_end, any_live;
-    int my_act;
-    F alpha, beta;
-    if (single) {
-      any_end = act == ACT_END;
-      any_live = act != ACT_IDLE;
-      my_act = act;
-      alpha = al; beta = be;
-    } else {
-      if (writer) sh.action = act;
-      any_end = __syncthreads_or(act == ACT_END);
-      any_live = __syncthreads_or(act != ACT_IDLE);
-      my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
-      alpha = (F)sh.scal[0]; beta = (F)sh.scal[1];
-    }
+    if (decider && dsc == my_sc) sh.action = act;
+    const bool any_end = __syncthreads_or(act == ACT_END);
+    const bool any_live = __syncthreads_or(act != ACT_IDLE);
+    const int my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
+    const F alpha = (F)sh.scal[0], beta = (F)sh.scal[1];
     if (!any_live) break;
     if (my_act == ACT_STEP) {
       g_l = F(0);
@@ -1421,7 +1398,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       // ---- scenes that ended an inner solve: x += d / sigma in FP64, then the FP64 residual
       const bool fin = my_act == ACT_END;
       if (fin) {
-        const double us = single ? unscale : sh.scal[2];
+        const double us = sh.scal[2];
         for_nodes([&](int i, int) {
           for (int c = 0; c < 3; ++c) x[3 * i + c] += us * (double)xi[3 * i + c];
         });
@@ -1440,10 +1417,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
         write_norm(v);
       }
       grid.sync();
-      scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr, tick, tot1);
-      bool again = false;
+      scene_totals<1, double>(a, partD + myrep * (size_t)nblk, nblk, sh, nullptr);
       if (act == ACT_END) {  // decision threads of those scenes
-        tt = scene_total(a, sh, tot1, 0, dsc);
+        tt = scene_total(a, sh, 0, dsc);
+        bool again = false;
         if (!isfinite(tt)) { status = 2; done = true; }
         else if (tt <= tol2_true || it >= a.max_iter || refine >= MAX_REFINE || !(tt > 0.0)) done = true;
         else {
@@ -1451,21 +1428,18 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
           begin_inner();
           again = true;
         }
-        if (writer) sh.action = again ? 1 : 0;
+        if (dsc == my_sc) sh.action = again ? 1 : 0;
       }
-      if (single) my_again = fin && again;
-      else {
-        __syncthreads();
-        my_again = fin && sh.action;
-        __syncthreads();
-      }
+      __syncthreads();
+      my_again = fin && sh.action;
+      __syncthreads();
       if (my_again) init_inner();
     }
     grid.sync();
     my_run = my_act == ACT_STEP || my_again;
   }
   if (decider && status == 0 && !(tt <= tol2_true)) status = 3;
-  report_solve(a, sh, single ? threadIdx.x == 0 : decider, dsc, it, status, refine, decider && bb > 0.0 ? sqrt(fmax(tt, 0.0) / bb) : 0.0);
+  report_solve(a, sh, decider, dsc, it, status, refine, decider && bb > 0.0 ? sqrt(fmax(tt, 0.0) / bb) : 0.0);
 }
 
 __global__ void k_to_float(size_t n, const double* __restrict__ src, float* __restrict__ dst, const int* n_dev,
