@@ -235,6 +235,21 @@ ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_nex
 ipc_status sim_profile(ipcsim* sim, int enable);
 ipc_status sim_profile_read(const ipcsim* sim, double* ms8, long long* n8, long long* work4);
 
+/* Host only (no GPU, no simulator): the partition of the rows among the CTAs
+ * of a cooperative PCG launch of `grid` CTAs, as sim_step plans it (block-
+ * Jacobi PCG of the Newton system, the solver of the Newton step; the paper
+ * does not describe its solver's parallel layout).  row: (nf + 4 nab + 1)
+ * BSR row offsets, FEM rows first, then the 4 pseudo-node rows of every ABD
+ * body; node_scene: (nf + 4 nab) scene of every row, or NULL with
+ * n_scenes = 1 (one solve).  Outputs (caller-owned): out4 = [FEM CTAs, ABD
+ * CTAs, independent solves (n_scenes when every scene got CTAs of its own,
+ * else 1), most FEM rows of one CTA]; seg (grid + 1): FEM row boundaries of
+ * the FEM CTAs; abd_seg (grid + 1): body boundaries of the ABD CTAs;
+ * cta_scene (grid): the solve every CTA serves (-1: none).  IPC_ERR_ARG for
+ * NULL outputs or non-positive sizes. */
+ipc_status sim_pcg_partition(const int* row, int nf, int nab, int grid, const int* node_scene, int n_scenes,
+                             int* out4, int* seg, int* abd_seg, int* cta_scene);
+
 /* Total number of CUDA kernels this library has launched in this process
  * (all simulators, all threads), for launch accounting. */
 unsigned long long sim_kernel_launches(void);

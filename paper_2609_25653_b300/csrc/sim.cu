@@ -1845,6 +1845,26 @@ ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* 
   return IPC_OK;
 }
 
+ipc_status sim_pcg_partition(const int* row, int nf, int nab, int grid, const int* node_scene, int n_scenes,
+                             int* out4, int* seg, int* abd_seg, int* cta_scene) {
+  if (!row || !out4 || !seg || !abd_seg || !cta_scene || nf < 0 || nab < 0 || grid < 2 || n_scenes < 1 ||
+      (n_scenes > 1 && !node_scene))
+    return IPC_ERR_ARG;
+  const int n_rows = nf + 4 * nab;
+  std::vector<int> r(row, row + n_rows + 1), ns;
+  if (node_scene) ns.assign(node_scene, node_scene + n_rows);
+  PcgPlan P;
+  pcg_plan_rows(r, nf, nab, grid, ns, n_scenes, P);
+  out4[0] = P.n_fem_ctas;
+  out4[1] = P.n_abd_ctas;
+  out4[2] = P.n_psc;
+  out4[3] = P.max_rows;
+  for (int c = 0; c <= P.n_fem_ctas; ++c) seg[c] = P.seg[c];
+  for (int c = 0; c <= P.n_abd_ctas; ++c) abd_seg[c] = P.abd_seg[c];
+  for (int c = 0; c < grid; ++c) cta_scene[c] = P.cta_scene[c];
+  return IPC_OK;
+}
+
 ipc_status sim_ccd_alpha(ipcsim* sim, const double* x_dev, const double* p_dev, double* alpha_host, int* n_cand_host) {
   if (!sim || !x_dev || !p_dev || !alpha_host) return IPC_ERR_ARG;
   unsigned long long one = double_bits(1.0);
