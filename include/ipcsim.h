@@ -241,14 +241,17 @@ ipc_status sim_profile_read(const ipcsim* sim, double* ms8, long long* n8, long 
  * does not describe its solver's parallel layout).  row: (nf + 4 nab + 1)
  * BSR row offsets, FEM rows first, then the 4 pseudo-node rows of every ABD
  * body; node_scene: (nf + 4 nab) scene of every row, or NULL with
- * n_scenes = 1 (one solve).  Outputs (caller-owned): out4 = [FEM CTAs, ABD
+ * n_scenes = 1 (one solve); row_extra: (nf) added cost of every FEM row, or
+ * NULL (sim_step passes 4 per contact incidence of the row, in units of
+ * stored blocks; every FEM row also costs its blocks + 2).  Outputs
+ * (caller-owned): out4 = [FEM CTAs, ABD
  * CTAs, independent solves (n_scenes when every scene got CTAs of its own,
  * else 1), most FEM rows of one CTA]; seg (grid + 1): FEM row boundaries of
  * the FEM CTAs; abd_seg (grid + 1): body boundaries of the ABD CTAs;
  * cta_scene (grid): the solve every CTA serves (-1: none).  IPC_ERR_ARG for
  * NULL outputs or non-positive sizes. */
 ipc_status sim_pcg_partition(const int* row, int nf, int nab, int grid, const int* node_scene, int n_scenes,
-                             int* out4, int* seg, int* abd_seg, int* cta_scene);
+                             const int* row_extra, int* out4, int* seg, int* abd_seg, int* cta_scene);
 
 /* Total number of CUDA kernels this library has launched in this process
  * (all simulators, all threads), for launch accounting. */

@@ -165,6 +165,10 @@ void launch_rhs(cudaStream_t, int n, const double* g, const double* gdir, double
 constexpr int PCG_ROW_GROUP = 4;  // default threads per FEM row in the PCG
 constexpr int PCG_REPLICA_COUNT = 8;
 constexpr int PCG_SCENES_MAX = 256;  // independent solves of one launch (one decision thread each)
+// planning cost of one contact incidence of a FEM row, in stored BSR blocks: the CTAs that own the rows in
+// contact set the pace of every grid barrier, so the partition spreads their incidences (measured on the
+// soft-gripper squeeze: 10.3 to 5.4 ms per mixed solve)
+constexpr int PCG_CONTACT_WEIGHT = 4;
 inline size_t pcg_partial_doubles(int grid) { return (size_t)PCG_REPLICA_COUNT * 7 * grid; }
 // co-resident CTAs of the PCG kernel for this shape (rowg: threads per FEM row, 1, 2, 4 or 8)
 int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem);
@@ -172,7 +176,7 @@ size_t pcg_smem_limit();
 // node_scene (empty: one solve) gives the scene of every row; scenes get CTAs of their own when their rows
 // are contiguous and the grid has room, else the plan is one solve
 void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, const std::vector<int>& node_scene,
-                   int n_scenes, PcgPlan& P);
+                   int n_scenes, PcgPlan& P, const std::vector<int>* row_extra = nullptr);
 // dynamic shared memory of a PCG CTA: contact sums of its rows, plus the operator rows when resident
 size_t pcg_contact_bytes(const PcgPlan& P);
 size_t pcg_resident_bytes(const PcgPlan& P, int fp32);

@@ -1556,11 +1556,13 @@ std::vector<int> share_parts(const std::vector<long long>& cost, int n_parts) {
 }  // namespace
 
 void pcg_plan_rows(const std::vector<int>& row, int nf, int nab, int grid, const std::vector<int>& node_scene,
-                   int n_scenes, PcgPlan& P) {
+                   int n_scenes, PcgPlan& P, const std::vector<int>* row_extra) {
   P.grid = grid;
-  // FEM rows balanced by stored blocks plus a per-row cost; ABD bodies by count
+  // FEM rows balanced by stored blocks plus a per-row cost (plus row_extra, the contact work of the row);
+  // ABD bodies by count
   std::vector<long long> pre(nf + 1, 0);
-  for (int i = 0; i < nf; ++i) pre[i + 1] = pre[i] + (row[i + 1] - row[i]) + 2;
+  for (int i = 0; i < nf; ++i)
+    pre[i + 1] = pre[i] + (row[i + 1] - row[i]) + 2 + (row_extra ? (long long)(*row_extra)[i] : 0);
   std::vector<long long> bpre(nab + 1);
   for (int b = 0; b <= nab; ++b) bpre[b] = b;
 

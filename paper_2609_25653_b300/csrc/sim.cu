@@ -80,6 +80,7 @@ struct ipcsim {
   bool plan_resident = false;
   size_t plan_smem = 0;
   int plan_want_grid = 0, plan_rowg = 0;
+  std::vector<int> h_inc_ptr, h_row_extra, plan_row_extra;  // contact-weighted planning (per FEM row)
   // contact incidences per owner (FEM node or ABD body)
   int *inc_ptr = nullptr, *inc_cursor = nullptr, *inc_tiles = nullptr;
   int2* inc = nullptr;
@@ -359,13 +360,27 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int rowg = sim->tune_rowg;
   const int want = std::min(std::max(1, sms * std::max(1, sim->tune_bps)), sim->pcg_grid_max);
-  if (!(sim->plan.grid > 0 && sim->plan_want_grid == want && sim->plan_fp32 == fp32 && sim->plan_rowg == rowg)) {
+  // contact work of every FEM row from the current incidence lists: the partition is redone when it changes
+  const int contact_w = PCG_CONTACT_WEIGHT;
+  bool extra_changed = false;
+  if (contact_w > 0 && sim->nf > 0) {
+    sim->h_inc_ptr.resize(sim->nf + 1);
+    CUDA_TRY(cudaMemcpyAsync(sim->h_inc_ptr.data(), sim->inc_ptr, sizeof(int) * (sim->nf + 1), cudaMemcpyDeviceToHost,
+                             sim->st));
+    CUDA_TRY(cudaStreamSynchronize(sim->st));
+    sim->h_row_extra.resize(sim->nf);
+    for (int i = 0; i < sim->nf; ++i) sim->h_row_extra[i] = contact_w * (sim->h_inc_ptr[i + 1] - sim->h_inc_ptr[i]);
+    extra_changed = sim->h_row_extra != sim->plan_row_extra;
+  }
+  if (extra_changed ||
+      !(sim->plan.grid > 0 && sim->plan_want_grid == want && sim->plan_fp32 == fp32 && sim->plan_rowg == rowg)) {
     int grid = want;
     bool resident = false;
     size_t smem = 0;
     for (int attempt = 0; attempt < 4; ++attempt) {
       if (sim->nab > 0 && grid < 2) { sim->err = "PCG needs two co-resident CTAs"; return IPC_ERR_CUDA; }
-      pcg_plan_rows(sim->h_row, sim->nf, sim->nab, grid, sim->h_node_scene, sim->n_scenes, sim->plan);
+      pcg_plan_rows(sim->h_row, sim->nf, sim->nab, grid, sim->h_node_scene, sim->n_scenes, sim->plan,
+                    contact_w > 0 ? &sim->h_row_extra : nullptr);
       const size_t bytes = pcg_resident_bytes(sim->plan, fp32);
       const int cap_res = bytes <= pcg_smem_limit() ? pcg_max_blocks(PCG_THREADS, fp32, rowg, bytes) : 0;
       if (cap_res >= grid) { resident = true; smem = bytes; break; }
@@ -392,6 +407,7 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
     }
     CUDA_TRY(cudaMemcpyAsync(sim->d_seg, buf.data(), sizeof(int) * n, cudaMemcpyHostToDevice, sim->st));
     sim->plan_want_grid = want;
+    sim->plan_row_extra = sim->h_row_extra;
     sim->plan_fp32 = fp32;
     sim->plan_rowg = rowg;
     sim->plan_resident = resident;
@@ -1846,15 +1862,17 @@ ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* 
 }
 
 ipc_status sim_pcg_partition(const int* row, int nf, int nab, int grid, const int* node_scene, int n_scenes,
-                             int* out4, int* seg, int* abd_seg, int* cta_scene) {
+                             const int* row_extra, int* out4, int* seg, int* abd_seg, int* cta_scene) {
   if (!row || !out4 || !seg || !abd_seg || !cta_scene || nf < 0 || nab < 0 || grid < 2 || n_scenes < 1 ||
       (n_scenes > 1 && !node_scene))
     return IPC_ERR_ARG;
   const int n_rows = nf + 4 * nab;
   std::vector<int> r(row, row + n_rows + 1), ns;
   if (node_scene) ns.assign(node_scene, node_scene + n_rows);
+  std::vector<int> extra;
+  if (row_extra) extra.assign(row_extra, row_extra + nf);
   PcgPlan P;
-  pcg_plan_rows(r, nf, nab, grid, ns, n_scenes, P);
+  pcg_plan_rows(r, nf, nab, grid, ns, n_scenes, P, row_extra ? &extra : nullptr);
   out4[0] = P.n_fem_ctas;
   out4[1] = P.n_abd_ctas;
   out4[2] = P.n_psc;

@@ -84,7 +84,7 @@ SIGNATURES = {
     "sim_step_many": ([C.POINTER(vp), C.c_int, C.POINTER(dp), C.POINTER(StepStats), ip], C.c_int),
     "sim_adjoint": ([vp, vp, vp, vp, dp, dp, vp, vp, vp, vp, vp, dp], C.c_int),
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
-    "sim_pcg_partition": ([ip, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip, ip, ip, ip], C.c_int),
+    "sim_pcg_partition": ([ip, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip, ip, ip, ip, ip], C.c_int),
 }
 
 PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "pcg_setup"]
@@ -110,17 +110,19 @@ def kernel_launches() -> int:
     return int(load().sim_kernel_launches())
 
 
-def pcg_partition(row, nf: int, nab: int, grid: int, node_scene=None, n_scenes: int = 1) -> dict:
+def pcg_partition(row, nf: int, nab: int, grid: int, node_scene=None, n_scenes: int = 1, row_extra=None) -> dict:
     """The PCG's partition of the rows among `grid` CTAs (sim_pcg_partition; host only, no GPU)."""
     row = np.ascontiguousarray(row, dtype=np.int32)
     ns = None if node_scene is None else np.ascontiguousarray(node_scene, dtype=np.int32)
+    ex = None if row_extra is None else np.ascontiguousarray(row_extra, dtype=np.int32)
     out4 = np.zeros(4, np.int32)
     seg = np.zeros(grid + 1, np.int32)
     abd_seg = np.zeros(grid + 1, np.int32)
     cta_scene = np.zeros(grid, np.int32)
     as_ip = lambda a: a.ctypes.data_as(ip)
     st = load().sim_pcg_partition(as_ip(row), nf, nab, grid, None if ns is None else as_ip(ns), n_scenes,
-                                  as_ip(out4), as_ip(seg), as_ip(abd_seg), as_ip(cta_scene))
+                                  None if ex is None else as_ip(ex), as_ip(out4), as_ip(seg), as_ip(abd_seg),
+                                  as_ip(cta_scene))
     if st != 0:
         raise ValueError(f"sim_pcg_partition failed ({st})")
     n_fem, n_abd = int(out4[0]), int(out4[1])

@@ -86,6 +86,24 @@ def test_too_few_ctas_or_unordered_rows_fall_back_to_one_solve():
     assert P["n_solves"] == 1
 
 
+def test_contact_work_moves_rows_off_the_contact_ctas():
+    """Rows with contact incidences cost more: the CTAs that own them get fewer rows, and the largest
+    weighted cost of a CTA stays within one row of its share."""
+    rng = np.random.default_rng(3)
+    row, nf, nab, _ = _system(rng, [10000], [1])
+    extra = np.zeros(nf, np.int32)
+    extra[4000:4600] = 4 * rng.integers(1, 40, size=600)  # a contact patch
+    plain = ipcsim.pcg_partition(row, nf, nab, 296)
+    P = ipcsim.pcg_partition(row, nf, nab, 296, row_extra=extra)
+    _check(P, row, nf, nab, 296, None, 1)
+    pre = np.concatenate([[0], np.cumsum(np.diff(row[:nf + 1]) + 2 + extra)])
+    def worst(seg):
+        return int(np.max(pre[seg[1:]] - pre[seg[:-1]]))
+    assert worst(P["seg"]) < worst(plain["seg"]) / 3
+    per_row_max = int(np.max(np.diff(row[:nf + 1]) + 2 + extra))
+    assert worst(P["seg"]) <= pre[-1] / P["n_fem_ctas"] + per_row_max
+
+
 def test_partition_rejects_bad_arguments():
     row = np.arange(0, 11, dtype=np.int32)
     with pytest.raises(ValueError):
