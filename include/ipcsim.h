@@ -242,8 +242,8 @@ ipc_status sim_profile_read(const ipcsim* sim, double* ms8, long long* n8, long 
  * BSR row offsets, FEM rows first, then the 4 pseudo-node rows of every ABD
  * body; node_scene: (nf + 4 nab) scene of every row, or NULL with
  * n_scenes = 1 (one solve); row_extra: (nf) added cost of every FEM row, or
- * NULL (sim_step passes 4 per contact incidence of the row, in units of
- * stored blocks; every FEM row also costs its blocks + 2).  Outputs
+ * NULL (every FEM row costs its stored blocks + 2, plus this; sim_step
+ * passes none in this version).  Outputs
  * (caller-owned): out4 = [FEM CTAs, ABD
  * CTAs, independent solves (n_scenes when every scene got CTAs of its own,
  * else 1), most FEM rows of one CTA]; seg (grid + 1): FEM row boundaries of
