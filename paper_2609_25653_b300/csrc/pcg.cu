@@ -523,19 +523,6 @@ __device__ inline void load_partials(const T* rep, int nblk, Partials<T>& P) {
     P.v[2][j] = in ? rep[2 * nblk + b] : T(0);
   }
 }
-template <typename T>
-__device__ inline void totals3(const T* rep, int nblk, const Partials<T>& P, Shared& sh, double& t0, double& t1,
-                               double& t2) {
-  T v[3] = {P.v[0][0] + P.v[0][1], P.v[1][0] + P.v[1][1], P.v[2][0] + P.v[2][1]};
-  for (int b = threadIdx.x + 2 * blockDim.x; b < nblk; b += blockDim.x) {
-    v[0] += rep[b];
-    v[1] += rep[nblk + b];
-    v[2] += rep[2 * nblk + b];
-  }
-  cta_sum<3, T>(v, sh);
-  t0 = sh.out[0]; t1 = sh.out[1]; t2 = sh.out[2];
-  __syncthreads();
-}
 
 // This CTA's 3 partial sums, written to every replica.
 template <typename T>
@@ -626,15 +613,6 @@ __device__ inline void report_solve(const PcgArgs& a, Shared& sh, bool decider, 
     a.out[2] = (int)sh.agg[2];
     a.res[0] = __longlong_as_double((long long)sh.agg[3]);
   }
-}
-
-__device__ inline double total_fp64(const double* rep /* [grid] */, int nblk, Shared& sh) {
-  double v[1] = {0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v[0] += rep[b];
-  cta_sum<1, double>(v, sh);
-  double t = sh.out[0];
-  __syncthreads();
-  return t;
 }
 
 // ---------------------------------------------------------------------------
