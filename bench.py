@@ -150,6 +150,22 @@ def pcg_bytes(work, sim, fp32, resident, launches):
             + work["pcg_pair_iters"] * (144 * e + 32) + work["pcg_fric_iters"] * (9 * e + 48))
 
 
+def slowest_rank(local, device="cuda"):
+    """The largest of every rank's value (a timed total), after which all ranks hold it; with one rank, or
+    without an initialised process group, the local value."""
+    try:
+        import torch.distributed as dist
+        if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+            return float(local)
+    except ImportError:
+        return float(local)
+    import torch
+    t = torch.tensor([float(local)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -212,12 +228,7 @@ def run_ours(args):
     launches = ipcsim.kernel_launches() - launches0
     prof, work = sim.profile_read()
     sim.profile(False)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(t.item())
+    total_ms = slowest_rank(sum(times))
     value = world * args.steps * n_sc / (total_ms / 1e3)
 
     # e2e through the public API with host buffers (transforms in, positions out), over the same steps
@@ -269,10 +280,7 @@ def run_ours(args):
             adj_ms.append(a0.elapsed_time(a1))
         adjoint = {"ms_per_step": round(sum(adj_ms) / len(adj_ms), 3), "steps": len(adj_ms),
                    "solve": "FP64 PCG on the unprojected Hessian, rtol 1e-12"}
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = slowest_rank(e2e_s)
     e2e_value = world * args.steps * n_sc / e2e_s
 
     # roofline of the dominant stage
