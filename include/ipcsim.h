@@ -142,12 +142,18 @@ ipc_status sim_create(const ipc_scene_desc* desc, const ipc_params* params, void
  * and stitch springs in scene order, ids shifted accordingly); pairs between
  * different scenes are never formed; every scene keeps its own barrier and
  * stitch stiffness (auto-scaled from its own material and mesh).  One
- * sim_step then advances all scenes with one Newton loop (a common step
- * length and a common convergence test, with the smallest scene bounding box
- * as L_bbox) whose PCG solves their block-diagonal system in one cooperative
- * launch.  sim_step takes the kinematic transforms of all scenes
- * concatenated; sim_get_state / sim_set_state use the concatenated layout.
- * Gravity is taken from the first scene. */
+ * sim_step then advances all scenes with one shared Newton loop in which
+ * every scene keeps its own control: its own convergence test (with the
+ * smallest scene bounding box as L_bbox), CCD step bound and backtracking
+ * line search, so each advances as it would alone; a converged scene stops
+ * moving while the others continue.  The linear systems are solved in one
+ * cooperative launch holding one independent PCG solve per scene (its own
+ * scalars, tolerance and stop; converged scenes are left out) when every
+ * scene's rows are contiguous, there are at most 256 scenes and the launch
+ * has room for CTAs of every scene; otherwise one solve covers the whole
+ * block-diagonal system.  sim_step takes the kinematic transforms of all
+ * scenes concatenated; sim_get_state / sim_set_state use the concatenated
+ * layout.  Gravity is taken from the first scene. */
 ipc_status sim_create_batch(const ipc_scene_desc* descs, int n, const ipc_params* params, void* stream, ipcsim** out);
 
 /* Advance one time step (Eq. 3).  kin_T_next_host: (n_kin, 12) transforms of
