@@ -112,6 +112,8 @@ typedef struct {
   int precision;      /* IPC_PREC_FP64 or IPC_PREC_MIXED */
   int pair_capacity;  /* initial contact-pair capacity; <= 0: automatic (grows on demand) */
   int broad_phase;    /* IPC_BROAD_LBVH (default) or IPC_BROAD_ALL_PAIRS (every pair tested; for checks) */
+  int pair_capacity_max; /* largest contact-pair buffer (pairs) the simulator grows to; a step that needs
+                            more fails with IPC_ERR_CAPACITY; <= 0: 2^23 */
 } ipc_params;
 
 enum { IPC_BROAD_LBVH = 0, IPC_BROAD_ALL_PAIRS = 1 };
@@ -129,6 +131,10 @@ typedef struct {
   double min_dist;        /* smallest primitive distance over the accepted iterates (m) */
   double energy_end;      /* incremental potential at the solution */
   double pnorm_end;       /* max|p| / (dt L) of the last Newton direction */
+  int pcg_unconverged;    /* PCG solves that stopped at max_pcg (or stagnated) above pcg_rtol: the
+                             Newton direction of those iterations is inexact (the step still ends
+                             only when the Newton test holds) */
+  int pad_;
 } ipc_step_stats;
 
 /* Build a simulator.  Validates the scene (IPC_ERR_INVERTED for a rest tet
@@ -230,6 +236,15 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t_dev, const double* zd_t_de
  * log2(rowg). */
 ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out4, float* ms8);
 
+/* Where the cooperative PCG keeps its operator (the solver of the Newton
+ * step; the paper does not describe its solver's layout).  streamed == 0
+ * (default): each CTA copies its rows of the BSR operator and of the
+ * block-Jacobi preconditioner into shared memory once per solve when every
+ * CTA's rows fit, else they are read from global memory in every iteration;
+ * streamed != 0: always read from global memory.  Both give the same
+ * arithmetic in the same order.  Takes effect at the next solve. */
+ipc_status sim_pcg_residency(ipcsim* sim, int streamed);
+
 /* Per-stage timing with CUDA events recorded on the simulator's stream
  * around each stage of sim_step (cheap; intervals are read at the
  * synchronisation points sim_step already has).  enable != 0 starts (and
@@ -315,7 +330,10 @@ ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* 
  * process exits; scenes needing more (more than about 87 000 nodes) are
  * rejected with IPC_ERR_ARG and a message naming the size.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * with that device current.  With CUDA's lazy module loading (the default)
+ * that first call may also load this library's device code onto the device,
+ * and with it the 8 MiB array: make the first call early, before the device
+ * memory is handed to another allocator and before any stream capture.
  * All calls share the array and it keeps the previous call's contents (the
  * call clears what it accumulates into): calls that overlap on the GPU, from
  * any simulator, race.  No cudaMalloc, cudaFree or allocating library

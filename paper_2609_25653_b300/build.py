@@ -10,6 +10,7 @@ import hashlib
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -52,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if f.read() == stamp:
                 return LIB
     nvcc = _nvcc()
-    objs = []
+    objs, cmds = [], []
     for src in SOURCES:
         obj = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *COMMON, *PER_FILE_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
@@ -60,8 +61,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             cmd.insert(1, "-Xptxas=-v")
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
-        subprocess.run(cmd, check=True)
+        cmds.append(cmd)
         objs.append(obj)
+    # the translation units are independent: compile them concurrently
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        for r in list(ex.map(lambda c: subprocess.run(c), cmds)):
+            if r.returncode != 0:
+                raise subprocess.CalledProcessError(r.returncode, r.args)
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run([nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"], check=True)
     os.replace(tmp, LIB)

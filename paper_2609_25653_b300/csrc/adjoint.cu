@@ -113,7 +113,7 @@ void launch_friction_apply(cudaStream_t st, const DevScene& S, int n, const int*
   if (n > 0) { k_friction_apply<<<nb(n, 128), 128, 0, st>>>(S, n, f_ids, f_w, f_Hu, lam, y); count_launch(); }
 }
 void launch_dot(cudaStream_t st, int n, const double* a, const double* b, double* out) {
-  if (n > 0) { k_dot<<<std::min(nb(n, 256), 148 * 4), 256, 0, st>>>(n, a, b, out); count_launch(); }
+  if (n > 0) { k_dot<<<stride_grid(n, 256, 4), 256, 0, st>>>(n, a, b, out); count_launch(); }
 }
 void launch_axpy(cudaStream_t st, int n, const double* x, double alpha, const double* y, double* out) {
   if (n > 0) { k_axpy<<<nb(n, 256), 256, 0, st>>>(n, x, alpha, y, out); count_launch(); }

@@ -8,7 +8,7 @@ namespace ipc {
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
-constexpr int BOUND_BLOCKS = 148 * 2;
+constexpr int BOUND_BLOCKS = 512;  // fan-in of the scene-bound reduction
 
 // ---------------------------------------------------------------------------
 // leaf boxes

@@ -22,7 +22,7 @@ struct Bvh {
   double* leafbox = nullptr; // (cap, 6) primitive boxes in primitive order
   int* hist = nullptr;       // radix histograms
   int hist_cap = 0;
-  double* bounds = nullptr;  // (2 * 148 * 8, 6) partial scene bounds
+  double* bounds = nullptr;  // (partial blocks + 1, 6) partial scene bounds
 };
 
 __device__ inline bool box_overlap(const double* a, const double* b) {

@@ -598,7 +598,7 @@ void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* 
                     double* Dc, const double* pD, double* gdir, double* E, unsigned long long* min_s, int hess_fp32) {
   if (mode >= 2) {
     // one warp per pair: as many warps as the thread-per-pair launch had threads / 32, at least one block
-    int wgrid = std::max(1, std::min((cap + BWARPS - 1) / BWARPS, 148 * 16));
+    int wgrid = stride_grid(cap, BWARPS, 16);
     k_barrier_warp<<<wgrid, 32 * BWARPS, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, project, g, pairH, Dc, pD,
                                                    gdir, E, min_s, hess_fp32);
   } else {

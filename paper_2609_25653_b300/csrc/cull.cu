@@ -562,7 +562,7 @@ void launch_sweep_bvh(cudaStream_t st, const DevScene& S, const double* xv, cons
   if (S.nsv) { k_sweep_pt_bvh<<<(S.nsv + 127) / 128, 128, 0, st>>>(S, xv, pv, view(tri), cand, n_cand, ccap, err); count_launch(); }
   if (S.nedge) { k_sweep_ee_bvh<<<(S.nedge + 127) / 128, 128, 0, st>>>(S, xv, pv, view(edge), cand, n_cand, ccap, err); count_launch(); }
   if (ccap > 0) {
-    const int grid = std::max(1, std::min((ccap + 127) / 128, 148 * 16));
+    const int grid = stride_grid(ccap, 128, 16);
     k_ccd_cand<<<grid, 128, 0, st>>>(S, xv, pv, s_frac, max_iter, cand, n_cand, ccap, alpha_bits, n_ccd);
     count_launch();
   }

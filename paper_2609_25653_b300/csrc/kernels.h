@@ -7,6 +7,15 @@
 
 namespace ipc {
 
+// Streaming multiprocessors of the current device (looked up once per device).
+int device_sms();
+// Blocks of a grid-stride launch over n items, `per_block` items per block and
+// at most `per_sm` resident blocks per SM of the current device (at least 1).
+inline int stride_grid(long long n, int per_block, int per_sm) {
+  const long long want = (n + per_block - 1) / per_block, cap = (long long)device_sms() * per_sm;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
 // Kernel launches issued by this library (all simulators, all threads).
 extern unsigned long long g_kernel_launches;
 inline void count_launch(int n = 1) { __atomic_fetch_add(&g_kernel_launches, (unsigned long long)n, __ATOMIC_RELAXED); }

@@ -86,9 +86,8 @@ extern "C" ipc_status sim_eval_barrier_noalloc(ipcsim* sim, const double* x_dev,
     *err = std::string("sim_eval_barrier_noalloc: ") + cudaGetErrorString(ce);
     return IPC_ERR_CUDA;
   }
-  int grid = n > 0 ? (n + 127) / 128 : 1;
-  if (grid > 148 * 8) grid = 148 * 8;
-  ipc::launch_barrier(st, grid, *S, x_dev, rec_dev, n_dev, n, sh, kappa, 1.0, 2, project, grad_dev, H_dev, Dc, pD, gdir,
+  // mode 2 (gradient and Hessian) launches one warp per pair and sizes that grid itself
+  ipc::launch_barrier(st, 1, *S, x_dev, rec_dev, n_dev, n, sh, kappa, 1.0, 2, project, grad_dev, H_dev, Dc, pD, gdir,
                       E_dev, nullptr);
   ce = cudaStreamSynchronize(st);
   if (ce == cudaSuccess) ce = cudaGetLastError();

@@ -20,7 +20,9 @@
 // control decisions without contending for one cache line.
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 #include <vector>
 #include "common.cuh"
 #include "kernels.h"
@@ -176,7 +178,7 @@ void launch_incidence(cudaStream_t st, const DevScene& S, const int* rec, const 
   const int n_own = S.nf + S.nab;
   const int n = n_own + 1;
   cudaMemsetAsync(inc_ptr, 0, sizeof(int) * n, st);
-  int grid = std::max(1, std::min((4 * (cap + n_fric) + 255) / 256, 148 * 8));
+  int grid = stride_grid(4LL * (cap + n_fric), 256, 8);
   k_incidence<false><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, inc_ptr, nullptr, 0, desc, err);
   int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   k_scan_tiles<<<ntiles, 1024, 0, st>>>(n, inc_ptr, tiles);
@@ -342,7 +344,7 @@ void launch_abd_contact(cudaStream_t st, const DevScene& S, const int* rec, cons
   // the diagonal contact blocks of the pseudo-nodes go into the BSR grid with the rest of the same-body part
   cudaMemsetAsync(Dc + 9 * (size_t)S.nf, 0, sizeof(double) * 36 * (size_t)S.nab, st);
   cudaMemsetAsync(abd_ptr, 0, sizeof(int) * (S.nab + 1), st);
-  int grid = std::max(1, std::min((cap + n_fric + 127) / 128, 148 * 8));
+  int grid = stride_grid((long long)cap + n_fric, 128, 8);
   k_abd_contact<false><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, abd_ptr,
                                              nullptr, nullptr, 0, nullptr, err);
   k_scan_totals<<<1, 1024, 0, st>>>(S.nab + 1, abd_ptr);
@@ -1457,14 +1459,18 @@ static void* pcg32_kernel(int rowg) {
 // fp32: the mixed-precision refinement solver; otherwise the FP64 pipelined solver
 static void* pcg_fn(int fp32, int rowg) { return fp32 ? pcg32_kernel(rowg) : pcg_kernel<double>(rowg); }
 
-int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem) {
-  int dev, sms, per_sm = 0;
+int device_sms() {
+  static std::mutex m;
+  static std::vector<std::pair<int, int>> known;
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  void* f = pcg_fn(fp32, rowg);
-  if (dyn_smem) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, dyn_smem);
-  return sms * per_sm;
+  std::lock_guard<std::mutex> lock(m);
+  for (const auto& k : known)
+    if (k.first == dev) return k.second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 1;
+  known.push_back({dev, sms});
+  return sms;
 }
 
 size_t pcg_smem_limit() {
@@ -1474,20 +1480,50 @@ size_t pcg_smem_limit() {
   return (size_t)optin;
 }
 
+// The dynamic shared-memory limit of a kernel is one process-wide setting per
+// device.  Every PCG variant has it raised to the most the device allows next
+// to the kernel's static shared memory, once, at its first use, and never
+// lowered, so that simulators planning and launching on several host threads
+// cannot change it under each other's launches.  Returns that limit (0 on
+// failure).
+static size_t ensure_smem_attr(void* f) {
+  static std::mutex m;
+  struct Entry { int dev; void* f; size_t limit; };
+  static std::vector<Entry> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(m);
+  for (const auto& d : done)
+    if (d.dev == dev && d.f == f) return d.limit;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return 0;
+  const size_t optin = pcg_smem_limit();
+  const size_t limit = optin > fa.sharedSizeBytes ? optin - fa.sharedSizeBytes : 0;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) != cudaSuccess) return 0;
+  done.push_back({dev, f, limit});
+  return limit;
+}
+
+int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem) {
+  int per_sm = 0;
+  const int sms = device_sms();
+  void* f = pcg_fn(fp32, rowg);
+  if (dyn_smem > ensure_smem_attr(f)) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, dyn_smem) != cudaSuccess) return 0;
+  return sms * per_sm;
+}
+
 cudaError_t launch_pcg(cudaStream_t st, int grid, int threads, const PcgArgs& a, int rowg, size_t dyn_smem) {
   void* args[] = {(void*)&a};
   count_launch();
   void* f = pcg_fn(a.fp32, rowg);
-  if (dyn_smem) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-    if (e != cudaSuccess) return e;
-  }
+  if (dyn_smem > ensure_smem_attr(f)) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, dyn_smem, st);
 }
 
 void launch_to_float(cudaStream_t st, size_t n, const double* src, float* dst, const int* n_dev, int stride) {
   if (!n) return;
-  int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+  int grid = stride_grid((long long)n, 256, 16);
   k_to_float<<<grid, 256, 0, st>>>(n, src, dst, n_dev, stride);
   count_launch();
 }

@@ -80,6 +80,8 @@ struct ipcsim {
   bool plan_resident = false;
   size_t plan_smem = 0;
   int plan_want_grid = 0, plan_rowg = 0;
+  bool pcg_streamed = false;   // never keep the operator in shared memory (sim_pcg_residency)
+  bool plan_streamed = false;
   std::vector<int> h_inc_ptr, h_row_extra, plan_row_extra;  // contact-weighted planning (per FEM row)
   // contact incidences per owner (FEM node or ABD body)
   int *inc_ptr = nullptr, *inc_cursor = nullptr, *inc_tiles = nullptr;
@@ -244,6 +246,10 @@ ipc_status grow_inc(ipcsim* sim) {
 // pair blocks of 1152 B): beyond them a step fails with IPC_ERR_CAPACITY.
 constexpr long long MAX_PAIRS = 1LL << 23;
 constexpr long long MAX_CANDIDATES = 1LL << 26;
+// the pair buffer limit of this simulator: pair_capacity_max when set, else MAX_PAIRS
+long long max_pairs(const ipcsim* sim) {
+  return sim->P.pair_capacity_max > 0 ? std::min<long long>(sim->P.pair_capacity_max, MAX_PAIRS) : MAX_PAIRS;
+}
 
 // ABD coupling blocks: a few per pair touching an ABD body; grown when a Newton iteration overflows them
 ipc_status grow_abd_list(ipcsim* sim, long long need) {
@@ -263,11 +269,12 @@ ipc_status grow_abd_list(ipcsim* sim, long long need) {
 }
 
 ipc_status grow_pairs(ipcsim* sim, int need) {
-  if (need < 0 || need > MAX_PAIRS) {
-    sim->err = "active-pair count " + std::to_string(need) + " exceeds the pair buffer limit";
+  const long long lim = max_pairs(sim);
+  if (need < 0 || need > lim) {
+    sim->err = "active-pair count " + std::to_string(need) + " exceeds the pair buffer limit " + std::to_string(lim);
     return IPC_ERR_CAPACITY;
   }
-  int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 1024), MAX_PAIRS);
+  int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 1024), lim);
   dfree(sim, sim->rec);
   dfree(sim, sim->rec_s);
   dfree(sim, sim->pairH);
@@ -301,11 +308,12 @@ ipc_status grow_cand(ipcsim* sim, int need) {
 }
 
 ipc_status grow_fric(ipcsim* sim, int need) {
-  if (need < 0 || need > MAX_PAIRS) {
-    sim->err = "friction-pair count " + std::to_string(need) + " exceeds the pair buffer limit";
+  const long long lim = max_pairs(sim);
+  if (need < 0 || need > lim) {
+    sim->err = "friction-pair count " + std::to_string(need) + " exceeds the pair buffer limit " + std::to_string(lim);
     return IPC_ERR_CAPACITY;
   }
-  int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 1024), MAX_PAIRS);
+  int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 1024), lim);
   dfree(sim, sim->f_ids); dfree(sim, sim->f_w); dfree(sim, sim->f_n); dfree(sim, sim->f_lam); dfree(sim, sim->f_Hu);
   ipc_status s;
   if ((s = dalloc(sim, &sim->f_ids, (size_t)4 * ncap))) return s;
@@ -355,9 +363,7 @@ inline void prof_collect(ipcsim* sim) {
 // Row partition, shared-memory residency and operator layout of the PCG for
 // the current launch shape (tune_rowg threads per FEM row, tune_bps CTAs per SM).
 ipc_status pcg_prepare(ipcsim* sim, int fp32) {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = device_sms();
   const int rowg = sim->tune_rowg;
   const int want = std::min(std::max(1, sms * std::max(1, sim->tune_bps)), sim->pcg_grid_max);
   // contact work of every FEM row from the current incidence lists: the partition is redone when it changes
@@ -373,22 +379,29 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
     extra_changed = sim->h_row_extra != sim->plan_row_extra;
   }
   if (extra_changed ||
-      !(sim->plan.grid > 0 && sim->plan_want_grid == want && sim->plan_fp32 == fp32 && sim->plan_rowg == rowg)) {
+      !(sim->plan.grid > 0 && sim->plan_want_grid == want && sim->plan_fp32 == fp32 && sim->plan_rowg == rowg &&
+        sim->plan_streamed == sim->pcg_streamed)) {
+    // shrink the grid until every CTA of the plan is co-resident, re-planning the rows for every grid
+    // size (fewer CTAs own more rows each, which can need more shared memory)
     int grid = want;
-    bool resident = false;
+    bool resident = false, fits = false;
     size_t smem = 0;
-    for (int attempt = 0; attempt < 4; ++attempt) {
-      if (sim->nab > 0 && grid < 2) { sim->err = "PCG needs two co-resident CTAs"; return IPC_ERR_CUDA; }
+    for (int attempt = 0; attempt < 32 && !fits; ++attempt) {
+      if (grid < 1 || (sim->nab > 0 && grid < 2)) break;
       pcg_plan_rows(sim->h_row, sim->nf, sim->nab, grid, sim->h_node_scene, sim->n_scenes, sim->plan,
                     contact_w > 0 ? &sim->h_row_extra : nullptr);
       const size_t bytes = pcg_resident_bytes(sim->plan, fp32);
-      const int cap_res = bytes <= pcg_smem_limit() ? pcg_max_blocks(PCG_THREADS, fp32, rowg, bytes) : 0;
-      if (cap_res >= grid) { resident = true; smem = bytes; break; }
+      const int cap_res = (!sim->pcg_streamed && bytes <= pcg_smem_limit()) ? pcg_max_blocks(PCG_THREADS, fp32, rowg, bytes) : 0;
+      if (cap_res >= grid) { resident = true; smem = bytes; fits = true; break; }
       smem = pcg_contact_bytes(sim->plan);
       const int cap = smem <= pcg_smem_limit() ? pcg_max_blocks(PCG_THREADS, fp32, rowg, smem) : 0;
       if (cap <= 0) { sim->err = "PCG kernel cannot be made resident"; return IPC_ERR_CUDA; }
-      if (cap >= grid) break;
+      if (cap >= grid) { fits = true; break; }
       grid = cap;
+    }
+    if (!fits) {
+      sim->err = "no PCG launch shape with every CTA co-resident (grid " + std::to_string(grid) + ")";
+      return IPC_ERR_CUDA;
     }
     // one device buffer: seg | abd_seg | cta_scene | sc_ptr | sc_cta
     const PcgPlan& pl = sim->plan;
@@ -410,6 +423,7 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
     sim->plan_row_extra = sim->h_row_extra;
     sim->plan_fp32 = fp32;
     sim->plan_rowg = rowg;
+    sim->plan_streamed = sim->pcg_streamed;
     sim->plan_resident = resident;
     sim->plan_smem = smem;
   }
@@ -515,7 +529,7 @@ void build_incidence(ipcsim* sim, int n_fric) {
                    &sim->sc_dev->flags);
 }
 
-int pair_grid(int cap) { return std::max(1, std::min((cap + 127) / 128, 148 * 8)); }
+int pair_grid(int cap) { return stride_grid(cap, 128, 8); }
 
 unsigned long long double_bits(double d);
 double bits_to_double(unsigned long long b);
@@ -535,7 +549,7 @@ void cull(ipcsim* sim, const double* xv) { cull_into(sim, xv, sim->rec, sim->rec
 void active_set(ipcsim* sim, const double* xv) {
   if (sim->cand_valid) {
     cudaMemsetAsync(&sim->sc_dev->n_pairs, 0, sizeof(int), sim->st);
-    launch_filter_active(sim->st, std::max(1, std::min((sim->ccap + 127) / 128, 148 * 8)), sim->S, xv, sim->sh,
+    launch_filter_active(sim->st, stride_grid(sim->ccap, 128, 8), sim->S, xv, sim->sh,
                          sim->cand, &sim->sc_dev->n_cand, sim->ccap, sim->rec, sim->rec_s, &sim->sc_dev->n_pairs,
                          sim->cap);
   } else {
@@ -1088,12 +1102,7 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   if ((s = dalloc(sim, &sim->Dinv, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->T_dev, 12 * (size_t)std::max(nkb, 1)))) return fail(s, "");
   if (P.precision != IPC_PREC_FP64 && P.precision != IPC_PREC_MIXED) return fail(IPC_ERR_ARG, "unknown precision");
-  {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    sim->pcg_grid_max = 4 * sms;  // sizes the partial-sum buffer: up to four CTAs per SM
-  }
+  sim->pcg_grid_max = 4 * device_sms();  // sizes the partial-sum buffer: up to four CTAs per SM
   if ((s = dalloc(sim, &sim->pcg_op, 9 * (size_t)nnzb))) return fail(s, "");
   if ((s = dalloc(sim, &sim->pcg_vec, 9 * (size_t)ndof))) return fail(s, "");
   if ((s = dalloc(sim, &sim->inc_ptr, (size_t)nf + nab + 1))) return fail(s, "");
@@ -1111,9 +1120,10 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   if (cudaMallocHost((void**)&sim->sc_host, sizeof(ipcsim::Scal)) != cudaSuccess) return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
   std::memset(sim->sc_host, 0, sizeof(ipcsim::Scal));
   int cap0 = P.pair_capacity > 0 ? P.pair_capacity : std::max(1024, 2 * (S.nsv + S.nedge));
-  if ((s = grow_pairs(sim, cap0 * 2 / 3 + 1))) return fail(s, "");
+  const int pairs0 = (int)std::min<long long>(cap0 * 2 / 3 + 1, max_pairs(sim));
+  if ((s = grow_pairs(sim, pairs0))) return fail(s, "");
   if ((s = grow_cand(sim, 4 * cap0))) return fail(s, "");
-  if ((s = grow_fric(sim, cap0 * 2 / 3 + 1))) return fail(s, "");
+  if ((s = grow_fric(sim, pairs0))) return fail(s, "");
   if (cudaMemcpyAsync(sim->T_dev, sim->h_Tcur.data(), sizeof(double) * 12 * nkb, cudaMemcpyHostToDevice, sim->st) != cudaSuccess && nkb)
     return fail(IPC_ERR_CUDA, "upload of transforms failed");
   // broad phase: leaf boxes widened by slightly more than dhat, so that every
@@ -1266,20 +1276,23 @@ ipc_status sim_surface(const ipcsim* sim, int* sv, int* tris, int* edges) {
   return IPC_OK;
 }
 
-ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats) {
-  if (!sim) return IPC_ERR_ARG;
-  if (sim->nkb && !kin_T_next) { sim->err = "kinematic transforms required"; return IPC_ERR_ARG; }
+}  // extern "C"
+
+namespace {
+
+// The body of sim_step.  Every return after the start of the step leaves the
+// state to the caller (sim_step), which puts it back to x_t on any error:
+// `started` is set once z_t and xk_t hold the state at the start of the step.
+ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, bool& started) {
   const DevScene& S = sim->S;
   const ipc_params& P = sim->P;
   const int ndof = 3 * sim->n_nodes, nk3 = 3 * sim->nk;
   const double dt = P.dt, dt2 = dt * dt;
-  ipc_step_stats st{};
-  st.alpha_min = 1.0;
-  st.min_dist = 1e300;
   cudaStream_t cs = sim->st;
   if (sim->nkb) CUDA_TRY(cudaMemcpyAsync(sim->T_dev, kin_T_next, sizeof(double) * 12 * sim->nkb, cudaMemcpyHostToDevice, cs));
   launch_predict(cs, S, sim->z, sim->zd, dt, sim->grav, sim->z_t, sim->z_tilde);
   if (nk3) CUDA_TRY(cudaMemcpyAsync(sim->xk_t, sim->xk, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, cs));
+  started = true;
   launch_kin_targets(cs, S, sim->T_dev, sim->xk_hat, sim->stitch_hat);
   launch_vertex_positions(cs, S, sim->z, sim->xk, sim->xv);
   CUDA_TRY(cudaMemcpyAsync(sim->xv_t, sim->xv, sizeof(double) * 3 * sim->nv, cudaMemcpyDeviceToDevice, cs));
@@ -1311,18 +1324,8 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   bool converged = false;
   int it = 0;
   std::vector<char> scene_done;  // batches: scenes whose Newton iteration has converged
-  auto restore = [&]() {
-    cudaMemcpyAsync(sim->z, sim->z_t, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, cs);
-    if (nk3) cudaMemcpyAsync(sim->xk, sim->xk_t, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, cs);
-    cudaStreamSynchronize(cs);
-  };
   auto finish = [&](ipc_status code, const char* msg) {
-    st.status = code;
-    if (code != IPC_OK) {
-      sim->err = msg;
-      restore();
-    }
-    if (stats) *stats = st;
+    sim->err = msg;
     return code;
   };
   while (it < P.max_newton) {
@@ -1464,6 +1467,7 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
       sim->pcg_fric_iters_acc += (long long)h.pcg_out[0] * (P.mu > 0 ? sim->n_fric : 0);
     }
     st.pcg_iters_max = std::max(st.pcg_iters_max, h.pcg_out[0]);
+    if (h.pcg_out[1] == 3) ++st.pcg_unconverged;
     st.n_pairs_max = std::max(st.n_pairs_max, h.n_pairs);
     st.n_ccd_max = std::max(st.n_ccd_max, h.n_ccd);
     double E = total_energy(sim, h.E);
@@ -1571,11 +1575,42 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
     sim->cand_valid = false;
   }
   if (!converged) return finish(IPC_ERR_NEWTON_MAXIT, "Newton did not converge");
+  CUDA_TRY(cudaGetLastError());
   launch_velocity(cs, ndof, sim->z, sim->z_t, 1.0 / dt, sim->zd);
-  std::memcpy(sim->h_Tcur.data(), kin_T_next, sizeof(double) * 12 * sim->nkb);
   CUDA_TRY(cudaStreamSynchronize(cs));
   CUDA_TRY(cudaGetLastError());
-  return finish(IPC_OK, "");
+  std::memcpy(sim->h_Tcur.data(), kin_T_next, sizeof(double) * 12 * sim->nkb);
+  return IPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats) {
+  if (!sim) return IPC_ERR_ARG;
+  if (sim->nkb && !kin_T_next) { sim->err = "kinematic transforms required"; return IPC_ERR_ARG; }
+  for (int i = 0; i < 12 * sim->nkb; ++i)
+    if (!std::isfinite(kin_T_next[i])) {
+      sim->err = "non-finite kinematic transform (body " + std::to_string(i / 12) + ")";
+      if (stats) { *stats = ipc_step_stats{}; stats->status = IPC_ERR_ARG; }
+      return IPC_ERR_ARG;
+    }
+  ipc_step_stats st{};
+  st.alpha_min = 1.0;
+  st.min_dist = 1e300;
+  bool started = false;
+  const ipc_status code = step_body(sim, kin_T_next, st, started);
+  st.status = code;
+  if (code != IPC_OK && started) {
+    // any failure after the start of the step: back to the state at its start (x_t, v_t unchanged)
+    const int ndof = 3 * sim->n_nodes, nk3 = 3 * sim->nk;
+    cudaMemcpyAsync(sim->z, sim->z_t, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, sim->st);
+    if (nk3) cudaMemcpyAsync(sim->xk, sim->xk_t, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, sim->st);
+    cudaStreamSynchronize(sim->st);
+  }
+  if (stats) *stats = st;
+  return code;
 }
 
 ipc_status sim_step_many(ipcsim* const* sims, int n, const double* const* kin_T_next_host, ipc_step_stats* stats_host,
@@ -1761,6 +1796,12 @@ ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_nex
     out4[3] = sim->plan_resident ? 1 : 0;
   }
   if (ms8) std::memcpy(ms8, sim->tune_ms, sizeof(sim->tune_ms));
+  return IPC_OK;
+}
+
+ipc_status sim_pcg_residency(ipcsim* sim, int streamed) {
+  if (!sim) return IPC_ERR_ARG;
+  sim->pcg_streamed = streamed != 0;
   return IPC_OK;
 }
 

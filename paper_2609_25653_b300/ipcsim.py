@@ -44,14 +44,16 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("mu", C.c_double),
                 ("eps_v", C.c_double), ("k_c", C.c_double), ("kappa_A", C.c_double), ("newton_tol", C.c_double),
                 ("pcg_rtol", C.c_double), ("s_ccd", C.c_double), ("max_newton", C.c_int), ("max_pcg", C.c_int),
-                ("precision", C.c_int), ("pair_capacity", C.c_int), ("broad_phase", C.c_int)]
+                ("precision", C.c_int), ("pair_capacity", C.c_int), ("broad_phase", C.c_int),
+                ("pair_capacity_max", C.c_int)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
                 ("pcg_iters_max", C.c_int), ("n_pairs_max", C.c_int), ("n_friction_pairs", C.c_int),
                 ("n_ccd_max", C.c_int), ("ls_halvings", C.c_int), ("alpha_min", C.c_double),
-                ("min_dist", C.c_double), ("energy_end", C.c_double), ("pnorm_end", C.c_double)]
+                ("min_dist", C.c_double), ("energy_end", C.c_double), ("pnorm_end", C.c_double),
+                ("pcg_unconverged", C.c_int), ("pad_", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,6 +87,7 @@ SIGNATURES = {
     "sim_adjoint": ([vp, vp, vp, vp, dp, dp, vp, vp, vp, vp, vp, dp], C.c_int),
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
     "sim_pcg_partition": ([ip, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip, ip, ip, ip, ip], C.c_int),
+    "sim_pcg_residency": ([vp, C.c_int], C.c_int),
 }
 
 PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "pcg_setup"]
@@ -156,7 +159,7 @@ def make_params(p: dict, precision=PREC_FP64) -> Params:
                   k_c=p.get("k_c", 0.0), kappa_A=p.get("kappa_A", 1e8), newton_tol=p["newton_tol"],
                   pcg_rtol=p.get("pcg_rtol", 1e-4), s_ccd=p.get("s_ccd", 0.1), max_newton=int(p.get("max_newton", 100)),
                   max_pcg=int(p.get("max_pcg", 0)), precision=int(precision), pair_capacity=int(p.get("pair_capacity", 0)),
-                  broad_phase=int(p.get("broad_phase", BROAD_LBVH)))
+                  broad_phase=int(p.get("broad_phase", BROAD_LBVH)), pair_capacity_max=int(p.get("pair_capacity_max", 0)))
 
 
 def _fill_desc(d, scene, keep):
@@ -366,6 +369,11 @@ class Simulator:
         ms = (C.c_float * 8)()
         self._check(load().sim_tuning(self.h, int(rowg), int(blocks_per_sm), int(bool(autotune_next_step)), out, ms))
         return (out[0], out[1]), list(ms)
+
+    def pcg_residency(self, streamed: bool):
+        """streamed=True: the PCG reads its operator from global memory in every iteration (never staged in
+        shared memory); False: staged when every CTA's rows fit (default)."""
+        self._check(load().sim_pcg_residency(self.h, int(bool(streamed))))
 
     def pcg_layout(self):
         """(CTAs, operator resident in shared memory) of the last PCG launch."""
