@@ -127,27 +127,43 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def pcg_bytes(work, sim, fp32, resident, launches):
-    """Algorithmic bytes the PCG kernel has to move, summed over the recorded launches.
+def pcg_work(work, sim, fp32, launches):
+    """Algorithmic work of the PCG kernel per launch: (bytes, flops), from the per-unit figures of the
+    method's solve, independent of how the kernel is built.
 
-    FP64 (pipelined CG, one barrier per iteration), per iteration and node: the
-    seven node-local vectors (z, q, s, p, r, u, w) and m read and written, x
-    read and written: 54 doubles = 432 B.  Mixed precision (FP32 CG inside FP64
-    refinement), per iteration and node: u read and w written in the product
-    phase, u, w, p, s, d, r read and p, s, d, r, u written in the update phase:
-    39 floats = 156 B.  The operator (9 elements + 4 B column index per BSR
-    block) and the 3x3 preconditioner blocks (9 elements per node) once per
-    iteration when they stream from memory, once per launch when every CTA
-    keeps its rows in shared memory.  Per barrier pair and iteration its
-    144-element block and 32 B record; per friction pair its 9-element block,
-    ids and weights (48 B)."""
+    Per iteration: the operator product reads every stored 3x3 block once (9 values + a 4 B column index:
+    76 B in FP64, 40 B in FP32) and takes 18 flops per block; the CG vectors move 7 values per DOF
+    (56 B in FP64, 28 B in FP32) and take 10 flops per DOF, the block-Jacobi preconditioner 6 flops per
+    DOF; every active barrier pair's 12x12 block (144 values + its 32 B record) takes 288 flops, every
+    friction pair's 3x3 block, ids and weights (9 values + 48 B) about 60 flops.  The mixed-precision
+    solver's inner iterations are FP32: its figures use 4-byte values."""
     e = 4 if fp32 else 8
-    n = sim.n_nodes
-    nodes = n * (156 if fp32 else 432)
-    op = work["bsr_blocks"] * (9 * e + 4) + 9 * n * e
-    per_iter = nodes + (0 if resident else op)
-    return (work["pcg_iters"] * per_iter + (launches * op if resident else 0)
-            + work["pcg_pair_iters"] * (144 * e + 32) + work["pcg_fric_iters"] * (9 * e + 48))
+    it = work["pcg_iters"]
+    ndof = 3 * sim.n_nodes
+    per_it_bytes = work["bsr_blocks"] * (9 * e + 4) + ndof * 7 * e
+    per_it_flops = work["bsr_blocks"] * 18 + ndof * 16
+    total_bytes = it * per_it_bytes + work["pcg_pair_iters"] * (144 * e + 32) + work["pcg_fric_iters"] * (9 * e + 48)
+    total_flops = it * per_it_flops + work["pcg_pair_iters"] * 288 + work["pcg_fric_iters"] * 60
+    n = max(launches, 1)
+    return total_bytes / n, total_flops / n
+
+
+def pcg_traffic(kernel, workload):
+    """DRAM bytes per launch of the PCG kernel from the committed ncu summary, or None when the kernel's
+    source has changed since that capture (the summary records the hash of the source it measured)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "pcg_traffic.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2609_25653_b300", "csrc", "pcg.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    for r in rec.get("captures", []):
+        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("pcg_cu_sha16") == sha:
+            return r.get("dram_bytes_per_launch")
+    return None
 
 
 def slowest_rank(local, device="cuda"):
@@ -166,6 +182,20 @@ def slowest_rank(local, device="cuda"):
     return float(t.item())
 
 
+def timed_indices(n_traj, warmup, steps, sample):
+    """Trajectory steps to time: `steps` steps spread evenly over the trajectory after the warm-up
+    ("trajectory"), or the `steps` steps right after it ("consecutive")."""
+    first = warmup
+    room = n_traj - first
+    if room < steps:
+        raise SystemExit("workload trajectory too short for the requested steps")
+    if sample == "consecutive":
+        return list(range(first, first + steps))
+    if steps == 1:
+        return [first]
+    return [first + round(j * (room - 1) / (steps - 1)) for j in range(steps)]
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -181,6 +211,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     wl = make_workload(args.workload)
     batched = isinstance(wl, list)
+    if batched and world > 1:
+        # independent scenes shard across ranks with no collective: rank r takes scenes r, r + N, ...
+        wl = shard_scenes(wl, rank, world)
     precision = args.precision or ("mixed" if batched else "fp64")
     prec = ipcsim.PREC_MIXED if precision == "mixed" else ipcsim.PREC_FP64
     if batched:
@@ -190,10 +223,10 @@ def run_ours(args):
         sc = wl
         sim = ipcsim.Simulator(sc, precision=prec, stream=stream)
     n_sc = len(wl) if batched else 1
-    n_total = args.warmup + args.steps + 1
-    if sc["kin_T"].shape[0] < n_total + 1 and len(sc.get("kin", [])):
-        raise SystemExit("workload trajectory too short for the requested steps")
+    n_traj = sc["kin_T"].shape[0] - 1 if len(sc.get("kin", [])) else sc["params"]["n_steps"]
+    timed = timed_indices(n_traj, args.warmup, args.steps, args.sample)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks_dev = ipcsim.device_peaks()  # FP64 / FP32 FMA roofs of this device, measured before the timed region
     from paper_2609_25653_b300 import autotune
     tuned_from_cache = autotune.prepare(sim, prec) if not args.no_autotune else None
     for w in range(args.warmup):
@@ -204,15 +237,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    # state at the start of the timed steps: the end-to-end leg replays the same steps from it
-    snap = sim.get_state()
-    snap_index = sim.step_index
     sim.profile(True)
     launches0 = ipcsim.kernel_launches()
-    times = []
-    stats = []
+    times, stats, snaps = [], [], []
+    untimed_launches = 0
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for s_idx in timed:
+            # untimed steps up to the next sampled step (the trajectory keeps running between samples)
+            l0 = ipcsim.kernel_launches()
+            sim.profile(False)
+            while sim.step_index < s_idx:
+                sim.step()
+            sim.profile(True, reset=False)
+            untimed_launches += ipcsim.kernel_launches() - l0
+            snaps.append((sim.get_state(), sim.step_index))
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
             stream.synchronize()
@@ -225,49 +263,50 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1))
             stats.append(st)
     torch.cuda.synchronize()
-    launches = ipcsim.kernel_launches() - launches0
+    launches = ipcsim.kernel_launches() - launches0 - untimed_launches
     prof, work = sim.profile_read()
     sim.profile(False)
     total_ms = slowest_rank(sum(times))
     value = world * args.steps * n_sc / (total_ms / 1e3)
 
-    # e2e through the public API with host buffers (transforms in, positions out), over the same steps
-    sim.set_state(*snap)
-    if sim.nkb:
-        sim.set_kinematic(sc["kin_T"][snap_index])
-    sim.step_index = snap_index
+    # e2e through the public API with host buffers (transforms in, positions out), the same sampled steps
+    def restore(j):
+        state, idx = snaps[j]
+        sim.set_state(*state)
+        if sim.nkb:
+            sim.set_kinematic(sc["kin_T"][idx])
+        sim.step_index = idx
+
     x_host = np.zeros((sim.nf, 3))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    T_pinned = torch.empty((max(sim.nkb, 1), 12), dtype=torch.float64).pin_memory()
+    e2e_s = 0.0
     e2e_steps_ms = []
-    for _ in range(args.steps):
+    for j in range(len(timed)):
+        restore(j)
+        torch.cuda.synchronize()
+        T_host = T_pinned.numpy()
+        T_host[:sim.nkb] = sc["kin_T"][sim.step_index + 1].reshape(-1, 12) if sim.nkb else 0.0
         t1 = time.perf_counter()
-        sim.step()
+        sim.step(T_host[:sim.nkb].reshape(-1, 3, 4) if sim.nkb else None)
         x_host[:] = sim.get_state()[0]
-        e2e_steps_ms.append(round((time.perf_counter() - t1) * 1e3, 2))
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+        dt_s = time.perf_counter() - t1
+        e2e_s += dt_s
+        e2e_steps_ms.append(round(dt_s * 1e3, 2))
     print("e2e step ms:", e2e_steps_ms, file=sys.stderr)
 
-    # adjoint ms/step: the backward of the same steps (unprojected Hessian re-assembly at the
-    # checkpointed end state, FP64 adjoint solve, parameter contractions), replayed from checkpoints
+    # adjoint ms/step: the backward of the same sampled steps (unprojected Hessian re-assembly at the
+    # checkpointed end state, FP64 adjoint solve, parameter contractions)
     adjoint = None
     if not batched and not args.no_adjoint:
-        sim.set_state(*snap)
-        if sim.nkb:
-            sim.set_kinematic(sc["kin_T"][snap_index])
-        sim.step_index = snap_index
-        ckpt = []
-        for _ in range(args.steps):
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        glogE = torch.zeros(sim.nt, dtype=torch.float64, device="cuda")
+        adj_ms = []
+        for j in range(len(timed)):
+            restore(j)
             z0, zd0 = sim.get_dofs()
             k0 = sim.step_index
             sim.step()
             z1, _ = sim.get_dofs()
-            ckpt.append((z0, zd0, z1, k0))
-        gen = torch.Generator(device="cuda").manual_seed(0)
-        glogE = torch.zeros(sim.nt, dtype=torch.float64, device="cuda")
-        adj_ms = []
-        for z0, zd0, z1, k0 in ckpt:
             gz = torch.randn(sim.ndof, dtype=torch.float64, device="cuda", generator=gen)
             gzd = 1e-2 * torch.randn(sim.ndof, dtype=torch.float64, device="cuda", generator=gen)
             torch.cuda.synchronize()
@@ -283,21 +322,41 @@ def run_ours(args):
     e2e_s = slowest_rank(e2e_s)
     e2e_value = world * args.steps * n_sc / e2e_s
 
-    # roofline of the dominant stage
+    # roofline of the dominant kernel (the PCG solve), from its algorithmic work per launch and its
+    # CUDA-event time per launch on the simulator's stream
     peaks, peak_src = load_peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
     pcg = prof["pcg"]
+    fp32 = prec == ipcsim.PREC_MIXED
     pcg_avg_ms = pcg["ms"] / max(pcg["n"], 1)
     pcg_grid, pcg_resident = sim.pcg_layout()
-    pcg_bytes_per_launch = pcg_bytes(work, sim, prec == ipcsim.PREC_MIXED, pcg_resident, pcg["n"]) / max(pcg["n"], 1)
-    achieved = pcg_bytes_per_launch / (pcg_avg_ms / 1e3) / 1e9 if pcg["n"] else 0.0
-    roofline = {"kernel": "k_pcg32" if precision == "mixed" else "k_pcg", "bound": "hbm", "achieved": round(achieved, 2),
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 5),
-                "traffic": None, "peak_source": peak_src,
-                "launch_ms": round(pcg_avg_ms, 5), "algorithmic_bytes_per_launch": int(pcg_bytes_per_launch),
-                "pcg_ctas": pcg_grid, "operator_in_shared_memory": pcg_resident,
-                "dominant_stage": dom,
-                "stage_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["n"]}}
+    b_launch, f_launch = pcg_work(work, sim, fp32, pcg["n"])
+    alu_peak = peaks_dev["fp32_tflops"] if fp32 else peaks_dev["fp64_tflops"]
+    t_mem = b_launch / (peaks["hbm_gbs"] * 1e9)
+    t_alu = f_launch / (alu_peak * 1e12)
+    kernel = "k_pcg32" if fp32 else "k_pcg"
+    gbs = b_launch / (pcg_avg_ms / 1e3) / 1e9 if pcg["n"] else 0.0
+    tfs = f_launch / (pcg_avg_ms / 1e3) / 1e12 if pcg["n"] else 0.0
+    if t_alu > t_mem:
+        bound = {"bound": "alu", "achieved": round(tfs, 5), "peak": round(alu_peak, 4), "unit": "TFLOP/s",
+                 "frac": round(tfs / alu_peak, 5)}
+    else:
+        bound = {"bound": "hbm", "achieved": round(gbs, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": round(gbs / peaks["hbm_gbs"], 5)}
+    roofline = dict(bound, traffic=pcg_traffic(kernel, sc["name"] if not batched else f"batched{n_sc}"),
+                    kernel=kernel,
+                    peak_source=("FP64 FMA rate measured in this run (sim_device_peaks)" if bound["bound"] == "alu"
+                                 and not fp32 else "FP32 FMA rate measured in this run (sim_device_peaks)"
+                                 if bound["bound"] == "alu" else f"HBM copy bandwidth, {peak_src} (MEASURED_PEAKS.json)"),
+                    hbm={"achieved_gbs": round(gbs, 2), "peak_gbs": peaks["hbm_gbs"],
+                         "frac": round(gbs / peaks["hbm_gbs"], 5)},
+                    alu={"achieved_tflops": round(tfs, 5), "peak_tflops": round(alu_peak, 4),
+                         "frac": round(tfs / alu_peak, 5), "pipe": "fp32" if fp32 else "fp64"},
+                    launch_ms=round(pcg_avg_ms, 5), algorithmic_bytes_per_launch=int(b_launch),
+                    algorithmic_flops_per_launch=int(f_launch),
+                    pcg_iterations_per_launch=round(work["pcg_iters"] / max(pcg["n"], 1), 1),
+                    pcg_ctas=pcg_grid, operator_in_shared_memory=pcg_resident, dominant_stage=dom,
+                    stage_ms_per_step={k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["n"]})
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle advances one scene at a time: scene-steps/s of the first scene of a batch
@@ -310,13 +369,19 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f64+f32",
             "data": "synthetic",
-            "config": workload_config(wl, args.workload, {"parallelism": f"replicas{world}", "precision": precision,
-                                                          "value_counts": "scene-steps" if batched else "steps",
-                                                          "pcg_threads_per_row": rowg, "pcg_blocks_per_sm": bps,
-                                                          "pcg_shape": "cached" if tuned_from_cache else ("autotuned" if tuned_from_cache is False else "default"),
-                                                          "newton_iters_per_step": round(sum(newton) / len(newton), 2),
-                                                          "pcg_iters_per_step": round(sum(s["pcg_iters_total"] for s in stats) / len(stats), 1),
-                                                          "active_pairs_max": max(s["n_pairs_max"] for s in stats)}),
+            "config": workload_config(wl, args.workload, {
+                "parallelism": (f"scene-shards{world}" if batched and world > 1 else f"replicas{world}"),
+                "precision": precision,
+                "value_counts": "scene-steps" if batched else "steps",
+                "timed_steps": timed if args.sample == "consecutive" or len(timed) <= 40 else f"{timed[0]}..{timed[-1]}",
+                "timed_sample": ("every step after the warm-up" if args.sample == "consecutive" else
+                                 f"{len(timed)} steps spread over the {n_traj}-step trajectory (untimed steps between)"),
+                "pcg_threads_per_row": rowg, "pcg_blocks_per_sm": bps,
+                "pcg_shape": "cached" if tuned_from_cache else ("autotuned" if tuned_from_cache is False else "default"),
+                "newton_iters_per_step": round(sum(newton) / len(newton), 2),
+                "pcg_iters_per_step": round(sum(s["pcg_iters_total"] for s in stats) / len(stats), 1),
+                "pcg_unconverged_solves": int(sum(s["pcg_unconverged"] for s in stats)),
+                "active_pairs_max": max(s["n_pairs_max"] for s in stats)}),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "adjoint": adjoint,
@@ -324,11 +389,18 @@ def run_ours(args):
                     "d2h_bytes_per_step": 24 * sim.nf},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "device_peaks_tflops": {k: round(v, 4) for k, v in peaks_dev.items()},
         }
         print(json.dumps(line))
     sim.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def shard_scenes(scenes_list, rank, world):
+    """Scenes of rank `rank` out of `world` (round robin: r, r + N, ...); every rank keeps at least one."""
+    mine = scenes_list[rank::world]
+    return mine if mine else scenes_list[:1]
 
 
 def _small_enough(S):
@@ -372,8 +444,8 @@ def oracle_sampled_iteration_seconds(o, budget):
     # pair sweeps over a prefix of the primitives
     per_sweep = max(0.5, (budget - t_el_h - t_el - t_solve) / 3)
     nsv, ne = len(S.sv), len(S.edges)
-    k = max(1, min(nsv, int(nsv * 0.01)))
-    m = max(2, min(ne, int(ne * 0.05)))
+    k = max(1, min(nsv, int(nsv * 0.04)))
+    m = max(2, min(ne, int(ne * 0.1)))
     sub = orc.OrcSurf(k, len(S.tris), 0, orc._i(S.sv), orc._i(S.tris), orc._i(S.edges), orc._i(S.vbody),
                       orc._i(S.bkind))
     rec = np.zeros((1 << 16, 8), np.int32)
@@ -394,7 +466,8 @@ def oracle_sampled_iteration_seconds(o, budget):
 
 
 def cpu_baseline(sc, seconds, newton_per_step=None):
-    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+    """The oracle as it stands on a bounded sample of the same workload (its brute-force pair loops on all
+    host cores, the rest on one)."""
     from oracle import ipc as orc
     o = orc.Oracle(sc)
     if _small_enough(o.S):
@@ -406,13 +479,30 @@ def cpu_baseline(sc, seconds, newton_per_step=None):
             el = time.perf_counter() - t0
             if el > seconds or n >= sc["params"]["n_steps"]:
                 break
-        return {"value": round(n / el, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"first {n} steps of the same workload ({el:.1f} s, brute-force pairs, scipy sparse LU)"}
+        return {"value": round(n / el, 4), "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+                "sample": (f"first {n} steps of the same workload ({el:.1f} s; brute-force pair loops on "
+                           f"{orc.get_threads()} threads, element loops and scipy sparse LU on one)")}
     t_it, detail = oracle_sampled_iteration_seconds(o, seconds)
     nps = newton_per_step or 5.0
-    return {"value": round(1.0 / (t_it * nps), 7), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": round(1.0 / (t_it * nps), 7), "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
             "sample": (f"extrapolated: one oracle Newton iteration = {t_it:.1f} s ({detail}); "
                        f"x {nps:.1f} Newton iterations per step as measured on the GPU run")}
+
+
+REDUCED = {"arm_gripper": "arm_gripper_grasp_reduced", "soft_cylinder": "soft_gripper_cylinder_reduced"}
+
+
+def oracle_newton_per_step(workload, seconds):
+    """Newton iterations per step of the oracle itself, measured over the first steps of the reduced
+    version of the workload (the same ingredients at a resolution it steps in seconds)."""
+    from oracle import ipc as orc
+    from paper_2609_25653_b300 import scenes
+    name = REDUCED.get(workload, "arm_gripper_grasp_reduced")
+    o = orc.Oracle(getattr(scenes, name)(0))
+    its, t0 = [], time.perf_counter()
+    while time.perf_counter() - t0 < seconds and len(its) < 12:
+        its.append(len(o.step()))
+    return sum(its) / len(its), f"{len(its)} oracle steps of {name}"
 
 
 def run_reference(args):
@@ -451,17 +541,19 @@ def run_reference(args):
             if time.perf_counter() - t0 > 180.0:
                 break
         t_it = float(sorted(its)[len(its) // 2])
-        nps = 5.0
+        nps, nps_src = oracle_newton_per_step(args.workload, min(60.0, 4 * args.cpu_seconds))
         v = 1.0 / (t_it * nps)
         n = len(its)
         ms = 1e3 / v
         sample = (f"{n} sampled oracle Newton iterations, median {t_it:.1f} s (last: {detail}); "
-                  f"x {nps:.0f} Newton iterations per step")
+                  f"x {nps:.2f} Newton iterations per step, measured by the oracle over {nps_src}")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 7), "unit": UNIT, "n_gpus": args.gpus, "steps": n,
             "warmup": min(args.warmup, 1), "ms_per_step": round(ms, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wl, args.workload, {"parallelism": "cpu-1", "reference_scene": sc["name"]}),
-            "cpu_baseline": {"value": round(v, 7), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": workload_config(wl, args.workload, {"parallelism": f"cpu-{orc.get_threads()}",
+                                                          "reference_scene": sc["name"]}),
+            "cpu_baseline": {"value": round(v, 7), "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+                             "sample": sample + f"; brute-force pair loops on {orc.get_threads()} threads"},
             "e2e": {"value": round(v, 7), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -477,6 +569,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default PCG launch shape")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ms/step measurement")
+    ap.add_argument("--sample", choices=["trajectory", "consecutive"], default="trajectory",
+                    help="time K steps spread over the whole trajectory (default) or the K steps after the warm-up")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
                     help="default: fp64 for single scenes, mixed (FP32 PCG, FP64 residuals) for batches")
     args = ap.parse_args()

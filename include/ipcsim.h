@@ -247,8 +247,8 @@ ipc_status sim_pcg_residency(ipcsim* sim, int streamed);
 
 /* Per-stage timing with CUDA events recorded on the simulator's stream
  * around each stage of sim_step (cheap; intervals are read at the
- * synchronisation points sim_step already has).  enable != 0 starts (and
- * clears) accounting; sim_profile_read returns accumulated milliseconds and
+ * synchronisation points sim_step already has).  enable == 1 starts (and
+ * clears) accounting, enable == 2 resumes it without clearing, 0 pauses it; sim_profile_read returns accumulated milliseconds and
  * interval counts per stage [PCG, elastic, barrier, culling, CCD, friction,
  * other, PCG setup (incidence lists, FP32 copies, operator layout)] and work4
  * = [PCG iterations, sum over iterations of barrier
@@ -273,6 +273,15 @@ ipc_status sim_profile_read(const ipcsim* sim, double* ms8, long long* n8, long 
  * NULL outputs or non-positive sizes. */
 ipc_status sim_pcg_partition(const int* row, int nf, int nab, int grid, const int* node_scene, int n_scenes,
                              const int* row_extra, int* out4, int* seg, int* abd_seg, int* cta_scene);
+
+/* Measured arithmetic roofs of the current device (not part of the paper's
+ * method: they are the denominators of the solver kernels' roofline, which
+ * on this part is set by the FP64 pipe rather than by memory): out2[0] =
+ * FP64 FMA rate, out2[1] = FP32 FMA rate, both in TFLOP/s (2 flops per FMA),
+ * from independent register FMA chains on every SM, best of five timed
+ * launches (about 0.2 s in all).  Allocates a small scratch buffer;
+ * synchronises the device's legacy default stream. */
+ipc_status sim_device_peaks(double* out2);
 
 /* Total number of CUDA kernels this library has launched in this process
  * (all simulators, all threads), for launch accounting. */

@@ -72,7 +72,18 @@ def lib():
         L.orc_project_psd.argtypes = [C.c_int, dp]
         L.orc_jacobi_eigen.argtypes = [C.c_int, dp, dp]
         L.orc_jacobi_eigen.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
     return _lib
+
+
+def set_threads(n: int):
+    """Threads of the brute-force pair loops (results do not depend on it); <= 0: all cores."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def _d(a):

@@ -7,6 +7,11 @@
 // Everything is written as the plain definition: no blocking, no fusion, no
 // spatial acceleration.  Candidate pairs are found by brute force over all
 // (surface vertex, surface triangle) and (surface edge, surface edge) pairs.
+// The two brute-force pair loops are spread over OpenMP threads in chunks of
+// the outer index; each chunk's pairs are kept apart and concatenated in chunk
+// order afterwards, so the output (pairs, their order, the minimum time of
+// impact) is the same as the serial loop's for any thread count
+// (orc_set_threads).
 // Compiled with -ffp-contract=off so every product and sum rounds exactly as
 // written.
 //
@@ -37,8 +42,14 @@
 #include <cstring>
 #include <algorithm>
 #include <vector>
+#include <omp.h>
 
 extern "C" {
+
+// Threads of the brute-force pair loops (<= 0: OpenMP's default).
+static int g_threads = 0;
+void orc_set_threads(int n) { g_threads = n; }
+int orc_get_threads(void) { return g_threads > 0 ? g_threads : omp_get_max_threads(); }
 
 // ---------------------------------------------------------------------------
 // small dense helpers
@@ -658,49 +669,68 @@ static bool excluded(const OrcSurf& S, const int* va, int na, const int* vb, int
 // All pairs with squared distance below sh.  Each output record holds
 // kind (0 PT, 1 EE), primitive a, primitive b, type, 4 vertex ids, s.
 // Returns the number of pairs (records beyond cap are not written).
+struct PairRec { int r[8]; double s; };
+static const int kChunks = 256;  // chunks of the outer loop index (output kept in chunk order)
+
 int orc_active_pairs(const OrcSurf* Sp, const double* x, double sh, int cap, int* rec_i, double* rec_s) {
   const OrcSurf& S = *Sp;
-  int count = 0;
-  double xs[12], w[4], s;
-  for (int i = 0; i < S.nsv; ++i) {
-    int p = S.sv[i];
-    for (int t = 0; t < S.ntri; ++t) {
-      const int* tv = S.tri + 3 * t;
-      if (excluded(S, &p, 1, tv, 3)) continue;
-      int ids[4] = {p, tv[0], tv[1], tv[2]};
-      for (int k = 0; k < 4; ++k)
-        for (int d = 0; d < 3; ++d) xs[3 * k + d] = x[3 * ids[k] + d];
-      int type = orc_pt_classify(xs, &s, w);
-      if (s < sh) {
-        if (count < cap) {
-          int* r = rec_i + 8 * count;
-          r[0] = 0; r[1] = i; r[2] = t; r[3] = type;
-          for (int k = 0; k < 4; ++k) r[4 + k] = ids[k];
-          rec_s[count] = s;
+  std::vector<std::vector<PairRec>> pt(kChunks), ee(kChunks);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(orc_get_threads())
+  for (int c = 0; c < kChunks; ++c) {
+    double xs[12], w[4], s;
+    for (int i = (int)((long long)S.nsv * c / kChunks); i < (int)((long long)S.nsv * (c + 1) / kChunks); ++i) {
+      int p = S.sv[i];
+      for (int t = 0; t < S.ntri; ++t) {
+        const int* tv = S.tri + 3 * t;
+        if (excluded(S, &p, 1, tv, 3)) continue;
+        int ids[4] = {p, tv[0], tv[1], tv[2]};
+        for (int k = 0; k < 4; ++k)
+          for (int d = 0; d < 3; ++d) xs[3 * k + d] = x[3 * ids[k] + d];
+        int type = orc_pt_classify(xs, &s, w);
+        if (s < sh) {
+          PairRec q;
+          q.r[0] = 0; q.r[1] = i; q.r[2] = t; q.r[3] = type;
+          for (int k = 0; k < 4; ++k) q.r[4 + k] = ids[k];
+          q.s = s;
+          pt[c].push_back(q);
         }
-        ++count;
+      }
+    }
+    // edge-edge rows: chunk c takes the rows ea with ea mod kChunks == c (the triangular loop stays balanced)
+    for (int ea = c; ea < S.nedge; ea += kChunks) {
+      const int* va = S.edge + 2 * ea;
+      for (int eb = ea + 1; eb < S.nedge; ++eb) {
+        const int* vb = S.edge + 2 * eb;
+        if (excluded(S, va, 2, vb, 2)) continue;
+        int ids[4] = {va[0], va[1], vb[0], vb[1]};
+        for (int k = 0; k < 4; ++k)
+          for (int d = 0; d < 3; ++d) xs[3 * k + d] = x[3 * ids[k] + d];
+        int type = orc_ee_classify(xs, &s, w);
+        if (s < sh) {
+          PairRec q;
+          q.r[0] = 1; q.r[1] = ea; q.r[2] = eb; q.r[3] = type;
+          for (int k = 0; k < 4; ++k) q.r[4 + k] = ids[k];
+          q.s = s;
+          ee[c].push_back(q);
+        }
       }
     }
   }
-  for (int ea = 0; ea < S.nedge; ++ea) {
-    const int* va = S.edge + 2 * ea;
-    for (int eb = ea + 1; eb < S.nedge; ++eb) {
-      const int* vb = S.edge + 2 * eb;
-      if (excluded(S, va, 2, vb, 2)) continue;
-      int ids[4] = {va[0], va[1], vb[0], vb[1]};
-      for (int k = 0; k < 4; ++k)
-        for (int d = 0; d < 3; ++d) xs[3 * k + d] = x[3 * ids[k] + d];
-      int type = orc_ee_classify(xs, &s, w);
-      if (s < sh) {
-        if (count < cap) {
-          int* r = rec_i + 8 * count;
-          r[0] = 1; r[1] = ea; r[2] = eb; r[3] = type;
-          for (int k = 0; k < 4; ++k) r[4 + k] = ids[k];
-          rec_s[count] = s;
-        }
-        ++count;
-      }
-    }
+  // serial order: point-triangle pairs by (vertex, triangle), then edge-edge pairs by (ea, eb)
+  std::vector<const PairRec*> out;
+  for (int c = 0; c < kChunks; ++c)
+    for (const PairRec& q : pt[c]) out.push_back(&q);
+  std::vector<const PairRec*> eev;
+  for (int c = 0; c < kChunks; ++c)
+    for (const PairRec& q : ee[c]) eev.push_back(&q);
+  std::stable_sort(eev.begin(), eev.end(), [](const PairRec* a, const PairRec* b) {
+    return a->r[1] != b->r[1] ? a->r[1] < b->r[1] : a->r[2] < b->r[2];
+  });
+  out.insert(out.end(), eev.begin(), eev.end());
+  const int count = (int)out.size();
+  for (int k = 0; k < count && k < cap; ++k) {
+    for (int j = 0; j < 8; ++j) rec_i[8 * k + j] = out[k]->r[j];
+    rec_s[k] = out[k]->s;
   }
   return count;
 }
@@ -766,44 +796,48 @@ static void swept_box(const double* x, const double* p, const int* ids, int n, d
 }
 
 // Largest step fraction alpha in (0, 1] along p: minimum ACCD time of impact
-// over every pair whose swept boxes over [x, x + p] overlap.
+// over every pair whose swept boxes over [x, x + p] overlap.  The minimum and
+// the candidate count do not depend on the order the pairs are visited in.
 double orc_ccd_alpha(const OrcSurf* Sp, const double* x, const double* p, double s_frac, int max_iter,
                      int* n_cand) {
   const OrcSurf& S = *Sp;
   double alpha = 1.0;
-  int nc = 0;
-  double xs[12], ps[12], la[3], ha[3], lb[3], hb[3];
-  for (int i = 0; i < S.nsv; ++i) {
-    int pv = S.sv[i];
-    swept_box(x, p, &pv, 1, la, ha);
-    for (int t = 0; t < S.ntri; ++t) {
-      const int* tv = S.tri + 3 * t;
-      if (excluded(S, &pv, 1, tv, 3)) continue;
-      swept_box(x, p, tv, 3, lb, hb);
-      if (!boxes_overlap(la, ha, lb, hb)) continue;
-      int ids[4] = {pv, tv[0], tv[1], tv[2]};
-      for (int k = 0; k < 4; ++k)
-        for (int d = 0; d < 3; ++d) { xs[3 * k + d] = x[3 * ids[k] + d]; ps[3 * k + d] = p[3 * ids[k] + d]; }
-      ++nc;
-      alpha = std::min(alpha, orc_accd(0, xs, ps, s_frac, 1.0, max_iter));
+  long long nc = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(orc_get_threads()) reduction(min : alpha) reduction(+ : nc)
+  for (int c = 0; c < kChunks; ++c) {
+    double xs[12], ps[12], la[3], ha[3], lb[3], hb[3];
+    for (int i = (int)((long long)S.nsv * c / kChunks); i < (int)((long long)S.nsv * (c + 1) / kChunks); ++i) {
+      int pv = S.sv[i];
+      swept_box(x, p, &pv, 1, la, ha);
+      for (int t = 0; t < S.ntri; ++t) {
+        const int* tv = S.tri + 3 * t;
+        if (excluded(S, &pv, 1, tv, 3)) continue;
+        swept_box(x, p, tv, 3, lb, hb);
+        if (!boxes_overlap(la, ha, lb, hb)) continue;
+        int ids[4] = {pv, tv[0], tv[1], tv[2]};
+        for (int k = 0; k < 4; ++k)
+          for (int d = 0; d < 3; ++d) { xs[3 * k + d] = x[3 * ids[k] + d]; ps[3 * k + d] = p[3 * ids[k] + d]; }
+        ++nc;
+        alpha = std::min(alpha, orc_accd(0, xs, ps, s_frac, 1.0, max_iter));
+      }
+    }
+    for (int ea = c; ea < S.nedge; ea += kChunks) {
+      const int* va = S.edge + 2 * ea;
+      swept_box(x, p, va, 2, la, ha);
+      for (int eb = ea + 1; eb < S.nedge; ++eb) {
+        const int* vb = S.edge + 2 * eb;
+        if (excluded(S, va, 2, vb, 2)) continue;
+        swept_box(x, p, vb, 2, lb, hb);
+        if (!boxes_overlap(la, ha, lb, hb)) continue;
+        int ids[4] = {va[0], va[1], vb[0], vb[1]};
+        for (int k = 0; k < 4; ++k)
+          for (int d = 0; d < 3; ++d) { xs[3 * k + d] = x[3 * ids[k] + d]; ps[3 * k + d] = p[3 * ids[k] + d]; }
+        ++nc;
+        alpha = std::min(alpha, orc_accd(1, xs, ps, s_frac, 1.0, max_iter));
+      }
     }
   }
-  for (int ea = 0; ea < S.nedge; ++ea) {
-    const int* va = S.edge + 2 * ea;
-    swept_box(x, p, va, 2, la, ha);
-    for (int eb = ea + 1; eb < S.nedge; ++eb) {
-      const int* vb = S.edge + 2 * eb;
-      if (excluded(S, va, 2, vb, 2)) continue;
-      swept_box(x, p, vb, 2, lb, hb);
-      if (!boxes_overlap(la, ha, lb, hb)) continue;
-      int ids[4] = {va[0], va[1], vb[0], vb[1]};
-      for (int k = 0; k < 4; ++k)
-        for (int d = 0; d < 3; ++d) { xs[3 * k + d] = x[3 * ids[k] + d]; ps[3 * k + d] = p[3 * ids[k] + d]; }
-      ++nc;
-      alpha = std::min(alpha, orc_accd(1, xs, ps, s_frac, 1.0, max_iter));
-    }
-  }
-  if (n_cand) *n_cand = nc;
+  if (n_cand) *n_cand = (int)nc;
   return alpha;
 }
 

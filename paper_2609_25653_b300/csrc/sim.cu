@@ -1808,6 +1808,7 @@ ipc_status sim_pcg_residency(ipcsim* sim, int streamed) {
 ipc_status sim_profile(ipcsim* sim, int enable) {
   if (!sim) return IPC_ERR_ARG;
   sim->prof = enable != 0;
+  if (enable == 2) return IPC_OK;  // resume: keep what has been accumulated
   for (int k = 0; k < 8; ++k) { sim->prof_ms[k] = 0; sim->prof_n[k] = 0; sim->ev_open[k] = false; }
   sim->pcg_iters_acc = sim->pcg_pair_iters_acc = sim->pcg_fric_iters_acc = 0;
   return IPC_OK;

@@ -88,6 +88,7 @@ SIGNATURES = {
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
     "sim_pcg_partition": ([ip, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip, ip, ip, ip, ip], C.c_int),
     "sim_pcg_residency": ([vp, C.c_int], C.c_int),
+    "sim_device_peaks": ([dp], C.c_int),
 }
 
 PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "pcg_setup"]
@@ -106,6 +107,15 @@ def load():
             f.restype = res
         _lib = L
     return _lib
+
+
+def device_peaks() -> dict:
+    """Measured FP64 and FP32 FMA rates of the current device, TFLOP/s (sim_device_peaks)."""
+    out = (C.c_double * 2)()
+    code = load().sim_device_peaks(out)
+    if code != IPC_OK:
+        raise IpcError(code, "sim_device_peaks failed")
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1]}
 
 
 def kernel_launches() -> int:
@@ -381,8 +391,9 @@ class Simulator:
         self._check(load().sim_tuning(self.h, 0, 0, 0, out, None))
         return out[2], bool(out[3])
 
-    def profile(self, enable=True):
-        self._check(load().sim_profile(self.h, int(enable)))
+    def profile(self, enable=True, reset=True):
+        """Per-stage CUDA-event accounting: on (cleared unless reset=False, which resumes it) or off."""
+        self._check(load().sim_profile(self.h, (1 if reset else 2) if enable else 0))
 
     def profile_read(self):
         ms = (C.c_double * 8)()

@@ -410,6 +410,7 @@ def _frame(R, t):
 
 
 def arm_gripper_grasp(seed: int = 0, n_steps: int = 400, tip_cell=1.25e-3, link_tris=2000, obj_tris=5000,
+                      base_tris=1000, close_per_step=0.05e-3, close_steps=100, hold_steps=20, lift_per_step=0.25e-3,
                       **param_overrides) -> dict:
     """Two fin-ray fingertips (E = 2e5 Pa, nu = 0.45, rho = 1100) stitched to
     two kinematic finger bases grasp and lift a rigid ABD ellipsoid (semi-axes
@@ -419,7 +420,10 @@ def arm_gripper_grasp(seed: int = 0, n_steps: int = 400, tip_cell=1.25e-3, link_
 
     Trajectory: the fingertips start in the pre-grasp pose 0.8 mm from the
     object, close 0.05 mm per step for 100 steps (5 mm), hold 20 steps, then
-    the gripper and arm lift at 50 mm/s."""
+    the gripper and arm lift at 50 mm/s (0.25 mm per step).  The resolution
+    (tip voxel size, link, object and base triangle counts) and the
+    trajectory timing are parameters, so that a reduced scene with every
+    ingredient fits the CPU oracle."""
     mm = 1e-3
     rng = SplitMix64(seed)
     a, b, c = 30 * mm, 25 * mm, 20 * mm
@@ -455,7 +459,7 @@ def arm_gripper_grasp(seed: int = 0, n_steps: int = 400, tip_cell=1.25e-3, link_
     fem_body = np.concatenate(fem_body)
     nt = len(tets)
     # finger bases: kinematic boxes 0.6 mm above each tip's mounting face (~1k triangles)
-    base_n = max(2, int(round(math.sqrt(1000 / 12))))
+    base_n = max(1, int(round(math.sqrt(base_tris / 12))))
     kin = []
     base_up, base_tris = subdivided_box((-12 * mm, -2 * mm, 0.6 * mm), (12 * mm, 22 * mm, 8.6 * mm), base_n)
     base_dn = base_up * np.array([1.0, -1.0, 1.0])  # mirror image for the -y finger
@@ -488,8 +492,8 @@ def arm_gripper_grasp(seed: int = 0, n_steps: int = 400, tip_cell=1.25e-3, link_
     phases = np.zeros(n_steps + 1)
     lift = np.zeros(n_steps + 1)
     for s in range(n_steps + 1):
-        phases[s] = min(s, 100) * 0.05 * mm
-        lift[s] = max(0, s - 120) * 0.25 * mm
+        phases[s] = min(s, close_steps) * close_per_step
+        lift[s] = max(0, s - close_steps - hold_steps) * lift_per_step
     wob_amp = 0.02 * rng.uniform(7)
     wob_w = 2 * math.pi * (0.5 + rng.uniform(7))
     wob_ph = 2 * math.pi * rng.uniform(7)
@@ -518,6 +522,19 @@ def arm_gripper_grasp(seed: int = 0, n_steps: int = 400, tip_cell=1.25e-3, link_
         gravity=np.array([0.0, 0.0, -9.81]),
         params=params,
     )
+
+
+def arm_gripper_grasp_reduced(seed: int = 0, n_steps: int = 16, **param_overrides) -> dict:
+    """Every ingredient of the arm-gripper grasp at a resolution the CPU oracle
+    steps in seconds: two fin-ray tips of 3 mm voxels (about 1.8k tets each), 7 kinematic arm links
+    of about 50 triangles on the seeded joint wobble, two stitched finger bases
+    of about 100 triangles, the ABD ellipsoid (about 300 triangles, 0.1 kg) on
+    the ground quad, mu = 0.6.  Faster trajectory: contact at about step 3,
+    squeeze to step 10 (0.3 mm per step), hold 2 steps, then lift."""
+    sc = arm_gripper_grasp(seed, n_steps=n_steps, tip_cell=3.0e-3, link_tris=48, obj_tris=300, base_tris=100,
+                           close_per_step=0.3e-3, close_steps=10, hold_steps=2, **param_overrides)
+    sc["name"] = f"arm_gripper_grasp_reduced_{len(sc['fem_tets'])}tet"
+    return sc
 
 
 def abd_box_drop(n_steps: int = 6, mu: float = 0.3, **param_overrides) -> dict:
@@ -669,16 +686,20 @@ def voxel_cylinder(r, h, cell, z0=0.0):
 
 
 def soft_gripper_cylinder(seed: int = 0, n_steps: int = 300, tip_cell=1.25e-3, cyl_cell=2.15e-3,
-                          close_per_step=0.05e-3, **param_overrides) -> dict:
+                          close_per_step=0.05e-3, cyl_r=25e-3, cyl_h=60e-3, close_steps=200, base_tris=1000,
+                          **param_overrides) -> dict:
     """The two fin-ray fingertips of the arm-gripper grasp squeeze a deformable
     Neo-Hookean cylinder (r = 25 mm, h = 60 mm, about 60k tets, E = 5e4 Pa,
     nu = 0.4, rho = 1100 assumed) resting on the ground quad; no arm links and
     no rigid object.  The fingertips start 0.8 mm from the cylinder; the
     finger bases close `close_per_step` (0.05 mm) per step for 200 steps
-    (10 mm in all), then hold.  dt = 5 ms, dhat = 0.5 mm, mu = 0.6."""
+    (10 mm in all), then hold.  dt = 5 ms, dhat = 0.5 mm, mu = 0.6.  The
+    cylinder's size and voxel size, the closing schedule and the base
+    resolution are parameters (the reduced scene uses them)."""
     mm = 1e-3
-    sc = arm_gripper_grasp(seed, n_steps=n_steps, tip_cell=tip_cell, link_tris=8, obj_tris=1000, **param_overrides)
-    cX, cT = voxel_cylinder(25 * mm, 60 * mm, cyl_cell, z0=0.3 * mm)
+    sc = arm_gripper_grasp(seed, n_steps=n_steps, tip_cell=tip_cell, link_tris=8, obj_tris=1000, base_tris=base_tris,
+                           **param_overrides)
+    cX, cT = voxel_cylinder(cyl_r, cyl_h, cyl_cell, z0=0.3 * mm)
     n_tip_v, n_tip_t = len(sc["fem_X"]), len(sc["fem_tets"])
     # move the fingertips (and their bases) in to 0.8 mm from the voxel surface
     shift = 25 * mm - float(np.abs(cX[:, 1]).max())
@@ -699,10 +720,20 @@ def soft_gripper_cylinder(seed: int = 0, n_steps: int = 300, tip_cell=1.25e-3, c
     b, gap = 25 * mm - shift, 0.8 * mm
     z_top = kin_T[0, 1, 2, 3]
     for s in range(n_steps + 1):
-        close = min(s, 200) * close_per_step
+        close = min(s, close_steps) * close_per_step
         kin_T[s, 1, :, 3] = (0.0, b + gap - close, z_top)
         kin_T[s, 2, :, 3] = (0.0, -(b + gap - close), z_top)
     sc["kin_T"] = kin_T
     sc["name"] = f"soft_gripper_cylinder_{len(tets)}tet"
     assert n_tip_t + nt_c == len(tets)
+    return sc
+
+
+def soft_gripper_cylinder_reduced(seed: int = 0, n_steps: int = 12, **param_overrides) -> dict:
+    """The soft-gripper squeeze at a resolution the CPU oracle steps in seconds: 3 mm fingertip voxels, a
+    deformable cylinder of radius 15 mm and height 30 mm in 3.75 mm voxels (E = 5e4 Pa, nu = 0.4) on the
+    ground quad, finger bases of about 100 triangles closing 0.3 mm per step for 10 steps, then holding."""
+    sc = soft_gripper_cylinder(seed, n_steps=n_steps, tip_cell=3.0e-3, cyl_cell=3.75e-3, close_per_step=0.3e-3,
+                               cyl_r=15e-3, cyl_h=30e-3, close_steps=10, base_tris=100, **param_overrides)
+    sc["name"] = f"soft_gripper_cylinder_reduced_{len(sc['fem_tets'])}tet"
     return sc

@@ -203,3 +203,33 @@ def test_incremental_potential_fd_with_stitch_springs():
         _, gm, _, _ = S.evaluate(z - e, ctx, want_hess=False)
         col = (gp - gm)[:F] / (2 * h)
         assert np.max(np.abs(col - Hd[:F, i])) <= 1e-6 * np.max(np.abs(Hd[:F, :F]))
+
+
+def test_pair_loops_do_not_depend_on_the_thread_count():
+    """The brute-force pair loops run on OpenMP threads in chunks: pairs, their order, the squared
+    distances, the CCD bound and the candidate count equal those of one thread."""
+    import ctypes as C
+    sc = scenes.fingertip_press(2)
+    S = ipc.Scene(sc)
+    r = np.random.default_rng(7)
+    x = S.positions(S.z0).copy()
+    x[:S.nf, 2] = 0.5e-3 + (x[:S.nf, 2] - 0.5e-3) * 0.96 - 0.35e-3
+    x[:S.nf] += 5e-5 * r.normal(size=(S.nf, 3))
+    x[S.nf + S.na_v + 8:] += np.array([0, 0, -0.45e-3])
+    p = np.zeros_like(x)
+    p[:S.nf] = 1e-3 * r.normal(size=(S.nf, 3)) + np.array([0, 0, -1.5e-3])
+    xf, pf = np.ascontiguousarray(x.reshape(-1)), np.ascontiguousarray(p.reshape(-1))
+    out = []
+    for nth in (1, 5):
+        ipc.set_threads(nth)
+        try:
+            rec, s = S.active_pairs(xf)
+            nc = C.c_int()
+            a = ipc.lib().orc_ccd_alpha(C.byref(S.surf), ipc._d(xf), ipc._d(pf), S.s_ccd, ipc.ACCD_MAX_ITER,
+                                        C.byref(nc))
+        finally:
+            ipc.set_threads(0)
+        out.append((rec, s, a, nc.value))
+    assert len(out[0][0]) > 20
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
