@@ -162,6 +162,33 @@ ipc_status sim_create(const ipc_scene_desc* desc, const ipc_params* params, void
  * layout.  Gravity is taken from the first scene. */
 ipc_status sim_create_batch(const ipc_scene_desc* descs, int n, const ipc_params* params, void* stream, ipcsim** out);
 
+/* Device-memory hook (not part of the paper's method: it lets a host
+ * framework own the simulator's device memory, e.g. PyTorch's caching
+ * allocator).  alloc returns `bytes` of device memory of the current device
+ * for use on `stream` (the simulator's stream), or NULL on failure; free
+ * returns a block alloc gave, with the same stream (work already queued on it
+ * may still read the block, so a caching allocator must order its reuse after
+ * that work, as stream-ordered allocators do).  ctx is passed through. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} ipc_allocator;
+
+/* sim_create (n == 1) or sim_create_batch (n > 1) with every device buffer
+ * of the simulator taken from `allocator` (required) instead of cudaMalloc:
+ * the scene data, the state, the work buffers, the contact-pair and
+ * candidate lists (which grow on demand during sim_step), the BVHs and the
+ * PCG buffers.  Blocks are given back when a list grows and at sim_destroy.
+ * Pinned host staging buffers still come from cudaMallocHost.  The
+ * allocator must stay valid until sim_destroy. */
+ipc_status sim_create_with_allocator(const ipc_scene_desc* descs, int n, const ipc_params* params,
+                                     const ipc_allocator* allocator, void* stream, ipcsim** out);
+
+/* Device memory accounting: out3 = [blocks taken from the caller's
+ * allocator, blocks taken by cudaMalloc, bytes held now]. */
+ipc_status sim_memory(const ipcsim* sim, long long* out3);
+
 /* Advance one time step (Eq. 3).  kin_T_next_host: (n_kin, 12) transforms of
  * the kinematic bodies at t+1 (may be NULL when n_kin == 0).  stats_host may
  * be NULL.  Synchronises the stream once per Newton iteration to read the
@@ -216,10 +243,10 @@ ipc_status sim_set_params(ipcsim* sim, const double* logE_host, double mu);
  * by FP64 PCG (relative residual 1e-12; IPC_ERR_PCG if H is not positive
  * definite there) and writes gz_t_dev = dL/dz_t and gzd_t_dev = dL/dzd_t
  * (overwritten), adds dL/dlogE into glogE_dev (n_tets, may be NULL) and
- * dL/dmu into *gmu_host (may be NULL).  The friction lag (normal forces,
- * normals and closest points at x_t) is held fixed: its own dependence on
- * x_t is not differentiated (exact when mu = 0).  Uses the simulator's work
- * buffers; the simulator's state is not changed. */
+ * dL/dmu into *gmu_host (may be NULL).  dL/dz_t includes the dependence of
+ * the lagged friction data (normal forces, normals and closest-point weights,
+ * all computed at x_t) on x_t.  Uses the simulator's work buffers; the
+ * simulator's state is not changed. */
 ipc_status sim_adjoint(ipcsim* sim, const double* z_t_dev, const double* zd_t_dev, const double* z_next_dev,
                        const double* kin_T_t_host, const double* kin_T_next_host, const double* gz_next_dev,
                        const double* gzd_next_dev, double* gz_t_dev, double* gzd_t_dev, double* glogE_dev,
@@ -248,7 +275,8 @@ ipc_status sim_pcg_residency(ipcsim* sim, int streamed);
 /* Per-stage timing with CUDA events recorded on the simulator's stream
  * around each stage of sim_step (cheap; intervals are read at the
  * synchronisation points sim_step already has).  enable == 1 starts (and
- * clears) accounting, enable == 2 resumes it without clearing, 0 pauses it; sim_profile_read returns accumulated milliseconds and
+ * clears) accounting, enable == 2 resumes it without clearing, 0 pauses it
+ * (keeping what was accumulated); sim_profile_read returns accumulated milliseconds and
  * interval counts per stage [PCG, elastic, barrier, culling, CCD, friction,
  * other, PCG setup (incidence lists, FP32 copies, operator layout)] and work4
  * = [PCG iterations, sum over iterations of barrier

@@ -759,8 +759,107 @@ def set_material(o: "Oracle", logE=None, mu=None):
 
 def step_context(S, z_t, zd_t, step_next):
     x_t = S.positions(z_t)
-    return dict(z_tilde=z_t + S.dt * zd_t + S.dt * S.dt * S.grav_acc, x_t=x_t,
-                lag=S.friction_lag(x_t.reshape(-1)) if S.mu_f > 0 else [], stitch_hat=S.stitch_targets(step_next))
+    ctx = dict(z_tilde=z_t + S.dt * zd_t + S.dt * S.dt * S.grav_acc, x_t=x_t, lag=[], lag_kind=[], lag_eps_x=[],
+               stitch_hat=S.stitch_targets(step_next))
+    if S.mu_f > 0:
+        rec, _ = S.active_pairs(x_t.reshape(-1))
+        ctx["lag"] = S.friction_lag(x_t.reshape(-1))
+        ctx["lag_kind"] = [int(k) for k in rec[:, 0]]
+        ctx["lag_eps_x"] = list(S.eps_x(rec))
+    return ctx
+
+
+def _free_weight_directions(kind, type_):
+    """Directions (4, k) along which the closest-point weights of a distance type move: w = w0 + B theta
+    with theta the type's free parameters (segment or barycentric coordinates); k = 0 for point-point."""
+    if kind == 0:
+        if type_ <= 2:
+            return np.zeros((4, 0))
+        if type_ <= 5:  # point against edge (t_k, t_k+1): w = e_p - (1 - t) e_k - t e_k+1
+            k = type_ - 3
+            B = np.zeros((4, 1))
+            B[1 + k, 0], B[1 + (k + 1) % 3, 0] = 1.0, -1.0
+            return B
+        return np.array([[0.0, 0.0], [1.0, 1.0], [-1.0, 0.0], [0.0, -1.0]])  # w = [1, -(1-b1-b2), -b1, -b2]
+    if type_ <= 3:
+        return np.zeros((4, 0))
+    if type_ <= 5:  # a point of edge b against edge a: w = [(1 - t), t, -1 (at that point)]
+        return np.array([[-1.0], [1.0], [0.0], [0.0]])
+    if type_ <= 7:  # a point of edge a against edge b: w = [1 (at that point), -(1 - t), -t]
+        return np.array([[0.0], [0.0], [1.0], [-1.0]])
+    return np.array([[-1.0, 0.0], [1.0, 0.0], [0.0, 1.0], [0.0, -1.0]])  # line-line (s, t)
+
+
+def friction_lag_jacobian(S, kind, xs, eps_x):
+    """The lagged friction data of one pair at x_t (Eq. 3, E_friction) and their derivatives with respect
+    to the pair's four positions at x_t (12 columns).
+
+    lambda = -kappa m 2 d b'(s) (s = d^2 the squared distance, m the edge-edge mollifier); n = v / d with
+    v = sum_q w_q x_q the vector between the closest points; w the closest-point weights.  Within one
+    distance type the weights minimise |V w|^2 over w = w0 + B theta (V the 3x4 matrix of positions), so
+    with A = V B the optimality condition A^T v = 0 gives, for a change dV,
+    d theta = -(A^T A)^-1 (dA^T v + A^T dV w)."""
+    xs = _f64(xs).reshape(4, 3)
+    t, s, w = classify(kind, xs)
+    _, gs, _ = (pt_dist if kind == 0 else ee_dist)(xs, t)
+    d = math.sqrt(s)
+    v = (w[:, None] * xs).sum(0)
+    n = v / d
+    _, b1, b2 = barrier(s, S.sh)
+    if kind == 1:
+        m, gm, _ = ee_mollifier(xs, eps_x)
+    else:
+        m, gm = 1.0, np.zeros(12)
+    lam = -S.kappa * m * 2.0 * d * b1
+    dlam = -S.kappa * (2.0 * d * b1 * gm + m * (b1 / d + 2.0 * d * b2) * gs)
+    B = _free_weight_directions(kind, t)
+    dw = np.zeros((4, 12))
+    if B.shape[1]:
+        A = xs.T @ B
+        G = A.T @ A
+        for j in range(4):
+            for dd in range(3):
+                rhs = B[j, :] * v[dd] + A[dd, :] * w[j]
+                dw[:, 3 * j + dd] = B @ (-np.linalg.solve(G, rhs))
+    dv = np.zeros((3, 12))
+    for j in range(4):
+        for dd in range(3):
+            dv[dd, 3 * j + dd] += w[j]
+    dv += xs.T @ dw
+    dn = (np.eye(3) - np.outer(n, n)) @ dv / d
+    return dict(type=t, w=w, n=n, lam=lam, dw=dw, dn=dn, dlam=dlam)
+
+
+def friction_lag_adjoint(S, ctx, x, lv):
+    """The part of dL/dx_t that flows through the lagged friction data (lambda_k, n_k, w_k at x_t), in
+    vertex space, for the vertex-space adjoint lv of one step.  Per pair
+    Phi = lv . grad_x D = mu lambda phi(r) a^T y,  a = sum_q w_q lv_q,  y = (I - n n^T) u,
+    u = sum_q w_q (x_q - x_t,q),  r = |y|,  phi(r) = f0'(r) / r,
+    and the contribution is -dt^2 dPhi/dx_t through lambda, n and w (the direct dependence of u on x_t is
+    the friction Hessian term of the adjoint)."""
+    out = np.zeros((S.nv, 3))
+    xt = ctx["x_t"]
+    eps = S.eps
+    for (ids, w0, n0, lam0), kind, eps_x in zip(ctx["lag"], ctx["lag_kind"], ctx["lag_eps_x"]):
+        J = friction_lag_jacobian(S, kind, xt[ids], eps_x)
+        w, n, lam = J["w"], J["n"], J["lam"]
+        u = (w[:, None] * (x[ids] - xt[ids])).sum(0)
+        T = np.eye(3) - np.outer(n, n)
+        y = T @ u
+        r = math.sqrt(float(y @ y))
+        phi = (-r / (eps * eps) + 2.0 / eps) if r < eps else 1.0 / r
+        dphi_over_r = ((-1.0 / (eps * eps)) / r if r > 0 else 0.0) if r < eps else -1.0 / (r ** 3)
+        a = (w[:, None] * lv[ids]).sum(0)
+        c2 = S.mu_f * lam * phi
+        c1 = S.mu_f * lam * dphi_over_r * float(a @ y)
+        Phi = c2 * float(a @ y)
+        z = c1 * y + c2 * a
+        g_u = c1 * y + c2 * (T @ a)
+        g_n = -(z * float(n @ u) + u * float(n @ z))
+        dPhi_dw = np.array([c2 * float(y @ lv[ids[q]]) + float(g_u @ (x[ids[q]] - xt[ids[q]])) for q in range(4)])
+        grad = (Phi / lam) * J["dlam"] + g_n @ J["dn"] + dPhi_dw @ J["dw"]
+        np.add.at(out, ids, -S.dt * S.dt * grad.reshape(4, 3))
+    return out
 
 
 def adjoint_step(o: "Oracle", z_t, zd_t, z_next, step_next, gz_next, gzd_next):
@@ -773,8 +872,8 @@ def adjoint_step(o: "Oracle", z_t, zd_t, z_next, step_next, gz_next, gzd_next):
         dL/dz_t = M lam - dL/dzd* / dt + dt^2 H_fric lam,   dL/dzd_t = dt M lam.
     theta = per-tet log E: dg/dlogE_e = dt^2 (gradient of V_e Psi_e), since
     Psi is linear in (mu, lam) and both scale with E; dg/dmu = dt^2 grad D / mu.
-    The friction lag (lambda_k, n_k, w_k computed at x_t) is held fixed: its
-    dependence on x_t is not differentiated (exact when mu = 0).
+    The friction lag (lambda_k, n_k, w_k computed at x_t) depends on x_t too;
+    that dependence is differentiated by friction_lag_adjoint.
     Returns (dL/dz_t, dL/dzd_t, dL/dlogE, dL/dmu) on the free DOFs."""
     S = o.S
     dt = S.dt
@@ -809,6 +908,7 @@ def adjoint_step(o: "Oracle", z_t, zd_t, z_next, step_next, gz_next, gzd_next):
         Hf = sp.csr_matrix((np.concatenate(fr_vals), (np.concatenate(fr_rows), np.concatenate(fr_cols))),
                            shape=(3 * S.nv, 3 * S.nv))
         gz_t = gz_t + dt * dt * (S.Jmap.T @ (Hf @ (S.Jmap @ lam_full)))
+        gz_t = gz_t + S.Jmap.T @ friction_lag_adjoint(S, ctx, x.reshape(-1, 3), lv).reshape(-1)
     gzd_t = dt * (S.M @ lam_full)
     gz_t[S.n_free:] = 0.0
     gzd_t[S.n_free:] = 0.0

@@ -260,38 +260,42 @@ __global__ void k_refit(int n, const int* __restrict__ prim, const double* __res
 // ---------------------------------------------------------------------------
 static int nb(int n, int t) { return (n + t - 1) / t; }
 
-cudaError_t bvh_alloc(Bvh& B, int n) {
-  B.n = n;
-  if (n <= B.cap) return cudaSuccess;
-  cudaFree(B.codes); cudaFree(B.prim); cudaFree(B.codes_tmp); cudaFree(B.prim_tmp);
-  cudaFree(B.left); cudaFree(B.right); cudaFree(B.parent); cudaFree(B.flag); cudaFree(B.box); cudaFree(B.leafbox);
-  cudaFree(B.hist); cudaFree(B.bounds);
-  int c = std::max(n, 1);
-  int nblk = nb(c, SORT_TILE);
-  cudaError_t e = cudaSuccess;
-  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
-  A((void**)&B.codes, sizeof(unsigned) * c);
-  A((void**)&B.prim, sizeof(int) * c);
-  A((void**)&B.codes_tmp, sizeof(unsigned) * c);
-  A((void**)&B.prim_tmp, sizeof(int) * c);
-  A((void**)&B.left, sizeof(int) * c);
-  A((void**)&B.right, sizeof(int) * c);
-  A((void**)&B.parent, sizeof(int) * 2 * c);
-  A((void**)&B.flag, sizeof(int) * c);
-  A((void**)&B.box, sizeof(float) * 6 * 2 * c);
-  A((void**)&B.leafbox, sizeof(double) * 6 * c);
-  A((void**)&B.hist, sizeof(int) * 256 * nblk);
-  A((void**)&B.bounds, sizeof(double) * 6 * (BOUND_BLOCKS + 1));
-  B.cap = c;
-  B.hist_cap = 256 * nblk;
-  return e;
+// Sizes of the arrays of a tree of capacity c (the order of Bvh's pointers).
+static void bvh_sizes(int c, size_t out[12]) {
+  const int nblk = nb(c, SORT_TILE);
+  const size_t sz[12] = {sizeof(unsigned) * c, sizeof(int) * c, sizeof(unsigned) * c, sizeof(int) * c,
+                         sizeof(int) * c, sizeof(int) * c, sizeof(int) * 2 * (size_t)c, sizeof(int) * c,
+                         sizeof(float) * 6 * 2 * (size_t)c, sizeof(double) * 6 * (size_t)c, sizeof(int) * 256 * (size_t)nblk,
+                         sizeof(double) * 6 * (BOUND_BLOCKS + 1)};
+  for (int i = 0; i < 12; ++i) out[i] = sz[i];
 }
 
-void bvh_free(Bvh& B) {
-  cudaFree(B.codes); cudaFree(B.prim); cudaFree(B.codes_tmp); cudaFree(B.prim_tmp);
-  cudaFree(B.left); cudaFree(B.right); cudaFree(B.parent); cudaFree(B.flag); cudaFree(B.box); cudaFree(B.leafbox);
-  cudaFree(B.hist); cudaFree(B.bounds);
+static void** bvh_ptr(Bvh& B, int i) {
+  void** p[12] = {(void**)&B.codes, (void**)&B.prim, (void**)&B.codes_tmp, (void**)&B.prim_tmp, (void**)&B.left,
+                  (void**)&B.right, (void**)&B.parent, (void**)&B.flag, (void**)&B.box, (void**)&B.leafbox,
+                  (void**)&B.hist, (void**)&B.bounds};
+  return p[i];
+}
+
+void bvh_free(Bvh& B, DevAlloc& mem) {
+  size_t sz[12];
+  bvh_sizes(B.cap, sz);
+  for (int i = 0; i < 12; ++i) mem.put(*bvh_ptr(B, i), sz[i]);
   B = Bvh{};
+}
+
+cudaError_t bvh_alloc(Bvh& B, int n, DevAlloc& mem) {
+  if (n <= B.cap && B.codes) { B.n = n; return cudaSuccess; }
+  bvh_free(B, mem);
+  B.n = n;
+  const int c = std::max(n, 1);
+  size_t sz[12];
+  bvh_sizes(c, sz);
+  B.cap = c;
+  B.hist_cap = 256 * nb(c, SORT_TILE);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 12 && e == cudaSuccess; ++i) e = mem.get(bvh_ptr(B, i), sz[i]);
+  return e;
 }
 
 void bvh_leaf_boxes(cudaStream_t st, Bvh& B, const int* ids, int nvp, const double* xv, const double* pv, double pad) {

@@ -483,7 +483,8 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
 // closest-point weights w, unit normal n, normal force lambda = -kappa m 2 d b'(s).
 __global__ void k_friction_lag(DevScene S, const double* __restrict__ xv, const int* __restrict__ rec,
                                const int* __restrict__ n_dev, int cap, double sh, double kappa_unused, int* __restrict__ f_ids,
-                               double* __restrict__ f_w, double* __restrict__ f_n, double* __restrict__ f_lam) {
+                               double* __restrict__ f_w, double* __restrict__ f_n, double* __restrict__ f_lam,
+                               int* __restrict__ f_rec) {
   int n = min(*n_dev, cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int* r = rec + 8 * (size_t)k;
@@ -492,8 +493,8 @@ __global__ void k_friction_lag(DevScene S, const double* __restrict__ xv, const 
     d3 x[4];
     load_stencil(S, xv, r, ids, x);
     double s, w[4];
-    if (kind == 0) pt_classify(x, s, w);
-    else ee_classify(x, s, w);
+    const int type = kind == 0 ? pt_classify(x, s, w) : ee_classify(x, s, w);
+    if (f_rec) { f_rec[4 * k] = kind; f_rec[4 * k + 1] = type; f_rec[4 * k + 2] = r[1]; f_rec[4 * k + 3] = r[2]; }
     const double kappa = S.scene_kappa[scene_of_vertex(S, ids[0])];
     double d = sqrt(s);
     d3 nrm = (1.0 / d) * (w[0] * x[0] + w[1] * x[1] + w[2] * x[2] + w[3] * x[3]);
@@ -503,6 +504,145 @@ __global__ void k_friction_lag(DevScene S, const double* __restrict__ xv, const 
     for (int q = 0; q < 4; ++q) { f_ids[4 * k + q] = ids[q]; f_w[4 * k + q] = w[q]; }
     f_n[3 * k] = nrm.x; f_n[3 * k + 1] = nrm.y; f_n[3 * k + 2] = nrm.z;
     f_lam[k] = -kappa * m * 2.0 * d * b1;
+  }
+}
+
+// Directions (4 slots x k) along which the closest-point weights of a
+// distance type move, w = w0 + B theta (theta: the segment or barycentric
+// coordinates the type leaves free); returns k (0 for point-point).
+__device__ inline int weight_directions(int kind, int type, double B[4][2]) {
+  for (int q = 0; q < 4; ++q) B[q][0] = B[q][1] = 0.0;
+  if (kind == 0) {
+    if (type <= 2) return 0;
+    if (type <= 5) {
+      const int k = type - 3;
+      B[1 + k][0] = 1.0;
+      B[1 + (k + 1) % 3][0] = -1.0;
+      return 1;
+    }
+    B[1][0] = 1.0; B[2][0] = -1.0; B[1][1] = 1.0; B[3][1] = -1.0;
+    return 2;
+  }
+  if (type <= 3) return 0;
+  if (type <= 5) { B[0][0] = -1.0; B[1][0] = 1.0; return 1; }
+  if (type <= 7) { B[2][0] = 1.0; B[3][0] = -1.0; return 1; }
+  B[0][0] = -1.0; B[1][0] = 1.0; B[2][1] = 1.0; B[3][1] = -1.0;
+  return 2;
+}
+
+// The part of the adjoint dL/dx_t that flows through the lagged friction data
+// of every friction pair (normal force lambda, normal n and closest-point
+// weights w, all computed at x_t).  For the adjoint lam (DOF space) of one
+// step, per pair (v_q the vertex-space adjoint of slot q):
+//   Phi = mu lambda phi(r) a.y,  a = sum_q w_q v_q,  y = (I - n n^T) u,
+//   u = sum_q w_q (x_q - xt_q),  r = |y|,  phi(r) = f0'(r) / r,
+// and -scale dPhi/dx_t through lambda, n and w is added into gz (DOF space;
+// kinematic vertices dropped).  Within one distance type the weights
+// minimise |V w|^2 over w = w0 + B theta, so with A = V B and A^T v = 0,
+// dtheta = -(A^T A)^-1 (dA^T v + A^T dV w); lambda = -kappa m 2 d b'(s)
+// through the squared distance s and the edge-edge mollifier m.
+__global__ void k_friction_lag_adjoint(DevScene S, const double* __restrict__ xv, const double* __restrict__ xv_t,
+                                       int n, const int* __restrict__ f_ids, const int* __restrict__ f_rec, double sh,
+                                       double mu, double eps, double scale, const double* __restrict__ lam_dof,
+                                       double* __restrict__ gz) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int kind = f_rec[4 * k], ta = f_rec[4 * k + 2], tb = f_rec[4 * k + 3];
+  int ids[4];
+  d3 x[4], xs[4], vq[4];
+  for (int q = 0; q < 4; ++q) {
+    ids[q] = f_ids[4 * k + q];
+    x[q] = ld3(xv_t, ids[q]);
+    xs[q] = ld3(xv, ids[q]);
+    const NodeMap m = vertex_nodes(S, ids[q]);
+    d3 a = mk(0, 0, 0);
+    for (int r = 0; r < m.n; ++r) a = a + m.w[r] * ld3(lam_dof, m.node[r]);
+    vq[q] = a;
+  }
+  double s, w[4];
+  const int type = kind == 0 ? pt_classify(x, s, w) : ee_classify(x, s, w);
+  // gradient of the squared distance of this type at x_t
+  double gs[12];
+  {
+    Red R;
+    double s2;
+    dist_reduced(kind, type, x, R, s2);
+    red_expand(R, gs, nullptr);
+  }
+  const double d = sqrt(s);
+  const d3 v = w[0] * x[0] + w[1] * x[1] + w[2] * x[2] + w[3] * x[3];
+  const d3 nrm = (1.0 / d) * v;
+  double b, b1, b2;
+  barrier_fn(s, sh, b, b1, b2);
+  double m = 1.0, gm[12];
+  for (int i = 0; i < 12; ++i) gm[i] = 0.0;
+  if (kind == 1) m = mollifier(x, 1e-3 * S.edge_rest_sq[ta] * S.edge_rest_sq[tb], gm, nullptr);
+  const double kappa = S.scene_kappa[scene_of_vertex(S, ids[0])];
+  const double lam = -kappa * m * 2.0 * d * b1;
+  // friction state at x*
+  d3 u = mk(0, 0, 0), Delta[4];
+  for (int q = 0; q < 4; ++q) {
+    Delta[q] = xs[q] - x[q];
+    u = u + w[q] * Delta[q];
+  }
+  const d3 y = u - dot(nrm, u) * nrm;
+  const double r = sqrt(dot(y, y));
+  const double phi = r < eps ? (-r / (eps * eps) + 2.0 / eps) : 1.0 / r;
+  const double dphi_r = r < eps ? (r > 0.0 ? (-1.0 / (eps * eps)) / r : 0.0) : -1.0 / (r * r * r);
+  const d3 a = w[0] * vq[0] + w[1] * vq[1] + w[2] * vq[2] + w[3] * vq[3];
+  const double ay = dot(a, y);
+  const double c2 = mu * lam * phi, c1 = mu * lam * dphi_r * ay;
+  const double phi_over_lam = mu * phi * ay;  // Phi / lambda
+  const d3 zc = c1 * y + c2 * a;
+  const d3 Ta = a - dot(nrm, a) * nrm;
+  const d3 g_u = c1 * y + c2 * Ta;
+  const double nu = dot(nrm, u), nz = dot(nrm, zc);
+  const d3 g_n = -1.0 * (nu * zc + nz * u);
+  double dPhi_dw[4];
+  for (int q = 0; q < 4; ++q) dPhi_dw[q] = c2 * dot(y, vq[q]) + dot(g_u, Delta[q]);
+  // weight derivatives: dw[q][col] for the 12 position components of x_t
+  double Bm[4][2];
+  const int nf = weight_directions(kind, type, Bm);
+  double A[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int c = 0; c < nf; ++c) {
+    d3 acol = Bm[0][c] * x[0] + Bm[1][c] * x[1] + Bm[2][c] * x[2] + Bm[3][c] * x[3];
+    A[0][c] = acol.x; A[1][c] = acol.y; A[2][c] = acol.z;
+  }
+  double Gi[2][2] = {{0, 0}, {0, 0}};
+  if (nf == 1) {
+    Gi[0][0] = 1.0 / (A[0][0] * A[0][0] + A[1][0] * A[1][0] + A[2][0] * A[2][0]);
+  } else if (nf == 2) {
+    const double g00 = A[0][0] * A[0][0] + A[1][0] * A[1][0] + A[2][0] * A[2][0];
+    const double g01 = A[0][0] * A[0][1] + A[1][0] * A[1][1] + A[2][0] * A[2][1];
+    const double g11 = A[0][1] * A[0][1] + A[1][1] * A[1][1] + A[2][1] * A[2][1];
+    const double det = g00 * g11 - g01 * g01;
+    Gi[0][0] = g11 / det; Gi[0][1] = -g01 / det; Gi[1][0] = -g01 / det; Gi[1][1] = g00 / det;
+  }
+  const double vv[3] = {v.x, v.y, v.z};
+  double grad[12];
+  for (int j = 0; j < 4; ++j)
+    for (int dd = 0; dd < 3; ++dd) {
+      const int col = 3 * j + dd;
+      // dw[:, col] = B dtheta, dtheta = -(A^T A)^-1 (B_j v_dd + A_dd w_j)
+      double dw[4] = {0, 0, 0, 0};
+      if (nf) {
+        double rhs[2] = {0, 0}, dth[2] = {0, 0};
+        for (int c = 0; c < nf; ++c) rhs[c] = Bm[j][c] * vv[dd] + A[dd][c] * w[j];
+        for (int c = 0; c < nf; ++c) dth[c] = -(Gi[c][0] * rhs[0] + Gi[c][1] * rhs[1]);
+        for (int q = 0; q < 4; ++q) dw[q] = Bm[q][0] * dth[0] + Bm[q][1] * dth[1];
+      }
+      // dv[:, col] = e_dd w_j + sum_q x_q dw_q;  dn = (I - n n^T) dv / d
+      d3 dv = dw[0] * x[0] + dw[1] * x[1] + dw[2] * x[2] + dw[3] * x[3];
+      if (dd == 0) dv.x += w[j]; else if (dd == 1) dv.y += w[j]; else dv.z += w[j];
+      const d3 dn = (1.0 / d) * (dv - dot(nrm, dv) * nrm);
+      const double dlam = -kappa * (2.0 * d * b1 * gm[col] + m * (b1 / d + 2.0 * d * b2) * gs[col]);
+      grad[col] = phi_over_lam * dlam + dot(g_n, dn) +
+                  dPhi_dw[0] * dw[0] + dPhi_dw[1] * dw[1] + dPhi_dw[2] * dw[2] + dPhi_dw[3] * dw[3];
+    }
+  for (int q = 0; q < 4; ++q) {
+    const NodeMap mq = vertex_nodes(S, ids[q]);
+    for (int rr = 0; rr < mq.n; ++rr)
+      for (int c = 0; c < 3; ++c) atomicAdd(gz + 3 * mq.node[rr] + c, -scale * mq.w[rr] * grad[3 * q + c]);
   }
 }
 
@@ -608,8 +748,16 @@ void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* 
   count_launch();
 }
 void launch_friction_lag(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
-                         int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam) {
-  k_friction_lag<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, f_ids, f_w, f_n, f_lam);
+                         int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam,
+                         int* f_rec) {
+  k_friction_lag<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, f_ids, f_w, f_n, f_lam, f_rec);
+  count_launch();
+}
+void launch_friction_lag_adjoint(cudaStream_t st, const DevScene& S, const double* xv, const double* xv_t, int n,
+                                 const int* f_ids, const int* f_rec, double sh, double mu, double eps, double scale,
+                                 const double* lam_dof, double* gz) {
+  if (n <= 0) return;
+  k_friction_lag_adjoint<<<(n + 63) / 64, 64, 0, st>>>(S, xv, xv_t, n, f_ids, f_rec, sh, mu, eps, scale, lam_dof, gz);
   count_launch();
 }
 void launch_friction(cudaStream_t st, const DevScene& S, const double* xv, const double* xv_t, int n, const int* f_ids,

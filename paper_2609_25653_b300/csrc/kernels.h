@@ -7,6 +7,36 @@
 
 namespace ipc {
 
+// Device memory of one simulator: from the caller's allocator when one was
+// given at creation (e.g. PyTorch's caching allocator), else from cudaMalloc.
+struct DevAlloc {
+  void* (*alloc_fn)(size_t, void*, void*) = nullptr;
+  void (*free_fn)(void*, void*, void*) = nullptr;
+  void* ctx = nullptr;
+  cudaStream_t st = nullptr;
+  long long by_allocator = 0, direct = 0, bytes = 0;
+  cudaError_t get(void** p, size_t nbytes) {
+    *p = nullptr;
+    if (alloc_fn) {
+      *p = alloc_fn(nbytes, (void*)st, ctx);
+      if (!*p) return cudaErrorMemoryAllocation;
+      ++by_allocator;
+    } else {
+      cudaError_t e = cudaMalloc(p, nbytes);
+      if (e != cudaSuccess) return e;
+      ++direct;
+    }
+    bytes += (long long)nbytes;
+    return cudaSuccess;
+  }
+  void put(void* p, size_t nbytes) {
+    if (!p) return;
+    if (free_fn) free_fn(p, (void*)st, ctx);
+    else cudaFree(p);
+    bytes -= (long long)nbytes;
+  }
+};
+
 // Streaming multiprocessors of the current device (looked up once per device).
 int device_sms();
 // Blocks of a grid-stride launch over n items, `per_block` items per block and
@@ -131,8 +161,14 @@ void launch_sub(cudaStream_t, int n, const double* a, const double* b, double* o
 void launch_barrier(cudaStream_t, int grid, const DevScene&, const double* xv, const int* rec, const int* n_dev, int cap,
                     double sh, double kappa, double scale, int mode, int project, double* g, double* pairH, double* Dc,
                     const double* pD, double* gdir, double* E, unsigned long long* min_s, int hess_fp32 = 0);
+// f_rec (may be null): (kind, type, primitive a, primitive b) of every friction pair, for the adjoint
 void launch_friction_lag(cudaStream_t, int grid, const DevScene&, const double* xv, const int* rec, const int* n_dev,
-                         int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam);
+                         int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam,
+                         int* f_rec = nullptr);
+// adjoint: -scale d(lam . grad D)/dx_t through the lagged friction data, added into gz (DOF space)
+void launch_friction_lag_adjoint(cudaStream_t, const DevScene&, const double* xv, const double* xv_t, int n,
+                                 const int* f_ids, const int* f_rec, double sh, double mu, double eps, double scale,
+                                 const double* lam_dof, double* gz);
 void launch_friction(cudaStream_t, const DevScene&, const double* xv, const double* xv_t, int n, const int* f_ids,
                      const double* f_w, const double* f_n, const double* f_lam, double mu, double eps, double scale,
                      int mode, double* g, double* f_Hu, double* Dc, const double* pD, double* gdir, double* E);
@@ -144,8 +180,8 @@ void launch_ccd_brute(cudaStream_t, const DevScene&, const double* xv, const dou
                       unsigned long long* alpha_bits, int* n_cand);
 
 // bvh.cu
-cudaError_t bvh_alloc(Bvh& B, int n);
-void bvh_free(Bvh& B);
+cudaError_t bvh_alloc(Bvh& B, int n, DevAlloc& mem);
+void bvh_free(Bvh& B, DevAlloc& mem);
 void bvh_leaf_boxes(cudaStream_t, Bvh& B, const int* ids, int nvp, const double* xv, const double* pv, double pad);
 void bvh_refit(cudaStream_t, Bvh& B);
 void bvh_build(cudaStream_t, Bvh& B);

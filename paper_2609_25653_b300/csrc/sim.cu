@@ -39,7 +39,8 @@ struct ipcsim {
   ipc_params P{};
   cudaStream_t st = nullptr;
   std::string err;
-  std::vector<void*> allocs;
+  DevAlloc mem;                                   // the caller's allocator, or cudaMalloc
+  std::vector<std::pair<void*, size_t>> allocs;   // every device block this simulator holds
 
   // host copies
   int nf = 0, nt = 0, nab = 0, nkb = 0, nv = 0, na_v = 0, nk = 0, n_nodes = 0, nbody = 0;
@@ -107,6 +108,7 @@ struct ipcsim {
   bool cand_valid = false;
   int fcap = 0, n_fric = 0;
   int* f_ids = nullptr;
+  int* f_rec = nullptr;        // (kind, type, primitive a, primitive b) of every friction pair (adjoint)
   double *f_w = nullptr, *f_n = nullptr, *f_lam = nullptr, *f_Hu = nullptr;
   // scalars (device) and pinned host mirror
   struct Scal {
@@ -172,22 +174,28 @@ template <typename T>
 ipc_status dalloc(ipcsim* sim, T** ptr, size_t count) {
   void* p = nullptr;
   size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = sim->mem.get(&p, bytes);
   if (e != cudaSuccess) {
-    sim->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    sim->err = std::string(sim->mem.alloc_fn ? "device allocator: " : "cudaMalloc: ") + cudaGetErrorString(e) +
+               " (" + std::to_string(bytes) + " bytes)";
     return IPC_ERR_CUDA;
   }
   cudaMemsetAsync(p, 0, bytes, sim->st);
-  sim->allocs.push_back(p);
+  sim->allocs.push_back({p, bytes});
   *ptr = (T*)p;
   return IPC_OK;
 }
 
 void dfree(ipcsim* sim, void* p) {
   if (!p) return;
-  auto it = std::find(sim->allocs.begin(), sim->allocs.end(), p);
-  if (it != sim->allocs.end()) sim->allocs.erase(it);
-  cudaFree(p);
+  for (auto it = sim->allocs.begin(); it != sim->allocs.end(); ++it)
+    if (it->first == p) {
+      // the block may still be read by work queued on the stream: a caching allocator that reuses it
+      // for the same stream orders the reuse after that work; cudaFree synchronises
+      sim->mem.put(p, it->second);
+      sim->allocs.erase(it);
+      return;
+    }
 }
 
 template <typename T>
@@ -315,8 +323,10 @@ ipc_status grow_fric(ipcsim* sim, int need) {
   }
   int ncap = (int)std::min<long long>(std::max<long long>(need + (long long)need / 2, 1024), lim);
   dfree(sim, sim->f_ids); dfree(sim, sim->f_w); dfree(sim, sim->f_n); dfree(sim, sim->f_lam); dfree(sim, sim->f_Hu);
+  dfree(sim, sim->f_rec);
   ipc_status s;
   if ((s = dalloc(sim, &sim->f_ids, (size_t)4 * ncap))) return s;
+  if ((s = dalloc(sim, &sim->f_rec, (size_t)4 * ncap))) return s;
   if ((s = dalloc(sim, &sim->f_w, (size_t)4 * ncap))) return s;
   if ((s = dalloc(sim, &sim->f_n, (size_t)3 * ncap))) return s;
   if ((s = dalloc(sim, &sim->f_lam, (size_t)ncap))) return s;
@@ -676,9 +686,10 @@ const char* sim_last_error(const ipcsim* sim) { return sim ? sim->err.c_str() : 
 void sim_destroy(ipcsim* sim) {
   if (!sim) return;
   if (sim->st) cudaStreamSynchronize(sim->st);
-  for (void* p : sim->allocs) cudaFree(p);
-  bvh_free(sim->tri_tree);
-  bvh_free(sim->edge_tree);
+  for (auto& a : sim->allocs) sim->mem.put(a.first, a.second);
+  sim->allocs.clear();
+  bvh_free(sim->tri_tree, sim->mem);
+  bvh_free(sim->edge_tree, sim->mem);
   for (auto& e : sim->ev)
     if (e) cudaEventDestroy(e);
   if (sim->sc_host) cudaFreeHost(sim->sc_host);
@@ -690,14 +701,25 @@ void sim_destroy(ipcsim* sim) {
 // Build a simulator for the scene D.  For a batch, D is the concatenation of
 // n_scenes independent scenes and tet_scene / abd_scene / kin_scene give the
 // scene of every tet, ABD body and kinematic body (NULL: all scene 0).
-static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params, void* stream, ipcsim** out,
-                              int n_scenes, const int* tet_scene, const int* abd_scene, const int* kin_scene) {
+static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params, const ipc_allocator* A, void* stream,
+                              ipcsim** out, int n_scenes, const int* tet_scene, const int* abd_scene,
+                              const int* kin_scene) {
   if (!out) return IPC_ERR_ARG;
   *out = nullptr;
   if (!D || !params) return IPC_ERR_ARG;
+  if (A && (!A->alloc || !A->free)) {
+    g_create_error = "allocator needs both alloc and free";
+    return IPC_ERR_ARG;
+  }
   ipcsim* sim = new ipcsim();
   sim->P = *params;
   sim->st = (cudaStream_t)stream;
+  sim->mem.st = sim->st;
+  if (A) {
+    sim->mem.alloc_fn = A->alloc;
+    sim->mem.free_fn = A->free;
+    sim->mem.ctx = A->ctx;
+  }
   auto fail = [&](ipc_status s, const std::string& msg) {
     if (!msg.empty()) sim->err = msg;
     g_create_error = sim->err;
@@ -1129,7 +1151,7 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   // broad phase: leaf boxes widened by slightly more than dhat, so that every
   // pair closer than dhat overlaps despite rounding of the widened bounds
   sim->bvh_pad = P.dhat * (1.0 + 1e-6);
-  if (bvh_alloc(sim->tri_tree, S.ntri) != cudaSuccess || bvh_alloc(sim->edge_tree, S.nedge) != cudaSuccess)
+  if (bvh_alloc(sim->tri_tree, S.ntri, sim->mem) != cudaSuccess || bvh_alloc(sim->edge_tree, S.nedge, sim->mem) != cudaSuccess)
     return fail(IPC_ERR_CUDA, "BVH allocation failed");
   // initial state must be intersection free: no pair at zero distance
   launch_vertex_positions(sim->st, S, sim->z, sim->xk, sim->xv);
@@ -1156,10 +1178,33 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
 }
 
 ipc_status sim_create(const ipc_scene_desc* D, const ipc_params* params, void* stream, ipcsim** out) {
-  return create_impl(D, params, stream, out, 1, nullptr, nullptr, nullptr);
+  return create_impl(D, params, nullptr, stream, out, 1, nullptr, nullptr, nullptr);
 }
 
+static ipc_status batch_impl(const ipc_scene_desc* descs, int n, const ipc_params* params, const ipc_allocator* A,
+                             void* stream, ipcsim** out);
+
 ipc_status sim_create_batch(const ipc_scene_desc* descs, int n, const ipc_params* params, void* stream, ipcsim** out) {
+  return batch_impl(descs, n, params, nullptr, stream, out);
+}
+
+ipc_status sim_create_with_allocator(const ipc_scene_desc* descs, int n, const ipc_params* params,
+                                     const ipc_allocator* allocator, void* stream, ipcsim** out) {
+  if (!allocator) return IPC_ERR_ARG;
+  if (n == 1) return create_impl(descs, params, allocator, stream, out, 1, nullptr, nullptr, nullptr);
+  return batch_impl(descs, n, params, allocator, stream, out);
+}
+
+ipc_status sim_memory(const ipcsim* sim, long long* out3) {
+  if (!sim || !out3) return IPC_ERR_ARG;
+  out3[0] = sim->mem.by_allocator;
+  out3[1] = sim->mem.direct;
+  out3[2] = sim->mem.bytes;
+  return IPC_OK;
+}
+
+static ipc_status batch_impl(const ipc_scene_desc* descs, int n, const ipc_params* params, const ipc_allocator* A,
+                             void* stream, ipcsim** out) {
   if (!out) return IPC_ERR_ARG;
   *out = nullptr;
   if (!descs || n <= 0 || !params) return IPC_ERR_ARG;
@@ -1251,7 +1296,7 @@ ipc_status sim_create_batch(const ipc_scene_desc* descs, int n, const ipc_params
   M.stitch_b_host = stb.data();
   M.stitch_X_host = stX.data();
   for (int d = 0; d < 3; ++d) M.gravity[d] = descs[0].gravity[d];
-  return create_impl(&M, params, stream, out, n, tet_scene.data(), abd_scene.data(), kin_scene.data());
+  return create_impl(&M, params, A, stream, out, n, tet_scene.data(), abd_scene.data(), kin_scene.data());
 }
 
 ipc_status sim_sizes(const ipcsim* sim, int* o) {
@@ -1708,7 +1753,7 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     int n = sim->sc_host->n_pairs;
     if (n > sim->fcap && (s = grow_fric(sim, n))) return s;
     launch_friction_lag(cs, pair_grid(sim->cap), S, sim->xv_t, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
-                        sim->kappa, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam);
+                        sim->kappa, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, sim->f_rec);
     sim->n_fric = n;
   }
   // unprojected Hessian at z*
@@ -1768,7 +1813,12 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   }
   launch_mass_apply(cs, S, sim->p, dt, tmp, gzd_t);
   launch_axpy(cs, ndof, tmp, -1.0 / dt, gzd_next, gz_t);
-  if (P.mu > 0) launch_friction_apply(cs, S, sim->n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->p, gz_t);
+  if (P.mu > 0) {
+    launch_friction_apply(cs, S, sim->n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->p, gz_t);
+    // through the lagged normal forces, normals and closest points at x_t
+    launch_friction_lag_adjoint(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_rec, sim->sh, P.mu,
+                                P.eps_v * dt, dt2, sim->p, gz_t);
+  }
   if ((s = sync_scalars(sim))) return s;
   CUDA_TRY(cudaGetLastError());
   if (sim->sc_host->pcg_out[1] == 3 && !(sim->sc_host->pcg_res <= 1e-10)) {
@@ -1808,7 +1858,7 @@ ipc_status sim_pcg_residency(ipcsim* sim, int streamed) {
 ipc_status sim_profile(ipcsim* sim, int enable) {
   if (!sim) return IPC_ERR_ARG;
   sim->prof = enable != 0;
-  if (enable == 2) return IPC_OK;  // resume: keep what has been accumulated
+  if (enable != 1) return IPC_OK;  // pause (0) or resume (2): keep what has been accumulated
   for (int k = 0; k < 8; ++k) { sim->prof_ms[k] = 0; sim->prof_n[k] = 0; sim->ev_open[k] = false; }
   sim->pcg_iters_acc = sim->pcg_pair_iters_acc = sim->pcg_fric_iters_acc = 0;
   return IPC_OK;

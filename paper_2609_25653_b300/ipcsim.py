@@ -48,6 +48,46 @@ class Params(C.Structure):
                 ("pair_capacity_max", C.c_int)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class TorchAllocator:
+    """The simulator's device memory from PyTorch's caching allocator (sim_create_with_allocator).
+
+    Keeps the ctypes callbacks alive for the simulator's lifetime and counts the calls."""
+
+    def __init__(self):
+        import torch
+        self.allocs = 0
+        self.frees = 0
+        self.live = {}
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                dev = torch.cuda.current_device()
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+            except Exception:
+                return None
+            self.allocs += 1
+            self.live[p] = nbytes
+            return p
+
+        def _free(ptr, stream, ctx):
+            if ptr:
+                self.frees += 1
+                self.live.pop(ptr, None)
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc = ALLOC_FN(_alloc)
+        self._free = FREE_FN(_free)
+        self.struct = Allocator(self._alloc, self._free, None)
+
+
 class StepStats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
                 ("pcg_iters_max", C.c_int), ("n_pairs_max", C.c_int), ("n_friction_pairs", C.c_int),
@@ -89,6 +129,9 @@ SIGNATURES = {
     "sim_pcg_partition": ([ip, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip, ip, ip, ip, ip], C.c_int),
     "sim_pcg_residency": ([vp, C.c_int], C.c_int),
     "sim_device_peaks": ([dp], C.c_int),
+    "sim_create_with_allocator": ([C.POINTER(SceneDesc), C.c_int, C.POINTER(Params), C.POINTER(Allocator), vp,
+                                   C.POINTER(vp)], C.c_int),
+    "sim_memory": ([vp, C.POINTER(C.c_longlong)], C.c_int),
 }
 
 PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "pcg_setup"]
@@ -235,7 +278,7 @@ def batch_scene(scenes):
 class Simulator:
     """One scene on the GPU.  `scene` is a dictionary from paper_2609_25653_b300.scenes."""
 
-    def __init__(self, scene: dict, precision=PREC_FP64, stream=None, _batch=None, **param_overrides):
+    def __init__(self, scene: dict, precision=PREC_FP64, stream=None, _batch=None, allocator=None, **param_overrides):
         L = load()
         self.scene = scene
         p = dict(scene["params"])
@@ -249,7 +292,11 @@ class Simulator:
         par = make_params(p, precision)
         h = C.c_void_p()
         st = C.c_void_p(stream.cuda_stream if stream is not None else 0)
-        if _batch is None:
+        self.allocator = allocator  # kept alive with the simulator
+        if allocator is not None:
+            code = L.sim_create_with_allocator(descs, len(scenes), C.byref(par), C.byref(allocator.struct), st,
+                                               C.byref(h))
+        elif _batch is None:
             code = L.sim_create(C.byref(descs[0]), C.byref(par), st, C.byref(h))
         else:
             code = L.sim_create_batch(descs, len(scenes), C.byref(par), st, C.byref(h))
@@ -379,6 +426,12 @@ class Simulator:
         ms = (C.c_float * 8)()
         self._check(load().sim_tuning(self.h, int(rowg), int(blocks_per_sm), int(bool(autotune_next_step)), out, ms))
         return (out[0], out[1]), list(ms)
+
+    def memory(self):
+        """(blocks from the caller's allocator, blocks from cudaMalloc, bytes held)."""
+        out = (C.c_longlong * 3)()
+        self._check(load().sim_memory(self.h, out))
+        return tuple(out)
 
     def pcg_residency(self, streamed: bool):
         """streamed=True: the PCG reads its operator from global memory in every iteration (never staged in

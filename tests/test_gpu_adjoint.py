@@ -78,3 +78,48 @@ def test_adjoint_fd_16_directions():
         ad = float(g @ d)
         worst = max(worst, abs(fd - ad) / max(abs(fd), 1e-30))
     assert worst < 1e-4, worst
+
+
+def test_adjoint_rollout_fd_with_friction():
+    """A 3-step rollout with friction (mu = 0.5): gradients with respect to the initial positions (which
+    move the lagged normal forces, normals and closest points of every step), the friction coefficient and
+    ln E against central differences of the GPU forward."""
+    from paper_2609_25653_b300 import autograd
+    sc = scenes.fingertip_press(0, n_steps=4, mu=0.5, **TIGHT)
+    sim = _sim(sc)
+    z0, zd0 = sim.get_dofs()
+    logE0 = torch.tensor(sc["fem_logE"], dtype=torch.float64)
+    r = np.random.default_rng(5)
+    target = {}
+
+    def loss(logE, mu, z_init):
+        traj = autograd.rollout(sim, logE, mu, 3, z_init, zd0)
+        if "t" not in target:
+            target["t"] = (traj[-1] + 1e-4 * torch.as_tensor(r.normal(size=traj[-1].shape), device="cuda")).detach()
+        return 0.5 * torch.sum((traj[-1] - target["t"]) ** 2)
+
+    logE = logE0.clone().requires_grad_(True)
+    mu = torch.tensor(0.5, dtype=torch.float64, requires_grad=True)
+    zi = z0.clone().requires_grad_(True)
+    L = loss(logE, mu, zi)
+    L.backward()
+    g_logE, g_mu, g_z = logE.grad.numpy(), mu.grad.item(), zi.grad.cpu().numpy()
+    worst = 0.0
+    with torch.no_grad():
+        for k in range(3):
+            d = r.normal(size=g_z.shape)
+            d[3 * sim.nf:] = 0.0
+            h = 1e-9
+            dz = torch.as_tensor(h * d, device="cuda")
+            fd = (loss(logE0, 0.5, z0 + dz).item() - loss(logE0, 0.5, z0 - dz).item()) / (2 * h)
+            worst = max(worst, abs(fd - g_z @ d) / max(abs(fd), 1e-30))
+        h = 1e-6
+        fd = (loss(logE0, 0.5 + h, z0).item() - loss(logE0, 0.5 - h, z0).item()) / (2 * h)
+        worst = max(worst, abs(fd - g_mu) / abs(fd))
+        for k in range(4):
+            d = r.normal(size=g_logE.shape)
+            h = 1e-4
+            dl = torch.as_tensor(h * d)
+            fd = (loss(logE0 + dl, 0.5, z0).item() - loss(logE0 - dl, 0.5, z0).item()) / (2 * h)
+            worst = max(worst, abs(fd - g_logE @ d) / max(abs(fd), 1e-30))
+    assert worst < 1e-4, worst

@@ -70,7 +70,7 @@ def test_pair_capacity_limit_fails_and_restores_state():
     """A pair buffer limit below what the step needs: IPC_ERR_CAPACITY, state at x_t."""
     from oracle import ipc as orc
     from paper_2609_25653_b300 import ipcsim
-    sc = scenes.fingertip_press(0, n_steps=6)
+    sc = scenes.abd_box_drop(n_steps=6)  # the box lands during the first step: more pairs than at x0
     ref = _sim(sc)
     S = orc.Scene(sc)
     x0 = torch.as_tensor(np.ascontiguousarray(S.positions(S.z0)), device="cuda")

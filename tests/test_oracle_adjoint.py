@@ -46,9 +46,13 @@ def test_adjoint_matches_central_differences(mu):
         h = 1e-6
         fd = (loss(_run(mu + h)) - loss(_run(mu - h))) / (2 * h)
         assert abs(fd - dmu) <= 1e-4 * abs(fd)
-    else:
-        # initial position: exact without friction (the friction lag is held fixed otherwise)
+    # initial position and velocity (with friction, through the lagged normal forces, normals and
+    # closest points at x_t as well)
+    for _ in range(2):
         d = r.normal(size=z_t.shape); d[nF:] = 0
         h = 1e-9
         fd = (loss(_run(mu, None, z_t + h * d, zd_t)) - loss(_run(mu, None, z_t - h * d, zd_t))) / (2 * h)
-        assert abs(fd - gz_t @ d) <= 1e-4 * abs(fd)
+        assert abs(fd - gz_t @ d) <= 1e-4 * abs(fd), (fd, gz_t @ d)
+        h = 1e-7
+        fd = (loss(_run(mu, None, z_t, zd_t + h * d)) - loss(_run(mu, None, z_t, zd_t - h * d))) / (2 * h)
+        assert abs(fd - gzd_t @ d) <= 1e-4 * abs(fd), (fd, gzd_t @ d)
