@@ -397,6 +397,81 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_material_id(args):
+    """Differentiable material identification at full size (about 100k tets): a forward rollout of
+    `--id-steps` steps with per-tet ln E and mu as parameters, the loss sum_t 1/2 |x_t - x*_t|^2 against a
+    target trajectory simulated with hidden parameters, its backward through the implicit adjoint of every
+    step (timed: adjoint ms/step), and the gradient against central differences of the GPU forward on 16
+    random parameter directions over the first `--fd-steps` steps."""
+    import numpy as np
+    import torch
+    from paper_2609_25653_b300 import autograd, ipcsim, scenes
+    torch.cuda.set_device(0)
+    n = args.id_steps
+    sc = scenes.material_identification(0, n_steps=max(n, args.fd_steps) + 1)
+    sim = ipcsim.Simulator(sc)
+    z0, zd0 = sim.get_dofs()
+    logE0 = torch.tensor(sc["fem_logE"], dtype=torch.float64)
+    hidden = torch.tensor(sc["hidden_logE"], dtype=torch.float64)
+    t0 = time.perf_counter()
+    with torch.no_grad():
+        target = [t.detach() for t in autograd.rollout(sim, hidden, sc["hidden_mu"], n, z0, zd0)]
+    t_target = time.perf_counter() - t0
+
+    def loss_of(traj):
+        return sum(0.5 * torch.sum((x - t) ** 2) for x, t in zip(traj, target))
+
+    logE = logE0.clone().requires_grad_(True)
+    mu = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    traj = autograd.rollout(sim, logE, mu, n, z0, zd0)
+    L = loss_of(traj)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    L.backward()
+    e1.record()
+    e1.synchronize()
+    adj_ms = e0.elapsed_time(e1) / n
+    # central differences over the first fd_steps steps, 16 random directions (ln E: 14, mu: 2)
+    m = args.fd_steps
+
+    def loss_short(le, mu_v):
+        with torch.no_grad():
+            tr = autograd.rollout(sim, le, mu_v, m, z0, zd0)
+            return float(sum(0.5 * torch.sum((x - t) ** 2) for x, t in zip(tr, target[:m])))
+
+    le = logE0.clone().requires_grad_(True)
+    muv = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+    Ls = sum(0.5 * torch.sum((x - t) ** 2) for x, t in
+                             zip(autograd.rollout(sim, le, muv, m, z0, zd0), target[:m]))
+    Ls.backward()
+    g_le, g_mu = le.grad.numpy(), float(muv.grad)
+    r = np.random.default_rng(2)
+    errs = []
+    for k in range(16):
+        if k < 14:
+            d = r.normal(size=g_le.shape)
+            d /= np.linalg.norm(d)
+            h = 1e-4
+            fd = (loss_short(logE0 + h * torch.as_tensor(d), 0.6) - loss_short(logE0 - h * torch.as_tensor(d), 0.6)) / (2 * h)
+            ad = float(g_le @ d)
+        else:
+            h = 1e-5
+            fd = (loss_short(logE0, 0.6 + h) - loss_short(logE0, 0.6 - h)) / (2 * h)
+            ad = g_mu
+        errs.append(abs(fd - ad) / max(abs(fd), 1e-300))
+    line = {"workload": sc["name"], "fem_tets": len(sc["fem_tets"]), "steps": n, "precision": "fp64",
+            "adjoint_ms_per_step": round(adj_ms, 3), "forward_ms_per_step": round(1e3 * t_fwd / n, 3),
+            "target_forward_s": round(t_target, 2), "loss": float(L),
+            "fd_check": {"directions": 16, "steps": m, "max_rel_err": float(max(errs)),
+                         "rel_errs": [float("%.3g" % e) for e in errs]},
+            "grad_norm_logE": float(np.linalg.norm(logE.grad.numpy())), "grad_mu": float(mu.grad)}
+    print(json.dumps(line))
+
+
 def shard_scenes(scenes_list, rank, world):
     """Scenes of rank `rank` out of `world` (round robin: r, r + N, ...); every rank keeps at least one."""
     mine = scenes_list[rank::world]
@@ -569,6 +644,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default PCG launch shape")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ms/step measurement")
+    ap.add_argument("--id-steps", type=int, default=100, help="material_id workload: rollout steps")
+    ap.add_argument("--fd-steps", type=int, default=10, help="material_id workload: steps of the FD check")
     ap.add_argument("--sample", choices=["trajectory", "consecutive"], default="trajectory",
                     help="time K steps spread over the whole trajectory (default) or the K steps after the warm-up")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
@@ -578,6 +655,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "material_id":
+        run_material_id(args)
     else:
         run_ours(args)
 

@@ -114,7 +114,18 @@ typedef struct {
   int broad_phase;    /* IPC_BROAD_LBVH (default) or IPC_BROAD_ALL_PAIRS (every pair tested; for checks) */
   int pair_capacity_max; /* largest contact-pair buffer (pairs) the simulator grows to; a step that needs
                             more fails with IPC_ERR_CAPACITY; <= 0: 2^23 */
+  int preconditioner; /* IPC_PRECOND_TWO_LEVEL (default) or IPC_PRECOND_BLOCK_JACOBI */
 } ipc_params;
+
+/* PCG preconditioners (the paper names StiffGIPC's solver without its
+ * details; both are this library's).  Block Jacobi: the inverse 3x3 diagonal
+ * blocks.  Two-level: block Jacobi plus a coarse correction
+ * P (P^T A P)^-1 P^T whose columns are the rigid-body motions (3
+ * translations, 3 rotations about the centre) of every FEM row segment of
+ * the PCG launch; P^T A P is assembled and inverted once per step, at the
+ * first Newton iteration.  Number FEM vertices in spatial order (e.g. Morton
+ * order) so that row segments are compact clusters. */
+enum { IPC_PRECOND_TWO_LEVEL = 0, IPC_PRECOND_BLOCK_JACOBI = 1 };
 
 enum { IPC_BROAD_LBVH = 0, IPC_BROAD_ALL_PAIRS = 1 };
 
@@ -137,13 +148,19 @@ typedef struct {
   int pad_;
 } ipc_step_stats;
 
-/* Build a simulator.  Validates the scene (IPC_ERR_INVERTED for a rest tet
+/* Build a simulator of the scene the paper's physics layer simulates
+ * (§III-C.1: FEM soft bodies, ABD rigid bodies, IPC contact; Eqs. 1-2: the
+ * fingertips coupled to the gripper by stitch springs; §III-C.2: arm links
+ * driven along the planned motion).  Validates the scene (IPC_ERR_INVERTED for a rest tet
  * with det(Dm) <= 0), prepares rest shapes, masses, the BSR pattern and the
  * contact surfaces on the host, uploads them, and allocates device memory
  * with cudaMalloc.  stream: a cudaStream_t (NULL = legacy default stream). */
 ipc_status sim_create(const ipc_scene_desc* desc, const ipc_params* params, void* stream, ipcsim** out);
 
-/* Batched data generation: one simulator for n independent scenes.  The
+/* Batched data generation (the paper's pipeline generates many simulated
+ * demonstrations, Fig. 2 and §III-C.3; running several independent scenes
+ * in one simulator is this library's, the paper does not describe it): one
+ * simulator for n independent scenes.  The
  * scenes are concatenated (FEM vertices, tets, ABD bodies, kinematic bodies
  * and stitch springs in scene order, ids shifted accordingly); pairs between
  * different scenes are never formed; every scene keeps its own barrier and
@@ -195,7 +212,8 @@ ipc_status sim_memory(const ipcsim* sim, long long* out3);
  * convergence data and returns when the step is done. */
 ipc_status sim_step(ipcsim* sim, const double* kin_T_next_host, ipc_step_stats* stats_host);
 
-/* Advance n independent simulators by one step each, concurrently: every
+/* Advance n independent simulators by one step each (Eq. 3 for each; the
+ * concurrency is this library's, not described in the paper), concurrently: every
  * simulator runs its own Newton loop (its own convergence, step lengths and
  * line search) on its own stream, driven from its own host thread, so the
  * kernels of different scenes overlap on the GPU.  Simulators must be
@@ -207,12 +225,14 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next_host, ipc_step_stats* 
 ipc_status sim_step_many(ipcsim* const* sims, int n, const double* const* kin_T_next_host, ipc_step_stats* stats_host,
                          ipc_status* status_host);
 
-/* Copy the state out: FEM positions and velocities (n_fem_verts, 3) and ABD
+/* The simulated part of the trajectory record of Eq. 4 (X_deform, the
+ * deformable positions; T_rigid, the affine bodies' q).  Copy the state out: FEM positions and velocities (n_fem_verts, 3) and ABD
  * q / qdot (n_abd, 12).  Any pointer may be NULL.  `on_device` != 0 means the
  * pointers are device pointers, else host pointers.  Synchronous. */
 ipc_status sim_get_state(const ipcsim* sim, double* x, double* v, double* abd_q, double* abd_qd, int on_device);
 
-/* Overwrite the state (same layouts).  Kinematic bodies keep their pose. */
+/* Overwrite the state (same layouts; e.g. to restart a rollout of Eq. 3 from
+ * a recorded step).  Kinematic bodies keep their pose. */
 ipc_status sim_set_state(ipcsim* sim, const double* x, const double* v, const double* abd_q, const double* abd_qd,
                          int on_device);
 
@@ -220,21 +240,30 @@ ipc_status sim_set_state(ipcsim* sim, const double* x, const double* v, const do
  * n_surface_verts, n_nodes, bsr_blocks] written to out9. */
 ipc_status sim_sizes(const ipcsim* sim, int* out9);
 
-/* Derived scalars fixed at create: [kappa, k_c, L_bbox, dhat]. */
+/* Derived scalars fixed at create: [kappa, k_c, L_bbox, dhat] (kappa: the
+ * barrier stiffness of E_barrier in Eq. 3; k_c: the stitch stiffness of
+ * Eq. 2; both auto-scaled when the parameters leave them 0, the paper gives
+ * no values). */
 ipc_status sim_scalars(const ipcsim* sim, double* out4);
 
-/* Place the kinematic bodies at the given transforms (host, (n_kin, 12)),
+/* Place the kinematic bodies (the arm links and finger bases that follow the
+ * planned motion of §III-C.2; T_link of Eq. 4) at the given transforms (host, (n_kin, 12)),
  * e.g. to restart a trajectory from an earlier step together with
  * sim_set_state. */
 ipc_status sim_set_kinematic(ipcsim* sim, const double* kin_T_host);
 
-/* Material and friction parameters for the following steps (the parameters
+/* Material and friction parameters (§III-C.1 specifies the FEM material by
+ * Young's modulus and Poisson ratio; mu is the friction coefficient of
+ * E_friction in Eq. 3) for the following steps (the parameters
  * the adjoint differentiates): per-tet ln Young's modulus (n_tets host
  * doubles, or NULL to keep) and the friction coefficient (mu < 0 keeps it).
  * The barrier stiffness and stitch stiffness fixed at create do not change. */
 ipc_status sim_set_params(ipcsim* sim, const double* logE_host, double mu);
 
-/* Implicit adjoint of one step (implicit function theorem).  Given the
+/* Implicit adjoint of one step (implicit function theorem applied to the
+ * minimisation of Eq. 3; the paper's simulator is not differentiated, this
+ * is an extension for identifying material and friction parameters from
+ * trajectories).  Given the
  * state at t (z_t_dev, zd_t_dev: DOF vectors (n_nodes, 3), FEM vertices then
  * ABD pseudo-nodes), the converged state z_next_dev of the step t -> t+1, the
  * kinematic transforms at t and t+1 (host, (n_kin, 12)) and the loss
@@ -252,7 +281,9 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t_dev, const double* zd_t_de
                        const double* gzd_next_dev, double* gz_t_dev, double* gzd_t_dev, double* glogE_dev,
                        double* gmu_host);
 
-/* Launch shape of the cooperative PCG: threads per FEM row (rowg = 1, 2, 4
+/* Launch shape of the cooperative PCG (the linear solve inside every Newton
+ * iteration of Eq. 3's minimisation; the paper names StiffGIPC's solver
+ * without its parallel layout, this is the library's): threads per FEM row (rowg = 1, 2, 4
  * or 8; <= 0 keeps the current value) and CTAs per SM (1 to 4; <= 0 keeps;
  * fewer are launched when the kernel cannot keep that many resident).  With
  * autotune_next_step != 0 the next sim_step times every shape (2 x 4) on its
@@ -272,7 +303,8 @@ ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_nex
  * arithmetic in the same order.  Takes effect at the next solve. */
 ipc_status sim_pcg_residency(ipcsim* sim, int streamed);
 
-/* Per-stage timing with CUDA events recorded on the simulator's stream
+/* Accounting of the library, no counterpart in the paper.  Per-stage timing
+ * with CUDA events recorded on the simulator's stream
  * around each stage of sim_step (cheap; intervals are read at the
  * synchronisation points sim_step already has).  enable == 1 starts (and
  * clears) accounting, enable == 2 resumes it without clearing, 0 pauses it
@@ -311,11 +343,13 @@ ipc_status sim_pcg_partition(const int* row, int nf, int nab, int grid, const in
  * synchronises the device's legacy default stream. */
 ipc_status sim_device_peaks(double* out2);
 
-/* Total number of CUDA kernels this library has launched in this process
+/* Accounting of the library, no counterpart in the paper.  Total number of
+ * CUDA kernels this library has launched in this process
  * (all simulators, all threads), for launch accounting. */
 unsigned long long sim_kernel_launches(void);
 
-/* Reason of the last failure of `sim`; with sim == NULL, of the last failed
+/* Error reporting of the library, no counterpart in the paper.  Reason of the
+ * last failure of `sim`; with sim == NULL, of the last failed
  * sim_create on the calling thread. */
 const char* sim_last_error(const ipcsim* sim);
 void sim_destroy(ipcsim* sim);
@@ -328,14 +362,16 @@ void sim_destroy(ipcsim* sim);
  * body (sim_sizes gives the counts).
  * ---------------------------------------------------------------------- */
 
-/* Elastic energy, gradient (n_fem_verts, 3) and, if H_dev != NULL, the
+/* E_FEM of Eq. 3, the Stable Neo-Hookean energy of §III-C.1.  Elastic energy,
+ * gradient (n_fem_verts, 3) and, if H_dev != NULL, the
  * per-tet 12x12 Hessians (n_tets, 144), PSD-projected when project != 0, at
  * FEM positions x_dev (n_fem_verts, 3).  Energies are V_e Psi (not scaled by
  * dt^2).  E_dev: one double.  grad_dev is overwritten. */
 ipc_status sim_eval_elastic(ipcsim* sim, const double* x_dev, int project, double* E_dev, double* grad_dev,
                             double* H_dev);
 
-/* Active contact pairs at all-vertex positions x_dev: every point-triangle
+/* The contact pairs of IPC (§III-C.1: barrier potentials between primitives
+ * closer than dhat).  Active contact pairs at all-vertex positions x_dev: every point-triangle
  * and edge-edge pair with squared distance < dhat^2 after the exclusion
  * rules.  Records (cap, 8) int32: kind (0 PT / 1 EE), primitive a, primitive b,
  * distance type, 4 vertex ids; s_dev (cap) squared distances.  Writes the
@@ -344,11 +380,13 @@ ipc_status sim_eval_elastic(ipcsim* sim, const double* x_dev, int project, doubl
  * triangles and edges as returned by sim_surface. */
 ipc_status sim_active_pairs(ipcsim* sim, const double* x_dev, int cap, int* rec_dev, double* s_dev, int* n_host);
 
-/* Surface topology (host buffers of sizes from sim_sizes): surface vertex
+/* The contact surfaces of the bodies of §III-C.1.  Surface topology (host
+ * buffers of sizes from sim_sizes): surface vertex
  * ids, triangles (3 ids), edges (2 ids), all in the global vertex order. */
 ipc_status sim_surface(const ipcsim* sim, int* sv_host, int* tris_host, int* edges_host);
 
-/* Barrier energy kappa * sum m_k b(s_k) (not scaled by dt^2), its gradient
+/* E_barrier of Eq. 3 (the log barrier of IPC).  Barrier energy kappa * sum
+ * m_k b(s_k) (not scaled by dt^2), its gradient
  * with respect to the free DOF nodes (n_nodes, 3: FEM vertices, then the 4
  * pseudo-nodes of each ABD body) and the per-pair vertex-space 12x12
  * Hessians (n, 144), PSD-projected when project != 0, of n pair records (as
@@ -378,10 +416,46 @@ ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* 
 ipc_status sim_eval_barrier_noalloc(ipcsim* sim, const double* x_dev, int n, const int* rec_dev, int project,
                                     double* E_dev, double* grad_dev, double* H_dev);
 
-/* Largest step fraction in (0, 1] along the vertex displacement p_dev
+/* The continuous collision detection of §III-C.1 (the guarantee of no
+ * interpenetration).  Largest step fraction in (0, 1] along the vertex displacement p_dev
  * (n_vertices_all, 3) from x_dev: minimum additive-CCD time of impact over
  * all pairs whose swept boxes overlap.  *n_cand_host: candidates tested. */
 ipc_status sim_ccd_alpha(ipcsim* sim, const double* x_dev, const double* p_dev, double* alpha_host, int* n_cand_host);
+
+/* ------------------------------------------------------------------------
+ * Physics-to-render dual-mesh mapping (§III-D.1, Eqs. 5-6): the render mesh
+ * of a deformable body is its simulation surface after L levels of Loop
+ * subdivision, precomputed as one sparse matrix W (N_fine x N_coarse, Eq. 5);
+ * every frame X_f = W X_c (Eq. 6).
+ * ---------------------------------------------------------------------- */
+typedef struct ipc_dual_mesh ipc_dual_mesh;
+
+/* Build W for the coarse triangle mesh tris_host ((n_tris, 3) ids into
+ * n_verts coarse vertices; outward orientation is kept by the subdivision)
+ * and 0 <= levels <= 6 (Loop's rules per level: an interior edge vertex
+ * 3/8 (a + b) + 1/8 (c + d), a boundary edge vertex (a + b) / 2, an old
+ * vertex of valence n (1 - n beta) v + beta sum of neighbours with
+ * beta = (5/8 - (3/8 + cos(2 pi / n) / 4)^2) / n, a boundary vertex
+ * 3/4 v + 1/8 of each boundary neighbour; new vertices follow the old ones,
+ * one per edge in increasing (min id, max id) order).  Host work; with
+ * upload != 0 also one upload of W (CSR: int row offsets, int columns,
+ * double weights) with cudaMalloc (upload == 0: host only, for
+ * sim_dual_mesh_topology; sim_dual_mesh_apply then returns IPC_ERR_ARG).
+ * IPC_ERR_ARG for ids out of range or levels outside [0, 6]. */
+ipc_status sim_dual_mesh_create(const int* tris_host, int n_tris, int n_verts, int levels, int upload,
+                                ipc_dual_mesh** out);
+/* out4 = [N_coarse, N_fine, fine triangles, nonzeros of W]. */
+ipc_status sim_dual_mesh_sizes(const ipc_dual_mesh* m, long long* out4);
+/* Host copies (any may be NULL): fine triangles (fine triangles, 3); W as CSR:
+ * row offsets (N_fine + 1), columns and weights (nonzeros). */
+ipc_status sim_dual_mesh_topology(const ipc_dual_mesh* m, int* fine_tris_host, int* row_host, int* col_host,
+                                  double* val_host);
+/* X_f = W X_c on the device: xc_dev (N_coarse, 3), xf_dev (N_fine, 3),
+ * enqueued on `stream` (a cudaStream_t); does not synchronise. */
+ipc_status sim_dual_mesh_apply(const ipc_dual_mesh* m, const double* xc_dev, double* xf_dev, void* stream);
+/* Reason of the last failed sim_dual_mesh_create on the calling thread. */
+const char* sim_dual_mesh_last_error(void);
+void sim_dual_mesh_destroy(ipc_dual_mesh* m);
 
 #ifdef __cplusplus
 }

@@ -61,6 +61,39 @@ struct __align__(16) PairDesc {
   double xb[4][3];
 };
 
+// Coarse level of the PCG preconditioner (coarse.cu): one aggregate per FEM
+// CTA of the launch (the CTA's row segment), six rigid-body modes each.
+struct CoarseDev {
+  const double* inv = nullptr;    // per solve: dense (P^T A P)^-1, row-major n_s x n_s at off[s]; null: off
+  const float* inv32 = nullptr;   // its FP32 copy (mixed precision)
+  const long long* off = nullptr; // (solves)
+  const int* solve_lo = nullptr;  // (solves) first aggregate of every solve
+  const int* solve_n = nullptr;   // (solves) coarse unknowns of every solve (6 per aggregate)
+  const double* centre = nullptr; // (aggregates, 3)
+  const int* rot = nullptr;       // (aggregates) 1: rotations kept
+  const double* x = nullptr;      // (nf, 3) positions the modes are built at
+  double* part = nullptr;         // (aggregates, 6) P^T v of the vector of the current iteration
+};
+// host-side layout of the coarse level for one PCG plan
+struct CoarseLayout {
+  int n_agg = 0, n_solves = 0, n_max = 0;
+  long long total = 0, total_n = 0;
+  bool consecutive = true;
+  std::vector<int> node_agg, agg_solve, solve_lo, solve_n;
+  std::vector<long long> off, boff;
+};
+// the same on the device
+struct CoarseDevLayout {
+  int n_agg = 0, n_solves = 0, n_max = 0;
+  long long total = 0, total_n = 0;
+  const int* node_agg = nullptr;
+  const int* agg_solve = nullptr;
+  const int* solve_lo = nullptr;
+  const int* solve_n = nullptr;
+  const long long* off = nullptr;
+  const long long* boff = nullptr;
+};
+
 // Arguments of one PCG solve (see pcg.cu).  CTAs [0, n_fem_ctas) own the FEM
 // rows seg_row[c] .. seg_row[c + 1]; the others own ABD bodies
 // b = cta - n_fem_ctas (mod n_abd_ctas).  Pointers of the operator type
@@ -118,6 +151,7 @@ struct PcgArgs {
   const int* scene_skip;     // (n_psc) or null: nonzero = scene not solved (x = 0)
   double* sc_res;            // (n_psc) or null: relative residual of every scene
   int* sc_it;                // (n_psc) or null: iterations of every scene
+  CoarseDev co;              // coarse level of the preconditioner (co.inv null: block Jacobi only)
 };
 
 // Row partition of one PCG launch shape.
@@ -237,6 +271,14 @@ void launch_abd_contact(cudaStream_t, const DevScene& S, const int* rec, const i
                         int* abd_ptr, int* cursor, int* ent, double* entv, long long ent_cap, double* Hval,
                         double* Dc, int* err);
 void launch_to_float(cudaStream_t, size_t n, const double* src, float* dst, const int* n_dev = nullptr, int stride = 0);
+
+// coarse.cu: layout of the coarse level for a plan, and its build (aggregate centres, Galerkin matrix
+// P^T A P per solve, Gauss-Jordan inversion); status (solves): nonzero where a pivot failed
+void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L);
+cudaError_t launch_coarse_build(cudaStream_t, const DevScene& S, const CoarseDevLayout& D, const int* seg,
+                                const double* x, const double* val, const int* rec, const int* n_pairs, int cap,
+                                const double* pairH, int n_fric, const int* f_ids, const double* f_w,
+                                const double* f_Hu, double* Ac, double* centre, int* rot, double* gj_buf, int* status);
 
 // conservative-advancement iterations per CCD candidate
 constexpr int ACCD_MAX_ITER = 10000;

@@ -481,6 +481,7 @@ struct Shared {
   double red[8][12];                // per-warp sums of the ABD rows
   double out[12];                   // results, read by every thread
   double scal[4];                   // scalars of an iteration (the scene's decision thread -> all)
+  double co_a[6], co_b[6];          // coarse images of the CTA's aggregate (FP64: of w and z; mixed: of r and s)
   int action;
   unsigned long long agg[4];        // end of the solve: maxima over the scenes
 };
@@ -587,6 +588,73 @@ __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] 
 }
 __device__ inline double scene_total(const PcgArgs& a, const Shared& sh, int j, int sc) {
   return a.n_psc == 1 ? sh.out[j] : sh.tot[j][sc];
+}
+
+// ---------------------------------------------------------------------------
+// Coarse level (coarse.cu builds it): the aggregate of a FEM CTA is its row
+// segment; P_i = [I | -[x_i - c]x] maps the aggregate's 6 rigid-body
+// coordinates to node i.
+// ---------------------------------------------------------------------------
+// P^T v over this CTA's rows r0..r1, v_i from get(i, v0, v1, v2), into
+// co.part[6 agg ..] (agg < 0: nothing).  Every thread of the CTA must call it.
+template <typename G>
+__device__ inline void coarse_restrict(const PcgArgs& a, int agg, int r0, int r1, Shared& sh, G&& get) {
+  double t[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
+  if (agg >= 0) {
+    const d3 c = ld3(a.co.centre, agg);
+    const bool rot = a.co.rot[agg] != 0;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      double v0, v1, v2;
+      get(i, v0, v1, v2);
+      t[0] += v0; t[1] += v1; t[2] += v2;
+      if (rot) {
+        const d3 r = ld3(a.co.x, i) - c;
+        q[0] = fma(r.y, v2, fma(-r.z, v1, q[0]));
+        q[1] = fma(r.z, v0, fma(-r.x, v2, q[1]));
+        q[2] = fma(r.x, v1, fma(-r.y, v0, q[2]));
+      }
+    }
+  }
+  cta_sum<3, double>(t, sh);
+  if (threadIdx.x < 3 && agg >= 0) a.co.part[6 * (size_t)agg + threadIdx.x] = sh.out[threadIdx.x];
+  __syncthreads();
+  cta_sum<3, double>(q, sh);
+  if (threadIdx.x < 3 && agg >= 0) a.co.part[6 * (size_t)agg + 3 + threadIdx.x] = sh.out[threadIdx.x];
+  __syncthreads();
+}
+
+// The rows of the coarse inverse that belong to aggregate agg (solve s) times
+// the solve's restricted vector co.part: 6 values into res (every thread).
+// Products in the stored precision M of the inverse.  Every thread must call it.
+template <typename M>
+__device__ inline void coarse_own(const PcgArgs& a, const M* inv, int agg, int s, Shared& sh, double res[6]) {
+  M acc[6] = {M(0), M(0), M(0), M(0), M(0), M(0)};
+  if (agg >= 0 && s >= 0) {
+    const int n = a.co.solve_n[s], lo = a.co.solve_lo[s];
+    const M* R = inv + a.co.off[s] + (size_t)6 * (agg - lo) * n;
+    const double* v = a.co.part + 6 * (size_t)lo;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const M vj = (M)v[j];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] = fma(R[(size_t)k * n + j], vj, acc[k]);
+    }
+  }
+  const double t0[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+  cta_sum<3, double>(t0, sh);
+  res[0] = sh.out[0]; res[1] = sh.out[1]; res[2] = sh.out[2];
+  __syncthreads();
+  const double t1[3] = {(double)acc[3], (double)acc[4], (double)acc[5]};
+  cta_sum<3, double>(t1, sh);
+  res[3] = sh.out[0]; res[4] = sh.out[1]; res[5] = sh.out[2];
+  __syncthreads();
+}
+
+// P_i c: translation plus rotation theta x (x_i - centre) of node i's aggregate
+__device__ inline d3 coarse_prolong(const PcgArgs& a, int agg, int i, const double* c) {
+  const d3 r = ld3(a.co.x, i) - ld3(a.co.centre, agg);
+  d3 o = mk(c[0], c[1], c[2]);
+  if (a.co.rot[agg]) o = o + mk(c[4] * r.z - c[5] * r.y, c[5] * r.x - c[3] * r.z, c[3] * r.y - c[4] * r.x);
+  return o;
 }
 
 // End of a solve: CTA 0 reports the iterations, worst status, restarts and
@@ -818,6 +886,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   }
   // preconditioner block of node i (owned by this CTA)
   auto Dof = [&](int i) -> const M* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvM + 9 * (size_t)i); };
+  // coarse level: this CTA's aggregate (its FEM rows), -1 without one
+  const bool coarse = a.co.inv != nullptr;
+  const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? cta : -1;
 
   Vecs<double> V;
   {
@@ -929,28 +1000,61 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     if (on) {
       const double sg = sh.scal[3];
       for_nodes([&](int i, const double*) {
-        double rv[3];
         for (int c = 0; c < 3; ++c) {
           const int q = 3 * i + c;
-          rv[c] = sg * t64[q];
-          V.r[q] = rv[c];
+          V.r[q] = sg * t64[q];
           V.z[q] = 0.0; V.q[q] = 0.0; V.s[q] = 0.0; V.p[q] = 0.0;
         }
+      });
+    }
+    // coarse image of r (its restriction must be complete before any CTA applies the inverse)
+    double cr[6] = {0, 0, 0, 0, 0, 0};
+    if (coarse) {
+      __syncthreads();
+      if (on) coarse_restrict(a, my_agg, r0, r1, sh, [&](int i, double& v0, double& v1, double& v2) {
+        v0 = V.r[3 * i]; v1 = V.r[3 * i + 1]; v2 = V.r[3 * i + 2];
+      });
+      grid.sync();
+      if (on) coarse_own<double>(a, a.co.inv, my_agg, my_sc, sh, cr);
+    }
+    if (on) {
+      for_nodes([&](int i, const double*) {
+        const int q = 3 * i;
         double u0, u1, u2;
-        apply3<M, double>(Dof(i), rv[0], rv[1], rv[2], u0, u1, u2);
-        V.u[3 * i] = u0; V.u[3 * i + 1] = u1; V.u[3 * i + 2] = u2;
+        apply3<M, double>(Dof(i), V.r[q], V.r[q + 1], V.r[q + 2], u0, u1, u2);
+        if (my_agg >= 0) {
+          const d3 cc = coarse_prolong(a, my_agg, i, cr);
+          u0 += cc.x; u1 += cc.y; u2 += cc.z;
+        }
+        V.u[q] = u0; V.u[q + 1] = u1; V.u[q + 2] = u2;
       });
     }
     grid.sync();
+    if (on) products(false, op, colp, rowp, M(0), pairH, fHu, V.u);
+    double cwv[6] = {0, 0, 0, 0, 0, 0};
+    if (coarse) {
+      // coarse image of w = A u: c_w = A_c^-1 P^T w, c_z = 0
+      if (on) coarse_restrict(a, my_agg, r0, r1, sh, [&](int i, double& v0, double& v1, double& v2) {
+        const double* y = acc + 3 * (i - r0);
+        v0 = y[0]; v1 = y[1]; v2 = y[2];
+      });
+      grid.sync();
+      if (on) coarse_own<double>(a, a.co.inv, my_agg, my_sc, sh, cwv);
+      if (on && threadIdx.x < 6) { sh.co_a[threadIdx.x] = cwv[threadIdx.x]; sh.co_b[threadIdx.x] = 0.0; }
+      __syncthreads();
+    }
     if (on) {
       double* mdst = par ? V.m1 : V.m0;
-      products(false, op, colp, rowp, M(0), pairH, fHu, V.u);
       double pv[3] = {0.0, 0.0, 0.0};
       for_nodes([&](int i, const double* y) {
         const int q = 3 * i;
         V.w[q] = y[0]; V.w[q + 1] = y[1]; V.w[q + 2] = y[2];
         double m0, m1, m2;
         apply3<M, double>(Dof(i), y[0], y[1], y[2], m0, m1, m2);
+        if (my_agg >= 0) {
+          const d3 cc = coarse_prolong(a, my_agg, i, cwv);
+          m0 += cc.x; m1 += cc.y; m2 += cc.z;
+        }
         mdst[q] = m0; mdst[q + 1] = m1; mdst[q + 2] = m2;
         const double u0 = V.u[q], u1 = V.u[q + 1], u2 = V.u[q + 2];
         const double rr0 = V.r[q], rr1 = V.r[q + 1], rr2 = V.r[q + 2];
@@ -974,6 +1078,12 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     Partials<double> P;
     if (a.n_psc == 1) load_partials<double>(rep, nblk, P);
     if (my_run) products(false, op, colp, rowp, M(0), pairH, fHu, mcur);
+    // coarse restriction of n = A m (read by every CTA of the solve after the coarse barrier below)
+    if (coarse && my_run)
+      coarse_restrict(a, my_agg, r0, r1, sh, [&](int i, double& v0, double& v1, double& v2) {
+        const double* y = acc + 3 * (i - r0);
+        v0 = y[0]; v1 = y[1]; v2 = y[2];
+      });
     scene_totals<3, double>(a, rep, nblk, sh, a.n_psc == 1 ? &P : nullptr);
     // the scalar recurrences of every scene (identical inputs in every CTA, identical results); the
     // CTA's own scene reaches its threads through shared memory
@@ -1015,6 +1125,25 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     const int my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
     const double alpha = sh.scal[0], beta = sh.scal[1], ax = sh.scal[2];
     if (!any_live) break;
+    // coarse images: c_z = A_c^-1 P^T n + beta c_z, c_w = c_w - alpha c_z (the recurrences of z and w)
+    double cwv[6] = {0, 0, 0, 0, 0, 0};
+    if (coarse) {
+      grid.sync();
+      if (my_act == ACT_STEP) {
+        double eta[6];
+        coarse_own<double>(a, a.co.inv, my_agg, my_sc, sh, eta);
+        for (int k = 0; k < 6; ++k) {
+          const double cz = fma(beta, sh.co_b[k], eta[k]);
+          cwv[k] = fma(-alpha, cz, sh.co_a[k]);
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+          sh.co_b[threadIdx.x] = fma(beta, sh.co_b[threadIdx.x], eta[threadIdx.x]);
+          sh.co_a[threadIdx.x] = cwv[threadIdx.x];
+        }
+        __syncthreads();
+      }
+    }
     if (my_act == ACT_STEP) {
       // every recurrence of the owned nodes, one thread per node
       double pv[3] = {0.0, 0.0, 0.0};
@@ -1045,6 +1174,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         }
         double m0, m1, m2;
         apply3<M, double>(Dof(i), wn[0], wn[1], wn[2], m0, m1, m2);
+        if (my_agg >= 0) {
+          const d3 cc = coarse_prolong(a, my_agg, i, cwv);
+          m0 += cc.x; m1 += cc.y; m2 += cc.z;
+        }
         mnext[3 * i] = m0; mnext[3 * i + 1] = m1; mnext[3 * i + 2] = m2;
         pv[0] += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
         pv[1] += wn[0] * un[0] + wn[1] * un[1] + wn[2] * un[2];
@@ -1158,6 +1291,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     if (!pcg_ok(a, ab0 >= 0 && ab0 <= ab1 && ab1 <= S.nab, 13)) ab0 = ab1 = 0;
   }
   auto Dof = [&](int i) -> const F* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvF + 9 * (size_t)i); };
+  // coarse level: this CTA's aggregate (its FEM rows), -1 without one; applied in FP32
+  const bool coarse = a.co.inv32 != nullptr;
+  const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? cta : -1;
 
   F* base = (F*)a.vec;
   F* r = base;
@@ -1269,25 +1405,50 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   // inner solve start of this CTA's scene: r = sigma t64, u = M^-1 r, p = s = d = 0, and the
   // CTA's parts of (r, u), (r, r)
   F g_l = F(0), rr_l = F(0);
-  auto init_inner = [&]() {
+  // every CTA must call it (the coarse level takes a grid barrier); `on`: this CTA's scene starts an
+  // inner solve
+  auto init_inner = [&](bool on) {
     const double sigma = sh.scal[3];
-    g_l = F(0);
-    rr_l = F(0);
-    for_nodes([&](int i, int) {
-      F rv[3], uv[3];
-      for (int c = 0; c < 3; ++c) {
-        const int q = 3 * i + c;
-        rv[c] = (F)(sigma * t64[q]);
-        r[q] = rv[c];
-        pv_[q] = F(0); sv[q] = F(0); xi[q] = F(0);
+    if (on) {
+      g_l = F(0);
+      rr_l = F(0);
+    }
+    if (on)
+      for_nodes([&](int i, int) {
+        for (int c = 0; c < 3; ++c) {
+          const int q = 3 * i + c;
+          r[q] = (F)(sigma * t64[q]);
+          pv_[q] = F(0); sv[q] = F(0); xi[q] = F(0);
+        }
+      });
+    // coarse image of r: c_r = A_c^-1 P^T r, c_s = 0
+    double cr[6] = {0, 0, 0, 0, 0, 0};
+    if (coarse) {
+      __syncthreads();
+      if (on) coarse_restrict(a, my_agg, r0, r1, sh, [&](int i, double& v0, double& v1, double& v2) {
+        v0 = r[3 * i]; v1 = r[3 * i + 1]; v2 = r[3 * i + 2];
+      });
+      grid.sync();
+      if (on) {
+        coarse_own<F>(a, a.co.inv32, my_agg, my_sc, sh, cr);
+        if (threadIdx.x < 6) { sh.co_a[threadIdx.x] = cr[threadIdx.x]; sh.co_b[threadIdx.x] = 0.0; }
+        __syncthreads();
       }
-      apply3<F, F>(Dof(i), rv[0], rv[1], rv[2], uv[0], uv[1], uv[2]);
-      for (int c = 0; c < 3; ++c) u[3 * i + c] = uv[c];
-      g_l += rv[0] * uv[0] + rv[1] * uv[1] + rv[2] * uv[2];
-      rr_l += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-    });
+    }
+    if (on)
+      for_nodes([&](int i, int) {
+        F rv[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]}, uv[3];
+        apply3<F, F>(Dof(i), rv[0], rv[1], rv[2], uv[0], uv[1], uv[2]);
+        if (my_agg >= 0) {
+          const d3 cc = coarse_prolong(a, my_agg, i, cr);
+          uv[0] += (F)cc.x; uv[1] += (F)cc.y; uv[2] += (F)cc.z;
+        }
+        for (int c = 0; c < 3; ++c) u[3 * i + c] = uv[c];
+        g_l += rv[0] * uv[0] + rv[1] * uv[1] + rv[2] * uv[2];
+        rr_l += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+      });
   };
-  if (my_run) init_inner();
+  init_inner(my_run);
   grid.sync();
 
   enum { ACT_IDLE = 0, ACT_STEP = 1, ACT_END = 2 };
@@ -1305,6 +1466,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       });
       const F pl[3] = {g_l, d_l, rr_l};
       write_partials<F>(partF + (size_t)par * 3 * nblk, repT, nblk, sh, pl);
+      // coarse restriction of w = A u (read by every CTA of the solve after the barrier)
+      if (coarse)
+        coarse_restrict(a, my_agg, r0, r1, sh, [&](int i, double& v0, double& v1, double& v2) {
+          v0 = w[3 * i]; v1 = w[3 * i + 1]; v2 = w[3 * i + 2];
+        });
     }
     grid.sync();
     // phase B: totals, the scalars of every scene, vector updates
@@ -1345,6 +1511,22 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     const int my_act = my_sc >= 0 ? sh.action : ACT_IDLE;
     const F alpha = (F)sh.scal[0], beta = (F)sh.scal[1];
     if (!any_live) break;
+    // coarse images: c_s = A_c^-1 P^T w + beta c_s, c_r = c_r - alpha c_s (the recurrences of s and r)
+    double crv[6] = {0, 0, 0, 0, 0, 0};
+    if (coarse && my_act == ACT_STEP) {
+      double eta[6];
+      coarse_own<F>(a, a.co.inv32, my_agg, my_sc, sh, eta);
+      for (int k = 0; k < 6; ++k) {
+        const F cs = fmaf(beta, (F)sh.co_b[k], (F)eta[k]);
+        crv[k] = (double)fmaf(-alpha, cs, (F)sh.co_a[k]);
+      }
+      __syncthreads();
+      if (threadIdx.x < 6) {
+        sh.co_b[threadIdx.x] = (double)fmaf(beta, (F)sh.co_b[threadIdx.x], (F)eta[threadIdx.x]);
+        sh.co_a[threadIdx.x] = crv[threadIdx.x];
+      }
+      __syncthreads();
+    }
     if (my_act == ACT_STEP) {
       g_l = F(0);
       rr_l = F(0);
@@ -1368,6 +1550,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
         }
         F un[3];
         apply3<F, F>(Dof(i), rn[0], rn[1], rn[2], un[0], un[1], un[2]);
+        if (my_agg >= 0) {
+          const d3 cc = coarse_prolong(a, my_agg, i, crv);
+          un[0] += (F)cc.x; un[1] += (F)cc.y; un[2] += (F)cc.z;
+        }
         for (int c = 0; c < 3; ++c) u[3 * i + c] = un[c];
         g_l += rn[0] * un[0] + rn[1] * un[1] + rn[2] * un[2];
         rr_l += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
@@ -1413,7 +1599,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       __syncthreads();
       my_again = fin && sh.action;
       __syncthreads();
-      if (my_again) init_inner();
+      init_inner(my_again);
     }
     grid.sync();
     my_run = my_act == ACT_STEP || my_again;

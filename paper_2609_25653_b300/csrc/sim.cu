@@ -151,6 +151,21 @@ struct ipcsim {
   // broad phase
   Bvh tri_tree, edge_tree;
   double bvh_pad = 0;
+  // coarse level of the PCG preconditioner (two-level additive Schwarz)
+  CoarseLayout co;
+  int co_plan_stamp = -1;        // plan_stamp the layout was made for
+  int plan_stamp = 0;            // incremented whenever pcg_prepare makes a new plan
+  bool co_ok = false;            // the last build succeeded (else block Jacobi only)
+  bool co_built_this_step = false;
+  int *co_node_agg = nullptr, *co_agg_solve = nullptr, *co_solve_lo = nullptr, *co_solve_n = nullptr;
+  int* co_rot = nullptr;
+  int* co_status = nullptr;
+  long long *co_off = nullptr, *co_boff = nullptr;
+  double *co_Ac = nullptr, *co_centre = nullptr, *co_x = nullptr, *co_part = nullptr, *co_gj = nullptr;
+  float* co_Ac32 = nullptr;
+  long long co_cap = 0, co_cap_n = 0;
+  int co_cap_agg = 0, co_cap_solves = 0;
+  std::vector<int> co_status_h;
   // per-step PCG work, for algorithmic-byte accounting
   long long pcg_iters_acc = 0;
   long long pcg_pair_iters_acc = 0;
@@ -436,9 +451,93 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
     sim->plan_streamed = sim->pcg_streamed;
     sim->plan_resident = resident;
     sim->plan_smem = smem;
+    ++sim->plan_stamp;
   }
   launch_layout(sim->st, sim->plan.n_fem_ctas + sim->nab, sim->d_seg, sim->S.bsr_row, sim->Hval, sim->pcg_op,
                 fp32);
+  return IPC_OK;
+}
+
+// Coarse level of the preconditioner for the current plan and assembled system
+// (Hval, pair and friction blocks): the layout (again when the plan changed),
+// the rigid-body modes at the current FEM positions xv, the Galerkin matrix
+// P^T A P of every solve and its inverse.  On a failed inversion the PCG runs
+// with block Jacobi alone (co_ok false).
+ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
+  sim->co_ok = false;
+  if (sim->P.preconditioner != IPC_PRECOND_TWO_LEVEL || sim->nf == 0 || sim->plan.n_fem_ctas <= 0) return IPC_OK;
+  CoarseLayout& L = sim->co;
+  if (sim->co_plan_stamp != sim->plan_stamp) {
+    coarse_layout(sim->plan, sim->nf, L);
+    sim->co_plan_stamp = sim->plan_stamp;
+    if (!L.consecutive || L.total <= 0) return IPC_OK;
+    ipc_status s;
+    if (L.total > sim->co_cap) {
+      dfree(sim, sim->co_Ac); dfree(sim, sim->co_Ac32);
+      sim->co_Ac = nullptr; sim->co_Ac32 = nullptr;
+      if ((s = dalloc(sim, &sim->co_Ac, (size_t)L.total))) return s;
+      if (fp32 || sim->P.precision == IPC_PREC_MIXED)
+        if ((s = dalloc(sim, &sim->co_Ac32, (size_t)L.total))) return s;
+      sim->co_cap = L.total;
+    }
+    if (L.total_n > sim->co_cap_n) {
+      dfree(sim, sim->co_gj);
+      sim->co_gj = nullptr;
+      if ((s = dalloc(sim, &sim->co_gj, 4 * (size_t)L.total_n))) return s;
+      sim->co_cap_n = L.total_n;
+    }
+    if (L.n_agg > sim->co_cap_agg) {
+      dfree(sim, sim->co_agg_solve); dfree(sim, sim->co_centre); dfree(sim, sim->co_rot); dfree(sim, sim->co_part);
+      sim->co_agg_solve = nullptr; sim->co_centre = nullptr; sim->co_rot = nullptr; sim->co_part = nullptr;
+      if ((s = dalloc(sim, &sim->co_agg_solve, (size_t)L.n_agg))) return s;
+      if ((s = dalloc(sim, &sim->co_centre, 3 * (size_t)L.n_agg))) return s;
+      if ((s = dalloc(sim, &sim->co_rot, (size_t)L.n_agg))) return s;
+      if ((s = dalloc(sim, &sim->co_part, 6 * (size_t)L.n_agg))) return s;
+      sim->co_cap_agg = L.n_agg;
+    }
+    if (L.n_solves > sim->co_cap_solves) {
+      dfree(sim, sim->co_solve_lo); dfree(sim, sim->co_solve_n); dfree(sim, sim->co_off); dfree(sim, sim->co_boff);
+      dfree(sim, sim->co_status);
+      sim->co_solve_lo = nullptr; sim->co_solve_n = nullptr; sim->co_off = nullptr; sim->co_boff = nullptr;
+      sim->co_status = nullptr;
+      if ((s = dalloc(sim, &sim->co_solve_lo, (size_t)L.n_solves))) return s;
+      if ((s = dalloc(sim, &sim->co_solve_n, (size_t)L.n_solves))) return s;
+      if ((s = dalloc(sim, &sim->co_off, (size_t)L.n_solves))) return s;
+      if ((s = dalloc(sim, &sim->co_boff, (size_t)L.n_solves))) return s;
+      if ((s = dalloc(sim, &sim->co_status, (size_t)L.n_solves))) return s;
+      sim->co_cap_solves = L.n_solves;
+    }
+    if (!sim->co_node_agg && (s = dalloc(sim, &sim->co_node_agg, (size_t)sim->nf))) return s;
+    if (!sim->co_x && (s = dalloc(sim, &sim->co_x, 3 * (size_t)sim->nf))) return s;
+    cudaStream_t cs = sim->st;
+    CUDA_TRY(cudaMemcpyAsync(sim->co_node_agg, L.node_agg.data(), sizeof(int) * sim->nf, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->co_agg_solve, L.agg_solve.data(), sizeof(int) * L.n_agg, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->co_solve_lo, L.solve_lo.data(), sizeof(int) * L.n_solves, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->co_solve_n, L.solve_n.data(), sizeof(int) * L.n_solves, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->co_off, L.off.data(), sizeof(long long) * L.n_solves, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->co_boff, L.boff.data(), sizeof(long long) * L.n_solves, cudaMemcpyHostToDevice, cs));
+    // the host vectors are read by the copies: wait for them before they can change
+    CUDA_TRY(cudaStreamSynchronize(cs));
+  }
+  if (!L.consecutive || L.total <= 0) return IPC_OK;
+  cudaStream_t cs = sim->st;
+  CUDA_TRY(cudaMemcpyAsync(sim->co_x, sim->xv, sizeof(double) * 3 * sim->nf, cudaMemcpyDeviceToDevice, cs));
+  CUDA_TRY(cudaMemsetAsync(sim->co_part, 0, sizeof(double) * 6 * L.n_agg, cs));
+  CoarseDevLayout D;
+  D.n_agg = L.n_agg; D.n_solves = L.n_solves; D.n_max = L.n_max; D.total = L.total; D.total_n = L.total_n;
+  D.node_agg = sim->co_node_agg; D.agg_solve = sim->co_agg_solve; D.solve_lo = sim->co_solve_lo;
+  D.solve_n = sim->co_solve_n; D.off = sim->co_off; D.boff = sim->co_boff;
+  CUDA_TRY(launch_coarse_build(cs, sim->S, D, sim->d_seg, sim->co_x, sim->Hval, sim->rec, &sim->sc_dev->n_pairs,
+                               sim->cap, sim->pairH, n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->co_Ac,
+                               sim->co_centre, sim->co_rot, sim->co_gj, sim->co_status));
+  sim->co_status_h.assign(L.n_solves, 0);
+  CUDA_TRY(cudaMemcpyAsync(sim->co_status_h.data(), sim->co_status, sizeof(int) * L.n_solves, cudaMemcpyDeviceToHost,
+                           cs));
+  CUDA_TRY(cudaStreamSynchronize(cs));
+  for (int v : sim->co_status_h)
+    if (v) return IPC_OK;  // a pivot failed: block Jacobi alone for this build
+  if (sim->co_Ac32) launch_to_float(cs, (size_t)L.total, sim->co_Ac, sim->co_Ac32);
+  sim->co_ok = true;
   return IPC_OK;
 }
 
@@ -511,6 +610,17 @@ ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric)
   a.abd_val = sim->abd_val;
   a.abd_val32 = sim->abd_val32;
   a.abd_cap = sim->abd_cap;
+  if (sim->co_ok) {
+    a.co.inv = fp32 ? nullptr : sim->co_Ac;
+    a.co.inv32 = fp32 ? sim->co_Ac32 : nullptr;
+    a.co.off = sim->co_off;
+    a.co.solve_lo = sim->co_solve_lo;
+    a.co.solve_n = sim->co_solve_n;
+    a.co.centre = sim->co_centre;
+    a.co.rot = sim->co_rot;
+    a.co.x = sim->co_x;
+    a.co.part = sim->co_part;
+  }
   CUDA_TRY(launch_pcg(sim->st, sim->plan.grid, PCG_THREADS, a, sim->tune_rowg, sim->plan_smem));
   if (check) {
     int site = 0;
@@ -1345,6 +1455,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
   CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
   ipc_status s = IPC_OK;
   sim->cand_valid = false;
+  sim->co_built_this_step = false;
   bool rec_current = false;  // sim->rec holds the active set at the current iterate
   const bool sweep = P.broad_phase != IPC_BROAD_ALL_PAIRS;
   // friction lag on the pairs active at x_t
@@ -1440,6 +1551,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
           sim->tune_bps = bi + 1;
           float ms = 0.f;
           if ((s = pcg_prepare(sim, fp32))) return s;
+          if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
           for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, cs);
             if ((s = pcg_run(sim, fp32, P.pcg_rtol, max_pcg, n_fric_it))) return s;
@@ -1457,6 +1569,12 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       sim->autotune_pending = false;
     }
     if ((s = pcg_prepare(sim, fp32))) return s;
+    // the coarse level is built once per step (and again when the launch shape changed); the later Newton
+    // iterations of the step keep it as their preconditioner
+    if (!sim->co_built_this_step || sim->co_plan_stamp != sim->plan_stamp) {
+      if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
+      sim->co_built_this_step = true;
+    }
     prof_end(sim, PROF_PCG_SETUP);
     prof_begin(sim, PROF_PCG);
     if ((s = pcg_run(sim, fp32, P.pcg_rtol, max_pcg, n_fric_it))) return s;
@@ -1799,7 +1917,9 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     const int n_fric_adj = P.mu > 0 ? sim->n_fric : 0;
     build_incidence(sim, n_fric_adj);
     if ((s = pcg_prepare(sim, 0))) return s;
+    if ((s = coarse_setup(sim, 0, n_fric_adj))) return s;
     if ((s = pcg_run(sim, 0, 1e-12, 10 * ndof + 1000, n_fric_adj))) return s;
+    sim->co_built_this_step = false;  // the next step builds its own coarse level
   }
   // contractions with lam (= sim->p)
   if (glogE) launch_theta_grad(cs, S, sim->xv, sim->p, dt2, glogE);

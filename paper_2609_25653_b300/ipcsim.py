@@ -24,6 +24,7 @@ STATUS = {0: "IPC_OK", -1: "IPC_ERR_ARG", -2: "IPC_ERR_INVERTED", -3: "IPC_ERR_I
           -8: "IPC_ERR_BVH_OVERFLOW", -9: "IPC_ERR_CUDA", -10: "IPC_ERR_CAPACITY"}
 PREC_FP64, PREC_MIXED = 0, 1
 BROAD_LBVH, BROAD_ALL_PAIRS = 0, 1
+PRECOND_TWO_LEVEL, PRECOND_BLOCK_JACOBI = 0, 1
 
 
 class SceneDesc(C.Structure):
@@ -45,7 +46,7 @@ class Params(C.Structure):
                 ("eps_v", C.c_double), ("k_c", C.c_double), ("kappa_A", C.c_double), ("newton_tol", C.c_double),
                 ("pcg_rtol", C.c_double), ("s_ccd", C.c_double), ("max_newton", C.c_int), ("max_pcg", C.c_int),
                 ("precision", C.c_int), ("pair_capacity", C.c_int), ("broad_phase", C.c_int),
-                ("pair_capacity_max", C.c_int)]
+                ("pair_capacity_max", C.c_int), ("preconditioner", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -132,6 +133,12 @@ SIGNATURES = {
     "sim_create_with_allocator": ([C.POINTER(SceneDesc), C.c_int, C.POINTER(Params), C.POINTER(Allocator), vp,
                                    C.POINTER(vp)], C.c_int),
     "sim_memory": ([vp, C.POINTER(C.c_longlong)], C.c_int),
+    "sim_dual_mesh_create": ([ip, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
+    "sim_dual_mesh_sizes": ([vp, C.POINTER(C.c_longlong)], C.c_int),
+    "sim_dual_mesh_topology": ([vp, ip, ip, ip, dp], C.c_int),
+    "sim_dual_mesh_apply": ([vp, vp, vp, vp], C.c_int),
+    "sim_dual_mesh_last_error": ([], C.c_char_p),
+    "sim_dual_mesh_destroy": ([vp], None),
 }
 
 PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "pcg_setup"]
@@ -212,7 +219,8 @@ def make_params(p: dict, precision=PREC_FP64) -> Params:
                   k_c=p.get("k_c", 0.0), kappa_A=p.get("kappa_A", 1e8), newton_tol=p["newton_tol"],
                   pcg_rtol=p.get("pcg_rtol", 1e-4), s_ccd=p.get("s_ccd", 0.1), max_newton=int(p.get("max_newton", 100)),
                   max_pcg=int(p.get("max_pcg", 0)), precision=int(precision), pair_capacity=int(p.get("pair_capacity", 0)),
-                  broad_phase=int(p.get("broad_phase", BROAD_LBVH)), pair_capacity_max=int(p.get("pair_capacity_max", 0)))
+                  broad_phase=int(p.get("broad_phase", BROAD_LBVH)), pair_capacity_max=int(p.get("pair_capacity_max", 0)),
+                  preconditioner=int(p.get("preconditioner", PRECOND_TWO_LEVEL)))
 
 
 def _fill_desc(d, scene, keep):
@@ -509,6 +517,57 @@ class Simulator:
         nc = C.c_int()
         self._check(load().sim_ccd_alpha(self.h, _ptr(xv_dev), _ptr(pv_dev), C.byref(a), C.byref(nc)))
         return a.value, nc.value
+
+
+class DualMesh:
+    """Render mesh of a deformable surface by L levels of Loop subdivision (Eqs. 5-6): W built once,
+    X_f = W X_c per frame on the device.  upload=False keeps W on the host (inspection without a GPU)."""
+
+    def __init__(self, tris, n_verts, levels, upload=True):
+        L = load()
+        t = _i32(tris)
+        h = C.c_void_p()
+        code = L.sim_dual_mesh_create(t.ctypes.data_as(ip), len(t), int(n_verts), int(levels), int(bool(upload)),
+                                      C.byref(h))
+        if code != IPC_OK:
+            raise IpcError(code, L.sim_dual_mesh_last_error().decode())
+        self.h = h
+        sz = (C.c_longlong * 4)()
+        L.sim_dual_mesh_sizes(h, sz)
+        self.n_coarse, self.n_fine, self.n_fine_tris, self.nnz = (int(v) for v in sz)
+
+    def topology(self):
+        """(fine triangles, W as scipy CSR)."""
+        import scipy.sparse as sp
+        tris = np.zeros((self.n_fine_tris, 3), np.int32)
+        row = np.zeros(self.n_fine + 1, np.int32)
+        col = np.zeros(max(self.nnz, 1), np.int32)
+        val = np.zeros(max(self.nnz, 1))
+        load().sim_dual_mesh_topology(self.h, tris.ctypes.data_as(ip), row.ctypes.data_as(ip), col.ctypes.data_as(ip),
+                                      val.ctypes.data_as(dp))
+        return tris, sp.csr_matrix((val[:self.nnz], col[:self.nnz], row), shape=(self.n_fine, self.n_coarse))
+
+    def apply(self, xc_dev, xf_dev=None, stream=None):
+        """X_f = W X_c for device tensors; returns xf_dev ((N_fine, 3), allocated when None)."""
+        import torch
+        if xf_dev is None:
+            xf_dev = torch.empty((self.n_fine, 3), dtype=torch.float64, device=xc_dev.device)
+        st = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        code = load().sim_dual_mesh_apply(self.h, _ptr(xc_dev.contiguous()), _ptr(xf_dev), st)
+        if code != IPC_OK:
+            raise IpcError(code, "sim_dual_mesh_apply failed")
+        return xf_dev
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sim_dual_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def step_many(sims, kin_T_next=None):

@@ -366,6 +366,23 @@ def subdivided_box(lo, hi, n):
     return np.asarray(vlist, dtype=np.float64), np.asarray(tris, dtype=np.int32)
 
 
+def morton_order(X, T):
+    """The mesh (X, T) with its vertices renumbered in Morton (Z-curve) order of their positions, so that
+    consecutive vertex ids are spatially close (the usual reordering of a generated tet mesh: runs of
+    consecutive vertices form compact clusters)."""
+    lo = X.min(0)
+    ext = float((X.max(0) - lo).max()) or 1.0
+    q = np.floor((X - lo) / ext * 1023.0).astype(np.int64)
+    code = np.zeros(len(X), np.int64)
+    for bit in range(10):
+        for d in range(3):
+            code |= ((q[:, d] >> bit) & 1) << (3 * bit + d)
+    order = np.argsort(code, kind="stable")
+    inv = np.empty_like(order)
+    inv[order] = np.arange(len(order))
+    return X[order], inv[T].astype(np.int32)
+
+
 def finray_tip(h=1.25e-3, width=20e-3, height=40e-3, depth=20e-3):
     """Voxelised fin-ray fingertip in its local frame (u, v, w).
 
@@ -373,7 +390,7 @@ def finray_tip(h=1.25e-3, width=20e-3, height=40e-3, depth=20e-3):
     u / width + w / height <= 1 (contact face u = 0, mounting face w = 0, back
     face the hypotenuse), extruded over v in [0, depth].  Three slanted rib
     voids (one cell thick) run between the contact face and the back face.
-    Cells are cut into 6 tets each."""
+    Cells are cut into 6 tets each; vertices are numbered in Morton order."""
     nu, nw, nv = int(round(width / h)), int(round(height / h)), int(round(depth / h))
     keep = np.zeros((nu, nv, nw), bool)
     for i in range(nu):
@@ -399,7 +416,7 @@ def finray_tip(h=1.25e-3, width=20e-3, height=40e-3, depth=20e-3):
     used = np.unique(T)
     remap = -np.ones(len(X), np.int64)
     remap[used] = np.arange(len(used))
-    return X[used], remap[T].astype(np.int32)
+    return morton_order(X[used], remap[T].astype(np.int32))
 
 
 def _frame(R, t):
@@ -534,6 +551,22 @@ def arm_gripper_grasp_reduced(seed: int = 0, n_steps: int = 16, **param_override
     sc = arm_gripper_grasp(seed, n_steps=n_steps, tip_cell=3.0e-3, link_tris=48, obj_tris=300, base_tris=100,
                            close_per_step=0.3e-3, close_steps=10, hold_steps=2, **param_overrides)
     sc["name"] = f"arm_gripper_grasp_reduced_{len(sc['fem_tets'])}tet"
+    return sc
+
+
+def material_identification(seed: int = 0, n_steps: int = 100, tip_cell=0.97e-3, hidden_seed: int = 1,
+                            sigma: float = 0.3, **param_overrides) -> dict:
+    """Differentiable material identification: the arm-gripper grasp refined to about 100k tets (two
+    fin-ray tips of 0.97 mm voxels) with per-tet ln Young's modulus drawn lognormal around 2e5 Pa
+    (sigma 0.3, seed `seed`) as the parameters to identify, mu = 0.6.  The returned scene also holds the
+    hidden parameters (`hidden_logE`, seed `hidden_seed`, and `hidden_mu` = 0.5) that simulate the target
+    trajectory of the loss."""
+    sc = arm_gripper_grasp(0, n_steps=n_steps, tip_cell=tip_cell, **param_overrides)
+    nt = len(sc["fem_tets"])
+    sc["fem_logE"] = math.log(2e5) + sigma * SplitMix64(seed + 7000).normal(nt)
+    sc["hidden_logE"] = math.log(2e5) + sigma * SplitMix64(hidden_seed + 7000).normal(nt)
+    sc["hidden_mu"] = 0.5
+    sc["name"] = f"material_identification_{nt}tet"
     return sc
 
 
@@ -682,7 +715,7 @@ def voxel_cylinder(r, h, cell, z0=0.0):
     used = np.unique(T)
     remap = -np.ones(len(X), np.int64)
     remap[used] = np.arange(len(used))
-    return X[used], remap[T].astype(np.int32)
+    return morton_order(X[used], remap[T].astype(np.int32))
 
 
 def soft_gripper_cylinder(seed: int = 0, n_steps: int = 300, tip_cell=1.25e-3, cyl_cell=2.15e-3,

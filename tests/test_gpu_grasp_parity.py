@@ -135,3 +135,38 @@ def test_soft_cylinder_mixed_precision_matches_oracle(cylinder):
     sim = _sim(sc, precision=ipcsim.PREC_MIXED, newton_tol=1e-6, pcg_rtol=1e-4)
     worst = max(_teacher_forced_step(sim, sc, S, states, k)[0] for k in CYL_STEPS)
     assert worst < 1e-5, worst
+
+
+def test_two_level_preconditioner_reaches_the_oracle_in_fewer_iterations(grasp):
+    """The coarse rigid-body correction changes the PCG's iterates, not the Newton step it solves for:
+    both preconditioners reach the oracle's next state, the two-level one with fewer PCG iterations."""
+    from paper_2609_25653_b300 import ipcsim
+    sc, S, states = grasp
+    two = _sim(sc)
+    jac = _sim(sc, preconditioner=ipcsim.PRECOND_BLOCK_JACOBI)
+    it_two = it_jac = 0
+    for k in (4, 10, 13):
+        e2, s2 = _teacher_forced_step(two, sc, S, states, k)
+        ej, sj = _teacher_forced_step(jac, sc, S, states, k)
+        assert e2 < 1e-8 and ej < 1e-8, (k, e2, ej)
+        it_two += s2["pcg_iters_total"]
+        it_jac += sj["pcg_iters_total"]
+    assert it_two < it_jac, (it_two, it_jac)
+
+
+def test_two_level_mixed_precision_batch_matches_single_scenes():
+    """Batches run one coarse level per scene (one dense block per independent solve)."""
+    from paper_2609_25653_b300 import ipcsim
+    scs = [scenes.arm_gripper_grasp_reduced(s, n_steps=6) for s in (0, 1)]
+    batch = ipcsim.Simulator.batch(scs, precision=ipcsim.PREC_MIXED)
+    single = [_sim(sc, precision=ipcsim.PREC_MIXED) for sc in scs]
+    for k in range(4):
+        st = batch.step()
+        assert st["status"] == 0
+        xb = batch.get_state()[0]
+        off = 0
+        for sim in single:
+            sim.step()
+            xs = sim.get_state()[0]
+            assert np.max(np.abs(xb[off:off + sim.nf] - xs)) / sim.L < 1e-5
+            off += sim.nf
