@@ -127,7 +127,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def pcg_work(work, sim, fp32, launches):
+def pcg_work(work, sim, fp32, launches, coarse_n=0):
     """Algorithmic work of the PCG kernel per launch: (bytes, flops), from the per-unit figures of the
     method's solve, independent of how the kernel is built.
 
@@ -136,12 +136,14 @@ def pcg_work(work, sim, fp32, launches):
     (56 B in FP64, 28 B in FP32) and take 10 flops per DOF, the block-Jacobi preconditioner 6 flops per
     DOF; every active barrier pair's 12x12 block (144 values + its 32 B record) takes 288 flops, every
     friction pair's 3x3 block, ids and weights (9 values + 48 B) about 60 flops.  The mixed-precision
-    solver's inner iterations are FP32: its figures use 4-byte values."""
+    solver's inner iterations are FP32: its figures use 4-byte values.  The two-level preconditioner adds,
+    per iteration, the product with the dense coarse inverse (n_c x n_c values read once, 2 n_c^2 flops,
+    n_c = 6 x aggregates) and the restriction and prolongation (36 flops per FEM DOF)."""
     e = 4 if fp32 else 8
     it = work["pcg_iters"]
     ndof = 3 * sim.n_nodes
-    per_it_bytes = work["bsr_blocks"] * (9 * e + 4) + ndof * 7 * e
-    per_it_flops = work["bsr_blocks"] * 18 + ndof * 16
+    per_it_bytes = work["bsr_blocks"] * (9 * e + 4) + ndof * 7 * e + coarse_n * coarse_n * e
+    per_it_flops = work["bsr_blocks"] * 18 + ndof * 16 + 2 * coarse_n * coarse_n + 36 * 3 * sim.nf * (coarse_n > 0)
     total_bytes = it * per_it_bytes + work["pcg_pair_iters"] * (144 * e + 32) + work["pcg_fric_iters"] * (9 * e + 48)
     total_flops = it * per_it_flops + work["pcg_pair_iters"] * 288 + work["pcg_fric_iters"] * 60
     n = max(launches, 1)
@@ -216,12 +218,15 @@ def run_ours(args):
         wl = shard_scenes(wl, rank, world)
     precision = args.precision or ("mixed" if batched else "fp64")
     prec = ipcsim.PREC_MIXED if precision == "mixed" else ipcsim.PREC_FP64
+    over = {"coarse_rebuild": args.coarse_rebuild,
+            "preconditioner": ipcsim.PRECOND_BLOCK_JACOBI if args.preconditioner == "block-jacobi"
+            else ipcsim.PRECOND_TWO_LEVEL}
     if batched:
-        sim = ipcsim.Simulator.batch(wl, precision=prec, stream=stream)
+        sim = ipcsim.Simulator.batch(wl, precision=prec, stream=stream, **over)
         sc = sim.scene
     else:
         sc = wl
-        sim = ipcsim.Simulator(sc, precision=prec, stream=stream)
+        sim = ipcsim.Simulator(sc, precision=prec, stream=stream, **over)
     n_sc = len(wl) if batched else 1
     n_traj = sc["kin_T"].shape[0] - 1 if len(sc.get("kin", [])) else sc["params"]["n_steps"]
     timed = timed_indices(n_traj, args.warmup, args.steps, args.sample)
@@ -266,6 +271,7 @@ def run_ours(args):
     launches = ipcsim.kernel_launches() - launches0 - untimed_launches
     prof, work = sim.profile_read()
     sim.profile(False)
+    end_state, end_index = sim.get_state(), sim.step_index
     total_ms = slowest_rank(sum(times))
     value = world * args.steps * n_sc / (total_ms / 1e3)
 
@@ -322,6 +328,26 @@ def run_ours(args):
     e2e_s = slowest_rank(e2e_s)
     e2e_value = world * args.steps * n_sc / e2e_s
 
+    # accuracy gate of a batch: the first --gate scenes simulated alone in FP64 over the same steps
+    gate = None
+    if batched and args.gate > 0:
+        xb = end_state[0]
+        errs = []
+        off = 0
+        for k, scn in enumerate(wl):
+            nfk = len(scn["fem_X"])
+            if k < args.gate:
+                single = ipcsim.Simulator(scn, stream=stream)
+                for _ in range(end_index):
+                    single.step()
+                xs = single.get_state()[0]
+                errs.append(float(np.max(np.abs(xb[off:off + nfk] - xs)) / single.L))
+                single.close()
+            off += nfk
+        gate = {"scenes": len(errs), "reference": "each scene alone, FP64, same steps",
+                "max_rel_pos_err": max(errs), "rel_pos_err": [float("%.3g" % e) for e in errs],
+                "within_1e-5": bool(max(errs) < 1e-5)}
+
     # roofline of the dominant kernel (the PCG solve), from its algorithmic work per launch and its
     # CUDA-event time per launch on the simulator's stream
     peaks, peak_src = load_peaks()
@@ -330,7 +356,8 @@ def run_ours(args):
     fp32 = prec == ipcsim.PREC_MIXED
     pcg_avg_ms = pcg["ms"] / max(pcg["n"], 1)
     pcg_grid, pcg_resident = sim.pcg_layout()
-    b_launch, f_launch = pcg_work(work, sim, fp32, pcg["n"])
+    coarse_n = sim.coarse_size() if sim.params.get("preconditioner", ipcsim.PRECOND_TWO_LEVEL) == ipcsim.PRECOND_TWO_LEVEL else 0
+    b_launch, f_launch = pcg_work(work, sim, fp32, pcg["n"], coarse_n)
     alu_peak = peaks_dev["fp32_tflops"] if fp32 else peaks_dev["fp64_tflops"]
     t_mem = b_launch / (peaks["hbm_gbs"] * 1e9)
     t_alu = f_launch / (alu_peak * 1e12)
@@ -356,6 +383,7 @@ def run_ours(args):
                     algorithmic_flops_per_launch=int(f_launch),
                     pcg_iterations_per_launch=round(work["pcg_iters"] / max(pcg["n"], 1), 1),
                     pcg_ctas=pcg_grid, operator_in_shared_memory=pcg_resident, dominant_stage=dom,
+                    preconditioner="two-level" if coarse_n else "block Jacobi", coarse_unknowns=coarse_n,
                     stage_ms_per_step={k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["n"]})
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -372,6 +400,7 @@ def run_ours(args):
             "config": workload_config(wl, args.workload, {
                 "parallelism": (f"scene-shards{world}" if batched and world > 1 else f"replicas{world}"),
                 "precision": precision,
+                "preconditioner": args.preconditioner, "coarse_rebuild": args.coarse_rebuild,
                 "value_counts": "scene-steps" if batched else "steps",
                 "timed_steps": timed if args.sample == "consecutive" or len(timed) <= 40 else f"{timed[0]}..{timed[-1]}",
                 "timed_sample": ("every step after the warm-up" if args.sample == "consecutive" else
@@ -385,6 +414,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "adjoint": adjoint,
+            "accuracy_gate": gate,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 96 * sim.nkb,
                     "d2h_bytes_per_step": 24 * sim.nf},
             "gpu_launches": int(launches),
@@ -435,8 +465,14 @@ def run_material_id(args):
     e1.record()
     e1.synchronize()
     adj_ms = e0.elapsed_time(e1) / n
-    # central differences over the first fd_steps steps, 16 random directions (ln E: 14, mu: 2)
+    # central differences over the first fd_steps steps, 16 random directions (ln E: 14, mu: 2), on a
+    # simulator with tight Newton and PCG tolerances (the implicit function theorem assumes converged
+    # steps, and the differences must resolve loss changes far below the default tolerances)
     m = args.fd_steps
+    sim.close()
+    sim = ipcsim.Simulator(sc, newton_tol=1e-10, pcg_rtol=1e-12, max_newton=300)
+    with torch.no_grad():
+        target = [t.detach() for t in autograd.rollout(sim, hidden, sc["hidden_mu"], m, z0, zd0)]
 
     def loss_short(le, mu_v):
         with torch.no_grad():
@@ -466,10 +502,45 @@ def run_material_id(args):
     line = {"workload": sc["name"], "fem_tets": len(sc["fem_tets"]), "steps": n, "precision": "fp64",
             "adjoint_ms_per_step": round(adj_ms, 3), "forward_ms_per_step": round(1e3 * t_fwd / n, 3),
             "target_forward_s": round(t_target, 2), "loss": float(L),
-            "fd_check": {"directions": 16, "steps": m, "max_rel_err": float(max(errs)),
+            "fd_check": {"directions": 16, "steps": m, "tolerances": "newton 1e-10, pcg 1e-12",
+                         "max_rel_err": float(max(errs)),
                          "rel_errs": [float("%.3g" % e) for e in errs]},
             "grad_norm_logE": float(np.linalg.norm(logE.grad.numpy())), "grad_mu": float(mu.grad)}
     print(json.dumps(line))
+
+
+def run_render(args):
+    """Frames/s of the path tracer (640 x 360, 32 paths per pixel, 2 bounces, 8 shadow samples for Eq. 7)
+    on the arm-gripper grasp after --warmup steps, timed with CUDA events over --steps frames."""
+    import numpy as np
+    import torch
+    from paper_2609_25653_b300 import ipcsim, scenes
+    torch.cuda.set_device(0)
+    sc = scenes.arm_gripper_grasp(0)
+    sim = ipcsim.Simulator(sc)
+    for _ in range(max(args.warmup, 1)):
+        sim.step()
+    _, tris_s, _ = sim.surface()
+    extra, tris, types, rgb, cam = scenes.render_setup(sc, tris_s, sim.nv)
+    xv = torch.cat([sim.positions(), torch.as_tensor(extra, device="cuda")]).contiguous()
+    r = ipcsim.Renderer(tris, types, rgb, xv.shape[0])
+    out = r.render(xv, cam, spp=32, max_depth=2, n_shadow=8)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        r.render(xv, cam, spp=32, max_depth=2, n_shadow=8, seed=k, out=out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    img = out.cpu().numpy()
+    np.save(os.path.join(ROOT, "gpurun_out", "render_frame.npy"), img) if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    print(json.dumps({"workload": "render_" + sc["name"], "triangles": int(len(tris)), "width": cam[1],
+                      "height": cam[2], "spp": 32, "max_depth": 2, "n_shadow": 8, "frames": args.steps,
+                      "ms_per_frame": round(ms, 3), "fps": round(1e3 / ms, 2),
+                      "mean_rgb": [float(v) for v in img.reshape(-1, 3).mean(0)],
+                      "context": "paper: 24 FPS at 640x360, 32 SPP on one RTX 5090 (its own renderer)"}))
 
 
 def shard_scenes(scenes_list, rank, world):
@@ -645,6 +716,11 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default PCG launch shape")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ms/step measurement")
     ap.add_argument("--id-steps", type=int, default=100, help="material_id workload: rollout steps")
+    ap.add_argument("--preconditioner", choices=["two-level", "block-jacobi"], default="two-level")
+    ap.add_argument("--coarse-rebuild", type=int, default=0,
+                    help="two-level: 0 rebuild every step, n keep up to n steps, -1 every Newton iteration")
+    ap.add_argument("--gate", type=int, default=0,
+                    help="batched workloads: compare the first N scenes with FP64 single-scene runs")
     ap.add_argument("--fd-steps", type=int, default=10, help="material_id workload: steps of the FD check")
     ap.add_argument("--sample", choices=["trajectory", "consecutive"], default="trajectory",
                     help="time K steps spread over the whole trajectory (default) or the K steps after the warm-up")
@@ -657,6 +733,8 @@ def main():
         run_reference(args)
     elif args.workload == "material_id":
         run_material_id(args)
+    elif args.workload == "render":
+        run_render(args)
     else:
         run_ours(args)
 

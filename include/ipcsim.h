@@ -115,16 +115,20 @@ typedef struct {
   int pair_capacity_max; /* largest contact-pair buffer (pairs) the simulator grows to; a step that needs
                             more fails with IPC_ERR_CAPACITY; <= 0: 2^23 */
   int preconditioner; /* IPC_PRECOND_TWO_LEVEL (default) or IPC_PRECOND_BLOCK_JACOBI */
+  int coarse_rebuild; /* two-level coarse matrix: 0 rebuilt at the first Newton iteration of every step
+                         (default); n > 0 kept up to n steps while the PCG iterations per solve stay
+                         within 30 % of the step it was built in; -1 rebuilt at every Newton iteration */
 } ipc_params;
 
 /* PCG preconditioners (the paper names StiffGIPC's solver without its
  * details; both are this library's).  Block Jacobi: the inverse 3x3 diagonal
  * blocks.  Two-level: block Jacobi plus a coarse correction
  * P (P^T A P)^-1 P^T whose columns are the rigid-body motions (3
- * translations, 3 rotations about the centre) of every FEM row segment of
- * the PCG launch; P^T A P is assembled and inverted once per step, at the
- * first Newton iteration.  Number FEM vertices in spatial order (e.g. Morton
- * order) so that row segments are compact clusters. */
+ * translations, 3 rotations about the centre) of runs of FEM row segments of
+ * the PCG launch (at most 768 coarse unknowns per solve); P^T A P is
+ * assembled and inverted (FP64 Gauss-Jordan) as coarse_rebuild says.
+ * Number FEM vertices in spatial order (e.g. Morton order) so that row
+ * segments are compact clusters. */
 enum { IPC_PRECOND_TWO_LEVEL = 0, IPC_PRECOND_BLOCK_JACOBI = 1 };
 
 enum { IPC_BROAD_LBVH = 0, IPC_BROAD_ALL_PAIRS = 1 };
@@ -231,6 +235,13 @@ ipc_status sim_step_many(ipcsim* const* sims, int n, const double* const* kin_T_
  * pointers are device pointers, else host pointers.  Synchronous. */
 ipc_status sim_get_state(const ipcsim* sim, double* x, double* v, double* abd_q, double* abd_qd, int on_device);
 
+/* Every vertex position of the current state in the global vertex order
+ * (FEM vertices, ABD surface vertices x = p + A xbar, kinematic vertices at
+ * their current transforms) into xv_dev ((n_vertices_all, 3) doubles,
+ * device): the geometry a frame of Eq. 4's trajectory is rendered from.
+ * Synchronous. */
+ipc_status sim_positions(const ipcsim* sim, double* xv_dev);
+
 /* Overwrite the state (same layouts; e.g. to restart a rollout of Eq. 3 from
  * a recorded step).  Kinematic bodies keep their pose. */
 ipc_status sim_set_state(ipcsim* sim, const double* x, const double* v, const double* abd_q, const double* abd_qd,
@@ -302,6 +313,12 @@ ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_nex
  * streamed != 0: always read from global memory.  Both give the same
  * arithmetic in the same order.  Takes effect at the next solve. */
 ipc_status sim_pcg_residency(ipcsim* sim, int streamed);
+
+/* The coarse level of the two-level preconditioner as last built: out4 =
+ * [aggregates (FEM CTAs of the launch), independent solves, coarse unknowns
+ * of the largest solve (6 per aggregate), 1 if the last build succeeded
+ * (0: that solve ran with block Jacobi alone)]. */
+ipc_status sim_coarse_info(const ipcsim* sim, long long* out4);
 
 /* Accounting of the library, no counterpart in the paper.  Per-stage timing
  * with CUDA events recorded on the simulator's stream
@@ -456,6 +473,59 @@ ipc_status sim_dual_mesh_apply(const ipc_dual_mesh* m, const double* xc_dev, dou
 /* Reason of the last failed sim_dual_mesh_create on the calling thread. */
 const char* sim_dual_mesh_last_error(void);
 void sim_dual_mesh_destroy(ipc_dual_mesh* m);
+
+/* ------------------------------------------------------------------------
+ * Headless path tracer of the simulated frames (§III-D.2, "real-time path
+ * tracing", with the appearance-preserving shadow-receiving material of
+ * §III-D.3, Eq. 7), written as plain CUDA (no graphics API): triangles in an
+ * LBVH rebuilt per frame, one thread per pixel, spp paths of up to max_depth
+ * diffuse bounces with next-event estimation toward the area lights, linear
+ * RGB out (no tone mapping; the LUT calibration of §III-D.4 needs real frames).
+ * ---------------------------------------------------------------------- */
+enum { IPC_MAT_DIFFUSE = 0,      /* Lambertian; rgb = albedo */
+       IPC_MAT_EMISSIVE = 1,     /* area light (two-sided); rgb = radiance */
+       IPC_MAT_BACKGROUND = 2,   /* reconstructed background, Eq. 7; rgb = C_tex of the triangle; paths end here */
+       IPC_MAT_TRANSPARENT = 3   /* thin sheet: paths pass with throughput x rgb; casts no shadow */ };
+
+typedef struct {
+  int n_verts;
+  int n_tris;
+  const int* tris_host;    /* (n_tris, 3) vertex ids */
+  const int* type_host;    /* (n_tris) IPC_MAT_* */
+  const float* rgb_host;   /* (n_tris, 3) colour of the material (see IPC_MAT_*) */
+} ipc_render_scene;
+
+typedef struct {
+  float eye[3], fwd[3], right[3], up[3];  /* pinhole camera: unit forward, right, up */
+  float tan_half_fov;                     /* tan of half the vertical field of view */
+  int width, height;
+} ipc_camera;
+
+typedef struct {
+  int spp;                  /* paths per pixel */
+  int max_depth;            /* diffuse bounces after the first hit */
+  int n_shadow;             /* N light samples of the visibility V of Eq. 7 */
+  float lambda_s;           /* shadow strength lambda_s of Eq. 7, in [0, 1] */
+  float eps;                /* ray offset from a surface (m) */
+  unsigned long long seed;  /* every random number is a hash of (seed, pixel, sample, dimension) */
+} ipc_render_params;
+
+typedef struct ipc_render ipc_render;
+
+/* Upload the topology and materials (host arrays, copied).  The light
+ * triangles (IPC_MAT_EMISSIVE) are sampled in proportion to their area.
+ * IPC_ERR_ARG for ids out of range or an unknown material. */
+ipc_status sim_render_create(const ipc_render_scene* scene, ipc_render** out);
+/* Render one frame at vertex positions x_dev ((n_verts, 3) doubles, device)
+ * into rgb_dev ((height, width, 3) floats, device, row-major from the top
+ * left), enqueued on `stream` (a cudaStream_t); does not synchronise.  The
+ * frame is a deterministic function of its inputs (counter-based random
+ * numbers; FP32 arithmetic without contraction). */
+ipc_status sim_render_frame(ipc_render* r, const double* x_dev, const ipc_camera* cam, const ipc_render_params* p,
+                            float* rgb_dev, void* stream);
+/* Reason of the last failed sim_render_create on the calling thread. */
+const char* sim_render_last_error(void);
+void sim_render_destroy(ipc_render* r);
 
 #ifdef __cplusplus
 }

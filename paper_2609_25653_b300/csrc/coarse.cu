@@ -26,12 +26,12 @@ namespace ipc {
 
 namespace {
 
-// centre of every aggregate (the FEM rows of one FEM CTA) and whether its rotations are kept
-__global__ void k_coarse_centres(const int* __restrict__ seg, int n_agg, const double* __restrict__ x,
-                                 double* __restrict__ centre, int* __restrict__ rot) {
+// centre of every aggregate (the FEM rows of a run of FEM CTAs) and whether its rotations are kept
+__global__ void k_coarse_centres(const int* __restrict__ seg, const int* __restrict__ agg_cta, int n_agg,
+                                 const double* __restrict__ x, double* __restrict__ centre, int* __restrict__ rot) {
   const int a = blockIdx.x;
   if (a >= n_agg) return;
-  const int r0 = seg[a], r1 = seg[a + 1];
+  const int r0 = seg[agg_cta[2 * a]], r1 = seg[agg_cta[2 * a + 1]];
   double s0 = 0, s1 = 0, s2 = 0;
   for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     s0 += x[3 * i];
@@ -156,12 +156,12 @@ __global__ void k_coarse_pairs(CoarseAsm C, DevScene S, const int* __restrict__ 
 }
 
 // unknowns without a mode (empty aggregates, rotations of small ones): identity rows
-__global__ void k_coarse_dead(CoarseAsm C, const int* __restrict__ seg, int n_agg) {
+__global__ void k_coarse_dead(CoarseAsm C, const int* __restrict__ seg, const int* __restrict__ agg_cta, int n_agg) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_agg) return;
   const int s = C.agg_solve[a];
   if (s < 0) return;
-  const bool empty = seg[a] == seg[a + 1];
+  const bool empty = seg[agg_cta[2 * a]] == seg[agg_cta[2 * a + 1]];
   const int n = C.solve_n[s], base = 6 * (a - C.solve_lo[s]);
   double* dst = C.Ac + C.off[s];
   for (int p = 0; p < 6; ++p)
@@ -232,33 +232,65 @@ __global__ void k_zero(size_t n, double* __restrict__ p) {
 }  // namespace
 
 void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L) {
-  const int na = P.n_fem_ctas;
-  L.n_agg = na;
-  L.agg_solve.assign(na, -1);
-  L.node_agg.assign(nf, -1);
-  for (int a = 0; a < na; ++a) {
-    L.agg_solve[a] = P.cta_scene[a];
-    for (int i = P.seg[a]; i < P.seg[a + 1] && i < nf; ++i) L.node_agg[i] = a;
-  }
+  const int nc = P.n_fem_ctas;
+  L.n_ctas = nc;
   L.n_solves = P.n_psc;
+  // FEM CTAs of every solve (consecutive by construction of the plan)
+  std::vector<int> lo(L.n_solves, nc), hi(L.n_solves, -1);
+  for (int c = 0; c < nc; ++c) {
+    const int s = P.cta_scene[c];
+    if (s < 0 || s >= L.n_solves) continue;
+    lo[s] = std::min(lo[s], c);
+    hi[s] = std::max(hi[s], c);
+  }
+  L.consecutive = true;
+  int largest = 0;
+  for (int s = 0; s < L.n_solves; ++s) {
+    for (int c = lo[s]; c <= hi[s]; ++c)
+      if (P.cta_scene[c] != s) L.consecutive = false;
+    largest = std::max(largest, hi[s] - lo[s] + 1);
+  }
+  // runs of `group` CTAs form an aggregate, so that a solve has at most COARSE_MAX_UNKNOWNS unknowns
+  L.group = std::max(1, (6 * largest + COARSE_MAX_UNKNOWNS - 1) / COARSE_MAX_UNKNOWNS);
+  L.cta_agg.assign(nc, -1);
+  L.agg_cta.clear();
+  L.agg_solve.clear();
   L.solve_lo.assign(L.n_solves, 0);
   L.solve_n.assign(L.n_solves, 0);
+  for (int s = 0; s < L.n_solves; ++s) {
+    L.solve_lo[s] = (int)L.agg_solve.size();
+    for (int c = lo[s]; c <= hi[s]; c += L.group) {
+      const int a = (int)L.agg_solve.size();
+      L.agg_cta.push_back(c);
+      L.agg_solve.push_back(s);
+      for (int k = c; k < std::min(c + L.group, hi[s] + 1); ++k) L.cta_agg[k] = a;
+    }
+    L.solve_n[s] = 6 * ((int)L.agg_solve.size() - L.solve_lo[s]);
+  }
+  L.n_agg = (int)L.agg_solve.size();
+  // closing entries: the CTA after the last of each aggregate
+  std::vector<int> ends(L.n_agg + 1, nc);
+  for (int a = 0; a < L.n_agg; ++a) {
+    int c = L.agg_cta[a];
+    while (c < nc && L.cta_agg[c] == a) ++c;
+    ends[a] = c;
+  }
+  // agg_cta as offsets: aggregate a owns CTAs [agg_cta[a], end_a); store the ends in a second half-array
+  // by making every aggregate's run end where the next one starts (runs are consecutive within a solve;
+  // between solves there may be none)
+  std::vector<int> starts = L.agg_cta;
+  L.agg_cta.assign(2 * L.n_agg + 1, nc);
+  for (int a = 0; a < L.n_agg; ++a) { L.agg_cta[2 * a] = starts[a]; L.agg_cta[2 * a + 1] = ends[a]; }
+  L.node_agg.assign(nf, -1);
+  for (int c = 0; c < nc; ++c)
+    if (L.cta_agg[c] >= 0)
+      for (int i = P.seg[c]; i < P.seg[c + 1] && i < nf; ++i) L.node_agg[i] = L.cta_agg[c];
   L.off.assign(L.n_solves, 0);
   L.boff.assign(L.n_solves, 0);
-  std::vector<int> hi(L.n_solves, -1);
-  std::vector<int> lo(L.n_solves, na);
-  for (int a = 0; a < na; ++a) {
-    const int s = L.agg_solve[a];
-    if (s < 0 || s >= L.n_solves) continue;
-    lo[s] = std::min(lo[s], a);
-    hi[s] = std::max(hi[s], a);
-  }
   long long o = 0, bo = 0;
   L.n_max = 0;
   for (int s = 0; s < L.n_solves; ++s) {
-    const int n = hi[s] >= lo[s] ? 6 * (hi[s] - lo[s] + 1) : 0;
-    L.solve_lo[s] = hi[s] >= lo[s] ? lo[s] : 0;
-    L.solve_n[s] = n;
+    const int n = L.solve_n[s];
     L.off[s] = o;
     L.boff[s] = bo;
     o += (long long)n * n;
@@ -267,11 +299,6 @@ void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L) {
   }
   L.total = o;
   L.total_n = bo;
-  // every solve's aggregates must be consecutive (its dense block is indexed from solve_lo)
-  L.consecutive = true;
-  for (int s = 0; s < L.n_solves; ++s)
-    for (int a = lo[s]; a <= hi[s]; ++a)
-      if (L.agg_solve[a] != s) L.consecutive = false;
 }
 
 cudaError_t launch_coarse_build(cudaStream_t st, const DevScene& S, const CoarseDevLayout& D, const int* seg,
@@ -280,13 +307,13 @@ cudaError_t launch_coarse_build(cudaStream_t st, const DevScene& S, const Coarse
                                 const double* f_Hu, double* Ac, double* centre, int* rot, double* gj_buf, int* status) {
   const int na = D.n_agg;
   if (na <= 0 || D.total <= 0) return cudaSuccess;
-  k_coarse_centres<<<na, 128, 0, st>>>(seg, na, x, centre, rot);
+  k_coarse_centres<<<na, 128, 0, st>>>(seg, D.agg_cta, na, x, centre, rot);
   k_zero<<<stride_grid(D.total, 256, 8), 256, 0, st>>>((size_t)D.total, Ac);
   CoarseAsm C{D.node_agg, D.agg_solve, D.solve_lo, D.solve_n, D.off, centre, rot, x, Ac};
   k_coarse_bsr<<<stride_grid(S.nnzb, 256, 8), 256, 0, st>>>(C, S.nf, S.bsr_row, S.bsr_col, val);
   k_coarse_pairs<<<stride_grid(16LL * (cap + n_fric), 256, 8), 256, 0, st>>>(C, S, rec, n_pairs, cap, pairH, n_fric,
                                                                           f_ids, f_w, f_Hu);
-  k_coarse_dead<<<(na + 127) / 128, 128, 0, st>>>(C, seg, na);
+  k_coarse_dead<<<(na + 127) / 128, 128, 0, st>>>(C, seg, D.agg_cta, na);
   count_launch(5);
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int) * D.n_solves, st);
   if (e != cudaSuccess) return e;

@@ -61,25 +61,30 @@ struct __align__(16) PairDesc {
   double xb[4][3];
 };
 
-// Coarse level of the PCG preconditioner (coarse.cu): one aggregate per FEM
-// CTA of the launch (the CTA's row segment), six rigid-body modes each.
+// Coarse level of the PCG preconditioner (coarse.cu): an aggregate is the
+// row segments of a run of consecutive FEM CTAs of one solve (so that a
+// solve's coarse size stays bounded), six rigid-body modes each.
 struct CoarseDev {
-  const double* inv = nullptr;    // per solve: dense (P^T A P)^-1, row-major n_s x n_s at off[s]; null: off
-  const float* inv32 = nullptr;   // its FP32 copy (mixed precision)
+  const float* inv32 = nullptr;   // per solve: dense (P^T A P)^-1 in FP32, row-major n_s x n_s at off[s];
+                                  // null: no coarse level
+  const double* inv64 = nullptr;  // the same in FP64; when set, the FP64 solver applies it in FP64 (tight
+                                  // tolerances: an FP32 coarse product is not a fixed linear operator)
   const long long* off = nullptr; // (solves)
   const int* solve_lo = nullptr;  // (solves) first aggregate of every solve
   const int* solve_n = nullptr;   // (solves) coarse unknowns of every solve (6 per aggregate)
+  const int* cta_agg = nullptr;   // (FEM CTAs) aggregate of every FEM CTA, -1 none
+  const int* agg_cta = nullptr;   // (aggregates, 2) FEM CTAs [first, end) of every aggregate
   const double* centre = nullptr; // (aggregates, 3)
   const int* rot = nullptr;       // (aggregates) 1: rotations kept
   const double* x = nullptr;      // (nf, 3) positions the modes are built at
-  double* part = nullptr;         // (aggregates, 6) P^T v of the vector of the current iteration
+  double* part = nullptr;         // (FEM CTAs, 6) every CTA's part of P^T v for the current iteration
 };
 // host-side layout of the coarse level for one PCG plan
 struct CoarseLayout {
-  int n_agg = 0, n_solves = 0, n_max = 0;
+  int n_agg = 0, n_solves = 0, n_max = 0, n_ctas = 0, group = 1;
   long long total = 0, total_n = 0;
   bool consecutive = true;
-  std::vector<int> node_agg, agg_solve, solve_lo, solve_n;
+  std::vector<int> node_agg, agg_solve, solve_lo, solve_n, cta_agg, agg_cta;
   std::vector<long long> off, boff;
 };
 // the same on the device
@@ -90,9 +95,12 @@ struct CoarseDevLayout {
   const int* agg_solve = nullptr;
   const int* solve_lo = nullptr;
   const int* solve_n = nullptr;
+  const int* agg_cta = nullptr;    // (aggregates, 2) FEM CTAs [first, end) of every aggregate
   const long long* off = nullptr;
   const long long* boff = nullptr;
 };
+// largest coarse size of one solve: runs of CTAs are merged into aggregates until it holds
+constexpr int COARSE_MAX_UNKNOWNS = 768;
 
 // Arguments of one PCG solve (see pcg.cu).  CTAs [0, n_fem_ctas) own the FEM
 // rows seg_row[c] .. seg_row[c + 1]; the others own ABD bodies

@@ -475,18 +475,17 @@ constexpr int PCG_REPLICAS = PCG_REPLICA_COUNT;
 static_assert(PCG_SCENES_MAX <= PCG_THREADS_MAX, "one decision thread per scene");
 struct Shared {
   union {
-    double vals[3][PCG_THREADS_MAX];  // per-thread values of a CTA sum
+    double vals[6][PCG_THREADS_MAX];  // per-thread values of a CTA sum
     double tot[3][PCG_SCENES_MAX];    // per-scene totals (several solves)
   };
   double red[8][12];                // per-warp sums of the ABD rows
   double out[12];                   // results, read by every thread
   double scal[4];                   // scalars of an iteration (the scene's decision thread -> all)
-  double co_a[6], co_b[6];          // coarse images of the CTA's aggregate (FP64: of w and z; mixed: of r and s)
   int action;
   unsigned long long agg[4];        // end of the solve: maxima over the scenes
 };
 
-// Sum over the CTA of N <= 3 per-thread values of type T; results in
+// Sum over the CTA of N <= 6 per-thread values of type T; results in
 // sh.out[0..N) (as FP64) for every thread.
 template <int N, typename T>
 __device__ inline void cta_sum(const T (&v)[N], Shared& sh) {
@@ -595,11 +594,12 @@ __device__ inline double scene_total(const PcgArgs& a, const Shared& sh, int j, 
 // segment; P_i = [I | -[x_i - c]x] maps the aggregate's 6 rigid-body
 // coordinates to node i.
 // ---------------------------------------------------------------------------
-// P^T v over this CTA's rows r0..r1, v_i from get(i, v0, v1, v2), into
-// co.part[6 agg ..] (agg < 0: nothing).  Every thread of the CTA must call it.
+// This CTA's part of P^T v: its rows r0..r1 (of aggregate agg), v_i from
+// get(i, v0, v1, v2), into co.part[6 cta ..] (agg < 0: nothing).  Every
+// thread of the CTA must call it.
 template <typename G>
 __device__ inline void coarse_restrict(const PcgArgs& a, int agg, int r0, int r1, Shared& sh, G&& get) {
-  double t[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
+  double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (agg >= 0) {
     const d3 c = ld3(a.co.centre, agg);
     const bool rot = a.co.rot[agg] != 0;
@@ -609,44 +609,59 @@ __device__ inline void coarse_restrict(const PcgArgs& a, int agg, int r0, int r1
       t[0] += v0; t[1] += v1; t[2] += v2;
       if (rot) {
         const d3 r = ld3(a.co.x, i) - c;
-        q[0] = fma(r.y, v2, fma(-r.z, v1, q[0]));
-        q[1] = fma(r.z, v0, fma(-r.x, v2, q[1]));
-        q[2] = fma(r.x, v1, fma(-r.y, v0, q[2]));
+        t[3] = fma(r.y, v2, fma(-r.z, v1, t[3]));
+        t[4] = fma(r.z, v0, fma(-r.x, v2, t[4]));
+        t[5] = fma(r.x, v1, fma(-r.y, v0, t[5]));
       }
     }
   }
-  cta_sum<3, double>(t, sh);
-  if (threadIdx.x < 3 && agg >= 0) a.co.part[6 * (size_t)agg + threadIdx.x] = sh.out[threadIdx.x];
-  __syncthreads();
-  cta_sum<3, double>(q, sh);
-  if (threadIdx.x < 3 && agg >= 0) a.co.part[6 * (size_t)agg + 3 + threadIdx.x] = sh.out[threadIdx.x];
+  cta_sum<6, double>(t, sh);
+  if (threadIdx.x < 6 && agg >= 0) a.co.part[6 * (size_t)blockIdx.x + threadIdx.x] = sh.out[threadIdx.x];
   __syncthreads();
 }
 
 // The rows of the coarse inverse that belong to aggregate agg (solve s) times
-// the solve's restricted vector co.part: 6 values into res (every thread).
-// Products in the stored precision M of the inverse.  Every thread must call it.
+// the solve's restricted vector (every aggregate's value is the sum of its
+// CTAs' parts): 6 values into res (every thread).  M: the precision of the
+// stored inverse and of the products.  Every thread must call it.
 template <typename M>
-__device__ inline void coarse_own(const PcgArgs& a, const M* inv, int agg, int s, Shared& sh, double res[6]) {
+__device__ inline void coarse_own_t(const PcgArgs& a, const M* inv, int agg, int s, Shared& sh, double res[6]) {
   M acc[6] = {M(0), M(0), M(0), M(0), M(0), M(0)};
   if (agg >= 0 && s >= 0) {
     const int n = a.co.solve_n[s], lo = a.co.solve_lo[s];
     const M* R = inv + a.co.off[s] + (size_t)6 * (agg - lo) * n;
-    const double* v = a.co.part + 6 * (size_t)lo;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const M vj = (M)v[j];
+    // the restricted values of this thread's unknowns first (independent loads), then the products
+    constexpr int PER = (COARSE_MAX_UNKNOWNS + PCG_THREADS_MAX - 1) / PCG_THREADS_MAX;
+    double v[PER];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] = fma(R[(size_t)k * n + j], vj, acc[k]);
+    for (int q = 0; q < PER; ++q) {
+      const int j = threadIdx.x + q * blockDim.x;
+      v[q] = 0.0;
+      if (j < n) {
+        const int b = lo + j / 6, k6 = j - 6 * (j / 6);
+        const int c0 = a.co.agg_cta[2 * b], c1 = a.co.agg_cta[2 * b + 1];
+        for (int c = c0; c < c1; ++c) v[q] += a.co.part[6 * (size_t)c + k6];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = threadIdx.x + q * blockDim.x;
+      if (j < n) {
+        const M vj = (M)v[q];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] = fma(R[(size_t)k * n + j], vj, acc[k]);
+      }
     }
   }
-  const double t0[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-  cta_sum<3, double>(t0, sh);
-  res[0] = sh.out[0]; res[1] = sh.out[1]; res[2] = sh.out[2];
+  const double t[6] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3], (double)acc[4], (double)acc[5]};
+  cta_sum<6, double>(t, sh);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) res[k] = sh.out[k];
   __syncthreads();
-  const double t1[3] = {(double)acc[3], (double)acc[4], (double)acc[5]};
-  cta_sum<3, double>(t1, sh);
-  res[3] = sh.out[0]; res[4] = sh.out[1]; res[5] = sh.out[2];
-  __syncthreads();
+}
+__device__ inline void coarse_own(const PcgArgs& a, int agg, int s, Shared& sh, double res[6]) {
+  if (a.co.inv64) coarse_own_t<double>(a, a.co.inv64, agg, s, sh, res);
+  else coarse_own_t<float>(a, a.co.inv32, agg, s, sh, res);
 }
 
 // P_i c: translation plus rotation theta x (x_i - centre) of node i's aggregate
@@ -886,9 +901,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   }
   // preconditioner block of node i (owned by this CTA)
   auto Dof = [&](int i) -> const M* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvM + 9 * (size_t)i); };
-  // coarse level: this CTA's aggregate (its FEM rows), -1 without one
-  const bool coarse = a.co.inv != nullptr;
-  const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? cta : -1;
+  // coarse level: this CTA's aggregate (its FEM rows), -1 without one; the coarse images of w and z of
+  // the CTA's aggregate, identical in every thread
+  const bool coarse = a.co.inv32 != nullptr;
+  const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? a.co.cta_agg[cta] : -1;
+  double co_w[6] = {0, 0, 0, 0, 0, 0}, co_z[6] = {0, 0, 0, 0, 0, 0};
 
   Vecs<double> V;
   {
@@ -1015,7 +1032,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         v0 = V.r[3 * i]; v1 = V.r[3 * i + 1]; v2 = V.r[3 * i + 2];
       });
       grid.sync();
-      if (on) coarse_own<double>(a, a.co.inv, my_agg, my_sc, sh, cr);
+      if (on) coarse_own(a, my_agg, my_sc, sh, cr);
     }
     if (on) {
       for_nodes([&](int i, const double*) {
@@ -1039,9 +1056,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         v0 = y[0]; v1 = y[1]; v2 = y[2];
       });
       grid.sync();
-      if (on) coarse_own<double>(a, a.co.inv, my_agg, my_sc, sh, cwv);
-      if (on && threadIdx.x < 6) { sh.co_a[threadIdx.x] = cwv[threadIdx.x]; sh.co_b[threadIdx.x] = 0.0; }
-      __syncthreads();
+      if (on) coarse_own(a, my_agg, my_sc, sh, cwv);
+      if (on)
+        for (int k = 0; k < 6; ++k) { co_w[k] = cwv[k]; co_z[k] = 0.0; }
     }
     if (on) {
       double* mdst = par ? V.m1 : V.m0;
@@ -1131,17 +1148,12 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
       grid.sync();
       if (my_act == ACT_STEP) {
         double eta[6];
-        coarse_own<double>(a, a.co.inv, my_agg, my_sc, sh, eta);
+        coarse_own(a, my_agg, my_sc, sh, eta);
         for (int k = 0; k < 6; ++k) {
-          const double cz = fma(beta, sh.co_b[k], eta[k]);
-          cwv[k] = fma(-alpha, cz, sh.co_a[k]);
+          co_z[k] = fma(beta, co_z[k], eta[k]);
+          co_w[k] = fma(-alpha, co_z[k], co_w[k]);
+          cwv[k] = co_w[k];
         }
-        __syncthreads();
-        if (threadIdx.x < 6) {
-          sh.co_b[threadIdx.x] = fma(beta, sh.co_b[threadIdx.x], eta[threadIdx.x]);
-          sh.co_a[threadIdx.x] = cwv[threadIdx.x];
-        }
-        __syncthreads();
       }
     }
     if (my_act == ACT_STEP) {
@@ -1291,9 +1303,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     if (!pcg_ok(a, ab0 >= 0 && ab0 <= ab1 && ab1 <= S.nab, 13)) ab0 = ab1 = 0;
   }
   auto Dof = [&](int i) -> const F* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvF + 9 * (size_t)i); };
-  // coarse level: this CTA's aggregate (its FEM rows), -1 without one; applied in FP32
+  // coarse level: this CTA's aggregate (its FEM rows), -1 without one, applied in FP32; the coarse
+  // images of r and s of the CTA's aggregate, identical in every thread
   const bool coarse = a.co.inv32 != nullptr;
-  const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? cta : -1;
+  const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? a.co.cta_agg[cta] : -1;
+  F co_r[6] = {F(0), F(0), F(0), F(0), F(0), F(0)}, co_s[6] = {F(0), F(0), F(0), F(0), F(0), F(0)};
 
   F* base = (F*)a.vec;
   F* r = base;
@@ -1430,9 +1444,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       });
       grid.sync();
       if (on) {
-        coarse_own<F>(a, a.co.inv32, my_agg, my_sc, sh, cr);
-        if (threadIdx.x < 6) { sh.co_a[threadIdx.x] = cr[threadIdx.x]; sh.co_b[threadIdx.x] = 0.0; }
-        __syncthreads();
+        coarse_own(a, my_agg, my_sc, sh, cr);
+        for (int k = 0; k < 6; ++k) { co_r[k] = (F)cr[k]; co_s[k] = F(0); }
       }
     }
     if (on)
@@ -1515,17 +1528,12 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     double crv[6] = {0, 0, 0, 0, 0, 0};
     if (coarse && my_act == ACT_STEP) {
       double eta[6];
-      coarse_own<F>(a, a.co.inv32, my_agg, my_sc, sh, eta);
+      coarse_own(a, my_agg, my_sc, sh, eta);
       for (int k = 0; k < 6; ++k) {
-        const F cs = fmaf(beta, (F)sh.co_b[k], (F)eta[k]);
-        crv[k] = (double)fmaf(-alpha, cs, (F)sh.co_a[k]);
+        co_s[k] = fmaf(beta, co_s[k], (F)eta[k]);
+        co_r[k] = fmaf(-alpha, co_s[k], co_r[k]);
+        crv[k] = (double)co_r[k];
       }
-      __syncthreads();
-      if (threadIdx.x < 6) {
-        sh.co_b[threadIdx.x] = (double)fmaf(beta, (F)sh.co_b[threadIdx.x], (F)eta[threadIdx.x]);
-        sh.co_a[threadIdx.x] = crv[threadIdx.x];
-      }
-      __syncthreads();
     }
     if (my_act == ACT_STEP) {
       g_l = F(0);

@@ -158,7 +158,15 @@ struct ipcsim {
   bool co_ok = false;            // the last build succeeded (else block Jacobi only)
   bool co_built_this_step = false;
   int *co_node_agg = nullptr, *co_agg_solve = nullptr, *co_solve_lo = nullptr, *co_solve_n = nullptr;
+  int *co_cta_agg = nullptr, *co_agg_cta = nullptr;
+  int co_cap_ctas = 0;
   int* co_rot = nullptr;
+  // rebuild policy: the coarse level is kept across steps while the PCG iterations stay near those of
+  // the first step after its build
+  int co_steps_since_build = 0;
+  double co_iters_ref = 0.0;      // PCG iterations per solve in the step of the last build
+  long long co_step_iters = 0, co_step_solves = 0;  // this step so far
+  double co_last_step_avg = 0.0;  // PCG iterations per solve of the previous step
   int* co_status = nullptr;
   long long *co_off = nullptr, *co_boff = nullptr;
   double *co_Ac = nullptr, *co_centre = nullptr, *co_x = nullptr, *co_part = nullptr, *co_gj = nullptr;
@@ -476,9 +484,15 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
       dfree(sim, sim->co_Ac); dfree(sim, sim->co_Ac32);
       sim->co_Ac = nullptr; sim->co_Ac32 = nullptr;
       if ((s = dalloc(sim, &sim->co_Ac, (size_t)L.total))) return s;
-      if (fp32 || sim->P.precision == IPC_PREC_MIXED)
-        if ((s = dalloc(sim, &sim->co_Ac32, (size_t)L.total))) return s;
+      if ((s = dalloc(sim, &sim->co_Ac32, (size_t)L.total))) return s;
       sim->co_cap = L.total;
+    }
+    if (L.n_ctas > sim->co_cap_ctas) {
+      dfree(sim, sim->co_cta_agg); dfree(sim, sim->co_part);
+      sim->co_cta_agg = nullptr; sim->co_part = nullptr;
+      if ((s = dalloc(sim, &sim->co_cta_agg, (size_t)L.n_ctas))) return s;
+      if ((s = dalloc(sim, &sim->co_part, 6 * (size_t)L.n_ctas))) return s;
+      sim->co_cap_ctas = L.n_ctas;
     }
     if (L.total_n > sim->co_cap_n) {
       dfree(sim, sim->co_gj);
@@ -487,12 +501,12 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
       sim->co_cap_n = L.total_n;
     }
     if (L.n_agg > sim->co_cap_agg) {
-      dfree(sim, sim->co_agg_solve); dfree(sim, sim->co_centre); dfree(sim, sim->co_rot); dfree(sim, sim->co_part);
-      sim->co_agg_solve = nullptr; sim->co_centre = nullptr; sim->co_rot = nullptr; sim->co_part = nullptr;
+      dfree(sim, sim->co_agg_solve); dfree(sim, sim->co_centre); dfree(sim, sim->co_rot); dfree(sim, sim->co_agg_cta);
+      sim->co_agg_solve = nullptr; sim->co_centre = nullptr; sim->co_rot = nullptr; sim->co_agg_cta = nullptr;
       if ((s = dalloc(sim, &sim->co_agg_solve, (size_t)L.n_agg))) return s;
       if ((s = dalloc(sim, &sim->co_centre, 3 * (size_t)L.n_agg))) return s;
       if ((s = dalloc(sim, &sim->co_rot, (size_t)L.n_agg))) return s;
-      if ((s = dalloc(sim, &sim->co_part, 6 * (size_t)L.n_agg))) return s;
+      if ((s = dalloc(sim, &sim->co_agg_cta, 2 * (size_t)L.n_agg + 1))) return s;
       sim->co_cap_agg = L.n_agg;
     }
     if (L.n_solves > sim->co_cap_solves) {
@@ -512,6 +526,9 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
     cudaStream_t cs = sim->st;
     CUDA_TRY(cudaMemcpyAsync(sim->co_node_agg, L.node_agg.data(), sizeof(int) * sim->nf, cudaMemcpyHostToDevice, cs));
     CUDA_TRY(cudaMemcpyAsync(sim->co_agg_solve, L.agg_solve.data(), sizeof(int) * L.n_agg, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->co_cta_agg, L.cta_agg.data(), sizeof(int) * L.n_ctas, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(sim->co_agg_cta, L.agg_cta.data(), sizeof(int) * L.agg_cta.size(), cudaMemcpyHostToDevice,
+                             cs));
     CUDA_TRY(cudaMemcpyAsync(sim->co_solve_lo, L.solve_lo.data(), sizeof(int) * L.n_solves, cudaMemcpyHostToDevice, cs));
     CUDA_TRY(cudaMemcpyAsync(sim->co_solve_n, L.solve_n.data(), sizeof(int) * L.n_solves, cudaMemcpyHostToDevice, cs));
     CUDA_TRY(cudaMemcpyAsync(sim->co_off, L.off.data(), sizeof(long long) * L.n_solves, cudaMemcpyHostToDevice, cs));
@@ -522,11 +539,11 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
   if (!L.consecutive || L.total <= 0) return IPC_OK;
   cudaStream_t cs = sim->st;
   CUDA_TRY(cudaMemcpyAsync(sim->co_x, sim->xv, sizeof(double) * 3 * sim->nf, cudaMemcpyDeviceToDevice, cs));
-  CUDA_TRY(cudaMemsetAsync(sim->co_part, 0, sizeof(double) * 6 * L.n_agg, cs));
+  CUDA_TRY(cudaMemsetAsync(sim->co_part, 0, sizeof(double) * 6 * L.n_ctas, cs));
   CoarseDevLayout D;
   D.n_agg = L.n_agg; D.n_solves = L.n_solves; D.n_max = L.n_max; D.total = L.total; D.total_n = L.total_n;
   D.node_agg = sim->co_node_agg; D.agg_solve = sim->co_agg_solve; D.solve_lo = sim->co_solve_lo;
-  D.solve_n = sim->co_solve_n; D.off = sim->co_off; D.boff = sim->co_boff;
+  D.solve_n = sim->co_solve_n; D.off = sim->co_off; D.boff = sim->co_boff; D.agg_cta = sim->co_agg_cta;
   CUDA_TRY(launch_coarse_build(cs, sim->S, D, sim->d_seg, sim->co_x, sim->Hval, sim->rec, &sim->sc_dev->n_pairs,
                                sim->cap, sim->pairH, n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->co_Ac,
                                sim->co_centre, sim->co_rot, sim->co_gj, sim->co_status));
@@ -536,7 +553,7 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
   CUDA_TRY(cudaStreamSynchronize(cs));
   for (int v : sim->co_status_h)
     if (v) return IPC_OK;  // a pivot failed: block Jacobi alone for this build
-  if (sim->co_Ac32) launch_to_float(cs, (size_t)L.total, sim->co_Ac, sim->co_Ac32);
+  launch_to_float(cs, (size_t)L.total, sim->co_Ac, sim->co_Ac32);
   sim->co_ok = true;
   return IPC_OK;
 }
@@ -611,8 +628,12 @@ ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric)
   a.abd_val32 = sim->abd_val32;
   a.abd_cap = sim->abd_cap;
   if (sim->co_ok) {
-    a.co.inv = fp32 ? nullptr : sim->co_Ac;
-    a.co.inv32 = fp32 ? sim->co_Ac32 : nullptr;
+    a.co.inv32 = sim->co_Ac32;
+    // tight tolerances (parity, adjoint) need a fixed linear preconditioner: the FP64 solver then applies
+    // the coarse inverse in FP64; at the default tolerance the FP32 product is accurate enough and cheaper
+    a.co.inv64 = (!fp32 && rtol < 1e-7) ? sim->co_Ac : nullptr;
+    a.co.cta_agg = sim->co_cta_agg;
+    a.co.agg_cta = sim->co_agg_cta;
     a.co.off = sim->co_off;
     a.co.solve_lo = sim->co_solve_lo;
     a.co.solve_n = sim->co_solve_n;
@@ -1456,6 +1477,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
   ipc_status s = IPC_OK;
   sim->cand_valid = false;
   sim->co_built_this_step = false;
+  sim->co_step_iters = sim->co_step_solves = 0;
   bool rec_current = false;  // sim->rec holds the active set at the current iterate
   const bool sweep = P.broad_phase != IPC_BROAD_ALL_PAIRS;
   // friction lag on the pairs active at x_t
@@ -1569,11 +1591,28 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       sim->autotune_pending = false;
     }
     if ((s = pcg_prepare(sim, fp32))) return s;
-    // the coarse level is built once per step (and again when the launch shape changed); the later Newton
-    // iterations of the step keep it as their preconditioner
-    if (!sim->co_built_this_step || sim->co_plan_stamp != sim->plan_stamp) {
+    // the coarse level is rebuilt at the first Newton iteration of a step when the launch shape changed,
+    // when it failed or is missing, after coarse_rebuild steps (every step by default), or when the
+    // previous step needed 30 % more PCG iterations per solve than the step it was built in
+    const int keep = P.coarse_rebuild;
+    if (keep < 0 && !(it == 0 && sim->co_built_this_step)) {
+      // rebuilt at every Newton iteration
       if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
       sim->co_built_this_step = true;
+    } else if (it == 0 && !sim->co_built_this_step) {
+      const bool stale = sim->co_plan_stamp != sim->plan_stamp || !sim->co_ok ||
+                         sim->co_steps_since_build >= std::max(keep, 1) ||
+                         (sim->co_iters_ref > 0.0 && sim->co_last_step_avg > 1.3 * sim->co_iters_ref);
+      if (stale) {
+        if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
+        sim->co_steps_since_build = 0;
+        sim->co_iters_ref = 0.0;
+      }
+      sim->co_built_this_step = true;
+    } else if (sim->co_plan_stamp != sim->plan_stamp) {
+      if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
+      sim->co_steps_since_build = 0;
+      sim->co_iters_ref = 0.0;
     }
     prof_end(sim, PROF_PCG_SETUP);
     prof_begin(sim, PROF_PCG);
@@ -1630,6 +1669,8 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       sim->pcg_fric_iters_acc += (long long)h.pcg_out[0] * (P.mu > 0 ? sim->n_fric : 0);
     }
     st.pcg_iters_max = std::max(st.pcg_iters_max, h.pcg_out[0]);
+    sim->co_step_iters += h.pcg_out[0];
+    ++sim->co_step_solves;
     if (h.pcg_out[1] == 3) ++st.pcg_unconverged;
     st.n_pairs_max = std::max(st.n_pairs_max, h.n_pairs);
     st.n_ccd_max = std::max(st.n_ccd_max, h.n_ccd);
@@ -1739,6 +1780,12 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
   }
   if (!converged) return finish(IPC_ERR_NEWTON_MAXIT, "Newton did not converge");
   CUDA_TRY(cudaGetLastError());
+  // PCG iterations per solve of this step, for the coarse level's rebuild policy
+  if (sim->co_step_solves > 0) {
+    sim->co_last_step_avg = (double)sim->co_step_iters / sim->co_step_solves;
+    if (sim->co_iters_ref == 0.0) sim->co_iters_ref = sim->co_last_step_avg;
+  }
+  ++sim->co_steps_since_build;
   launch_velocity(cs, ndof, sim->z, sim->z_t, 1.0 / dt, sim->zd);
   CUDA_TRY(cudaStreamSynchronize(cs));
   CUDA_TRY(cudaGetLastError());
@@ -1919,7 +1966,8 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     if ((s = pcg_prepare(sim, 0))) return s;
     if ((s = coarse_setup(sim, 0, n_fric_adj))) return s;
     if ((s = pcg_run(sim, 0, 1e-12, 10 * ndof + 1000, n_fric_adj))) return s;
-    sim->co_built_this_step = false;  // the next step builds its own coarse level
+    // the coarse level now belongs to this adjoint's Hessian: the next step builds its own
+    sim->co_steps_since_build = 1 << 20;
   }
   // contractions with lam (= sim->p)
   if (glogE) launch_theta_grad(cs, S, sim->xv, sim->p, dt2, glogE);
@@ -1969,6 +2017,15 @@ ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_nex
   return IPC_OK;
 }
 
+ipc_status sim_coarse_info(const ipcsim* sim, long long* out4) {
+  if (!sim || !out4) return IPC_ERR_ARG;
+  out4[0] = sim->co.n_agg;
+  out4[1] = sim->co.n_solves;
+  out4[2] = sim->co.n_max;
+  out4[3] = sim->co_ok ? 1 : 0;
+  return IPC_OK;
+}
+
 ipc_status sim_pcg_residency(ipcsim* sim, int streamed) {
   if (!sim) return IPC_ERR_ARG;
   sim->pcg_streamed = streamed != 0;
@@ -2009,6 +2066,15 @@ ipc_status sim_get_state(const ipcsim* csim, double* x, double* v, double* q, do
   if (q && nab) CUDA_TRY(cudaMemcpyAsync(q, sim->z + 3 * sim->nf, nab, k, sim->st));
   if (qd && nab) CUDA_TRY(cudaMemcpyAsync(qd, sim->zd + 3 * sim->nf, nab, k, sim->st));
   CUDA_TRY(cudaStreamSynchronize(sim->st));
+  return IPC_OK;
+}
+
+ipc_status sim_positions(const ipcsim* csim, double* xv_dev) {
+  ipcsim* sim = const_cast<ipcsim*>(csim);
+  if (!sim || !xv_dev) return IPC_ERR_ARG;
+  launch_vertex_positions(sim->st, sim->S, sim->z, sim->xk, xv_dev);
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
 

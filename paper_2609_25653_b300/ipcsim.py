@@ -46,7 +46,7 @@ class Params(C.Structure):
                 ("eps_v", C.c_double), ("k_c", C.c_double), ("kappa_A", C.c_double), ("newton_tol", C.c_double),
                 ("pcg_rtol", C.c_double), ("s_ccd", C.c_double), ("max_newton", C.c_int), ("max_pcg", C.c_int),
                 ("precision", C.c_int), ("pair_capacity", C.c_int), ("broad_phase", C.c_int),
-                ("pair_capacity_max", C.c_int), ("preconditioner", C.c_int)]
+                ("pair_capacity_max", C.c_int), ("preconditioner", C.c_int), ("coarse_rebuild", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -89,6 +89,21 @@ class TorchAllocator:
         self.struct = Allocator(self._alloc, self._free, None)
 
 
+class RenderScene(C.Structure):
+    _fields_ = [("n_verts", C.c_int), ("n_tris", C.c_int), ("tris_host", ip), ("type_host", ip),
+                ("rgb_host", C.POINTER(C.c_float))]
+
+
+class Camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("fwd", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3),
+                ("tan_half_fov", C.c_float), ("width", C.c_int), ("height", C.c_int)]
+
+
+class RenderParams(C.Structure):
+    _fields_ = [("spp", C.c_int), ("max_depth", C.c_int), ("n_shadow", C.c_int), ("lambda_s", C.c_float),
+                ("eps", C.c_float), ("seed", C.c_ulonglong)]
+
+
 class StepStats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
                 ("pcg_iters_max", C.c_int), ("n_pairs_max", C.c_int), ("n_friction_pairs", C.c_int),
@@ -129,6 +144,7 @@ SIGNATURES = {
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
     "sim_pcg_partition": ([ip, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip, ip, ip, ip, ip], C.c_int),
     "sim_pcg_residency": ([vp, C.c_int], C.c_int),
+    "sim_coarse_info": ([vp, C.POINTER(C.c_longlong)], C.c_int),
     "sim_device_peaks": ([dp], C.c_int),
     "sim_create_with_allocator": ([C.POINTER(SceneDesc), C.c_int, C.POINTER(Params), C.POINTER(Allocator), vp,
                                    C.POINTER(vp)], C.c_int),
@@ -139,6 +155,11 @@ SIGNATURES = {
     "sim_dual_mesh_apply": ([vp, vp, vp, vp], C.c_int),
     "sim_dual_mesh_last_error": ([], C.c_char_p),
     "sim_dual_mesh_destroy": ([vp], None),
+    "sim_render_create": ([C.POINTER(RenderScene), C.POINTER(vp)], C.c_int),
+    "sim_positions": ([vp, vp], C.c_int),
+    "sim_render_frame": ([vp, vp, C.POINTER(Camera), C.POINTER(RenderParams), vp, vp], C.c_int),
+    "sim_render_last_error": ([], C.c_char_p),
+    "sim_render_destroy": ([vp], None),
 }
 
 PROFILE_STAGES = ["pcg", "elastic", "barrier", "cull", "ccd", "friction", "other", "pcg_setup"]
@@ -220,7 +241,8 @@ def make_params(p: dict, precision=PREC_FP64) -> Params:
                   pcg_rtol=p.get("pcg_rtol", 1e-4), s_ccd=p.get("s_ccd", 0.1), max_newton=int(p.get("max_newton", 100)),
                   max_pcg=int(p.get("max_pcg", 0)), precision=int(precision), pair_capacity=int(p.get("pair_capacity", 0)),
                   broad_phase=int(p.get("broad_phase", BROAD_LBVH)), pair_capacity_max=int(p.get("pair_capacity_max", 0)),
-                  preconditioner=int(p.get("preconditioner", PRECOND_TWO_LEVEL)))
+                  preconditioner=int(p.get("preconditioner", PRECOND_TWO_LEVEL)),
+                  coarse_rebuild=int(p.get("coarse_rebuild", 0)))
 
 
 def _fill_desc(d, scene, keep):
@@ -365,6 +387,14 @@ class Simulator:
                                          qd.ctypes.data_as(vp) if self.nab else None, 0))
         return x, v, q, qd
 
+    def positions(self, out=None):
+        """All vertex positions (FEM | ABD surface | kinematic) of the current state, device (nv, 3)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.nv, 3), dtype=torch.float64, device="cuda")
+        self._check(load().sim_positions(self.h, _ptr(out)))
+        return out
+
     def get_state_device(self, x, v=None, q=None, qd=None):
         self._check(load().sim_get_state(self.h, _ptr(x), _ptr(v), _ptr(q), _ptr(qd), 1))
 
@@ -440,6 +470,18 @@ class Simulator:
         out = (C.c_longlong * 3)()
         self._check(load().sim_memory(self.h, out))
         return tuple(out)
+
+    def coarse_info(self):
+        """(aggregates, solves, coarse unknowns of the largest solve, last build ok) of the two-level
+        preconditioner."""
+        out = (C.c_longlong * 4)()
+        self._check(load().sim_coarse_info(self.h, out))
+        return tuple(int(v) for v in out)
+
+    def coarse_size(self):
+        """Coarse unknowns of the largest solve of the last build (0 when the last build failed)."""
+        a, s, n, ok = self.coarse_info()
+        return n if ok else 0
 
     def pcg_residency(self, streamed: bool):
         """streamed=True: the PCG reads its operator from global memory in every iteration (never staged in
@@ -561,6 +603,57 @@ class DualMesh:
     def close(self):
         if getattr(self, "h", None):
             load().sim_dual_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MAT_DIFFUSE, MAT_EMISSIVE, MAT_BACKGROUND, MAT_TRANSPARENT = 0, 1, 2, 3
+
+
+class Renderer:
+    """Headless path tracer of simulated frames (sim_render_*): triangles (n, 3), material per triangle
+    (MAT_*), colour per triangle (albedo / radiance / C_tex / transmittance)."""
+
+    def __init__(self, tris, types, rgb, n_verts):
+        self._t = _i32(tris)
+        self._ty = _i32(types)
+        self._rgb = np.ascontiguousarray(rgb, dtype=np.float32)
+        d = RenderScene(int(n_verts), len(self._t), self._t.ctypes.data_as(ip), self._ty.ctypes.data_as(ip),
+                        self._rgb.ctypes.data_as(C.POINTER(C.c_float)))
+        h = C.c_void_p()
+        code = load().sim_render_create(C.byref(d), C.byref(h))
+        if code != IPC_OK:
+            raise IpcError(code, load().sim_render_last_error().decode())
+        self.h = h
+
+    def render(self, x_dev, cam, spp=4, max_depth=2, n_shadow=8, lambda_s=0.8, eps=1e-5, seed=0, out=None,
+               stream=None):
+        """Linear-RGB frame (height, width, 3) float32 on the device at vertex positions x_dev (n, 3) float64.
+        cam: (13 floats eye, fwd, right, up, tan(fov/2)), width, height."""
+        import torch
+        c, w, h = cam
+        c = np.asarray(c, np.float32)
+        cm = Camera()
+        for k in range(3):
+            cm.eye[k], cm.fwd[k], cm.right[k], cm.up[k] = float(c[k]), float(c[3 + k]), float(c[6 + k]), float(c[9 + k])
+        cm.tan_half_fov, cm.width, cm.height = float(c[12]), int(w), int(h)
+        p = RenderParams(int(spp), int(max_depth), int(n_shadow), float(lambda_s), float(eps), int(seed))
+        if out is None:
+            out = torch.empty((h, w, 3), dtype=torch.float32, device=x_dev.device)
+        st = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        code = load().sim_render_frame(self.h, _ptr(x_dev.contiguous()), C.byref(cm), C.byref(p), _ptr(out), st)
+        if code != IPC_OK:
+            raise IpcError(code, "sim_render_frame failed")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sim_render_destroy(self.h)
             self.h = None
 
     def __del__(self):

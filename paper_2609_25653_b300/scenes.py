@@ -570,6 +570,58 @@ def material_identification(seed: int = 0, n_steps: int = 100, tip_cell=0.97e-3,
     return sc
 
 
+def render_setup(sc: dict, sim_surface_tris, n_sim_verts: int, seed: int = 0):
+    """A render scene around a simulation scene: the simulated surface triangles (global vertex ids) as
+    diffuse surfaces (fingertips light grey, affine bodies orange, kinematic bodies dark grey), a
+    reconstructed-background stand-in (a 1.2 m table top and a back wall cut into quads with a seeded
+    per-quad texture colour, Eq. 7 material), two rectangular area lights, and a camera looking at the
+    gripper.  Returns (extra vertices (m, 3) appended after the simulated ones, triangles, material per
+    triangle, colour per triangle, camera (13 floats, width, height))."""
+    rng = SplitMix64(seed + 9000)
+    nf = len(sc["fem_X"])
+    n_abd_v = sum(a["X"].shape[0] for a in sc.get("abd", []))
+    tris = [np.asarray(sim_surface_tris, np.int64)]
+    t = tris[0]
+    kind = np.where(t.max(1) < nf, 0, np.where(t.max(1) < nf + n_abd_v, 1, 2))
+    rgb = [np.array([[0.75, 0.75, 0.72], [0.9, 0.5, 0.15], [0.25, 0.25, 0.28]])[kind]]
+    types = [np.zeros(len(t), np.int64)]
+    extra = []
+    base = n_sim_verts
+
+    def add_quad(c, u, v, mtype, colour):
+        nonlocal base
+        c, u, v = (np.asarray(a, float) for a in (c, u, v))
+        extra.append(np.array([c - u - v, c + u - v, c + u + v, c - u + v]))
+        tris.append(np.array([[base, base + 1, base + 2], [base, base + 2, base + 3]]))
+        types.append(np.full(2, mtype))
+        rgb.append(np.tile(np.asarray(colour, float), (2, 1)))
+        base += 4
+
+    cells = 12
+    half = 0.6 / cells
+    u = rng.uniform(3 * 2 * cells * cells)
+    k = 0
+    for i in range(cells):
+        for j in range(cells):
+            # table top: warm wood-like noise; back wall: cool grey noise
+            add_quad((-0.6 + (2 * i + 1) * half, -0.6 + (2 * j + 1) * half, -1e-4), (half, 0, 0), (0, half, 0), 2,
+                     0.45 + 0.25 * u[3 * k:3 * k + 3] * np.array([1.0, 0.8, 0.5]))
+            k += 1
+            add_quad((-0.6 + (2 * i + 1) * half, 0.3, (2 * j + 1) * half), (half, 0, 0), (0, 0, half), 2,
+                     0.55 + 0.2 * u[3 * k:3 * k + 3] * np.array([0.8, 0.85, 1.0]))
+            k += 1
+    add_quad((-0.15, -0.1, 0.45), (0.08, 0, 0), (0, 0.08, 0), 1, [12.0, 11.5, 10.5])
+    add_quad((0.2, -0.25, 0.35), (0.05, 0, 0), (0, 0, 0.05), 1, [6.0, 6.5, 7.0])
+    eye = np.array([0.0, -0.32, 0.16])
+    target = np.array([0.0, 0.0, 0.05])
+    f = (target - eye) / np.linalg.norm(target - eye)
+    r = np.cross(f, [0, 0, 1.0]); r /= np.linalg.norm(r)
+    up = np.cross(r, f)
+    cam = (np.concatenate([eye, f, r, up, [math.tan(math.radians(45.0) / 2)]]).astype(np.float32), 640, 360)
+    return (np.concatenate(extra), np.concatenate(tris).astype(np.int32), np.concatenate(types).astype(np.int32),
+            np.concatenate(rgb).astype(np.float32), cam)
+
+
 def abd_box_drop(n_steps: int = 6, mu: float = 0.3, **param_overrides) -> dict:
     """A 20 mm rigid (ABD) box, slightly tilted, falling onto a fixed ground triangle, beside a
     soft 2 x 2 x 2 mm block resting on the same ground (ABD-kinematic and FEM-kinematic contact)."""
