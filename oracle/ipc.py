@@ -452,14 +452,28 @@ class Scene:
         self.stitch_b = _i32(sc.get("stitch_b", np.zeros(0, np.int32)))
         self.stitch_X = _f64(sc.get("stitch_X", np.zeros((0, 3))))
 
+        # joints between affine bodies (E_joint of Eq. 3): quadratic springs
+        # 1/2 k |J_a(abar) q_a - J_b(bbar) q_b - t|^2, where J(v) = [I, v0 I, v1 I, v2 I] maps a body-frame
+        # point v to world (x = p + A v) and [0, v0 I, v1 I, v2 I] a body-frame direction; body b = -1 is
+        # the world (its term vanishes, t is the world anchor)
+        jn = sc.get("joints", [])
+        self.n_joints = len(jn)
+        self.joint_body = np.array([[j["a"], j["b"]] for j in jn], np.int64).reshape(-1, 2)
+        self.joint_kind = np.array([[j["a_kind"], j["b_kind"]] for j in jn], np.int64).reshape(-1, 2)
+        self.joint_vec = np.array([[j["a_vec"], j["b_vec"]] for j in jn], np.float64).reshape(-1, 2, 3)
+        self.joint_k = np.array([j["k"] for j in jn], np.float64)
+        self.joint_t = np.array([j.get("t", (0.0, 0.0, 0.0)) for j in jn], np.float64).reshape(-1, 3)
+
         # scalar parameters fixed at creation -----------------------------
         surf_fem_edges = self.edges[(self.edges[:, 0] < self.nf) & (self.edges[:, 1] < self.nf)]
         if len(surf_fem_edges):
             d = Xrest[surf_fem_edges[:, 0]] - Xrest[surf_fem_edges[:, 1]]
             ell = float(np.mean(np.sqrt(np.einsum("ij,ij->i", d, d))))
-        else:
+        elif len(vol):
             ell = float(np.mean(np.cbrt(vol)))
-        Emax = float(np.exp(np.max(sc["fem_logE"])))
+        else:
+            ell = self.dhat  # no deformable body: the automatic stiffnesses use dhat and E = 1e5 Pa
+        Emax = float(np.exp(np.max(sc["fem_logE"]))) if len(sc["fem_logE"]) else 1e5
         self.kappa = P["kappa"] if P["kappa"] > 0 else Emax * ell / barrier_d2_dist(0.5 * self.dhat, self.dhat)
         self.k_c = P["k_c"] if P["k_c"] > 0 else 100.0 * Emax * ell
         free_pts = [X]
@@ -492,6 +506,15 @@ class Scene:
             Tm = Ts[i]
             out[3 * o:3 * (o + n)] = (_f64(K["X"]) @ Tm[:, :3].T + Tm[:, 3]).reshape(-1)
             o += n
+        return out
+
+    def joint_targets(self, step):
+        """The joints' b-side vectors and targets of step `step` (scene keys joint_b / joint_t, per step)."""
+        out = {}
+        if self.n_joints and "joint_b" in self.sc:
+            out["joint_b"] = _f64(self.sc["joint_b"][step])
+        if self.n_joints and "joint_t" in self.sc:
+            out["joint_t"] = _f64(self.sc["joint_t"][step])
         return out
 
     def stitch_targets(self, step):
@@ -629,10 +652,42 @@ class Scene:
                 idx = np.arange(base + 3, base + 12)
                 H = H + sp.csr_matrix((dt2 * Ha.reshape(-1), (np.repeat(idx, 9), np.tile(idx, 9))),
                                       shape=(self.ndof, self.ndof))
-        E = E_in + dt2 * (total_pot + E_abd)
+        # joints (E_joint): the drive directions of this step come from ctx["joint_b"] when given
+        E_jt = 0.0
+        if self.n_joints:
+            G, t = self.joint_operator(ctx.get("joint_b"), ctx.get("joint_t"))
+            r = G @ z - t
+            kk = np.repeat(self.joint_k, 3)
+            E_jt = 0.5 * float(r @ (kk * r))
+            if want_grad:
+                g = g + dt2 * (G.T @ (kk * r))
+            if want_hess:
+                H = H + dt2 * (G.T @ sp.diags(kk) @ G)
+        E = E_in + dt2 * (total_pot + E_abd + E_jt)
         info = dict(n_pairs=len(rec), min_s=float(s.min()) if len(s) else math.inf,
-                    E_inertia=E_in, E_elastic=E_pot, E_barrier=E_bar, E_friction=E_fr, E_stitch=E_st, E_abd=E_abd)
+                    E_inertia=E_in, E_elastic=E_pot, E_barrier=E_bar, E_friction=E_fr, E_stitch=E_st, E_abd=E_abd,
+                    E_joint=E_jt)
         return E, g, H, info
+
+    def joint_operator(self, joint_b=None, joint_t=None):
+        """G (3 n_joints x ndof) and t with r_j = (G z - t)_j = J_a q_a - J_b q_b - t_j for every joint."""
+        rows, cols, vals = [], [], []
+        for j in range(self.n_joints):
+            for side, sign in ((0, 1.0), (1, -1.0)):
+                body = int(self.joint_body[j, side])
+                if body < 0:
+                    continue
+                v = self.joint_vec[j, side] if (side == 0 or joint_b is None) else _f64(joint_b[j])
+                w = (0.0 if self.joint_kind[j, side] == 1 else 1.0, v[0], v[1], v[2])
+                base = self.n_fem_dof + 12 * body
+                for m in range(4):
+                    for d in range(3):
+                        rows.append(3 * j + d)
+                        cols.append(base + 3 * m + d)
+                        vals.append(sign * w[m])
+        G = sp.csr_matrix((vals, (rows, cols)), shape=(3 * self.n_joints, self.ndof))
+        t = (self.joint_t if joint_t is None else _f64(joint_t)).reshape(-1)
+        return G, t
 
     def energy(self, z, ctx):
         return self.evaluate(z, ctx, want_grad=False, want_hess=False)[0]
@@ -678,7 +733,7 @@ class Oracle:
         z_tilde = z_t + S.dt * self.zd + S.dt * S.dt * S.grav_acc
         x_t = S.positions(z_t)
         ctx = dict(z_tilde=z_tilde, x_t=x_t, lag=S.friction_lag(x_t.reshape(-1)) if S.mu_f > 0 else [],
-                   stitch_hat=S.stitch_targets(t1))
+                   stitch_hat=S.stitch_targets(t1), **S.joint_targets(t1))
         zD_hat = S.kin_positions(t1)
         F = slice(0, S.n_free)
         D = slice(S.n_free, S.ndof)
@@ -760,7 +815,7 @@ def set_material(o: "Oracle", logE=None, mu=None):
 def step_context(S, z_t, zd_t, step_next):
     x_t = S.positions(z_t)
     ctx = dict(z_tilde=z_t + S.dt * zd_t + S.dt * S.dt * S.grav_acc, x_t=x_t, lag=[], lag_kind=[], lag_eps_x=[],
-               stitch_hat=S.stitch_targets(step_next))
+               stitch_hat=S.stitch_targets(step_next), **S.joint_targets(step_next))
     if S.mu_f > 0:
         rec, _ = S.active_pairs(x_t.reshape(-1))
         ctx["lag"] = S.friction_lag(x_t.reshape(-1))

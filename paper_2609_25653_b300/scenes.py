@@ -622,6 +622,78 @@ def render_setup(sc: dict, sim_surface_tris, n_sim_verts: int, seed: int = 0):
             np.concatenate(rgb).astype(np.float32), cam)
 
 
+def jointed_arm(n_links: int = 3, n_steps: int = 12, swing: float = 0.6, with_block: bool = True,
+                gravity: bool = True, **param_overrides) -> dict:
+    """A planar arm of affine (ABD) links joined by revolute joints with drive potentials (E_joint of
+    Eq. 3): link i is a 40 x 8 x 8 mm box (density 1000), hinged to link i - 1 (link 0 to the world) about
+    the vertical axis by two point springs on the hinge axis (k 2e4 N/m; the boxes stop 4 mm short of
+    the hinges, so that neighbouring links stay apart when they turn), and driven toward its joint angle
+    theta_i(t) by a direction spring between the link's axis and the parent's axis turned by theta_i
+    (k 40 N/m).  The joint angles ramp to `swing` (rad, sign alternating) over the first steps, sweeping
+    the tip into a soft 10 mm block (E 1e5) resting on a ground triangle.  Scene keys joints / joint_b /
+    joint_t describe the joints and their per-step drive targets."""
+    mm = 1e-3
+    L, w, gap = 40 * mm, 8 * mm, 4 * mm
+    lX, lT = subdivided_box((-L / 2 + gap, -w / 2, -w / 2), (L / 2 - gap, w / 2, w / 2), 2)
+    z0 = 12 * mm
+    abd, joints = [], []
+    for i in range(n_links):
+        q0 = np.concatenate([[L * i + L / 2, 0.0, z0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+        abd.append(dict(X=lX.copy(), tris=lT.copy(), rho=1000.0, q0=q0))
+    k_h, k_d = 2e4, 40.0
+    for i in range(n_links):
+        for s in (-1.0, 1.0):
+            a_pt = (-L / 2, 0.0, s * w / 2)
+            if i == 0:
+                joints.append(dict(a=0, a_kind=0, a_vec=a_pt, b=-1, b_kind=0, b_vec=(0.0, 0.0, 0.0), k=k_h,
+                                   t=(0.0, 0.0, z0 + s * w / 2)))
+            else:
+                joints.append(dict(a=i, a_kind=0, a_vec=a_pt, b=i - 1, b_kind=0, b_vec=(L / 2, 0.0, s * w / 2), k=k_h,
+                                   t=(0.0, 0.0, 0.0)))
+        # drive: the link's axis toward the parent's axis turned by theta_i (the world x axis for link 0)
+        joints.append(dict(a=i, a_kind=1, a_vec=(1.0, 0.0, 0.0), b=(i - 1 if i else -1), b_kind=1,
+                           b_vec=(1.0, 0.0, 0.0), k=k_d, t=(0.0, 0.0, 0.0) if i else (1.0, 0.0, 0.0)))
+    nj = len(joints)
+    joint_b = np.zeros((n_steps + 1, nj, 3))
+    joint_t = np.zeros((n_steps + 1, nj, 3))
+    for s in range(n_steps + 1):
+        ramp = swing * min(1.0, s / max(1, n_steps // 2))
+        for j, jt in enumerate(joints):
+            joint_b[s, j] = jt["b_vec"]
+            joint_t[s, j] = jt["t"]
+        for i in range(n_links):
+            th = ramp * (1.0 if i % 2 == 0 else -0.5)
+            j = 3 * i + 2
+            d = np.array([math.cos(th), math.sin(th), 0.0])
+            if i == 0:
+                joint_t[s, j] = d
+            else:
+                joint_b[s, j] = d
+    gX = np.array([[-1.0, -1.0, 0.0], [2.0, -1.0, 0.0], [-1.0, 2.0, 0.0]])
+    gT = np.array([[0, 1, 2]], np.int32)
+    kin = [dict(X=gX, tris=gT)]
+    kin_T = np.tile(translation((0.0, 0.0, 0.0)), (n_steps + 1, 1, 1, 1))
+    if with_block:
+        reach = L * n_links
+        X, tets = grid_tets((reach - 8 * mm, 16 * mm, 0.4 * mm), 5 * mm, 2, 2, 2)
+    else:
+        X, tets = np.zeros((0, 3)), np.zeros((0, 4), np.int32)
+    nt = len(tets)
+    params = default_params(dt=1e-2, dhat=0.5 * mm, mu=0.2, n_steps=n_steps)
+    params.update(param_overrides)
+    return dict(
+        name=f"jointed_arm_{n_links}links",
+        fem_X=X, fem_tets=tets,
+        fem_logE=np.full(nt, math.log(1e5)), fem_nu=np.full(nt, 0.4), fem_rho=np.full(nt, 1000.0),
+        fem_body=np.zeros(nt, np.int32),
+        kin=kin, kin_T=kin_T, abd=abd,
+        stitch_v=np.zeros(0, np.int32), stitch_b=np.zeros(0, np.int32), stitch_X=np.zeros((0, 3)),
+        joints=joints, joint_b=joint_b, joint_t=joint_t,
+        gravity=np.array([0.0, 0.0, -9.81 if gravity else 0.0]),
+        params=params,
+    )
+
+
 def abd_box_drop(n_steps: int = 6, mu: float = 0.3, **param_overrides) -> dict:
     """A 20 mm rigid (ABD) box, slightly tilted, falling onto a fixed ground triangle, beside a
     soft 2 x 2 x 2 mm block resting on the same ground (ABD-kinematic and FEM-kinematic contact)."""
