@@ -410,6 +410,7 @@ def run_ours(args):
                 "newton_iters_per_step": round(sum(newton) / len(newton), 2),
                 "pcg_iters_per_step": round(sum(s["pcg_iters_total"] for s in stats) / len(stats), 1),
                 "pcg_unconverged_solves": int(sum(s["pcg_unconverged"] for s in stats)),
+                "pcg_two_level_fallbacks": int(sum(s["pcg_fallbacks"] for s in stats)),
                 "active_pairs_max": max(s["n_pairs_max"] for s in stats)}),
             "roofline": roofline,
             "cpu_baseline": cpu,

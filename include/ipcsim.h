@@ -4,18 +4,21 @@
  * t+1 minimise one incremental potential over every free degree of freedom,
  *
  *   E(z) = 1/2 (z - z~)^T M (z - z~)
- *        + dt^2 [ E_FEM + E_barrier + E_friction + E_stitch + E_ABD ],
+ *        + dt^2 [ E_FEM + E_barrier + E_friction + E_stitch + E_ABD + E_joint ],
  *
  * with E_FEM the Neo-Hookean energy of the tetrahedral fingertips and
  * deformable objects (§III-C.1), E_barrier the log-barrier contact potential
  * on point-triangle and edge-edge pairs, E_friction the lagged, smoothly
  * mollified friction potential, E_stitch the stitch springs of Eq. 2 that
  * attach fingertip vertices to the gripper bases, and E_ABD the stiff
- * orthogonality energy of affine bodies (§III-C.1).  Arm links and finger
- * bases are kinematic: they follow the rigid transforms given to each step
- * (the joint drive E_joint of Eq. 3 is not modelled; the links are
- * prescribed).  The step is a projected Newton iteration with a
- * block-Jacobi PCG linear solve, an additive-CCD bound on every step length
+ * orthogonality energy of affine bodies (§III-C.1).  Kinematic bodies
+ * (arm links and finger bases in the grasping scenes) follow the rigid
+ * transforms given to each step; links modelled as affine bodies are instead
+ * driven by E_joint, the quadratic joint drive potentials of Eq. 3 (springs
+ * between body-frame points and directions of two affine bodies, or of one
+ * body and the world, with per-step targets), and are solved with
+ * everything else.  The step is a projected Newton iteration with a
+ * preconditioned PCG linear solve, an additive-CCD bound on every step length
  * and a backtracking line search, so no pair of primitives ever
  * interpenetrates.
  *
@@ -92,6 +95,23 @@ typedef struct {
   const int* stitch_b_host;     /* (n_stitch) kinematic body id */
   const double* stitch_X_host;  /* (n_stitch, 3) anchor in that body's frame */
   double gravity[3];
+  /* joint drives of Eq. 3 (E_joint, revolute and prismatic joints as
+   * quadratic drive potentials): joint j adds
+   *   E_j = k_j / 2 | J_a q_a - J_b q_b - t_j |^2
+   * where q_a, q_b are the q of affine bodies a and b, J q = p + A v for a
+   * body-frame point v (kind 0) and A v for a body-frame direction (kind 1).
+   * Body b = -1 is the world (its term drops; t_j is then a world point or
+   * direction).  A revolute joint is two point springs on the hinge axis plus
+   * a direction spring whose b-side direction turns with the drive angle; a
+   * prismatic joint is a point spring whose b-side point slides with the
+   * drive offset.  The b-side vectors and t change per step
+   * (sim_set_joint_targets); a-side vectors are fixed. */
+  int n_joints;
+  const int* joint_body_host;   /* (n_joints, 2) bodies a (>= 0) and b (>= -1), ABD ids of this scene */
+  const int* joint_kind_host;   /* (n_joints, 2) 0 point, 1 direction, for sides a and b */
+  const double* joint_vec_host; /* (n_joints, 2, 3) v on side a, initial v on side b (body frames) */
+  const double* joint_k_host;   /* (n_joints) stiffness (N/m for points, J for directions), >= 0 */
+  const double* joint_t_host;   /* (n_joints, 3) initial target offset t (world frame) */
 } ipc_scene_desc;
 
 enum { IPC_PREC_FP64 = 0, IPC_PREC_MIXED = 1 };
@@ -149,7 +169,9 @@ typedef struct {
   int pcg_unconverged;    /* PCG solves that stopped at max_pcg (or stagnated) above pcg_rtol: the
                              Newton direction of those iterations is inexact (the step still ends
                              only when the Newton test holds) */
-  int pad_;
+  int pcg_fallbacks;      /* two-level solves that broke down or ended far above pcg_rtol (the coarse
+                             inverse not positive definite on that system) and were repeated with
+                             block Jacobi; their iterations are in pcg_iters_total */
 } ipc_step_stats;
 
 /* Build a simulator of the scene the paper's physics layer simulates
@@ -270,6 +292,14 @@ ipc_status sim_set_kinematic(ipcsim* sim, const double* kin_T_host);
  * doubles, or NULL to keep) and the friction coefficient (mu < 0 keeps it).
  * The barrier stiffness and stitch stiffness fixed at create do not change. */
 ipc_status sim_set_params(ipcsim* sim, const double* logE_host, double mu);
+
+/* Joint drive targets for the following steps (E_joint of Eq. 3: the
+ * reference trajectory q_ref enters only through these): vec_b_host
+ * (n_joints, 3) the b-side body-frame vectors, t_host (n_joints, 3) the
+ * target offsets, all joints of all scenes concatenated; either may be NULL to
+ * keep it.  sim_adjoint uses the targets set last, so set those of the step
+ * being differentiated before calling it.  IPC_ERR_ARG on a non-finite value. */
+ipc_status sim_set_joint_targets(ipcsim* sim, const double* vec_b_host, const double* t_host);
 
 /* Implicit adjoint of one step (implicit function theorem applied to the
  * minimisation of Eq. 3; the paper's simulator is not differentiated, this

@@ -3,7 +3,8 @@
 `IpcStep.apply(sim, step, logE, mu, z_t, zd_t)` advances one step on the GPU
 (sim_step) and returns (z_{t+1}, zd_{t+1}); its backward calls sim_adjoint,
 which recomputes the step's Hessian at the converged positions from the
-saved checkpoint (z_t, zd_t, z_{t+1}) and solves the adjoint system.  The
+saved checkpoint (z_t, zd_t, z_{t+1}) and the step's joint drive targets and
+solves the adjoint system.  The
 parameters are the per-tet ln Young's modulus and the friction coefficient
 (material and friction identification from trajectories).
 """
@@ -20,7 +21,8 @@ class IpcStep(torch.autograd.Function):
         T = sim.scene["kin_T"]
         if sim.nkb:
             sim.set_kinematic(T[step])
-        sim.step(T[step + 1] if sim.nkb else None)
+        jt = sim.joint_targets(step + 1)
+        sim.step(T[step + 1] if sim.nkb else None, joint_targets=jt if jt[0] is not None else None)
         z_next, zd_next = sim.get_dofs()
         ctx.sim = sim
         ctx.step = step
@@ -40,7 +42,8 @@ class IpcStep(torch.autograd.Function):
             gzd = torch.zeros_like(z_next)
         T = sim.scene["kin_T"]
         gz_t, gzd_t, glogE, gmu = sim.adjoint(z_t, zd_t, z_next, T[ctx.step] if sim.nkb else None,
-                                              T[ctx.step + 1] if sim.nkb else None, gz.double(), gzd.double())
+                                              T[ctx.step + 1] if sim.nkb else None, gz.double(), gzd.double(),
+                                              step_next=ctx.step + 1)
         dev = ctx.needs_input_grad
         return (None, None, glogE.to("cpu") if dev[2] else None,
                 torch.tensor(gmu, dtype=torch.float64) if dev[3] else None, gz_t, gzd_t)

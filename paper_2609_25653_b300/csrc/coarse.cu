@@ -7,7 +7,11 @@
 // every FEM row segment of the PCG launch (the rows one CTA owns, a compact
 // cluster of nodes when the mesh is numbered in spatial order) the three
 // translations and three small rotations about the segment's centre,
-//   P_i = [ I | -[x_i - c_a]x ]   (node i of aggregate a, 3 x 6),
+//   P_i = [ I | -[(x_i - c_a) / rho_a]x ]   (node i of aggregate a, 3 x 6),
+// with rho_a the aggregate's RMS radius: the scale leaves the coarse space
+// (and so the preconditioner) unchanged but gives the rotation columns the
+// size of the translation columns, so that A_c is not ill-conditioned by the
+// length unit alone and its FP32 copy stays positive definite,
 // and the preconditioner is additive:  M^-1 = D^-1 + P (P^T A P)^-1 P^T.
 // Here the Galerkin matrix A_c = P^T A P (BSR operator, barrier pair blocks
 // and friction blocks) is assembled densely per independent solve and
@@ -26,9 +30,11 @@ namespace ipc {
 
 namespace {
 
-// centre of every aggregate (the FEM rows of a run of FEM CTAs) and whether its rotations are kept
+// centre of every aggregate (the FEM rows of a run of FEM CTAs) and the scale 1 / rho of its rotations
+// (0: rotations dropped)
 __global__ void k_coarse_centres(const int* __restrict__ seg, const int* __restrict__ agg_cta, int n_agg,
-                                 const double* __restrict__ x, double* __restrict__ centre, int* __restrict__ rot) {
+                                 const double* __restrict__ x, double* __restrict__ centre, double* __restrict__ rot) {
+  __shared__ double c_sh[3];
   const int a = blockIdx.x;
   if (a >= n_agg) return;
   const int r0 = seg[agg_cta[2 * a]], r1 = seg[agg_cta[2 * a + 1]];
@@ -43,14 +49,27 @@ __global__ void k_coarse_centres(const int* __restrict__ seg, const int* __restr
   s1 = block_sum(s1);
   __syncthreads();
   s2 = block_sum(s2);
+  const int n = r1 - r0;
+  const double inv = n > 0 ? 1.0 / n : 0.0;
   if (threadIdx.x == 0) {
-    const int n = r1 - r0;
-    const double inv = n > 0 ? 1.0 / n : 0.0;
-    centre[3 * a] = s0 * inv;
-    centre[3 * a + 1] = s1 * inv;
-    centre[3 * a + 2] = s2 * inv;
+    c_sh[0] = s0 * inv;
+    c_sh[1] = s1 * inv;
+    c_sh[2] = s2 * inv;
+  }
+  __syncthreads();
+  const d3 c = mk(c_sh[0], c_sh[1], c_sh[2]);
+  double q = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const d3 r = ld3(x, i) - c;
+    q += dot(r, r);
+  }
+  q = block_sum(q);
+  if (threadIdx.x == 0) {
+    centre[3 * a] = c.x;
+    centre[3 * a + 1] = c.y;
+    centre[3 * a + 2] = c.z;
     // fewer than four nodes cannot carry three independent rotations: translations only
-    rot[a] = n >= 4 ? 1 : 0;
+    rot[a] = (n >= 4 && q > 0.0) ? 1.0 / sqrt(q * inv) : 0.0;
   }
 }
 
@@ -91,7 +110,7 @@ struct CoarseAsm {
   const int* solve_n;       // (n_solves) coarse unknowns of every solve
   const long long* off;     // (n_solves) offset of every solve's matrix
   const double* centre;     // (n_agg, 3)
-  const int* rot;           // (n_agg)
+  const double* rot;        // (n_agg) 1 / rho, 0: no rotations
   const double* x;          // (nf, 3)
   double* Ac;
 };
@@ -101,9 +120,9 @@ __device__ inline void add_block(const CoarseAsm& C, int i, int j, const double*
   if (a < 0 || b < 0) return;
   const int s = C.agg_solve[a];
   if (s < 0 || C.agg_solve[b] != s) return;
-  const d3 ri = ld3(C.x, i) - ld3(C.centre, a), rj = ld3(C.x, j) - ld3(C.centre, b);
+  const d3 ri = C.rot[a] * (ld3(C.x, i) - ld3(C.centre, a)), rj = C.rot[b] * (ld3(C.x, j) - ld3(C.centre, b));
   double B[36];
-  galerkin_block(M, ri, rj, C.rot[a], C.rot[b], B);
+  galerkin_block(M, ri, rj, C.rot[a] != 0.0, C.rot[b] != 0.0, B);
   const int n = C.solve_n[s], lo = C.solve_lo[s];
   double* dst = C.Ac + C.off[s];
   const int ra = 6 * (a - lo), cb = 6 * (b - lo);
@@ -304,7 +323,7 @@ void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L) {
 cudaError_t launch_coarse_build(cudaStream_t st, const DevScene& S, const CoarseDevLayout& D, const int* seg,
                                 const double* x, const double* val, const int* rec, const int* n_pairs, int cap,
                                 const double* pairH, int n_fric, const int* f_ids, const double* f_w,
-                                const double* f_Hu, double* Ac, double* centre, int* rot, double* gj_buf, int* status) {
+                                const double* f_Hu, double* Ac, double* centre, double* rot, double* gj_buf, int* status) {
   const int na = D.n_agg;
   if (na <= 0 || D.total <= 0) return cudaSuccess;
   k_coarse_centres<<<na, 128, 0, st>>>(seg, D.agg_cta, na, x, centre, rot);

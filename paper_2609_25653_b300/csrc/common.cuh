@@ -44,6 +44,15 @@ struct DevScene {
   const int* stitch_v;
   const int* stitch_b;
   const double* stitch_X;    // (n_stitch, 3)
+  // joint drives between affine bodies: side a (sign +) and b (sign -), body -1 = the world
+  int nj;
+  const int* jt_body;        // (nj, 2)
+  const int* jt_kind;        // (nj, 2) 0 body-frame point, 1 body-frame direction
+  const double* jt_va;       // (nj, 3) vector on side a
+  const double* jt_vb;       // (nj, 3) vector on side b (set per step)
+  const double* jt_k;        // (nj)
+  const double* jt_t;        // (nj, 3) target offset (set per step)
+  const int* jt_blk;         // (nj, 64) BSR block of pseudo-node pair (4 s + m, 4 s' + n), -1 for the world
   const int* bsr_row;        // (n_nodes + 1)
   const int* bsr_col;        // (nnzb)
   const int* bsr_diag;       // (n_nodes) index of the diagonal block

@@ -545,6 +545,60 @@ __global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kapp
   if (threadIdx.x == 0) atomicAdd(E, s);
 }
 
+// Joint drive potentials (E_joint of Eq. 3), one thread per joint.  Side a
+// enters with sign +, side b with sign -; a side's map to world is
+// w . (p, a0, a1, a2) with weights w = (1, v) for a body-frame point v and
+// (0, v) for a direction, so the residual is r = sum_m w_m q_m - t over the
+// eight pseudo-nodes of the two bodies (the world side has none).  Energy
+// k/2 |r|^2, gradient k w_m r at pseudo-node m, Hessian k w_m w_n I for the
+// block pair (m, n): constant in z and positive semi-definite, so nothing is
+// projected.
+__global__ void k_joints(DevScene S, const double* __restrict__ z, double scale, int mode, double* __restrict__ g,
+                         double* __restrict__ Hval, double* __restrict__ E) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (j < S.nj) {
+    double w[8];
+    int node[8];
+    d3 r = {-S.jt_t[3 * j], -S.jt_t[3 * j + 1], -S.jt_t[3 * j + 2]};
+    for (int s = 0; s < 2; ++s) {
+      const int b = S.jt_body[2 * j + s];
+      const d3 v = ld3(s == 0 ? S.jt_va : S.jt_vb, j);
+      const double sg = s == 0 ? 1.0 : -1.0;
+      const double wm[4] = {S.jt_kind[2 * j + s] == 1 ? 0.0 : sg, sg * v.x, sg * v.y, sg * v.z};
+      for (int m = 0; m < 4; ++m) {
+        node[4 * s + m] = b >= 0 ? S.nf + 4 * b + m : -1;
+        w[4 * s + m] = b >= 0 ? wm[m] : 0.0;
+        if (b >= 0) r = r + w[4 * s + m] * ld3(z, node[4 * s + m]);
+      }
+    }
+    const double k = S.jt_k[j];
+    e = 0.5 * k * dot(r, r);
+    if (S.E_sc) scene_energy(S, S.node_scene[node[0]], 6, e);
+    if (mode >= 1)
+      for (int m = 0; m < 8; ++m)
+        if (node[m] >= 0 && w[m] != 0.0) {
+          const double c = scale * k * w[m];
+          atomicAdd(g + 3 * node[m], c * r.x);
+          atomicAdd(g + 3 * node[m] + 1, c * r.y);
+          atomicAdd(g + 3 * node[m] + 2, c * r.z);
+        }
+    if (mode >= 2)
+      for (int m = 0; m < 8; ++m)
+        for (int n = 0; n < 8; ++n) {
+          const double c = scale * k * w[m] * w[n];
+          const int blk = S.jt_blk[64 * j + 8 * m + n];
+          if (c == 0.0 || blk < 0) continue;
+          double* dst = Hval + 9 * (size_t)blk;
+          atomicAdd(dst, c);
+          atomicAdd(dst + 4, c);
+          atomicAdd(dst + 8, c);
+        }
+  }
+  const double s = block_sum(e);
+  if (threadIdx.x == 0) atomicAdd(E, s);
+}
+
 // The same energy, gradient and projected Hessian with one warp per body: the
 // 9x9 Hessian is built by the lanes in shared memory (padded to 10 x 10 with a
 // zero row and column, which keeps eigenvalue 0) and projected by the warp's
@@ -712,6 +766,10 @@ void launch_abd_orth(cudaStream_t st, const DevScene& S, const double* z, double
       k_abd_orth<<<nb(S.nab, 64), 64, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E);
     count_launch();
   }
+}
+void launch_joints(cudaStream_t st, const DevScene& S, const double* z, double scale, int mode, double* g, double* Hval,
+                   double* E) {
+  if (S.nj) { k_joints<<<nb(S.nj, 64), 64, 0, st>>>(S, z, scale, mode, g, Hval, E); count_launch(); }
 }
 void launch_trial(cudaStream_t st, int ndof, int nk3, const double* z, const double* p, double alpha, double* z_out,
                   const double* xk, const double* pD, const double* xk_hat, double* xk_out) {

@@ -75,7 +75,7 @@ struct CoarseDev {
   const int* cta_agg = nullptr;   // (FEM CTAs) aggregate of every FEM CTA, -1 none
   const int* agg_cta = nullptr;   // (aggregates, 2) FEM CTAs [first, end) of every aggregate
   const double* centre = nullptr; // (aggregates, 3)
-  const int* rot = nullptr;       // (aggregates) 1: rotations kept
+  const double* rot = nullptr;    // (aggregates) 1 / RMS radius scaling the rotations, 0: none
   const double* x = nullptr;      // (nf, 3) positions the modes are built at
   double* part = nullptr;         // (FEM CTAs, 6) every CTA's part of P^T v for the current iteration
 };
@@ -189,6 +189,8 @@ void launch_stitch(cudaStream_t, const DevScene&, const double* xv, const double
                    int mode, double* g, double* E);
 void launch_abd_orth(cudaStream_t, const DevScene&, const double* z, double kappa_A, double scale, int mode, int project,
                      double* g, double* Hval, double* E);
+void launch_joints(cudaStream_t, const DevScene&, const double* z, double scale, int mode, double* g, double* Hval,
+                   double* E);
 void launch_trial(cudaStream_t, int ndof, int nk3, const double* z, const double* p, double alpha, double* z_out,
                   const double* xk, const double* pD, const double* xk_hat, double* xk_out);
 void launch_velocity(cudaStream_t, int ndof, const double* z, const double* z_t, double inv_dt, double* zd);
@@ -286,7 +288,7 @@ void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L);
 cudaError_t launch_coarse_build(cudaStream_t, const DevScene& S, const CoarseDevLayout& D, const int* seg,
                                 const double* x, const double* val, const int* rec, const int* n_pairs, int cap,
                                 const double* pairH, int n_fric, const int* f_ids, const double* f_w,
-                                const double* f_Hu, double* Ac, double* centre, int* rot, double* gj_buf, int* status);
+                                const double* f_Hu, double* Ac, double* centre, double* rot, double* gj_buf, int* status);
 
 // conservative-advancement iterations per CCD candidate
 constexpr int ACCD_MAX_ITER = 10000;

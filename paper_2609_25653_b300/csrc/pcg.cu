@@ -602,13 +602,13 @@ __device__ inline void coarse_restrict(const PcgArgs& a, int agg, int r0, int r1
   double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (agg >= 0) {
     const d3 c = ld3(a.co.centre, agg);
-    const bool rot = a.co.rot[agg] != 0;
+    const double rs = a.co.rot[agg];
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       double v0, v1, v2;
       get(i, v0, v1, v2);
       t[0] += v0; t[1] += v1; t[2] += v2;
-      if (rot) {
-        const d3 r = ld3(a.co.x, i) - c;
+      if (rs != 0.0) {
+        const d3 r = rs * (ld3(a.co.x, i) - c);
         t[3] = fma(r.y, v2, fma(-r.z, v1, t[3]));
         t[4] = fma(r.z, v0, fma(-r.x, v2, t[4]));
         t[5] = fma(r.x, v1, fma(-r.y, v0, t[5]));
@@ -664,11 +664,12 @@ __device__ inline void coarse_own(const PcgArgs& a, int agg, int s, Shared& sh, 
   else coarse_own_t<float>(a, a.co.inv32, agg, s, sh, res);
 }
 
-// P_i c: translation plus rotation theta x (x_i - centre) of node i's aggregate
+// P_i c: translation plus rotation theta x (x_i - centre) / rho of node i's aggregate
 __device__ inline d3 coarse_prolong(const PcgArgs& a, int agg, int i, const double* c) {
-  const d3 r = ld3(a.co.x, i) - ld3(a.co.centre, agg);
+  const double rs = a.co.rot[agg];
+  const d3 r = rs * (ld3(a.co.x, i) - ld3(a.co.centre, agg));
   d3 o = mk(c[0], c[1], c[2]);
-  if (a.co.rot[agg]) o = o + mk(c[4] * r.z - c[5] * r.y, c[5] * r.x - c[3] * r.z, c[3] * r.y - c[4] * r.x);
+  if (rs != 0.0) o = o + mk(c[4] * r.z - c[5] * r.y, c[5] * r.x - c[3] * r.z, c[3] * r.y - c[4] * r.x);
   return o;
 }
 
@@ -1114,7 +1115,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
       else {
         if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
         if (rr <= tol_in2 || it - it_best > STALL || it >= a.max_iter) act = ACT_REFRESH;
-        else if (fresh) {
+        else if (!(gamma > 0.0)) {
+          // r^T M^-1 r <= 0 with r != 0: the preconditioner is not positive definite (breakdown)
+          status = 1; done = true; act = ACT_IDLE;
+        } else if (fresh) {
           if (!(delta > 0.0)) { status = 1; done = true; act = ACT_IDLE; }
           else al = gamma / delta;
         } else {
@@ -1503,7 +1507,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       else {
         if (fresh || rr < rr_best) { rr_best = rr; it_best = it; }
         if (rr <= tol_in2 || it - it_best > STALL || it >= a.max_iter) act = ACT_END;
-        else if (fresh) {
+        else if (!(gamma > F(0))) {
+          // r^T M^-1 r <= 0 with r != 0: the preconditioner is not positive definite (breakdown)
+          status = 1; done = true; act = ACT_IDLE;
+        } else if (fresh) {
           if (!(delta > F(0))) { status = 1; done = true; act = ACT_IDLE; }
           else al = gamma / delta;
         } else {

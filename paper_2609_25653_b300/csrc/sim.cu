@@ -113,7 +113,7 @@ struct ipcsim {
   // scalars (device) and pinned host mirror
   struct Scal {
     // cleared at the start of every Newton iteration
-    double E[8];                 // inertia, elastic, barrier, friction, stitch, abd
+    double E[8];                 // inertia, elastic, barrier, friction, stitch, abd, joints (adjoint scratch: 6, 7)
     unsigned long long pn[2];    // max|p_F|, max|p_D|
     int n_ccd;
     int pcg_out[3];
@@ -132,6 +132,10 @@ struct ipcsim {
   int pcg_grid_max = 1;
   // per-scene Newton control of a batch (n_scenes > 1): device accumulators and pinned host mirrors
   double* E_sc_dev = nullptr;
+  // joint drive targets (b-side vectors, offsets), rewritten by sim_set_joint_targets
+  int nj = 0;
+  double* jt_vb = nullptr;
+  double* jt_t = nullptr;
   unsigned long long* alpha_sc_dev = nullptr;
   unsigned long long* pn_sc_dev = nullptr;
   double* alpha_trial_dev = nullptr;
@@ -160,7 +164,10 @@ struct ipcsim {
   int *co_node_agg = nullptr, *co_agg_solve = nullptr, *co_solve_lo = nullptr, *co_solve_n = nullptr;
   int *co_cta_agg = nullptr, *co_agg_cta = nullptr;
   int co_cap_ctas = 0;
-  int* co_rot = nullptr;
+  double* co_rot = nullptr;
+  // two-level solves repeated with block Jacobi, and the iterations those failed solves took
+  long long pcg_fallbacks = 0, pcg_fallback_iters = 0;
+  bool co_force_rebuild = false;
   // rebuild policy: the coarse level is kept across steps while the PCG iterations stay near those of
   // the first step after its build
   int co_steps_since_build = 0;
@@ -473,6 +480,7 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
 // with block Jacobi alone (co_ok false).
 ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
   sim->co_ok = false;
+  sim->co_force_rebuild = false;
   if (sim->P.preconditioner != IPC_PRECOND_TWO_LEVEL || sim->nf == 0 || sim->plan.n_fem_ctas <= 0) return IPC_OK;
   CoarseLayout& L = sim->co;
   if (sim->co_plan_stamp != sim->plan_stamp) {
@@ -561,7 +569,30 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
 // One PCG solve of H_FF p = rhs on the assembled system (Hval, pairH, f_Hu,
 // Dinv and, for FP32 iterations, their FP32 copies); the incidence lists
 // must describe the current pairs and pcg_prepare must have run on this Hval.
+ipc_status pcg_launch(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric, bool use_coarse);
+
+// One linear solve.  A two-level solve that broke down or ended far above its tolerance (the coarse
+// inverse was not positive definite on this system) is repeated with block Jacobi alone, and the coarse
+// level is rebuilt at the next Newton iteration; fallbacks and the iterations of the failed solves are
+// counted in sim->pcg_fallbacks / sim->pcg_fallback_iters.
 ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric) {
+  ipc_status s = pcg_launch(sim, fp32, rtol, max_iter, n_fric, true);
+  if (s || !sim->co_ok) return s;
+  ipcsim::Scal* h = sim->sc_host;
+  CUDA_TRY(cudaMemcpyAsync(h->pcg_out, sim->sc_dev->pcg_out, sizeof(h->pcg_out), cudaMemcpyDeviceToHost, sim->st));
+  CUDA_TRY(cudaMemcpyAsync(&h->pcg_res, &sim->sc_dev->pcg_res, sizeof(double), cudaMemcpyDeviceToHost, sim->st));
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  const int status = h->pcg_out[1];
+  if (status == 1 || status == 2 || (status == 3 && !(h->pcg_res < 0.5))) {
+    ++sim->pcg_fallbacks;
+    sim->pcg_fallback_iters += h->pcg_out[0];
+    sim->co_force_rebuild = true;
+    return pcg_launch(sim, fp32, rtol, max_iter, n_fric, false);
+  }
+  return IPC_OK;
+}
+
+ipc_status pcg_launch(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric, bool use_coarse) {
   const DevScene& S = sim->S;
   PcgArgs a{};
   a.S = S;
@@ -627,11 +658,12 @@ ipc_status pcg_run(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fric)
   a.abd_val = sim->abd_val;
   a.abd_val32 = sim->abd_val32;
   a.abd_cap = sim->abd_cap;
-  if (sim->co_ok) {
+  if (sim->co_ok && use_coarse) {
     a.co.inv32 = sim->co_Ac32;
-    // tight tolerances (parity, adjoint) need a fixed linear preconditioner: the FP64 solver then applies
-    // the coarse inverse in FP64; at the default tolerance the FP32 product is accurate enough and cheaper
-    a.co.inv64 = (!fp32 && rtol < 1e-7) ? sim->co_Ac : nullptr;
+    // the FP64 (pipelined) solver needs a fixed, symmetric linear preconditioner: it applies the coarse
+    // inverse in FP64 (with the FP32 product its recurrences lost r^T M^-1 r > 0 in a third of the grasp's
+    // solves); the mixed solver's FP32 inner iteration uses the FP32 copy
+    a.co.inv64 = !fp32 ? sim->co_Ac : nullptr;
     a.co.cta_agg = sim->co_cta_agg;
     a.co.agg_cta = sim->co_agg_cta;
     a.co.off = sim->co_off;
@@ -742,9 +774,10 @@ ipc_status sync_scalars(ipcsim* sim) {
   return IPC_OK;
 }
 
+// E: inertia, elastic, barrier, friction, stitch, ABD orthogonality, joints
 double total_energy(const ipcsim* sim, const double* E) {
   double dt2 = sim->P.dt * sim->P.dt;
-  return E[0] + dt2 * (E[1] + E[2] + E[3] + E[4] + E[5]);
+  return E[0] + dt2 * (E[1] + E[2] + E[3] + E[4] + E[5] + E[6]);
 }
 
 double bits_to_double(unsigned long long b) {
@@ -780,6 +813,7 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
                       &sim->sc_dev->E[3]);
     launch_stitch(sim->st, S, xvq, sim->stitch_hat, sim->k_c, dt2, 0, nullptr, &sim->sc_dev->E[4]);
     launch_abd_orth(sim->st, S, zq, sim->P.kappa_A, dt2, 0, 0, nullptr, nullptr, &sim->sc_dev->E[5]);
+    launch_joints(sim->st, S, zq, dt2, 0, nullptr, nullptr, &sim->sc_dev->E[6]);
     ipc_status s = sync_scalars(sim);
     if (s) return s;
     if (sim->sc_host->flags & ERRF_BVH) { sim->err = "BVH traversal stack overflow"; return IPC_ERR_BVH_OVERFLOW; }
@@ -863,6 +897,19 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     return fail(IPC_ERR_ARG, "invalid parameters or sizes");
   if ((D->n_tets > 0 && (!D->tets_host || !D->fem_X_host || !D->logE_host || !D->nu_host || !D->rho_host)))
     return fail(IPC_ERR_ARG, "missing FEM arrays");
+  const int nj = D->n_joints;
+  if (nj < 0 || (nj > 0 && (!D->joint_body_host || !D->joint_kind_host || !D->joint_vec_host || !D->joint_k_host ||
+                            !D->joint_t_host)))
+    return fail(IPC_ERR_ARG, "invalid joint arrays");
+  for (int j = 0; j < nj; ++j) {
+    const int a = D->joint_body_host[2 * j], b = D->joint_body_host[2 * j + 1];
+    bool ok = a >= 0 && a < D->n_abd && b >= -1 && b < D->n_abd && std::isfinite(D->joint_k_host[j]) &&
+              D->joint_k_host[j] >= 0;
+    for (int s = 0; s < 2; ++s) ok = ok && (D->joint_kind_host[2 * j + s] == 0 || D->joint_kind_host[2 * j + s] == 1);
+    for (int c = 0; c < 6; ++c) ok = ok && std::isfinite(D->joint_vec_host[6 * j + c]);
+    for (int c = 0; c < 3; ++c) ok = ok && std::isfinite(D->joint_t_host[3 * j + c]);
+    if (!ok) return fail(IPC_ERR_ARG, "joint " + std::to_string(j) + ": body, kind or value out of range");
+  }
 
   const int nf = D->n_fem_verts, nt = D->n_tets, nab = D->n_abd, nkb = D->n_kin;
   sim->nf = nf; sim->nt = nt; sim->nab = nab; sim->nkb = nkb;
@@ -1101,6 +1148,16 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   for (int i = 0; i < nab; ++i)
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) rows[nf + 4 * i + a].push_back(nf + 4 * i + b);
+  // joints couple the pseudo-nodes of their two bodies
+  for (int j = 0; j < nj; ++j) {
+    const int ba = D->joint_body_host[2 * j], bb = D->joint_body_host[2 * j + 1];
+    if (bb < 0 || bb == ba) continue;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        rows[nf + 4 * ba + a].push_back(nf + 4 * bb + b);
+        rows[nf + 4 * bb + b].push_back(nf + 4 * ba + a);
+      }
+  }
   std::vector<int> row_ptr(n_nodes + 1, 0), col, diag(n_nodes);
   for (int i = 0; i < n_nodes; ++i) {
     auto& r = rows[i];
@@ -1127,6 +1184,14 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   for (int i = 0; i < nab; ++i)
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) abd_blk[16 * i + 4 * a + b] = find_blk(nf + 4 * i + a, nf + 4 * i + b);
+  // joint blocks: pseudo-node m of side s against pseudo-node n of side s'
+  std::vector<int> jt_blk(64 * (size_t)nj, -1);
+  for (int j = 0; j < nj; ++j)
+    for (int p = 0; p < 8; ++p)
+      for (int q = 0; q < 8; ++q) {
+        const int bp = D->joint_body_host[2 * j + p / 4], bq = D->joint_body_host[2 * j + q / 4];
+        if (bp >= 0 && bq >= 0) jt_blk[64 * j + 8 * p + q] = find_blk(nf + 4 * bp + p % 4, nf + 4 * bq + q % 4);
+      }
   // constant part: mass blocks and the stitch Hessian dt^2 k_c I
   std::vector<double> Hc(9 * (size_t)nnzb, 0.0);
   for (int v = 0; v < nf; ++v)
@@ -1185,6 +1250,25 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     if ((s = upload(sim, &ip, stv))) return fail(s, ""); S.stitch_v = ip;
     if ((s = upload(sim, &ip, stb))) return fail(s, ""); S.stitch_b = ip;
     if ((s = upload(sim, &dp, stx))) return fail(s, ""); S.stitch_X = dp;
+    S.nj = nj;
+    sim->nj = nj;
+    if (nj) {
+      std::vector<int> jb(D->joint_body_host, D->joint_body_host + 2 * nj), jk(D->joint_kind_host, D->joint_kind_host + 2 * nj);
+      std::vector<double> va(3 * (size_t)nj), vb(3 * (size_t)nj), jkk(D->joint_k_host, D->joint_k_host + nj),
+          jt(D->joint_t_host, D->joint_t_host + 3 * nj);
+      for (int j = 0; j < nj; ++j)
+        for (int c = 0; c < 3; ++c) {
+          va[3 * j + c] = D->joint_vec_host[6 * j + c];
+          vb[3 * j + c] = D->joint_vec_host[6 * j + 3 + c];
+        }
+      if ((s = upload(sim, &ip, jb))) return fail(s, ""); S.jt_body = ip;
+      if ((s = upload(sim, &ip, jk))) return fail(s, ""); S.jt_kind = ip;
+      if ((s = upload(sim, &dp, va))) return fail(s, ""); S.jt_va = dp;
+      if ((s = upload(sim, &sim->jt_vb, vb))) return fail(s, ""); S.jt_vb = sim->jt_vb;
+      if ((s = upload(sim, &dp, jkk))) return fail(s, ""); S.jt_k = dp;
+      if ((s = upload(sim, &sim->jt_t, jt))) return fail(s, ""); S.jt_t = sim->jt_t;
+      if ((s = upload(sim, &ip, jt_blk))) return fail(s, ""); S.jt_blk = ip;
+    }
     if ((s = upload(sim, &ip, row_ptr))) return fail(s, ""); S.bsr_row = ip;
     sim->h_row = row_ptr;
     if ((s = upload(sim, &ip, col))) return fail(s, ""); S.bsr_col = ip;
@@ -1339,14 +1423,33 @@ static ipc_status batch_impl(const ipc_scene_desc* descs, int n, const ipc_param
   if (!out) return IPC_ERR_ARG;
   *out = nullptr;
   if (!descs || n <= 0 || !params) return IPC_ERR_ARG;
-  std::vector<double> fX, fV0, logE, nu, rho, aX, arho, aq0, kX, kT0, stX;
-  std::vector<int> tets, fbody, anv, antri, atris, knv, kntri, ktris, stv, stb, tet_scene, abd_scene, kin_scene;
+  std::vector<double> fX, fV0, logE, nu, rho, aX, arho, aq0, kX, kT0, stX, jvec, jk, jt;
+  std::vector<int> tets, fbody, anv, antri, atris, knv, kntri, ktris, stv, stb, tet_scene, abd_scene, kin_scene, jbody,
+      jkind;
   bool any_v0 = false;
   for (int k = 0; k < n; ++k) any_v0 |= descs[k].fem_V0_host != nullptr;
   int voff = 0, boff = 0, koff = 0;
   for (int k = 0; k < n; ++k) {
     const ipc_scene_desc& D = descs[k];
-    if (D.n_fem_verts < 0 || D.n_tets < 0 || D.n_abd < 0 || D.n_kin < 0 || D.n_stitch < 0) return IPC_ERR_ARG;
+    if (D.n_fem_verts < 0 || D.n_tets < 0 || D.n_abd < 0 || D.n_kin < 0 || D.n_stitch < 0 || D.n_joints < 0)
+      return IPC_ERR_ARG;
+    if (D.n_joints > 0 && (!D.joint_body_host || !D.joint_kind_host || !D.joint_vec_host || !D.joint_k_host ||
+                           !D.joint_t_host))
+      return IPC_ERR_ARG;
+    for (int j = 0; j < D.n_joints; ++j) {
+      // bodies are shifted by the affine bodies of the scenes before; the world (-1) stays; ids out of the
+      // scene's range are left out of range for create's check
+      for (int s = 0; s < 2; ++s) {
+        const int b = D.joint_body_host[2 * j + s];
+        jbody.push_back(b >= 0 && b < D.n_abd ? b + (int)abd_scene.size() : (b == -1 ? -1 : -2));
+        jkind.push_back(D.joint_kind_host[2 * j + s]);
+      }
+      jk.push_back(D.joint_k_host[j]);
+    }
+    if (D.n_joints) {
+      jvec.insert(jvec.end(), D.joint_vec_host, D.joint_vec_host + 6 * D.n_joints);
+      jt.insert(jt.end(), D.joint_t_host, D.joint_t_host + 3 * D.n_joints);
+    }
     fX.insert(fX.end(), D.fem_X_host, D.fem_X_host + 3 * D.n_fem_verts);
     if (any_v0) {
       if (D.fem_V0_host) fV0.insert(fV0.end(), D.fem_V0_host, D.fem_V0_host + 3 * D.n_fem_verts);
@@ -1426,6 +1529,12 @@ static ipc_status batch_impl(const ipc_scene_desc* descs, int n, const ipc_param
   M.stitch_v_host = stv.data();
   M.stitch_b_host = stb.data();
   M.stitch_X_host = stX.data();
+  M.n_joints = (int)jk.size();
+  M.joint_body_host = jbody.data();
+  M.joint_kind_host = jkind.data();
+  M.joint_vec_host = jvec.data();
+  M.joint_k_host = jk.data();
+  M.joint_t_host = jt.data();
   for (int d = 0; d < 3; ++d) M.gravity[d] = descs[0].gravity[d];
   return create_impl(&M, params, A, stream, out, n, tet_scene.data(), abd_scene.data(), kin_scene.data());
 }
@@ -1526,6 +1635,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
     prof_end(sim, PROF_ELASTIC);
     launch_stitch(cs, S, sim->xv, sim->stitch_hat, sim->k_c, dt2, 1, sim->g, &sim->sc_dev->E[4]);
     launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g, sim->Hval, &sim->sc_dev->E[5]);
+    launch_joints(cs, S, sim->z, dt2, 2, sim->g, sim->Hval, &sim->sc_dev->E[6]);
     prof_begin(sim, PROF_BARRIER);
     launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh, sim->kappa,
                    dt2, 2, 1, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2], &sim->sc_dev->min_s,
@@ -1600,7 +1710,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
       sim->co_built_this_step = true;
     } else if (it == 0 && !sim->co_built_this_step) {
-      const bool stale = sim->co_plan_stamp != sim->plan_stamp || !sim->co_ok ||
+      const bool stale = sim->co_plan_stamp != sim->plan_stamp || !sim->co_ok || sim->co_force_rebuild ||
                          sim->co_steps_since_build >= std::max(keep, 1) ||
                          (sim->co_iters_ref > 0.0 && sim->co_last_step_avg > 1.3 * sim->co_iters_ref);
       if (stale) {
@@ -1609,13 +1719,14 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
         sim->co_iters_ref = 0.0;
       }
       sim->co_built_this_step = true;
-    } else if (sim->co_plan_stamp != sim->plan_stamp) {
+    } else if (sim->co_plan_stamp != sim->plan_stamp || sim->co_force_rebuild) {
       if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
       sim->co_steps_since_build = 0;
       sim->co_iters_ref = 0.0;
     }
     prof_end(sim, PROF_PCG_SETUP);
     prof_begin(sim, PROF_PCG);
+    const long long fb0 = sim->pcg_fallbacks, fbi0 = sim->pcg_fallback_iters;
     if ((s = pcg_run(sim, fp32, P.pcg_rtol, max_pcg, n_fric_it))) return s;
     sim->pcg_skip_on = false;
     prof_end(sim, PROF_PCG);
@@ -1662,7 +1773,8 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
     sim->cand_valid = sweep;
     ++it;
     st.newton_iters = it;
-    st.pcg_iters_total += h.pcg_out[0];
+    st.pcg_iters_total += h.pcg_out[0] + (int)(sim->pcg_fallback_iters - fbi0);
+    st.pcg_fallbacks += (int)(sim->pcg_fallbacks - fb0);
     if (sim->prof) {
       sim->pcg_iters_acc += h.pcg_out[0];
       sim->pcg_pair_iters_acc += (long long)h.pcg_out[0] * std::min(h.n_pairs, sim->cap);
@@ -1883,6 +1995,20 @@ ipc_status sim_set_params(ipcsim* sim, const double* logE_host, double mu) {
   return IPC_OK;
 }
 
+ipc_status sim_set_joint_targets(ipcsim* sim, const double* vec_b_host, const double* t_host) {
+  if (!sim) return IPC_ERR_ARG;
+  const int nj = sim->nj;
+  for (const double* h : {vec_b_host, t_host})
+    if (h)
+      for (int i = 0; i < 3 * nj; ++i)
+        if (!std::isfinite(h[i])) { sim->err = "non-finite joint target"; return IPC_ERR_ARG; }
+  if (nj == 0) return IPC_OK;
+  if (vec_b_host) CUDA_TRY(cudaMemcpyAsync(sim->jt_vb, vec_b_host, sizeof(double) * 3 * nj, cudaMemcpyHostToDevice, sim->st));
+  if (t_host) CUDA_TRY(cudaMemcpyAsync(sim->jt_t, t_host, sizeof(double) * 3 * nj, cudaMemcpyHostToDevice, sim->st));
+  CUDA_TRY(cudaStreamSynchronize(sim->st));
+  return IPC_OK;
+}
+
 ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const double* z_next,
                        const double* kin_T_t_host, const double* kin_T_next_host, const double* gz_next,
                        const double* gzd_next, double* gz_t, double* gzd_t, double* glogE, double* gmu_host) {
@@ -1933,6 +2059,7 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     cull(sim, sim->xv);
     launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
     launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g, sim->Hval, &sim->sc_dev->E[5]);
+    launch_joints(cs, S, z_next, dt2, 2, sim->g, sim->Hval, &sim->sc_dev->E[6]);
     launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
                    sim->kappa, dt2, 2, 0, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2],
                    nullptr);
@@ -1952,6 +2079,7 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
       CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
       launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
       launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g, sim->Hval, &sim->sc_dev->E[5]);
+      launch_joints(cs, S, z_next, dt2, 2, sim->g, sim->Hval, &sim->sc_dev->E[6]);
     }
     build_abd_contact(sim, P.mu > 0 ? sim->n_fric : 0);
     if ((s = sync_scalars(sim))) return s;

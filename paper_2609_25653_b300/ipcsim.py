@@ -38,6 +38,8 @@ class SceneDesc(C.Structure):
         ("kin_tris_host", ip), ("kin_T0_host", dp),
         ("n_stitch", C.c_int), ("stitch_v_host", ip), ("stitch_b_host", ip), ("stitch_X_host", dp),
         ("gravity", C.c_double * 3),
+        ("n_joints", C.c_int), ("joint_body_host", ip), ("joint_kind_host", ip), ("joint_vec_host", dp),
+        ("joint_k_host", dp), ("joint_t_host", dp),
     ]
 
 
@@ -109,7 +111,7 @@ class StepStats(C.Structure):
                 ("pcg_iters_max", C.c_int), ("n_pairs_max", C.c_int), ("n_friction_pairs", C.c_int),
                 ("n_ccd_max", C.c_int), ("ls_halvings", C.c_int), ("alpha_min", C.c_double),
                 ("min_dist", C.c_double), ("energy_end", C.c_double), ("pnorm_end", C.c_double),
-                ("pcg_unconverged", C.c_int), ("pad_", C.c_int)]
+                ("pcg_unconverged", C.c_int), ("pcg_fallbacks", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -141,6 +143,7 @@ SIGNATURES = {
     "sim_eval_barrier_noalloc": ([vp, vp, C.c_int, vp, C.c_int, vp, vp, vp], C.c_int),
     "sim_step_many": ([C.POINTER(vp), C.c_int, C.POINTER(dp), C.POINTER(StepStats), ip], C.c_int),
     "sim_adjoint": ([vp, vp, vp, vp, dp, dp, vp, vp, vp, vp, vp, dp], C.c_int),
+    "sim_set_joint_targets": ([vp, dp, dp], C.c_int),
     "sim_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
     "sim_pcg_partition": ([ip, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip, ip, ip, ip, ip], C.c_int),
     "sim_pcg_residency": ([vp, C.c_int], C.c_int),
@@ -292,6 +295,14 @@ def _fill_desc(d, scene, keep):
         d.stitch_X_host = arr_d(scene["stitch_X"])
     for k in range(3):
         d.gravity[k] = float(scene["gravity"][k])
+    joints = scene.get("joints", [])
+    d.n_joints = len(joints)
+    if joints:
+        d.joint_body_host = arr_i([[j["a"], j["b"]] for j in joints])
+        d.joint_kind_host = arr_i([[j["a_kind"], j["b_kind"]] for j in joints])
+        d.joint_vec_host = arr_d([[j["a_vec"], j["b_vec"]] for j in joints])
+        d.joint_k_host = arr_d([j["k"] for j in joints])
+        d.joint_t_host = arr_d([j.get("t", (0.0, 0.0, 0.0)) for j in joints])
 
 
 def batch_scene(scenes):
@@ -340,6 +351,8 @@ class Simulator:
         self.nv = self.nf + sum(a["X"].shape[0] for sc in scenes for a in sc.get("abd", [])) + \
             sum(k["X"].shape[0] for sc in scenes for k in sc.get("kin", []))
         self.n_scenes = len(scenes)
+        self._scenes = scenes
+        self.nj = sum(len(s.get("joints", [])) for s in scenes)
         sc = (C.c_double * 4)()
         L.sim_scalars(h, sc)
         self.kappa, self.k_c, self.L, self.dhat = list(sc)
@@ -364,8 +377,43 @@ class Simulator:
         if code != IPC_OK:
             raise IpcError(code, load().sim_last_error(self.h).decode())
 
-    def step(self, kin_T_next=None, raise_on_error=True):
-        """Advance one step; kin_T_next (n_kin, 3, 4).  Defaults to the scene's trajectory."""
+    def joint_targets(self, step):
+        """The joints' b-side vectors and targets of trajectory step `step` (scene keys joint_b / joint_t,
+        (n_steps + 1, n_joints, 3) each), all scenes concatenated; (None, None) without per-step targets."""
+        if not self.nj or not any("joint_b" in s or "joint_t" in s for s in self._scenes):
+            return None, None
+        vb, t = [], []
+        for s in self._scenes:
+            jn = s.get("joints", [])
+            if not jn:
+                continue
+            vb.append(_f64(s["joint_b"][step]) if "joint_b" in s else _f64([j["b_vec"] for j in jn]))
+            t.append(_f64(s["joint_t"][step]) if "joint_t" in s else _f64([j.get("t", (0, 0, 0)) for j in jn]))
+        return np.concatenate(vb).reshape(-1, 3), np.concatenate(t).reshape(-1, 3)
+
+    def set_joint_targets(self, vec_b=None, t=None):
+        """Drive targets of the joints for the following steps (sim_set_joint_targets): b-side body-frame
+        vectors (n_joints, 3) and target offsets (n_joints, 3); None keeps."""
+        a = None if vec_b is None else _f64(vec_b).reshape(-1)
+        b = None if t is None else _f64(t).reshape(-1)
+        for x in (a, b):
+            if x is not None and x.size != 3 * self.nj:
+                raise ValueError(f"joint targets need {3 * self.nj} values, got {x.size}")
+        self._check(load().sim_set_joint_targets(self.h, None if a is None else a.ctypes.data_as(dp),
+                                                 None if b is None else b.ctypes.data_as(dp)))
+
+    def _trajectory_joint_targets(self, step):
+        vb, t = self.joint_targets(step)
+        if vb is not None:
+            self.set_joint_targets(vb, t)
+
+    def step(self, kin_T_next=None, raise_on_error=True, joint_targets=None):
+        """Advance one step; kin_T_next (n_kin, 3, 4), joint_targets (vec_b, t).  Both default to the
+        scene's trajectory."""
+        if joint_targets is not None:
+            self.set_joint_targets(*joint_targets)
+        else:
+            self._trajectory_joint_targets(self.step_index + 1)
         if kin_T_next is None and self.nkb:
             kin_T_next = self.scene["kin_T"][self.step_index + 1]
         T = _f64(kin_T_next).reshape(-1) if self.nkb else None
@@ -441,9 +489,12 @@ class Simulator:
         qd = C.c_void_p(zd.data_ptr() + off) if self.nab else None
         self._check(load().sim_set_state(self.h, _ptr(z), _ptr(zd), q, qd, 1))
 
-    def adjoint(self, z_t, zd_t, z_next, T_t, T_next, gz_next, gzd_next, glogE=None):
-        """Backward of one step: returns (dL/dz_t, dL/dzd_t, glogE (accumulated), dL/dmu)."""
+    def adjoint(self, z_t, zd_t, z_next, T_t, T_next, gz_next, gzd_next, glogE=None, step_next=None):
+        """Backward of one step: returns (dL/dz_t, dL/dzd_t, glogE (accumulated), dL/dmu).  step_next: the
+        trajectory index of z_next, whose joint targets are set first (scenes with per-step targets)."""
         import torch
+        if step_next is not None:
+            self._trajectory_joint_targets(step_next)
         gz_t = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
         gzd_t = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
         if glogE is None:
@@ -673,6 +724,7 @@ def step_many(sims, kin_T_next=None):
     arrs = []
     ptrs = (dp * n)()
     for i, s in enumerate(sims):
+        s._trajectory_joint_targets(s.step_index + 1)
         T = kin_T_next[i] if kin_T_next is not None else (s.scene["kin_T"][s.step_index + 1] if s.nkb else None)
         if T is not None and s.nkb:
             a = _f64(T).reshape(-1)
