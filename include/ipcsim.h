@@ -448,9 +448,10 @@ ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* 
  * allocates its scratch with cudaMalloc on every call.  Same arguments,
  * outputs and error codes as sim_eval_barrier; the caller still provides
  * every input and output buffer.  Its scratch is one static device array of
- * 2^20 doubles (8 MiB) that every GPU loading this library holds until the
- * process exits; scenes needing more (more than about 87 000 nodes) are
- * rejected with IPC_ERR_ARG and a message naming the size.  The first call
+ * 2^20 8-byte slots (8 MiB) that every GPU loading this library holds until
+ * the process exits (its sums are kept as three-word order-independent
+ * accumulators, 48 slots per node); scenes needing more (more than about
+ * 21 800 nodes) are rejected with IPC_ERR_ARG and a message naming the size.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current.  With CUDA's lazy module loading (the default)
  * that first call may also load this library's device code onto the device,

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libipcsim.so")
 
-SOURCES = ["fem.cu", "contact.cu", "cull.cu", "bvh.cu", "pcg.cu", "adjoint.cu", "sim.cu", "noalloc.cu", "peaks.cu", "coarse.cu", "dual_mesh.cu", "render.cu"]
+SOURCES = ["fem.cu", "contact.cu", "cull.cu", "bvh.cu", "pcg.cu", "adjoint.cu", "sim.cu", "noalloc.cu", "peaks.cu", "coarse.cu", "dual_mesh.cu", "render.cu", "order.cu"]
 PER_FILE_FLAGS = {"cull.cu": ["-fmad=false"], "render.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INC]

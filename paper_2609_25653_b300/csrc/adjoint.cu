@@ -55,11 +55,10 @@ __global__ void k_mass_apply(DevScene S, const double* __restrict__ lam, double 
   st3(yd, i, dt * r);
 }
 
-// y += (w w^T (x) Hu) lam for every friction pair (Hu already scaled by dt^2);
-// acc[0] += lam . grad D / mu (grad D taken from the scaled gradient g_fr).
+// y += (w w^T (x) Hu) lam for every friction pair (Hu already scaled by dt^2), into accumulators.
 __global__ void k_friction_apply(DevScene S, int n, const int* __restrict__ f_ids, const double* __restrict__ f_w,
                                  const double* __restrict__ f_Hu, const double* __restrict__ lam,
-                                 double* __restrict__ y) {
+                                 acc_t* __restrict__ y) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int* ids = f_ids + 4 * k;
@@ -77,20 +76,17 @@ __global__ void k_friction_apply(DevScene S, int n, const int* __restrict__ f_id
     if (S.vkind[ids[q]] == VK_KIN || w[q] == 0.0) continue;
     NodeMap m = vertex_nodes(S, ids[q]);
     for (int t = 0; t < m.n; ++t) {
-      double c = w[q] * m.w[t];
-      atomicAdd(y + 3 * m.node[t], c * tv.x);
-      atomicAdd(y + 3 * m.node[t] + 1, c * tv.y);
-      atomicAdd(y + 3 * m.node[t] + 2, c * tv.z);
+      acc_add3(y, m.node[t], (w[q] * m.w[t]) * tv, S.err);
     }
   }
 }
 
-// out[0] += sum_i a_i b_i
-__global__ void k_dot(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+// out (accumulator) += sum_i a_i b_i
+__global__ void k_dot(int n, const double* __restrict__ a, const double* __restrict__ b, acc_t* __restrict__ out) {
   double s = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += a[i] * b[i];
   s = block_sum(s);
-  if (threadIdx.x == 0) atomicAdd(out, s);
+  if (threadIdx.x == 0) acc_add(out, s);
 }
 
 // a = gz + gzd / dt (free DOFs); also used for gz_t -= gzd / dt
@@ -109,10 +105,10 @@ void launch_mass_apply(cudaStream_t st, const DevScene& S, const double* lam, do
   if (S.n_nodes) { k_mass_apply<<<nb(S.n_nodes, 256), 256, 0, st>>>(S, lam, dt, y, yd); count_launch(); }
 }
 void launch_friction_apply(cudaStream_t st, const DevScene& S, int n, const int* f_ids, const double* f_w,
-                           const double* f_Hu, const double* lam, double* y) {
+                           const double* f_Hu, const double* lam, acc_t* y) {
   if (n > 0) { k_friction_apply<<<nb(n, 128), 128, 0, st>>>(S, n, f_ids, f_w, f_Hu, lam, y); count_launch(); }
 }
-void launch_dot(cudaStream_t st, int n, const double* a, const double* b, double* out) {
+void launch_dot(cudaStream_t st, int n, const double* a, const double* b, acc_t* out) {
   if (n > 0) { k_dot<<<stride_grid(n, 256, 4), 256, 0, st>>>(n, a, b, out); count_launch(); }
 }
 void launch_axpy(cudaStream_t st, int n, const double* x, double alpha, const double* y, double* out) {

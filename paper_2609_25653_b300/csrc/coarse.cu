@@ -112,7 +112,8 @@ struct CoarseAsm {
   const double* centre;     // (n_agg, 3)
   const double* rot;        // (n_agg) 1 / rho, 0: no rotations
   const double* x;          // (nf, 3)
-  double* Ac;
+  acc_t* Ac;                // accumulators of the solves' matrices
+  int* err;
 };
 
 __device__ inline void add_block(const CoarseAsm& C, int i, int j, const double* M) {
@@ -124,11 +125,11 @@ __device__ inline void add_block(const CoarseAsm& C, int i, int j, const double*
   double B[36];
   galerkin_block(M, ri, rj, C.rot[a] != 0.0, C.rot[b] != 0.0, B);
   const int n = C.solve_n[s], lo = C.solve_lo[s];
-  double* dst = C.Ac + C.off[s];
+  acc_t* dst = C.Ac + 3 * C.off[s];
   const int ra = 6 * (a - lo), cb = 6 * (b - lo);
   for (int p = 0; p < 6; ++p)
     for (int q = 0; q < 6; ++q)
-      if (B[6 * p + q] != 0.0) atomicAdd(dst + (size_t)(ra + p) * n + cb + q, B[6 * p + q]);
+      if (B[6 * p + q] != 0.0) acc_add(dst + 3 * ((size_t)(ra + p) * n + cb + q), B[6 * p + q], C.err);
 }
 
 // BSR blocks between FEM nodes
@@ -174,15 +175,16 @@ __global__ void k_coarse_pairs(CoarseAsm C, DevScene S, const int* __restrict__ 
   }
 }
 
-// unknowns without a mode (empty aggregates, rotations of small ones): identity rows
-__global__ void k_coarse_dead(CoarseAsm C, const int* __restrict__ seg, const int* __restrict__ agg_cta, int n_agg) {
+// unknowns without a mode (empty aggregates, rotations of small ones): identity rows of the assembled Ac
+__global__ void k_coarse_dead(CoarseAsm C, const int* __restrict__ seg, const int* __restrict__ agg_cta, int n_agg,
+                              double* __restrict__ Ac) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_agg) return;
   const int s = C.agg_solve[a];
   if (s < 0) return;
   const bool empty = seg[agg_cta[2 * a]] == seg[agg_cta[2 * a + 1]];
   const int n = C.solve_n[s], base = 6 * (a - C.solve_lo[s]);
-  double* dst = C.Ac + C.off[s];
+  double* dst = Ac + C.off[s];
   for (int p = 0; p < 6; ++p)
     if (empty || (p >= 3 && !C.rot[a])) dst[(size_t)(base + p) * n + base + p] = 1.0;
 }
@@ -323,18 +325,21 @@ void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L) {
 cudaError_t launch_coarse_build(cudaStream_t st, const DevScene& S, const CoarseDevLayout& D, const int* seg,
                                 const double* x, const double* val, const int* rec, const int* n_pairs, int cap,
                                 const double* pairH, int n_fric, const int* f_ids, const double* f_w,
-                                const double* f_Hu, double* Ac, double* centre, double* rot, double* gj_buf, int* status) {
+                                const double* f_Hu, double* Ac, acc_t* Ac_acc, double* centre, double* rot,
+                                double* gj_buf, int* status) {
   const int na = D.n_agg;
   if (na <= 0 || D.total <= 0) return cudaSuccess;
   k_coarse_centres<<<na, 128, 0, st>>>(seg, D.agg_cta, na, x, centre, rot);
-  k_zero<<<stride_grid(D.total, 256, 8), 256, 0, st>>>((size_t)D.total, Ac);
-  CoarseAsm C{D.node_agg, D.agg_solve, D.solve_lo, D.solve_n, D.off, centre, rot, x, Ac};
+  cudaError_t e = cudaMemsetAsync(Ac_acc, 0, sizeof(acc_t) * 3 * (size_t)D.total, st);
+  if (e != cudaSuccess) return e;
+  CoarseAsm C{D.node_agg, D.agg_solve, D.solve_lo, D.solve_n, D.off, centre, rot, x, Ac_acc, S.err};
   k_coarse_bsr<<<stride_grid(S.nnzb, 256, 8), 256, 0, st>>>(C, S.nf, S.bsr_row, S.bsr_col, val);
   k_coarse_pairs<<<stride_grid(16LL * (cap + n_fric), 256, 8), 256, 0, st>>>(C, S, rec, n_pairs, cap, pairH, n_fric,
                                                                           f_ids, f_w, f_Hu);
-  k_coarse_dead<<<(na + 127) / 128, 128, 0, st>>>(C, seg, D.agg_cta, na);
-  count_launch(5);
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int) * D.n_solves, st);
+  launch_acc_finalize(st, (size_t)D.total, Ac_acc, nullptr, Ac);
+  k_coarse_dead<<<(na + 127) / 128, 128, 0, st>>>(C, seg, D.agg_cta, na, Ac);
+  count_launch(4);
+  e = cudaMemsetAsync(status, 0, sizeof(int) * D.n_solves, st);
   if (e != cudaSuccess) return e;
   // Gauss-Jordan: one cooperative launch, all CTAs co-resident
   int per_sm = 0;

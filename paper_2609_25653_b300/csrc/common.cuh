@@ -16,6 +16,141 @@ namespace ipc {
 
 constexpr int VK_FEM = 0, VK_ABD = 1, VK_KIN = 2;
 
+// error flag bits written by kernels
+enum : int { ERRF_BVH = 1, ERRF_PCG_BREAK = 2, ERRF_NAN = 4, ERRF_PAIR_OVF = 8, ERRF_FRIC_OVF = 16, ERRF_INC = 32,
+             ERRF_ABD = 64, ERRF_ACC = 128 };
+
+// order-preserving encoding of non-negative doubles for atomicMin
+__device__ inline unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// ---------------------------------------------------------------------------
+// Order-independent accumulation.  Every sum that many threads add into
+// (energies, gradient, Hessian blocks, Dirichlet couplings, the coarse
+// matrix) is kept as an exact 192-bit two's-complement fixed-point number
+// with resolution 2^-ACC_FRAC (three 64-bit words, least significant first).
+// A double is converted exactly (bits below 2^-ACC_FRAC are dropped, toward
+// zero) and added with integer atomics whose carries are propagated word by
+// word; integer addition is associative, so the words after a set of
+// contributions do not depend on their order, and acc_value rounds the exact
+// sum to the nearest double once.  Contributions of magnitude >= 2^ACC_MAX
+// (or not finite) are not added and raise ERRF_ACC in *err.
+// ---------------------------------------------------------------------------
+using acc_t = unsigned long long;
+constexpr int ACC_FRAC = 96;  // resolution 2^-96 ~ 1.3e-29
+constexpr int ACC_MAX = 94;   // |x| < 2^94 ~ 2e28 per contribution
+constexpr int E_SLOTS = 32;
+
+// x as three words (w0 least significant) of x * 2^ACC_FRAC truncated toward zero; false if out of range
+__host__ __device__ inline bool acc_words(double x, acc_t w[3]) {
+  w[0] = w[1] = w[2] = 0;
+  union { double d; acc_t u; } cv;
+  cv.d = x;
+  const int ex = (int)((cv.u >> 52) & 0x7ff);
+  if (ex == 0) return true;        // zero or subnormal: below the resolution
+  if (ex == 0x7ff) return false;   // inf / nan
+  acc_t man = (cv.u & ((1ull << 52) - 1)) | (1ull << 52);  // |x| = man * 2^(ex - 1075)
+  int sh = ex - 1075 + ACC_FRAC;
+  if (ex - 1023 >= ACC_MAX) return false;
+  if (sh < 0) {
+    if (sh <= -53) return true;
+    man >>= -sh;
+    sh = 0;
+  }
+  // man < 2^53 placed at bit sh (sh <= ACC_FRAC + ACC_MAX - 53 < 192 - 53)
+  const int q = sh >> 6, r = sh & 63;
+  acc_t lo = man << r, hi = r ? (man >> (64 - r)) : 0;
+  if (q == 0) { w[0] = lo; w[1] = hi; }
+  else if (q == 1) { w[1] = lo; w[2] = hi; }
+  else { w[2] = lo; }
+  if (cv.u >> 63) {  // two's complement
+    w[0] = ~w[0]; w[1] = ~w[1]; w[2] = ~w[2];
+    if (++w[0] == 0 && ++w[1] == 0) ++w[2];
+  }
+  return true;
+}
+
+// three words (least significant first) added into a, carries propagated
+__device__ inline void acc_add_words(acc_t* a, const acc_t w[3]) {
+  acc_t c1 = 0;
+  if (w[0]) {
+    const acc_t o = atomicAdd(a, w[0]);
+    c1 = (o + w[0] < o) ? 1ull : 0ull;
+  }
+  acc_t t1 = w[1] + c1, c2 = (t1 < w[1]) ? 1ull : 0ull;
+  if (t1) {
+    const acc_t o = atomicAdd(a + 1, t1);
+    c2 += (o + t1 < o) ? 1ull : 0ull;
+  }
+  const acc_t t2 = w[2] + c2;
+  if (t2) atomicAdd(a + 2, t2);
+}
+
+__device__ inline void acc_add(acc_t* a, double x, int* err = nullptr) {
+  acc_t w[3];
+  if (!acc_words(x, w)) {
+    if (err) atomicOr(err, ERRF_ACC);
+    return;
+  }
+  acc_add_words(a, w);
+}
+
+// exact sum of n accumulators (plain loads; the caller orders it after their writers)
+__device__ inline void acc_sum_words(const acc_t* a, int n, acc_t w[3]) {
+  w[0] = w[1] = w[2] = 0;
+  for (int k = 0; k < n; ++k) {
+    const acc_t s0 = a[3 * k], s1 = a[3 * k + 1], s2 = a[3 * k + 2];
+    const acc_t t0 = w[0] + s0, c0 = t0 < w[0] ? 1ull : 0ull;
+    const acc_t t1 = w[1] + s1, c1a = t1 < w[1] ? 1ull : 0ull;
+    const acc_t t1c = t1 + c0, c1b = t1c < t1 ? 1ull : 0ull;
+    w[0] = t0;
+    w[1] = t1c;
+    w[2] = w[2] + s2 + c1a + c1b;
+  }
+}
+
+// the exact sum held in a rounded to the nearest double
+__host__ __device__ inline double acc_value(const acc_t* a) {
+  acc_t w0 = a[0], w1 = a[1], w2 = a[2];
+  const bool neg = (w2 >> 63) != 0;
+  if (neg) {
+    w0 = ~w0; w1 = ~w1; w2 = ~w2;
+    if (++w0 == 0 && ++w1 == 0) ++w2;
+  }
+  // the top 64 significant bits with a sticky bit for everything below, then one rounding to 53 bits
+  acc_t top, rest;
+  int e;  // value = top * 2^(e - ACC_FRAC)
+  auto lead = [](acc_t v) {  // leading zero bits of v != 0
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return __builtin_clzll(v);
+#endif
+  };
+  if (w2) {
+    const int z = lead(w2);
+    top = z ? (w2 << z) | (w1 >> (64 - z)) : w2;
+    rest = z ? ((w1 << z) | w0) : (w1 | w0);
+    e = 128 - z;
+  } else if (w1) {
+    const int z = lead(w1);
+    top = z ? (w1 << z) | (w0 >> (64 - z)) : w1;
+    rest = z ? (w0 << z) : w0;
+    e = 64 - z;
+  } else {
+    top = w0;
+    rest = 0;
+    e = 0;
+  }
+  if (top == 0) return 0.0;
+  if (rest) top |= 1ull;  // sticky: below the 11 bits dropped by the conversion
+  double v = (double)top;  // round to nearest even
+  // scale by 2^(e - ACC_FRAC) exactly (power of two, normal range)
+  union { double d; acc_t u; } s;
+  s.u = (acc_t)(1023 + e - ACC_FRAC) << 52;
+  v *= s.d;
+  return neg ? -v : v;
+}
+
 // Read-only scene topology and material data on the device.
 struct DevScene {
   int nf, nt, nab, nkb, nv, na_v, nk, n_nodes;
@@ -66,7 +201,9 @@ struct DevScene {
   // node, energy terms per scene (n_scenes, 8), CCD bound per scene (double bits),
   // max |p_F| and max |p_D| per scene (double bits), line-search step per scene
   const int* node_scene;
-  double* E_sc;
+  acc_t* E_sc;               // (n_scenes, 8) accumulators
+  int* err;                  // error flags of the iteration (ERRF_*)
+  acc_t* e_slots;            // (E_SLOTS) accumulators spreading one energy sum over many addresses
   unsigned long long* alpha_sc;
   unsigned long long* pn_sc;
   const double* alpha_trial;
@@ -76,7 +213,7 @@ __device__ inline int scene_of_vertex(const DevScene& S, int v) { return S.body_
 
 // energy term comp of one element of scene sc (batches only)
 __device__ inline void scene_energy(const DevScene& S, int sc, int comp, double e) {
-  if (S.E_sc && e != 0.0) atomicAdd(S.E_sc + 8 * sc + comp, e);
+  if (S.E_sc && e != 0.0) acc_add(S.E_sc + 3 * (8 * sc + comp), e, S.err);
 }
 
 // ---------------------------------------------------------------------------
@@ -94,9 +231,13 @@ __host__ __device__ inline d3 cross(d3 a, d3 b) {
 __device__ inline d3 ld3(const double* p, int i) { return {p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
 __device__ inline void st3(double* p, int i, d3 v) { p[3 * i] = v.x; p[3 * i + 1] = v.y; p[3 * i + 2] = v.z; }
 __device__ inline double comp(d3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+// v added into the accumulators of the three entries of node i
+__device__ inline void acc_add3(acc_t* a, int i, d3 v, int* err) {
+  acc_add(a + 9 * (size_t)i, v.x, err);
+  acc_add(a + 9 * (size_t)i + 3, v.y, err);
+  acc_add(a + 9 * (size_t)i + 6, v.z, err);
+}
 
-// order-preserving encoding of non-negative doubles for atomicMin
-__device__ inline unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 
 // block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0
 __device__ inline double block_sum(double v) {
@@ -145,8 +286,5 @@ __device__ inline NodeMap vertex_nodes(const DevScene& S, int v) {
   return m;
 }
 
-// error flag bits written by kernels
-enum : int { ERRF_BVH = 1, ERRF_PCG_BREAK = 2, ERRF_NAN = 4, ERRF_PAIR_OVF = 8, ERRF_FRIC_OVF = 16, ERRF_INC = 32,
-             ERRF_ABD = 64 };
 
 }  // namespace ipc

@@ -110,14 +110,14 @@ __device__ inline void project_pair(double* H, int mask) {
 }
 
 // Scatter a vertex-space 12-vector (scaled) to node space.
-__device__ inline void scatter_grad(const DevScene& S, const int* ids, const double* gv, double scale, double* g) {
+__device__ inline void scatter_grad(const DevScene& S, const int* ids, const double* gv, double scale, acc_t* g) {
   for (int k = 0; k < 4; ++k) {
     NodeMap m = vertex_nodes(S, ids[k]);
     for (int r = 0; r < m.n; ++r) {
       double w = scale * m.w[r];
-      atomicAdd(g + 3 * m.node[r], w * gv[3 * k]);
-      atomicAdd(g + 3 * m.node[r] + 1, w * gv[3 * k + 1]);
-      atomicAdd(g + 3 * m.node[r] + 2, w * gv[3 * k + 2]);
+      acc_add(g + 3 * ((size_t)(3 * m.node[r])), w * gv[3 * k], S.err);
+      acc_add(g + 3 * ((size_t)(3 * m.node[r] + 1)), w * gv[3 * k + 1], S.err);
+      acc_add(g + 3 * ((size_t)(3 * m.node[r] + 2)), w * gv[3 * k + 2], S.err);
     }
   }
 }
@@ -125,7 +125,7 @@ __device__ inline void scatter_grad(const DevScene& S, const int* ids, const dou
 // Diagonal node blocks of J^T H J (for the block-Jacobi preconditioner) and
 // H_FD p_D (the Dirichlet coupling) of a dense 12x12 vertex-space block.
 __device__ inline void scatter_diag_dirichlet(const DevScene& S, const int* ids, const double* H, const double* pD,
-                                              double* Dc, double* gdir) {
+                                              acc_t* Dc, acc_t* gdir) {
   NodeMap m[4];
   bool kin[4];
   d3 pk[4];
@@ -146,9 +146,9 @@ __device__ inline void scatter_diag_dirichlet(const DevScene& S, const int* ids,
     }
     if (y.x != 0.0 || y.y != 0.0 || y.z != 0.0)
       for (int r = 0; r < m[a].n; ++r) {
-        atomicAdd(gdir + 3 * m[a].node[r], m[a].w[r] * y.x);
-        atomicAdd(gdir + 3 * m[a].node[r] + 1, m[a].w[r] * y.y);
-        atomicAdd(gdir + 3 * m[a].node[r] + 2, m[a].w[r] * y.z);
+        acc_add(gdir + 3 * ((size_t)(3 * m[a].node[r])), m[a].w[r] * y.x, S.err);
+        acc_add(gdir + 3 * ((size_t)(3 * m[a].node[r] + 1)), m[a].w[r] * y.y, S.err);
+        acc_add(gdir + 3 * ((size_t)(3 * m[a].node[r] + 2)), m[a].w[r] * y.z, S.err);
       }
     // diagonal node blocks
     for (int b = 0; b < 4; ++b) {
@@ -157,9 +157,9 @@ __device__ inline void scatter_diag_dirichlet(const DevScene& S, const int* ids,
         for (int q = 0; q < m[b].n; ++q) {
           if (m[a].node[r] != m[b].node[q]) continue;
           double w = m[a].w[r] * m[b].w[q];
-          double* dst = Dc + 9 * m[a].node[r];
+          acc_t* dst = Dc + 27 * (size_t)m[a].node[r];
           for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) atomicAdd(dst + 3 * i + j, w * H[12 * (3 * a + i) + 3 * b + j]);
+            for (int j = 0; j < 3; ++j) acc_add(dst + 3 * (3 * i + j), w * H[12 * (3 * a + i) + 3 * b + j], S.err);
         }
     }
   }
@@ -168,12 +168,12 @@ __device__ inline void scatter_diag_dirichlet(const DevScene& S, const int* ids,
 // mode 0: energy (and min s) only; mode 2: also gradient, projected Hessian, preconditioner diagonal, Dirichlet term.
 __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __restrict__ xv, const int* __restrict__ rec,
                                                  const int* __restrict__ n_dev, int cap, double sh, double kappa_unused,
-                                                 double scale, int mode, int project, double* __restrict__ g,
-                                                 double* __restrict__ pairH, double* __restrict__ Dc,
-                                                 const double* __restrict__ pD, double* __restrict__ gdir,
-                                                 double* __restrict__ E, unsigned long long* __restrict__ min_s) {
+                                                 double scale, int mode, int project, acc_t* __restrict__ g,
+                                                 double* __restrict__ pairH, acc_t* __restrict__ Dc,
+                                                 const double* __restrict__ pD, acc_t* __restrict__ gdir,
+                                                 acc_t* __restrict__ E, unsigned long long* __restrict__ min_s) {
   int n = min(*n_dev, cap);
-  double e_acc = 0.0, smin = 1e300;
+  double smin = 1e300;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     {
       const int* r = rec + 8 * (size_t)k;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
       double eps_x = kind == 1 ? 1e-3 * S.edge_rest_sq[r[1]] * S.edge_rest_sq[r[2]] : 0.0;
       if (mode == 0) {
         double m = kind == 1 ? moll_value(x, eps_x) : 1.0;
-        e_acc += kappa * m * b;
+        acc_add(S.e_slots + 3 * (k & (E_SLOTS - 1)), kappa * m * b, S.err);
         if (S.E_sc) scene_energy(S, scene_of_vertex(S, ids[0]), 2, kappa * m * b);
       } else if (b != 0.0 || b1 != 0.0) {
         double gs[12], Hs[144];
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
           d3 nn = cross(a, bb);
           if (dot(nn, nn) < eps_x) { m = mollifier(x, eps_x, gm, Hm); moll = true; }
         }
-        e_acc += kappa * m * b;
+        acc_add(S.e_slots + 3 * (k & (E_SLOTS - 1)), kappa * m * b, S.err);
         if (S.E_sc) scene_energy(S, scene_of_vertex(S, ids[0]), 2, kappa * m * b);
         double grad[12];
         for (int i = 0; i < 12; ++i) grad[i] = kappa * (m * b1 * gs[i] + (moll ? b * gm[i] : 0.0));
@@ -228,8 +228,6 @@ __global__ void __launch_bounds__(128) k_barrier(DevScene S, const double* __res
       }
     }
   }
-  double s = block_sum(e_acc);
-  if (threadIdx.x == 0) atomicAdd(E, s);
   double m = block_max(-smin);
   if (threadIdx.x == 0 && min_s) atomicMin(min_s, dbits(-m));
 }
@@ -292,16 +290,16 @@ __device__ inline void warp_project_f32(PairWork& W, int n, int lane) {
 __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const double* __restrict__ xv,
                                                              const int* __restrict__ rec, const int* __restrict__ n_dev,
                                                              int cap, double sh, double kappa_unused, double scale,
-                                                             int project, double* __restrict__ g,
-                                                             double* __restrict__ pairH, double* __restrict__ Dc,
-                                                             const double* __restrict__ pD, double* __restrict__ gdir,
-                                                             double* __restrict__ E, unsigned long long* min_s,
+                                                             int project, acc_t* __restrict__ g,
+                                                             double* __restrict__ pairH, acc_t* __restrict__ Dc,
+                                                             const double* __restrict__ pD, acc_t* __restrict__ gdir,
+                                                             acc_t* __restrict__ E, unsigned long long* min_s,
                                                              int hess_fp32) {
   __shared__ PairWork work[BWARPS];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   PairWork& W = work[wid];
   int n = min(*n_dev, cap);
-  double e_acc = 0.0, smin = 1e300;
+  double smin = 1e300;
   int gw = blockIdx.x * BWARPS + wid, nw = gridDim.x * BWARPS;
   for (int k = gw; k < n; k += nw) {
     const int* r = rec + 8 * (size_t)k;
@@ -351,7 +349,7 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
       W.moll = moll;
       W.sc[0] = sd; W.sc[1] = b; W.sc[2] = b1; W.sc[3] = b2; W.sc[4] = mval; W.sc[5] = m1; W.sc[6] = m2;
       smin = fmin(smin, sd);
-      e_acc += kappa * mval * b;
+      acc_add(S.e_slots + 3 * (k & (E_SLOTS - 1)), kappa * mval * b, S.err);
       if (S.E_sc) scene_energy(S, scene_of_vertex(S, W.ids[0]), 2, kappa * mval * b);
     }
     __syncwarp();
@@ -438,7 +436,7 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
     if (lane < 12) {
       double gi = kappa * (mval * b1 * W.gs[lane] + (moll ? b * m1 * W.gc[lane] : 0.0));
       NodeMap m = vertex_nodes(S, W.ids[lane / 3]);
-      for (int t = 0; t < m.n; ++t) atomicAdd(g + 3 * m.node[t] + lane % 3, scale * m.w[t] * gi);
+      for (int t = 0; t < m.n; ++t) acc_add(g + 3 * ((size_t)(3 * m.node[t] + lane % 3)), scale * m.w[t] * gi, S.err);
     }
     // diagonal node blocks (a, b) entry (i, j): item = (a, b, i, j), 144 items
     for (int e = lane; e < 144; e += 32) {
@@ -450,7 +448,7 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
       double h = W.V[e];
       for (int t = 0; t < ma.n; ++t)
         for (int u = 0; u < mb.n; ++u)
-          if (ma.node[t] == mb.node[u]) atomicAdd(Dc + 9 * ma.node[t] + 3 * i + j, ma.w[t] * mb.w[u] * h);
+          if (ma.node[t] == mb.node[u]) acc_add(Dc + 3 * (9 * (size_t)ma.node[t] + 3 * i + j), ma.w[t] * mb.w[u] * h, S.err);
     }
     // Dirichlet: free slot a row i: sum over kinematic slots b of H_ab pD_b
     if (lane < 12) {
@@ -467,14 +465,12 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
         }
         if (y != 0.0) {
           NodeMap m = vertex_nodes(S, va);
-          for (int t = 0; t < m.n; ++t) atomicAdd(gdir + 3 * m.node[t] + i, m.w[t] * y);
+          for (int t = 0; t < m.n; ++t) acc_add(gdir + 3 * ((size_t)(3 * m.node[t] + i)), m.w[t] * y, S.err);
         }
       }
     }
     __syncwarp();
   }
-  double sblk = block_sum(e_acc);
-  if (threadIdx.x == 0) atomicAdd(E, sblk);
   double mm = block_max(-smin);
   if (threadIdx.x == 0 && min_s) atomicMin(min_s, dbits(-mm));
 }
@@ -544,7 +540,7 @@ __device__ inline int weight_directions(int kind, int type, double B[4][2]) {
 __global__ void k_friction_lag_adjoint(DevScene S, const double* __restrict__ xv, const double* __restrict__ xv_t,
                                        int n, const int* __restrict__ f_ids, const int* __restrict__ f_rec, double sh,
                                        double mu, double eps, double scale, const double* __restrict__ lam_dof,
-                                       double* __restrict__ gz) {
+                                       acc_t* __restrict__ gz) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int kind = f_rec[4 * k], ta = f_rec[4 * k + 2], tb = f_rec[4 * k + 3];
@@ -642,7 +638,7 @@ __global__ void k_friction_lag_adjoint(DevScene S, const double* __restrict__ xv
   for (int q = 0; q < 4; ++q) {
     const NodeMap mq = vertex_nodes(S, ids[q]);
     for (int rr = 0; rr < mq.n; ++rr)
-      for (int c = 0; c < 3; ++c) atomicAdd(gz + 3 * mq.node[rr] + c, -scale * mq.w[rr] * grad[3 * q + c]);
+      for (int c = 0; c < 3; ++c) acc_add(gz + 3 * ((size_t)(3 * mq.node[rr] + c)), -scale * mq.w[rr] * grad[3 * q + c], S.err);
   }
 }
 
@@ -651,8 +647,8 @@ __global__ void k_friction_lag_adjoint(DevScene S, const double* __restrict__ xv
 __global__ void k_friction(DevScene S, const double* __restrict__ xv, const double* __restrict__ xv_t, int n,
                            const int* __restrict__ f_ids, const double* __restrict__ f_w, const double* __restrict__ f_n,
                            const double* __restrict__ f_lam, double mu, double eps, double scale, int mode,
-                           double* __restrict__ g, double* __restrict__ f_Hu, double* __restrict__ Dc,
-                           const double* __restrict__ pD, double* __restrict__ gdir, double* __restrict__ E) {
+                           acc_t* __restrict__ g, double* __restrict__ f_Hu, acc_t* __restrict__ Dc,
+                           const double* __restrict__ pD, acc_t* __restrict__ gdir, acc_t* __restrict__ E) {
   double e_acc = 0.0;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) {
@@ -678,9 +674,9 @@ __global__ void k_friction(DevScene S, const double* __restrict__ xv, const doub
         NodeMap m = vertex_nodes(S, ids[q]);
         for (int r = 0; r < m.n; ++r) {
           double ww = scale * w[q] * m.w[r];
-          atomicAdd(g + 3 * m.node[r], ww * gu.x);
-          atomicAdd(g + 3 * m.node[r] + 1, ww * gu.y);
-          atomicAdd(g + 3 * m.node[r] + 2, ww * gu.z);
+          acc_add(g + 3 * ((size_t)(3 * m.node[r])), ww * gu.x, S.err);
+          acc_add(g + 3 * ((size_t)(3 * m.node[r] + 1)), ww * gu.y, S.err);
+          acc_add(g + 3 * ((size_t)(3 * m.node[r] + 2)), ww * gu.z, S.err);
         }
       }
     }
@@ -709,9 +705,9 @@ __global__ void k_friction(DevScene S, const double* __restrict__ xv, const doub
         for (int r = 0; r < m[a_].n; ++r) {
           double ww = w[a_] * m[a_].w[r];
           if (hd.x != 0.0 || hd.y != 0.0 || hd.z != 0.0) {
-            atomicAdd(gdir + 3 * m[a_].node[r], ww * hd.x);
-            atomicAdd(gdir + 3 * m[a_].node[r] + 1, ww * hd.y);
-            atomicAdd(gdir + 3 * m[a_].node[r] + 2, ww * hd.z);
+            acc_add(gdir + 3 * ((size_t)(3 * m[a_].node[r])), ww * hd.x, S.err);
+            acc_add(gdir + 3 * ((size_t)(3 * m[a_].node[r] + 1)), ww * hd.y, S.err);
+            acc_add(gdir + 3 * ((size_t)(3 * m[a_].node[r] + 2)), ww * hd.z, S.err);
           }
         }
         for (int b_ = 0; b_ < 4; ++b_) {
@@ -720,22 +716,33 @@ __global__ void k_friction(DevScene S, const double* __restrict__ xv, const doub
             for (int q = 0; q < m[b_].n; ++q) {
               if (m[a_].node[r] != m[b_].node[q]) continue;
               double ww = w[a_] * m[a_].w[r] * w[b_] * m[b_].w[q];
-              for (int i = 0; i < 9; ++i) atomicAdd(Dc + 9 * m[a_].node[r] + i, ww * Hu[i]);
+              for (int i = 0; i < 9; ++i) acc_add(Dc + 3 * (9 * (size_t)m[a_].node[r] + i), ww * Hu[i], S.err);
             }
         }
       }
     }
   }
   double s = block_sum(e_acc);
-  if (threadIdx.x == 0) atomicAdd(E, s);
+  if (threadIdx.x == 0) acc_add(E, s, S.err);
 }
 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+// E += the exact sum of the barrier's per-pair slots (one thread; the slots are few)
+__global__ void k_fold_slots(const acc_t* __restrict__ slots, acc_t* __restrict__ E) {
+  if (blockIdx.x || threadIdx.x) return;
+  acc_t w[3];
+  acc_sum_words(slots, E_SLOTS, w);
+  acc_add_words(E, w);
+}
+
 void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
-                    int cap, double sh, double kappa, double scale, int mode, int project, double* g, double* pairH,
-                    double* Dc, const double* pD, double* gdir, double* E, unsigned long long* min_s, int hess_fp32) {
+                    int cap, double sh, double kappa, double scale, int mode, int project, acc_t* g, double* pairH,
+                    acc_t* Dc, const double* pD, acc_t* gdir, acc_t* E, unsigned long long* min_s, int hess_fp32) {
+  // the energy of every pair goes into slot (pair mod E_SLOTS), folded into E afterwards: no partial sum
+  // depends on the launch shape, and the slots spread the atomic traffic
+  cudaMemsetAsync(S.e_slots, 0, sizeof(acc_t) * 3 * E_SLOTS, st);
   if (mode >= 2) {
     // one warp per pair: as many warps as the thread-per-pair launch had threads / 32, at least one block
     int wgrid = stride_grid(cap, BWARPS, 16);
@@ -745,7 +752,8 @@ void launch_barrier(cudaStream_t st, int grid, const DevScene& S, const double* 
     k_barrier<<<grid, 128, 0, st>>>(S, xv, rec, n_dev, cap, sh, kappa, scale, mode, project, g, pairH, Dc, pD, gdir,
                                     E, min_s);
   }
-  count_launch();
+  k_fold_slots<<<1, 32, 0, st>>>(S.e_slots, E);
+  count_launch(2);
 }
 void launch_friction_lag(cudaStream_t st, int grid, const DevScene& S, const double* xv, const int* rec, const int* n_dev,
                          int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam,
@@ -755,14 +763,14 @@ void launch_friction_lag(cudaStream_t st, int grid, const DevScene& S, const dou
 }
 void launch_friction_lag_adjoint(cudaStream_t st, const DevScene& S, const double* xv, const double* xv_t, int n,
                                  const int* f_ids, const int* f_rec, double sh, double mu, double eps, double scale,
-                                 const double* lam_dof, double* gz) {
+                                 const double* lam_dof, acc_t* gz) {
   if (n <= 0) return;
   k_friction_lag_adjoint<<<(n + 63) / 64, 64, 0, st>>>(S, xv, xv_t, n, f_ids, f_rec, sh, mu, eps, scale, lam_dof, gz);
   count_launch();
 }
 void launch_friction(cudaStream_t st, const DevScene& S, const double* xv, const double* xv_t, int n, const int* f_ids,
                      const double* f_w, const double* f_n, const double* f_lam, double mu, double eps, double scale,
-                     int mode, double* g, double* f_Hu, double* Dc, const double* pD, double* gdir, double* E) {
+                     int mode, acc_t* g, double* f_Hu, acc_t* Dc, const double* pD, acc_t* gdir, acc_t* E) {
   if (n <= 0) return;
   k_friction<<<(n + 127) / 128, 128, 0, st>>>(S, xv, xv_t, n, f_ids, f_w, f_n, f_lam, mu, eps, scale, mode, g, f_Hu, Dc,
                                               pD, gdir, E);

@@ -74,9 +74,9 @@ __global__ void k_vertex_disp(DevScene S, const double* __restrict__ p, const do
   st3(pv, v, x);
 }
 
-// Inertia 1/2 (z - z~)^T M (z - z~): energy into E[0]; gradient g = M (z - z~) (overwrites g).
+// Inertia 1/2 (z - z~)^T M (z - z~): energy into E[0]; gradient M (z - z~) added into g.
 __global__ void k_inertia(DevScene S, const double* __restrict__ z, const double* __restrict__ z_tilde,
-                          double* __restrict__ g, double* __restrict__ E, int want_grad) {
+                          acc_t* __restrict__ g, acc_t* __restrict__ E, int want_grad) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (i < S.nf) {
@@ -84,7 +84,7 @@ __global__ void k_inertia(DevScene S, const double* __restrict__ z, const double
     double m = S.node_mass[i];
     e = 0.5 * m * dot(dz, dz);
     if (S.E_sc) scene_energy(S, S.node_scene[i], 0, e);
-    if (want_grad) st3(g, i, m * dz);
+    if (want_grad) acc_add3(g, i, m * dz, S.err);
   } else if (i < S.n_nodes) {
     int b = (i - S.nf) / 4, r = (i - S.nf) % 4;
     int base = S.nf + 4 * b;
@@ -93,10 +93,10 @@ __global__ void k_inertia(DevScene S, const double* __restrict__ z, const double
     for (int s = 0; s < 4; ++s) acc = acc + Sm[4 * r + s] * (ld3(z, base + s) - ld3(z_tilde, base + s));
     e = 0.5 * dot(ld3(z, i) - ld3(z_tilde, i), acc);
     if (S.E_sc) scene_energy(S, S.node_scene[i], 0, e);
-    if (want_grad) st3(g, i, acc);
+    if (want_grad) acc_add3(g, i, acc, S.err);
   }
   double s = block_sum(e);
-  if (threadIdx.x == 0) atomicAdd(E, s);
+  if (threadIdx.x == 0) acc_add(E, s, S.err);
 }
 
 
@@ -374,10 +374,10 @@ __device__ inline void snh_projected_hessian_f32(const d3* fd, double mu_d, doub
 // its gradient and PSD-projected Hessian scattered into the BSR matrix.
 // scale = dt^2 for the incremental potential; mode: 0 energy only, 1 + gradient, 2 + Hessian.
 // F32H: the projected Hessian in FP32 (mixed precision); energy and gradient always FP64.
-template <typename HT, bool F32H>
+template <bool F32H>
 __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __restrict__ xv, double scale, int mode,
-                                                 int project, double* __restrict__ g, HT* __restrict__ Hval,
-                                                 double* __restrict__ tetH, double* __restrict__ E) {
+                                                 int project, acc_t* __restrict__ g, acc_t* __restrict__ Hval,
+                                                 double* __restrict__ tetH, acc_t* __restrict__ E) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   double energy = 0.0;
   if (e < S.nt) {
@@ -409,9 +409,7 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
       double sv = scale * V;
       for (int a = 0; a < 4; ++a) {
         d3 ga = Cc[a][0] * Pc[0] + Cc[a][1] * Pc[1] + Cc[a][2] * Pc[2];
-        atomicAdd(g + 3 * id[a], sv * ga.x);
-        atomicAdd(g + 3 * id[a] + 1, sv * ga.y);
-        atomicAdd(g + 3 * id[a] + 2, sv * ga.z);
+        if (g) acc_add3(g, id[a], sv * ga, S.err);
       }
       if (mode >= 2 && project) {
         using HC = typename std::conditional<F32H, float, double>::type;
@@ -421,9 +419,9 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
         for (int a = 0; a < 4; ++a)
           for (int b = 0; b < 4; ++b) {
             if (Hval) {
-              HT* dst = Hval + 9 * (size_t)S.tet_blk[16 * e + 4 * a + b];
+              acc_t* dst = Hval + 27 * (size_t)S.tet_blk[16 * e + 4 * a + b];
               for (int i = 0; i < 3; ++i)
-                for (int k = 0; k < 3; ++k) atomicAdd(dst + 3 * i + k, (HT)H12[12 * (3 * a + i) + 3 * b + k]);
+                for (int k = 0; k < 3; ++k) acc_add(dst + 3 * (3 * i + k), (double)H12[12 * (3 * a + i) + 3 * b + k], S.err);
             }
             if (tetH)
               for (int i = 0; i < 3; ++i)
@@ -459,8 +457,8 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
                 blk[3 * i + k] = sv * s;
               }
             if (Hval) {
-              HT* dst = Hval + 9 * (size_t)S.tet_blk[16 * e + 4 * a + b];
-              for (int q = 0; q < 9; ++q) atomicAdd(dst + q, (HT)blk[q]);
+              acc_t* dst = Hval + 27 * (size_t)S.tet_blk[16 * e + 4 * a + b];
+              for (int q = 0; q < 9; ++q) acc_add(dst + 3 * q, blk[q], S.err);
             }
             if (tetH)
               for (int i = 0; i < 3; ++i)
@@ -470,12 +468,12 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
     }
   }
   double s = block_sum(energy);
-  if (threadIdx.x == 0 && E) atomicAdd(E, s);
+  if (threadIdx.x == 0 && E) acc_add(E, s, S.err);
 }
 
 // Stitch springs 1/2 k_c |x_i - x^_i|^2 (Eq. 2); the constant Hessian k_c I is part of the fixed matrix.
 __global__ void k_stitch(DevScene S, const double* __restrict__ xv, const double* __restrict__ stitch_hat, double k_c_unused,
-                         double scale, int mode, double* __restrict__ g, double* __restrict__ E) {
+                         double scale, int mode, acc_t* __restrict__ g, acc_t* __restrict__ E) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (i < S.n_stitch) {
@@ -484,19 +482,15 @@ __global__ void k_stitch(DevScene S, const double* __restrict__ xv, const double
     d3 d = ld3(xv, v) - ld3(stitch_hat, i);
     e = 0.5 * k_c * dot(d, d);
     if (S.E_sc) scene_energy(S, scene_of_vertex(S, v), 4, e);
-    if (mode >= 1) {
-      atomicAdd(g + 3 * v, scale * k_c * d.x);
-      atomicAdd(g + 3 * v + 1, scale * k_c * d.y);
-      atomicAdd(g + 3 * v + 2, scale * k_c * d.z);
-    }
+    if (mode >= 1) acc_add3(g, v, (scale * k_c) * d, S.err);
   }
   double s = block_sum(e);
-  if (threadIdx.x == 0) atomicAdd(E, s);
+  if (threadIdx.x == 0) acc_add(E, s, S.err);
 }
 
 // ABD orthogonality kappa_A V sum_ij (a_i . a_j - delta_ij)^2 over the columns of A.
 __global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kappa_A, double scale, int mode, int project,
-                           double* __restrict__ g, double* __restrict__ Hval, double* __restrict__ E) {
+                           acc_t* __restrict__ g, acc_t* __restrict__ Hval, acc_t* __restrict__ E) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (b < S.nab) {
@@ -513,9 +507,7 @@ __global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kapp
     if (mode >= 1) {
       for (int i = 0; i < 3; ++i) {
         d3 gi = 4.0 * k * (G[i][0] * a[0] + G[i][1] * a[1] + G[i][2] * a[2]);
-        atomicAdd(g + 3 * (base + 1 + i), scale * gi.x);
-        atomicAdd(g + 3 * (base + 1 + i) + 1, scale * gi.y);
-        atomicAdd(g + 3 * (base + 1 + i) + 2, scale * gi.z);
+        acc_add3(g, base + 1 + i, scale * gi, S.err);
       }
     }
     if (mode >= 2) {
@@ -535,14 +527,14 @@ __global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kapp
       if (project) project_psd<9, double>(H);
       for (int ki = 0; ki < 3; ++ki)
         for (int li = 0; li < 3; ++li) {
-          double* dst = Hval + 9 * (size_t)S.abd_blk[16 * b + 4 * (1 + ki) + (1 + li)];
+          acc_t* dst = Hval + 27 * (size_t)S.abd_blk[16 * b + 4 * (1 + ki) + (1 + li)];
           for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) atomicAdd(dst + 3 * r + c, scale * H[9 * (3 * ki + r) + 3 * li + c]);
+            for (int c = 0; c < 3; ++c) acc_add(dst + 3 * (3 * r + c), scale * H[9 * (3 * ki + r) + 3 * li + c], S.err);
         }
     }
   }
   double s = block_sum(e);
-  if (threadIdx.x == 0) atomicAdd(E, s);
+  if (threadIdx.x == 0) acc_add(E, s, S.err);
 }
 
 // Joint drive potentials (E_joint of Eq. 3), one thread per joint.  Side a
@@ -553,8 +545,8 @@ __global__ void k_abd_orth(DevScene S, const double* __restrict__ z, double kapp
 // k/2 |r|^2, gradient k w_m r at pseudo-node m, Hessian k w_m w_n I for the
 // block pair (m, n): constant in z and positive semi-definite, so nothing is
 // projected.
-__global__ void k_joints(DevScene S, const double* __restrict__ z, double scale, int mode, double* __restrict__ g,
-                         double* __restrict__ Hval, double* __restrict__ E) {
+__global__ void k_joints(DevScene S, const double* __restrict__ z, double scale, int mode, acc_t* __restrict__ g,
+                         acc_t* __restrict__ Hval, acc_t* __restrict__ E) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (j < S.nj) {
@@ -578,10 +570,7 @@ __global__ void k_joints(DevScene S, const double* __restrict__ z, double scale,
     if (mode >= 1)
       for (int m = 0; m < 8; ++m)
         if (node[m] >= 0 && w[m] != 0.0) {
-          const double c = scale * k * w[m];
-          atomicAdd(g + 3 * node[m], c * r.x);
-          atomicAdd(g + 3 * node[m] + 1, c * r.y);
-          atomicAdd(g + 3 * node[m] + 2, c * r.z);
+          acc_add3(g, node[m], (scale * k * w[m]) * r, S.err);
         }
     if (mode >= 2)
       for (int m = 0; m < 8; ++m)
@@ -589,14 +578,14 @@ __global__ void k_joints(DevScene S, const double* __restrict__ z, double scale,
           const double c = scale * k * w[m] * w[n];
           const int blk = S.jt_blk[64 * j + 8 * m + n];
           if (c == 0.0 || blk < 0) continue;
-          double* dst = Hval + 9 * (size_t)blk;
-          atomicAdd(dst, c);
-          atomicAdd(dst + 4, c);
-          atomicAdd(dst + 8, c);
+          acc_t* dst = Hval + 27 * (size_t)blk;
+          acc_add(dst, c, S.err);
+          acc_add(dst + 12, c, S.err);
+          acc_add(dst + 24, c, S.err);
         }
   }
   const double s = block_sum(e);
-  if (threadIdx.x == 0) atomicAdd(E, s);
+  if (threadIdx.x == 0) acc_add(E, s, S.err);
 }
 
 // The same energy, gradient and projected Hessian with one warp per body: the
@@ -614,8 +603,8 @@ struct OrthWork {
 
 __global__ void __launch_bounds__(32 * ORTH_WARPS) k_abd_orth_warp(DevScene S, const double* __restrict__ z,
                                                                     double kappa_A, double scale, int mode, int project,
-                                                                    double* __restrict__ g, double* __restrict__ Hval,
-                                                                    double* __restrict__ E) {
+                                                                    acc_t* __restrict__ g, acc_t* __restrict__ Hval,
+                                                                    acc_t* __restrict__ E) {
   __shared__ OrthWork work[ORTH_WARPS];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x * ORTH_WARPS + wid;
@@ -631,13 +620,13 @@ __global__ void __launch_bounds__(32 * ORTH_WARPS) k_abd_orth_warp(DevScene S, c
     double e = 0.0;
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) e += G[i][j] * G[i][j];
-    atomicAdd(E, k * e);
+    acc_add(E, k * e, S.err);
     if (S.E_sc) scene_energy(S, S.node_scene[base], 5, k * e);
   }
   if (mode >= 1 && lane < 9) {
     const int i = lane / 3, c = lane % 3;
     const double gi = 4.0 * k * (G[i][0] * comp(a[0], c) + G[i][1] * comp(a[1], c) + G[i][2] * comp(a[2], c));
-    atomicAdd(g + 3 * (base + 1 + i) + c, scale * gi);
+    acc_add(g + 3 * (3 * (base + 1 + i) + c), scale * gi, S.err);
   }
   if (mode < 2) return;
   for (int e = lane; e < 144; e += 32) {
@@ -656,8 +645,8 @@ __global__ void __launch_bounds__(32 * ORTH_WARPS) k_abd_orth_warp(DevScene S, c
   for (int e = lane; e < 81; e += 32) {
     const int row = e / 9, col = e % 9;
     const int ki = row / 3, r = row % 3, li = col / 3, c = col % 3;
-    double* dst = Hval + 9 * (size_t)S.abd_blk[16 * b + 4 * (1 + ki) + (1 + li)];
-    atomicAdd(dst + 3 * r + c, scale * W.H[12 * row + col]);
+    acc_t* dst = Hval + 27 * (size_t)S.abd_blk[16 * b + 4 * (1 + ki) + (1 + li)];
+    acc_add(dst + 3 * (3 * r + c), scale * W.H[12 * row + col], S.err);
   }
 }
 
@@ -740,25 +729,25 @@ void launch_vertex_positions(cudaStream_t st, const DevScene& S, const double* z
 void launch_vertex_disp(cudaStream_t st, const DevScene& S, const double* p, const double* pD, double* pv) {
   if (S.nv) { k_vertex_disp<<<nb(S.nv, 256), 256, 0, st>>>(S, p, pD, pv); count_launch(); }
 }
-void launch_inertia(cudaStream_t st, const DevScene& S, const double* z, const double* z_tilde, double* g, double* E,
+void launch_inertia(cudaStream_t st, const DevScene& S, const double* z, const double* z_tilde, acc_t* g, acc_t* E,
                     int want_grad) {
   if (S.n_nodes) { k_inertia<<<nb(S.n_nodes, 256), 256, 0, st>>>(S, z, z_tilde, g, E, want_grad); count_launch(); }
 }
 void launch_elastic(cudaStream_t st, const DevScene& S, const double* xv, double scale, int mode, int project,
-                    double* g, double* Hval, double* tetH, double* E, int hess_fp32) {
+                    acc_t* g, acc_t* Hval, double* tetH, acc_t* E, int hess_fp32) {
   if (!S.nt) return;
   if (hess_fp32 && mode >= 2 && project)
-    k_elastic<double, true><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+    k_elastic<true><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
   else
-    k_elastic<double, false><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+    k_elastic<false><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
   count_launch();
 }
 void launch_stitch(cudaStream_t st, const DevScene& S, const double* xv, const double* stitch_hat, double k_c,
-                   double scale, int mode, double* g, double* E) {
+                   double scale, int mode, acc_t* g, acc_t* E) {
   if (S.n_stitch) { k_stitch<<<nb(S.n_stitch, 256), 256, 0, st>>>(S, xv, stitch_hat, k_c, scale, mode, g, E); count_launch(); }
 }
 void launch_abd_orth(cudaStream_t st, const DevScene& S, const double* z, double kappa_A, double scale, int mode,
-                     int project, double* g, double* Hval, double* E) {
+                     int project, acc_t* g, acc_t* Hval, acc_t* E) {
   if (S.nab) {
     if (mode >= 2)
       k_abd_orth_warp<<<nb(S.nab, ORTH_WARPS), 32 * ORTH_WARPS, 0, st>>>(S, z, kappa_A, scale, mode, project, g, Hval, E);
@@ -767,8 +756,20 @@ void launch_abd_orth(cudaStream_t st, const DevScene& S, const double* z, double
     count_launch();
   }
 }
-void launch_joints(cudaStream_t st, const DevScene& S, const double* z, double scale, int mode, double* g, double* Hval,
-                   double* E) {
+__global__ void k_acc_finalize(size_t n, const acc_t* __restrict__ acc, const double* __restrict__ base,
+                               double* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = acc_value(acc + 3 * i);
+    out[i] = base ? base[i] + v : v;
+  }
+}
+void launch_acc_finalize(cudaStream_t st, size_t n, const acc_t* acc, const double* base, double* out) {
+  if (!n) return;
+  k_acc_finalize<<<stride_grid((long long)n, 256, 8), 256, 0, st>>>(n, acc, base, out);
+  count_launch();
+}
+void launch_joints(cudaStream_t st, const DevScene& S, const double* z, double scale, int mode, acc_t* g, acc_t* Hval,
+                   acc_t* E) {
   if (S.nj) { k_joints<<<nb(S.nj, 64), 64, 0, st>>>(S, z, scale, mode, g, Hval, E); count_launch(); }
 }
 void launch_trial(cudaStream_t st, int ndof, int nk3, const double* z, const double* p, double alpha, double* z_out,

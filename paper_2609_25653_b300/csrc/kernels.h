@@ -180,17 +180,21 @@ void launch_predict(cudaStream_t, const DevScene&, const double* z, const double
 void launch_kin_targets(cudaStream_t, const DevScene&, const double* T, double* xk_hat, double* stitch_hat);
 void launch_vertex_positions(cudaStream_t, const DevScene&, const double* z, const double* xk, double* xv);
 void launch_vertex_disp(cudaStream_t, const DevScene&, const double* p, const double* pD, double* pv);
-void launch_inertia(cudaStream_t, const DevScene&, const double* z, const double* z_tilde, double* g, double* E,
+// Accumulating outputs (acc_t: three words per value, see common.cuh): g (n_nodes, 3), Hval (nnzb, 9),
+// Dc (n_nodes, 9), gdir (n_nodes, 3) and E (one value) are added into, never overwritten.
+void launch_inertia(cudaStream_t, const DevScene&, const double* z, const double* z_tilde, acc_t* g, acc_t* E,
                     int want_grad);
 // hess_fp32: the projected Hessian in FP32 (mixed precision); energy and gradient stay FP64
-void launch_elastic(cudaStream_t, const DevScene&, const double* xv, double scale, int mode, int project, double* g,
-                    double* Hval, double* tetH, double* E, int hess_fp32 = 0);
+void launch_elastic(cudaStream_t, const DevScene&, const double* xv, double scale, int mode, int project, acc_t* g,
+                    acc_t* Hval, double* tetH, acc_t* E, int hess_fp32 = 0);
 void launch_stitch(cudaStream_t, const DevScene&, const double* xv, const double* stitch_hat, double k_c, double scale,
-                   int mode, double* g, double* E);
+                   int mode, acc_t* g, acc_t* E);
 void launch_abd_orth(cudaStream_t, const DevScene&, const double* z, double kappa_A, double scale, int mode, int project,
-                     double* g, double* Hval, double* E);
-void launch_joints(cudaStream_t, const DevScene&, const double* z, double scale, int mode, double* g, double* Hval,
-                   double* E);
+                     acc_t* g, acc_t* Hval, acc_t* E);
+void launch_joints(cudaStream_t, const DevScene&, const double* z, double scale, int mode, acc_t* g, acc_t* Hval,
+                   acc_t* E);
+// out[i] = (base ? base[i] : 0) + the value of accumulator i, for i < n
+void launch_acc_finalize(cudaStream_t, size_t n, const acc_t* acc, const double* base, double* out);
 void launch_trial(cudaStream_t, int ndof, int nk3, const double* z, const double* p, double alpha, double* z_out,
                   const double* xk, const double* pD, const double* xk_hat, double* xk_out);
 void launch_velocity(cudaStream_t, int ndof, const double* z, const double* z_t, double inv_dt, double* zd);
@@ -203,8 +207,8 @@ void launch_sub(cudaStream_t, int n, const double* a, const double* b, double* o
 
 // contact.cu
 void launch_barrier(cudaStream_t, int grid, const DevScene&, const double* xv, const int* rec, const int* n_dev, int cap,
-                    double sh, double kappa, double scale, int mode, int project, double* g, double* pairH, double* Dc,
-                    const double* pD, double* gdir, double* E, unsigned long long* min_s, int hess_fp32 = 0);
+                    double sh, double kappa, double scale, int mode, int project, acc_t* g, double* pairH, acc_t* Dc,
+                    const double* pD, acc_t* gdir, acc_t* E, unsigned long long* min_s, int hess_fp32 = 0);
 // f_rec (may be null): (kind, type, primitive a, primitive b) of every friction pair, for the adjoint
 void launch_friction_lag(cudaStream_t, int grid, const DevScene&, const double* xv, const int* rec, const int* n_dev,
                          int cap, double sh, double kappa, int* f_ids, double* f_w, double* f_n, double* f_lam,
@@ -212,10 +216,29 @@ void launch_friction_lag(cudaStream_t, int grid, const DevScene&, const double* 
 // adjoint: -scale d(lam . grad D)/dx_t through the lagged friction data, added into gz (DOF space)
 void launch_friction_lag_adjoint(cudaStream_t, const DevScene&, const double* xv, const double* xv_t, int n,
                                  const int* f_ids, const int* f_rec, double sh, double mu, double eps, double scale,
-                                 const double* lam_dof, double* gz);
+                                 const double* lam_dof, acc_t* gz);
 void launch_friction(cudaStream_t, const DevScene&, const double* xv, const double* xv_t, int n, const int* f_ids,
                      const double* f_w, const double* f_n, const double* f_lam, double mu, double eps, double scale,
-                     int mode, double* g, double* f_Hu, double* Dc, const double* pD, double* gdir, double* E);
+                     int mode, acc_t* g, double* f_Hu, acc_t* Dc, const double* pD, acc_t* gdir, acc_t* E);
+
+// order.cu: canonical order of atomically appended lists (stable LSD radix sort of 64-bit keys with an
+// index payload; the length min(*n_dev, cap) is read on the device)
+struct OrderWork {
+  unsigned long long *keys = nullptr, *keys_tmp = nullptr;  // (cap)
+  int *idx = nullptr, *idx_tmp = nullptr;                   // (cap)
+  int* hist = nullptr;                                      // sort_hist_ints(cap)
+  int* tiles = nullptr;                                     // scan_tile_ints(sort_hist_ints(cap))
+  int* rec_tmp = nullptr;                                   // (cap, 8)
+  double* s_tmp = nullptr;                                  // (cap)
+  int cap = 0;
+};
+size_t sort_hist_ints(int cap);
+void launch_sort_u64(cudaStream_t, const int* n_dev, int cap, int key_bits, unsigned long long* keys, int* idx,
+                     unsigned long long* keys_tmp, int* idx_tmp, int* hist, int* scan_tiles);
+// contact pairs (and their squared distances, may be null) into (kind, a, b) order; prim_bits >= the bits of
+// every primitive id
+void launch_sort_pairs(cudaStream_t, const int* n_dev, int cap, int prim_bits, int* rec, double* rec_s,
+                       const OrderWork& W);
 
 // cull.cu
 void launch_cull_brute(cudaStream_t, const DevScene&, const double* xv, double sh, int* rec, double* rec_s, int* count,
@@ -244,9 +267,14 @@ void launch_filter_active(cudaStream_t, int grid, const DevScene&, const double*
 void launch_theta_grad(cudaStream_t, const DevScene&, const double* xv, const double* lam, double scale, double* out);
 void launch_mass_apply(cudaStream_t, const DevScene&, const double* lam, double dt, double* y, double* yd);
 void launch_friction_apply(cudaStream_t, const DevScene&, int n, const int* f_ids, const double* f_w, const double* f_Hu,
-                           const double* lam, double* y);
-void launch_dot(cudaStream_t, int n, const double* a, const double* b, double* out);
+                           const double* lam, acc_t* y);
+// out: an accumulator (three words)
+void launch_dot(cudaStream_t, int n, const double* a, const double* b, acc_t* out);
 void launch_axpy(cudaStream_t, int n, const double* x, double alpha, const double* y, double* out);
+
+// exclusive scan of n ints in place (tiles: scan_tile_ints(n) ints of scratch)
+size_t scan_tile_ints(size_t n);
+void launch_scan_exclusive(cudaStream_t, int n, int* a, int* tiles);
 
 // pcg.cu
 void launch_dinv(cudaStream_t, int n_nodes, const int* diag, const double* val, const double* Dc, double* Dinv);
@@ -276,10 +304,19 @@ void launch_layout(cudaStream_t, int n_seg, const int* seg, const int* row, cons
 void launch_incidence(cudaStream_t, const DevScene& S, const int* rec, const int* n_pairs, int cap, int n_fric,
                       const int* f_ids, const double* f_w, int* inc_ptr, int* cursor, int* tiles, int2* inc,
                       long long inc_cap, PairDesc* desc, int* err);
+// Work of the per-body coupling lists' order, sized for 4 (pair capacity + friction pairs) chunk slots.
+struct AbdChunks {
+  unsigned long long *keys = nullptr, *keys_tmp = nullptr;
+  int *idx = nullptr, *idx_tmp = nullptr, *hist = nullptr, *tiles = nullptr;
+  int *size = nullptr, *scan = nullptr, *pos = nullptr;
+  int* n = nullptr;        // chunk slots of the current lists (device)
+  int pair_bits = 1, key_bits = 1;
+  int cap = 0;
+};
 void launch_abd_contact(cudaStream_t, const DevScene& S, const int* rec, const int* n_pairs, int cap,
                         const double* pairH, int n_fric, const int* f_ids, const double* f_w, const double* f_Hu,
-                        int* abd_ptr, int* cursor, int* ent, double* entv, long long ent_cap, double* Hval,
-                        double* Dc, int* err);
+                        int* abd_ptr, const AbdChunks& C, int* ent, double* entv, long long ent_cap, acc_t* Hval,
+                        acc_t* Dc, int* err);
 void launch_to_float(cudaStream_t, size_t n, const double* src, float* dst, const int* n_dev = nullptr, int stride = 0);
 
 // coarse.cu: layout of the coarse level for a plan, and its build (aggregate centres, Galerkin matrix
@@ -288,7 +325,8 @@ void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L);
 cudaError_t launch_coarse_build(cudaStream_t, const DevScene& S, const CoarseDevLayout& D, const int* seg,
                                 const double* x, const double* val, const int* rec, const int* n_pairs, int cap,
                                 const double* pairH, int n_fric, const int* f_ids, const double* f_w,
-                                const double* f_Hu, double* Ac, double* centre, double* rot, double* gj_buf, int* status);
+                                const double* f_Hu, double* Ac, acc_t* Ac_acc, double* centre, double* rot,
+                                double* gj_buf, int* status);
 
 // conservative-advancement iterations per CCD candidate
 constexpr int ACCD_MAX_ITER = 10000;

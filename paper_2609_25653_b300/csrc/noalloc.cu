@@ -57,12 +57,13 @@ extern "C" ipc_status sim_eval_barrier_noalloc(ipcsim* sim, const double* x_dev,
   if (s) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nk = S->nk > 0 ? S->nk : 1;
-  // layout: [count (one double slot) | Dc (n_nodes, 9) | gdir (n_nodes, 3) | pD (nk, 3)]
-  const size_t need = 1 + 9 * (size_t)S->n_nodes + 3 * (size_t)S->n_nodes + 3 * nk;
+  // layout in 8-byte slots: [count | E (3) | Dc (n_nodes, 9, 3) | gdir (n_nodes, 3, 3) | grad (n_nodes, 3, 3) |
+  // pD (nk, 3)]; the sums are order-independent accumulators of three words per value
+  const size_t need = 4 + (27 + 9 + 9) * (size_t)S->n_nodes + 3 * nk;
   if (need > kNoallocScratchDoubles) {
     *err = "sim_eval_barrier_noalloc: this scene needs " + std::to_string(need) +
-           " scratch doubles, more than the " + std::to_string(kNoallocScratchDoubles) +
-           " of the static buffer (at most about " + std::to_string((kNoallocScratchDoubles - 4) / 12) +
+           " scratch slots, more than the " + std::to_string(kNoallocScratchDoubles) +
+           " of the static buffer (at most about " + std::to_string((kNoallocScratchDoubles - 8) / 48) +
            " nodes); use sim_eval_barrier";
     return IPC_ERR_ARG;
   }
@@ -73,22 +74,24 @@ extern "C" ipc_status sim_eval_barrier_noalloc(ipcsim* sim, const double* x_dev,
     return IPC_ERR_CUDA;
   }
   int* n_dev = reinterpret_cast<int*>(base);
-  double* Dc = base + 1;
-  double* gdir = Dc + 9 * (size_t)S->n_nodes;
-  double* pD = gdir + 3 * (size_t)S->n_nodes;
+  ipc::acc_t* Eacc = reinterpret_cast<ipc::acc_t*>(base + 1);
+  ipc::acc_t* Dc = Eacc + 3;
+  ipc::acc_t* gdir = Dc + 27 * (size_t)S->n_nodes;
+  ipc::acc_t* gacc = gdir + 9 * (size_t)S->n_nodes;
+  double* pD = reinterpret_cast<double*>(gacc + 9 * (size_t)S->n_nodes);
   // the array keeps the previous call's contents: clear what is accumulated into
   int n_host = n;
   ce = cudaMemcpyAsync(n_dev, &n_host, sizeof(int), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(base + 1, 0, sizeof(double) * (need - 1), st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(E_dev, 0, sizeof(double), st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(grad_dev, 0, sizeof(double) * 3 * (size_t)S->n_nodes, st);
   if (ce != cudaSuccess) {
     *err = std::string("sim_eval_barrier_noalloc: ") + cudaGetErrorString(ce);
     return IPC_ERR_CUDA;
   }
   // mode 2 (gradient and Hessian) launches one warp per pair and sizes that grid itself
-  ipc::launch_barrier(st, 1, *S, x_dev, rec_dev, n_dev, n, sh, kappa, 1.0, 2, project, grad_dev, H_dev, Dc, pD, gdir,
-                      E_dev, nullptr);
+  ipc::launch_barrier(st, 1, *S, x_dev, rec_dev, n_dev, n, sh, kappa, 1.0, 2, project, gacc, H_dev, Dc, pD, gdir, Eacc,
+                      nullptr);
+  ipc::launch_acc_finalize(st, 3 * (size_t)S->n_nodes, gacc, nullptr, grad_dev);
+  ipc::launch_acc_finalize(st, 1, Eacc, nullptr, E_dev);
   ce = cudaStreamSynchronize(st);
   if (ce == cudaSuccess) ce = cudaGetLastError();
   if (ce != cudaSuccess) {

@@ -172,6 +172,35 @@ __global__ void k_scan_add(int n, int* __restrict__ a, const int* __restrict__ t
   if (i < n) a[i] += tiles[i / SCAN_TILE];
 }
 
+// Every owner's incidences in increasing code (pair, then friction flag, then slot) order: the fill
+// appends them in the order its threads reach the cursor.  Lists are short (the contacts of one node).
+__global__ void k_sort_incidence(int n_own, const int* __restrict__ inc_ptr, long long inc_cap,
+                                 int2* __restrict__ inc) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_own) return;
+  const long long b = inc_ptr[o], e = min((long long)inc_ptr[o + 1], inc_cap);
+  for (long long i = b + 1; i < e; ++i) {
+    const int2 x = inc[i];
+    long long j = i - 1;
+    while (j >= b && inc[j].x > x.x) {
+      inc[j + 1] = inc[j];
+      --j;
+    }
+    inc[j + 1] = x;
+  }
+}
+
+size_t scan_tile_ints(size_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+void launch_scan_exclusive(cudaStream_t st, int n, int* a, int* tiles) {
+  if (n <= 0) return;
+  const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<ntiles, 1024, 0, st>>>(n, a, tiles);
+  k_scan_totals<<<1, 1024, 0, st>>>(ntiles, tiles);
+  k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(n, a, tiles);
+  count_launch(3);
+}
+
 void launch_incidence(cudaStream_t st, const DevScene& S, const int* rec, const int* n_pairs, int cap, int n_fric,
                       const int* f_ids, const double* f_w, int* inc_ptr, int* cursor, int* tiles, int2* inc,
                       long long inc_cap, PairDesc* desc, int* err) {
@@ -186,7 +215,8 @@ void launch_incidence(cudaStream_t st, const DevScene& S, const int* rec, const 
   k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(n, inc_ptr, tiles);
   cudaMemcpyAsync(cursor, inc_ptr, sizeof(int) * n_own, cudaMemcpyDeviceToDevice, st);
   k_incidence<true><<<grid, 256, 0, st>>>(S, rec, n_pairs, cap, n_fric, f_ids, f_w, cursor, inc, inc_cap, desc, err);
-  for (int k = 0; k < 5; ++k) count_launch();
+  k_sort_incidence<<<(n_own + 127) / 128, 128, 0, st>>>(n_own, inc_ptr, inc_cap, inc);
+  for (int k = 0; k < 6; ++k) count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -240,13 +270,17 @@ __device__ inline void pair_block(const double* H, const double* fw, const doubl
   }
 }
 
+// The list of a body is the concatenation of its chunks (the entries one pair adds for that body) in
+// (pair, first slot) order: the counting pass writes every chunk's key (body, pair, slot) and size, the
+// keys are sorted, and the scan of the sizes in sorted order gives every chunk its position.
 template <bool FILL>
 __global__ void k_abd_contact(DevScene S, const int* __restrict__ rec, const int* __restrict__ n_pairs, int cap,
                               const double* __restrict__ pairH, int n_fric, const int* __restrict__ f_ids,
-                              const double* __restrict__ f_w, const double* __restrict__ f_Hu,
-                              int* __restrict__ cnt_or_cursor, int* __restrict__ ent, double* __restrict__ entv,
-                              long long ent_cap, double* __restrict__ Hval, int* __restrict__ err) {
+                              const double* __restrict__ f_w, const double* __restrict__ f_Hu, int* __restrict__ cnt,
+                              AbdChunks C, int* __restrict__ ent, double* __restrict__ entv, long long ent_cap,
+                              acc_t* __restrict__ Hval, int* __restrict__ err) {
   const int np = min(*n_pairs, cap);
+  if (!FILL && blockIdx.x == 0 && threadIdx.x == 0) *C.n = 4 * (np + n_fric);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np + n_fric; e += gridDim.x * blockDim.x) {
     const bool fric = e >= np;
     const int k = fric ? e - np : e;
@@ -258,6 +292,12 @@ __global__ void k_abd_contact(DevScene S, const int* __restrict__ rec, const int
     pair_slots(S, ids, fw, P);
     for (int q0 = 0; q0 < 4; ++q0) {
       const int b = P.body[q0];
+      const int chunk = 4 * e + q0;
+      if (!FILL) {
+        C.keys[chunk] = ~0ull;  // no chunk: sorted behind every body's chunks
+        C.idx[chunk] = chunk;
+        C.size[chunk] = 0;
+      }
       if (b < 0) continue;
       bool first = true;
       for (int q = 0; q < q0; ++q) first = first && P.body[q] != b;
@@ -273,7 +313,11 @@ __global__ void k_abd_contact(DevScene S, const int* __restrict__ rec, const int
         }
       }
       if (!FILL) {
-        if (count) atomicAdd(cnt_or_cursor + b, count);
+        if (count) {
+          atomicAdd(cnt + b, count);
+          C.keys[chunk] = ((unsigned long long)b << (C.pair_bits + 2)) | ((unsigned long long)e << 2) | q0;
+          C.size[chunk] = count;
+        }
         continue;
       }
       double B[9];
@@ -290,11 +334,11 @@ __global__ void k_abd_contact(DevScene S, const int* __restrict__ rec, const int
               for (int i = 0; i < 9; ++i) acc[i] += ww * B[i];
             }
           }
-          double* dst = Hval + 9 * (size_t)S.abd_blk[16 * b + 4 * t + u];
-          for (int i = 0; i < 9; ++i) atomicAdd(dst + i, acc[i]);
+          acc_t* dst = Hval + 27 * (size_t)S.abd_blk[16 * b + 4 * t + u];
+          for (int i = 0; i < 9; ++i) acc_add(dst + 3 * i, acc[i], S.err);
         }
       if (!count) continue;
-      int pos = atomicAdd(cnt_or_cursor + b, count);
+      int pos = C.pos[chunk];
       if (pos < 0 || pos + count > ent_cap) { atomicOr(err, ERRF_ABD); continue; }
       for (int j = 0; j < 4; ++j) {
         if (P.kind[j] == VK_FEM) {
@@ -336,22 +380,37 @@ __global__ void k_abd_contact(DevScene S, const int* __restrict__ rec, const int
   }
 }
 
+// positions of the sorted chunks: scan[i] = size of sorted chunk i (0 past the count), then pos[chunk] = scan
+__global__ void k_chunk_sizes(AbdChunks C, int bound) {
+  const int n = *C.n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += gridDim.x * blockDim.x)
+    C.scan[i] = i < n ? C.size[C.idx[i]] : 0;
+}
+__global__ void k_chunk_pos(AbdChunks C) {
+  const int n = *C.n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) C.pos[C.idx[i]] = C.scan[i];
+}
+
 void launch_abd_contact(cudaStream_t st, const DevScene& S, const int* rec, const int* n_pairs, int cap,
                         const double* pairH, int n_fric, const int* f_ids, const double* f_w, const double* f_Hu,
-                        int* abd_ptr, int* cursor, int* ent, double* entv, long long ent_cap, double* Hval,
-                        double* Dc, int* err) {
+                        int* abd_ptr, const AbdChunks& C, int* ent, double* entv, long long ent_cap, acc_t* Hval,
+                        acc_t* Dc, int* err) {
   if (S.nab == 0) return;
   // the diagonal contact blocks of the pseudo-nodes go into the BSR grid with the rest of the same-body part
-  cudaMemsetAsync(Dc + 9 * (size_t)S.nf, 0, sizeof(double) * 36 * (size_t)S.nab, st);
+  cudaMemsetAsync(Dc + 27 * (size_t)S.nf, 0, sizeof(acc_t) * 108 * (size_t)S.nab, st);
   cudaMemsetAsync(abd_ptr, 0, sizeof(int) * (S.nab + 1), st);
-  int grid = stride_grid((long long)cap + n_fric, 128, 8);
-  k_abd_contact<false><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, abd_ptr,
+  const int bound = 4 * (cap + n_fric);  // chunk slots of the largest list this launch can see
+  const int grid = stride_grid((long long)cap + n_fric, 128, 8);
+  k_abd_contact<false><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, abd_ptr, C,
                                              nullptr, nullptr, 0, nullptr, err);
   k_scan_totals<<<1, 1024, 0, st>>>(S.nab + 1, abd_ptr);
-  cudaMemcpyAsync(cursor, abd_ptr, sizeof(int) * S.nab, cudaMemcpyDeviceToDevice, st);
-  k_abd_contact<true><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, cursor, ent,
+  launch_sort_u64(st, C.n, bound, C.key_bits, C.keys, C.idx, C.keys_tmp, C.idx_tmp, C.hist, C.tiles);
+  k_chunk_sizes<<<stride_grid(bound, 256, 8), 256, 0, st>>>(C, bound);
+  launch_scan_exclusive(st, bound, C.scan, C.tiles);
+  k_chunk_pos<<<stride_grid(bound, 256, 8), 256, 0, st>>>(C);
+  k_abd_contact<true><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, nullptr, C, ent,
                                             entv, ent_cap, Hval, err);
-  count_launch(3);
+  count_launch(5);
 }
 
 // ---------------------------------------------------------------------------
@@ -706,12 +765,18 @@ __device__ inline void report_solve(const PcgArgs& a, Shared& sh, bool decider, 
 // ---------------------------------------------------------------------------
 // FEM segment [r0, r1): acc[3 (i - r0) + c].  The contact incidences of the
 // segment (a contiguous range of the owner-ordered incidence list) are spread
-// over all threads and added with shared-memory atomics; the BSR part of a
-// row is formed by a group of ROWG threads.  Every thread must call it.
+// over all threads, one chunk of blockDim at a time; within a chunk the
+// pieces of one owner's run (split at warp boundaries) are added in thread
+// order by the thread holding its last piece, so that every sum is formed in
+// the same order in every run.  The BSR part of a row is formed by a group of
+// ROWG threads.  Every thread must call it.
 template <typename M, typename V, typename A, int ROWG>
 __device__ inline void fem_products(const PcgArgs& a, int r0, int r1, int k0, OpView<M> op, const int* colp,
                                     const int* rowp /* relative to k0, indexed from r0; null: global row */,
-                                    const M* pairH, const M* fHu, const V* v, A* acc) {
+                                    const M* pairH, const M* fHu, const V* v, A* acc, Shared& sh) {
+  // chunk scratch: per-thread run-end pieces (3 values) and the owner of every thread's incidence
+  A (*piece)[PCG_THREADS_MAX] = reinterpret_cast<A (*)[PCG_THREADS_MAX]>(&sh.vals[0][0]);
+  int* owner_of_t = reinterpret_cast<int*>(&sh.vals[3][0]);
   for (int j = threadIdx.x; j < 3 * (r1 - r0); j += blockDim.x) acc[j] = A(0);
   __syncthreads();
   // incidences e of the segment, consecutive per lane; their owners are non-decreasing, so the
@@ -737,14 +802,26 @@ __device__ inline void fem_products(const PcgArgs& a, int r0, int r1, int k0, Op
       if (lane >= o && ow == own) { y0 += t0; y1 += t1; y2 += t2; }
     }
     const int next = __shfl_down_sync(0xffffffffu, own, 1);
-    if (own >= 0 && (lane == 31 || next != own)) {
+    const bool end = own >= 0 && (lane == 31 || next != own);
+    piece[0][threadIdx.x] = y0;
+    piece[1][threadIdx.x] = y1;
+    piece[2][threadIdx.x] = y2;
+    owner_of_t[threadIdx.x] = own;
+    __syncthreads();
+    // the owner's last piece in this chunk: its run does not continue at the next thread
+    if (end && !(threadIdx.x + 1 < blockDim.x && owner_of_t[threadIdx.x + 1] == own)) {
+      int t0 = threadIdx.x;
+      while (t0 > 0 && owner_of_t[t0 - 1] == own) --t0;
+      A s0 = A(0), s1 = A(0), s2 = A(0);
+      for (int t = t0 | 31; t < (int)threadIdx.x; t += 32) {  // earlier pieces end at lane 31 of their warps
+        s0 += piece[0][t]; s1 += piece[1][t]; s2 += piece[2][t];
+      }
+      s0 += y0; s1 += y1; s2 += y2;
       A* t = acc + 3 * (own - r0);
-      atomicAdd(t, y0);
-      atomicAdd(t + 1, y1);
-      atomicAdd(t + 2, y2);
+      t[0] += s0; t[1] += s1; t[2] += s2;
     }
+    __syncthreads();
   }
-  __syncthreads();
   const int groups = blockDim.x / ROWG, g = threadIdx.x / ROWG, gl = threadIdx.x & (ROWG - 1);
   for (int base = r0; base < r1; base += groups) {
     const int i = base + g;
@@ -933,7 +1010,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
     using MM = decltype(mtag);
     if (fem_cta) {
       fem_products<MM, double, double, ROWG>(a, r0, r1, k0, op_view_fem, colp_fem, rowp_fem, mat_pairH, mat_fHu,
-                                             vin, acc);
+                                             vin, acc, sh);
     } else {
       for (int b = ab0, j = 0; b < ab1; ++b, ++j) {
         const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
@@ -1333,7 +1410,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   // FP32 products of the iteration operator, FP64 products of the assembled one
   auto products32 = [&](const F* vin) {
     if (fem_cta) {
-      fem_products<F, F, F, ROWG>(a, r0, r1, k0, op, colp, rowp, pairH, fHu, vin, accf);
+      fem_products<F, F, F, ROWG>(a, r0, r1, k0, op, colp, rowp, pairH, fHu, vin, accf, sh);
     } else {
       for (int b = ab0, j = 0; b < ab1; ++b, ++j) {
         const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;
@@ -1345,7 +1422,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   auto products64 = [&](const double* vin) {
     if (fem_cta) {
       fem_products<double, double, double, ROWG>(a, r0, r1, k0, OpView<double>{a.val64 + 9 * (size_t)k0, 1, 9},
-                                                 a.col + k0, nullptr, a.pairH64, a.fHu64, vin, acc);
+                                                 a.col + k0, nullptr, a.pairH64, a.fHu64, vin, acc, sh);
     } else {
       for (int b = ab0, j = 0; b < ab1; ++b, ++j) {
         const int rr = nf + 4 * b, kb0 = a.row[rr], nl = a.row[rr + 4] - kb0;

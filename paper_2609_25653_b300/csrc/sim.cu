@@ -62,6 +62,13 @@ struct ipcsim {
   double *xv = nullptr, *xv_t = nullptr, *xv_trial = nullptr, *z_trial = nullptr, *xk_trial = nullptr;
   double *g = nullptr, *gdir = nullptr, *rhs = nullptr, *p = nullptr, *pD = nullptr, *pv = nullptr;
   double *Hconst = nullptr, *Hval = nullptr, *Dc = nullptr, *Dinv = nullptr;
+  // order-independent accumulators of one assembly: gradient, BSR values, preconditioner diagonal,
+  // Dirichlet term, adjoint gradient (three words per value)
+  acc_t *g_acc = nullptr, *H_acc = nullptr, *Dc_acc = nullptr, *gdir_acc = nullptr, *gz_acc = nullptr;
+  // canonical pair order: sort buffers (up to ow.cap pairs) and the bits of the largest primitive id
+  OrderWork ow;
+  int prim_bits = 1;
+  AbdChunks abd_ch;  // order of the per-body ABD coupling lists
   double *y = nullptr, *partial = nullptr;
   double* T_dev = nullptr;
   // PCG: operator in the CTA-major layout (iteration type), nine iteration vectors, row partition
@@ -113,7 +120,8 @@ struct ipcsim {
   // scalars (device) and pinned host mirror
   struct Scal {
     // cleared at the start of every Newton iteration
-    double E[8];                 // inertia, elastic, barrier, friction, stitch, abd, joints (adjoint scratch: 6, 7)
+    acc_t E[24];                 // 8 accumulators: inertia, elastic, barrier, friction, stitch, abd, joints
+                                 // (adjoint scratch: 6, 7)
     unsigned long long pn[2];    // max|p_F|, max|p_D|
     int n_ccd;
     int pcg_out[3];
@@ -131,7 +139,9 @@ struct ipcsim {
   Scal* sc_host = nullptr;
   int pcg_grid_max = 1;
   // per-scene Newton control of a batch (n_scenes > 1): device accumulators and pinned host mirrors
-  double* E_sc_dev = nullptr;
+  acc_t* E_sc_dev = nullptr;    // (n_scenes, 8) accumulators
+  double E_h[8] = {0};          // the accumulators of sc_host->E as doubles (sync_scalars)
+  std::vector<double> E_sc_v;   // (n_scenes, 8) the same per scene
   // joint drive targets (b-side vectors, offsets), rewritten by sim_set_joint_targets
   int nj = 0;
   double* jt_vb = nullptr;
@@ -139,7 +149,7 @@ struct ipcsim {
   unsigned long long* alpha_sc_dev = nullptr;
   unsigned long long* pn_sc_dev = nullptr;
   double* alpha_trial_dev = nullptr;
-  double* E_sc_h = nullptr;
+  acc_t* E_sc_h = nullptr;
   unsigned long long* alpha_sc_h = nullptr;
   unsigned long long* pn_sc_h = nullptr;
   // PCG launch shape: threads per FEM row and CTAs per SM
@@ -177,6 +187,7 @@ struct ipcsim {
   int* co_status = nullptr;
   long long *co_off = nullptr, *co_boff = nullptr;
   double *co_Ac = nullptr, *co_centre = nullptr, *co_x = nullptr, *co_part = nullptr, *co_gj = nullptr;
+  acc_t* co_Ac_acc = nullptr;
   float* co_Ac32 = nullptr;
   long long co_cap = 0, co_cap_n = 0;
   int co_cap_agg = 0, co_cap_solves = 0;
@@ -306,6 +317,24 @@ ipc_status grow_abd_list(ipcsim* sim, long long need) {
   return IPC_OK;
 }
 
+// Sort buffers for pair lists of up to cap entries.
+ipc_status grow_order(ipcsim* sim, int cap) {
+  OrderWork& W = sim->ow;
+  if (cap <= W.cap) return IPC_OK;
+  dfree(sim, W.keys); dfree(sim, W.keys_tmp); dfree(sim, W.idx); dfree(sim, W.idx_tmp); dfree(sim, W.hist);
+  dfree(sim, W.tiles); dfree(sim, W.rec_tmp); dfree(sim, W.s_tmp);
+  W = OrderWork{};
+  ipc_status s;
+  const size_t nh = sort_hist_ints(cap);
+  if ((s = dalloc(sim, &W.keys, (size_t)cap)) || (s = dalloc(sim, &W.keys_tmp, (size_t)cap)) ||
+      (s = dalloc(sim, &W.idx, (size_t)cap)) || (s = dalloc(sim, &W.idx_tmp, (size_t)cap)) ||
+      (s = dalloc(sim, &W.hist, nh)) || (s = dalloc(sim, &W.tiles, scan_tile_ints(nh))) ||
+      (s = dalloc(sim, &W.rec_tmp, 8 * (size_t)cap)) || (s = dalloc(sim, &W.s_tmp, (size_t)cap)))
+    return s;
+  W.cap = cap;
+  return IPC_OK;
+}
+
 ipc_status grow_pairs(ipcsim* sim, int need) {
   const long long lim = max_pairs(sim);
   if (need < 0 || need > lim) {
@@ -327,6 +356,7 @@ ipc_status grow_pairs(ipcsim* sim, int need) {
     if ((s = dalloc(sim, &sim->pairH32, (size_t)144 * ncap))) return s;
   }
   sim->cap = ncap;
+  if ((s = grow_order(sim, ncap))) return s;
   return grow_inc(sim);
 }
 
@@ -489,9 +519,10 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
     if (!L.consecutive || L.total <= 0) return IPC_OK;
     ipc_status s;
     if (L.total > sim->co_cap) {
-      dfree(sim, sim->co_Ac); dfree(sim, sim->co_Ac32);
-      sim->co_Ac = nullptr; sim->co_Ac32 = nullptr;
+      dfree(sim, sim->co_Ac); dfree(sim, sim->co_Ac32); dfree(sim, sim->co_Ac_acc);
+      sim->co_Ac = nullptr; sim->co_Ac32 = nullptr; sim->co_Ac_acc = nullptr;
       if ((s = dalloc(sim, &sim->co_Ac, (size_t)L.total))) return s;
+      if ((s = dalloc(sim, &sim->co_Ac_acc, 3 * (size_t)L.total))) return s;
       if ((s = dalloc(sim, &sim->co_Ac32, (size_t)L.total))) return s;
       sim->co_cap = L.total;
     }
@@ -554,7 +585,7 @@ ipc_status coarse_setup(ipcsim* sim, int fp32, int n_fric) {
   D.solve_n = sim->co_solve_n; D.off = sim->co_off; D.boff = sim->co_boff; D.agg_cta = sim->co_agg_cta;
   CUDA_TRY(launch_coarse_build(cs, sim->S, D, sim->d_seg, sim->co_x, sim->Hval, sim->rec, &sim->sc_dev->n_pairs,
                                sim->cap, sim->pairH, n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->co_Ac,
-                               sim->co_centre, sim->co_rot, sim->co_gj, sim->co_status));
+                               sim->co_Ac_acc, sim->co_centre, sim->co_rot, sim->co_gj, sim->co_status));
   sim->co_status_h.assign(L.n_solves, 0);
   CUDA_TRY(cudaMemcpyAsync(sim->co_status_h.data(), sim->co_status, sizeof(int) * L.n_solves, cudaMemcpyDeviceToHost,
                            cs));
@@ -687,12 +718,43 @@ ipc_status pcg_launch(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fr
   return IPC_OK;
 }
 
+// Chunk-order buffers of the ABD coupling lists for 4 (cap + n_fric) chunk slots.
+ipc_status grow_abd_chunks(ipcsim* sim, int n_fric) {
+  AbdChunks& C = sim->abd_ch;
+  const long long need = 4LL * ((long long)sim->cap + n_fric);
+  if (need <= C.cap) return IPC_OK;
+  if (need > (1LL << 30)) { sim->err = "ABD coupling chunk count exceeds 2^30"; return IPC_ERR_CAPACITY; }
+  for (void* p : {(void*)C.keys, (void*)C.keys_tmp, (void*)C.idx, (void*)C.idx_tmp, (void*)C.hist, (void*)C.tiles,
+                  (void*)C.size, (void*)C.scan, (void*)C.pos, (void*)C.n})
+    dfree(sim, p);
+  C = AbdChunks{};
+  const int cap = (int)std::min<long long>(need + need / 2, 1LL << 30);
+  const size_t nh = sort_hist_ints(cap);
+  ipc_status s;
+  if ((s = dalloc(sim, &C.keys, (size_t)cap)) || (s = dalloc(sim, &C.keys_tmp, (size_t)cap)) ||
+      (s = dalloc(sim, &C.idx, (size_t)cap)) || (s = dalloc(sim, &C.idx_tmp, (size_t)cap)) ||
+      (s = dalloc(sim, &C.hist, nh)) || (s = dalloc(sim, &C.tiles, std::max(scan_tile_ints(nh), scan_tile_ints(cap)))) ||
+      (s = dalloc(sim, &C.size, (size_t)cap)) || (s = dalloc(sim, &C.scan, (size_t)cap)) ||
+      (s = dalloc(sim, &C.pos, (size_t)cap)) || (s = dalloc(sim, &C.n, 1)))
+    return s;
+  C.cap = cap;
+  C.pair_bits = 1;
+  while ((1LL << C.pair_bits) <= cap / 4) ++C.pair_bits;
+  int body_bits = 1;
+  while ((1LL << body_bits) <= sim->nab) ++body_bits;
+  C.key_bits = body_bits + C.pair_bits + 2;
+  return IPC_OK;
+}
+
 // ABD contact: same-body blocks into the BSR grid, coupling blocks into the per-body lists.
-void build_abd_contact(ipcsim* sim, int n_fric) {
-  if (!sim->nab) return;
+ipc_status build_abd_contact(ipcsim* sim, int n_fric) {
+  if (!sim->nab) return IPC_OK;
+  ipc_status s = grow_abd_chunks(sim, n_fric);
+  if (s) return s;
   launch_abd_contact(sim->st, sim->S, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->pairH, n_fric, sim->f_ids,
-                     sim->f_w, sim->f_Hu, sim->abd_ptr, sim->abd_cursor, sim->abd_ent, sim->abd_val, sim->abd_cap,
-                     sim->Hval, sim->Dc, &sim->sc_dev->flags);
+                     sim->f_w, sim->f_Hu, sim->abd_ptr, sim->abd_ch, sim->abd_ent, sim->abd_val, sim->abd_cap,
+                     sim->H_acc, sim->Dc_acc, &sim->sc_dev->flags);
+  return IPC_OK;
 }
 
 // Contact incidences of the current pairs (and friction pairs) per owner.
@@ -715,6 +777,8 @@ void cull_into(ipcsim* sim, const double* xv, int* rec, double* rec_s, int cap) 
   else
     launch_cull_bvh(sim->st, sim->S, xv, sim->sh, sim->bvh_pad, sim->tri_tree, sim->edge_tree, rec, rec_s,
                     &sim->sc_dev->n_pairs, cap, &sim->sc_dev->flags);
+  // canonical (kind, a, b) order (the sort buffers cover cap: grown with the pair buffer, or by the caller)
+  launch_sort_pairs(sim->st, &sim->sc_dev->n_pairs, std::min(cap, sim->ow.cap), sim->prim_bits, rec, rec_s, sim->ow);
 }
 void cull(ipcsim* sim, const double* xv) { cull_into(sim, xv, sim->rec, sim->rec_s, sim->cap); }
 
@@ -725,9 +789,29 @@ void active_set(ipcsim* sim, const double* xv) {
     launch_filter_active(sim->st, stride_grid(sim->ccap, 128, 8), sim->S, xv, sim->sh,
                          sim->cand, &sim->sc_dev->n_cand, sim->ccap, sim->rec, sim->rec_s, &sim->sc_dev->n_pairs,
                          sim->cap);
+    launch_sort_pairs(sim->st, &sim->sc_dev->n_pairs, sim->cap, sim->prim_bits, sim->rec, sim->rec_s, sim->ow);
   } else {
     cull(sim, xv);
   }
+}
+
+// Clear the accumulators of one assembly (gradient, BSR values, preconditioner diagonal, Dirichlet term).
+ipc_status assembly_begin(ipcsim* sim) {
+  const size_t ndof = 3 * (size_t)sim->n_nodes;
+  CUDA_TRY(cudaMemsetAsync(sim->g_acc, 0, sizeof(acc_t) * 3 * ndof, sim->st));
+  CUDA_TRY(cudaMemsetAsync(sim->H_acc, 0, sizeof(acc_t) * 27 * (size_t)sim->nnzb, sim->st));
+  CUDA_TRY(cudaMemsetAsync(sim->Dc_acc, 0, sizeof(acc_t) * 27 * (size_t)sim->n_nodes, sim->st));
+  CUDA_TRY(cudaMemsetAsync(sim->gdir_acc, 0, sizeof(acc_t) * 3 * ndof, sim->st));
+  return IPC_OK;
+}
+
+// The assembled values: g, Hval = Hconst + the accumulated Hessian terms, Dc, gdir.
+void assembly_end(ipcsim* sim) {
+  const size_t ndof = 3 * (size_t)sim->n_nodes;
+  launch_acc_finalize(sim->st, ndof, sim->g_acc, nullptr, sim->g);
+  launch_acc_finalize(sim->st, 9 * (size_t)sim->nnzb, sim->H_acc, sim->Hconst, sim->Hval);
+  launch_acc_finalize(sim->st, 9 * (size_t)sim->n_nodes, sim->Dc_acc, nullptr, sim->Dc);
+  launch_acc_finalize(sim->st, ndof, sim->gdir_acc, nullptr, sim->gdir);
 }
 
 // Clear the per-iteration scalars and set the CCD bound and minimum distance to their neutral values.
@@ -737,7 +821,7 @@ ipc_status reset_iteration_scalars(ipcsim* sim) {
   CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->alpha, init, sizeof(init), cudaMemcpyHostToDevice, sim->st));
   if (sim->n_scenes > 1) {
     const int ns = sim->n_scenes;
-    CUDA_TRY(cudaMemsetAsync(sim->E_sc_dev, 0, sizeof(double) * 8 * ns, sim->st));
+    CUDA_TRY(cudaMemsetAsync(sim->E_sc_dev, 0, sizeof(acc_t) * 24 * ns, sim->st));
     CUDA_TRY(cudaMemsetAsync(sim->pn_sc_dev, 0, sizeof(unsigned long long) * 2 * ns, sim->st));
     for (int k = 0; k < ns; ++k) sim->alpha_sc_h[k] = double_bits(1.0);
     CUDA_TRY(cudaMemcpyAsync(sim->alpha_sc_dev, sim->alpha_sc_h, sizeof(unsigned long long) * ns,
@@ -763,13 +847,18 @@ ipc_status sync_scalars(ipcsim* sim) {
   CUDA_TRY(cudaMemcpyAsync(sim->sc_host, sim->sc_dev, sizeof(ipcsim::Scal), cudaMemcpyDeviceToHost, sim->st));
   if (sim->n_scenes > 1) {
     const int ns = sim->n_scenes;
-    CUDA_TRY(cudaMemcpyAsync(sim->E_sc_h, sim->E_sc_dev, sizeof(double) * 8 * ns, cudaMemcpyDeviceToHost, sim->st));
+    CUDA_TRY(cudaMemcpyAsync(sim->E_sc_h, sim->E_sc_dev, sizeof(acc_t) * 24 * ns, cudaMemcpyDeviceToHost, sim->st));
     CUDA_TRY(cudaMemcpyAsync(sim->alpha_sc_h, sim->alpha_sc_dev, sizeof(unsigned long long) * ns,
                              cudaMemcpyDeviceToHost, sim->st));
     CUDA_TRY(cudaMemcpyAsync(sim->pn_sc_h, sim->pn_sc_dev, sizeof(unsigned long long) * 2 * ns,
                              cudaMemcpyDeviceToHost, sim->st));
   }
   CUDA_TRY(cudaStreamSynchronize(sim->st));
+  for (int k = 0; k < 8; ++k) sim->E_h[k] = acc_value(sim->sc_host->E + 3 * k);
+  if (sim->n_scenes > 1) {
+    sim->E_sc_v.resize(8 * (size_t)sim->n_scenes);
+    for (size_t k = 0; k < sim->E_sc_v.size(); ++k) sim->E_sc_v[k] = acc_value(sim->E_sc_h + 3 * k);
+  }
   prof_collect(sim);
   return IPC_OK;
 }
@@ -797,33 +886,34 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
   double dt2 = sim->P.dt * sim->P.dt;
   launch_vertex_positions(sim->st, S, zq, xkq, xvq);
   for (;;) {
-    CUDA_TRY(cudaMemsetAsync(sim->sc_dev->E, 0, sizeof(double) * 8, sim->st));
-    if (sim->n_scenes > 1) CUDA_TRY(cudaMemsetAsync(sim->E_sc_dev, 0, sizeof(double) * 8 * sim->n_scenes, sim->st));
+    CUDA_TRY(cudaMemsetAsync(sim->sc_dev->E, 0, sizeof(sim->sc_dev->E), sim->st));
+    if (sim->n_scenes > 1) CUDA_TRY(cudaMemsetAsync(sim->E_sc_dev, 0, sizeof(acc_t) * 24 * sim->n_scenes, sim->st));
     unsigned long long big = double_bits(1e300);
     CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->min_s, &big, sizeof(big), cudaMemcpyHostToDevice, sim->st));
     active_set(sim, xvq);
-    launch_inertia(sim->st, S, zq, sim->z_tilde, nullptr, &sim->sc_dev->E[0], 0);
-    launch_elastic(sim->st, S, xvq, dt2, 0, 0, nullptr, nullptr, nullptr, &sim->sc_dev->E[1]);
+    launch_inertia(sim->st, S, zq, sim->z_tilde, nullptr, sim->sc_dev->E + 0, 0);
+    launch_elastic(sim->st, S, xvq, dt2, 0, 0, nullptr, nullptr, nullptr, sim->sc_dev->E + 3);
     launch_barrier(sim->st, pair_grid(sim->cap), S, xvq, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
-                   sim->kappa, dt2, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, &sim->sc_dev->E[2],
+                   sim->kappa, dt2, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, sim->sc_dev->E + 6,
                    &sim->sc_dev->min_s);
     if (sim->P.mu > 0)
       launch_friction(sim->st, S, xvq, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, sim->P.mu,
                       sim->P.eps_v * sim->P.dt, dt2, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
-                      &sim->sc_dev->E[3]);
-    launch_stitch(sim->st, S, xvq, sim->stitch_hat, sim->k_c, dt2, 0, nullptr, &sim->sc_dev->E[4]);
-    launch_abd_orth(sim->st, S, zq, sim->P.kappa_A, dt2, 0, 0, nullptr, nullptr, &sim->sc_dev->E[5]);
-    launch_joints(sim->st, S, zq, dt2, 0, nullptr, nullptr, &sim->sc_dev->E[6]);
+                      sim->sc_dev->E + 9);
+    launch_stitch(sim->st, S, xvq, sim->stitch_hat, sim->k_c, dt2, 0, nullptr, sim->sc_dev->E + 12);
+    launch_abd_orth(sim->st, S, zq, sim->P.kappa_A, dt2, 0, 0, nullptr, nullptr, sim->sc_dev->E + 15);
+    launch_joints(sim->st, S, zq, dt2, 0, nullptr, nullptr, sim->sc_dev->E + 18);
     ipc_status s = sync_scalars(sim);
     if (s) return s;
     if (sim->sc_host->flags & ERRF_BVH) { sim->err = "BVH traversal stack overflow"; return IPC_ERR_BVH_OVERFLOW; }
+    if (sim->sc_host->flags & ERRF_ACC) { sim->err = "an energy term is not finite or exceeds 2^94"; return IPC_ERR_NAN; }
     if (sim->sc_host->n_pairs > sim->cap) {
       if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s;
       continue;
     }
     break;
   }
-  *E_out = total_energy(sim, sim->sc_host->E);
+  *E_out = total_energy(sim, sim->E_h);
   if (n_pairs) *n_pairs = sim->sc_host->n_pairs;
   return IPC_OK;
 }
@@ -1212,6 +1302,10 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   DevScene& S = sim->S;
   S.nf = nf; S.nt = nt; S.nab = nab; S.nkb = nkb; S.nv = nv; S.na_v = na_v; S.nk = nk; S.n_nodes = n_nodes;
   S.nsv = (int)sv.size(); S.ntri = (int)tris_all.size() / 3; S.nedge = (int)ev.size(); S.nbody = sim->nbody;
+  {
+    const int mx = std::max(std::max(nv, S.nsv), std::max(S.ntri, S.nedge));
+    while (sim->prim_bits < 31 && (1LL << sim->prim_bits) <= mx) ++sim->prim_bits;
+  }
   S.nnzb = nnzb;
   S.n_stitch = D->n_stitch;
   ipc_status s;
@@ -1290,16 +1384,16 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
       if ((s = dalloc(sim, &sim->d_pcg_sc_res, (size_t)n_scenes))) return fail(s, "");
       if (cudaMallocHost(&sim->pcg_skip_h, sizeof(int) * (size_t)n_scenes) != cudaSuccess)
         return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
-      if ((s = dalloc(sim, &sim->E_sc_dev, 8 * (size_t)n_scenes))) return fail(s, ""); S.E_sc = sim->E_sc_dev;
+      if ((s = dalloc(sim, &sim->E_sc_dev, 24 * (size_t)n_scenes))) return fail(s, ""); S.E_sc = sim->E_sc_dev;
       if ((s = dalloc(sim, &sim->alpha_sc_dev, (size_t)n_scenes))) return fail(s, ""); S.alpha_sc = sim->alpha_sc_dev;
       if ((s = dalloc(sim, &sim->pn_sc_dev, 2 * (size_t)n_scenes))) return fail(s, ""); S.pn_sc = sim->pn_sc_dev;
       if ((s = dalloc(sim, &sim->alpha_trial_dev, (size_t)n_scenes))) return fail(s, "");
       S.alpha_trial = sim->alpha_trial_dev;
       void* hb = nullptr;
-      if (cudaMallocHost(&hb, sizeof(double) * 11 * (size_t)n_scenes) != cudaSuccess)
+      if (cudaMallocHost(&hb, sizeof(acc_t) * 27 * (size_t)n_scenes) != cudaSuccess)
         return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
-      sim->E_sc_h = static_cast<double*>(hb);
-      sim->alpha_sc_h = reinterpret_cast<unsigned long long*>(sim->E_sc_h + 8 * (size_t)n_scenes);
+      sim->E_sc_h = static_cast<acc_t*>(hb);
+      sim->alpha_sc_h = sim->E_sc_h + 24 * (size_t)n_scenes;
       sim->pn_sc_h = sim->alpha_sc_h + n_scenes;
     }
   }
@@ -1336,6 +1430,11 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   if ((s = dalloc(sim, &sim->stitch_hat, 3 * (size_t)D->n_stitch))) return fail(s, "");
   if ((s = dalloc(sim, &sim->Hval, 9 * (size_t)nnzb))) return fail(s, "");
   if ((s = dalloc(sim, &sim->Dc, 9 * (size_t)n_nodes))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->H_acc, 27 * (size_t)nnzb))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->Dc_acc, 27 * (size_t)n_nodes))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->g_acc, 3 * (size_t)ndof))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->gdir_acc, 3 * (size_t)ndof))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->gz_acc, 3 * (size_t)ndof))) return fail(s, "");
   if ((s = dalloc(sim, &sim->Dinv, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->T_dev, 12 * (size_t)std::max(nkb, 1)))) return fail(s, "");
   if (P.precision != IPC_PREC_FP64 && P.precision != IPC_PREC_MIXED) return fail(IPC_ERR_ARG, "unknown precision");
@@ -1354,6 +1453,12 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     if ((s = dalloc(sim, &sim->Dinv32, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->partial, pcg_partial_doubles(sim->pcg_grid_max)))) return fail(s, "");
   if ((s = dalloc(sim, &sim->sc_dev, 1))) return fail(s, "");
+  S.err = &sim->sc_dev->flags;
+  {
+    acc_t* slots = nullptr;
+    if ((s = dalloc(sim, &slots, 3 * (size_t)E_SLOTS))) return fail(s, "");
+    S.e_slots = slots;
+  }
   if (cudaMallocHost((void**)&sim->sc_host, sizeof(ipcsim::Scal)) != cudaSuccess) return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
   std::memset(sim->sc_host, 0, sizeof(ipcsim::Scal));
   int cap0 = P.pair_capacity > 0 ? P.pair_capacity : std::max(1024, 2 * (S.nsv + S.nedge));
@@ -1618,9 +1723,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
   while (it < P.max_newton) {
     // ---- assemble gradient, Hessian and Dirichlet coupling at the current iterate
     if ((s = reset_iteration_scalars(sim))) return s;
-    CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
-    CUDA_TRY(cudaMemsetAsync(sim->gdir, 0, sizeof(double) * ndof, cs));
-    CUDA_TRY(cudaMemsetAsync(sim->Dc, 0, sizeof(double) * 9 * sim->n_nodes, cs));
+    if ((s = assembly_begin(sim))) return s;
     launch_vertex_positions(cs, S, sim->z, sim->xk, sim->xv);
     launch_sub(cs, nk3, sim->xk_hat, sim->xk, sim->pD);
     if (!rec_current) {
@@ -1628,26 +1731,28 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       cull(sim, sim->xv);
       prof_end(sim, PROF_CULL);
     }
-    launch_inertia(cs, S, sim->z, sim->z_tilde, sim->g, &sim->sc_dev->E[0], 1);
+    launch_inertia(cs, S, sim->z, sim->z_tilde, sim->g_acc, sim->sc_dev->E + 0, 1);
     prof_begin(sim, PROF_ELASTIC);
-    launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1],
+    launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g_acc, sim->H_acc, nullptr, sim->sc_dev->E + 3,
                    P.precision == IPC_PREC_MIXED);
     prof_end(sim, PROF_ELASTIC);
-    launch_stitch(cs, S, sim->xv, sim->stitch_hat, sim->k_c, dt2, 1, sim->g, &sim->sc_dev->E[4]);
-    launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g, sim->Hval, &sim->sc_dev->E[5]);
-    launch_joints(cs, S, sim->z, dt2, 2, sim->g, sim->Hval, &sim->sc_dev->E[6]);
+    launch_stitch(cs, S, sim->xv, sim->stitch_hat, sim->k_c, dt2, 1, sim->g_acc, sim->sc_dev->E + 12);
+    launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g_acc, sim->H_acc, sim->sc_dev->E + 15);
+    launch_joints(cs, S, sim->z, dt2, 2, sim->g_acc, sim->H_acc, sim->sc_dev->E + 18);
     prof_begin(sim, PROF_BARRIER);
     launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh, sim->kappa,
-                   dt2, 2, 1, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2], &sim->sc_dev->min_s,
-                   P.precision == IPC_PREC_MIXED);
+                   dt2, 2, 1, sim->g_acc, sim->pairH, sim->Dc_acc, sim->pD, sim->gdir_acc, sim->sc_dev->E + 6,
+                   &sim->sc_dev->min_s, P.precision == IPC_PREC_MIXED);
     prof_end(sim, PROF_BARRIER);
     if (P.mu > 0) {
       prof_begin(sim, PROF_FRICTION);
       launch_friction(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, P.mu,
-                      P.eps_v * dt, dt2, 2, sim->g, sim->f_Hu, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[3]);
+                      P.eps_v * dt, dt2, 2, sim->g_acc, sim->f_Hu, sim->Dc_acc, sim->pD, sim->gdir_acc,
+                      sim->sc_dev->E + 9);
       prof_end(sim, PROF_FRICTION);
     }
-    build_abd_contact(sim, P.mu > 0 ? sim->n_fric : 0);
+    if ((s = build_abd_contact(sim, P.mu > 0 ? sim->n_fric : 0))) return s;
+    assembly_end(sim);
     launch_rhs(cs, ndof, sim->g, sim->gdir, sim->rhs);
     launch_dinv(cs, sim->n_nodes, S.bsr_diag, sim->Hval, sim->Dc, sim->Dinv);
     // ---- PCG
@@ -1749,6 +1854,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
     CUDA_TRY(cudaGetLastError());
     const ipcsim::Scal& h = *sim->sc_host;
     if (h.flags & ERRF_BVH) return finish(IPC_ERR_BVH_OVERFLOW, "BVH traversal stack overflow");
+    if (h.flags & ERRF_ACC) return finish(IPC_ERR_NAN, "an energy, gradient or Hessian term is not finite or exceeds 2^94");
     if (h.flags & ERRF_INC) return finish(IPC_ERR_CUDA, "contact incidence list overflow");
     if (h.flags & ERRF_ABD) {
       // the ABD coupling list overflowed: grow it and redo this iteration
@@ -1786,7 +1892,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
     if (h.pcg_out[1] == 3) ++st.pcg_unconverged;
     st.n_pairs_max = std::max(st.n_pairs_max, h.n_pairs);
     st.n_ccd_max = std::max(st.n_ccd_max, h.n_ccd);
-    double E = total_energy(sim, h.E);
+    double E = total_energy(sim, sim->E_h);
     if (!std::isfinite(E)) return finish(IPC_ERR_NAN, "non-finite energy");
     if (h.pcg_out[1] == 2) return finish(IPC_ERR_NAN, "non-finite PCG iterate");
     if (h.pcg_out[1] == 1) return finish(IPC_ERR_PCG, "PCG breakdown (p^T A p <= 0)");
@@ -1805,7 +1911,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       std::vector<char> need_test(ns, 0);
       bool all_done = true;
       for (int k = 0; k < ns; ++k) {
-        E0[k] = total_energy(sim, sim->E_sc_h + 8 * k);
+        E0[k] = total_energy(sim, sim->E_sc_v.data() + 8 * k);
         pns[k] = bits_to_double(sim->pn_sc_h[2 * k]);
         pds[k] = bits_to_double(sim->pn_sc_h[2 * k + 1]);
         if (!scene_done[k] && pds[k] == 0.0 && pns[k] <= tol_abs) scene_done[k] = 1;
@@ -1825,7 +1931,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
         bool changed = false, pending = false;
         for (int k = 0; k < ns; ++k) {
           if (!need_test[k]) continue;
-          const double Ek = total_energy(sim, sim->E_sc_h + 8 * k);
+          const double Ek = total_energy(sim, sim->E_sc_v.data() + 8 * k);
           if (Ek <= E0[k] + 1e-13 * std::fabs(E0[k])) { need_test[k] = 0; continue; }
           al[k] *= 0.5;
           changed = true;
@@ -2051,21 +2157,19 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   launch_vertex_positions(cs, S, z_next, sim->xk_hat, sim->xv);
   for (;;) {
     CUDA_TRY(cudaMemsetAsync(sim->sc_dev, 0, sizeof(ipcsim::Scal), cs));
-    CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
-    CUDA_TRY(cudaMemsetAsync(sim->g, 0, sizeof(double) * ndof, cs));
-    CUDA_TRY(cudaMemsetAsync(sim->gdir, 0, sizeof(double) * ndof, cs));
-    CUDA_TRY(cudaMemsetAsync(sim->Dc, 0, sizeof(double) * 9 * sim->n_nodes, cs));
+    if ((s = assembly_begin(sim))) return s;
     if (nk3) CUDA_TRY(cudaMemsetAsync(sim->pD, 0, sizeof(double) * nk3, cs));
     cull(sim, sim->xv);
-    launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
-    launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g, sim->Hval, &sim->sc_dev->E[5]);
-    launch_joints(cs, S, z_next, dt2, 2, sim->g, sim->Hval, &sim->sc_dev->E[6]);
+    launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g_acc, sim->H_acc, nullptr, sim->sc_dev->E + 3);
+    launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g_acc, sim->H_acc, sim->sc_dev->E + 15);
+    launch_joints(cs, S, z_next, dt2, 2, sim->g_acc, sim->H_acc, sim->sc_dev->E + 18);
     launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
-                   sim->kappa, dt2, 2, 0, sim->g, sim->pairH, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[2],
-                   nullptr);
+                   sim->kappa, dt2, 2, 0, sim->g_acc, sim->pairH, sim->Dc_acc, sim->pD, sim->gdir_acc,
+                   sim->sc_dev->E + 6, nullptr);
     if (P.mu > 0)
       launch_friction(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, P.mu,
-                      P.eps_v * dt, dt2, 2, sim->g, sim->f_Hu, sim->Dc, sim->pD, sim->gdir, &sim->sc_dev->E[3]);
+                      P.eps_v * dt, dt2, 2, sim->g_acc, sim->f_Hu, sim->Dc_acc, sim->pD, sim->gdir_acc,
+                      sim->sc_dev->E + 9);
     if ((s = sync_scalars(sim))) return s;
     if (sim->sc_host->flags & ERRF_BVH) { sim->err = "BVH traversal stack overflow"; return IPC_ERR_BVH_OVERFLOW; }
     if (sim->sc_host->n_pairs > sim->cap) { if ((s = grow_pairs(sim, sim->sc_host->n_pairs))) return s; continue; }
@@ -2075,17 +2179,19 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     // the ABD coupling list of the unprojected Hessian (grown until it fits)
     CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), cs));
     if (tries > 0) {
-      // a retry: rebuild the BSR values without the partial contact blocks of the overflowed pass
-      CUDA_TRY(cudaMemcpyAsync(sim->Hval, sim->Hconst, sizeof(double) * 9 * sim->nnzb, cudaMemcpyDeviceToDevice, cs));
-      launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g, sim->Hval, nullptr, &sim->sc_dev->E[1]);
-      launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g, sim->Hval, &sim->sc_dev->E[5]);
-      launch_joints(cs, S, z_next, dt2, 2, sim->g, sim->Hval, &sim->sc_dev->E[6]);
+      // a retry: rebuild the BSR values without the partial contact blocks of the overflowed pass (the
+      // gradient accumulated again is not used by the adjoint)
+      CUDA_TRY(cudaMemsetAsync(sim->H_acc, 0, sizeof(acc_t) * 27 * sim->nnzb, cs));
+      launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g_acc, sim->H_acc, nullptr, sim->sc_dev->E + 3);
+      launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g_acc, sim->H_acc, sim->sc_dev->E + 15);
+      launch_joints(cs, S, z_next, dt2, 2, sim->g_acc, sim->H_acc, sim->sc_dev->E + 18);
     }
-    build_abd_contact(sim, P.mu > 0 ? sim->n_fric : 0);
+    if ((s = build_abd_contact(sim, P.mu > 0 ? sim->n_fric : 0))) return s;
     if ((s = sync_scalars(sim))) return s;
     if (!(sim->sc_host->flags & ERRF_ABD)) break;
     if (tries > 8 || (s = grow_abd_list(sim, 4 * sim->abd_cap))) { sim->err = "ABD coupling list growth failed"; return IPC_ERR_CAPACITY; }
   }
+  assembly_end(sim);
   launch_dinv(cs, sim->n_nodes, S.bsr_diag, sim->Hval, sim->Dc, sim->Dinv);
   launch_axpy(cs, ndof, gz_next, 1.0 / dt, gzd_next, sim->rhs);
   {
@@ -2100,20 +2206,23 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   // contractions with lam (= sim->p)
   if (glogE) launch_theta_grad(cs, S, sim->xv, sim->p, dt2, glogE);
   double* tmp = sim->y;  // scratch: friction gradient, then M lam
-  CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->E[6], 0, sizeof(double), cs));
+  CUDA_TRY(cudaMemsetAsync(sim->sc_dev->E + 18, 0, 6 * sizeof(acc_t), cs));
   if (P.mu > 0 && sim->n_fric) {
-    CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(double) * ndof, cs));
+    CUDA_TRY(cudaMemsetAsync(sim->g_acc, 0, sizeof(acc_t) * 3 * ndof, cs));
     launch_friction(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_w, sim->f_n, sim->f_lam, P.mu,
-                    P.eps_v * dt, dt2, 1, tmp, nullptr, nullptr, nullptr, nullptr, &sim->sc_dev->E[7]);
-    launch_dot(cs, ndof, tmp, sim->p, &sim->sc_dev->E[6]);
+                    P.eps_v * dt, dt2, 1, sim->g_acc, nullptr, nullptr, nullptr, nullptr, sim->sc_dev->E + 21);
+    launch_acc_finalize(cs, ndof, sim->g_acc, nullptr, tmp);
+    launch_dot(cs, ndof, tmp, sim->p, sim->sc_dev->E + 18);
   }
   launch_mass_apply(cs, S, sim->p, dt, tmp, gzd_t);
   launch_axpy(cs, ndof, tmp, -1.0 / dt, gzd_next, gz_t);
   if (P.mu > 0) {
-    launch_friction_apply(cs, S, sim->n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->p, gz_t);
+    CUDA_TRY(cudaMemsetAsync(sim->gz_acc, 0, sizeof(acc_t) * 3 * ndof, cs));
+    launch_friction_apply(cs, S, sim->n_fric, sim->f_ids, sim->f_w, sim->f_Hu, sim->p, sim->gz_acc);
     // through the lagged normal forces, normals and closest points at x_t
     launch_friction_lag_adjoint(cs, S, sim->xv, sim->xv_t, sim->n_fric, sim->f_ids, sim->f_rec, sim->sh, P.mu,
-                                P.eps_v * dt, dt2, sim->p, gz_t);
+                                P.eps_v * dt, dt2, sim->p, sim->gz_acc);
+    launch_acc_finalize(cs, ndof, sim->gz_acc, gz_t, gz_t);
   }
   if ((s = sync_scalars(sim))) return s;
   CUDA_TRY(cudaGetLastError());
@@ -2123,7 +2232,7 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   }
   if (sim->sc_host->pcg_out[1] == 3) sim->sc_host->pcg_out[1] = 0;
   if (sim->sc_host->pcg_out[1]) { sim->err = "adjoint PCG breakdown (Hessian not positive definite)"; return IPC_ERR_PCG; }
-  if (gmu_host && P.mu > 0) *gmu_host += -sim->sc_host->E[6] / P.mu;
+  if (gmu_host && P.mu > 0) *gmu_host += -sim->E_h[6] / P.mu;
   return IPC_OK;
 }
 
@@ -2226,16 +2335,22 @@ ipc_status sim_set_state(ipcsim* sim, const double* x, const double* v, const do
 ipc_status sim_eval_elastic(ipcsim* sim, const double* x_dev, int project, double* E_dev, double* grad_dev,
                             double* H_dev) {
   if (!sim || !x_dev || !E_dev || !grad_dev) return IPC_ERR_ARG;
-  CUDA_TRY(cudaMemsetAsync(E_dev, 0, sizeof(double), sim->st));
-  CUDA_TRY(cudaMemsetAsync(grad_dev, 0, sizeof(double) * 3 * sim->nf, sim->st));
-  launch_elastic(sim->st, sim->S, x_dev, 1.0, H_dev ? 2 : 1, project, grad_dev, nullptr, H_dev, E_dev);
+  // the simulator's gradient accumulators and its scratch energy slot 7
+  acc_t* Eacc = sim->sc_dev->E + 21;
+  CUDA_TRY(cudaMemsetAsync(Eacc, 0, 3 * sizeof(acc_t), sim->st));
+  CUDA_TRY(cudaMemsetAsync(sim->g_acc, 0, sizeof(acc_t) * 9 * (size_t)sim->nf, sim->st));
+  launch_elastic(sim->st, sim->S, x_dev, 1.0, H_dev ? 2 : 1, project, sim->g_acc, nullptr, H_dev, Eacc);
+  launch_acc_finalize(sim->st, 3 * (size_t)sim->nf, sim->g_acc, nullptr, grad_dev);
+  launch_acc_finalize(sim->st, 1, Eacc, nullptr, E_dev);
   CUDA_TRY(cudaStreamSynchronize(sim->st));
   CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
 
 ipc_status sim_active_pairs(ipcsim* sim, const double* x_dev, int cap, int* rec_dev, double* s_dev, int* n_host) {
-  if (!sim || !x_dev || !rec_dev || !n_host) return IPC_ERR_ARG;
+  if (!sim || !x_dev || !rec_dev || !n_host || cap < 0) return IPC_ERR_ARG;
+  ipc_status so = grow_order(sim, cap);
+  if (so) return so;
   CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), sim->st));
   rebuild_trees(sim, x_dev);
   cull_into(sim, x_dev, rec_dev, s_dev, cap);
@@ -2249,21 +2364,29 @@ ipc_status sim_eval_barrier(ipcsim* sim, const double* x_dev, int n, const int* 
                             double* grad_dev, double* H_dev) {
   if (!sim || !x_dev || n < 0 || (n && !rec_dev) || !E_dev || !grad_dev || (n && !H_dev)) return IPC_ERR_ARG;
   int* n_dev;
-  double *Dc, *gdir, *pDz, *gnode;
+  double* pDz;
+  acc_t *Dc, *gdir, *gnode, *Eacc;
   ipc_status s;
+  const size_t n3 = 3 * (size_t)sim->n_nodes;
   if ((s = dalloc(sim, &n_dev, 1))) return s;
-  if ((s = dalloc(sim, &Dc, 9 * (size_t)sim->n_nodes))) return s;
-  if ((s = dalloc(sim, &gdir, 3 * (size_t)sim->n_nodes))) return s;
+  if ((s = dalloc(sim, &Dc, 27 * (size_t)sim->n_nodes))) return s;
+  if ((s = dalloc(sim, &gdir, 3 * n3))) return s;
   if ((s = dalloc(sim, &pDz, 3 * (size_t)std::max(sim->nk, 1)))) return s;
-  if ((s = dalloc(sim, &gnode, 3 * (size_t)sim->n_nodes))) return s;
+  if ((s = dalloc(sim, &gnode, 3 * n3))) return s;
+  if ((s = dalloc(sim, &Eacc, 3))) return s;
   CUDA_TRY(cudaMemcpyAsync(n_dev, &n, sizeof(int), cudaMemcpyHostToDevice, sim->st));
-  CUDA_TRY(cudaMemsetAsync(E_dev, 0, sizeof(double), sim->st));
+  CUDA_TRY(cudaMemsetAsync(Dc, 0, sizeof(acc_t) * 27 * (size_t)sim->n_nodes, sim->st));
+  CUDA_TRY(cudaMemsetAsync(gdir, 0, sizeof(acc_t) * 3 * n3, sim->st));
+  CUDA_TRY(cudaMemsetAsync(pDz, 0, sizeof(double) * 3 * (size_t)std::max(sim->nk, 1), sim->st));
+  CUDA_TRY(cudaMemsetAsync(gnode, 0, sizeof(acc_t) * 3 * n3, sim->st));
+  CUDA_TRY(cudaMemsetAsync(Eacc, 0, sizeof(acc_t) * 3, sim->st));
   launch_barrier(sim->st, pair_grid(n), sim->S, x_dev, rec_dev, n_dev, n, sim->sh, sim->kappa, 1.0, 2, project, gnode,
-                 H_dev, Dc, pDz, gdir, E_dev, nullptr);
-  CUDA_TRY(cudaMemcpyAsync(grad_dev, gnode, sizeof(double) * 3 * sim->n_nodes, cudaMemcpyDeviceToDevice, sim->st));
+                 H_dev, Dc, pDz, gdir, Eacc, nullptr);
+  launch_acc_finalize(sim->st, n3, gnode, nullptr, grad_dev);
+  launch_acc_finalize(sim->st, 1, Eacc, nullptr, E_dev);
   CUDA_TRY(cudaStreamSynchronize(sim->st));
   CUDA_TRY(cudaGetLastError());
-  dfree(sim, n_dev); dfree(sim, Dc); dfree(sim, gdir); dfree(sim, pDz); dfree(sim, gnode);
+  dfree(sim, n_dev); dfree(sim, Dc); dfree(sim, gdir); dfree(sim, pDz); dfree(sim, gnode); dfree(sim, Eacc);
   return IPC_OK;
 }
 
