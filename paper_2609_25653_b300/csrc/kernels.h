@@ -312,6 +312,14 @@ struct AbdChunks {
   int* n = nullptr;        // chunk slots of the current lists (device)
   int pair_bits = 1, key_bits = 1;
   int cap = 0;
+  // the raw lists (one entry per pair and slot) and the merge of equal codes, sized like the lists
+  int* ent_raw = nullptr;
+  double* val_raw = nullptr;
+  unsigned long long *ekeys = nullptr, *ekeys_tmp = nullptr;
+  int *eidx = nullptr, *eidx_tmp = nullptr, *ehist = nullptr, *etiles = nullptr, *ehead = nullptr;
+  int* body_cnt = nullptr;  // (n_abd + 1)
+  int code_bits = 1, ekey_bits = 1;
+  long long ecap = 0;
 };
 void launch_abd_contact(cudaStream_t, const DevScene& S, const int* rec, const int* n_pairs, int cap,
                         const double* pairH, int n_fric, const int* f_ids, const double* f_w, const double* f_Hu,

@@ -391,6 +391,49 @@ __global__ void k_chunk_pos(AbdChunks C) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) C.pos[C.idx[i]] = C.scan[i];
 }
 
+// Merge of a body's entries with equal code (column node, row): the raw list holds one entry per pair and
+// slot; sorted by (body, code) (stable: chunk order within a code) and summed run by run in that order.
+__global__ void k_ent_keys(int nab, const int* __restrict__ ptr, const int* __restrict__ ent, int code_bits,
+                           long long ent_cap, unsigned long long* __restrict__ keys, int* __restrict__ idx) {
+  const int n = (int)min((long long)ptr[nab], ent_cap);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nab - 1;  // body: the last b with ptr[b] <= e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ptr[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    keys[e] = ((unsigned long long)lo << code_bits) | (unsigned)ent[e];
+    idx[e] = e;
+  }
+}
+__global__ void k_ent_heads(const int* __restrict__ n_dev, long long cap, int bound,
+                            const unsigned long long* __restrict__ keys, int* __restrict__ head) {
+  const int n = (int)min((long long)*n_dev, cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += gridDim.x * blockDim.x)
+    head[i] = (i < n && (i == 0 || keys[i] != keys[i - 1])) ? 1 : 0;
+}
+__global__ void k_ent_merge(const int* __restrict__ n_dev, long long cap, int code_bits,
+                            const unsigned long long* __restrict__ keys, const int* __restrict__ idx,
+                            const int* __restrict__ pos, const double* __restrict__ val_raw, int* __restrict__ ent,
+                            double* __restrict__ val, int* __restrict__ body_cnt) {
+  const int n = (int)min((long long)*n_dev, cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i > 0 && keys[i] == keys[i - 1]) continue;
+    double sum[9];
+    for (int q = 0; q < 9; ++q) sum[q] = 0.0;
+    int j = i;
+    do {
+      const double* v = val_raw + 9 * (size_t)idx[j];
+      for (int q = 0; q < 9; ++q) sum[q] += v[q];
+      ++j;
+    } while (j < n && keys[j] == keys[i]);
+    const int p = pos[i];
+    ent[p] = (int)(keys[i] & ((1ull << code_bits) - 1ull));
+    for (int q = 0; q < 9; ++q) val[9 * (size_t)p + q] = sum[q];
+    atomicAdd(body_cnt + (int)(keys[i] >> code_bits), 1);
+  }
+}
+
 void launch_abd_contact(cudaStream_t st, const DevScene& S, const int* rec, const int* n_pairs, int cap,
                         const double* pairH, int n_fric, const int* f_ids, const double* f_w, const double* f_Hu,
                         int* abd_ptr, const AbdChunks& C, int* ent, double* entv, long long ent_cap, acc_t* Hval,
@@ -408,9 +451,21 @@ void launch_abd_contact(cudaStream_t st, const DevScene& S, const int* rec, cons
   k_chunk_sizes<<<stride_grid(bound, 256, 8), 256, 0, st>>>(C, bound);
   launch_scan_exclusive(st, bound, C.scan, C.tiles);
   k_chunk_pos<<<stride_grid(bound, 256, 8), 256, 0, st>>>(C);
-  k_abd_contact<true><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, nullptr, C, ent,
-                                            entv, ent_cap, Hval, err);
-  count_launch(5);
+  k_abd_contact<true><<<grid, 128, 0, st>>>(S, rec, n_pairs, cap, pairH, n_fric, f_ids, f_w, f_Hu, nullptr, C,
+                                            C.ent_raw, C.val_raw, ent_cap, Hval, err);
+  // merge equal codes into the lists the PCG reads
+  const int eb = (int)ent_cap;
+  const int egrid = stride_grid(eb, 256, 8);
+  k_ent_keys<<<egrid, 256, 0, st>>>(S.nab, abd_ptr, C.ent_raw, C.code_bits, ent_cap, C.ekeys, C.eidx);
+  launch_sort_u64(st, abd_ptr + S.nab, eb, C.ekey_bits, C.ekeys, C.eidx, C.ekeys_tmp, C.eidx_tmp, C.ehist, C.etiles);
+  k_ent_heads<<<egrid, 256, 0, st>>>(abd_ptr + S.nab, ent_cap, eb, C.ekeys, C.ehead);
+  launch_scan_exclusive(st, eb, C.ehead, C.etiles);
+  cudaMemsetAsync(C.body_cnt, 0, sizeof(int) * (S.nab + 1), st);
+  k_ent_merge<<<egrid, 256, 0, st>>>(abd_ptr + S.nab, ent_cap, C.code_bits, C.ekeys, C.eidx, C.ehead, C.val_raw, ent,
+                                     entv, C.body_cnt);
+  k_scan_totals<<<1, 1024, 0, st>>>(S.nab + 1, C.body_cnt);
+  cudaMemcpyAsync(abd_ptr, C.body_cnt, sizeof(int) * (S.nab + 1), cudaMemcpyDeviceToDevice, st);
+  count_launch(9);
 }
 
 // ---------------------------------------------------------------------------

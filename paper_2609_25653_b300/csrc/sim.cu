@@ -303,16 +303,33 @@ long long max_pairs(const ipcsim* sim) {
 // ABD coupling blocks: a few per pair touching an ABD body; grown when a Newton iteration overflows them
 ipc_status grow_abd_list(ipcsim* sim, long long need) {
   if (sim->nab == 0 || need <= sim->abd_cap) return IPC_OK;
-  dfree(sim, sim->abd_ent);
-  dfree(sim, sim->abd_val);
-  dfree(sim, sim->abd_val32);
+  if (need > (1LL << 30)) { sim->err = "ABD coupling list exceeds 2^30 entries"; return IPC_ERR_CAPACITY; }
+  AbdChunks& C = sim->abd_ch;
+  for (void* p : {(void*)sim->abd_ent, (void*)sim->abd_val, (void*)sim->abd_val32, (void*)C.ent_raw, (void*)C.val_raw,
+                  (void*)C.ekeys, (void*)C.ekeys_tmp, (void*)C.eidx, (void*)C.eidx_tmp, (void*)C.ehist,
+                  (void*)C.etiles, (void*)C.ehead, (void*)C.body_cnt})
+    dfree(sim, p);
   sim->abd_ent = nullptr;
   sim->abd_val = nullptr;
   sim->abd_val32 = nullptr;
+  C.ent_raw = nullptr; C.val_raw = nullptr; C.ekeys = nullptr; C.ekeys_tmp = nullptr; C.eidx = nullptr;
+  C.eidx_tmp = nullptr; C.ehist = nullptr; C.etiles = nullptr; C.ehead = nullptr; C.body_cnt = nullptr;
   ipc_status s;
-  if ((s = dalloc(sim, &sim->abd_ent, (size_t)need))) return s;
-  if ((s = dalloc(sim, &sim->abd_val, 9 * (size_t)need))) return s;
-  if (sim->P.precision == IPC_PREC_MIXED && (s = dalloc(sim, &sim->abd_val32, 9 * (size_t)need))) return s;
+  const size_t n = (size_t)need, nh = sort_hist_ints((int)need);
+  if ((s = dalloc(sim, &sim->abd_ent, n))) return s;
+  if ((s = dalloc(sim, &sim->abd_val, 9 * n))) return s;
+  if (sim->P.precision == IPC_PREC_MIXED && (s = dalloc(sim, &sim->abd_val32, 9 * n))) return s;
+  if ((s = dalloc(sim, &C.ent_raw, n)) || (s = dalloc(sim, &C.val_raw, 9 * n)) || (s = dalloc(sim, &C.ekeys, n)) ||
+      (s = dalloc(sim, &C.ekeys_tmp, n)) || (s = dalloc(sim, &C.eidx, n)) || (s = dalloc(sim, &C.eidx_tmp, n)) ||
+      (s = dalloc(sim, &C.ehist, nh)) || (s = dalloc(sim, &C.etiles, std::max(scan_tile_ints(nh), scan_tile_ints(n)))) ||
+      (s = dalloc(sim, &C.ehead, n)) || (s = dalloc(sim, &C.body_cnt, (size_t)sim->nab + 1)))
+    return s;
+  C.code_bits = 3;
+  while ((1LL << (C.code_bits - 2)) <= sim->n_nodes) ++C.code_bits;
+  int body_bits = 1;
+  while ((1LL << body_bits) <= sim->nab) ++body_bits;
+  C.ekey_bits = body_bits + C.code_bits;
+  C.ecap = need;
   sim->abd_cap = need;
   return IPC_OK;
 }
@@ -727,7 +744,10 @@ ipc_status grow_abd_chunks(ipcsim* sim, int n_fric) {
   for (void* p : {(void*)C.keys, (void*)C.keys_tmp, (void*)C.idx, (void*)C.idx_tmp, (void*)C.hist, (void*)C.tiles,
                   (void*)C.size, (void*)C.scan, (void*)C.pos, (void*)C.n})
     dfree(sim, p);
-  C = AbdChunks{};
+  // the chunk buffers only: the raw lists and merge buffers (grow_abd_list) stay
+  C.keys = C.keys_tmp = nullptr;
+  C.idx = C.idx_tmp = C.hist = C.tiles = C.size = C.scan = C.pos = C.n = nullptr;
+  C.cap = 0;
   const int cap = (int)std::min<long long>(need + need / 2, 1LL << 30);
   const size_t nh = sort_hist_ints(cap);
   ipc_status s;
