@@ -282,12 +282,13 @@ void launch_rhs(cudaStream_t, int n, const double* g, const double* gdir, double
 constexpr int PCG_ROW_GROUP = 4;  // default threads per FEM row in the PCG
 constexpr int PCG_REPLICA_COUNT = 8;
 constexpr int PCG_SCENES_MAX = 256;  // independent solves of one launch (one decision thread each)
-// planning cost of one contact incidence of a FEM row, in stored BSR blocks (0: the partition ignores
-// contact and is planned once per launch shape).  With 4, re-planned whenever the incidence counts change,
-// the mixed solve of the soft-gripper squeeze went from 10.3 to 5.4 ms, but concurrent stepping of
-// separate simulators then failed its comparison with sequential stepping once (after other simulators
-// had run in the same process; not reproduced in a fresh process), so it stays off until that is explained
-constexpr int PCG_CONTACT_WEIGHT = 0;
+// Contact work of a FEM row in units of a stored BSR block, per contact incidence (a 3 x 12 pair-block row
+// times the pair's vertices is about four blocks' work): the FEM rows are partitioned with it at the first
+// Newton iteration of every step (the plan then stays for the step; the coarse level is rebuilt at that
+// iteration anyway).  Two simulators stepping concurrently once disagreed with sequential stepping when
+// the plan followed the contacts at every iteration; that was the process-wide shared-memory limit race
+// (fixed), not the partition.
+constexpr int PCG_CONTACT_WEIGHT = 4;
 inline size_t pcg_partial_doubles(int grid) { return (size_t)PCG_REPLICA_COUNT * 7 * grid; }
 // co-resident CTAs of the PCG kernel for this shape (rowg: threads per FEM row, 1, 2, 4 or 8)
 int pcg_max_blocks(int threads, int fp32, int rowg, size_t dyn_smem);

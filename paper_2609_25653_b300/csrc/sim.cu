@@ -449,14 +449,16 @@ inline void prof_collect(ipcsim* sim) {
 
 // Row partition, shared-memory residency and operator layout of the PCG for
 // the current launch shape (tune_rowg threads per FEM row, tune_bps CTAs per SM).
-ipc_status pcg_prepare(ipcsim* sim, int fp32) {
+// Plan of the cooperative PCG launch and the operator layout of the current Hessian.  With
+// contacts = true the FEM rows are re-partitioned with the contact work of the current incidence lists
+// (PCG_CONTACT_WEIGHT per incidence, in units of a BSR block) when it changed; otherwise the plan is kept.
+ipc_status pcg_prepare(ipcsim* sim, int fp32, bool contacts = false) {
   const int sms = device_sms();
   const int rowg = sim->tune_rowg;
   const int want = std::min(std::max(1, sms * std::max(1, sim->tune_bps)), sim->pcg_grid_max);
-  // contact work of every FEM row from the current incidence lists: the partition is redone when it changes
   const int contact_w = PCG_CONTACT_WEIGHT;
   bool extra_changed = false;
-  if (contact_w > 0 && sim->nf > 0) {
+  if (contacts && contact_w > 0 && sim->nf > 0) {
     sim->h_inc_ptr.resize(sim->nf + 1);
     CUDA_TRY(cudaMemcpyAsync(sim->h_inc_ptr.data(), sim->inc_ptr, sizeof(int) * (sim->nf + 1), cudaMemcpyDeviceToHost,
                              sim->st));
@@ -476,7 +478,7 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32) {
     for (int attempt = 0; attempt < 32 && !fits; ++attempt) {
       if (grid < 1 || (sim->nab > 0 && grid < 2)) break;
       pcg_plan_rows(sim->h_row, sim->nf, sim->nab, grid, sim->h_node_scene, sim->n_scenes, sim->plan,
-                    contact_w > 0 ? &sim->h_row_extra : nullptr);
+                    sim->h_row_extra.empty() ? nullptr : &sim->h_row_extra);
       const size_t bytes = pcg_resident_bytes(sim->plan, fp32);
       const int cap_res = (!sim->pcg_streamed && bytes <= pcg_smem_limit()) ? pcg_max_blocks(PCG_THREADS, fp32, rowg, bytes) : 0;
       if (cap_res >= grid) { resident = true; smem = bytes; fits = true; break; }
@@ -1825,7 +1827,9 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       sim->tune_bps = best_b;
       sim->autotune_pending = false;
     }
-    if ((s = pcg_prepare(sim, fp32))) return s;
+    // the partition follows the contact work at the first Newton iteration of a step, when the coarse level
+    // (whose aggregates are the CTA row segments) is rebuilt anyway
+    if ((s = pcg_prepare(sim, fp32, it == 0 && P.coarse_rebuild <= 0))) return s;
     // the coarse level is rebuilt at the first Newton iteration of a step when the launch shape changed,
     // when it failed or is missing, after coarse_rebuild steps (every step by default), or when the
     // previous step needed 30 % more PCG iterations per solve than the step it was built in
