@@ -475,6 +475,12 @@ class Scene:
             ell = self.dhat  # no deformable body: the automatic stiffnesses use dhat and E = 1e5 Pa
         Emax = float(np.exp(np.max(sc["fem_logE"]))) if len(sc["fem_logE"]) else 1e5
         self.kappa = P["kappa"] if P["kappa"] > 0 else Emax * ell / barrier_d2_dist(0.5 * self.dhat, self.dhat)
+        # adaptive barrier stiffness (IPC's kappa growth): after a Newton iteration whose iterate had its
+        # smallest distance below kappa_dmin * dhat without that distance having grown since the step's
+        # previous iterate, kappa doubles, up to kappa_max_factor times its initial value
+        self.kappa_adaptive = bool(P.get("kappa_adaptive", 0))
+        self.kappa_dmin = float(P.get("kappa_dmin", 1e-2))
+        self.kappa_max = self.kappa * float(P.get("kappa_max_factor", 100.0))
         self.k_c = P["k_c"] if P["k_c"] > 0 else 100.0 * Emax * ell
         free_pts = [X]
         for i, A in enumerate(abd):
@@ -739,6 +745,7 @@ class Oracle:
         D = slice(S.n_free, S.ndof)
         it_stats = []
         converged = False
+        s_prev = math.inf  # smallest squared distance of the previous iterate (adaptive kappa)
         for it in range(S.max_newton):
             E, g, H, info = S.evaluate(z, ctx)
             pD = zD_hat - z[D]
@@ -785,6 +792,12 @@ class Oracle:
             if alpha == 1.0:
                 z[D] = zD_hat
             rec["alpha"] = alpha
+            if S.kappa_adaptive:
+                s_it = info["min_s"]
+                if s_it < (S.kappa_dmin * S.dhat) ** 2 and s_it <= s_prev:
+                    S.kappa = min(2.0 * S.kappa, S.kappa_max)
+                s_prev = s_it
+            rec["kappa"] = S.kappa
             it_stats.append(rec)
             if record_iterates:
                 rec["z"] = z.copy()
