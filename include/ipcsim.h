@@ -138,6 +138,14 @@ typedef struct {
   int coarse_rebuild; /* two-level coarse matrix: 0 rebuilt at the first Newton iteration of every step
                          (default); n > 0 kept up to n steps while the PCG iterations per solve stay
                          within 30 % of the step it was built in; -1 rebuilt at every Newton iteration */
+  int kappa_adaptive; /* adaptive barrier stiffness (IPC's kappa growth; the paper keeps IPC's barrier
+                         without stating its stiffness policy): != 0: after every Newton iteration whose
+                         iterate had its smallest primitive distance below kappa_dmin * dhat while that
+                         distance had not grown since the step's previous iterate, the scene's kappa
+                         doubles, up to kappa_max_factor times its initial value; kappa carries over to
+                         the following steps.  sim_adjoint is not available with it. */
+  double kappa_dmin;       /* fraction of dhat (<= 0: 1e-2) */
+  double kappa_max_factor; /* (<= 0: 100) */
 } ipc_params;
 
 /* PCG preconditioners (the paper names StiffGIPC's solver without its
@@ -172,6 +180,7 @@ typedef struct {
   int pcg_fallbacks;      /* two-level solves that broke down or ended far above pcg_rtol (the coarse
                              inverse not positive definite on that system) and were repeated with
                              block Jacobi; their iterations are in pcg_iters_total */
+  double kappa_end;       /* barrier stiffness of the first scene after the step */
 } ipc_step_stats;
 
 /* Build a simulator of the scene the paper's physics layer simulates

@@ -204,6 +204,7 @@ struct DevScene {
   acc_t* E_sc;               // (n_scenes, 8) accumulators
   int* err;                  // error flags of the iteration (ERRF_*)
   acc_t* e_slots;            // (E_SLOTS) accumulators spreading one energy sum over many addresses
+  unsigned long long* min_sc;  // batches: smallest squared distance of every scene's assembly (double bits)
   unsigned long long* alpha_sc;
   unsigned long long* pn_sc;
   const double* alpha_trial;

@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(32 * BWARPS) k_barrier_warp(DevScene S, const 
       smin = fmin(smin, sd);
       acc_add(S.e_slots + 3 * (k & (E_SLOTS - 1)), kappa * mval * b, S.err);
       if (S.E_sc) scene_energy(S, scene_of_vertex(S, W.ids[0]), 2, kappa * mval * b);
+      if (S.min_sc) atomicMin(S.min_sc + scene_of_vertex(S, W.ids[0]), dbits(sd));
     }
     __syncwarp();
     double b = W.sc[1], b1 = W.sc[2], b2 = W.sc[3], mval = W.sc[4], m1 = W.sc[5], m2 = W.sc[6];

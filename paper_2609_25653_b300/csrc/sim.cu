@@ -140,6 +140,12 @@ struct ipcsim {
   int pcg_grid_max = 1;
   // per-scene Newton control of a batch (n_scenes > 1): device accumulators and pinned host mirrors
   acc_t* E_sc_dev = nullptr;    // (n_scenes, 8) accumulators
+  // barrier stiffness per scene (adaptive growth): current, cap, at the start of the step, the smallest
+  // squared distance of the previous iterate; device copy of the current values; per-scene minima of a batch
+  std::vector<double> kappa_cur, kappa_max, kappa_step, s_prev;
+  double* d_scene_kappa = nullptr;
+  unsigned long long* min_sc_dev = nullptr;
+  std::vector<unsigned long long> min_sc_h;
   double E_h[8] = {0};          // the accumulators of sc_host->E as doubles (sync_scalars)
   std::vector<double> E_sc_v;   // (n_scenes, 8) the same per scene
   // joint drive targets (b-side vectors, offsets), rewritten by sim_set_joint_targets
@@ -845,6 +851,8 @@ ipc_status reset_iteration_scalars(ipcsim* sim) {
     const int ns = sim->n_scenes;
     CUDA_TRY(cudaMemsetAsync(sim->E_sc_dev, 0, sizeof(acc_t) * 24 * ns, sim->st));
     CUDA_TRY(cudaMemsetAsync(sim->pn_sc_dev, 0, sizeof(unsigned long long) * 2 * ns, sim->st));
+    // 0x7f bytes: a double near 1.4e306, above every squared distance
+    CUDA_TRY(cudaMemsetAsync(sim->min_sc_dev, 0x7f, sizeof(unsigned long long) * ns, sim->st));
     for (int k = 0; k < ns; ++k) sim->alpha_sc_h[k] = double_bits(1.0);
     CUDA_TRY(cudaMemcpyAsync(sim->alpha_sc_dev, sim->alpha_sc_h, sizeof(unsigned long long) * ns,
                              cudaMemcpyHostToDevice, sim->st));
@@ -873,6 +881,8 @@ ipc_status sync_scalars(ipcsim* sim) {
     CUDA_TRY(cudaMemcpyAsync(sim->alpha_sc_h, sim->alpha_sc_dev, sizeof(unsigned long long) * ns,
                              cudaMemcpyDeviceToHost, sim->st));
     CUDA_TRY(cudaMemcpyAsync(sim->pn_sc_h, sim->pn_sc_dev, sizeof(unsigned long long) * 2 * ns,
+                             cudaMemcpyDeviceToHost, sim->st));
+    CUDA_TRY(cudaMemcpyAsync(sim->min_sc_h.data(), sim->min_sc_dev, sizeof(unsigned long long) * ns,
                              cudaMemcpyDeviceToHost, sim->st));
   }
   CUDA_TRY(cudaStreamSynchronize(sim->st));
@@ -1214,6 +1224,13 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   sim->sh = P.dhat * P.dhat;
   sim->kappa = scene_kappa[0];
   sim->k_c = scene_kc[0];
+  {
+    const double fmax = P.kappa_max_factor > 0 ? P.kappa_max_factor : 100.0;
+    sim->kappa_cur = scene_kappa;
+    sim->kappa_max.resize(n_scenes);
+    for (int k = 0; k < n_scenes; ++k) sim->kappa_max[k] = fmax * scene_kappa[k];
+    sim->s_prev.assign(n_scenes, INFINITY);
+  }
   sim->n_scenes = n_scenes;
   // L_bbox over the free bodies at the initial state, per scene; the Newton test uses the smallest
   {
@@ -1391,7 +1408,7 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     if ((s = upload(sim, &ip, diag))) return fail(s, ""); S.bsr_diag = ip;
     if ((s = upload(sim, &sim->Hconst, Hc))) return fail(s, "");
     if ((s = upload(sim, &ip, body_scene))) return fail(s, ""); S.body_scene = ip;
-    if ((s = upload(sim, &dp, scene_kappa))) return fail(s, ""); S.scene_kappa = dp;
+    if ((s = upload(sim, &dp, scene_kappa))) return fail(s, ""); S.scene_kappa = dp; sim->d_scene_kappa = dp;
     if ((s = upload(sim, &dp, scene_kc))) return fail(s, ""); S.scene_kc = dp;
     S.n_scenes = n_scenes;
     if (n_scenes > 1) {
@@ -1407,6 +1424,8 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
       if (cudaMallocHost(&sim->pcg_skip_h, sizeof(int) * (size_t)n_scenes) != cudaSuccess)
         return fail(IPC_ERR_CUDA, "cudaMallocHost failed");
       if ((s = dalloc(sim, &sim->E_sc_dev, 24 * (size_t)n_scenes))) return fail(s, ""); S.E_sc = sim->E_sc_dev;
+      if ((s = dalloc(sim, &sim->min_sc_dev, (size_t)n_scenes))) return fail(s, ""); S.min_sc = sim->min_sc_dev;
+      sim->min_sc_h.assign(n_scenes, 0);
       if ((s = dalloc(sim, &sim->alpha_sc_dev, (size_t)n_scenes))) return fail(s, ""); S.alpha_sc = sim->alpha_sc_dev;
       if ((s = dalloc(sim, &sim->pn_sc_dev, 2 * (size_t)n_scenes))) return fail(s, ""); S.pn_sc = sim->pn_sc_dev;
       if ((s = dalloc(sim, &sim->alpha_trial_dev, (size_t)n_scenes))) return fail(s, "");
@@ -1695,6 +1714,31 @@ namespace {
 // The body of sim_step.  Every return after the start of the step leaves the
 // state to the caller (sim_step), which puts it back to x_t on any error:
 // `started` is set once z_t and xk_t hold the state at the start of the step.
+// Adaptive barrier stiffness after an accepted Newton iterate: s_it[k] is the smallest squared distance of
+// scene k's iterate (its assembly), done[k] != 0 skips a scene.  kappa doubles, up to its cap, when s_it is
+// below (kappa_dmin dhat)^2 and not larger than the previous iterate's.
+ipc_status adapt_kappa(ipcsim* sim, const std::vector<double>& s_it, const std::vector<char>* done) {
+  const ipc_params& P = sim->P;
+  if (!P.kappa_adaptive) return IPC_OK;
+  const double dmin = (P.kappa_dmin > 0 ? P.kappa_dmin : 1e-2) * P.dhat;
+  bool changed = false;
+  for (int k = 0; k < sim->n_scenes; ++k) {
+    if (done && !done->empty() && (*done)[k]) continue;
+    if (s_it[k] < dmin * dmin && s_it[k] <= sim->s_prev[k] && sim->kappa_cur[k] < sim->kappa_max[k]) {
+      sim->kappa_cur[k] = std::min(2.0 * sim->kappa_cur[k], sim->kappa_max[k]);
+      changed = true;
+    }
+    sim->s_prev[k] = s_it[k];
+  }
+  if (changed) {
+    sim->kappa = sim->kappa_cur[0];
+    CUDA_TRY(cudaMemcpyAsync(sim->d_scene_kappa, sim->kappa_cur.data(), sizeof(double) * sim->n_scenes,
+                             cudaMemcpyHostToDevice, sim->st));
+    CUDA_TRY(cudaStreamSynchronize(sim->st));
+  }
+  return IPC_OK;
+}
+
 ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, bool& started) {
   const DevScene& S = sim->S;
   const ipc_params& P = sim->P;
@@ -1702,6 +1746,8 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
   const double dt = P.dt, dt2 = dt * dt;
   cudaStream_t cs = sim->st;
   if (sim->nkb) CUDA_TRY(cudaMemcpyAsync(sim->T_dev, kin_T_next, sizeof(double) * 12 * sim->nkb, cudaMemcpyHostToDevice, cs));
+  sim->kappa_step = sim->kappa_cur;
+  sim->s_prev.assign(sim->n_scenes, INFINITY);
   launch_predict(cs, S, sim->z, sim->zd, dt, sim->grav, sim->z_t, sim->z_tilde);
   if (nk3) CUDA_TRY(cudaMemcpyAsync(sim->xk_t, sim->xk, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, cs));
   started = true;
@@ -1877,6 +1923,10 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
     if ((s = sync_scalars(sim))) return s;
     CUDA_TRY(cudaGetLastError());
     const ipcsim::Scal& h = *sim->sc_host;
+    // smallest squared distance of every scene's iterate (for the adaptive stiffness)
+    std::vector<double> s_it(sim->n_scenes, bits_to_double(h.min_s));
+    if (sim->n_scenes > 1)
+      for (int k = 0; k < sim->n_scenes; ++k) s_it[k] = bits_to_double(sim->min_sc_h[k]);
     if (h.flags & ERRF_BVH) return finish(IPC_ERR_BVH_OVERFLOW, "BVH traversal stack overflow");
     if (h.flags & ERRF_ACC) return finish(IPC_ERR_NAN, "an energy, gradient or Hessian term is not finite or exceeds 2^94");
     if (h.flags & ERRF_INC) return finish(IPC_ERR_CUDA, "contact incidence list overflow");
@@ -1984,6 +2034,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
       std::swap(sim->z, sim->z_trial);
       std::swap(sim->xk, sim->xk_trial);
       sim->cand_valid = false;
+      if ((s = adapt_kappa(sim, s_it, &scene_done))) return s;
       bool all = true;
       for (int k = 0; k < ns; ++k) all = all && scene_done[k];
       if (all) { converged = true; break; }
@@ -2019,6 +2070,7 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
     std::swap(sim->z, sim->z_trial);
     std::swap(sim->xk, sim->xk_trial);
     sim->cand_valid = false;
+    if ((s = adapt_kappa(sim, s_it, nullptr))) return s;
   }
   if (!converged) return finish(IPC_ERR_NEWTON_MAXIT, "Newton did not converge");
   CUDA_TRY(cudaGetLastError());
@@ -2055,12 +2107,20 @@ ipc_status sim_step(ipcsim* sim, const double* kin_T_next, ipc_step_stats* stats
   const ipc_status code = step_body(sim, kin_T_next, st, started);
   st.status = code;
   if (code != IPC_OK && started) {
-    // any failure after the start of the step: back to the state at its start (x_t, v_t unchanged)
+    // any failure after the start of the step: back to the state at its start (x_t, v_t unchanged, and the
+    // barrier stiffness of the step's start)
     const int ndof = 3 * sim->n_nodes, nk3 = 3 * sim->nk;
     cudaMemcpyAsync(sim->z, sim->z_t, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, sim->st);
     if (nk3) cudaMemcpyAsync(sim->xk, sim->xk_t, sizeof(double) * nk3, cudaMemcpyDeviceToDevice, sim->st);
+    if (sim->kappa_cur != sim->kappa_step) {
+      sim->kappa_cur = sim->kappa_step;
+      sim->kappa = sim->kappa_cur[0];
+      cudaMemcpyAsync(sim->d_scene_kappa, sim->kappa_cur.data(), sizeof(double) * sim->n_scenes,
+                      cudaMemcpyHostToDevice, sim->st);
+    }
     cudaStreamSynchronize(sim->st);
   }
+  st.kappa_end = sim->kappa_cur.empty() ? sim->kappa : sim->kappa_cur[0];
   if (stats) *stats = st;
   return code;
 }
@@ -2144,6 +2204,10 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
                        const double* gzd_next, double* gz_t, double* gzd_t, double* glogE, double* gmu_host) {
   if (!sim || !z_t || !zd_t || !z_next || !gz_next || !gzd_next || !gz_t || !gzd_t) return IPC_ERR_ARG;
   if (sim->nkb && (!kin_T_t_host || !kin_T_next_host)) { sim->err = "kinematic transforms required"; return IPC_ERR_ARG; }
+  if (sim->P.kappa_adaptive) {
+    sim->err = "sim_adjoint needs a fixed barrier stiffness (kappa_adaptive is on)";
+    return IPC_ERR_ARG;
+  }
   const DevScene& S = sim->S;
   const ipc_params& P = sim->P;
   cudaStream_t cs = sim->st;

@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("eps_v", C.c_double), ("k_c", C.c_double), ("kappa_A", C.c_double), ("newton_tol", C.c_double),
                 ("pcg_rtol", C.c_double), ("s_ccd", C.c_double), ("max_newton", C.c_int), ("max_pcg", C.c_int),
                 ("precision", C.c_int), ("pair_capacity", C.c_int), ("broad_phase", C.c_int),
-                ("pair_capacity_max", C.c_int), ("preconditioner", C.c_int), ("coarse_rebuild", C.c_int)]
+                ("pair_capacity_max", C.c_int), ("preconditioner", C.c_int), ("coarse_rebuild", C.c_int),
+                ("kappa_adaptive", C.c_int), ("kappa_dmin", C.c_double), ("kappa_max_factor", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -111,7 +112,7 @@ class StepStats(C.Structure):
                 ("pcg_iters_max", C.c_int), ("n_pairs_max", C.c_int), ("n_friction_pairs", C.c_int),
                 ("n_ccd_max", C.c_int), ("ls_halvings", C.c_int), ("alpha_min", C.c_double),
                 ("min_dist", C.c_double), ("energy_end", C.c_double), ("pnorm_end", C.c_double),
-                ("pcg_unconverged", C.c_int), ("pcg_fallbacks", C.c_int)]
+                ("pcg_unconverged", C.c_int), ("pcg_fallbacks", C.c_int), ("kappa_end", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -245,7 +246,8 @@ def make_params(p: dict, precision=PREC_FP64) -> Params:
                   max_pcg=int(p.get("max_pcg", 0)), precision=int(precision), pair_capacity=int(p.get("pair_capacity", 0)),
                   broad_phase=int(p.get("broad_phase", BROAD_LBVH)), pair_capacity_max=int(p.get("pair_capacity_max", 0)),
                   preconditioner=int(p.get("preconditioner", PRECOND_TWO_LEVEL)),
-                  coarse_rebuild=int(p.get("coarse_rebuild", 0)))
+                  coarse_rebuild=int(p.get("coarse_rebuild", 0)), kappa_adaptive=int(p.get("kappa_adaptive", 0)),
+                  kappa_dmin=float(p.get("kappa_dmin", 1e-2)), kappa_max_factor=float(p.get("kappa_max_factor", 100.0)))
 
 
 def _fill_desc(d, scene, keep):
