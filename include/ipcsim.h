@@ -341,7 +341,7 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t_dev, const double* zd_t_de
  * [rowg, blocks_per_sm, CTAs of the last PCG launch (0 before the first),
  * 1 if that launch kept its operator rows in shared memory]; ms8 (may be
  * NULL) the last autotuning times in ms, index 4 * (blocks_per_sm - 1) +
- * log2(rowg). */
+ * log2(rowg) (-1: no co-resident plan with that shape). */
 ipc_status sim_tuning(ipcsim* sim, int rowg, int blocks_per_sm, int autotune_next_step, int* out4, float* ms8);
 
 /* Where the cooperative PCG keeps its operator (the solver of the Newton

@@ -263,7 +263,7 @@ __device__ inline double block_max(double v) {
   if (lane == 0) shm[w] = v;
   __syncthreads();
   int nw = (blockDim.x + 31) >> 5;
-  v = (threadIdx.x < nw) ? shm[threadIdx.x] : 0.0;
+  v = (threadIdx.x < nw) ? shm[threadIdx.x] : -INFINITY;  // lanes without a warp must not raise the maximum
   if (w == 0)
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
   return v;

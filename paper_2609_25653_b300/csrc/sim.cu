@@ -490,7 +490,18 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32, bool contacts = false) {
       if (cap_res >= grid) { resident = true; smem = bytes; fits = true; break; }
       smem = pcg_contact_bytes(sim->plan);
       const int cap = smem <= pcg_smem_limit() ? pcg_max_blocks(PCG_THREADS, fp32, rowg, smem) : 0;
-      if (cap <= 0) { sim->err = "PCG kernel cannot be made resident"; return IPC_ERR_CUDA; }
+      if (cap < grid && !sim->h_row_extra.empty()) {
+        // the contact-weighted partition gave a CTA more rows than this grid's shared memory per CTA holds
+        // (cheap rows gather in few CTAs): plan this grid without the contact work before shrinking it
+        sim->h_row_extra.clear();
+        --attempt;
+        continue;
+      }
+      if (cap <= 0) {
+        sim->err = "PCG kernel cannot be made resident (grid " + std::to_string(grid) + ", largest segment " +
+                   std::to_string(sim->plan.max_rows) + " rows, " + std::to_string(smem) + " B of shared memory)";
+        return IPC_ERR_CUDA;
+      }
       if (cap >= grid) { fits = true; break; }
       grid = cap;
     }
@@ -1855,7 +1866,11 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
           sim->tune_rowg = rowgs[ri];
           sim->tune_bps = bi + 1;
           float ms = 0.f;
-          if ((s = pcg_prepare(sim, fp32))) return s;
+          if (pcg_prepare(sim, fp32) != IPC_OK) {
+            // no co-resident plan with this shape (e.g. too few CTAs for the batch's scenes): not a candidate
+            sim->tune_ms[4 * bi + ri] = -1.f;
+            continue;
+          }
           if ((s = coarse_setup(sim, fp32, n_fric_it))) return s;
           for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, cs);

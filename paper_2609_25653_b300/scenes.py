@@ -784,7 +784,8 @@ def batched_grasps(n_scenes: int = 64, seed0: int = 0, n_steps: int = 200, tets_
     a seeded rigid object (ellipsoid or box, 1k-8k triangles, 20-60 mm, ABD,
     0.1 kg), a random approach pose (yaw in [0, 2 pi), offset +/- 10 mm), and
     the close-and-lift trajectory of the single-scene grasp; no arm links.
-    FP32-PCG / FP64-barrier configuration, dt = 5 ms.  Scene k is translated
+    FP32-PCG / FP64-barrier configuration, dt = 5 ms, at most 500 Newton
+    iterations per step.  Scene k is translated
     to grid cell (k mod 8, k div 8) with `spacing` metres between cells; a
     rigid translation leaves each scene's motion unchanged."""
     mm = 1e-3
@@ -818,6 +819,9 @@ def batched_grasps(n_scenes: int = 64, seed0: int = 0, n_steps: int = 200, tets_
             sc["kin_T"][s, 1, 1, 3] += shift
             sc["kin_T"][s, 2, 1, 3] -= shift
         sc["name"] = f"batched_grasp_{k}_{len(sc['fem_tets'])}tet"
+        # some random poses meet lift steps where the projected Newton iteration converges slowly (full
+        # steps, about 300 iterations; scene 14 at step 138): a larger cap than the single-scene default
+        sc["params"] = dict(sc["params"], max_newton=500)
         # scenes sit on an 8-wide grid, `spacing` apart, so that their ground quads do not overlap
         out.append(translate_scene(sc, ((k % 8) * spacing, (k // 8) * spacing, 0.0)) if spacing else sc)
     return out
