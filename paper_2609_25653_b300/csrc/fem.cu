@@ -208,9 +208,9 @@ __device__ inline void snh_projected_hessian(const d3* f, double mu, double lam,
       w[3 * a] = m.x; w[3 * a + 1] = m.y; w[3 * a + 2] = m.z;
     }
     double c = sv * lamb;
-    for (int i = 0; i < 12; ++i) {
+    for (int i = 0; i < 12; ++i) {  // upper triangle; the lower one is its mirror
       double ci = c * w[i];
-      for (int j = 0; j < 12; ++j) H12[12 * i + j] += ci * w[j];
+      for (int j = i; j < 12; ++j) H12[12 * i + j] += ci * w[j];
     }
   };
   const double r2 = 0.70710678118654752440;
@@ -235,6 +235,8 @@ __device__ inline void snh_projected_hessian(const d3* f, double mu, double lam,
     double B[9] = {Y[q], 0, 0, 0, Y[3 + q], 0, 0, 0, Y[6 + q]};
     add_mode(B, A[4 * q]);
   }
+  for (int i = 1; i < 12; ++i)
+    for (int j = 0; j < i; ++j) H12[12 * i + j] = H12[12 * j + i];
 }
 
 // The same projection in FP32, for the mixed-precision path (whose operator is
@@ -341,9 +343,9 @@ __device__ inline void snh_projected_hessian_f32(const d3* fd, double mu_d, doub
       for (int d = 0; d < 3; ++d) w[3 * a + d] = y0 * U[0][d] + y1 * U[1][d] + y2 * U[2][d];
     }
     const float c = sv * lamb;
-    for (int i = 0; i < 12; ++i) {
+    for (int i = 0; i < 12; ++i) {  // upper triangle; the lower one is its mirror
       const float ci = c * w[i];
-      for (int j = 0; j < 12; ++j) H12[12 * i + j] += ci * w[j];
+      for (int j = i; j < 12; ++j) H12[12 * i + j] += ci * w[j];
     }
   };
   const float r2 = 0.70710678f;
@@ -368,6 +370,8 @@ __device__ inline void snh_projected_hessian_f32(const d3* fd, double mu_d, doub
     const float B[9] = {Y[q], 0, 0, 0, Y[3 + q], 0, 0, 0, Y[6 + q]};
     add_mode(B, Am[4 * q]);
   }
+  for (int i = 1; i < 12; ++i)
+    for (int j = 0; j < i; ++j) H12[12 * i + j] = H12[12 * j + i];
 }
 
 // Neo-Hookean energy Psi = mu/2 (|F|^2 - 3) - mu (J - 1) + lam/2 (J - 1)^2 per tet (§III-C.1),

@@ -78,6 +78,8 @@ struct CoarseDev {
   const double* rot = nullptr;    // (aggregates) 1 / RMS radius scaling the rotations, 0: none
   const double* x = nullptr;      // (nf, 3) positions the modes are built at
   double* part = nullptr;         // (FEM CTAs, 6) every CTA's part of P^T v for the current iteration
+  int smem_off = -1;              // byte offset in the dynamic shared memory where every CTA stages its
+                                  // aggregate's six rows of the inverse once per solve; -1: read from global
 };
 // host-side layout of the coarse level for one PCG plan
 struct CoarseLayout {

@@ -739,11 +739,12 @@ __device__ inline void coarse_restrict(const PcgArgs& a, int agg, int r0, int r1
 // CTAs' parts): 6 values into res (every thread).  M: the precision of the
 // stored inverse and of the products.  Every thread must call it.
 template <typename M>
-__device__ inline void coarse_own_t(const PcgArgs& a, const M* inv, int agg, int s, Shared& sh, double res[6]) {
+__device__ inline void coarse_own_t(const PcgArgs& a, const M* inv, int agg, int s, Shared& sh, double res[6],
+                                    const M* rows) {
   M acc[6] = {M(0), M(0), M(0), M(0), M(0), M(0)};
   if (agg >= 0 && s >= 0) {
     const int n = a.co.solve_n[s], lo = a.co.solve_lo[s];
-    const M* R = inv + a.co.off[s] + (size_t)6 * (agg - lo) * n;
+    const M* R = rows ? rows : inv + a.co.off[s] + (size_t)6 * (agg - lo) * n;
     // the restricted values of this thread's unknowns first (independent loads), then the products
     constexpr int PER = (COARSE_MAX_UNKNOWNS + PCG_THREADS_MAX - 1) / PCG_THREADS_MAX;
     double v[PER];
@@ -773,9 +774,33 @@ __device__ inline void coarse_own_t(const PcgArgs& a, const M* inv, int agg, int
   for (int k = 0; k < 6; ++k) res[k] = sh.out[k];
   __syncthreads();
 }
-__device__ inline void coarse_own(const PcgArgs& a, int agg, int s, Shared& sh, double res[6]) {
-  if (a.co.inv64) coarse_own_t<double>(a, a.co.inv64, agg, s, sh, res);
-  else coarse_own_t<float>(a, a.co.inv32, agg, s, sh, res);
+// rows: the aggregate's six rows staged in shared memory (coarse_stage), or null
+__device__ inline void coarse_own(const PcgArgs& a, int agg, int s, Shared& sh, double res[6], const void* rows) {
+  if (a.co.inv64) coarse_own_t<double>(a, a.co.inv64, agg, s, sh, res, (const double*)rows);
+  else coarse_own_t<float>(a, a.co.inv32, agg, s, sh, res, (const float*)rows);
+}
+
+// The six rows of the coarse inverse that belong to this CTA's aggregate, copied into the dynamic shared
+// memory at a.co.smem_off once per solve (they stay fixed during the solve); returns them, or null when
+// they are read from global memory.  Every thread must call it.
+__device__ inline const void* coarse_stage(const PcgArgs& a, int agg, int s, unsigned char* dyn) {
+  if (a.co.inv32 == nullptr || a.co.smem_off < 0) return nullptr;
+  const void* out = nullptr;
+  if (agg >= 0 && s >= 0) {
+    const int n = a.co.solve_n[s], lo = a.co.solve_lo[s];
+    const size_t first = a.co.off[s] + (size_t)6 * (agg - lo) * n;
+    if (a.co.inv64) {
+      double* d = reinterpret_cast<double*>(dyn + a.co.smem_off);
+      for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) d[i] = a.co.inv64[first + i];
+      out = d;
+    } else {
+      float* d = reinterpret_cast<float*>(dyn + a.co.smem_off);
+      for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) d[i] = a.co.inv32[first + i];
+      out = d;
+    }
+  }
+  __syncthreads();
+  return out;
 }
 
 // P_i c: translation plus rotation theta x (x_i - centre) / rho of node i's aggregate
@@ -1038,6 +1063,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   // the CTA's aggregate, identical in every thread
   const bool coarse = a.co.inv32 != nullptr;
   const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? a.co.cta_agg[cta] : -1;
+  const void* co_rows = coarse_stage(a, my_agg, my_sc, dyn);
   double co_w[6] = {0, 0, 0, 0, 0, 0}, co_z[6] = {0, 0, 0, 0, 0, 0};
 
   Vecs<double> V;
@@ -1165,7 +1191,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         v0 = V.r[3 * i]; v1 = V.r[3 * i + 1]; v2 = V.r[3 * i + 2];
       });
       grid.sync();
-      if (on) coarse_own(a, my_agg, my_sc, sh, cr);
+      if (on) coarse_own(a, my_agg, my_sc, sh, cr, co_rows);
     }
     if (on) {
       for_nodes([&](int i, const double*) {
@@ -1189,7 +1215,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         v0 = y[0]; v1 = y[1]; v2 = y[2];
       });
       grid.sync();
-      if (on) coarse_own(a, my_agg, my_sc, sh, cwv);
+      if (on) coarse_own(a, my_agg, my_sc, sh, cwv, co_rows);
       if (on)
         for (int k = 0; k < 6; ++k) { co_w[k] = cwv[k]; co_z[k] = 0.0; }
     }
@@ -1284,7 +1310,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
       grid.sync();
       if (my_act == ACT_STEP) {
         double eta[6];
-        coarse_own(a, my_agg, my_sc, sh, eta);
+        coarse_own(a, my_agg, my_sc, sh, eta, co_rows);
         for (int k = 0; k < 6; ++k) {
           co_z[k] = fma(beta, co_z[k], eta[k]);
           co_w[k] = fma(-alpha, co_z[k], co_w[k]);
@@ -1443,6 +1469,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
   // images of r and s of the CTA's aggregate, identical in every thread
   const bool coarse = a.co.inv32 != nullptr;
   const int my_agg = (coarse && fem_cta && my_sc >= 0 && r1 > r0) ? a.co.cta_agg[cta] : -1;
+  const void* co_rows = coarse_stage(a, my_agg, my_sc, dyn);
   F co_r[6] = {F(0), F(0), F(0), F(0), F(0), F(0)}, co_s[6] = {F(0), F(0), F(0), F(0), F(0), F(0)};
 
   F* base = (F*)a.vec;
@@ -1580,7 +1607,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
       });
       grid.sync();
       if (on) {
-        coarse_own(a, my_agg, my_sc, sh, cr);
+        coarse_own(a, my_agg, my_sc, sh, cr, co_rows);
         for (int k = 0; k < 6; ++k) { co_r[k] = (F)cr[k]; co_s[k] = F(0); }
       }
     }
@@ -1667,7 +1694,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg32(PcgArgs a) {
     double crv[6] = {0, 0, 0, 0, 0, 0};
     if (coarse && my_act == ACT_STEP) {
       double eta[6];
-      coarse_own(a, my_agg, my_sc, sh, eta);
+      coarse_own(a, my_agg, my_sc, sh, eta, co_rows);
       for (int k = 0; k < 6; ++k) {
         co_s[k] = fmaf(beta, co_s[k], (F)eta[k]);
         co_r[k] = fmaf(-alpha, co_s[k], co_r[k]);

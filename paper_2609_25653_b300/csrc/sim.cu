@@ -87,6 +87,7 @@ struct ipcsim {
   double* d_pcg_sc_res = nullptr;  // (n_scenes) relative residual of every scene's last solve
   bool plan_resident = false;
   size_t plan_smem = 0;
+  size_t plan_co_smem = 0;  // shared memory for the coarse rows of every CTA after the plan's (0: none)
   int plan_want_grid = 0, plan_rowg = 0;
   bool pcg_streamed = false;   // never keep the operator in shared memory (sim_pcg_residency)
   bool plan_streamed = false;
@@ -532,6 +533,13 @@ ipc_status pcg_prepare(ipcsim* sim, int fp32, bool contacts = false) {
     sim->plan_streamed = sim->pcg_streamed;
     sim->plan_resident = resident;
     sim->plan_smem = smem;
+    // room for the six coarse rows of every CTA (one solve's largest coarse size) when it keeps the grid
+    sim->plan_co_smem = 0;
+    if (sim->P.preconditioner == IPC_PRECOND_TWO_LEVEL && sim->nf > 0) {
+      const size_t co = 6 * (size_t)COARSE_MAX_UNKNOWNS * (fp32 ? sizeof(float) : sizeof(double));
+      if (smem + co <= pcg_smem_limit() && pcg_max_blocks(PCG_THREADS, fp32, rowg, smem + co) >= sim->plan.grid)
+        sim->plan_co_smem = co;
+    }
     ++sim->plan_stamp;
   }
   launch_layout(sim->st, sim->plan.n_fem_ctas + sim->nab, sim->d_seg, sim->S.bsr_row, sim->Hval, sim->pcg_op,
@@ -741,7 +749,9 @@ ipc_status pcg_launch(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fr
     a.co.x = sim->co_x;
     a.co.part = sim->co_part;
   }
-  CUDA_TRY(launch_pcg(sim->st, sim->plan.grid, PCG_THREADS, a, sim->tune_rowg, sim->plan_smem));
+  a.co.smem_off = (a.co.inv32 && sim->plan_co_smem) ? (int)sim->plan_smem : -1;
+  CUDA_TRY(launch_pcg(sim->st, sim->plan.grid, PCG_THREADS, a, sim->tune_rowg,
+                      sim->plan_smem + (a.co.smem_off >= 0 ? sim->plan_co_smem : 0)));
   if (check) {
     int site = 0;
     CUDA_TRY(cudaMemcpyAsync(&site, sim->pcg_check, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
