@@ -233,55 +233,73 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     peaks_dev = ipcsim.device_peaks()  # FP64 / FP32 FMA roofs of this device, measured before the timed region
     from paper_2609_25653_b300 import autotune
-    tuned_from_cache = autotune.prepare(sim, prec) if not args.no_autotune else None
+    # launch shape: a cached choice; else, for one scene, every shape timed over the sampled steps
+    # (replayed from their saved states, below); for a batch (whose steps are too long to replay eight
+    # times), every shape timed on the first linear system of the first warm-up step
+    tuned_from_cache = autotune.cached(sim, prec) if not args.no_autotune else None
+    tune_replay = tuned_from_cache is False and not batched
+    if tuned_from_cache is False and batched:
+        sim.tuning(autotune_next_step=True)
     for w in range(args.warmup):
         sim.step()
-        if w == 0 and tuned_from_cache is False:
-            autotune.record(sim, prec)  # the first warm-up step timed every PCG launch shape
-    (rowg, bps), _ = sim.tuning()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    sim.profile(True)
-    launches0 = ipcsim.kernel_launches()
-    times, stats, snaps = [], [], []
-    untimed_launches = 0
-    with ClockSampler(local) as clk:
-        for s_idx in timed:
-            # untimed steps up to the next sampled step (the trajectory keeps running between samples)
-            l0 = ipcsim.kernel_launches()
-            sim.profile(False)
-            while sim.step_index < s_idx:
-                sim.step()
-            sim.profile(True, reset=False)
-            untimed_launches += ipcsim.kernel_launches() - l0
-            snaps.append((sim.get_state(), sim.step_index))
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-            stream.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = sim.step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            stats.append(st)
-    torch.cuda.synchronize()
-    launches = ipcsim.kernel_launches() - launches0 - untimed_launches
-    prof, work = sim.profile_read()
-    sim.profile(False)
+        if w == 0 and tuned_from_cache is False and batched:
+            autotune.record(sim, prec)
+    # the trajectory, untimed, saving the state before every sampled step
+    snaps = []
+    for s_idx in timed:
+        while sim.step_index < s_idx:
+            sim.step()
+        snaps.append((sim.get_state(), sim.step_index))
+        sim.step()
     end_state, end_index = sim.get_state(), sim.step_index
-    total_ms = slowest_rank(sum(times))
-    value = world * args.steps * n_sc / (total_ms / 1e3)
 
-    # e2e through the public API with host buffers (transforms in, positions out), the same sampled steps
     def restore(j):
         state, idx = snaps[j]
         sim.set_state(*state)
         if sim.nkb:
             sim.set_kinematic(sc["kin_T"][idx])
         sim.step_index = idx
+
+    def replay(j):
+        restore(j)
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = sim.step()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), st
+
+    tune_ms = None
+    if tune_replay:
+        _, tune_ms = autotune.tune_on_steps(sim, lambda j: replay(j)[0], len(snaps))
+        autotune.record(sim, prec, ms=tune_ms)
+    (rowg, bps), _ = sim.tuning()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    # the timed pass: every sampled step replayed from its saved state (the same work as in the
+    # trajectory: a restarted step is bit-identical), L2 flushed before each
+    sim.profile(True)
+    times, stats = [], []
+    launches = 0
+    with ClockSampler(local) as clk:
+        for j in range(len(snaps)):
+            l0 = ipcsim.kernel_launches()
+            ms, st = replay(j)
+            launches += ipcsim.kernel_launches() - l0
+            times.append(ms)
+            stats.append(st)
+    torch.cuda.synchronize()
+    prof, work = sim.profile_read()
+    sim.profile(False)
+    total_ms = slowest_rank(sum(times))
+    value = world * args.steps * n_sc / (total_ms / 1e3)
+
+    # e2e through the public API with host buffers (transforms in, positions out), the same sampled steps
 
     x_host = np.zeros((sim.nf, 3))
     T_pinned = torch.empty((max(sim.nkb, 1), 12), dtype=torch.float64).pin_memory()
@@ -403,10 +421,14 @@ def run_ours(args):
                 "preconditioner": args.preconditioner, "coarse_rebuild": args.coarse_rebuild,
                 "value_counts": "scene-steps" if batched else "steps",
                 "timed_steps": timed if args.sample == "consecutive" or len(timed) <= 40 else f"{timed[0]}..{timed[-1]}",
-                "timed_sample": ("every step after the warm-up" if args.sample == "consecutive" else
-                                 f"{len(timed)} steps spread over the {n_traj}-step trajectory (untimed steps between)"),
+                "timed_sample": ("every step after the warm-up, each replayed from its saved state" if args.sample == "consecutive" else
+                                 f"{len(timed)} steps spread over the {n_traj}-step trajectory, each replayed "
+                                 "from its state saved in one untimed pass"),
                 "pcg_threads_per_row": rowg, "pcg_blocks_per_sm": bps,
-                "pcg_shape": "cached" if tuned_from_cache else ("autotuned" if tuned_from_cache is False else "default"),
+                "pcg_shape": "cached" if tuned_from_cache else (("autotuned over the sampled steps" if tune_replay else
+                                                                  "autotuned on the first linear system")
+                                                                 if tuned_from_cache is False else "default"),
+                "pcg_shape_ms": [round(m, 2) for m in tune_ms] if tune_ms else None,
                 "newton_iters_per_step": round(sum(newton) / len(newton), 2),
                 "pcg_iters_per_step": round(sum(s["pcg_iters_total"] for s in stats) / len(stats), 1),
                 "pcg_unconverged_solves": int(sum(s["pcg_unconverged"] for s in stats)),

@@ -246,10 +246,6 @@ __global__ void k_coarse_gj(double* __restrict__ A, const long long* __restrict_
   }
 }
 
-__global__ void k_zero(size_t n, double* __restrict__ p) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = 0.0;
-}
-
 }  // namespace
 
 void coarse_layout(const PcgPlan& P, int nf, CoarseLayout& L) {

@@ -161,6 +161,13 @@ struct DevScene {
   const double* mu;          // (nt)
   const double* lam;         // (nt) model parameter (first Lame + mu)
   const int* tet_blk;        // (nt, 16) BSR block of (a, b)
+  // elastic gathers: the FEM BSR blocks (the first nfb) with their tets (code tet << 4 | a << 2 | b, in tet
+  // order), and every FEM node with its tets (code tet << 2 | a)
+  int nfb;
+  const int* eg_blk_ptr;
+  const int* eg_blk_ent;
+  const int* eg_node_ptr;
+  const int* eg_node_ent;
   const int* vkind;          // (nv)
   const int* vbody;          // (nv) body id (FEM bodies, then ABD, then kinematic)
   const int* vabd;           // (nv) ABD body index for ABD vertices, else -1

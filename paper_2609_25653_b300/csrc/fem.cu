@@ -378,10 +378,13 @@ __device__ inline void snh_projected_hessian_f32(const d3* fd, double mu_d, doub
 // its gradient and PSD-projected Hessian scattered into the BSR matrix.
 // scale = dt^2 for the incremental potential; mode: 0 energy only, 1 + gradient, 2 + Hessian.
 // F32H: the projected Hessian in FP32 (mixed precision); energy and gradient always FP64.
+// Outputs: g (accumulators) or tG (the tet's 12 gradient entries, per tet); tU (the upper triangle of
+// the tet's 12x12, 78 values per tet, row by row) and/or tetH (the full 12x12, per tet).
 template <bool F32H>
 __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __restrict__ xv, double scale, int mode,
-                                                 int project, acc_t* __restrict__ g, acc_t* __restrict__ Hval,
-                                                 double* __restrict__ tetH, acc_t* __restrict__ E) {
+                                                 int project, acc_t* __restrict__ g, double* __restrict__ tG,
+                                                 double* __restrict__ tU, double* __restrict__ tetH,
+                                                 acc_t* __restrict__ E) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   double energy = 0.0;
   if (e < S.nt) {
@@ -414,24 +417,24 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
       for (int a = 0; a < 4; ++a) {
         d3 ga = Cc[a][0] * Pc[0] + Cc[a][1] * Pc[1] + Cc[a][2] * Pc[2];
         if (g) acc_add3(g, id[a], sv * ga, S.err);
+        if (tG) {
+          tG[12 * (size_t)e + 3 * a] = sv * ga.x;
+          tG[12 * (size_t)e + 3 * a + 1] = sv * ga.y;
+          tG[12 * (size_t)e + 3 * a + 2] = sv * ga.z;
+        }
       }
       if (mode >= 2 && project) {
         using HC = typename std::conditional<F32H, float, double>::type;
         HC H12[144];
         if constexpr (F32H) snh_projected_hessian_f32(f, mu, lam, Cc, sv, H12);
         else snh_projected_hessian(f, mu, lam, Cc, sv, H12);
-        for (int a = 0; a < 4; ++a)
-          for (int b = 0; b < 4; ++b) {
-            if (Hval) {
-              acc_t* dst = Hval + 27 * (size_t)S.tet_blk[16 * e + 4 * a + b];
-              for (int i = 0; i < 3; ++i)
-                for (int k = 0; k < 3; ++k) acc_add(dst + 3 * (3 * i + k), (double)H12[12 * (3 * a + i) + 3 * b + k], S.err);
-            }
-            if (tetH)
-              for (int i = 0; i < 3; ++i)
-                for (int k = 0; k < 3; ++k)
-                  tetH[144 * (size_t)e + 12 * (3 * a + i) + 3 * b + k] = H12[12 * (3 * a + i) + 3 * b + k];
-          }
+        if (tU) {
+          double* u = tU + 78 * (size_t)e;
+          for (int r = 0, o = 0; r < 12; ++r)
+            for (int c = r; c < 12; ++c) u[o++] = (double)H12[12 * r + c];
+        }
+        if (tetH)
+          for (int i = 0; i < 144; ++i) tetH[144 * (size_t)e + i] = (double)H12[i];
       } else if (mode >= 2) {
         double H[81];
         double gv[9] = {cf[0].x, cf[0].y, cf[0].z, cf[1].x, cf[1].y, cf[1].z, cf[2].x, cf[2].y, cf[2].z};
@@ -460,10 +463,13 @@ __global__ void __launch_bounds__(128) k_elastic(DevScene S, const double* __res
                   for (int l = 0; l < 3; ++l) s += Cc[a][j] * Cc[b][l] * H[9 * (3 * j + i) + 3 * l + k];
                 blk[3 * i + k] = sv * s;
               }
-            if (Hval) {
-              acc_t* dst = Hval + 27 * (size_t)S.tet_blk[16 * e + 4 * a + b];
-              for (int q = 0; q < 9; ++q) acc_add(dst + 3 * q, blk[q], S.err);
-            }
+            // upper triangle of the tet's 12x12: rows 3a + i <= columns 3b + k
+            if (tU)
+              for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) {
+                  const int r = 3 * a + i, c = 3 * b + k;
+                  if (r <= c) tU[78 * (size_t)e + 12 * r - r * (r - 1) / 2 + (c - r)] = blk[3 * i + k];
+                }
             if (tetH)
               for (int i = 0; i < 3; ++i)
                 for (int k = 0; k < 3; ++k) tetH[144 * (size_t)e + 12 * (3 * a + i) + 3 * b + k] = blk[3 * i + k];
@@ -738,13 +744,61 @@ void launch_inertia(cudaStream_t st, const DevScene& S, const double* z, const d
   if (S.n_nodes) { k_inertia<<<nb(S.n_nodes, 256), 256, 0, st>>>(S, z, z_tilde, g, E, want_grad); count_launch(); }
 }
 void launch_elastic(cudaStream_t st, const DevScene& S, const double* xv, double scale, int mode, int project,
-                    acc_t* g, acc_t* Hval, double* tetH, acc_t* E, int hess_fp32) {
+                    acc_t* g, double* tetH, acc_t* E, int hess_fp32) {
   if (!S.nt) return;
   if (hess_fp32 && mode >= 2 && project)
-    k_elastic<true><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+    k_elastic<true><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, nullptr, nullptr, tetH, E);
   else
-    k_elastic<false><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, Hval, tetH, E);
+    k_elastic<false><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, mode, project, g, nullptr, nullptr, tetH, E);
   count_launch();
+}
+
+// FEM BSR blocks from the tets' stored upper triangles: Hval[k] = Hconst[k] + the 3x3 parts of the tets of
+// block k, added in tet order (one thread per value; no atomics, the same order in every run)
+__global__ void k_elastic_gather_H(DevScene S, const double* __restrict__ tU, const double* __restrict__ Hc,
+                                   double* __restrict__ Hval) {
+  const size_t n = 9 * (size_t)S.nfb;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i / 9), q = (int)(i - 9 * (size_t)k), bi = q / 3, bj = q - 3 * (q / 3);
+    double sum = 0.0;
+    for (int l = S.eg_blk_ptr[k]; l < S.eg_blk_ptr[k + 1]; ++l) {
+      const int code = S.eg_blk_ent[l], e = code >> 4, a = (code >> 2) & 3, b = code & 3;
+      const int row = 3 * a + bi, col = 3 * b + bj;
+      const int r = row < col ? row : col, c = row < col ? col : row;
+      sum += tU[78 * (size_t)e + 12 * r - r * (r - 1) / 2 + (c - r)];
+    }
+    Hval[i] = Hc[i] + sum;
+  }
+}
+
+// FEM node gradients from the tets' stored gradients, added in tet order, then into the accumulators
+__global__ void k_elastic_gather_g(DevScene S, const double* __restrict__ tG, acc_t* __restrict__ g) {
+  const int n = 3 * S.nf;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int v = i / 3, c = i - 3 * (i / 3);
+    double sum = 0.0;
+    for (int l = S.eg_node_ptr[v]; l < S.eg_node_ptr[v + 1]; ++l) {
+      const int code = S.eg_node_ent[l];
+      sum += tG[12 * (size_t)(code >> 2) + 3 * (code & 3) + c];
+    }
+    acc_add(g + 3 * (size_t)i, sum, S.err);
+  }
+}
+
+void launch_elastic_assembly(cudaStream_t st, const DevScene& S, const double* xv, double scale, int project, acc_t* g,
+                             const double* Hconst, double* Hval, acc_t* E, int hess_fp32, double* tU, double* tG) {
+  if (S.nt) {
+    if (hess_fp32 && project)
+      k_elastic<true><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, 2, project, nullptr, tG, tU, nullptr, E);
+    else
+      k_elastic<false><<<nb(S.nt, 128), 128, 0, st>>>(S, xv, scale, 2, project, nullptr, tG, tU, nullptr, E);
+    k_elastic_gather_g<<<stride_grid(3LL * S.nf, 256, 8), 256, 0, st>>>(S, tG, g);
+    count_launch(2);
+  }
+  if (S.nfb) {  // FEM nodes without tets still take their mass and stitch blocks
+    k_elastic_gather_H<<<stride_grid(9LL * S.nfb, 256, 8), 256, 0, st>>>(S, tU, Hconst, Hval);
+    count_launch();
+  }
 }
 void launch_stitch(cudaStream_t st, const DevScene& S, const double* xv, const double* stitch_hat, double k_c,
                    double scale, int mode, acc_t* g, acc_t* E) {

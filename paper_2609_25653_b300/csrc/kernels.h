@@ -188,7 +188,11 @@ void launch_inertia(cudaStream_t, const DevScene&, const double* z, const double
                     int want_grad);
 // hess_fp32: the projected Hessian in FP32 (mixed precision); energy and gradient stay FP64
 void launch_elastic(cudaStream_t, const DevScene&, const double* xv, double scale, int mode, int project, acc_t* g,
-                    acc_t* Hval, double* tetH, acc_t* E, int hess_fp32 = 0);
+                    double* tetH, acc_t* E, int hess_fp32 = 0);
+// The Newton assembly of the elastic term: gradient into g, and the FEM BSR blocks written as
+// Hval = Hconst + the tets' blocks (gathered in tet order from the per-tet scratch tU (78 nt), tG (12 nt))
+void launch_elastic_assembly(cudaStream_t, const DevScene&, const double* xv, double scale, int project, acc_t* g,
+                             const double* Hconst, double* Hval, acc_t* E, int hess_fp32, double* tU, double* tG);
 void launch_stitch(cudaStream_t, const DevScene&, const double* xv, const double* stitch_hat, double k_c, double scale,
                    int mode, acc_t* g, acc_t* E);
 void launch_abd_orth(cudaStream_t, const DevScene&, const double* z, double kappa_A, double scale, int mode, int project,

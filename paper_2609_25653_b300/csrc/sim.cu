@@ -62,6 +62,8 @@ struct ipcsim {
   double *xv = nullptr, *xv_t = nullptr, *xv_trial = nullptr, *z_trial = nullptr, *xk_trial = nullptr;
   double *g = nullptr, *gdir = nullptr, *rhs = nullptr, *p = nullptr, *pD = nullptr, *pv = nullptr;
   double *Hconst = nullptr, *Hval = nullptr, *Dc = nullptr, *Dinv = nullptr;
+  double *el_tU = nullptr, *el_tG = nullptr;  // per-tet elastic Hessian (upper triangle) and gradient
+  int nfb = 0;                                 // FEM BSR blocks (rows of the FEM nodes come first)
   // order-independent accumulators of one assembly: gradient, BSR values, preconditioner diagonal,
   // Dirichlet term, adjoint gradient (three words per value)
   acc_t *g_acc = nullptr, *H_acc = nullptr, *Dc_acc = nullptr, *gdir_acc = nullptr, *gz_acc = nullptr;
@@ -845,20 +847,22 @@ void active_set(ipcsim* sim, const double* xv) {
 }
 
 // Clear the accumulators of one assembly (gradient, BSR values, preconditioner diagonal, Dirichlet term).
+// The FEM blocks are written whole by the elastic assembly; only the ABD blocks accumulate.
 ipc_status assembly_begin(ipcsim* sim) {
   const size_t ndof = 3 * (size_t)sim->n_nodes;
   CUDA_TRY(cudaMemsetAsync(sim->g_acc, 0, sizeof(acc_t) * 3 * ndof, sim->st));
-  CUDA_TRY(cudaMemsetAsync(sim->H_acc, 0, sizeof(acc_t) * 27 * (size_t)sim->nnzb, sim->st));
+  CUDA_TRY(cudaMemsetAsync(sim->H_acc + 27 * (size_t)sim->nfb, 0, sizeof(acc_t) * 27 * (size_t)(sim->nnzb - sim->nfb),
+                           sim->st));
   CUDA_TRY(cudaMemsetAsync(sim->Dc_acc, 0, sizeof(acc_t) * 27 * (size_t)sim->n_nodes, sim->st));
   CUDA_TRY(cudaMemsetAsync(sim->gdir_acc, 0, sizeof(acc_t) * 3 * ndof, sim->st));
   return IPC_OK;
 }
 
-// The assembled values: g, Hval = Hconst + the accumulated Hessian terms, Dc, gdir.
+// The assembled values: g, the ABD blocks Hval = Hconst + the accumulated Hessian terms, Dc, gdir.
 void assembly_end(ipcsim* sim) {
-  const size_t ndof = 3 * (size_t)sim->n_nodes;
+  const size_t ndof = 3 * (size_t)sim->n_nodes, f = 9 * (size_t)sim->nfb;
   launch_acc_finalize(sim->st, ndof, sim->g_acc, nullptr, sim->g);
-  launch_acc_finalize(sim->st, 9 * (size_t)sim->nnzb, sim->H_acc, sim->Hconst, sim->Hval);
+  launch_acc_finalize(sim->st, 9 * (size_t)sim->nnzb - f, sim->H_acc + 3 * f, sim->Hconst + f, sim->Hval + f);
   launch_acc_finalize(sim->st, 9 * (size_t)sim->n_nodes, sim->Dc_acc, nullptr, sim->Dc);
   launch_acc_finalize(sim->st, ndof, sim->gdir_acc, nullptr, sim->gdir);
 }
@@ -945,7 +949,7 @@ ipc_status energy_at(ipcsim* sim, const double* zq, const double* xkq, double* x
     CUDA_TRY(cudaMemcpyAsync(&sim->sc_dev->min_s, &big, sizeof(big), cudaMemcpyHostToDevice, sim->st));
     active_set(sim, xvq);
     launch_inertia(sim->st, S, zq, sim->z_tilde, nullptr, sim->sc_dev->E + 0, 0);
-    launch_elastic(sim->st, S, xvq, dt2, 0, 0, nullptr, nullptr, nullptr, sim->sc_dev->E + 3);
+    launch_elastic(sim->st, S, xvq, dt2, 0, 0, nullptr, nullptr, sim->sc_dev->E + 3);
     launch_barrier(sim->st, pair_grid(sim->cap), S, xvq, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
                    sim->kappa, dt2, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, sim->sc_dev->E + 6,
                    &sim->sc_dev->min_s);
@@ -1342,6 +1346,26 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
         const int bp = D->joint_body_host[2 * j + p / 4], bq = D->joint_body_host[2 * j + q / 4];
         if (bp >= 0 && bq >= 0) jt_blk[64 * j + 8 * p + q] = find_blk(nf + 4 * bp + p % 4, nf + 4 * bq + q % 4);
       }
+  // elastic gathers: tets of every FEM block and of every FEM node, in tet order
+  const int nfb = row_ptr[nf];
+  sim->nfb = nfb;
+  if (nt >= (1 << 27)) return fail(IPC_ERR_ARG, "too many tets (at most 2^27)");
+  std::vector<int> eg_blk_ptr(nfb + 1, 0), eg_blk_ent(16 * (size_t)nt), eg_node_ptr(nf + 1, 0), eg_node_ent(4 * (size_t)nt);
+  for (int e = 0; e < nt; ++e)
+    for (int a = 0; a < 4; ++a) {
+      ++eg_node_ptr[D->tets_host[4 * e + a] + 1];
+      for (int b = 0; b < 4; ++b) ++eg_blk_ptr[tet_blk[16 * e + 4 * a + b] + 1];
+    }
+  for (int k = 0; k < nfb; ++k) eg_blk_ptr[k + 1] += eg_blk_ptr[k];
+  for (int v = 0; v < nf; ++v) eg_node_ptr[v + 1] += eg_node_ptr[v];
+  {
+    std::vector<int> cb(eg_blk_ptr.begin(), eg_blk_ptr.end() - 1), cn(eg_node_ptr.begin(), eg_node_ptr.end() - 1);
+    for (int e = 0; e < nt; ++e)
+      for (int a = 0; a < 4; ++a) {
+        eg_node_ent[cn[D->tets_host[4 * e + a]]++] = (e << 2) | a;
+        for (int b = 0; b < 4; ++b) eg_blk_ent[cb[tet_blk[16 * e + 4 * a + b]]++] = (e << 4) | (a << 2) | b;
+      }
+  }
   // constant part: mass blocks and the stitch Hessian dt^2 k_c I
   std::vector<double> Hc(9 * (size_t)nnzb, 0.0);
   for (int v = 0; v < nf; ++v)
@@ -1385,6 +1409,11 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
     sim->h_nu.assign(D->nu_host, D->nu_host + nt);
     sim->h_logE.assign(D->logE_host, D->logE_host + nt);
     if ((s = upload(sim, &ip, tet_blk))) return fail(s, ""); S.tet_blk = ip;
+    S.nfb = nfb;
+    if ((s = upload(sim, &ip, eg_blk_ptr))) return fail(s, ""); S.eg_blk_ptr = ip;
+    if ((s = upload(sim, &ip, eg_blk_ent))) return fail(s, ""); S.eg_blk_ent = ip;
+    if ((s = upload(sim, &ip, eg_node_ptr))) return fail(s, ""); S.eg_node_ptr = ip;
+    if ((s = upload(sim, &ip, eg_node_ent))) return fail(s, ""); S.eg_node_ent = ip;
     if ((s = upload(sim, &ip, vkind))) return fail(s, ""); S.vkind = ip;
     if ((s = upload(sim, &ip, vbody))) return fail(s, ""); S.vbody = ip;
     if ((s = upload(sim, &ip, vabd))) return fail(s, ""); S.vabd = ip;
@@ -1493,6 +1522,8 @@ static ipc_status create_impl(const ipc_scene_desc* D, const ipc_params* params,
   if ((s = dalloc(sim, &sim->Hval, 9 * (size_t)nnzb))) return fail(s, "");
   if ((s = dalloc(sim, &sim->Dc, 9 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->H_acc, 27 * (size_t)nnzb))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->el_tU, 78 * (size_t)nt))) return fail(s, "");
+  if ((s = dalloc(sim, &sim->el_tG, 12 * (size_t)nt))) return fail(s, "");
   if ((s = dalloc(sim, &sim->Dc_acc, 27 * (size_t)n_nodes))) return fail(s, "");
   if ((s = dalloc(sim, &sim->g_acc, 3 * (size_t)ndof))) return fail(s, "");
   if ((s = dalloc(sim, &sim->gdir_acc, 3 * (size_t)ndof))) return fail(s, "");
@@ -1822,8 +1853,8 @@ ipc_status step_body(ipcsim* sim, const double* kin_T_next, ipc_step_stats& st, 
     }
     launch_inertia(cs, S, sim->z, sim->z_tilde, sim->g_acc, sim->sc_dev->E + 0, 1);
     prof_begin(sim, PROF_ELASTIC);
-    launch_elastic(cs, S, sim->xv, dt2, 2, 1, sim->g_acc, sim->H_acc, nullptr, sim->sc_dev->E + 3,
-                   P.precision == IPC_PREC_MIXED);
+    launch_elastic_assembly(cs, S, sim->xv, dt2, 1, sim->g_acc, sim->Hconst, sim->Hval, sim->sc_dev->E + 3,
+                            P.precision == IPC_PREC_MIXED, sim->el_tU, sim->el_tG);
     prof_end(sim, PROF_ELASTIC);
     launch_stitch(cs, S, sim->xv, sim->stitch_hat, sim->k_c, dt2, 1, sim->g_acc, sim->sc_dev->E + 12);
     launch_abd_orth(cs, S, sim->z, P.kappa_A, dt2, 2, 1, sim->g_acc, sim->H_acc, sim->sc_dev->E + 15);
@@ -2273,7 +2304,8 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     if ((s = assembly_begin(sim))) return s;
     if (nk3) CUDA_TRY(cudaMemsetAsync(sim->pD, 0, sizeof(double) * nk3, cs));
     cull(sim, sim->xv);
-    launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g_acc, sim->H_acc, nullptr, sim->sc_dev->E + 3);
+    launch_elastic_assembly(cs, S, sim->xv, dt2, 0, sim->g_acc, sim->Hconst, sim->Hval, sim->sc_dev->E + 3, 0,
+                            sim->el_tU, sim->el_tG);
     launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g_acc, sim->H_acc, sim->sc_dev->E + 15);
     launch_joints(cs, S, z_next, dt2, 2, sim->g_acc, sim->H_acc, sim->sc_dev->E + 18);
     launch_barrier(cs, pair_grid(sim->cap), S, sim->xv, sim->rec, &sim->sc_dev->n_pairs, sim->cap, sim->sh,
@@ -2292,10 +2324,10 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     // the ABD coupling list of the unprojected Hessian (grown until it fits)
     CUDA_TRY(cudaMemsetAsync(&sim->sc_dev->flags, 0, sizeof(int), cs));
     if (tries > 0) {
-      // a retry: rebuild the BSR values without the partial contact blocks of the overflowed pass (the
-      // gradient accumulated again is not used by the adjoint)
-      CUDA_TRY(cudaMemsetAsync(sim->H_acc, 0, sizeof(acc_t) * 27 * sim->nnzb, cs));
-      launch_elastic(cs, S, sim->xv, dt2, 2, 0, sim->g_acc, sim->H_acc, nullptr, sim->sc_dev->E + 3);
+      // a retry: rebuild the ABD blocks without the partial contact blocks of the overflowed pass (the
+      // gradient accumulated again is not used by the adjoint; the FEM blocks hold no contact terms)
+      CUDA_TRY(cudaMemsetAsync(sim->H_acc + 27 * (size_t)sim->nfb, 0, sizeof(acc_t) * 27 * (size_t)(sim->nnzb - sim->nfb),
+                               cs));
       launch_abd_orth(cs, S, z_next, P.kappa_A, dt2, 2, 0, sim->g_acc, sim->H_acc, sim->sc_dev->E + 15);
       launch_joints(cs, S, z_next, dt2, 2, sim->g_acc, sim->H_acc, sim->sc_dev->E + 18);
     }
@@ -2452,7 +2484,7 @@ ipc_status sim_eval_elastic(ipcsim* sim, const double* x_dev, int project, doubl
   acc_t* Eacc = sim->sc_dev->E + 21;
   CUDA_TRY(cudaMemsetAsync(Eacc, 0, 3 * sizeof(acc_t), sim->st));
   CUDA_TRY(cudaMemsetAsync(sim->g_acc, 0, sizeof(acc_t) * 9 * (size_t)sim->nf, sim->st));
-  launch_elastic(sim->st, sim->S, x_dev, 1.0, H_dev ? 2 : 1, project, sim->g_acc, nullptr, H_dev, Eacc);
+  launch_elastic(sim->st, sim->S, x_dev, 1.0, H_dev ? 2 : 1, project, sim->g_acc, H_dev, Eacc);
   launch_acc_finalize(sim->st, 3 * (size_t)sim->nf, sim->g_acc, nullptr, grad_dev);
   launch_acc_finalize(sim->st, 1, Eacc, nullptr, E_dev);
   CUDA_TRY(cudaStreamSynchronize(sim->st));
