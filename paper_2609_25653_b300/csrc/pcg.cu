@@ -600,22 +600,52 @@ struct Shared {
 };
 
 // Sum over the CTA of N <= 6 per-thread values of type T; results in
-// sh.out[0..N) (as FP64) for every thread.
+// sh.out[0..N) (as FP64) for every thread.  Only the first `active` threads
+// may hold non-zero values (the others are left out, which changes no bit).
+// FP64: a pairwise tree over the thread index, all N values at once: at width
+// w, (value j, slot t < w) adds slot t + w, and the N w additions of a level
+// are shared out over every thread.  This part issues about 2 FP64 lanes per
+// clock per SM, so a warp-wide FP64 add holds its sub-partition's FP64 unit
+// for dozens of cycles: left to one warp (8 adds per lane, then 5 shuffle
+// levels: 13 warp-wide adds per value on one sub-partition) the sums of an
+// iteration were a large part of its critical path; the tree issues about
+// 255 useful lane additions per value over all four sub-partitions.
+// FP32: warp 0 adds 8 values per lane, then 5 shuffle levels.
 template <int N, typename T>
-__device__ inline void cta_sum(const T (&v)[N], Shared& sh) {
+__device__ inline void cta_sum(const T (&v)[N], Shared& sh, int active = PCG_THREADS_MAX) {
   T (*vals)[PCG_THREADS_MAX] = reinterpret_cast<T (*)[PCG_THREADS_MAX]>(&sh.vals[0][0]);
+  if constexpr (sizeof(T) == 8) {
+    const int nt = blockDim.x;
+    active = max(1, min(active, nt));
+    int w = 1;
+    while (w < active) w <<= 1;  // w <= PCG_THREADS_MAX
+    for (int t = threadIdx.x; t < w; t += nt)
 #pragma unroll
-  for (int j = 0; j < N; ++j) vals[j][threadIdx.x] = v[j];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
+      for (int j = 0; j < N; ++j) vals[j][t] = (t == (int)threadIdx.x && t < active) ? v[j] : T(0);
+    __syncthreads();
+    for (int lw = 31 - __clz(w) - 1; lw >= 0; --lw) {
+      const int h = 1 << lw;
+      for (int f = threadIdx.x; f < N * h; f += nt) {
+        const int j = f >> lw, t = f & (h - 1);
+        vals[j][t] += vals[j][t + h];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x < N) sh.out[threadIdx.x] = (double)vals[threadIdx.x][0];
+  } else {
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T t = T(0);
-      for (int k = lane; k < (int)blockDim.x; k += 32) t += vals[j][k];
+    for (int j = 0; j < N; ++j) vals[j][threadIdx.x] = v[j];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if (lane == 0) sh.out[j] = (double)t;
+      for (int j = 0; j < N; ++j) {
+        T t = T(0);
+        for (int k = lane; k < (int)blockDim.x; k += 32) t += vals[j][k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) sh.out[j] = (double)t;
+      }
     }
   }
   __syncthreads();
@@ -643,8 +673,8 @@ __device__ inline void load_partials(const T* rep, int nblk, Partials<T>& P) {
 // This CTA's 3 partial sums, written to every replica.
 template <typename T>
 __device__ inline void write_partials(T* rep0 /* replica 0 of this parity, [3][grid] */, size_t rep_stride, int nblk,
-                                      Shared& sh, const T (&v)[3]) {
-  cta_sum<3, T>(v, sh);
+                                      Shared& sh, const T (&v)[3], int active = PCG_THREADS_MAX) {
+  cta_sum<3, T>(v, sh, active);
   if (threadIdx.x < 3 * PCG_REPLICAS) {
     int rep = threadIdx.x / 3, j = threadIdx.x % 3;
     rep0[rep * rep_stride + (size_t)j * nblk + blockIdx.x] = (T)sh.out[j];
@@ -729,7 +759,7 @@ __device__ inline void coarse_restrict(const PcgArgs& a, int agg, int r0, int r1
       }
     }
   }
-  cta_sum<6, double>(t, sh);
+  cta_sum<6, double>(t, sh, agg >= 0 ? r1 - r0 : 1);
   if (threadIdx.x < 6 && agg >= 0) a.co.part[6 * (size_t)blockIdx.x + threadIdx.x] = sh.out[threadIdx.x];
   __syncthreads();
 }
@@ -769,7 +799,7 @@ __device__ inline void coarse_own_t(const PcgArgs& a, const M* inv, int agg, int
     }
   }
   const double t[6] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3], (double)acc[4], (double)acc[5]};
-  cta_sum<6, double>(t, sh);
+  cta_sum<6, double>(t, sh, (agg >= 0 && s >= 0) ? a.co.solve_n[s] : 1);
 #pragma unroll
   for (int k = 0; k < 6; ++k) res[k] = sh.out[k];
   __syncthreads();
@@ -1059,6 +1089,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   }
   // preconditioner block of node i (owned by this CTA)
   auto Dof = [&](int i) -> const M* { return (fem_cta ? dinv_loc + 9 * (size_t)(i - r0) : dinvM + 9 * (size_t)i); };
+  // threads that own a node in the first pass of for_nodes (the others hold zero partial sums)
+  const int n_act = fem_cta ? r1 - r0 : 4;
   // coarse level: this CTA's aggregate (its FEM rows), -1 without one; the coarse images of w and z of
   // the CTA's aggregate, identical in every thread
   const bool coarse = a.co.inv32 != nullptr;
@@ -1238,7 +1270,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         pv[1] += y[0] * u0 + y[1] * u1 + y[2] * u2;
         pv[2] += rr0 * rr0 + rr1 * rr1 + rr2 * rr2;
       });
-      write_partials<double>(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv);
+      write_partials<double>(partT + (size_t)par * 3 * nblk, repT, nblk, sh, pv, n_act);
     }
     grid.sync();
   };
@@ -1357,7 +1389,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
         pv[1] += wn[0] * un[0] + wn[1] * un[1] + wn[2] * un[2];
         pv[2] += rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
       });
-      write_partials<double>(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv);
+      write_partials<double>(partT + (size_t)(par ^ 1) * 3 * nblk, repT, nblk, sh, pv, n_act);
     }
     bool my_restart = false;
     if (any_refresh) {
