@@ -685,7 +685,7 @@ __device__ inline void write_partials(T* rep0 /* replica 0 of this parity, [3][g
 // Totals of N per-CTA values for every solve, in a fixed order so that every
 // CTA holds bit-identical totals.  One solve: the CTA sum over all CTAs into
 // sh.out (the first 2 x blockDim values may already be in P); several: one
-// warp per scene over that scene's CTAs into sh.tot[j][s].  Every thread must
+// thread per value and scene over that scene's CTAs into sh.tot[j][s].  Every thread must
 // call it; read the results with scene_total.
 template <int N, typename T>
 __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] */, int nblk, Shared& sh,
@@ -707,25 +707,14 @@ __device__ inline void scene_totals(const PcgArgs& a, const T* rep /* [N][grid] 
     cta_sum<N, T>(v, sh);
     return;
   }
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int sc = threadIdx.x >> 5; sc < a.n_psc; sc += nw) {
+  // one thread per (value, scene) adds the scene's few CTA values in CTA order (a warp per scene with a
+  // shuffle tree per value issued far more FP64 adds than the sums need, on few sub-partitions)
+  for (int idx = threadIdx.x; idx < N * a.n_psc; idx += blockDim.x) {
+    const int j = idx / a.n_psc, sc = idx - j * a.n_psc;
     const int k0 = a.sc_ptr[sc], k1 = a.sc_ptr[sc + 1];
-    T v[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = T(0);
-    for (int k = k0 + lane; k < k1; k += 32) {
-      const int c = a.sc_cta[k];
-#pragma unroll
-      for (int j = 0; j < N; ++j) v[j] += rep[(size_t)j * nblk + c];
-    }
-#pragma unroll
-    for (int j = 0; j < N; ++j)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
-    if (lane == 0) {
-#pragma unroll
-      for (int j = 0; j < N; ++j) sh.tot[j][sc] = (double)v[j];
-    }
+    T v = T(0);
+    for (int k = k0; k < k1; ++k) v += rep[(size_t)j * nblk + a.sc_cta[k]];
+    sh.tot[j][sc] = (double)v;
   }
   __syncthreads();
 }
