@@ -146,6 +146,7 @@ struct PcgArgs {
   void* partial;             // pcg_partial_doubles(grid) doubles
   double rtol;
   int max_iter;
+  int max_replace;           // true-residual restarts before the solve gives up (<= 0: 10)
   int fp32;
   int* out;                  // [iterations, status, true-residual restarts]
   double* res;               // [relative residual]

@@ -1161,7 +1161,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PcgArgs a) {
   // ---- per-scene state, held by the scene's decision thread
   constexpr bool F32 = sizeof(M) == 4;
   constexpr int STALL = 80;  // iterations without a new minimum of the recursive residual before a refresh
-  const int max_replace = 10;
+  const int max_replace = a.max_replace > 0 ? a.max_replace : 10;
   double bb = 0.0, tol2_true = 0.0, sigma = 1.0, unscale = 1.0, tt = 0.0, tol_in2 = 0.0;
   double alpha_old = 1.0, gamma_old = 1.0, rr_best = 0.0;
   int it = 0, it_best = 0, replaced = 0, status = 0;

@@ -63,6 +63,7 @@ struct ipcsim {
   double *g = nullptr, *gdir = nullptr, *rhs = nullptr, *p = nullptr, *pD = nullptr, *pv = nullptr;
   double *Hconst = nullptr, *Hval = nullptr, *Dc = nullptr, *Dinv = nullptr;
   double *el_tU = nullptr, *el_tG = nullptr;  // per-tet elastic Hessian (upper triangle) and gradient
+  int pcg_max_replace = 10;                    // true-residual restarts of a PCG solve
   int nfb = 0;                                 // FEM BSR blocks (rows of the FEM nodes come first)
   // order-independent accumulators of one assembly: gradient, BSR values, preconditioner diagonal,
   // Dirichlet term, adjoint gradient (three words per value)
@@ -717,6 +718,7 @@ ipc_status pcg_launch(ipcsim* sim, int fp32, double rtol, int max_iter, int n_fr
   a.partial = sim->partial;
   a.rtol = rtol;
   a.max_iter = max_iter;
+  a.max_replace = sim->pcg_max_replace;
   a.fp32 = fp32;
   a.out = sim->sc_dev->pcg_out;
   a.res = &sim->sc_dev->pcg_res;
@@ -2344,7 +2346,25 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
     build_incidence(sim, n_fric_adj);
     if ((s = pcg_prepare(sim, 0))) return s;
     if ((s = coarse_setup(sim, 0, n_fric_adj))) return s;
-    if ((s = pcg_run(sim, 0, 1e-12, 10 * ndof + 1000, n_fric_adj))) return s;
+    // rtol 1e-12 on the unprojected (possibly indefinite) Hessian: more true-residual restarts than a
+    // Newton solve, and a two-level solve that spent them above 1e-10 is repeated with block Jacobi alone
+    const int max_it = 10 * ndof + 1000;
+    sim->pcg_max_replace = 40;
+    s = pcg_run(sim, 0, 1e-12, max_it, n_fric_adj);
+    if (!s && sim->co_ok) {
+      ipcsim::Scal* h = sim->sc_host;
+      if (cudaMemcpyAsync(h->pcg_out, sim->sc_dev->pcg_out, sizeof(h->pcg_out), cudaMemcpyDeviceToHost, cs) ||
+          cudaMemcpyAsync(&h->pcg_res, &sim->sc_dev->pcg_res, sizeof(double), cudaMemcpyDeviceToHost, cs) ||
+          cudaStreamSynchronize(cs)) {
+        s = IPC_ERR_CUDA;
+        sim->err = "adjoint PCG status copy failed";
+      } else if (h->pcg_out[1] == 3 && !(h->pcg_res <= 1e-10)) {
+        ++sim->pcg_fallbacks;
+        s = pcg_launch(sim, 0, 1e-12, max_it, n_fric_adj, false);
+      }
+    }
+    sim->pcg_max_replace = 10;
+    if (s) return s;
     // the coarse level now belongs to this adjoint's Hessian: the next step builds its own
     sim->co_steps_since_build = 1 << 20;
   }
@@ -2372,7 +2392,9 @@ ipc_status sim_adjoint(ipcsim* sim, const double* z_t, const double* zd_t, const
   if ((s = sync_scalars(sim))) return s;
   CUDA_TRY(cudaGetLastError());
   if (sim->sc_host->pcg_out[1] == 3 && !(sim->sc_host->pcg_res <= 1e-10)) {
-    sim->err = "adjoint PCG stopped at relative residual " + std::to_string(sim->sc_host->pcg_res);
+    char buf[32];
+    snprintf(buf, sizeof buf, "%.3e", sim->sc_host->pcg_res);
+    sim->err = std::string("adjoint PCG stopped at relative residual ") + buf;
     return IPC_ERR_PCG;
   }
   if (sim->sc_host->pcg_out[1] == 3) sim->sc_host->pcg_out[1] = 0;
