@@ -557,8 +557,8 @@ def run_render(args):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     img = out.cpu().numpy()
-    np.save(os.path.join(ROOT, "gpurun_out", "render_frame.npy"), img) if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    if args.frame_out:
+        np.save(args.frame_out, img)  # the last frame, (height, width, 3) linear RGB
     print(json.dumps({"workload": "render_" + sc["name"], "triangles": int(len(tris)), "width": cam[1],
                       "height": cam[2], "spp": 32, "max_depth": 2, "n_shadow": 8, "frames": args.steps,
                       "ms_per_frame": round(ms, 3), "fps": round(1e3 / ms, 2),
@@ -745,6 +745,7 @@ def main():
     ap.add_argument("--gate", type=int, default=0,
                     help="batched workloads: compare the first N scenes with FP64 single-scene runs")
     ap.add_argument("--fd-steps", type=int, default=10, help="material_id workload: steps of the FD check")
+    ap.add_argument("--frame-out", default=None, help="render workload: save the last frame (.npy) here")
     ap.add_argument("--sample", choices=["trajectory", "consecutive"], default="trajectory",
                     help="time K steps spread over the whole trajectory (default) or the K steps after the warm-up")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
