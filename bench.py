@@ -2,16 +2,21 @@
 """Benchmark of the IPC time step (Eq. 3) on B300: steps/s.
 
 One "step" is one call of sim_step: the whole Newton solve of one time step
-of the workload (culling, assembly, PCG, CCD, line search).  Inputs live in
-HBM; between timed steps the L2 is flushed by writing a 256 MB buffer outside
+of the workload (culling, assembly, PCG, CCD, line search).  The sampled steps
+are spread over the trajectory; one untimed pass runs it and saves the state
+before each of them, and each is then replayed from its state (a restarted
+step is bit-identical to the step in the trajectory).  Inputs live in HBM;
+before each timed step the L2 is flushed by writing a 256 MB buffer outside
 the timed events.  Each step is timed with CUDA events on the simulator's
 stream; `value` = steps / sum of step times (max over ranks for N > 1, each
-rank running its own replica: a single scene does not shard).
+rank running its own replica of a single scene, or its own shard of a batch).
 
-`e2e` replays the same steps (from the state saved before the timed steps)
-through the public API with host buffers: the kinematic transforms go host ->
-device and the positions come back to host memory every step, inside the
-timed region.
+Without a cached PCG launch shape, a single-scene workload first times every
+shape over the same replayed steps and keeps the fastest total.
+
+`e2e` replays the same steps through the public API with host buffers: the
+kinematic transforms go host -> device and the positions come back to host
+memory every step, inside the timed region.
 
 `--impl reference` times the plain FP64 CPU oracle on the same workload.
 """
